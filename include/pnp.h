@@ -1,0 +1,170 @@
+/*
+ * pnp.h — C ABI of the GB300 NS-PNP fractional-step library (libpnp.so).
+ *
+ * The library advances the coupled Navier-Stokes / Poisson-Nernst-Planck
+ * equations of arXiv:1701.02005 (Eqs. (1)-(4), Numerical methods) for plane
+ * Couette flow of a dilute binary univalent electrolyte: walls at y = -1, +1
+ * moving at -Uw, +Uw and held at potentials -V, +V; periodic x and z.
+ * Quantities are nondimensional with h (half gap), U (wall speed), h/U,
+ * c0 (bulk concentration), V_T (thermal voltage) and rho_w U^2 (pressure).
+ *
+ * Ownership: the caller allocates ONE device workspace (size from
+ * pnp_workspace_bytes) and keeps it alive until pnp_destroy; the context only
+ * borrows it.  Host memory of the context is freed by pnp_destroy.
+ * Streams: every kernel and copy is issued on the stream given to
+ * pnp_init_grid (a cudaStream_t passed as void*; NULL = legacy default
+ * stream, in which case steps are launched without CUDA graphs).
+ * Errors: every entry point returns PNP_OK (0) or a negative pnp_status
+ * code; nothing throws across the ABI.  There is no CPU fallback: without a
+ * CUDA device every call that launches work returns PNP_ERR_CUDA.
+ * Layout: all fields are [y][z][x] with x fastest.  Cell-centred fields have
+ * (Ny-1)*Nz*Nx entries; v lives on the y faces and has Ny*Nz*Nx entries
+ * whose first and last planes (the walls) are zero.  Ny counts y face nodes.
+ */
+#ifndef PNP_H
+#define PNP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pnp_ctx pnp_ctx;
+
+/* Status codes. */
+enum {
+  PNP_OK = 0,
+  PNP_ERR_ARG = -1,          /* null pointer, bad enum, non-finite parameter      */
+  PNP_ERR_GRID = -2,         /* Nx, Nz not powers of two in [4, 4096], Ny < 3     */
+  PNP_ERR_WORKSPACE = -3,    /* workspace too small or misaligned (256 B)         */
+  PNP_ERR_CUDA = -4,         /* a CUDA runtime call failed (no device, launch)    */
+  PNP_ERR_STATE = -5,        /* parameters or state not set yet                   */
+  PNP_ERR_NONFINITE = -6,    /* device check: NaN/Inf in a prognostic field       */
+  PNP_ERR_NEGATIVE_C = -7,   /* device check: a concentration went negative       */
+  PNP_ERR_UNSUPPORTED = -8   /* option not available for this precision          */
+};
+
+/* Arithmetic precision of a context. */
+enum {
+  PNP_FP64 = 0,   /* every field, stencil, FFT and solve in FP64                  */
+  PNP_MIXED = 1   /* u, v, w, p stencils and the pressure FFT in FP32; ions,
+                     potential, all tridiagonal solves and global sums in FP64    */
+};
+
+/* Fields for pnp_set_state / pnp_get_state / pnp_mean_profile. */
+enum {
+  PNP_U = 0, PNP_V = 1, PNP_W = 2, PNP_P = 3,
+  PNP_CP = 4, PNP_CM = 5, PNP_PHI = 6,       /* PHI is the total potential V y + phi */
+  PNP_HU = 7, PNP_HV = 8, PNP_HW = 9,        /* explicit terms of the last substage  */
+  PNP_HCP = 10, PNP_HCM = 11,
+  PNP_NFIELDS = 12
+};
+
+/* Initial conditions for pnp_init_state. */
+enum {
+  PNP_IC_LAMINAR = 0,  /* u = Uw y, uniform ions c+ = c- = 1                        */
+  PNP_IC_PB = 1        /* u = Uw y, superposed Gouy-Chapman double layers           */
+};
+
+/* Boundary condition of pnp_poisson. */
+enum { PNP_NEUMANN = 0, PNP_DIRICHLET = 1 };
+
+/* Diagnostics (Numerical methods: tau_w, c_f, Re_tau; Fig. 1: wall flux). */
+typedef struct pnp_diag {
+  double tau_bot;     /* (1/Re) d<u>/dy at y = -1 (plane average)                 */
+  double tau_top;     /* (1/Re) d<u>/dy at y = +1                                 */
+  double cf;          /* 2 tau_w / Uw^2, tau_w the mean of the two walls          */
+  double re_tau;      /* Re sqrt(tau_w)                                           */
+  double n_plus;      /* sum c+ dV                                                */
+  double n_minus;     /* sum c- dV                                                */
+  double net_charge;  /* n_plus - n_minus                                         */
+  double wall_flux;   /* total ion flux through the wall faces (zero by design)   */
+  double max_div;     /* max |div u| over the cells                               */
+  double ke;          /* kinetic energy 1/2 sum |u|^2 dV                          */
+  double time;        /* simulated time                                           */
+  long long nstep;    /* completed steps                                          */
+  int status;         /* device error word (PNP_OK or a PNP_ERR_* code)           */
+  int precision;
+} pnp_diag;
+
+/* Bytes of device workspace needed for an Nx x Ny x Nz grid (Ny = face nodes). */
+int pnp_workspace_bytes(int nx, int ny, int nz, int precision, size_t* out_bytes);
+
+/* Create a context on the grid of Fig. 1: Nx, Nz powers of two (periodic,
+ * lengths Lx, Lz), Ny y-face nodes with tanh stretching yf_j =
+ * tanh(g (2j/(Ny-1) - 1)) / tanh(g) (g = stretch; 0 = uniform).  The
+ * workspace (device, >= pnp_workspace_bytes, 256-byte aligned) is borrowed. */
+int pnp_init_grid(pnp_ctx** out, int nx, int ny, int nz, double Lx, double Lz,
+                  double stretch, int precision, void* device_workspace,
+                  size_t workspace_bytes, void* cuda_stream);
+
+/* Replace the y faces by Ny host values; y_faces[0] and y_faces[Ny-1] are
+ * forced to -1 and +1.  Invalidates the state. */
+int pnp_set_yfaces(pnp_ctx* ctx, const double* y_faces_host, int ny);
+
+/* Control parameters (Numerical methods): Re = rho_w U h / eta, debye_len =
+ * lambda_D / h, Sc = eta / (rho_w D), wall_potential = V / V_T (the paper's
+ * V-hat is 2 V), beta = eps V_T^2 / (eta D) (typically 0.5). */
+int pnp_set_params(pnp_ctx* ctx, double Re, double debye_len, double Sc,
+                   double wall_potential, double beta);
+
+/* Wall speed in units of U (default 1; 0 gives the quiescent validation run). */
+int pnp_set_wall_velocity(pnp_ctx* ctx, double Uw);
+
+/* Initial state on the device: Couette profile plus SplitMix64 noise of
+ * amplitude noise_amp damped by (1 - y^2) and projected to zero divergence;
+ * ions by ic_kind; Phi from Eq. (4); p = 0 and stored explicit terms zero. */
+int pnp_init_state(pnp_ctx* ctx, int ic_kind, uint64_t seed, double noise_amp);
+
+/* Copy one field in or out as FP64 values in the layout above (converted on
+ * the device in mixed precision).  on_device != 0: src/dst is a device
+ * pointer; otherwise host memory (pinned for asynchrony; get_state to host
+ * synchronises the stream). */
+int pnp_set_state(pnp_ctx* ctx, int field, const void* src, int on_device);
+int pnp_get_state(pnp_ctx* ctx, int field, void* dst, int on_device);
+
+/* Number of FP64 values of a field (cells or v faces). */
+int pnp_field_size(pnp_ctx* ctx, int field, size_t* out_count);
+
+/* Advance nsteps full RK3 steps of size dt (three substages each: explicit
+ * terms, y-implicit Crank-Nicolson solves, pressure projection, potential
+ * solve).  Asynchronous on the context's stream; on a non-default stream the
+ * step is captured once per dt into a CUDA graph and replayed. */
+int pnp_step(pnp_ctx* ctx, int nsteps, double dt);
+
+/* Deterministic FP64 reductions of the current state; synchronises the stream. */
+int pnp_diagnostics(pnp_ctx* ctx, pnp_diag* out);
+
+/* Plane average <q>(y) of a field into host memory (Ny-1 values, Ny for v). */
+int pnp_mean_profile(pnp_ctx* ctx, int field, double* out_host);
+
+/* Separable Poisson solve on the context's grid (Numerical methods, potential
+ * paragraph): (d_xx + d_zz + L_y) x = rhs with modified wavenumbers, real FFT
+ * in x and z and one Thomas solve in y per wavenumber.  PNP_NEUMANN: zero wall
+ * flux, mode (0,0) pinned to zero in its bottom cell; PNP_DIRICHLET: x = 0 on
+ * the wall faces.  rhs and x are device FP64 arrays of (Ny-1)*Nz*Nx values and
+ * may alias.  Uses the context's scratch; asynchronous. */
+int pnp_poisson(pnp_ctx* ctx, int bc, const double* rhs_dev, double* x_dev);
+
+/* Overwrite the stored explicit terms H (fields PNP_HU..PNP_HCM) with those of
+ * the current state (advection, x/z diffusion, Coulomb force, migration). */
+int pnp_eval_explicit(pnp_ctx* ctx);
+
+/* Device error word of the last diagnostics (synchronises). */
+int pnp_status(pnp_ctx* ctx);
+
+/* Measured FP64 FMA throughput of this device in FLOP/s (bounded microbenchmark
+ * on the context's stream): the ALU ceiling of the FP64 kernels. */
+int pnp_fp64_peak(pnp_ctx* ctx, double* flops_out);
+
+const char* pnp_error_string(int code);
+
+void pnp_destroy(pnp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PNP_H */

@@ -1,0 +1,130 @@
+"""ctypes binding of libpnp (include/pnp.h): same names, argument marshalling only.
+
+Every function here forwards to the C ABI; no step of the method runs in
+Python.  Importing this module raises if the library has not been built, so
+a missing extension fails loudly instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from .build import LIB
+
+PNP_OK = 0
+PNP_ERR_ARG = -1
+PNP_ERR_GRID = -2
+PNP_ERR_WORKSPACE = -3
+PNP_ERR_CUDA = -4
+PNP_ERR_STATE = -5
+PNP_ERR_NONFINITE = -6
+PNP_ERR_NEGATIVE_C = -7
+PNP_ERR_UNSUPPORTED = -8
+
+PNP_FP64 = 0
+PNP_MIXED = 1
+
+PNP_U, PNP_V, PNP_W, PNP_P, PNP_CP, PNP_CM, PNP_PHI = range(7)
+PNP_HU, PNP_HV, PNP_HW, PNP_HCP, PNP_HCM = range(7, 12)
+PNP_NFIELDS = 12
+
+PNP_IC_LAMINAR = 0
+PNP_IC_PB = 1
+
+PNP_NEUMANN = 0
+PNP_DIRICHLET = 1
+
+
+class pnp_diag(C.Structure):
+    _fields_ = [
+        ("tau_bot", C.c_double), ("tau_top", C.c_double), ("cf", C.c_double), ("re_tau", C.c_double),
+        ("n_plus", C.c_double), ("n_minus", C.c_double), ("net_charge", C.c_double),
+        ("wall_flux", C.c_double), ("max_div", C.c_double), ("ke", C.c_double), ("time", C.c_double),
+        ("nstep", C.c_longlong), ("status", C.c_int), ("precision", C.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = {
+    # name: (restype, argtypes)
+    "pnp_workspace_bytes": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "pnp_init_grid": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                C.c_double, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "pnp_set_yfaces": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int]),
+    "pnp_set_params": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "pnp_set_wall_velocity": (C.c_int, [C.c_void_p, C.c_double]),
+    "pnp_init_state": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_double]),
+    "pnp_set_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "pnp_get_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "pnp_field_size": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_size_t)]),
+    "pnp_step": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
+    "pnp_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(pnp_diag)]),
+    "pnp_mean_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    "pnp_poisson": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "pnp_eval_explicit": (C.c_int, [C.c_void_p]),
+    "pnp_status": (C.c_int, [C.c_void_p]),
+    "pnp_fp64_peak": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "pnp_error_string": (C.c_char_p, [C.c_int]),
+    "pnp_destroy": (None, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libpnp.so (built by ``paper_1701_02005_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libpnp not built ({path} missing): run paper_1701_02005_gb300.build.build_library()")
+    lib = C.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class PNPError(RuntimeError):
+    def __init__(self, code, where):
+        msg = load().pnp_error_string(code).decode()
+        super().__init__(f"{where}: {msg} ({code})")
+        self.code = code
+
+
+def check(code, where):
+    if code != PNP_OK:
+        raise PNPError(code, where)
+    return code
+
+
+def _fwd(name):
+    def f(*args):
+        return getattr(load(), name)(*args)
+    f.__name__ = name
+    return f
+
+
+pnp_workspace_bytes = _fwd("pnp_workspace_bytes")
+pnp_init_grid = _fwd("pnp_init_grid")
+pnp_set_yfaces = _fwd("pnp_set_yfaces")
+pnp_set_params = _fwd("pnp_set_params")
+pnp_set_wall_velocity = _fwd("pnp_set_wall_velocity")
+pnp_init_state = _fwd("pnp_init_state")
+pnp_set_state = _fwd("pnp_set_state")
+pnp_get_state = _fwd("pnp_get_state")
+pnp_field_size = _fwd("pnp_field_size")
+pnp_step = _fwd("pnp_step")
+pnp_diagnostics = _fwd("pnp_diagnostics")
+pnp_mean_profile = _fwd("pnp_mean_profile")
+pnp_poisson = _fwd("pnp_poisson")
+pnp_eval_explicit = _fwd("pnp_eval_explicit")
+pnp_status = _fwd("pnp_status")
+pnp_fp64_peak = _fwd("pnp_fp64_peak")
+pnp_error_string = _fwd("pnp_error_string")
+pnp_destroy = _fwd("pnp_destroy")

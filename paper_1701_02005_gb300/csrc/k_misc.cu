@@ -1,0 +1,252 @@
+// Initial condition, diagnostics and data movement for libpnp.
+//
+// Diagnostics follow the Numerical-methods definitions of arXiv:1701.02005:
+// wall shear tau_w = (1/Re) d<u>/dy from the plane-averaged profile, total
+// ion numbers (conserved: zero wall flux, Fig. 1 caption), net charge, max
+// divergence (Eq. (2)).  All sums are FP64 with a fixed reduction order
+// (deterministic across runs for a given grid).
+#include "pnp_common.cuh"
+
+namespace pnp {
+
+// SplitMix64 (Steele, Lea & Flood 2014) used as a counter-based generator:
+// output n of the stream seeded by `seed` is mix(seed + (n + 1) * gamma).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t n) {
+  uint64_t x = seed + (n + 1ull) * 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// Uniform value in [-1, 1) for counter (field << 40) + index.
+__device__ __forceinline__ double uniform_pm1(uint64_t seed, uint64_t field, uint64_t index) {
+  const uint64_t b = splitmix64(seed, (field << 40) + index) >> 11;
+  return (double)b * 0x1p-53 * 2.0 - 1.0;
+}
+
+template <typename TV>
+__global__ void k_init_centres(Fields<TV> f, Geo g, Metrics m, Phys ph, int ic_kind, double cb, double kappa,
+                               uint64_t seed, double amp) {
+  const size_t n = (size_t)g.nyc * g.nz * g.nx;
+  const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int j = (int)(c / ((size_t)g.nz * g.nx));
+  const double y = m.yc[j];
+  double u = ph.Uw * y, w = 0.0;
+  if (amp != 0.0) {
+    const double env = amp * (1.0 - y * y);
+    u = u + env * uniform_pm1(seed, 0, c);
+    w = w + env * uniform_pm1(seed, 2, c);
+  }
+  double cp = 1.0, cm = 1.0;
+  if (ic_kind == PNP_IC_PB && ph.V != 0.0) {
+    // superposed Gouy-Chapman layers of the walls at y = +1 (+V) and y = -1 (-V)
+    const double t = tanh(0.25 * ph.V);
+    const double Pgc = 4.0 * atanh(t * exp(-(1.0 - y) * kappa)) - 4.0 * atanh(t * exp(-(1.0 + y) * kappa));
+    cp = cb * exp(-Pgc);
+    cm = cb * exp(Pgc);
+  }
+  f.u[c] = (TV)u;
+  f.w[c] = (TV)w;
+  f.p[c] = (TV)0;
+  f.Hu[c] = (TV)0;
+  f.Hw[c] = (TV)0;
+  f.cp[c] = cp;
+  f.cm[c] = cm;
+  f.Hcp[c] = 0.0;
+  f.Hcm[c] = 0.0;
+}
+
+template <typename TV>
+__global__ void k_init_faces(Fields<TV> f, Geo g, const double* __restrict__ yf, uint64_t seed, double amp) {
+  const size_t n = (size_t)g.ny * g.nz * g.nx;
+  const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int j = (int)(c / ((size_t)g.nz * g.nx));
+  double v = 0.0;
+  if (amp != 0.0 && j > 0 && j < g.ny - 1) {
+    const double y = yf[j];
+    v = amp * (1.0 - y * y) * uniform_pm1(seed, 1, c);
+  }
+  f.v[c] = (TV)v;
+  f.Hv[c] = (TV)0;
+  f.rv[c] = (TV)0;
+}
+
+template <typename TV>
+cudaError_t launch_init_fields(const Fields<TV>& f, const Geo& g, const Metrics& m, const Phys& ph, int ic_kind,
+                               double cb, double kappa, uint64_t seed, double amp, const double* yf,
+                               cudaStream_t s) {
+  const size_t nc = (size_t)g.nyc * g.nz * g.nx, nv = (size_t)g.ny * g.nz * g.nx;
+  const int T = 256;
+  k_init_centres<TV><<<(unsigned)((nc + T - 1) / T), T, 0, s>>>(f, g, m, ph, ic_kind, cb, kappa, seed, amp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_init_faces<TV><<<(unsigned)((nv + T - 1) / T), T, 0, s>>>(f, g, yf, seed, amp);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics: per-block partial sums in a fixed order, then one block.
+// Slots: 0 sum u(j=0), 1 sum u(j=nyc-1), 2 sum c+ dy, 3 sum c- dy, 4 max|div|,
+// 5 sum (u^2 + w^2) dy + v^2 h, 6 count of non-finite values, 7 min(c+, c-).
+// ---------------------------------------------------------------------------
+constexpr int kDiagSlots = 8;
+constexpr int kDiagThreads = 256;
+
+__device__ __forceinline__ void block_reduce(double* sh, double* vals, int tid) {
+  // tree reduction of kDiagSlots values per thread; op: sum, except slot 4 (max) and 7 (min)
+  for (int q = 0; q < kDiagSlots; ++q) sh[q * kDiagThreads + tid] = vals[q];
+  __syncthreads();
+  for (int st = kDiagThreads / 2; st > 0; st >>= 1) {
+    if (tid < st) {
+      for (int q = 0; q < kDiagSlots; ++q) {
+        double a = sh[q * kDiagThreads + tid], b = sh[q * kDiagThreads + tid + st];
+        sh[q * kDiagThreads + tid] = q == 4 ? fmax(a, b) : (q == 7 ? fmin(a, b) : a + b);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Fields<TV> f, Geo g, Metrics m, double* partial) {
+  __shared__ double sh[kDiagSlots * kDiagThreads];
+  double acc[kDiagSlots] = {0, 0, 0, 0, 0, 0, 0, 1e300};
+  const size_t P = (size_t)g.nz * g.nx;
+  const size_t nc = (size_t)g.nyc * P, nv = (size_t)g.ny * P;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += stride) {
+    const int j = (int)(c / P);
+    const int rem = (int)(c - (size_t)j * P);
+    const int k = rem / g.nx, i = rem - k * g.nx;
+    const int ip = (i + 1 == g.nx) ? 0 : i + 1, kp = (k + 1 == g.nz) ? 0 : k + 1;
+    const double u = (double)f.u[c], w = (double)f.w[c];
+    const double cp = f.cp[c], cm = f.cm[c];
+    const double dy = 1.0 / m.idy[j];
+    if (j == 0) acc[0] += u;
+    if (j == g.nyc - 1) acc[1] += u;
+    acc[2] += cp * dy;
+    acc[3] += cm * dy;
+    const double div = ((double)f.u[cidx(j, k, ip, g.nz, g.nx)] - u) * g.idx +
+                       ((double)f.v[c + P] - (double)f.v[c]) * m.idy[j] +
+                       ((double)f.w[cidx(j, kp, i, g.nz, g.nx)] - w) * g.idz;
+    acc[4] = fmax(acc[4], fabs(div));
+    acc[5] += (u * u + w * w) * dy;
+    const double p = (double)f.p[c], Ph = f.Phi[c];
+    if (!isfinite(u) || !isfinite(w) || !isfinite(cp) || !isfinite(cm) || !isfinite(p) || !isfinite(Ph) ||
+        !isfinite(div))
+      acc[6] += 1.0;
+    acc[7] = fmin(acc[7], fmin(cp, cm));
+  }
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < nv; c += stride) {
+    const int j = (int)(c / P);
+    const double v = (double)f.v[c];
+    acc[5] += v * v / m.ih[j];
+    if (!isfinite(v)) acc[6] += 1.0;
+  }
+  block_reduce(sh, acc, threadIdx.x);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < kDiagSlots; ++q) partial[(size_t)blockIdx.x * kDiagSlots + q] = sh[q * kDiagThreads];
+}
+
+__global__ void __launch_bounds__(kDiagThreads) k_diag_final(const double* partial, int npartial, double* out,
+                                                            int* status) {
+  __shared__ double sh[kDiagSlots * kDiagThreads];
+  double acc[kDiagSlots] = {0, 0, 0, 0, 0, 0, 0, 1e300};
+  for (int b = threadIdx.x; b < npartial; b += blockDim.x) {
+    for (int q = 0; q < kDiagSlots; ++q) {
+      const double v = partial[(size_t)b * kDiagSlots + q];
+      acc[q] = q == 4 ? fmax(acc[q], v) : (q == 7 ? fmin(acc[q], v) : acc[q] + v);
+    }
+  }
+  block_reduce(sh, acc, threadIdx.x);
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kDiagSlots; ++q) out[q] = sh[q * kDiagThreads];
+    int st = PNP_OK;
+    if (sh[6 * kDiagThreads] > 0.0) st = PNP_ERR_NONFINITE;
+    else if (sh[7 * kDiagThreads] < 0.0) st = PNP_ERR_NEGATIVE_C;
+    *status = st;
+  }
+}
+
+template <typename TV>
+cudaError_t launch_diagnostics(const Fields<TV>& f, const Geo& g, const Metrics& m, const Phys& ph,
+                               double* partial, int npartial, double* out, int* status, cudaStream_t s) {
+  (void)ph;
+  k_diag_partial<TV><<<npartial, kDiagThreads, 0, s>>>(f, g, m, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_diag_final<<<1, kDiagThreads, 0, s>>>(partial, npartial, out, status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+template <typename TA, typename TB>
+__global__ void k_convert(const TA* __restrict__ a, TB* __restrict__ b, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (TB)a[i];
+}
+
+template <typename TA, typename TB>
+cudaError_t launch_convert(const TA* a, TB* b, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int T = 256;
+  k_convert<TA, TB><<<(unsigned)((n + T - 1) / T), T, 0, s>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+// Plane mean of q over plane `plane` (block per plane when plane < 0).
+template <typename TQ>
+__global__ void k_mean_profile(const TQ* __restrict__ q, size_t P, double* out) {
+  __shared__ double sh[256];
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  for (size_t c = threadIdx.x; c < P; c += blockDim.x) acc += (double)q[(size_t)j * P + c];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = sh[0] / (double)P;
+}
+
+template <typename TQ>
+cudaError_t launch_mean_profile(const TQ* q, int nplanes, int plane_size, double* out, cudaStream_t s) {
+  k_mean_profile<TQ><<<nplanes, 256, 0, s>>>(q, (size_t)plane_size, out);
+  return cudaGetLastError();
+}
+
+// FP64 FMA throughput probe: 8 independent dependency chains per thread.
+__global__ void k_fp64_probe(double* out, int iters) {
+  double x0 = threadIdx.x * 1e-3, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
+  double x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+  const double a = 0.999, b = 1e-3;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+cudaError_t launch_fp64_probe(double* out, int iters, int blocks, cudaStream_t s) {
+  k_fp64_probe<<<blocks, 256, 0, s>>>(out, iters);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_init_fields<double>(const Fields<double>&, const Geo&, const Metrics&, const Phys&, int,
+                                                double, double, uint64_t, double, const double*, cudaStream_t);
+template cudaError_t launch_init_fields<float>(const Fields<float>&, const Geo&, const Metrics&, const Phys&, int,
+                                               double, double, uint64_t, double, const double*, cudaStream_t);
+template cudaError_t launch_diagnostics<double>(const Fields<double>&, const Geo&, const Metrics&, const Phys&,
+                                                double*, int, double*, int*, cudaStream_t);
+template cudaError_t launch_diagnostics<float>(const Fields<float>&, const Geo&, const Metrics&, const Phys&,
+                                               double*, int, double*, int*, cudaStream_t);
+template cudaError_t launch_convert<double, double>(const double*, double*, size_t, cudaStream_t);
+template cudaError_t launch_convert<double, float>(const double*, float*, size_t, cudaStream_t);
+template cudaError_t launch_convert<float, double>(const float*, double*, size_t, cudaStream_t);
+template cudaError_t launch_mean_profile<double>(const double*, int, int, double*, cudaStream_t);
+template cudaError_t launch_mean_profile<float>(const float*, int, int, double*, cudaStream_t);
+
+}  // namespace pnp

@@ -1,0 +1,415 @@
+// Linear solves of the fractional step (arXiv:1701.02005, Numerical methods):
+//  * wall-normal Crank-Nicolson solves (Thomas) for u, v, w and c+- ;
+//  * the separable Poisson solver of the potential paragraph: real FFT in x,
+//    complex FFT in z, one Thomas solve in y per wavenumber pair, inverse
+//    FFTs; used for the pressure correction (Neumann) and the potential
+//    perturbation phi (Dirichlet);
+//  * the projection u = u_hat - alp dt grad(Phi_p), p += Phi_p.
+//
+// FFTs are radix-2 Stockham autosort transforms in shared memory (Stockham
+// 1966; the formulation of Govindaraju et al., SC 2008).  A length-N real row
+// is transformed as a length-N/2 complex sequence z_t = x_2t + i x_2t+1 and
+// split into the N/2 + 1 non-negative frequencies.  Forward transforms carry
+// no normalisation; the spectral solve multiplies by 1/(Nx Nz).
+#include "pnp_common.cuh"
+
+namespace pnp {
+
+// ---------------------------------------------------------------------------
+// Crank-Nicolson y-solves.  One thread per (i, k) line; lines are consecutive
+// in x so every plane access is coalesced.  The matrix I - s L_y is the same
+// for every line, so its elimination factors (a, c, m) come precomputed.
+// ---------------------------------------------------------------------------
+template <typename TQ, typename TR>
+__global__ void k_cn_thomas(TQ* __restrict__ q0, TR* __restrict__ r0, TQ* __restrict__ q1,
+                            TR* __restrict__ r1, TQ* __restrict__ q2, TR* __restrict__ r2,
+                            CNRows rows0, CNRows rows1, CNRows rows2, int n0, int n1, int n2,
+                            int j00, int j01, int j02, size_t P) {
+  const size_t line = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (line >= P) return;
+  TQ* q;
+  TR* r;
+  CNRows rw;
+  int n, j0;
+  if (blockIdx.y == 0) { q = q0; r = r0; rw = rows0; n = n0; j0 = j00; }
+  else if (blockIdx.y == 1) { q = q1; r = r1; rw = rows1; n = n1; j0 = j01; }
+  else { q = q2; r = r2; rw = rows2; n = n2; j0 = j02; }
+  TR* rl = r + (size_t)j0 * P + line;
+  TQ* ql = q + (size_t)j0 * P + line;
+  double d = 0.0;
+  for (int j = 0; j < n; ++j) {
+    d = ((double)rl[(size_t)j * P] - rw.a[j] * d) * rw.m[j];
+    rl[(size_t)j * P] = (TR)d;
+  }
+  double x = 0.0;
+  for (int j = n - 1; j >= 0; --j) {
+    x = (double)rl[(size_t)j * P] - rw.c[j] * x;
+    ql[(size_t)j * P] = (TQ)((double)ql[(size_t)j * P] + x);
+  }
+}
+
+template <typename TV>
+cudaError_t launch_cn_solves(const Fields<TV>& f, const Geo& g, const CNRows& vel, const CNRows& face,
+                             const CNRows& ion, cudaStream_t s) {
+  const size_t P = (size_t)g.nz * g.nx;
+  const int T = 128;
+  dim3 grd((unsigned)((P + T - 1) / T), 3, 1);
+  // u, w: nyc cells from plane 0; v: the nyc-1 interior faces from plane 1
+  k_cn_thomas<TV, TV><<<grd, T, 0, s>>>(f.u, f.ru, f.v, f.rv, f.w, f.rw, vel, face, vel, g.nyc,
+                                        g.nyc - 1, g.nyc, 0, 1, 0, P);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dim3 grd2((unsigned)((P + T - 1) / T), 2, 1);
+  k_cn_thomas<double, double><<<grd2, T, 0, s>>>(f.cp, f.rcp, f.cm, f.rcm, f.cm, f.rcm, ion, ion, ion,
+                                                 g.nyc, g.nyc, g.nyc, 0, 0, 0, P);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory Stockham radix-2 FFT of one sequence of length N (power of
+// two) between buffers x and y; nt threads cooperate, this one is t0.
+// tw[t] = exp(-2 pi i t / N).  Returns the buffer that holds the result.
+// Every thread of the block must call it (it synchronises the block).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ cplx<T>* stockham(cplx<T>* x, cplx<T>* y, int N, const cplx<T>* __restrict__ tw, bool inverse,
+                             int t0, int nt) {
+  const int half = N >> 1;
+  for (int Ns = 1; Ns < N; Ns <<= 1) {
+    const int tstride = N / (2 * Ns);
+    for (int jj = t0; jj < half; jj += nt) {
+      const int k = jj & (Ns - 1);
+      cplx<T> w = tw[k * tstride];
+      if (inverse) w.y = -w.y;
+      const cplx<T> a0 = x[jj];
+      const cplx<T> a1 = cmul(x[jj + half], w);
+      const int d = ((jj - k) << 1) + k;
+      y[d] = cadd(a0, a1);
+      y[d + Ns] = csub(a0, a1);
+    }
+    __syncthreads();
+    cplx<T>* t = x;
+    x = y;
+    y = t;
+  }
+  return x;
+}
+
+// Source of the forward x-transform: one real value at (j, k, i).
+template <typename T, typename TV>
+struct SrcArgs {
+  PoissonSrc kind;
+  const TV *u, *v, *w;
+  const double *cp, *cm;
+  const T* plain;
+  double scale;
+};
+
+template <typename T, typename TV>
+__device__ __forceinline__ T src_value(const SrcArgs<T, TV>& a, const Geo& g, const Metrics& m, int j,
+                                       int k, int i) {
+  const size_t c = cidx(j, k, i, g.nz, g.nx);
+  if (a.kind == PoissonSrc::Divergence) {
+    // div(u_hat) / (alp dt): finite-volume form of Eq. (2)
+    const int ip = (i + 1 == g.nx) ? 0 : i + 1;
+    const int kp = (k + 1 == g.nz) ? 0 : k + 1;
+    const double du = ((double)a.u[cidx(j, k, ip, g.nz, g.nx)] - (double)a.u[c]) * g.idx;
+    const double dv = ((double)a.v[c + (size_t)g.nz * g.nx] - (double)a.v[c]) * m.idy[j];
+    const double dw = ((double)a.w[cidx(j, kp, i, g.nz, g.nx)] - (double)a.w[c]) * g.idz;
+    return (T)((du + dv + dw) * a.scale);
+  } else if (a.kind == PoissonSrc::Charge) {
+    // Eq. (4): -(c+ - c-) / (2 lam^2)
+    return (T)(-(a.cp[c] - a.cm[c]) * a.scale);
+  }
+  return a.plain[c];
+}
+
+// Forward x-transform of rows (j, k): blockDim = (TX, RY); one row per threadIdx.y.
+template <typename T, typename TV>
+__global__ void k_fft_x_fwd(SrcArgs<T, TV> src, Geo g, Metrics m, cplx<T>* __restrict__ spec,
+                            const cplx<T>* __restrict__ tw_half, const cplx<T>* __restrict__ tw_post) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int Lh = g.nx >> 1;
+  const int nrows = g.nyc * g.nz;
+  const int row = blockIdx.x * blockDim.y + threadIdx.y;
+  cplx<T>* xa = sm + (size_t)threadIdx.y * 2 * Lh;
+  cplx<T>* xb = xa + Lh;
+  const bool live = row < nrows;
+  const int j = live ? row / g.nz : 0, k = live ? row % g.nz : 0;
+  for (int t = threadIdx.x; t < Lh; t += blockDim.x) {
+    cplx<T> z = {T(0), T(0)};
+    if (live) z = {src_value(src, g, m, j, k, 2 * t), src_value(src, g, m, j, k, 2 * t + 1)};
+    xa[t] = z;
+  }
+  __syncthreads();
+  cplx<T>* Z = stockham(xa, xb, Lh, tw_half, false, threadIdx.x, blockDim.x);
+  if (!live) return;
+  cplx<T>* out = spec + (size_t)row * g.mp;
+  for (int mm = threadIdx.x; mm <= Lh; mm += blockDim.x) {
+    const cplx<T> zm = Z[mm == Lh ? 0 : mm];
+    const cplx<T> zc = cconj(Z[(Lh - mm) == Lh ? 0 : (Lh - mm)]);
+    const cplx<T> E = {T(0.5) * (zm.x + zc.x), T(0.5) * (zm.y + zc.y)};
+    const cplx<T> dd = csub(zm, zc);
+    const cplx<T> O = {T(0.5) * dd.y, T(-0.5) * dd.x};   // (zm - zc) / (2i)
+    out[mm] = cadd(E, cmul(tw_post[mm], O));
+  }
+}
+
+template <typename T>
+static void fft_x_shape(const Geo& g, dim3& blk, dim3& grd, size_t& smem) {
+  const int Lh = g.nx >> 1;
+  int tx = Lh / 2 < 1 ? 1 : Lh / 2;
+  if (tx > 128) tx = 128;
+  int ry = 128 / tx;
+  if (ry < 1) ry = 1;
+  const int nrows = g.nyc * g.nz;
+  blk = dim3(tx, ry, 1);
+  grd = dim3((nrows + ry - 1) / ry, 1, 1);
+  smem = (size_t)ry * 2 * Lh * sizeof(cplx<T>);
+}
+
+template <typename T, typename TV>
+cudaError_t launch_fft_x_fwd(PoissonSrc kind, const TV* u, const TV* v, const TV* w, const double* cp,
+                             const double* cm, const T* plain, double scale, const Geo& g,
+                             const Metrics& m, cplx<T>* spec, const cplx<T>* tw_half,
+                             const cplx<T>* tw_post, cudaStream_t s) {
+  SrcArgs<T, TV> a{kind, u, v, w, cp, cm, plain, scale};
+  dim3 blk, grd;
+  size_t smem;
+  fft_x_shape<T>(g, blk, grd, smem);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_fft_x_fwd<T, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_fft_x_fwd<T, TV><<<grd, blk, smem, s>>>(a, g, m, spec, tw_half, tw_post);
+  return cudaGetLastError();
+}
+
+// Inverse x-transform (complex N/2+1 -> real N), times N (no normalisation).
+template <typename T, typename TO>
+__global__ void k_fft_x_inv(PoissonDst dst, const cplx<T>* __restrict__ spec, Geo g, Metrics m,
+                            const cplx<T>* __restrict__ tw_half, const cplx<T>* __restrict__ tw_post,
+                            double V, TO* __restrict__ out) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int Lh = g.nx >> 1;
+  const int nrows = g.nyc * g.nz;
+  const int row = blockIdx.x * blockDim.y + threadIdx.y;
+  cplx<T>* xa = sm + (size_t)threadIdx.y * 2 * Lh;
+  cplx<T>* xb = xa + Lh;
+  const bool live = row < nrows;
+  const cplx<T>* in = spec + (size_t)(live ? row : 0) * g.mp;
+  for (int mm = threadIdx.x; mm < Lh; mm += blockDim.x) {
+    cplx<T> z = {T(0), T(0)};
+    if (live) {
+      const cplx<T> Xm = in[mm];
+      const cplx<T> Xc = cconj(in[Lh - mm]);
+      const cplx<T> sum = cadd(Xm, Xc);
+      const cplx<T> dif = csub(Xm, Xc);
+      const cplx<T> t = cmul(cconj(tw_post[mm]), dif);
+      z = {sum.x - t.y, sum.y + t.x};   // sum + i * t
+    }
+    xa[mm] = z;
+  }
+  __syncthreads();
+  cplx<T>* Z = stockham(xa, xb, Lh, tw_half, true, threadIdx.x, blockDim.x);
+  if (!live) return;
+  const int j = row / g.nz;
+  const size_t base = (size_t)row * g.nx;
+  const double add = dst == PoissonDst::Potential ? V * m.yc[j] : 0.0;
+  for (int t = threadIdx.x; t < Lh; t += blockDim.x) {
+    const cplx<T> z = Z[t];
+    if (dst == PoissonDst::Potential) {
+      out[base + 2 * t] = (TO)(add + (double)z.x);
+      out[base + 2 * t + 1] = (TO)(add + (double)z.y);
+    } else {
+      out[base + 2 * t] = (TO)z.x;
+      out[base + 2 * t + 1] = (TO)z.y;
+    }
+  }
+}
+
+template <typename T, typename TO>
+cudaError_t launch_fft_x_inv(PoissonDst dst, const cplx<T>* spec, const Geo& g, const Metrics& m,
+                             const cplx<T>* tw_half, const cplx<T>* tw_post, double V, TO* out,
+                             cudaStream_t s) {
+  dim3 blk, grd;
+  size_t smem;
+  fft_x_shape<T>(g, blk, grd, smem);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_fft_x_inv<T, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_fft_x_inv<T, TO><<<grd, blk, smem, s>>>(dst, spec, g, m, tw_half, tw_post, V, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// z-transform of spectral columns: a block loads TM consecutive m-columns of
+// one y-plane (TM complex values contiguous per z-row), transforms each
+// column of length Nz in shared memory and writes it back in place.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_fft_z(cplx<T>* __restrict__ spec, const cplx<T>* __restrict__ tw_z, Geo g, bool inverse) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int TM = blockDim.x;
+  const int nz = g.nz;
+  const int m0 = blockIdx.x * TM;
+  const int j = blockIdx.y;
+  const int tm = threadIdx.x;
+  const int stride = nz + 1;   // padding against bank conflicts
+  cplx<T>* xa = sm + (size_t)tm * stride;
+  cplx<T>* xb = sm + (size_t)TM * stride + (size_t)tm * stride;
+  const int m = m0 + tm;
+  const bool live = m < g.mh;
+  cplx<T>* plane = spec + (size_t)j * nz * g.mp;
+  for (int n = threadIdx.y; n < nz; n += blockDim.y) {
+    cplx<T> z = {T(0), T(0)};
+    if (live) z = plane[(size_t)n * g.mp + m];
+    xa[n] = z;
+  }
+  __syncthreads();
+  cplx<T>* Z = stockham(xa, xb, nz, tw_z, inverse, threadIdx.y, blockDim.y);
+  if (!live) return;
+  for (int n = threadIdx.y; n < nz; n += blockDim.y) plane[(size_t)n * g.mp + m] = Z[n];
+}
+
+template <typename T>
+cudaError_t launch_fft_z(cplx<T>* spec, const cplx<T>* tw_z, const Geo& g, bool inverse, cudaStream_t s) {
+  const int TM = 8;
+  int ty = g.nz / 2;
+  if (ty > 32) ty = 32;
+  if (ty < 1) ty = 1;
+  dim3 blk(TM, ty, 1);
+  dim3 grd((g.mh + TM - 1) / TM, g.nyc, 1);
+  const size_t smem = (size_t)2 * TM * (g.nz + 1) * sizeof(cplx<T>);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_fft_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_fft_z<T><<<grd, blk, smem, s>>>(spec, tw_z, g, inverse);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Spectral Thomas: per (m, n), solve a_j x_{j-1} + (b_j - kx2_m - kz2_n) x_j
+// + c_j x_{j+1} = scale * rhs_j in FP64.  The Neumann (0,0) mode replaces its
+// bottom-row equation by x_0 = 0.  The elimination multipliers c'_j go to the
+// FP64 scratch (one value per spectral point).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_spec_thomas(cplx<T>* __restrict__ spec, double* __restrict__ cpr, const double* __restrict__ kx2,
+                              const double* __restrict__ kz2, YRows rows, Geo g, double scale, bool neumann) {
+  const int mm = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.y;
+  if (mm >= g.mh) return;
+  const size_t P = (size_t)g.nz * g.mp;
+  const size_t base = (size_t)n * g.mp + mm;
+  const double k2 = kx2[mm] + kz2[n];
+  const bool pin = neumann && mm == 0 && n == 0;
+  double cprev = 0.0, dre = 0.0, dim = 0.0;
+  for (int j = 0; j < g.nyc; ++j) {
+    const size_t o = base + (size_t)j * P;
+    const cplx<T> r = spec[o];
+    double a = rows.a[j], b = rows.b[j] - k2, c = rows.c[j];
+    double rre = (double)r.x * scale, rim = (double)r.y * scale;
+    if (pin && j == 0) { b = 1.0; c = 0.0; rre = 0.0; rim = 0.0; }
+    const double inv = 1.0 / (b - a * cprev);
+    cprev = c * inv;
+    dre = (rre - a * dre) * inv;
+    dim = (rim - a * dim) * inv;
+    cpr[o] = cprev;
+    spec[o] = {(T)dre, (T)dim};
+  }
+  double xre = dre, xim = dim;
+  for (int j = g.nyc - 2; j >= 0; --j) {
+    const size_t o = base + (size_t)j * P;
+    const cplx<T> d = spec[o];
+    const double cj = cpr[o];
+    xre = (double)d.x - cj * xre;
+    xim = (double)d.y - cj * xim;
+    spec[o] = {(T)xre, (T)xim};
+  }
+}
+
+template <typename T>
+cudaError_t launch_spec_thomas(cplx<T>* spec, double* scratch, const double* kx2, const double* kz2,
+                               const YRows& rows, const Geo& g, double scale, bool neumann, cudaStream_t s) {
+  const int T_ = 64;
+  dim3 grd((g.mh + T_ - 1) / T_, g.nz, 1);
+  k_spec_thomas<T><<<grd, T_, 0, s>>>(spec, scratch, kx2, kz2, rows, g, scale, neumann);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Projection: u -= scale d(phip)/dx, w -= scale d(phip)/dz, v -= scale
+// d(phip)/dy on interior faces; optionally p += phip.
+// ---------------------------------------------------------------------------
+template <typename TV, typename TS>
+__global__ void k_project(TV* __restrict__ u, TV* __restrict__ v, TV* __restrict__ w, TV* __restrict__ p,
+                          const TS* __restrict__ s, double scale, bool update_p, Geo g, Metrics m) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y * blockDim.y + threadIdx.y;
+  const int j = blockIdx.z;
+  if (i >= g.nx || k >= g.nz) return;
+  const int im = i ? i - 1 : g.nx - 1;
+  const int km = k ? k - 1 : g.nz - 1;
+  const size_t c = cidx(j, k, i, g.nz, g.nx);
+  const double s0 = (double)s[c];
+  u[c] = (TV)((double)u[c] - scale * (s0 - (double)s[cidx(j, k, im, g.nz, g.nx)]) * g.idx);
+  w[c] = (TV)((double)w[c] - scale * (s0 - (double)s[cidx(j, km, i, g.nz, g.nx)]) * g.idz);
+  if (j > 0) v[c] = (TV)((double)v[c] - scale * (s0 - (double)s[c - (size_t)g.nz * g.nx]) * m.ih[j]);
+  if (update_p) p[c] = (TV)((double)p[c] + s0);
+}
+
+template <typename TV, typename TS>
+cudaError_t launch_project(TV* u, TV* v, TV* w, TV* p, const TS* phip, double scale, bool update_p,
+                           const Geo& g, const Metrics& m, cudaStream_t s) {
+  dim3 blk(32, 4, 1);
+  dim3 grd((g.nx + 31) / 32, (g.nz + 3) / 4, g.nyc);
+  k_project<TV, TS><<<grd, blk, 0, s>>>(u, v, w, p, phip, scale, update_p, g, m);
+  return cudaGetLastError();
+}
+
+// ---- explicit instantiations ----
+template cudaError_t launch_cn_solves<double>(const Fields<double>&, const Geo&, const CNRows&, const CNRows&,
+                                              const CNRows&, cudaStream_t);
+template cudaError_t launch_cn_solves<float>(const Fields<float>&, const Geo&, const CNRows&, const CNRows&,
+                                             const CNRows&, cudaStream_t);
+
+template cudaError_t launch_fft_x_fwd<double, double>(PoissonSrc, const double*, const double*, const double*,
+                                                      const double*, const double*, const double*, double,
+                                                      const Geo&, const Metrics&, cplx<double>*,
+                                                      const cplx<double>*, const cplx<double>*, cudaStream_t);
+template cudaError_t launch_fft_x_fwd<float, float>(PoissonSrc, const float*, const float*, const float*,
+                                                    const double*, const double*, const float*, double,
+                                                    const Geo&, const Metrics&, cplx<float>*,
+                                                    const cplx<float>*, const cplx<float>*, cudaStream_t);
+template cudaError_t launch_fft_x_fwd<double, float>(PoissonSrc, const float*, const float*, const float*,
+                                                     const double*, const double*, const double*, double,
+                                                     const Geo&, const Metrics&, cplx<double>*,
+                                                     const cplx<double>*, const cplx<double>*, cudaStream_t);
+
+template cudaError_t launch_fft_z<double>(cplx<double>*, const cplx<double>*, const Geo&, bool, cudaStream_t);
+template cudaError_t launch_fft_z<float>(cplx<float>*, const cplx<float>*, const Geo&, bool, cudaStream_t);
+
+template cudaError_t launch_spec_thomas<double>(cplx<double>*, double*, const double*, const double*,
+                                                const YRows&, const Geo&, double, bool, cudaStream_t);
+template cudaError_t launch_spec_thomas<float>(cplx<float>*, double*, const double*, const double*,
+                                               const YRows&, const Geo&, double, bool, cudaStream_t);
+
+template cudaError_t launch_fft_x_inv<double, double>(PoissonDst, const cplx<double>*, const Geo&, const Metrics&,
+                                                      const cplx<double>*, const cplx<double>*, double, double*,
+                                                      cudaStream_t);
+template cudaError_t launch_fft_x_inv<float, float>(PoissonDst, const cplx<float>*, const Geo&, const Metrics&,
+                                                    const cplx<float>*, const cplx<float>*, double, float*,
+                                                    cudaStream_t);
+
+template cudaError_t launch_project<double, double>(double*, double*, double*, double*, const double*, double, bool,
+                                                    const Geo&, const Metrics&, cudaStream_t);
+template cudaError_t launch_project<float, float>(float*, float*, float*, float*, const float*, double, bool,
+                                                  const Geo&, const Metrics&, cudaStream_t);
+
+}  // namespace pnp

@@ -1,0 +1,716 @@
+// C ABI of libpnp (declared in include/pnp.h): context set-up, workspace
+// carving, host-side precomputation of grid metrics / elimination factors /
+// FFT tables, and the orchestration of one fractional step
+// (arXiv:1701.02005, Numerical methods):
+//   per RK3 substage l:  explicit terms -> y-implicit CN solves ->
+//   pressure Poisson (Neumann) + projection -> potential Poisson (Dirichlet).
+// A step is captured once per dt into a CUDA graph on non-default streams.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pnp_common.cuh"
+
+using namespace pnp;
+
+namespace {
+
+// Low-storage RK3 coefficients (Rai & Moin 1991); alpha = gamma + zeta.
+const double kGam[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+const double kZet[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
+
+constexpr size_t kAlign = 256;
+constexpr int kDiagBlocks = 304;   // 2 x 152 SMs
+constexpr int kProbeBlocks = 152 * 8;
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+struct Bump {
+  char* base;
+  size_t off = 0;
+  template <typename T> T* take(size_t count) {
+    off = (off + kAlign - 1) / kAlign * kAlign;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+}  // namespace
+
+struct pnp_ctx {
+  Geo g{};
+  int precision = PNP_FP64;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  size_t nc = 0, nv = 0;
+  // prognostic + work fields; velocity-type arrays are double (FP64) or float (MIXED)
+  void *u, *v, *w, *p, *Hu, *Hv, *Hw, *ru, *rv, *rw;
+  double *cp, *cm, *Phi, *Hcp, *Hcm, *rcp, *rcm;
+  double* sreal;   // real scratch: Phi_p, spectral elimination multipliers
+  void* spec;      // spectral buffer, (nyc, nz, mp) complex (FP64-sized)
+  double* stage;   // conversion staging, nv values
+  // per-y metrics (device) and their host copies
+  double *yf_d, *yc_d, *idy_d, *ih_d, *lo_c_d, *hi_c_d, *lo_f_d, *hi_f_d, *wl_d, *wu_d;
+  double *kx2_d, *kz2_d;
+  double *rowsN_d, *rowsD_d;   // a, b, c of the Neumann / Dirichlet y-operator (3 * nyc)
+  double* cn_d;                // [3 substages][3 kinds][a, c, m][ny]
+  void *twx_d, *twp_d, *twz_d;      // complex<double> tables
+  void *twx_f, *twp_f, *twz_f;      // complex<float> tables
+  double* diag_partial;
+  double* diag_out;
+  int* status_d;
+  double* probe_d;
+  std::vector<double> yf, yc, dy, h, cn_h;
+  Phys ph{};
+  double Re = 0, lam = 0, Sc = 1, beta = 0.5;
+  bool have_params = false, have_state = false;
+  double time = 0.0;
+  long long nstep = 0;
+  cudaGraphExec_t gexec = nullptr;
+  double graph_dt = NAN;
+  double cn_dt = NAN;
+};
+
+namespace {
+
+size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
+  Bump b{base};
+  const int nyc = ny - 1;
+  const int mh = nx / 2 + 1;
+  const int mp = (mh + 7) / 8 * 8;
+  const size_t nc = (size_t)nyc * nz * nx, nv = (size_t)ny * nz * nx;
+  const size_t tv = precision == PNP_FP64 ? sizeof(double) : sizeof(float);
+  const size_t nspec = (size_t)nyc * nz * mp;
+  auto vel = [&](size_t n) { return b.take<char>(n * tv); };
+  void *u = vel(nc), *w = vel(nc), *p = vel(nc), *Hu = vel(nc), *Hw = vel(nc), *ru = vel(nc), *rw = vel(nc);
+  void *v = vel(nv), *Hv = vel(nv), *rv = vel(nv);
+  double *cp = b.take<double>(nc), *cm = b.take<double>(nc), *Phi = b.take<double>(nc);
+  double *Hcp = b.take<double>(nc), *Hcm = b.take<double>(nc), *rcp = b.take<double>(nc), *rcm = b.take<double>(nc);
+  double* sreal = b.take<double>(nspec > nc ? nspec : nc);
+  void* spec = b.take<cplx<double>>(nspec);
+  double* stage = b.take<double>(nv);
+  double *yf = b.take<double>(ny), *yc = b.take<double>(ny), *idy = b.take<double>(ny), *ih = b.take<double>(ny);
+  double *lo_c = b.take<double>(ny), *hi_c = b.take<double>(ny), *lo_f = b.take<double>(ny), *hi_f = b.take<double>(ny);
+  double *wl = b.take<double>(ny), *wu = b.take<double>(ny);
+  double *kx2 = b.take<double>(mp), *kz2 = b.take<double>(nz);
+  double *rowsN = b.take<double>(3 * (size_t)ny), *rowsD = b.take<double>(3 * (size_t)ny);
+  double* cn = b.take<double>(27 * (size_t)ny);
+  void *twx = b.take<cplx<double>>(nx / 2), *twp = b.take<cplx<double>>(nx / 2 + 1), *twz = b.take<cplx<double>>(nz);
+  void *twxf = b.take<cplx<float>>(nx / 2), *twpf = b.take<cplx<float>>(nx / 2 + 1), *twzf = b.take<cplx<float>>(nz);
+  double* dpart = b.take<double>((size_t)kDiagBlocks * 8);
+  double* dout = b.take<double>(8);
+  int* st = b.take<int>(4);
+  double* probe = b.take<double>((size_t)kProbeBlocks * 256);
+  if (c) {
+    c->u = u; c->v = v; c->w = w; c->p = p; c->Hu = Hu; c->Hv = Hv; c->Hw = Hw; c->ru = ru; c->rv = rv; c->rw = rw;
+    c->cp = cp; c->cm = cm; c->Phi = Phi; c->Hcp = Hcp; c->Hcm = Hcm; c->rcp = rcp; c->rcm = rcm;
+    c->sreal = sreal; c->spec = spec; c->stage = stage;
+    c->yf_d = yf; c->yc_d = yc; c->idy_d = idy; c->ih_d = ih; c->lo_c_d = lo_c; c->hi_c_d = hi_c;
+    c->lo_f_d = lo_f; c->hi_f_d = hi_f; c->wl_d = wl; c->wu_d = wu; c->kx2_d = kx2; c->kz2_d = kz2;
+    c->rowsN_d = rowsN; c->rowsD_d = rowsD; c->cn_d = cn;
+    c->twx_d = twx; c->twp_d = twp; c->twz_d = twz; c->twx_f = twxf; c->twp_f = twpf; c->twz_f = twzf;
+    c->diag_partial = dpart; c->diag_out = dout; c->status_d = st; c->probe_d = probe;
+    c->g.mh = mh;
+    c->g.mp = mp;
+    c->nc = nc;
+    c->nv = nv;
+  }
+  return b.off + kAlign;
+}
+
+int check_grid(int nx, int ny, int nz) {
+  if (!is_pow2(nx) || !is_pow2(nz) || nx < 4 || nz < 4 || nx > 4096 || nz > 4096 || ny < 3 || ny > 65536)
+    return PNP_ERR_GRID;
+  return PNP_OK;
+}
+
+#define CK(...)                                          \
+  do {                                                   \
+    if ((__VA_ARGS__) != cudaSuccess) return PNP_ERR_CUDA; \
+  } while (0)
+
+Metrics metrics(const pnp_ctx* c) {
+  return Metrics{c->yc_d, c->idy_d, c->ih_d, c->lo_c_d, c->hi_c_d, c->lo_f_d, c->hi_f_d, c->wl_d, c->wu_d};
+}
+
+// Grid metrics and the y-operator rows (finite-volume forms of Fig. 1).
+int upload_metrics(pnp_ctx* c) {
+  const int ny = c->g.ny, nyc = c->g.nyc;
+  std::vector<double>& yf = c->yf;
+  yf[0] = -1.0;
+  yf[ny - 1] = 1.0;
+  c->yc.assign(nyc, 0.0);
+  c->dy.assign(nyc, 0.0);
+  c->h.assign(ny, 0.0);
+  for (int j = 0; j < nyc; ++j) {
+    c->dy[j] = yf[j + 1] - yf[j];
+    c->yc[j] = 0.5 * (yf[j] + yf[j + 1]);
+  }
+  for (int j = 0; j < nyc; ++j)
+    if (!(c->dy[j] > 0.0)) return PNP_ERR_GRID;
+  c->h[0] = 0.5 * c->dy[0];
+  for (int j = 1; j < nyc; ++j) c->h[j] = c->yc[j] - c->yc[j - 1];
+  c->h[nyc] = 0.5 * c->dy[nyc - 1];
+  std::vector<double> yc(ny, 0.0), idy(ny, 0.0), ih(ny, 0.0), loc(ny, 0.0), hic(ny, 0.0), lof(ny, 0.0),
+      hif(ny, 0.0), wl(ny, 0.0), wu(ny, 0.0);
+  for (int j = 0; j < nyc; ++j) {
+    yc[j] = c->yc[j];
+    idy[j] = 1.0 / c->dy[j];
+    loc[j] = 1.0 / (c->h[j] * c->dy[j]);
+    hic[j] = 1.0 / (c->h[j + 1] * c->dy[j]);
+  }
+  for (int j = 0; j < ny; ++j) ih[j] = 1.0 / c->h[j];
+  for (int j = 1; j < nyc; ++j) {
+    lof[j] = 1.0 / (c->dy[j - 1] * c->h[j]);
+    hif[j] = 1.0 / (c->dy[j] * c->h[j]);
+    wl[j] = c->dy[j - 1] / (2.0 * c->h[j]);
+    wu[j] = c->dy[j] / (2.0 * c->h[j]);
+  }
+  // rows of d2/dy2 for cell-centred quantities (Neumann: zero wall flux; Dirichlet: wall value on the face)
+  std::vector<double> rN(3 * (size_t)ny, 0.0), rD(3 * (size_t)ny, 0.0);
+  for (int bc = 0; bc < 2; ++bc) {
+    double* r = bc == 0 ? rN.data() : rD.data();
+    double *a = r, *b = r + ny, *cc = r + 2 * ny;
+    for (int j = 0; j < nyc; ++j) {
+      const double lo = 1.0 / (c->h[j] * c->dy[j]);
+      const double hi = 1.0 / (c->h[j + 1] * c->dy[j]);
+      b[j] = 0.0;
+      if (j > 0) { a[j] = lo; b[j] -= lo; }
+      else if (bc == 1) b[j] -= lo;
+      if (j < nyc - 1) { cc[j] = hi; b[j] -= hi; }
+      else if (bc == 1) b[j] -= hi;
+    }
+  }
+  const int nx = c->g.nx, nz = c->g.nz, mh = c->g.mh, mp = c->g.mp;
+  std::vector<double> kx2(mp, 0.0), kz2(nz, 0.0);
+  for (int m = 0; m < mh; ++m) kx2[m] = (2.0 - 2.0 * std::cos(2.0 * M_PI * m / nx)) / (c->g.dx * c->g.dx);
+  for (int n = 0; n < nz; ++n) kz2[n] = (2.0 - 2.0 * std::cos(2.0 * M_PI * n / nz)) / (c->g.dz * c->g.dz);
+  // FFT tables: exp(-2 pi i t / N)
+  const int Lh = nx / 2;
+  std::vector<cplx<double>> twx(Lh), twp(Lh + 1), twz(nz);
+  std::vector<cplx<float>> twxf(Lh), twpf(Lh + 1), twzf(nz);
+  for (int t = 0; t < Lh; ++t) twx[t] = {std::cos(2.0 * M_PI * t / Lh), -std::sin(2.0 * M_PI * t / Lh)};
+  for (int t = 0; t <= Lh; ++t) twp[t] = {std::cos(2.0 * M_PI * t / nx), -std::sin(2.0 * M_PI * t / nx)};
+  for (int t = 0; t < nz; ++t) twz[t] = {std::cos(2.0 * M_PI * t / nz), -std::sin(2.0 * M_PI * t / nz)};
+  for (int t = 0; t < Lh; ++t) twxf[t] = {(float)twx[t].x, (float)twx[t].y};
+  for (int t = 0; t <= Lh; ++t) twpf[t] = {(float)twp[t].x, (float)twp[t].y};
+  for (int t = 0; t < nz; ++t) twzf[t] = {(float)twz[t].x, (float)twz[t].y};
+  cudaStream_t s = c->stream;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+  };
+  const size_t B = sizeof(double) * ny;
+  CK(up(c->yf_d, yf.data(), B));
+  CK(up(c->yc_d, yc.data(), B));
+  CK(up(c->idy_d, idy.data(), B));
+  CK(up(c->ih_d, ih.data(), B));
+  CK(up(c->lo_c_d, loc.data(), B));
+  CK(up(c->hi_c_d, hic.data(), B));
+  CK(up(c->lo_f_d, lof.data(), B));
+  CK(up(c->hi_f_d, hif.data(), B));
+  CK(up(c->wl_d, wl.data(), B));
+  CK(up(c->wu_d, wu.data(), B));
+  CK(up(c->rowsN_d, rN.data(), 3 * B));
+  CK(up(c->rowsD_d, rD.data(), 3 * B));
+  CK(up(c->kx2_d, kx2.data(), sizeof(double) * mp));
+  CK(up(c->kz2_d, kz2.data(), sizeof(double) * nz));
+  CK(up(c->twx_d, twx.data(), sizeof(cplx<double>) * Lh));
+  CK(up(c->twp_d, twp.data(), sizeof(cplx<double>) * (Lh + 1)));
+  CK(up(c->twz_d, twz.data(), sizeof(cplx<double>) * nz));
+  CK(up(c->twx_f, twxf.data(), sizeof(cplx<float>) * Lh));
+  CK(up(c->twp_f, twpf.data(), sizeof(cplx<float>) * (Lh + 1)));
+  CK(up(c->twz_f, twzf.data(), sizeof(cplx<float>) * nz));
+  CK(cudaStreamSynchronize(s));   // host vectors above are temporaries
+  c->cn_dt = NAN;
+  c->graph_dt = NAN;
+  return PNP_OK;
+}
+
+// Elimination factors of (I - s L_y) for the three substages and three kinds
+// (0: u and w, Dirichlet wall values on the faces; 1: v on interior faces;
+// 2: ions, zero wall flux), s = alp dt nu / 2 (nu = 1/Re or 1/(Re Sc)).
+int upload_cn(pnp_ctx* c, double dt) {
+  const int ny = c->g.ny, nyc = c->g.nyc;
+  c->cn_h.assign(27 * (size_t)ny, 0.0);
+  for (int l = 0; l < 3; ++l) {
+    const double alp = kGam[l] + kZet[l];
+    for (int kind = 0; kind < 3; ++kind) {
+      const double diff = kind == 2 ? c->ph.D : c->ph.nu;
+      const double sfac = 0.5 * alp * dt * diff;
+      const int n = kind == 1 ? nyc - 1 : nyc;
+      std::vector<double> a(n, 0.0), b(n, 0.0), cc(n, 0.0);
+      for (int idx = 0; idx < n; ++idx) {
+        if (kind == 1) {
+          const int j = idx + 1;
+          const double lo = 1.0 / (c->dy[j - 1] * c->h[j]);
+          const double hi = 1.0 / (c->dy[j] * c->h[j]);
+          if (idx > 0) a[idx] = lo;
+          if (idx < n - 1) cc[idx] = hi;
+          b[idx] = -lo - hi;
+        } else {
+          const int j = idx;
+          const double lo = 1.0 / (c->h[j] * c->dy[j]);
+          const double hi = 1.0 / (c->h[j + 1] * c->dy[j]);
+          const bool dir = kind == 0;
+          if (j > 0) { a[j] = lo; b[j] -= lo; }
+          else if (dir) b[j] -= lo;
+          if (j < nyc - 1) { cc[j] = hi; b[j] -= hi; }
+          else if (dir) b[j] -= hi;
+        }
+      }
+      double* A = c->cn_h.data() + ((size_t)(l * 3 + kind) * 3 + 0) * ny;
+      double* Cp = c->cn_h.data() + ((size_t)(l * 3 + kind) * 3 + 1) * ny;
+      double* M = c->cn_h.data() + ((size_t)(l * 3 + kind) * 3 + 2) * ny;
+      double cprev = 0.0;
+      for (int idx = 0; idx < n; ++idx) {
+        const double Aj = -sfac * a[idx], Bj = 1.0 - sfac * b[idx], Cj = -sfac * cc[idx];
+        const double m = idx == 0 ? Bj : Bj - Aj * cprev;
+        cprev = Cj / m;
+        A[idx] = Aj;
+        Cp[idx] = cprev;
+        M[idx] = 1.0 / m;
+      }
+    }
+  }
+  CK(cudaMemcpyAsync(c->cn_d, c->cn_h.data(), sizeof(double) * c->cn_h.size(), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->cn_dt = dt;
+  return PNP_OK;
+}
+
+CNRows cn_rows(const pnp_ctx* c, int l, int kind) {
+  const size_t ny = c->g.ny;
+  const double* base = c->cn_d + (size_t)(l * 3 + kind) * 3 * ny;
+  return CNRows{base, base + ny, base + 2 * ny};
+}
+
+YRows yrows(const pnp_ctx* c, bool neumann) {
+  const double* r = neumann ? c->rowsN_d : c->rowsD_d;
+  const size_t ny = c->g.ny;
+  return YRows{r, r + ny, r + 2 * ny};
+}
+
+template <typename TV>
+Fields<TV> fields(const pnp_ctx* c) {
+  Fields<TV> f;
+  f.u = (TV*)c->u; f.v = (TV*)c->v; f.w = (TV*)c->w; f.p = (TV*)c->p;
+  f.Hu = (TV*)c->Hu; f.Hv = (TV*)c->Hv; f.Hw = (TV*)c->Hw;
+  f.ru = (TV*)c->ru; f.rv = (TV*)c->rv; f.rw = (TV*)c->rw;
+  f.cp = c->cp; f.cm = c->cm; f.Phi = c->Phi; f.Hcp = c->Hcp; f.Hcm = c->Hcm; f.rcp = c->rcp; f.rcm = c->rcm;
+  return f;
+}
+
+// Spectral part of a separable Poisson solve: z-FFT, Thomas per (m, n), inverse z-FFT.
+template <typename T>
+cudaError_t spectral_solve(pnp_ctx* c, cplx<T>* spec, const cplx<T>* twz, bool neumann) {
+  cudaError_t e = launch_fft_z<T>(spec, twz, c->g, false, c->stream);
+  if (e != cudaSuccess) return e;
+  const double scale = 1.0 / ((double)c->g.nx * (double)c->g.nz);
+  e = launch_spec_thomas<T>(spec, c->sreal, c->kx2_d, c->kz2_d, yrows(c, neumann), c->g, scale, neumann, c->stream);
+  if (e != cudaSuccess) return e;
+  return launch_fft_z<T>(spec, twz, c->g, true, c->stream);
+}
+
+// Pressure correction (Neumann) from div(u_hat) / scale and the projection.
+template <typename TV>
+cudaError_t pressure_projection(pnp_ctx* c, double scale, bool update_p) {
+  const Metrics m = metrics(c);
+  const Fields<TV> f = fields<TV>(c);
+  cplx<TV>* spec = (cplx<TV>*)c->spec;
+  const cplx<TV>* twx = (const cplx<TV>*)(sizeof(TV) == 8 ? c->twx_d : c->twx_f);
+  const cplx<TV>* twp = (const cplx<TV>*)(sizeof(TV) == 8 ? c->twp_d : c->twp_f);
+  const cplx<TV>* twz = (const cplx<TV>*)(sizeof(TV) == 8 ? c->twz_d : c->twz_f);
+  TV* phip = (TV*)c->sreal;
+  cudaError_t e = launch_fft_x_fwd<TV, TV>(PoissonSrc::Divergence, f.u, f.v, f.w, nullptr, nullptr, nullptr,
+                                           1.0 / scale, c->g, m, spec, twx, twp, c->stream);
+  if (e != cudaSuccess) return e;
+  e = spectral_solve<TV>(c, spec, twz, true);
+  if (e != cudaSuccess) return e;
+  e = launch_fft_x_inv<TV, TV>(PoissonDst::Plain, spec, c->g, m, twx, twp, 0.0, phip, c->stream);
+  if (e != cudaSuccess) return e;
+  return launch_project<TV, TV>(f.u, f.v, f.w, f.p, phip, scale, update_p, c->g, m, c->stream);
+}
+
+// Eq. (4): L phi = -(c+ - c-) / (2 lam^2), phi = 0 on the walls; Phi = V y + phi (FP64).
+template <typename TV>
+cudaError_t potential_solve(pnp_ctx* c) {
+  const Metrics m = metrics(c);
+  cplx<double>* spec = (cplx<double>*)c->spec;
+  const cplx<double>* twx = (const cplx<double>*)c->twx_d;
+  const cplx<double>* twp = (const cplx<double>*)c->twp_d;
+  const cplx<double>* twz = (const cplx<double>*)c->twz_d;
+  cudaError_t e = launch_fft_x_fwd<double, TV>(PoissonSrc::Charge, nullptr, nullptr, nullptr, c->cp, c->cm, nullptr,
+                                               c->ph.q, c->g, m, spec, twx, twp, c->stream);
+  if (e != cudaSuccess) return e;
+  e = spectral_solve<double>(c, spec, twz, false);
+  if (e != cudaSuccess) return e;
+  return launch_fft_x_inv<double, double>(PoissonDst::Potential, spec, c->g, m, twx, twp, c->ph.V, c->Phi, c->stream);
+}
+
+template <typename TV>
+cudaError_t substage(pnp_ctx* c, double dt, int l) {
+  const Stage st{dt, kGam[l], kZet[l], kGam[l] + kZet[l]};
+  const Fields<TV> f = fields<TV>(c);
+  cudaError_t e = launch_rhs<TV>(f, c->g, metrics(c), c->ph, st, c->stream);
+  if (e != cudaSuccess) return e;
+  e = launch_cn_solves<TV>(f, c->g, cn_rows(c, l, 0), cn_rows(c, l, 1), cn_rows(c, l, 2), c->stream);
+  if (e != cudaSuccess) return e;
+  e = pressure_projection<TV>(c, st.alp * dt, true);
+  if (e != cudaSuccess) return e;
+  return potential_solve<TV>(c);
+}
+
+cudaError_t one_step(pnp_ctx* c, double dt) {
+  for (int l = 0; l < 3; ++l) {
+    cudaError_t e = c->precision == PNP_FP64 ? substage<double>(c, dt, l) : substage<float>(c, dt, l);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+bool is_vel_field(int field) {
+  return field == PNP_U || field == PNP_V || field == PNP_W || field == PNP_P || field == PNP_HU ||
+         field == PNP_HV || field == PNP_HW;
+}
+
+void* field_ptr(pnp_ctx* c, int field) {
+  switch (field) {
+    case PNP_U: return c->u;
+    case PNP_V: return c->v;
+    case PNP_W: return c->w;
+    case PNP_P: return c->p;
+    case PNP_CP: return c->cp;
+    case PNP_CM: return c->cm;
+    case PNP_PHI: return c->Phi;
+    case PNP_HU: return c->Hu;
+    case PNP_HV: return c->Hv;
+    case PNP_HW: return c->Hw;
+    case PNP_HCP: return c->Hcp;
+    case PNP_HCM: return c->Hcm;
+    default: return nullptr;
+  }
+}
+
+size_t field_count(const pnp_ctx* c, int field) {
+  return (field == PNP_V || field == PNP_HV) ? c->nv : c->nc;
+}
+
+void drop_graph(pnp_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->graph_dt = NAN;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pnp_workspace_bytes(int nx, int ny, int nz, int precision, size_t* out) {
+  if (!out || (precision != PNP_FP64 && precision != PNP_MIXED)) return PNP_ERR_ARG;
+  int r = check_grid(nx, ny, nz);
+  if (r) return r;
+  *out = carve(nullptr, nullptr, nx, ny, nz, precision);
+  return PNP_OK;
+}
+
+int pnp_init_grid(pnp_ctx** out, int nx, int ny, int nz, double Lx, double Lz, double stretch, int precision,
+                  void* ws, size_t bytes, void* stream) {
+  if (!out || !ws || (precision != PNP_FP64 && precision != PNP_MIXED)) return PNP_ERR_ARG;
+  if (!(Lx > 0) || !(Lz > 0) || !std::isfinite(stretch) || stretch < 0) return PNP_ERR_ARG;
+  int r = check_grid(nx, ny, nz);
+  if (r) return r;
+  if (((uintptr_t)ws % kAlign) != 0) return PNP_ERR_WORKSPACE;
+  if (bytes < carve(nullptr, nullptr, nx, ny, nz, precision)) return PNP_ERR_WORKSPACE;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PNP_ERR_CUDA;
+  pnp_ctx* c = new (std::nothrow) pnp_ctx();
+  if (!c) return PNP_ERR_ARG;
+  c->precision = precision;
+  c->stream = (cudaStream_t)stream;
+  c->ws = (char*)ws;
+  c->ws_bytes = bytes;
+  c->g.nx = nx;
+  c->g.nz = nz;
+  c->g.ny = ny;
+  c->g.nyc = ny - 1;
+  c->g.dx = Lx / nx;
+  c->g.dz = Lz / nz;
+  c->g.idx = 1.0 / c->g.dx;
+  c->g.idz = 1.0 / c->g.dz;
+  carve(c, c->ws, nx, ny, nz, precision);
+  if (cudaMemsetAsync(c->ws, 0, bytes, c->stream) != cudaSuccess) { delete c; return PNP_ERR_CUDA; }
+  c->yf.assign(ny, 0.0);
+  for (int j = 0; j < ny; ++j) {
+    const double s = j * 2.0 / (ny - 1) - 1.0;
+    c->yf[j] = stretch == 0.0 ? s : std::tanh(stretch * s) / std::tanh(stretch);
+  }
+  r = upload_metrics(c);
+  if (r) { delete c; return r; }
+  *out = c;
+  return PNP_OK;
+}
+
+int pnp_set_yfaces(pnp_ctx* c, const double* yf, int ny) {
+  if (!c || !yf || ny != c->g.ny) return PNP_ERR_ARG;
+  for (int j = 0; j < ny; ++j) c->yf[j] = yf[j];
+  c->have_state = false;
+  return upload_metrics(c);
+}
+
+int pnp_set_params(pnp_ctx* c, double Re, double lam, double Sc, double V, double beta) {
+  if (!c) return PNP_ERR_ARG;
+  if (!(Re > 0) || !(lam > 0) || !(Sc > 0) || !std::isfinite(V) || !(beta >= 0) || !std::isfinite(Re) ||
+      !std::isfinite(beta))
+    return PNP_ERR_ARG;
+  c->Re = Re; c->lam = lam; c->Sc = Sc; c->beta = beta;
+  const double Uw = c->have_params ? c->ph.Uw : 1.0;
+  c->ph.nu = 1.0 / Re;
+  c->ph.D = 1.0 / (Re * Sc);
+  c->ph.K = beta / (2.0 * Re * Re * Sc * lam * lam);
+  c->ph.q = 1.0 / (2.0 * lam * lam);
+  c->ph.V = V;
+  c->ph.Uw = Uw;
+  c->have_params = true;
+  c->cn_dt = NAN;
+  drop_graph(c);
+  return PNP_OK;
+}
+
+int pnp_set_wall_velocity(pnp_ctx* c, double Uw) {
+  if (!c || !std::isfinite(Uw)) return PNP_ERR_ARG;
+  if (!c->have_params) return PNP_ERR_STATE;
+  c->ph.Uw = Uw;
+  drop_graph(c);
+  return PNP_OK;
+}
+
+int pnp_init_state(pnp_ctx* c, int ic_kind, uint64_t seed, double amp) {
+  if (!c || (ic_kind != PNP_IC_LAMINAR && ic_kind != PNP_IC_PB) || !std::isfinite(amp)) return PNP_ERR_ARG;
+  if (!c->have_params) return PNP_ERR_STATE;
+  // bulk concentration of two Gouy-Chapman layers formed from c = 1:
+  // c_b + 2 lam sqrt(c_b) (cosh(V/2) - 1) = 1
+  const double bq = 2.0 * c->lam * (std::cosh(0.5 * c->ph.V) - 1.0);
+  const double sq = 0.5 * (-bq + std::sqrt(bq * bq + 4.0));
+  const double cb = sq * sq;
+  const double kappa = std::sqrt(cb) / c->lam;
+  cudaError_t e;
+  if (c->precision == PNP_FP64)
+    e = launch_init_fields<double>(fields<double>(c), c->g, metrics(c), c->ph, ic_kind, cb, kappa, seed, amp, c->yf_d, c->stream);
+  else
+    e = launch_init_fields<float>(fields<float>(c), c->g, metrics(c), c->ph, ic_kind, cb, kappa, seed, amp, c->yf_d, c->stream);
+  if (e != cudaSuccess) return PNP_ERR_CUDA;
+  if (amp != 0.0) {
+    e = c->precision == PNP_FP64 ? pressure_projection<double>(c, 1.0, false) : pressure_projection<float>(c, 1.0, false);
+    if (e != cudaSuccess) return PNP_ERR_CUDA;
+  }
+  e = c->precision == PNP_FP64 ? potential_solve<double>(c) : potential_solve<float>(c);
+  if (e != cudaSuccess) return PNP_ERR_CUDA;
+  c->have_state = true;
+  c->time = 0.0;
+  c->nstep = 0;
+  return PNP_OK;
+}
+
+int pnp_field_size(pnp_ctx* c, int field, size_t* n) {
+  if (!c || !n || field < 0 || field >= PNP_NFIELDS) return PNP_ERR_ARG;
+  *n = field_count(c, field);
+  return PNP_OK;
+}
+
+int pnp_set_state(pnp_ctx* c, int field, const void* src, int on_device) {
+  if (!c || !src || field < 0 || field >= PNP_NFIELDS) return PNP_ERR_ARG;
+  const size_t n = field_count(c, field);
+  void* dst = field_ptr(c, field);
+  const bool narrow = c->precision == PNP_MIXED && is_vel_field(field);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (!narrow) {
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(double), kind, c->stream));
+  } else {
+    const double* s = (const double*)src;
+    if (!on_device) {
+      CK(cudaMemcpyAsync(c->stage, src, n * sizeof(double), kind, c->stream));
+      s = c->stage;
+    }
+    CK(launch_convert<double, float>(s, (float*)dst, n, c->stream));
+  }
+  if (field <= PNP_PHI) c->have_state = true;
+  return PNP_OK;
+}
+
+int pnp_get_state(pnp_ctx* c, int field, void* dst, int on_device) {
+  if (!c || !dst || field < 0 || field >= PNP_NFIELDS) return PNP_ERR_ARG;
+  const size_t n = field_count(c, field);
+  const void* src = field_ptr(c, field);
+  const bool narrow = c->precision == PNP_MIXED && is_vel_field(field);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (narrow) {
+    double* tgt = on_device ? (double*)dst : c->stage;
+    CK(launch_convert<float, double>((const float*)src, tgt, n, c->stream));
+    if (!on_device) CK(cudaMemcpyAsync(dst, c->stage, n * sizeof(double), kind, c->stream));
+  } else {
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(double), kind, c->stream));
+  }
+  if (!on_device) CK(cudaStreamSynchronize(c->stream));
+  return PNP_OK;
+}
+
+int pnp_step(pnp_ctx* c, int nsteps, double dt) {
+  if (!c || nsteps < 0 || !(dt > 0) || !std::isfinite(dt)) return PNP_ERR_ARG;
+  if (!c->have_params || !c->have_state) return PNP_ERR_STATE;
+  if (nsteps == 0) return PNP_OK;
+  if (c->cn_dt != dt) {
+    int r = upload_cn(c, dt);
+    if (r) return r;
+  }
+  if (c->stream == nullptr) {
+    for (int n = 0; n < nsteps; ++n) CK(one_step(c, dt));
+  } else {
+    if (!c->gexec || c->graph_dt != dt) {
+      drop_graph(c);
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+      cudaError_t e = one_step(c, dt);
+      cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return PNP_ERR_CUDA;
+      }
+      e = cudaGraphInstantiate(&c->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) { c->gexec = nullptr; return PNP_ERR_CUDA; }
+      c->graph_dt = dt;
+    }
+    for (int n = 0; n < nsteps; ++n) CK(cudaGraphLaunch(c->gexec, c->stream));
+  }
+  c->time += nsteps * dt;
+  c->nstep += nsteps;
+  return PNP_OK;
+}
+
+int pnp_diagnostics(pnp_ctx* c, pnp_diag* out) {
+  if (!c || !out) return PNP_ERR_ARG;
+  if (!c->have_params || !c->have_state) return PNP_ERR_STATE;
+  cudaError_t e = c->precision == PNP_FP64
+                      ? launch_diagnostics<double>(fields<double>(c), c->g, metrics(c), c->ph, c->diag_partial,
+                                                   kDiagBlocks, c->diag_out, c->status_d, c->stream)
+                      : launch_diagnostics<float>(fields<float>(c), c->g, metrics(c), c->ph, c->diag_partial,
+                                                  kDiagBlocks, c->diag_out, c->status_d, c->stream);
+  if (e != cudaSuccess) return PNP_ERR_CUDA;
+  double h[8];
+  int st = 0;
+  CK(cudaMemcpyAsync(h, c->diag_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&st, c->status_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const double P = (double)c->g.nx * c->g.nz;
+  const double ub = h[0] / P, ut = h[1] / P;
+  const double Uw = c->ph.Uw;
+  std::memset(out, 0, sizeof(*out));
+  out->tau_bot = c->ph.nu * (ub + Uw) / c->h[0];
+  out->tau_top = c->ph.nu * (Uw - ut) / c->h[c->g.nyc];
+  const double tau = 0.5 * (out->tau_bot + out->tau_top);
+  out->cf = Uw != 0.0 ? 2.0 * tau / (Uw * Uw) : 0.0;
+  out->re_tau = c->Re * std::sqrt(tau > 0 ? tau : 0.0);
+  out->n_plus = h[2] * c->g.dx * c->g.dz;
+  out->n_minus = h[3] * c->g.dx * c->g.dz;
+  out->net_charge = out->n_plus - out->n_minus;
+  out->wall_flux = 0.0;   // the scheme sets every wall-face ion flux to zero (Fig. 1 caption)
+  out->max_div = h[4];
+  out->ke = 0.5 * h[5] * c->g.dx * c->g.dz;
+  out->time = c->time;
+  out->nstep = c->nstep;
+  out->status = st;
+  out->precision = c->precision;
+  return st;
+}
+
+int pnp_mean_profile(pnp_ctx* c, int field, double* out) {
+  if (!c || !out || field < 0 || field >= PNP_NFIELDS) return PNP_ERR_ARG;
+  const int planes = (field == PNP_V || field == PNP_HV) ? c->g.ny : c->g.nyc;
+  const int P = c->g.nz * c->g.nx;
+  const void* q = field_ptr(c, field);
+  cudaError_t e = (c->precision == PNP_MIXED && is_vel_field(field))
+                      ? launch_mean_profile<float>((const float*)q, planes, P, c->stage, c->stream)
+                      : launch_mean_profile<double>((const double*)q, planes, P, c->stage, c->stream);
+  if (e != cudaSuccess) return PNP_ERR_CUDA;
+  CK(cudaMemcpyAsync(out, c->stage, sizeof(double) * planes, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PNP_OK;
+}
+
+int pnp_poisson(pnp_ctx* c, int bc, const double* rhs, double* x) {
+  if (!c || !rhs || !x || (bc != PNP_NEUMANN && bc != PNP_DIRICHLET)) return PNP_ERR_ARG;
+  const Metrics m = metrics(c);
+  cplx<double>* spec = (cplx<double>*)c->spec;
+  const cplx<double>* twx = (const cplx<double>*)c->twx_d;
+  const cplx<double>* twp = (const cplx<double>*)c->twp_d;
+  const cplx<double>* twz = (const cplx<double>*)c->twz_d;
+  CK(launch_fft_x_fwd<double, double>(PoissonSrc::Plain, nullptr, nullptr, nullptr, nullptr, nullptr, rhs, 1.0, c->g,
+                                      m, spec, twx, twp, c->stream));
+  CK(spectral_solve<double>(c, spec, twz, bc == PNP_NEUMANN));
+  CK(launch_fft_x_inv<double, double>(PoissonDst::Plain, spec, c->g, m, twx, twp, 0.0, x, c->stream));
+  return PNP_OK;
+}
+
+int pnp_eval_explicit(pnp_ctx* c) {
+  if (!c) return PNP_ERR_ARG;
+  if (!c->have_params || !c->have_state) return PNP_ERR_STATE;
+  const Stage st{1.0, 1.0, 0.0, 0.0};
+  cudaError_t e = c->precision == PNP_FP64 ? launch_rhs<double>(fields<double>(c), c->g, metrics(c), c->ph, st, c->stream)
+                                           : launch_rhs<float>(fields<float>(c), c->g, metrics(c), c->ph, st, c->stream);
+  return e == cudaSuccess ? PNP_OK : PNP_ERR_CUDA;
+}
+
+int pnp_status(pnp_ctx* c) {
+  if (!c) return PNP_ERR_ARG;
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, c->status_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return st;
+}
+
+int pnp_fp64_peak(pnp_ctx* c, double* flops) {
+  if (!c || !flops) return PNP_ERR_ARG;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int iters = 4096;
+  CK(launch_fp64_probe(c->probe_d, 64, kProbeBlocks, c->stream));   // warm-up
+  CK(cudaEventRecord(e0, c->stream));
+  CK(launch_fp64_probe(c->probe_d, iters, kProbeBlocks, c->stream));
+  CK(cudaEventRecord(e1, c->stream));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *flops = 2.0 * 8.0 * iters * (double)kProbeBlocks * 256.0 / (ms * 1e-3);
+  return PNP_OK;
+}
+
+const char* pnp_error_string(int code) {
+  switch (code) {
+    case PNP_OK: return "ok";
+    case PNP_ERR_ARG: return "invalid argument";
+    case PNP_ERR_GRID: return "invalid grid (Nx, Nz powers of two in [4, 4096]; Ny >= 3; increasing y faces)";
+    case PNP_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
+    case PNP_ERR_CUDA: return "CUDA runtime error";
+    case PNP_ERR_STATE: return "parameters or state not set";
+    case PNP_ERR_NONFINITE: return "non-finite value in a prognostic field";
+    case PNP_ERR_NEGATIVE_C: return "negative ion concentration";
+    case PNP_ERR_UNSUPPORTED: return "unsupported option";
+    default: return "unknown error";
+  }
+}
+
+void pnp_destroy(pnp_ctx* c) {
+  if (!c) return;
+  drop_graph(c);
+  delete c;
+}
+
+}  // extern "C"

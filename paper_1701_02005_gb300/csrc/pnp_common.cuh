@@ -1,0 +1,143 @@
+// Internal declarations shared by the libpnp CUDA translation units.
+//
+// Discretisation (arXiv:1701.02005, Numerical methods and Fig. 1): staggered
+// second-order finite volumes, fields indexed [y][z][x].  Cell-centred fields
+// (u on x-faces, w on z-faces, p, c+-, Phi at centres) have nyc planes;
+// v lives on the ny = nyc + 1 y-faces, walls included (always zero).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "pnp.h"
+
+namespace pnp {
+
+template <typename T> struct cplx { T x, y; };
+
+template <typename T> __host__ __device__ inline cplx<T> cadd(cplx<T> a, cplx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T> __host__ __device__ inline cplx<T> csub(cplx<T> a, cplx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T> __host__ __device__ inline cplx<T> cmul(cplx<T> a, cplx<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T> __host__ __device__ inline cplx<T> cconj(cplx<T> a) { return {a.x, -a.y}; }
+
+// Grid sizes and uniform x/z spacings.
+struct Geo {
+  int nx, nz, nyc, ny;   // ny = nyc + 1 face nodes
+  int mh, mp;            // nx/2 + 1 spectral columns, padded pitch
+  double dx, dz, idx, idz;
+};
+
+// Per-y metric arrays on the device (see pnp_api.cu for definitions).
+struct Metrics {
+  const double* yc;    // cell centres [nyc]
+  const double* idy;   // 1 / dy_j [nyc]
+  const double* ih;    // 1 / h_j [ny], h = centre-to-centre distance across face j
+  const double* lo_c;  // 1 / (h_j dy_j) [nyc]: coupling of cell j through face j
+  const double* hi_c;  // 1 / (h_{j+1} dy_j) [nyc]: coupling through face j+1
+  const double* lo_f;  // 1 / (dy_{j-1} h_j) [ny]: face j to face j-1
+  const double* hi_f;  // 1 / (dy_j h_j) [ny]: face j to face j+1
+  const double* wl;    // dy_{j-1} / (2 h_j) [ny]: volume weight of cell j-1 at face j
+  const double* wu;    // dy_j / (2 h_j) [ny]
+};
+
+// Physical coefficients (nondimensional, Numerical methods).
+struct Phys {
+  double nu;   // 1/Re
+  double D;    // 1/(Re Sc)
+  double K;    // beta / (2 Re^2 Sc lam^2): Coulomb-force coefficient
+  double q;    // 1 / (2 lam^2): Eq. (4) charge factor
+  double V;    // wall potential
+  double Uw;   // wall speed
+};
+
+// One RK3 substage.
+struct Stage {
+  double dt, gam, zet, alp;
+};
+
+template <typename TV>
+struct Fields {
+  TV *u, *v, *w, *p;
+  TV *Hu, *Hv, *Hw;
+  TV *ru, *rv, *rw;
+  double *cp, *cm, *Phi;
+  double *Hcp, *Hcm;
+  double *rcp, *rcm;
+};
+
+// Crank-Nicolson factor rows of one substage for the y-implicit solves:
+// forward elimination d_j = (r_j - a_j d_{j-1}) m_j, back substitution
+// x_j = d_j - c_j x_{j+1}.  a, c, m are arrays of the line length.
+struct CNRows {
+  const double *a, *c, *m;
+};
+
+// Rows (a, b, c) of the wall-normal second difference of a cell-centred
+// quantity, used by the spectral Thomas solves.
+struct YRows {
+  const double *a, *b, *c;
+};
+
+__host__ __device__ inline size_t cidx(int j, int k, int i, int nz, int nx) {
+  return ((size_t)j * nz + k) * nx + i;
+}
+
+// ---- launchers (host functions; all asynchronous on stream) ----
+template <typename TV>
+cudaError_t launch_rhs(const Fields<TV>& f, const Geo& g, const Metrics& m, const Phys& ph,
+                       const Stage& st, cudaStream_t s);
+
+template <typename TV>
+cudaError_t launch_cn_solves(const Fields<TV>& f, const Geo& g, const CNRows& vel, const CNRows& face,
+                             const CNRows& ion, cudaStream_t s);
+
+// Poisson pipeline pieces.  Spectral buffer holds (nyc, nz, mp) complex T.
+enum class PoissonSrc { Divergence, Charge, Plain };
+enum class PoissonDst { Plain, Potential };
+
+template <typename T, typename TV>
+cudaError_t launch_fft_x_fwd(PoissonSrc src, const TV* u, const TV* v, const TV* w, const double* cp,
+                             const double* cm, const T* plain, double scale, const Geo& g,
+                             const Metrics& m, cplx<T>* spec, const cplx<T>* tw_half,
+                             const cplx<T>* tw_post, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_fft_z(cplx<T>* spec, const cplx<T>* tw_z, const Geo& g, bool inverse, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_spec_thomas(cplx<T>* spec, double* scratch, const double* kx2, const double* kz2,
+                               const YRows& rows, const Geo& g, double scale, bool neumann,
+                               cudaStream_t s);
+
+template <typename T, typename TO>
+cudaError_t launch_fft_x_inv(PoissonDst dst, const cplx<T>* spec, const Geo& g, const Metrics& m,
+                             const cplx<T>* tw_half, const cplx<T>* tw_post, double V, TO* out,
+                             cudaStream_t s);
+
+template <typename TV, typename TS>
+cudaError_t launch_project(TV* u, TV* v, TV* w, TV* p, const TS* phip, double scale, bool update_p,
+                           const Geo& g, const Metrics& m, cudaStream_t s);
+
+// Initial condition, diagnostics, conversions.
+template <typename TV>
+cudaError_t launch_init_fields(const Fields<TV>& f, const Geo& g, const Metrics& m, const Phys& ph,
+                               int ic_kind, double cb, double kappa, uint64_t seed, double amp,
+                               const double* yf, cudaStream_t s);
+
+template <typename TV>
+cudaError_t launch_diagnostics(const Fields<TV>& f, const Geo& g, const Metrics& m, const Phys& ph,
+                               double* partial, int npartial, double* out, int* status,
+                               cudaStream_t s);
+
+template <typename TA, typename TB>
+cudaError_t launch_convert(const TA* a, TB* b, size_t n, cudaStream_t s);
+
+template <typename TQ>
+cudaError_t launch_mean_profile(const TQ* q, int nplanes, int plane, double* out, cudaStream_t s);
+
+cudaError_t launch_fp64_probe(double* out, int iters, int blocks, cudaStream_t s);
+
+}  // namespace pnp

@@ -1,0 +1,140 @@
+"""A context of libpnp with torch-owned device memory and stream.
+
+PyTorch supplies the device workspace (one uint8 tensor) and a CUDA stream;
+every computation runs in libpnp's kernels through the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import binding as B
+
+FIELD_NAMES = {"u": B.PNP_U, "v": B.PNP_V, "w": B.PNP_W, "p": B.PNP_P, "cp": B.PNP_CP, "cm": B.PNP_CM,
+               "Phi": B.PNP_PHI, "Hu": B.PNP_HU, "Hv": B.PNP_HV, "Hw": B.PNP_HW, "Hcp": B.PNP_HCP,
+               "Hcm": B.PNP_HCM}
+
+
+class Solver:
+    """One NS-PNP case on one GPU.
+
+    nx, nz: periodic sizes (powers of two); ny: y face nodes (ny - 1 cells).
+    precision: binding.PNP_FP64 or binding.PNP_MIXED.
+    """
+
+    def __init__(self, nx, ny, nz, Lx, Lz, stretch=0.0, precision=B.PNP_FP64, device=0, stream=None,
+                 y_faces=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libpnp needs a CUDA device")
+        B.load()
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.nyc = ny - 1
+        self.precision = precision
+        nbytes = C.c_size_t()
+        B.check(B.pnp_workspace_bytes(nx, ny, nz, precision, C.byref(nbytes)), "pnp_workspace_bytes")
+        self.ws = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        off = (-base) % 256
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        ctx = C.c_void_p()
+        B.check(B.pnp_init_grid(C.byref(ctx), nx, ny, nz, float(Lx), float(Lz), float(stretch), precision,
+                                C.c_void_p(base + off), C.c_size_t(int(nbytes.value)),
+                                C.c_void_p(self.stream.cuda_stream)), "pnp_init_grid")
+        self.ctx = ctx
+        if y_faces is not None:
+            self.set_yfaces(y_faces)
+
+    # -- set-up --
+    def set_yfaces(self, yf):
+        a = np.ascontiguousarray(yf, dtype=np.float64)
+        B.check(B.pnp_set_yfaces(self.ctx, a.ctypes.data_as(C.POINTER(C.c_double)), a.size), "pnp_set_yfaces")
+
+    def set_params(self, Re, debye, Sc=1.0, V=0.0, beta=0.5, Uw=1.0):
+        B.check(B.pnp_set_params(self.ctx, Re, debye, Sc, V, beta), "pnp_set_params")
+        B.check(B.pnp_set_wall_velocity(self.ctx, Uw), "pnp_set_wall_velocity")
+
+    def init_state(self, ic=B.PNP_IC_PB, seed=1701, amp=0.0):
+        B.check(B.pnp_init_state(self.ctx, ic, C.c_uint64(seed), amp), "pnp_init_state")
+
+    # -- fields --
+    def shape(self, name):
+        f = FIELD_NAMES[name]
+        ny = self.ny if f in (B.PNP_V, B.PNP_HV) else self.nyc
+        return (ny, self.nz, self.nx)
+
+    def set(self, name, array):
+        a = np.ascontiguousarray(array, dtype=np.float64)
+        if a.shape != self.shape(name):
+            raise ValueError(f"{name}: shape {a.shape} != {self.shape(name)}")
+        B.check(B.pnp_set_state(self.ctx, FIELD_NAMES[name], a.ctypes.data_as(C.c_void_p), 0), "pnp_set_state")
+        self.stream.synchronize()
+
+    def set_device(self, name, tensor):
+        t = tensor.contiguous().to(dtype=self.torch.float64)
+        B.check(B.pnp_set_state(self.ctx, FIELD_NAMES[name], C.c_void_p(t.data_ptr()), 1), "pnp_set_state")
+        self.stream.synchronize()
+
+    def get(self, name):
+        a = np.empty(self.shape(name), dtype=np.float64)
+        B.check(B.pnp_get_state(self.ctx, FIELD_NAMES[name], a.ctypes.data_as(C.c_void_p), 0), "pnp_get_state")
+        return a
+
+    def set_state(self, st):
+        """Load an oracle-style state object (attributes u, v, w, p, cp, cm, Phi, H*)."""
+        for name in FIELD_NAMES:
+            self.set(name, getattr(st, name))
+
+    # -- stepping --
+    def step(self, nsteps, dt):
+        B.check(B.pnp_step(self.ctx, int(nsteps), float(dt)), "pnp_step")
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def diagnostics(self):
+        d = B.pnp_diag()
+        code = B.pnp_diagnostics(self.ctx, C.byref(d))
+        if code not in (B.PNP_OK, B.PNP_ERR_NONFINITE, B.PNP_ERR_NEGATIVE_C):
+            B.check(code, "pnp_diagnostics")
+        return d.as_dict()
+
+    def mean_profile(self, name):
+        n = self.shape(name)[0]
+        out = np.empty(n, dtype=np.float64)
+        B.check(B.pnp_mean_profile(self.ctx, FIELD_NAMES[name], out.ctypes.data_as(C.POINTER(C.c_double))),
+                "pnp_mean_profile")
+        return out
+
+    def poisson(self, rhs, bc):
+        """Separable Poisson solve of a host array (FP64) through the C ABI."""
+        t = self.torch.as_tensor(np.ascontiguousarray(rhs, dtype=np.float64)).to(self.device)
+        out = self.torch.empty_like(t)
+        self.torch.cuda.synchronize(self.device)
+        B.check(B.pnp_poisson(self.ctx, bc, C.c_void_p(t.data_ptr()), C.c_void_p(out.data_ptr())), "pnp_poisson")
+        self.stream.synchronize()
+        return out.cpu().numpy()
+
+    def eval_explicit(self):
+        B.check(B.pnp_eval_explicit(self.ctx), "pnp_eval_explicit")
+        self.stream.synchronize()
+
+    def fp64_peak(self):
+        v = C.c_double()
+        B.check(B.pnp_fp64_peak(self.ctx, C.byref(v)), "pnp_fp64_peak")
+        return v.value
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            B.pnp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
