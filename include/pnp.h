@@ -159,6 +159,30 @@ int pnp_status(pnp_ctx* ctx);
  * on the context's stream): the ALU ceiling of the FP64 kernels. */
 int pnp_fp64_peak(pnp_ctx* ctx, double* flops_out);
 
+/* Launch sites timed by pnp_profile, in launch order within a substage. */
+enum {
+  PNP_SITE_RHS = 0,         /* explicit terms + CN right-hand sides            */
+  PNP_SITE_CN = 1,          /* wall-normal CN Thomas solves (2 launches)       */
+  PNP_SITE_P_FFTX = 2,      /* divergence + forward real x-FFT                 */
+  PNP_SITE_P_FFTZ = 3,      /* forward z-FFT                                   */
+  PNP_SITE_P_THOMAS = 4,    /* spectral Thomas, Neumann                        */
+  PNP_SITE_P_IFFTZ = 5,     /* inverse z-FFT                                   */
+  PNP_SITE_P_IFFTX = 6,     /* inverse real x-FFT -> Phi_p                     */
+  PNP_SITE_PROJECT = 7,     /* projection + pressure update                    */
+  PNP_SITE_E_FFTX = 8,      /* charge + forward real x-FFT                     */
+  PNP_SITE_E_FFTZ = 9,
+  PNP_SITE_E_THOMAS = 10,   /* spectral Thomas, Dirichlet                      */
+  PNP_SITE_E_IFFTZ = 11,
+  PNP_SITE_E_IFFTX = 12,    /* inverse real x-FFT -> Phi = V y + phi           */
+  PNP_PROFILE_SITES = 13
+};
+
+/* Advance nsteps steps without a CUDA graph, timing every launch site with
+ * CUDA events on the context's stream.  ms_out[site] receives the summed
+ * milliseconds over all 3*nsteps substages (nsites >= PNP_PROFILE_SITES);
+ * *launches_per_step the number of kernel launches of one step. */
+int pnp_profile(pnp_ctx* ctx, int nsteps, double dt, double* ms_out, int nsites, int* launches_per_step);
+
 const char* pnp_error_string(int code);
 
 void pnp_destroy(pnp_ctx* ctx);

@@ -34,6 +34,9 @@ PNP_IC_PB = 1
 PNP_NEUMANN = 0
 PNP_DIRICHLET = 1
 
+PROFILE_SITES = ("rhs", "cn_thomas", "p_fftx", "p_fftz", "p_thomas", "p_ifftz", "p_ifftx", "project",
+                 "e_fftx", "e_fftz", "e_thomas", "e_ifftz", "e_ifftx")
+
 
 class pnp_diag(C.Structure):
     _fields_ = [
@@ -66,6 +69,8 @@ EXPORTS = {
     "pnp_eval_explicit": (C.c_int, [C.c_void_p]),
     "pnp_status": (C.c_int, [C.c_void_p]),
     "pnp_fp64_peak": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "pnp_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_int,
+                              C.POINTER(C.c_int)]),
     "pnp_error_string": (C.c_char_p, [C.c_int]),
     "pnp_destroy": (None, [C.c_void_p]),
 }
@@ -126,5 +131,6 @@ pnp_poisson = _fwd("pnp_poisson")
 pnp_eval_explicit = _fwd("pnp_eval_explicit")
 pnp_status = _fwd("pnp_status")
 pnp_fp64_peak = _fwd("pnp_fp64_peak")
+pnp_profile = _fwd("pnp_profile")
 pnp_error_string = _fwd("pnp_error_string")
 pnp_destroy = _fwd("pnp_destroy")

@@ -40,7 +40,15 @@ struct Bump {
 
 }  // namespace
 
+// Optional per-launch-site event timing (pnp_profile).
+struct Prof {
+  static constexpr int kMax = 16;
+  cudaEvent_t ev[kMax];
+  int n = 0;
+};
+
 struct pnp_ctx {
+  Prof* prof = nullptr;
   Geo g{};
   int precision = PNP_FP64;
   cudaStream_t stream = nullptr;
@@ -132,6 +140,11 @@ int check_grid(int nx, int ny, int nz) {
   do {                                                   \
     if ((__VA_ARGS__) != cudaSuccess) return PNP_ERR_CUDA; \
   } while (0)
+
+// Records the next site-boundary event when profiling (no-op otherwise).
+inline void mark(pnp_ctx* c) {
+  if (c->prof && c->prof->n < Prof::kMax) cudaEventRecord(c->prof->ev[c->prof->n++], c->stream);
+}
 
 Metrics metrics(const pnp_ctx* c) {
   return Metrics{c->yc_d, c->idy_d, c->ih_d, c->lo_c_d, c->hi_c_d, c->lo_f_d, c->hi_f_d, c->wl_d, c->wu_d};
@@ -309,10 +322,14 @@ template <typename T>
 cudaError_t spectral_solve(pnp_ctx* c, cplx<T>* spec, const cplx<T>* twz, bool neumann) {
   cudaError_t e = launch_fft_z<T>(spec, twz, c->g, false, c->stream);
   if (e != cudaSuccess) return e;
+  mark(c);
   const double scale = 1.0 / ((double)c->g.nx * (double)c->g.nz);
   e = launch_spec_thomas<T>(spec, c->sreal, c->kx2_d, c->kz2_d, yrows(c, neumann), c->g, scale, neumann, c->stream);
   if (e != cudaSuccess) return e;
-  return launch_fft_z<T>(spec, twz, c->g, true, c->stream);
+  mark(c);
+  e = launch_fft_z<T>(spec, twz, c->g, true, c->stream);
+  mark(c);
+  return e;
 }
 
 // Pressure correction (Neumann) from div(u_hat) / scale and the projection.
@@ -328,11 +345,15 @@ cudaError_t pressure_projection(pnp_ctx* c, double scale, bool update_p) {
   cudaError_t e = launch_fft_x_fwd<TV, TV>(PoissonSrc::Divergence, f.u, f.v, f.w, nullptr, nullptr, nullptr,
                                            1.0 / scale, c->g, m, spec, twx, twp, c->stream);
   if (e != cudaSuccess) return e;
+  mark(c);
   e = spectral_solve<TV>(c, spec, twz, true);
   if (e != cudaSuccess) return e;
   e = launch_fft_x_inv<TV, TV>(PoissonDst::Plain, spec, c->g, m, twx, twp, 0.0, phip, c->stream);
   if (e != cudaSuccess) return e;
-  return launch_project<TV, TV>(f.u, f.v, f.w, f.p, phip, scale, update_p, c->g, m, c->stream);
+  mark(c);
+  e = launch_project<TV, TV>(f.u, f.v, f.w, f.p, phip, scale, update_p, c->g, m, c->stream);
+  mark(c);
+  return e;
 }
 
 // Eq. (4): L phi = -(c+ - c-) / (2 lam^2), phi = 0 on the walls; Phi = V y + phi (FP64).
@@ -346,19 +367,25 @@ cudaError_t potential_solve(pnp_ctx* c) {
   cudaError_t e = launch_fft_x_fwd<double, TV>(PoissonSrc::Charge, nullptr, nullptr, nullptr, c->cp, c->cm, nullptr,
                                                c->ph.q, c->g, m, spec, twx, twp, c->stream);
   if (e != cudaSuccess) return e;
+  mark(c);
   e = spectral_solve<double>(c, spec, twz, false);
   if (e != cudaSuccess) return e;
-  return launch_fft_x_inv<double, double>(PoissonDst::Potential, spec, c->g, m, twx, twp, c->ph.V, c->Phi, c->stream);
+  e = launch_fft_x_inv<double, double>(PoissonDst::Potential, spec, c->g, m, twx, twp, c->ph.V, c->Phi, c->stream);
+  mark(c);
+  return e;
 }
 
 template <typename TV>
 cudaError_t substage(pnp_ctx* c, double dt, int l) {
   const Stage st{dt, kGam[l], kZet[l], kGam[l] + kZet[l]};
   const Fields<TV> f = fields<TV>(c);
+  mark(c);
   cudaError_t e = launch_rhs<TV>(f, c->g, metrics(c), c->ph, st, c->stream);
   if (e != cudaSuccess) return e;
+  mark(c);
   e = launch_cn_solves<TV>(f, c->g, cn_rows(c, l, 0), cn_rows(c, l, 1), cn_rows(c, l, 2), c->stream);
   if (e != cudaSuccess) return e;
+  mark(c);
   e = pressure_projection<TV>(c, st.alp * dt, true);
   if (e != cudaSuccess) return e;
   return potential_solve<TV>(c);
@@ -690,6 +717,43 @@ int pnp_fp64_peak(pnp_ctx* c, double* flops) {
   cudaEventDestroy(e1);
   *flops = 2.0 * 8.0 * iters * (double)kProbeBlocks * 256.0 / (ms * 1e-3);
   return PNP_OK;
+}
+
+int pnp_profile(pnp_ctx* c, int nsteps, double dt, double* ms_out, int nsites, int* launches_per_step) {
+  if (!c || !ms_out || nsites < PNP_PROFILE_SITES || nsteps < 1 || !(dt > 0)) return PNP_ERR_ARG;
+  if (!c->have_params || !c->have_state) return PNP_ERR_STATE;
+  if (c->cn_dt != dt) {
+    int r = upload_cn(c, dt);
+    if (r) return r;
+  }
+  Prof prof;
+  for (int i = 0; i < Prof::kMax; ++i) CK(cudaEventCreate(&prof.ev[i]));
+  for (int i = 0; i < PNP_PROFILE_SITES; ++i) ms_out[i] = 0.0;
+  c->prof = &prof;
+  int rc = PNP_OK;
+  for (int n = 0; n < nsteps && rc == PNP_OK; ++n) {
+    for (int l = 0; l < 3 && rc == PNP_OK; ++l) {
+      prof.n = 0;
+      cudaError_t e = c->precision == PNP_FP64 ? substage<double>(c, dt, l) : substage<float>(c, dt, l);
+      if (e != cudaSuccess || prof.n != PNP_PROFILE_SITES + 1 || cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        rc = PNP_ERR_CUDA;
+        break;
+      }
+      for (int i = 0; i < PNP_PROFILE_SITES; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, prof.ev[i], prof.ev[i + 1]) != cudaSuccess) rc = PNP_ERR_CUDA;
+        ms_out[i] += ms;
+      }
+    }
+  }
+  c->prof = nullptr;
+  for (int i = 0; i < Prof::kMax; ++i) cudaEventDestroy(prof.ev[i]);
+  if (rc == PNP_OK) {
+    c->time += nsteps * dt;
+    c->nstep += nsteps;
+  }
+  if (launches_per_step) *launches_per_step = 3 * (PNP_PROFILE_SITES + 1);
+  return rc;
 }
 
 const char* pnp_error_string(int code) {

@@ -138,3 +138,12 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def profile(solver, nsteps, dt):
+    """Per-launch-site milliseconds (summed) and launches per step via pnp_profile."""
+    n = len(B.PROFILE_SITES)
+    ms = (C.c_double * n)()
+    lps = C.c_int()
+    B.check(B.pnp_profile(solver.ctx, int(nsteps), float(dt), ms, n, C.byref(lps)), "pnp_profile")
+    return dict(zip(B.PROFILE_SITES, list(ms))), lps.value
