@@ -103,6 +103,7 @@ struct SrcArgs {
   const double *cp, *cm;
   const T* plain;
   double scale;
+  const float *sa, *sb;   // FP32 charge shadows c+', c-'
 };
 
 template <typename T, typename TV>
@@ -120,6 +121,9 @@ __device__ __forceinline__ T src_value(const SrcArgs<T, TV>& a, const Geo& g, co
   } else if (a.kind == PoissonSrc::Charge) {
     // Eq. (4): -(c+ - c-) / (2 lam^2)
     return (T)(-(a.cp[c] - a.cm[c]) * a.scale);
+  } else if (a.kind == PoissonSrc::ChargeShadow) {
+    // fluctuating charge about the reference profile, FP32
+    return T(-(a.sa[c] - a.sb[c])) * T(a.scale);
   }
   return a.plain[c];
 }
@@ -173,8 +177,8 @@ template <typename T, typename TV>
 cudaError_t launch_fft_x_fwd(PoissonSrc kind, const TV* u, const TV* v, const TV* w, const double* cp,
                              const double* cm, const T* plain, double scale, const Geo& g,
                              const Metrics& m, cplx<T>* spec, const cplx<T>* tw_half,
-                             const cplx<T>* tw_post, cudaStream_t s) {
-  SrcArgs<T, TV> a{kind, u, v, w, cp, cm, plain, scale};
+                             const cplx<T>* tw_post, cudaStream_t s, const float* sa, const float* sb) {
+  SrcArgs<T, TV> a{kind, u, v, w, cp, cm, plain, scale, sa, sb};
   dim3 blk, grd;
   size_t smem;
   fft_x_shape<T>(g, blk, grd, smem);
@@ -190,7 +194,7 @@ cudaError_t launch_fft_x_fwd(PoissonSrc kind, const TV* u, const TV* v, const TV
 template <typename T, typename TO>
 __global__ void k_fft_x_inv(PoissonDst dst, const cplx<T>* __restrict__ spec, Geo g, Metrics m,
                             const cplx<T>* __restrict__ tw_half, const cplx<T>* __restrict__ tw_post,
-                            double V, TO* __restrict__ out) {
+                            double V, TO* __restrict__ out, const double* __restrict__ plane_add) {
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
   const int Lh = g.nx >> 1;
@@ -218,9 +222,13 @@ __global__ void k_fft_x_inv(PoissonDst dst, const cplx<T>* __restrict__ spec, Ge
   const int j = row / g.nz;
   const size_t base = (size_t)row * g.nx;
   const double add = dst == PoissonDst::Potential ? V * m.yc[j] : 0.0;
+  const T addT = dst == PoissonDst::PotentialShadow ? (T)plane_add[j] : T(0);
   for (int t = threadIdx.x; t < Lh; t += blockDim.x) {
     const cplx<T> z = Z[t];
-    if (dst == PoissonDst::Potential) {
+    if (dst == PoissonDst::PotentialShadow) {
+      out[base + 2 * t] = (TO)(addT + z.x);
+      out[base + 2 * t + 1] = (TO)(addT + z.y);
+    } else if (dst == PoissonDst::Potential) {
       out[base + 2 * t] = (TO)(add + (double)z.x);
       out[base + 2 * t + 1] = (TO)(add + (double)z.y);
     } else {
@@ -233,7 +241,7 @@ __global__ void k_fft_x_inv(PoissonDst dst, const cplx<T>* __restrict__ spec, Ge
 template <typename T, typename TO>
 cudaError_t launch_fft_x_inv(PoissonDst dst, const cplx<T>* spec, const Geo& g, const Metrics& m,
                              const cplx<T>* tw_half, const cplx<T>* tw_post, double V, TO* out,
-                             cudaStream_t s) {
+                             cudaStream_t s, const double* plane_add) {
   dim3 blk, grd;
   size_t smem;
   fft_x_shape<T>(g, blk, grd, smem);
@@ -241,7 +249,7 @@ cudaError_t launch_fft_x_inv(PoissonDst dst, const cplx<T>* spec, const Geo& g, 
     cudaError_t e = cudaFuncSetAttribute(k_fft_x_inv<T, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_fft_x_inv<T, TO><<<grd, blk, smem, s>>>(dst, spec, g, m, tw_half, tw_post, V, out);
+  k_fft_x_inv<T, TO><<<grd, blk, smem, s>>>(dst, spec, g, m, tw_half, tw_post, V, out, plane_add);
   return cudaGetLastError();
 }
 
@@ -301,7 +309,9 @@ cudaError_t launch_fft_z(cplx<T>* spec, const cplx<T>* tw_z, const Geo& g, bool 
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_spec_thomas(cplx<T>* __restrict__ spec, double* __restrict__ cpr, const double* __restrict__ kx2,
-                              const double* __restrict__ kz2, YRows rows, Geo g, double scale, bool neumann) {
+                              const double* __restrict__ kz2, YRows rows, Geo g, double scale, bool neumann,
+                              const double* __restrict__ mean_rhs, const double* __restrict__ mean_shift,
+                              double* __restrict__ mean_out) {
   const int mm = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = blockIdx.y;
   if (mm >= g.mh) return;
@@ -309,21 +319,37 @@ __global__ void k_spec_thomas(cplx<T>* __restrict__ spec, double* __restrict__ c
   const size_t base = (size_t)n * g.mp + mm;
   const double k2 = kx2[mm] + kz2[n];
   const bool pin = neumann && mm == 0 && n == 0;
+  // FP64 mean mode: the (0,0) source gets the FP64 reference charge and its
+  // elimination runs entirely in FP64 storage (mean_out), never in spec.
+  const bool mean_mode = mean_rhs != nullptr && mm == 0 && n == 0;
   double cprev = 0.0, dre = 0.0, dim = 0.0;
   for (int j = 0; j < g.nyc; ++j) {
     const size_t o = base + (size_t)j * P;
     const cplx<T> r = spec[o];
     double a = rows.a[j], b = rows.b[j] - k2, c = rows.c[j];
     double rre = (double)r.x * scale, rim = (double)r.y * scale;
+    if (mean_mode) { rre += mean_rhs[j]; rim = 0.0; }
     if (pin && j == 0) { b = 1.0; c = 0.0; rre = 0.0; rim = 0.0; }
     const double inv = 1.0 / (b - a * cprev);
     cprev = c * inv;
     dre = (rre - a * dre) * inv;
     dim = (rim - a * dim) * inv;
     cpr[o] = cprev;
-    spec[o] = {(T)dre, (T)dim};
+    if (mean_mode) mean_out[j] = dre;
+    else spec[o] = {(T)dre, (T)dim};
   }
   double xre = dre, xim = dim;
+  if (mean_mode) {
+    mean_out[g.nyc - 1] = xre + mean_shift[g.nyc - 1];
+    spec[base + (size_t)(g.nyc - 1) * P] = {T(0), T(0)};
+    for (int j = g.nyc - 2; j >= 0; --j) {
+      const size_t o = base + (size_t)j * P;
+      xre = mean_out[j] - cpr[o] * xre;
+      mean_out[j] = xre + mean_shift[j];
+      spec[o] = {T(0), T(0)};
+    }
+    return;
+  }
   for (int j = g.nyc - 2; j >= 0; --j) {
     const size_t o = base + (size_t)j * P;
     const cplx<T> d = spec[o];
@@ -336,10 +362,12 @@ __global__ void k_spec_thomas(cplx<T>* __restrict__ spec, double* __restrict__ c
 
 template <typename T>
 cudaError_t launch_spec_thomas(cplx<T>* spec, double* scratch, const double* kx2, const double* kz2,
-                               const YRows& rows, const Geo& g, double scale, bool neumann, cudaStream_t s) {
+                               const YRows& rows, const Geo& g, double scale, bool neumann, cudaStream_t s,
+                               const double* mean_rhs, const double* mean_shift, double* mean_out) {
   const int T_ = 64;
   dim3 grd((g.mh + T_ - 1) / T_, g.nz, 1);
-  k_spec_thomas<T><<<grd, T_, 0, s>>>(spec, scratch, kx2, kz2, rows, g, scale, neumann);
+  k_spec_thomas<T><<<grd, T_, 0, s>>>(spec, scratch, kx2, kz2, rows, g, scale, neumann, mean_rhs, mean_shift,
+                                      mean_out);
   return cudaGetLastError();
 }
 
@@ -382,30 +410,35 @@ template cudaError_t launch_cn_solves<float>(const Fields<float>&, const Geo&, c
 template cudaError_t launch_fft_x_fwd<double, double>(PoissonSrc, const double*, const double*, const double*,
                                                       const double*, const double*, const double*, double,
                                                       const Geo&, const Metrics&, cplx<double>*,
-                                                      const cplx<double>*, const cplx<double>*, cudaStream_t);
+                                                      const cplx<double>*, const cplx<double>*, cudaStream_t,
+                                                      const float*, const float*);
 template cudaError_t launch_fft_x_fwd<float, float>(PoissonSrc, const float*, const float*, const float*,
                                                     const double*, const double*, const float*, double,
                                                     const Geo&, const Metrics&, cplx<float>*,
-                                                    const cplx<float>*, const cplx<float>*, cudaStream_t);
+                                                    const cplx<float>*, const cplx<float>*, cudaStream_t,
+                                                    const float*, const float*);
 template cudaError_t launch_fft_x_fwd<double, float>(PoissonSrc, const float*, const float*, const float*,
                                                      const double*, const double*, const double*, double,
                                                      const Geo&, const Metrics&, cplx<double>*,
-                                                     const cplx<double>*, const cplx<double>*, cudaStream_t);
+                                                     const cplx<double>*, const cplx<double>*, cudaStream_t,
+                                                     const float*, const float*);
 
 template cudaError_t launch_fft_z<double>(cplx<double>*, const cplx<double>*, const Geo&, bool, cudaStream_t);
 template cudaError_t launch_fft_z<float>(cplx<float>*, const cplx<float>*, const Geo&, bool, cudaStream_t);
 
 template cudaError_t launch_spec_thomas<double>(cplx<double>*, double*, const double*, const double*,
-                                                const YRows&, const Geo&, double, bool, cudaStream_t);
+                                                const YRows&, const Geo&, double, bool, cudaStream_t,
+                                                const double*, const double*, double*);
 template cudaError_t launch_spec_thomas<float>(cplx<float>*, double*, const double*, const double*,
-                                               const YRows&, const Geo&, double, bool, cudaStream_t);
+                                               const YRows&, const Geo&, double, bool, cudaStream_t,
+                                               const double*, const double*, double*);
 
 template cudaError_t launch_fft_x_inv<double, double>(PoissonDst, const cplx<double>*, const Geo&, const Metrics&,
                                                       const cplx<double>*, const cplx<double>*, double, double*,
-                                                      cudaStream_t);
+                                                      cudaStream_t, const double*);
 template cudaError_t launch_fft_x_inv<float, float>(PoissonDst, const cplx<float>*, const Geo&, const Metrics&,
                                                     const cplx<float>*, const cplx<float>*, double, float*,
-                                                    cudaStream_t);
+                                                    cudaStream_t, const double*);
 
 template cudaError_t launch_project<double, double>(double*, double*, double*, double*, const double*, double, bool,
                                                     const Geo&, const Metrics&, cudaStream_t);

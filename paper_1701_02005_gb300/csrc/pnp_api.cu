@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "pnp_common.cuh"
+#include "pnp_mixed.cuh"
 
 using namespace pnp;
 
@@ -72,6 +73,17 @@ struct pnp_ctx {
   double* diag_out;
   int* status_d;
   double* probe_d;
+  // mixed-precision path: FP32 shadows, FP32 metrics / velocity CN rows, reference profiles
+  float *cpS, *cmS, *phiS, *HcpS, *HcmS;
+  float* mf[8];      // idy, ih, lo_c, hi_c, lo_f, hi_f, wl, wu
+  float* cnF_d;      // [3 substages][2 kinds][a, c, m][ny]
+  float *crefp_f, *crefm_f, *crfp_f, *crfm_f, *rhoref_f, *rhorf_f, *dPref_f, *Fvref_f;
+  double *Rrefp_d, *Rrefm_d, *cref64p_d, *cref64m_d, *Phiref64_d, *meanrhs_d, *meanshift_d, *delta_d;
+  double *Hrefp_d, *Hrefm_d;
+  std::vector<double> href_p, href_m, lyc_p, lyc_m;
+  bool refs_valid = false;   // references and shadows match the FP64 fields
+  bool fp64_fresh = true;    // FP64 Phi, Hc+- arrays are current (else the shadows are)
+  double refs_dt = NAN;
   std::vector<double> yf, yc, dy, h, cn_h;
   Phys ph{};
   double Re = 0, lam = 0, Sc = 1, beta = 0.5;
@@ -113,7 +125,25 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
   double* dout = b.take<double>(8);
   int* st = b.take<int>(4);
   double* probe = b.take<double>((size_t)kProbeBlocks * 256);
+  float *cpS = b.take<float>(nc), *cmS = b.take<float>(nc), *phiS = b.take<float>(nc);
+  float *HcpS = b.take<float>(nc), *HcmS = b.take<float>(nc);
+  float* mf[8];
+  for (int q = 0; q < 8; ++q) mf[q] = b.take<float>(ny);
+  float* cnF = b.take<float>(18 * (size_t)ny);
+  float *crefp = b.take<float>(ny), *crefm = b.take<float>(ny), *crfp = b.take<float>(ny), *crfm = b.take<float>(ny);
+  float *rhoref = b.take<float>(ny), *rhorf = b.take<float>(ny), *dPref = b.take<float>(ny), *Fvref = b.take<float>(ny);
+  double *Rrefp = b.take<double>(3 * (size_t)ny), *Rrefm = b.take<double>(3 * (size_t)ny);
+  double *cr64p = b.take<double>(ny), *cr64m = b.take<double>(ny), *Pr64 = b.take<double>(ny);
+  double *mrhs = b.take<double>(ny), *mshift = b.take<double>(ny), *delta = b.take<double>(ny);
+  double *Hrp = b.take<double>(ny), *Hrm = b.take<double>(ny);
   if (c) {
+    c->cpS = cpS; c->cmS = cmS; c->phiS = phiS; c->HcpS = HcpS; c->HcmS = HcmS;
+    for (int q = 0; q < 8; ++q) c->mf[q] = mf[q];
+    c->cnF_d = cnF;
+    c->crefp_f = crefp; c->crefm_f = crefm; c->crfp_f = crfp; c->crfm_f = crfm;
+    c->rhoref_f = rhoref; c->rhorf_f = rhorf; c->dPref_f = dPref; c->Fvref_f = Fvref;
+    c->Rrefp_d = Rrefp; c->Rrefm_d = Rrefm; c->cref64p_d = cr64p; c->cref64m_d = cr64m; c->Phiref64_d = Pr64;
+    c->meanrhs_d = mrhs; c->meanshift_d = mshift; c->delta_d = delta; c->Hrefp_d = Hrp; c->Hrefm_d = Hrm;
     c->u = u; c->v = v; c->w = w; c->p = p; c->Hu = Hu; c->Hv = Hv; c->Hw = Hw; c->ru = ru; c->rv = rv; c->rw = rw;
     c->cp = cp; c->cm = cm; c->Phi = Phi; c->Hcp = Hcp; c->Hcm = Hcm; c->rcp = rcp; c->rcm = rcm;
     c->sreal = sreal; c->spec = spec; c->stage = stage;
@@ -237,7 +267,16 @@ int upload_metrics(pnp_ctx* c) {
   CK(up(c->twx_f, twxf.data(), sizeof(cplx<float>) * Lh));
   CK(up(c->twp_f, twpf.data(), sizeof(cplx<float>) * (Lh + 1)));
   CK(up(c->twz_f, twzf.data(), sizeof(cplx<float>) * nz));
+  {
+    const std::vector<double>* src[8] = {&idy, &ih, &loc, &hic, &lof, &hif, &wl, &wu};
+    std::vector<float> tmp(8 * (size_t)ny);
+    for (int q = 0; q < 8; ++q)
+      for (int j = 0; j < ny; ++j) tmp[(size_t)q * ny + j] = (float)(*src[q])[j];
+    for (int q = 0; q < 8; ++q) CK(up(c->mf[q], tmp.data() + (size_t)q * ny, sizeof(float) * ny));
+    CK(cudaStreamSynchronize(s));
+  }
   CK(cudaStreamSynchronize(s));   // host vectors above are temporaries
+  c->refs_valid = false;
   c->cn_dt = NAN;
   c->graph_dt = NAN;
   return PNP_OK;
@@ -289,9 +328,17 @@ int upload_cn(pnp_ctx* c, double dt) {
       }
     }
   }
+  std::vector<float> cnf(18 * (size_t)ny, 0.f);
+  for (int l = 0; l < 3; ++l)
+    for (int kind = 0; kind < 2; ++kind)
+      for (int a = 0; a < 3; ++a)
+        for (int j = 0; j < ny; ++j)
+          cnf[((size_t)(l * 2 + kind) * 3 + a) * ny + j] = (float)c->cn_h[((size_t)(l * 3 + kind) * 3 + a) * ny + j];
   CK(cudaMemcpyAsync(c->cn_d, c->cn_h.data(), sizeof(double) * c->cn_h.size(), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->cnF_d, cnf.data(), sizeof(float) * cnf.size(), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->cn_dt = dt;
+  c->refs_dt = NAN;
   return PNP_OK;
 }
 
@@ -299,6 +346,24 @@ CNRows cn_rows(const pnp_ctx* c, int l, int kind) {
   const size_t ny = c->g.ny;
   const double* base = c->cn_d + (size_t)(l * 3 + kind) * 3 * ny;
   return CNRows{base, base + ny, base + 2 * ny};
+}
+
+CNRowsF cn_rows_f(const pnp_ctx* c, int l, int kind) {
+  const size_t ny = c->g.ny;
+  const float* base = c->cnF_d + (size_t)(l * 2 + kind) * 3 * ny;
+  return CNRowsF{base, base + ny, base + 2 * ny};
+}
+
+MetricsF metrics_f(const pnp_ctx* c) {
+  return MetricsF{c->mf[0], c->mf[1], c->mf[2], c->mf[3], c->mf[4], c->mf[5], c->mf[6], c->mf[7]};
+}
+
+Shadows shadows(const pnp_ctx* c) { return Shadows{c->cpS, c->cmS, c->phiS, c->HcpS, c->HcmS}; }
+
+MixedRefs mixed_refs(const pnp_ctx* c) {
+  return MixedRefs{c->crefp_f, c->crefm_f, c->crfp_f, c->crfm_f, c->rhoref_f, c->rhorf_f, c->dPref_f, c->Fvref_f,
+                   c->Rrefp_d, c->Rrefm_d, c->cref64p_d, c->cref64m_d, c->Phiref64_d, c->meanrhs_d,
+                   c->meanshift_d, c->delta_d};
 }
 
 YRows yrows(const pnp_ctx* c, bool neumann) {
@@ -391,12 +456,156 @@ cudaError_t substage(pnp_ctx* c, double dt, int l) {
   return potential_solve<TV>(c);
 }
 
+// Mixed-precision substage (policy in k_mixed.cu).
+cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
+  const Stage st{dt, kGam[l], kZet[l], kGam[l] + kZet[l]};
+  const Fields<float> f = fields<float>(c);
+  const Shadows sh = shadows(c);
+  const MixedRefs R = mixed_refs(c);
+  const Metrics m = metrics(c);
+  mark(c);
+  cudaError_t e = launch_mixed_rhs(f, sh, R, c->g, metrics_f(c), c->ph, st, l, c->stream);
+  if (e != cudaSuccess) return e;
+  mark(c);
+  e = launch_mixed_cn(f, sh, R, c->g, cn_rows_f(c, l, 0), cn_rows_f(c, l, 1), cn_rows(c, l, 2), c->stream);
+  if (e != cudaSuccess) return e;
+  mark(c);
+  e = pressure_projection<float>(c, st.alp * dt, true);
+  if (e != cudaSuccess) return e;
+  // potential: FP32 FFT of the fluctuating charge, FP64 y-solves and (0,0) mode
+  cplx<float>* spec = (cplx<float>*)c->spec;
+  const cplx<float>* twx = (const cplx<float>*)c->twx_f;
+  const cplx<float>* twp = (const cplx<float>*)c->twp_f;
+  const cplx<float>* twz = (const cplx<float>*)c->twz_f;
+  e = launch_fft_x_fwd<float, float>(PoissonSrc::ChargeShadow, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                     c->ph.q, c->g, m, spec, twx, twp, c->stream, sh.cp, sh.cm);
+  if (e != cudaSuccess) return e;
+  mark(c);
+  e = launch_fft_z<float>(spec, twz, c->g, false, c->stream);
+  if (e != cudaSuccess) return e;
+  mark(c);
+  const double scale = 1.0 / ((double)c->g.nx * (double)c->g.nz);
+  e = launch_spec_thomas<float>(spec, c->sreal, c->kx2_d, c->kz2_d, yrows(c, false), c->g, scale, false, c->stream,
+                                c->meanrhs_d, c->meanshift_d, c->delta_d);
+  if (e != cudaSuccess) return e;
+  mark(c);
+  e = launch_fft_z<float>(spec, twz, c->g, true, c->stream);
+  if (e != cudaSuccess) return e;
+  mark(c);
+  e = launch_fft_x_inv<float, float>(PoissonDst::PotentialShadow, spec, c->g, m, twx, twp, 0.0, sh.phi, c->stream,
+                                     c->delta_d);
+  mark(c);
+  return e;
+}
+
 cudaError_t one_step(pnp_ctx* c, double dt) {
   for (int l = 0; l < 3; ++l) {
-    cudaError_t e = c->precision == PNP_FP64 ? substage<double>(c, dt, l) : substage<float>(c, dt, l);
+    cudaError_t e = c->precision == PNP_FP64 ? substage<double>(c, dt, l) : substage_mixed(c, dt, l);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+void drop_graph(pnp_ctx* c);
+
+// Mixed precision: bring the FP64 Phi and Hc+- arrays up to date from the shadows.
+int materialize(pnp_ctx* c) {
+  if (c->precision != PNP_MIXED || c->fp64_fresh) return PNP_OK;
+  const size_t P = (size_t)c->g.nz * c->g.nx;
+  CK(launch_from_shadow(c->phiS, c->Phiref64_d, c->Phi, P, c->nc, c->stream));
+  CK(launch_from_shadow(c->HcpS, c->Hrefp_d, c->Hcp, P, c->nc, c->stream));
+  CK(launch_from_shadow(c->HcmS, c->Hrefm_d, c->Hcm, P, c->nc, c->stream));
+  c->fp64_fresh = true;
+  return PNP_OK;
+}
+
+// Mixed precision: reference profiles (plane means of c+, c-, Phi) and every
+// per-plane FP64 constant derived from them; then the FP32 shadows.
+int refresh_refs(pnp_ctx* c, double dt) {
+  if (c->precision != PNP_MIXED) return PNP_OK;
+  const int ny = c->g.ny, nyc = c->g.nyc;
+  const size_t P = (size_t)c->g.nz * c->g.nx;
+  if (!c->refs_valid) {
+    int r = materialize(c);
+    if (r) return r;
+    CK(launch_plane_means3(c->cp, c->cm, c->Phi, nyc, P, c->cref64p_d, c->cref64m_d, c->Phiref64_d, c->stream));
+    std::vector<double> cp(nyc), cm(nyc), Ph(nyc);
+    CK(cudaMemcpyAsync(cp.data(), c->cref64p_d, sizeof(double) * nyc, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(cm.data(), c->cref64m_d, sizeof(double) * nyc, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(Ph.data(), c->Phiref64_d, sizeof(double) * nyc, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const double D = c->ph.D, K = c->ph.K, q = c->ph.q, V = c->ph.V;
+    std::vector<float> crefp(ny, 0.f), crefm(ny, 0.f), crfp(ny, 0.f), crfm(ny, 0.f), rhoref(ny, 0.f), rhorf(ny, 0.f),
+        dPref(ny, 0.f), Fvref(ny, 0.f);
+    std::vector<double> mrhs(ny, 0.0), mshift(ny, 0.0);
+    c->href_p.assign(ny, 0.0);
+    c->href_m.assign(ny, 0.0);
+    c->lyc_p.assign(ny, 0.0);
+    c->lyc_m.assign(ny, 0.0);
+    for (int j = 0; j < nyc; ++j) {
+      crefp[j] = (float)cp[j];
+      crefm[j] = (float)cm[j];
+      rhoref[j] = (float)(cp[j] - cm[j]);
+      mrhs[j] = -q * (cp[j] - cm[j]);
+      mshift[j] = V * c->yc[j] - Ph[j];
+    }
+    // reference migration flux on interior faces, its divergence, the implicit
+    // diffusion of the reference and the reference Coulomb force on v (all FP64)
+    std::vector<double> Fp(ny, 0.0), Fm(ny, 0.0);
+    for (int j = 1; j < nyc; ++j) {
+      const double ih = 1.0 / c->h[j];
+      const double dP = Ph[j] - Ph[j - 1];
+      const double cfp = 0.5 * (cp[j - 1] + cp[j]), cfm = 0.5 * (cm[j - 1] + cm[j]);
+      const double rf = 0.5 * ((cp[j - 1] - cm[j - 1]) + (cp[j] - cm[j]));
+      Fp[j] = -1.0 * D * cfp * dP * ih;
+      Fm[j] = +1.0 * D * cfm * dP * ih;
+      crfp[j] = (float)cfp;
+      crfm[j] = (float)cfm;
+      rhorf[j] = (float)rf;
+      dPref[j] = (float)dP;
+      Fvref[j] = (float)(-K * rf * dP * ih);
+    }
+    for (int j = 0; j < nyc; ++j) {
+      const double idy = 1.0 / c->dy[j];
+      c->href_p[j] = -(Fp[j + 1] - Fp[j]) * idy;
+      c->href_m[j] = -(Fm[j + 1] - Fm[j]) * idy;
+      const double lo = 1.0 / (c->h[j] * c->dy[j]), hi = 1.0 / (c->h[j + 1] * c->dy[j]);
+      c->lyc_p[j] = (j > 0 ? lo * (cp[j - 1] - cp[j]) : 0.0) + (j < nyc - 1 ? hi * (cp[j + 1] - cp[j]) : 0.0);
+      c->lyc_m[j] = (j > 0 ? lo * (cm[j - 1] - cm[j]) : 0.0) + (j < nyc - 1 ? hi * (cm[j + 1] - cm[j]) : 0.0);
+    }
+    auto upf = [&](float* d, const std::vector<float>& v) {
+      return cudaMemcpyAsync(d, v.data(), sizeof(float) * ny, cudaMemcpyHostToDevice, c->stream);
+    };
+    auto upd = [&](double* d, const std::vector<double>& v) {
+      return cudaMemcpyAsync(d, v.data(), sizeof(double) * ny, cudaMemcpyHostToDevice, c->stream);
+    };
+    CK(upf(c->crefp_f, crefp)); CK(upf(c->crefm_f, crefm)); CK(upf(c->crfp_f, crfp)); CK(upf(c->crfm_f, crfm));
+    CK(upf(c->rhoref_f, rhoref)); CK(upf(c->rhorf_f, rhorf)); CK(upf(c->dPref_f, dPref)); CK(upf(c->Fvref_f, Fvref));
+    CK(upd(c->meanrhs_d, mrhs)); CK(upd(c->meanshift_d, mshift));
+    CK(upd(c->Hrefp_d, c->href_p)); CK(upd(c->Hrefm_d, c->href_m));
+    CK(launch_make_shadows(c->cp, c->cm, c->Phi, c->Hcp, c->Hcm, shadows(c), mixed_refs(c), c->Hrefp_d, c->Hrefm_d, P,
+                           c->nc, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->refs_valid = true;
+    c->refs_dt = NAN;
+    drop_graph(c);
+  }
+  if (!(c->refs_dt == dt)) {
+    // Rref(l, j) = dt alp_l (H_ref + D L_y c_ref): the reference part of the ion CN right-hand side
+    std::vector<double> Rp(3 * (size_t)ny, 0.0), Rm(3 * (size_t)ny, 0.0);
+    for (int l = 0; l < 3; ++l) {
+      const double alp = kGam[l] + kZet[l];
+      for (int j = 0; j < nyc; ++j) {
+        Rp[(size_t)l * nyc + j] = dt * alp * (c->href_p[j] + c->ph.D * c->lyc_p[j]);
+        Rm[(size_t)l * nyc + j] = dt * alp * (c->href_m[j] + c->ph.D * c->lyc_m[j]);
+      }
+    }
+    CK(cudaMemcpyAsync(c->Rrefp_d, Rp.data(), sizeof(double) * 3 * nyc, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->Rrefm_d, Rm.data(), sizeof(double) * 3 * nyc, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->refs_dt = dt;
+  }
+  return PNP_OK;
 }
 
 bool is_vel_field(int field) {
@@ -537,6 +746,8 @@ int pnp_init_state(pnp_ctx* c, int ic_kind, uint64_t seed, double amp) {
   e = c->precision == PNP_FP64 ? potential_solve<double>(c) : potential_solve<float>(c);
   if (e != cudaSuccess) return PNP_ERR_CUDA;
   c->have_state = true;
+  c->fp64_fresh = true;
+  c->refs_valid = false;
   c->time = 0.0;
   c->nstep = 0;
   return PNP_OK;
@@ -554,6 +765,11 @@ int pnp_set_state(pnp_ctx* c, int field, const void* src, int on_device) {
   void* dst = field_ptr(c, field);
   const bool narrow = c->precision == PNP_MIXED && is_vel_field(field);
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (c->precision == PNP_MIXED && !is_vel_field(field)) {
+    int r = materialize(c);
+    if (r) return r;
+    c->refs_valid = false;
+  }
   if (!narrow) {
     CK(cudaMemcpyAsync(dst, src, n * sizeof(double), kind, c->stream));
   } else {
@@ -574,6 +790,10 @@ int pnp_get_state(pnp_ctx* c, int field, void* dst, int on_device) {
   const void* src = field_ptr(c, field);
   const bool narrow = c->precision == PNP_MIXED && is_vel_field(field);
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  {
+    int r = materialize(c);
+    if (r) return r;
+  }
   if (narrow) {
     double* tgt = on_device ? (double*)dst : c->stage;
     CK(launch_convert<float, double>((const float*)src, tgt, n, c->stream));
@@ -593,6 +813,11 @@ int pnp_step(pnp_ctx* c, int nsteps, double dt) {
     int r = upload_cn(c, dt);
     if (r) return r;
   }
+  {
+    int r = refresh_refs(c, dt);
+    if (r) return r;
+  }
+  if (c->precision == PNP_MIXED) c->fp64_fresh = false;
   if (c->stream == nullptr) {
     for (int n = 0; n < nsteps; ++n) CK(one_step(c, dt));
   } else {
@@ -622,6 +847,10 @@ int pnp_step(pnp_ctx* c, int nsteps, double dt) {
 int pnp_diagnostics(pnp_ctx* c, pnp_diag* out) {
   if (!c || !out) return PNP_ERR_ARG;
   if (!c->have_params || !c->have_state) return PNP_ERR_STATE;
+  {
+    int r = materialize(c);
+    if (r) return r;
+  }
   cudaError_t e = c->precision == PNP_FP64
                       ? launch_diagnostics<double>(fields<double>(c), c->g, metrics(c), c->ph, c->diag_partial,
                                                    kDiagBlocks, c->diag_out, c->status_d, c->stream)
@@ -659,6 +888,10 @@ int pnp_mean_profile(pnp_ctx* c, int field, double* out) {
   if (!c || !out || field < 0 || field >= PNP_NFIELDS) return PNP_ERR_ARG;
   const int planes = (field == PNP_V || field == PNP_HV) ? c->g.ny : c->g.nyc;
   const int P = c->g.nz * c->g.nx;
+  {
+    int r = materialize(c);
+    if (r) return r;
+  }
   const void* q = field_ptr(c, field);
   cudaError_t e = (c->precision == PNP_MIXED && is_vel_field(field))
                       ? launch_mean_profile<float>((const float*)q, planes, P, c->stage, c->stream)
@@ -687,8 +920,15 @@ int pnp_eval_explicit(pnp_ctx* c) {
   if (!c) return PNP_ERR_ARG;
   if (!c->have_params || !c->have_state) return PNP_ERR_STATE;
   const Stage st{1.0, 1.0, 0.0, 0.0};
-  cudaError_t e = c->precision == PNP_FP64 ? launch_rhs<double>(fields<double>(c), c->g, metrics(c), c->ph, st, c->stream)
-                                           : launch_rhs<float>(fields<float>(c), c->g, metrics(c), c->ph, st, c->stream);
+  cudaError_t e;
+  if (c->precision == PNP_FP64) {
+    e = launch_rhs<double>(fields<double>(c), c->g, metrics(c), c->ph, st, c->stream);
+  } else {
+    int r = refresh_refs(c, std::isfinite(c->refs_dt) ? c->refs_dt : 1.0);
+    if (r) return r;
+    e = launch_mixed_rhs(fields<float>(c), shadows(c), mixed_refs(c), c->g, metrics_f(c), c->ph, st, 0, c->stream);
+    c->fp64_fresh = false;
+  }
   return e == cudaSuccess ? PNP_OK : PNP_ERR_CUDA;
 }
 
@@ -726,6 +966,11 @@ int pnp_profile(pnp_ctx* c, int nsteps, double dt, double* ms_out, int nsites, i
     int r = upload_cn(c, dt);
     if (r) return r;
   }
+  {
+    int r = refresh_refs(c, dt);
+    if (r) return r;
+  }
+  if (c->precision == PNP_MIXED) c->fp64_fresh = false;
   Prof prof;
   for (int i = 0; i < Prof::kMax; ++i) CK(cudaEventCreate(&prof.ev[i]));
   for (int i = 0; i < PNP_PROFILE_SITES; ++i) ms_out[i] = 0.0;
@@ -734,7 +979,7 @@ int pnp_profile(pnp_ctx* c, int nsteps, double dt, double* ms_out, int nsites, i
   for (int n = 0; n < nsteps && rc == PNP_OK; ++n) {
     for (int l = 0; l < 3 && rc == PNP_OK; ++l) {
       prof.n = 0;
-      cudaError_t e = c->precision == PNP_FP64 ? substage<double>(c, dt, l) : substage<float>(c, dt, l);
+      cudaError_t e = c->precision == PNP_FP64 ? substage<double>(c, dt, l) : substage_mixed(c, dt, l);
       if (e != cudaSuccess || prof.n != PNP_PROFILE_SITES + 1 || cudaStreamSynchronize(c->stream) != cudaSuccess) {
         rc = PNP_ERR_CUDA;
         break;

@@ -95,14 +95,15 @@ cudaError_t launch_cn_solves(const Fields<TV>& f, const Geo& g, const CNRows& ve
                              const CNRows& ion, cudaStream_t s);
 
 // Poisson pipeline pieces.  Spectral buffer holds (nyc, nz, mp) complex T.
-enum class PoissonSrc { Divergence, Charge, Plain };
-enum class PoissonDst { Plain, Potential };
+enum class PoissonSrc { Divergence, Charge, ChargeShadow, Plain };
+enum class PoissonDst { Plain, Potential, PotentialShadow };
 
 template <typename T, typename TV>
 cudaError_t launch_fft_x_fwd(PoissonSrc src, const TV* u, const TV* v, const TV* w, const double* cp,
                              const double* cm, const T* plain, double scale, const Geo& g,
                              const Metrics& m, cplx<T>* spec, const cplx<T>* tw_half,
-                             const cplx<T>* tw_post, cudaStream_t s);
+                             const cplx<T>* tw_post, cudaStream_t s, const float* sa = nullptr,
+                             const float* sb = nullptr);
 
 template <typename T>
 cudaError_t launch_fft_z(cplx<T>* spec, const cplx<T>* tw_z, const Geo& g, bool inverse, cudaStream_t s);
@@ -110,12 +111,13 @@ cudaError_t launch_fft_z(cplx<T>* spec, const cplx<T>* tw_z, const Geo& g, bool 
 template <typename T>
 cudaError_t launch_spec_thomas(cplx<T>* spec, double* scratch, const double* kx2, const double* kz2,
                                const YRows& rows, const Geo& g, double scale, bool neumann,
-                               cudaStream_t s);
+                               cudaStream_t s, const double* mean_rhs = nullptr,
+                               const double* mean_shift = nullptr, double* mean_out = nullptr);
 
 template <typename T, typename TO>
 cudaError_t launch_fft_x_inv(PoissonDst dst, const cplx<T>* spec, const Geo& g, const Metrics& m,
                              const cplx<T>* tw_half, const cplx<T>* tw_post, double V, TO* out,
-                             cudaStream_t s);
+                             cudaStream_t s, const double* plane_add = nullptr);
 
 template <typename TV, typename TS>
 cudaError_t launch_project(TV* u, TV* v, TV* w, TV* p, const TS* phip, double scale, bool update_p,

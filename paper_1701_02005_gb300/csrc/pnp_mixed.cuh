@@ -1,0 +1,53 @@
+// Declarations of the mixed-precision path (see k_mixed.cu for the policy).
+#pragma once
+
+#include "pnp_common.cuh"
+
+namespace pnp {
+
+// FP32 copies of the per-y metric arrays (same meaning as Metrics).
+struct MetricsF {
+  const float *idy, *ih, *lo_c, *hi_c, *lo_f, *hi_f, *wl, *wu;
+};
+
+// FP32 elimination factors of the velocity Crank-Nicolson matrices.
+struct CNRowsF {
+  const float *a, *c, *m;
+};
+
+// FP32 fluctuation shadows (relative to the reference profiles).
+struct Shadows {
+  float *cp, *cm;    // c+' , c-'
+  float *phi;        // phi' = Phi - Phi_ref
+  float *Hcp, *Hcm;  // explicit ion terms minus their reference part
+};
+
+// Per-plane reference data.  FP32 arrays feed the FP32 stencils; FP64 arrays
+// hold the exact reference and the folded reference-reference terms.
+struct MixedRefs {
+  const float *cref_p, *cref_m;   // c_ref per cell plane [nyc]
+  const float *crf_p, *crf_m;     // 0.5 (c_ref_{j-1} + c_ref_j) per interior y-face [ny]
+  const float* rho_ref;           // c+_ref - c-_ref [nyc]
+  const float* rhorf;             // face mean of rho_ref [ny]
+  const float* dPref;             // Phi_ref_j - Phi_ref_{j-1} per interior face [ny]
+  const float* Fvref;             // -K rhorf dPref / h: reference Coulomb force on v [ny]
+  const double *Rref_p, *Rref_m;  // [3][nyc]: dt alp_l (H_ref + D L_y c_ref)
+  const double *cref64_p, *cref64_m, *Phiref64;   // exact references [nyc]
+  const double* mean_rhs;         // -q rho_ref [nyc]: FP64 (0,0) mode source of Eq. (4)
+  const double* mean_shift;       // V y_c - Phi_ref [nyc]
+  double* delta;                  // [nyc] written each solve: V y_c + phi_mean - Phi_ref
+};
+
+cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
+                             const MetricsF& m, const Phys& ph, const Stage& st, int l, cudaStream_t s);
+cudaError_t launch_mixed_cn(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
+                            const CNRowsF& cell, const CNRowsF& face, const CNRows& ion, cudaStream_t s);
+cudaError_t launch_plane_means3(const double* a, const double* b, const double* c, int nplanes, size_t P,
+                                double* oa, double* ob, double* oc, cudaStream_t s);
+cudaError_t launch_make_shadows(const double* cp, const double* cm, const double* Phi, const double* Hcp,
+                                const double* Hcm, const Shadows& sh, const MixedRefs& R, const double* Href_p,
+                                const double* Href_m, size_t P, size_t n, cudaStream_t s);
+cudaError_t launch_from_shadow(const float* sh, const double* ref, double* out, size_t P, size_t n, cudaStream_t s);
+
+
+}  // namespace pnp

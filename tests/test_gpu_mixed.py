@@ -1,0 +1,101 @@
+"""GPU mixed precision (FP32 stencils / FP64 ions, solves and sums) against the
+FP64 oracle.
+
+Tolerance: 1e-4 on the plane-averaged streamwise profile <u>(y) (absolute, in
+units of the wall speed) and relative 1e-4 on the wall shear stress, the
+stated accuracy target of the mixed path.  Ion numbers are FP64 sums of FP64
+fields and must stay conserved to 1e-10 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import pnp_oracle as o
+from tests import seeded
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed(g, prm):
+    from paper_1701_02005_gb300 import binding as B
+    from paper_1701_02005_gb300.solver import Solver
+
+    s = Solver(g.nx, g.ny, g.nz, g.Lx, g.Lz, precision=B.PNP_MIXED, y_faces=g.yf)
+    s.set_params(prm.Re, prm.lam, prm.Sc, prm.V, prm.beta, prm.Uw)
+    return s
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def test_mixed_explicit_terms_close_to_oracle():
+    g = o.Grid(32, 21, 16, 2 * math.pi, math.pi, stretch=2.0)
+    prm = o.Params(Re=300.0, lam=0.05, Sc=1.0, V=2.0, beta=0.5)
+    st = o.initial_state(g, prm, o.IC_PB, seed=5, amp=0.1)
+    shp = (g.nyc, g.nz, g.nx)
+    st.cp = st.cp * seeded.positive_field(6, shp, 0.98, 1.02)
+    st.cm = st.cm * seeded.positive_field(7, shp, 0.98, 1.02)
+    st.Phi = o.potential_from_ions(g, prm, st.cp, st.cm)
+    s = _mixed(g, prm)
+    s.set_state(st)
+    s.eval_explicit()
+    H = o.explicit_terms(g, prm, st)
+    errs = {n: _rel(s.get(n), ref) for n, ref in zip(("Hu", "Hv", "Hw", "Hcp", "Hcm"), H)}
+    # FP32 stencils: relative 1e-5 of each field's scale
+    assert all(e <= 2e-5 for e in errs.values()), errs
+    s.close()
+
+
+def test_mixed_c1_against_fp64_oracle():
+    g = o.Grid(32, 33, 32, 2 * math.pi, math.pi, stretch=2.0)
+    prm = o.Params(Re=400.0, lam=0.05, Sc=1.0, V=2.0, beta=0.5)
+    st0 = o.initial_state(g, prm, o.IC_PB, seed=1701, amp=1e-2)
+    s = _mixed(g, prm)
+    s.set_state(st0)
+    nsteps, dt = 100, 0.01
+    s.step(nsteps, dt)
+    ref = o.step(g, prm, st0, dt, nsteps)
+    du = np.max(np.abs(s.mean_profile("u") - o.mean_profile(ref.u)))
+    d, dr, d0 = s.diagnostics(), o.diagnostics(g, prm, ref), o.diagnostics(g, prm, st0)
+    tau_err = max(abs(d["tau_bot"] - dr["tau_bot"]) / abs(dr["tau_bot"]),
+                  abs(d["tau_top"] - dr["tau_top"]) / abs(dr["tau_top"]))
+    field_errs = {n: _rel(s.get(n), getattr(ref, n)) for n in ("u", "v", "w", "cp", "cm", "Phi")}
+    print("mixed C1: <u> err", du, "tau err", tau_err, "fields", field_errs)
+    assert du <= 1e-4 and tau_err <= 1e-4, (du, tau_err)
+    assert field_errs["cp"] <= 1e-5 and field_errs["cm"] <= 1e-5 and field_errs["Phi"] <= 1e-5, field_errs
+    assert abs(d["n_plus"] - d0["n_plus"]) <= 1e-10 * d0["n_plus"]
+    assert abs(d["n_minus"] - d0["n_minus"]) <= 1e-10 * d0["n_minus"]
+    assert d["status"] == 0
+    s.close()
+
+
+def test_mixed_double_layer_at_rest_stays_poisson_boltzmann():
+    # walls at rest: a discrete Poisson-Boltzmann state (from the FP64 oracle march)
+    # must stay stationary in mixed precision — the Debye-layer cancellation is FP64.
+    g = o.Grid(4, 33, 4, 1.0, 1.0, stretch=1.5)
+    prm = o.Params(Re=1.0, lam=0.1, Sc=1.0, V=2.0, beta=0.5, Uw=0.0)
+    st = o.initial_state(g, prm, o.IC_LAMINAR)
+    st = o.step(g, prm, st, 8e-3, 600)
+    s = _mixed(g, prm)
+    s.set_state(st)
+    s.step(200, 8e-3)
+    ref = o.step(g, prm, st, 8e-3, 200)
+    for n in ("cp", "cm", "Phi"):
+        assert _rel(s.get(n), getattr(ref, n)) <= 1e-9, n
+    assert np.max(np.abs(s.get("u"))) <= 1e-6
+    s.close()
+
+
+def test_mixed_laminar_couette_exact():
+    g = o.Grid(16, 17, 8, 2 * math.pi, math.pi, stretch=2.0)
+    prm = o.Params(Re=400.0, lam=0.05, Sc=1.0, V=0.0)
+    s = _mixed(g, prm)
+    s.init_state(0, 1, 0.0)
+    s.step(20, 0.01)
+    d = s.diagnostics()
+    # FP32 storage of u: relative 1e-5 on tau_w, 1e-6 absolute on u
+    assert abs(d["tau_bot"] - 1 / 400) <= 1e-5 * (1 / 400)
+    assert np.max(np.abs(s.get("u") - g.yc[:, None, None])) <= 1e-6
+    s.close()
