@@ -40,33 +40,31 @@ def cells(wl=WL):
 
 
 # --------------------------------------------------------------------------
-# Algorithmic cost per cell per substage of each launch site (FP64 words / ops
-# read from the kernel sources: fields touched once each, flops of the
-# finite-volume formulas).  Used for the roofline of the dominant kernel.
+# Algorithmic cost per cell per substage of each launch site: bytes every
+# input read once and every output written once, and FP64-pipe instructions
+# (FP64 arithmetic and FP64<->FP32 conversions), counted from the kernel
+# sources.  ``half`` = spectral points per real point ((Nx/2+1)/Nx).
 # --------------------------------------------------------------------------
 def site_cost(site, precision):
-    tv = 8 if precision == "fp64" else 4   # velocity/pressure word size
-    td = 8
-    half = 0.5 * (1 + 2.0 / WL["nx"])       # spectral points per real point (nx/2+1 of nx)
-    ts_p = 16 if precision == "fp64" else 8  # pressure spectral complex word
-    cost = {
-        # reads u v w p H_u H_v H_w (vel), c+ c- Phi H_c+ H_c- (fp64); writes H x5 and r x5
-        "rhs": dict(bytes=7 * tv + 5 * td + 3 * tv * 2 + 2 * td * 2, flops=265),
-        # read r, write d, read d, read q, write q  (u, v, w in vel type; c+- fp64)
-        "cn_thomas": dict(bytes=3 * 5 * tv + 2 * 5 * td, flops=3 * 5 + 2 * 5),
-        "p_fftx": dict(bytes=3 * tv + ts_p * half, flops=6 + 5 * math.log2(WL["nx"]) / 2 + 6),
-        "p_fftz": dict(bytes=2 * ts_p * half, flops=half * 5 * math.log2(WL["nz"])),
-        "p_thomas": dict(bytes=2 * 2 * ts_p * half + 2 * 8 * half, flops=half * 16),
-        "p_ifftz": dict(bytes=2 * ts_p * half, flops=half * 5 * math.log2(WL["nz"])),
-        "p_ifftx": dict(bytes=ts_p * half + tv, flops=5 * math.log2(WL["nx"]) / 2 + 6),
-        "project": dict(bytes=tv + 4 * 2 * tv, flops=12),
-        "e_fftx": dict(bytes=2 * td + 16 * half, flops=2 + 5 * math.log2(WL["nx"]) / 2 + 6),
-        "e_fftz": dict(bytes=2 * 16 * half, flops=half * 5 * math.log2(WL["nz"])),
-        "e_thomas": dict(bytes=2 * 2 * 16 * half + 2 * 8 * half, flops=half * 16),
-        "e_ifftz": dict(bytes=2 * 16 * half, flops=half * 5 * math.log2(WL["nz"])),
-        "e_ifftx": dict(bytes=16 * half + td, flops=5 * math.log2(WL["nx"]) / 2 + 7),
-    }
-    return cost[site]
+    half = (WL["nx"] // 2 + 1) / WL["nx"]
+    if precision == "fp64":
+        table = {
+            "rhs": (176, 220), "cn_thomas": (200, 20),
+            "p_fftx": (24 + 16 * half, 30), "p_fftz": (32 * half, 20), "p_thomas": (80 * half, 10 * half),
+            "p_ifftz": (32 * half, 20), "p_ifftx": (16 * half + 8, 22), "project": (72, 8),
+            "e_fftx": (16 + 16 * half, 24), "e_fftz": (32 * half, 20), "e_thomas": (80 * half, 10 * half),
+            "e_ifftz": (32 * half, 20), "e_ifftx": (16 * half + 8, 22),
+        }
+    else:
+        table = {
+            "rhs": (120, 4), "cn_thomas": (148, 12),
+            "p_fftx": (12 + 8 * half, 0), "p_fftz": (16 * half, 0), "p_thomas": (48 * half, 14 * half),
+            "p_ifftz": (16 * half, 0), "p_ifftx": (8 * half + 4, 0), "project": (36, 0),
+            "e_fftx": (8 + 8 * half, 0), "e_fftz": (16 * half, 0), "e_thomas": (48 * half, 14 * half),
+            "e_ifftz": (16 * half, 0), "e_ifftx": (8 * half + 4, 0.25),
+        }
+    b, f = table[site]
+    return {"bytes": b, "fp64_ops": f}
 
 
 # --------------------------------------------------------------------------
@@ -206,7 +204,6 @@ def run_ours(args):
     s.set_params(WL["Re"], WL["lam"], WL["Sc"], WL["V"], WL["beta"])
     s.init_state(B.PNP_IC_PB, WL["seed"] + rank, WL["amp"])
     dt = WL["dt"]
-    fp64_peak = s.fp64_peak()
     K, W = args.steps, args.warmup
     s.step(W, dt)
     s.synchronize()
@@ -243,26 +240,71 @@ def run_ours(args):
     total = sum(per_launch.values())
     dom = max(per_launch, key=per_launch.get)
     pname = "fp64" if prec == B.PNP_FP64 else "mixed"
-    cst = site_cost(dom, pname)
+    fp64_peak = max(s.fp64_peak(), s.fp64_peak())   # measured now, at working clocks
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
+    sites = {}
+    for k, v in per_launch.items():
+        cst = site_cost(k, pname)
+        d = v * 1e-3
+        gbs = cst["bytes"] * n_cells / d / 1e9
+        tf = 2.0 * cst["fp64_ops"] * n_cells / d / 1e12   # FP64 ops counted as FMA-equivalent flops
+        sites[k] = {"ms": round(v, 4), "share": round(v / total, 4), "hbm_frac": round(gbs / hbm_peak, 4),
+                    "fp64_frac": round(tf / (fp64_peak / 1e12), 4)}
+    cst = site_cost(dom, pname)
     dur = per_launch[dom] * 1e-3
-    alu_tf = cst["flops"] * n_cells / dur / 1e12
     hbm_gbs = cst["bytes"] * n_cells / dur / 1e9
+    alu_tf = 2.0 * cst["fp64_ops"] * n_cells / dur / 1e12
     if alu_tf / (fp64_peak / 1e12) > hbm_gbs / hbm_peak:
         roof = {"bound": "alu", "achieved": alu_tf, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
                 "frac": alu_tf / (fp64_peak / 1e12), "traffic": None, "kernel": dom,
-                "peak_source": "FP64 FMA probe measured live (pnp_fp64_peak)",
-                "hbm_view": {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak}}
+                "peak_source": "FP64 FMA throughput measured live in this run (pnp_fp64_peak)",
+                "per_unit": f"{cst['fp64_ops']} FP64-pipe instructions per cell x {n_cells} cells per launch"}
     else:
         roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_gbs / hbm_peak,
-                "traffic": None, "kernel": dom, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
-                "alu_view": {"achieved_tflops": alu_tf, "fp64_peak_tflops": fp64_peak / 1e12}}
+                "traffic": None, "kernel": dom, "peak_source": hbm_src,
+                "per_unit": f"{cst['bytes']:.1f} B per cell x {n_cells} cells per launch"}
     roof["share"] = per_launch[dom] / total
+
+    # the FP64 path on the same workload, and the mixed-vs-FP64 error from one initial state
+    cmp = None
+    if prec == B.PNP_MIXED and not args.no_fp64_compare:
+        s64 = Solver(WL["nx"], WL["ny"], WL["nz"], WL["Lx"], WL["Lz"], stretch=WL["stretch"], precision=B.PNP_FP64,
+                     device=local)
+        s64.set_params(WL["Re"], WL["lam"], WL["Sc"], WL["V"], WL["beta"])
+        s64.init_state(B.PNP_IC_PB, WL["seed"] + rank, WL["amp"])
+        smx = Solver(WL["nx"], WL["ny"], WL["nz"], WL["Lx"], WL["Lz"], stretch=WL["stretch"], precision=B.PNP_MIXED,
+                     device=local)
+        smx.set_params(WL["Re"], WL["lam"], WL["Sc"], WL["V"], WL["beta"])
+        for nm in ("u", "v", "w", "p", "cp", "cm", "Phi"):
+            smx.set_device(nm, torch.from_numpy(s64.get(nm)).to(s64.device))
+        Kc = args.compare_steps
+        s64.step(1, dt)
+        s64.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(s64.stream)
+        s64.step(Kc - 1, dt)
+        f1.record(s64.stream)
+        s64.synchronize()
+        t64 = f0.elapsed_time(f1) / 1e3 / (Kc - 1)
+        smx.step(Kc, dt)
+        smx.synchronize()
+        um64, ummx = s64.mean_profile("u"), smx.mean_profile("u")
+        d64, dmx = s64.diagnostics(), smx.diagnostics()
+        cmp = {"fp64_value": n_cells / t64, "fp64_ms_per_step": 1e3 * t64, "speedup": (value / world) / (n_cells / t64),
+               "steps": Kc, "mean_u_abs_err": float(np.max(np.abs(ummx - um64))),
+               "tau_w_rel_err": float(max(abs(dmx["tau_bot"] - d64["tau_bot"]) / abs(d64["tau_bot"]),
+                                          abs(dmx["tau_top"] - d64["tau_top"]) / abs(d64["tau_top"]))),
+               "n_plus_rel_drift": float(abs(dmx["n_plus"] - d64["n_plus"]) / d64["n_plus"]),
+               "tolerance": 1e-4}
+        s64.close()
+        smx.close()
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -303,11 +345,12 @@ def run_ours(args):
                    "precision": pname, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (working set ~2 GB vs 129 MB), no flush"},
         "roofline": roof,
+        "mixed_vs_fp64": cmp,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": lps * K,
         "clocks": clocks,
-        "per_site_ms": {k: round(v, 4) for k, v in per_launch.items()},
+        "sites": sites,
         "status": diag["status"],
         "check": {"max_div": diag["max_div"], "n_plus": diag["n_plus"], "tau_bot": diag["tau_bot"]},
     }
@@ -325,11 +368,20 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--compare-steps", type=int, default=20)
+    ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", default=None,
+                    help="NX,NY,NZ override of the workload grid (small cases for profiler captures only)")
     args = ap.parse_args()
+    if args.grid:
+        nx, ny, nz = (int(x) for x in args.grid.split(","))
+        WL.update(nx=nx, ny=ny, nz=nz)
+        global WL_NAME
+        WL_NAME = WL_NAME.replace("256x193x256", f"{nx}x{ny}x{nz}") + " (grid override)"
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

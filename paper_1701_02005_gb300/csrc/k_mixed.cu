@@ -26,7 +26,7 @@ __device__ __forceinline__ float Lf(const float* p, size_t i) { return __ldg(p +
 // Momentum right-hand sides, FP32 (u, w on every cell; v on faces j >= 1).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_mom_mixed(Fields<float> f, Shadows sh, MixedRefs R, Geo g, MetricsF mt,
-                                                   Phys ph, Stage st) {
+                                                   CoefF cf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y * blockDim.y + threadIdx.y;
   const int j = blockIdx.z;
@@ -35,15 +35,15 @@ __global__ void __launch_bounds__(128) k_mom_mixed(Fields<float> f, Shadows sh, 
   const int im = i ? i - 1 : nx - 1, ip = (i + 1 == nx) ? 0 : i + 1;
   const int km = k ? k - 1 : nz - 1, kp = (k + 1 == nz) ? 0 : k + 1;
   const bool has_dn = j > 0, has_up = j < nyc - 1;
-  const float idx = (float)g.idx, idz = (float)g.idz;
+  const float idx = cf.idx, idz = cf.idz;
   const float idx2 = idx * idx, idz2 = idz * idz;
   const size_t c0 = cidx(j, k, i, nz, nx);
   const size_t cxm = cidx(j, k, im, nz, nx), cxp = cidx(j, k, ip, nz, nx);
   const size_t czm = cidx(j, km, i, nz, nx), czp = cidx(j, kp, i, nz, nx);
   const size_t P = (size_t)nz * nx;
   const float idyj = mt.idy[j];
-  const float nu = (float)ph.nu, K = (float)ph.K, Uw = (float)ph.Uw;
-  const float dt = (float)st.dt, gam = (float)st.gam, zet = (float)st.zet, alp = (float)st.alp;
+  const float nu = cf.nu, K = cf.K, Uw = cf.Uw;
+  const float dt = cf.dt, gam = cf.gam, zet = cf.zet, alp = cf.alp;
 
   const float u0 = Lf(f.u, c0), uxm = Lf(f.u, cxm), uxp = Lf(f.u, cxp), uzm = Lf(f.u, czm), uzp = Lf(f.u, czp);
   const float uym = has_dn ? Lf(f.u, c0 - P) : 0.f, uyp = has_up ? Lf(f.u, c0 + P) : 0.f;
@@ -134,8 +134,7 @@ __global__ void __launch_bounds__(128) k_mom_mixed(Fields<float> f, Shadows sh, 
 // constant, r_c = Rref(j) + dt [gam H' + zet H'_old + alp D L_y c'] in FP64.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_ion_mixed(Fields<float> f, double* __restrict__ rcp, double* __restrict__ rcm,
-                                                   Shadows sh, MixedRefs R, Geo g, MetricsF mt, Phys ph, Stage st,
-                                                   int l) {
+                                                   Shadows sh, MixedRefs R, Geo g, MetricsF mt, CoefF cf, int l) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y * blockDim.y + threadIdx.y;
   const int j = blockIdx.z;
@@ -144,13 +143,13 @@ __global__ void __launch_bounds__(128) k_ion_mixed(Fields<float> f, double* __re
   const int im = i ? i - 1 : nx - 1, ip = (i + 1 == nx) ? 0 : i + 1;
   const int km = k ? k - 1 : nz - 1, kp = (k + 1 == nz) ? 0 : k + 1;
   const bool has_dn = j > 0, has_up = j < nyc - 1;
-  const float idx = (float)g.idx, idz = (float)g.idz;
+  const float idx = cf.idx, idz = cf.idz;
   const size_t c0 = cidx(j, k, i, nz, nx);
   const size_t cxm = cidx(j, k, im, nz, nx), cxp = cidx(j, k, ip, nz, nx);
   const size_t czm = cidx(j, km, i, nz, nx), czp = cidx(j, kp, i, nz, nx);
   const size_t P = (size_t)nz * nx;
-  const float D = (float)ph.D;
-  const float dt = (float)st.dt, gam = (float)st.gam, zet = (float)st.zet, alp = (float)st.alp;
+  const float D = cf.D;
+  const float dt = cf.dt, gam = cf.gam, zet = cf.zet, alp = cf.alp;
   const float idyj = mt.idy[j], ihj = mt.ih[j], ihjp = mt.ih[j + 1];
   const float lo = mt.lo_c[j], hi = mt.hi_c[j];
 
@@ -205,6 +204,7 @@ __global__ void __launch_bounds__(128) k_ion_mixed(Fields<float> f, double* __re
 __global__ void k_cn_ion_mixed(double* __restrict__ cp, double* __restrict__ rcp, float* __restrict__ sp,
                                double* __restrict__ cm, double* __restrict__ rcm, float* __restrict__ sm,
                                CNRows rows, MixedRefs R, int n, size_t P) {
+  constexpr int CH = 8;   // planes loaded ahead per sweep step
   const size_t line = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (line >= P) return;
   const bool plus = blockIdx.y == 0;
@@ -213,18 +213,41 @@ __global__ void k_cn_ion_mixed(double* __restrict__ cp, double* __restrict__ rcp
   float* s = plus ? sp : sm;
   const double* cref = plus ? R.cref64_p : R.cref64_m;
   double d = 0.0;
-  for (int j = 0; j < n; ++j) {
-    const size_t o = (size_t)j * P + line;
-    d = (r[o] - rows.a[j] * d) * rows.m[j];
-    r[o] = d;
+  for (int jb = 0; jb < n; jb += CH) {
+    double rr[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+      if (jb + u < n) rr[u] = r[(size_t)(jb + u) * P + line];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int j = jb + u;
+      if (j < n) {
+        d = (rr[u] - rows.a[j] * d) * rows.m[j];
+        r[(size_t)j * P + line] = d;
+      }
+    }
   }
   double x = 0.0;
-  for (int j = n - 1; j >= 0; --j) {
-    const size_t o = (size_t)j * P + line;
-    x = r[o] - rows.c[j] * x;
-    const double cn = q[o] + x;
-    q[o] = cn;
-    s[o] = (float)(cn - cref[j]);
+  for (int jb = n - 1; jb >= 0; jb -= CH) {
+    double dd[CH], qq[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+      if (jb - u >= 0) {
+        const size_t o = (size_t)(jb - u) * P + line;
+        dd[u] = r[o];
+        qq[u] = q[o];
+      }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int j = jb - u;
+      if (j >= 0) {
+        const size_t o = (size_t)j * P + line;
+        x = dd[u] - rows.c[j] * x;
+        const double cn = qq[u] + x;
+        q[o] = cn;
+        s[o] = (float)(cn - cref[j]);
+      }
+    }
   }
 }
 
@@ -232,6 +255,7 @@ __global__ void k_cn_ion_mixed(double* __restrict__ cp, double* __restrict__ rcp
 __global__ void k_cn_vel_f32(float* __restrict__ u, float* __restrict__ ru, float* __restrict__ v,
                              float* __restrict__ rv, float* __restrict__ w, float* __restrict__ rw,
                              CNRowsF cell, CNRowsF face, int nyc, size_t P) {
+  constexpr int CH = 8;
   const size_t line = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (line >= P) return;
   float* q;
@@ -244,14 +268,37 @@ __global__ void k_cn_vel_f32(float* __restrict__ u, float* __restrict__ ru, floa
   float* rl = r + (size_t)j0 * P + line;
   float* ql = q + (size_t)j0 * P + line;
   float d = 0.f;
-  for (int j = 0; j < n; ++j) {
-    d = (rl[(size_t)j * P] - rw_.a[j] * d) * rw_.m[j];
-    rl[(size_t)j * P] = d;
+  for (int jb = 0; jb < n; jb += CH) {
+    float rr[CH];
+#pragma unroll
+    for (int k = 0; k < CH; ++k)
+      if (jb + k < n) rr[k] = rl[(size_t)(jb + k) * P];
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+      const int j = jb + k;
+      if (j < n) {
+        d = (rr[k] - rw_.a[j] * d) * rw_.m[j];
+        rl[(size_t)j * P] = d;
+      }
+    }
   }
   float x = 0.f;
-  for (int j = n - 1; j >= 0; --j) {
-    x = rl[(size_t)j * P] - rw_.c[j] * x;
-    ql[(size_t)j * P] += x;
+  for (int jb = n - 1; jb >= 0; jb -= CH) {
+    float dd[CH], qq[CH];
+#pragma unroll
+    for (int k = 0; k < CH; ++k)
+      if (jb - k >= 0) {
+        dd[k] = rl[(size_t)(jb - k) * P];
+        qq[k] = ql[(size_t)(jb - k) * P];
+      }
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+      const int j = jb - k;
+      if (j >= 0) {
+        x = dd[k] - rw_.c[j] * x;
+        ql[(size_t)j * P] = qq[k] + x;
+      }
+    }
   }
 }
 
@@ -314,13 +361,13 @@ __global__ void k_from_shadow(const float* __restrict__ s, const double* __restr
 
 // ---------------------------------------------------------------------------
 cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
-                             const MetricsF& m, const Phys& ph, const Stage& st, int l, cudaStream_t s) {
+                             const MetricsF& m, const CoefF& cf, int l, cudaStream_t s) {
   dim3 blk(32, 4, 1);
   dim3 grd((g.nx + 31) / 32, (g.nz + 3) / 4, g.nyc);
-  k_mom_mixed<<<grd, blk, 0, s>>>(f, sh, R, g, m, ph, st);
+  k_mom_mixed<<<grd, blk, 0, s>>>(f, sh, R, g, m, cf);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_ion_mixed<<<grd, blk, 0, s>>>(f, f.rcp, f.rcm, sh, R, g, m, ph, st, l);
+  k_ion_mixed<<<grd, blk, 0, s>>>(f, f.rcp, f.rcm, sh, R, g, m, cf, l);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@ __global__ void k_cn_thomas(TQ* __restrict__ q0, TR* __restrict__ r0, TQ* __rest
                             TR* __restrict__ r1, TQ* __restrict__ q2, TR* __restrict__ r2,
                             CNRows rows0, CNRows rows1, CNRows rows2, int n0, int n1, int n2,
                             int j00, int j01, int j02, size_t P) {
+  constexpr int CH = 8;   // planes loaded ahead per sweep step
   const size_t line = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (line >= P) return;
   TQ* q;
@@ -37,14 +38,37 @@ __global__ void k_cn_thomas(TQ* __restrict__ q0, TR* __restrict__ r0, TQ* __rest
   TR* rl = r + (size_t)j0 * P + line;
   TQ* ql = q + (size_t)j0 * P + line;
   double d = 0.0;
-  for (int j = 0; j < n; ++j) {
-    d = ((double)rl[(size_t)j * P] - rw.a[j] * d) * rw.m[j];
-    rl[(size_t)j * P] = (TR)d;
+  for (int jb = 0; jb < n; jb += CH) {
+    double rr[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+      if (jb + u < n) rr[u] = (double)rl[(size_t)(jb + u) * P];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int j = jb + u;
+      if (j < n) {
+        d = (rr[u] - rw.a[j] * d) * rw.m[j];
+        rl[(size_t)j * P] = (TR)d;
+      }
+    }
   }
   double x = 0.0;
-  for (int j = n - 1; j >= 0; --j) {
-    x = (double)rl[(size_t)j * P] - rw.c[j] * x;
-    ql[(size_t)j * P] = (TQ)((double)ql[(size_t)j * P] + x);
+  for (int jb = n - 1; jb >= 0; jb -= CH) {
+    double dd[CH], qq[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+      if (jb - u >= 0) {
+        dd[u] = (double)rl[(size_t)(jb - u) * P];
+        qq[u] = (double)ql[(size_t)(jb - u) * P];
+      }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int j = jb - u;
+      if (j >= 0) {
+        x = dd[u] - rw.c[j] * x;
+        ql[(size_t)j * P] = (TQ)(qq[u] + x);
+      }
+    }
   }
 }
 
@@ -104,6 +128,9 @@ struct SrcArgs {
   const T* plain;
   double scale;
   const float *sa, *sb;   // FP32 charge shadows c+', c-'
+  T sx, sz;               // scale / dx, scale / dz in the transform's precision
+  const T* idyT;          // 1 / dy in the transform's precision
+  T ss;                   // scale
 };
 
 template <typename T, typename TV>
@@ -114,16 +141,16 @@ __device__ __forceinline__ T src_value(const SrcArgs<T, TV>& a, const Geo& g, co
     // div(u_hat) / (alp dt): finite-volume form of Eq. (2)
     const int ip = (i + 1 == g.nx) ? 0 : i + 1;
     const int kp = (k + 1 == g.nz) ? 0 : k + 1;
-    const double du = ((double)a.u[cidx(j, k, ip, g.nz, g.nx)] - (double)a.u[c]) * g.idx;
-    const double dv = ((double)a.v[c + (size_t)g.nz * g.nx] - (double)a.v[c]) * m.idy[j];
-    const double dw = ((double)a.w[cidx(j, kp, i, g.nz, g.nx)] - (double)a.w[c]) * g.idz;
-    return (T)((du + dv + dw) * a.scale);
+    const T du = ((T)a.u[cidx(j, k, ip, g.nz, g.nx)] - (T)a.u[c]) * a.sx;
+    const T dv = ((T)a.v[c + (size_t)g.nz * g.nx] - (T)a.v[c]) * (a.idyT[j] * a.ss);
+    const T dw = ((T)a.w[cidx(j, kp, i, g.nz, g.nx)] - (T)a.w[c]) * a.sz;
+    return du + dv + dw;
   } else if (a.kind == PoissonSrc::Charge) {
     // Eq. (4): -(c+ - c-) / (2 lam^2)
     return (T)(-(a.cp[c] - a.cm[c]) * a.scale);
   } else if (a.kind == PoissonSrc::ChargeShadow) {
     // fluctuating charge about the reference profile, FP32
-    return T(-(a.sa[c] - a.sb[c])) * T(a.scale);
+    return T(-(a.sa[c] - a.sb[c])) * a.ss;
   }
   return a.plain[c];
 }
@@ -177,8 +204,10 @@ template <typename T, typename TV>
 cudaError_t launch_fft_x_fwd(PoissonSrc kind, const TV* u, const TV* v, const TV* w, const double* cp,
                              const double* cm, const T* plain, double scale, const Geo& g,
                              const Metrics& m, cplx<T>* spec, const cplx<T>* tw_half,
-                             const cplx<T>* tw_post, cudaStream_t s, const float* sa, const float* sb) {
-  SrcArgs<T, TV> a{kind, u, v, w, cp, cm, plain, scale, sa, sb};
+                             const cplx<T>* tw_post, cudaStream_t s, const float* sa, const float* sb,
+                             const T* idyT) {
+  SrcArgs<T, TV> a{kind, u, v, w, cp, cm, plain, scale, sa, sb, (T)(scale * g.idx), (T)(scale * g.idz), idyT,
+                   (T)scale};
   dim3 blk, grd;
   size_t smem;
   fft_x_shape<T>(g, blk, grd, smem);
@@ -304,14 +333,14 @@ cudaError_t launch_fft_z(cplx<T>* spec, const cplx<T>* tw_z, const Geo& g, bool 
 // ---------------------------------------------------------------------------
 // Spectral Thomas: per (m, n), solve a_j x_{j-1} + (b_j - kx2_m - kz2_n) x_j
 // + c_j x_{j+1} = scale * rhs_j in FP64.  The Neumann (0,0) mode replaces its
-// bottom-row equation by x_0 = 0.  The elimination multipliers c'_j go to the
-// FP64 scratch (one value per spectral point).
+// bottom-row equation by x_0 = 0.  The elimination factors depend only on the
+// grid, so they are computed once (k_spec_factors): inv_j = 1 / (B_j - a_j
+// c'_{j-1}) and c'_j = c_j inv_j, stored per spectral point in FP64.
+// The sweeps load CH planes ahead so that a thread keeps CH independent
+// memory requests in flight instead of one per serial step.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void k_spec_thomas(cplx<T>* __restrict__ spec, double* __restrict__ cpr, const double* __restrict__ kx2,
-                              const double* __restrict__ kz2, YRows rows, Geo g, double scale, bool neumann,
-                              const double* __restrict__ mean_rhs, const double* __restrict__ mean_shift,
-                              double* __restrict__ mean_out) {
+__global__ void k_spec_factors(double* __restrict__ cpr, double* __restrict__ inv, const double* __restrict__ kx2,
+                               const double* __restrict__ kz2, YRows rows, Geo g, bool neumann) {
   const int mm = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = blockIdx.y;
   if (mm >= g.mh) return;
@@ -319,30 +348,74 @@ __global__ void k_spec_thomas(cplx<T>* __restrict__ spec, double* __restrict__ c
   const size_t base = (size_t)n * g.mp + mm;
   const double k2 = kx2[mm] + kz2[n];
   const bool pin = neumann && mm == 0 && n == 0;
+  double cprev = 0.0;
+  for (int j = 0; j < g.nyc; ++j) {
+    double a = rows.a[j], b = rows.b[j] - k2, c = rows.c[j];
+    if (pin && j == 0) { b = 1.0; c = 0.0; }
+    const double iv = 1.0 / (b - a * cprev);
+    cprev = c * iv;
+    cpr[base + (size_t)j * P] = cprev;
+    inv[base + (size_t)j * P] = iv;
+  }
+}
+
+cudaError_t launch_spec_factors(double* cpr, double* inv, const double* kx2, const double* kz2, const YRows& rows,
+                                const Geo& g, bool neumann, cudaStream_t s) {
+  const int T_ = 64;
+  dim3 grd((g.mh + T_ - 1) / T_, g.nz, 1);
+  k_spec_factors<<<grd, T_, 0, s>>>(cpr, inv, kx2, kz2, rows, g, neumann);
+  return cudaGetLastError();
+}
+
+constexpr int kCH = 8;
+
+template <typename T>
+__global__ void k_spec_thomas(cplx<T>* __restrict__ spec, const double* __restrict__ cpr,
+                              const double* __restrict__ inv, YRows rows, Geo g, double scale, bool neumann,
+                              const double* __restrict__ mean_rhs, const double* __restrict__ mean_shift,
+                              double* __restrict__ mean_out) {
+  const int mm = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.y;
+  if (mm >= g.mh) return;
+  const size_t P = (size_t)g.nz * g.mp;
+  const size_t base = (size_t)n * g.mp + mm;
+  const int ny = g.nyc;
+  const bool pin = neumann && mm == 0 && n == 0;
   // FP64 mean mode: the (0,0) source gets the FP64 reference charge and its
   // elimination runs entirely in FP64 storage (mean_out), never in spec.
   const bool mean_mode = mean_rhs != nullptr && mm == 0 && n == 0;
-  double cprev = 0.0, dre = 0.0, dim = 0.0;
-  for (int j = 0; j < g.nyc; ++j) {
-    const size_t o = base + (size_t)j * P;
-    const cplx<T> r = spec[o];
-    double a = rows.a[j], b = rows.b[j] - k2, c = rows.c[j];
-    double rre = (double)r.x * scale, rim = (double)r.y * scale;
-    if (mean_mode) { rre += mean_rhs[j]; rim = 0.0; }
-    if (pin && j == 0) { b = 1.0; c = 0.0; rre = 0.0; rim = 0.0; }
-    const double inv = 1.0 / (b - a * cprev);
-    cprev = c * inv;
-    dre = (rre - a * dre) * inv;
-    dim = (rim - a * dim) * inv;
-    cpr[o] = cprev;
-    if (mean_mode) mean_out[j] = dre;
-    else spec[o] = {(T)dre, (T)dim};
+  double dre = 0.0, dim = 0.0;
+  for (int j0 = 0; j0 < ny; j0 += kCH) {
+    cplx<T> rr[kCH];
+    double iv[kCH];
+#pragma unroll
+    for (int u = 0; u < kCH; ++u) {
+      if (j0 + u < ny) {
+        const size_t o = base + (size_t)(j0 + u) * P;
+        rr[u] = spec[o];
+        iv[u] = inv[o];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kCH; ++u) {
+      const int j = j0 + u;
+      if (j < ny) {
+        const double a = rows.a[j];
+        double rre = (double)rr[u].x * scale, rim = (double)rr[u].y * scale;
+        if (mean_mode) { rre += mean_rhs[j]; rim = 0.0; }
+        if (pin && j == 0) { rre = 0.0; rim = 0.0; }
+        dre = (rre - a * dre) * iv[u];
+        dim = (rim - a * dim) * iv[u];
+        if (mean_mode) mean_out[j] = dre;
+        else spec[base + (size_t)j * P] = {(T)dre, (T)dim};
+      }
+    }
   }
   double xre = dre, xim = dim;
   if (mean_mode) {
-    mean_out[g.nyc - 1] = xre + mean_shift[g.nyc - 1];
-    spec[base + (size_t)(g.nyc - 1) * P] = {T(0), T(0)};
-    for (int j = g.nyc - 2; j >= 0; --j) {
+    mean_out[ny - 1] = xre + mean_shift[ny - 1];
+    spec[base + (size_t)(ny - 1) * P] = {T(0), T(0)};
+    for (int j = ny - 2; j >= 0; --j) {
       const size_t o = base + (size_t)j * P;
       xre = mean_out[j] - cpr[o] * xre;
       mean_out[j] = xre + mean_shift[j];
@@ -350,24 +423,36 @@ __global__ void k_spec_thomas(cplx<T>* __restrict__ spec, double* __restrict__ c
     }
     return;
   }
-  for (int j = g.nyc - 2; j >= 0; --j) {
-    const size_t o = base + (size_t)j * P;
-    const cplx<T> d = spec[o];
-    const double cj = cpr[o];
-    xre = (double)d.x - cj * xre;
-    xim = (double)d.y - cj * xim;
-    spec[o] = {(T)xre, (T)xim};
+  for (int j1 = ny - 2; j1 >= 0; j1 -= kCH) {
+    cplx<T> dd[kCH];
+    double cc[kCH];
+#pragma unroll
+    for (int u = 0; u < kCH; ++u) {
+      if (j1 - u >= 0) {
+        const size_t o = base + (size_t)(j1 - u) * P;
+        dd[u] = spec[o];
+        cc[u] = cpr[o];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kCH; ++u) {
+      const int j = j1 - u;
+      if (j >= 0) {
+        xre = (double)dd[u].x - cc[u] * xre;
+        xim = (double)dd[u].y - cc[u] * xim;
+        spec[base + (size_t)j * P] = {(T)xre, (T)xim};
+      }
+    }
   }
 }
 
 template <typename T>
-cudaError_t launch_spec_thomas(cplx<T>* spec, double* scratch, const double* kx2, const double* kz2,
-                               const YRows& rows, const Geo& g, double scale, bool neumann, cudaStream_t s,
-                               const double* mean_rhs, const double* mean_shift, double* mean_out) {
+cudaError_t launch_spec_thomas(cplx<T>* spec, const double* cpr, const double* inv, const YRows& rows, const Geo& g,
+                               double scale, bool neumann, cudaStream_t s, const double* mean_rhs,
+                               const double* mean_shift, double* mean_out) {
   const int T_ = 64;
   dim3 grd((g.mh + T_ - 1) / T_, g.nz, 1);
-  k_spec_thomas<T><<<grd, T_, 0, s>>>(spec, scratch, kx2, kz2, rows, g, scale, neumann, mean_rhs, mean_shift,
-                                      mean_out);
+  k_spec_thomas<T><<<grd, T_, 0, s>>>(spec, cpr, inv, rows, g, scale, neumann, mean_rhs, mean_shift, mean_out);
   return cudaGetLastError();
 }
 
@@ -375,9 +460,9 @@ cudaError_t launch_spec_thomas(cplx<T>* spec, double* scratch, const double* kx2
 // Projection: u -= scale d(phip)/dx, w -= scale d(phip)/dz, v -= scale
 // d(phip)/dy on interior faces; optionally p += phip.
 // ---------------------------------------------------------------------------
-template <typename TV, typename TS>
-__global__ void k_project(TV* __restrict__ u, TV* __restrict__ v, TV* __restrict__ w, TV* __restrict__ p,
-                          const TS* __restrict__ s, double scale, bool update_p, Geo g, Metrics m) {
+template <typename T>
+__global__ void k_project(T* __restrict__ u, T* __restrict__ v, T* __restrict__ w, T* __restrict__ p,
+                          const T* __restrict__ s, T cx, T cz, T sc, const T* __restrict__ ih, bool update_p, Geo g) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y * blockDim.y + threadIdx.y;
   const int j = blockIdx.z;
@@ -385,19 +470,19 @@ __global__ void k_project(TV* __restrict__ u, TV* __restrict__ v, TV* __restrict
   const int im = i ? i - 1 : g.nx - 1;
   const int km = k ? k - 1 : g.nz - 1;
   const size_t c = cidx(j, k, i, g.nz, g.nx);
-  const double s0 = (double)s[c];
-  u[c] = (TV)((double)u[c] - scale * (s0 - (double)s[cidx(j, k, im, g.nz, g.nx)]) * g.idx);
-  w[c] = (TV)((double)w[c] - scale * (s0 - (double)s[cidx(j, km, i, g.nz, g.nx)]) * g.idz);
-  if (j > 0) v[c] = (TV)((double)v[c] - scale * (s0 - (double)s[c - (size_t)g.nz * g.nx]) * m.ih[j]);
-  if (update_p) p[c] = (TV)((double)p[c] + s0);
+  const T s0 = s[c];
+  u[c] = u[c] - cx * (s0 - s[cidx(j, k, im, g.nz, g.nx)]);
+  w[c] = w[c] - cz * (s0 - s[cidx(j, km, i, g.nz, g.nx)]);
+  if (j > 0) v[c] = v[c] - sc * (s0 - s[c - (size_t)g.nz * g.nx]) * ih[j];
+  if (update_p) p[c] = p[c] + s0;
 }
 
-template <typename TV, typename TS>
-cudaError_t launch_project(TV* u, TV* v, TV* w, TV* p, const TS* phip, double scale, bool update_p,
-                           const Geo& g, const Metrics& m, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_project(T* u, T* v, T* w, T* p, const T* phip, double scale, bool update_p, const Geo& g,
+                           const T* ih, cudaStream_t s) {
   dim3 blk(32, 4, 1);
   dim3 grd((g.nx + 31) / 32, (g.nz + 3) / 4, g.nyc);
-  k_project<TV, TS><<<grd, blk, 0, s>>>(u, v, w, p, phip, scale, update_p, g, m);
+  k_project<T><<<grd, blk, 0, s>>>(u, v, w, p, phip, (T)(scale * g.idx), (T)(scale * g.idz), (T)scale, ih, update_p, g);
   return cudaGetLastError();
 }
 
@@ -411,27 +496,27 @@ template cudaError_t launch_fft_x_fwd<double, double>(PoissonSrc, const double*,
                                                       const double*, const double*, const double*, double,
                                                       const Geo&, const Metrics&, cplx<double>*,
                                                       const cplx<double>*, const cplx<double>*, cudaStream_t,
-                                                      const float*, const float*);
+                                                      const float*, const float*, const double*);
 template cudaError_t launch_fft_x_fwd<float, float>(PoissonSrc, const float*, const float*, const float*,
                                                     const double*, const double*, const float*, double,
                                                     const Geo&, const Metrics&, cplx<float>*,
                                                     const cplx<float>*, const cplx<float>*, cudaStream_t,
-                                                    const float*, const float*);
+                                                    const float*, const float*, const float*);
 template cudaError_t launch_fft_x_fwd<double, float>(PoissonSrc, const float*, const float*, const float*,
                                                      const double*, const double*, const double*, double,
                                                      const Geo&, const Metrics&, cplx<double>*,
                                                      const cplx<double>*, const cplx<double>*, cudaStream_t,
-                                                     const float*, const float*);
+                                                     const float*, const float*, const double*);
 
 template cudaError_t launch_fft_z<double>(cplx<double>*, const cplx<double>*, const Geo&, bool, cudaStream_t);
 template cudaError_t launch_fft_z<float>(cplx<float>*, const cplx<float>*, const Geo&, bool, cudaStream_t);
 
-template cudaError_t launch_spec_thomas<double>(cplx<double>*, double*, const double*, const double*,
-                                                const YRows&, const Geo&, double, bool, cudaStream_t,
-                                                const double*, const double*, double*);
-template cudaError_t launch_spec_thomas<float>(cplx<float>*, double*, const double*, const double*,
-                                               const YRows&, const Geo&, double, bool, cudaStream_t,
-                                               const double*, const double*, double*);
+template cudaError_t launch_spec_thomas<double>(cplx<double>*, const double*, const double*, const YRows&,
+                                                const Geo&, double, bool, cudaStream_t, const double*,
+                                                const double*, double*);
+template cudaError_t launch_spec_thomas<float>(cplx<float>*, const double*, const double*, const YRows&,
+                                               const Geo&, double, bool, cudaStream_t, const double*,
+                                               const double*, double*);
 
 template cudaError_t launch_fft_x_inv<double, double>(PoissonDst, const cplx<double>*, const Geo&, const Metrics&,
                                                       const cplx<double>*, const cplx<double>*, double, double*,
@@ -440,9 +525,9 @@ template cudaError_t launch_fft_x_inv<float, float>(PoissonDst, const cplx<float
                                                     const cplx<float>*, const cplx<float>*, double, float*,
                                                     cudaStream_t, const double*);
 
-template cudaError_t launch_project<double, double>(double*, double*, double*, double*, const double*, double, bool,
-                                                    const Geo&, const Metrics&, cudaStream_t);
-template cudaError_t launch_project<float, float>(float*, float*, float*, float*, const float*, double, bool,
-                                                  const Geo&, const Metrics&, cudaStream_t);
+template cudaError_t launch_project<double>(double*, double*, double*, double*, const double*, double, bool,
+                                            const Geo&, const double*, cudaStream_t);
+template cudaError_t launch_project<float>(float*, float*, float*, float*, const float*, double, bool, const Geo&,
+                                           const float*, cudaStream_t);
 
 }  // namespace pnp

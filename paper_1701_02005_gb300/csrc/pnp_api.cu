@@ -80,6 +80,8 @@ struct pnp_ctx {
   float *crefp_f, *crefm_f, *crfp_f, *crfm_f, *rhoref_f, *rhorf_f, *dPref_f, *Fvref_f;
   double *Rrefp_d, *Rrefm_d, *cref64p_d, *cref64m_d, *Phiref64_d, *meanrhs_d, *meanshift_d, *delta_d;
   double *Hrefp_d, *Hrefm_d;
+  // spectral elimination factors (grid-only): c'_j and 1/pivot_j per spectral point
+  double *spc_cprN, *spc_invN, *spc_cprD, *spc_invD;
   std::vector<double> href_p, href_m, lyc_p, lyc_m;
   bool refs_valid = false;   // references and shadows match the FP64 fields
   bool fp64_fresh = true;    // FP64 Phi, Hc+- arrays are current (else the shadows are)
@@ -136,7 +138,10 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
   double *cr64p = b.take<double>(ny), *cr64m = b.take<double>(ny), *Pr64 = b.take<double>(ny);
   double *mrhs = b.take<double>(ny), *mshift = b.take<double>(ny), *delta = b.take<double>(ny);
   double *Hrp = b.take<double>(ny), *Hrm = b.take<double>(ny);
+  double *fcN = b.take<double>(nspec), *fiN = b.take<double>(nspec), *fcD = b.take<double>(nspec),
+         *fiD = b.take<double>(nspec);
   if (c) {
+    c->spc_cprN = fcN; c->spc_invN = fiN; c->spc_cprD = fcD; c->spc_invD = fiD;
     c->cpS = cpS; c->cmS = cmS; c->phiS = phiS; c->HcpS = HcpS; c->HcmS = HcmS;
     for (int q = 0; q < 8; ++q) c->mf[q] = mf[q];
     c->cnF_d = cnF;
@@ -275,6 +280,12 @@ int upload_metrics(pnp_ctx* c) {
     for (int q = 0; q < 8; ++q) CK(up(c->mf[q], tmp.data() + (size_t)q * ny, sizeof(float) * ny));
     CK(cudaStreamSynchronize(s));
   }
+  {
+    const YRows rn{c->rowsN_d, c->rowsN_d + ny, c->rowsN_d + 2 * ny};
+    const YRows rd{c->rowsD_d, c->rowsD_d + ny, c->rowsD_d + 2 * ny};
+    CK(launch_spec_factors(c->spc_cprN, c->spc_invN, c->kx2_d, c->kz2_d, rn, c->g, true, s));
+    CK(launch_spec_factors(c->spc_cprD, c->spc_invD, c->kx2_d, c->kz2_d, rd, c->g, false, s));
+  }
   CK(cudaStreamSynchronize(s));   // host vectors above are temporaries
   c->refs_valid = false;
   c->cn_dt = NAN;
@@ -358,6 +369,11 @@ MetricsF metrics_f(const pnp_ctx* c) {
   return MetricsF{c->mf[0], c->mf[1], c->mf[2], c->mf[3], c->mf[4], c->mf[5], c->mf[6], c->mf[7]};
 }
 
+CoefF coef_f(const pnp_ctx* c, const Stage& st) {
+  return CoefF{(float)c->g.idx, (float)c->g.idz, (float)c->ph.nu, (float)c->ph.D, (float)c->ph.K, (float)c->ph.Uw,
+               (float)st.dt, (float)st.gam, (float)st.zet, (float)st.alp};
+}
+
 Shadows shadows(const pnp_ctx* c) { return Shadows{c->cpS, c->cmS, c->phiS, c->HcpS, c->HcmS}; }
 
 MixedRefs mixed_refs(const pnp_ctx* c) {
@@ -389,7 +405,8 @@ cudaError_t spectral_solve(pnp_ctx* c, cplx<T>* spec, const cplx<T>* twz, bool n
   if (e != cudaSuccess) return e;
   mark(c);
   const double scale = 1.0 / ((double)c->g.nx * (double)c->g.nz);
-  e = launch_spec_thomas<T>(spec, c->sreal, c->kx2_d, c->kz2_d, yrows(c, neumann), c->g, scale, neumann, c->stream);
+  e = launch_spec_thomas<T>(spec, neumann ? c->spc_cprN : c->spc_cprD, neumann ? c->spc_invN : c->spc_invD,
+                            yrows(c, neumann), c->g, scale, neumann, c->stream);
   if (e != cudaSuccess) return e;
   mark(c);
   e = launch_fft_z<T>(spec, twz, c->g, true, c->stream);
@@ -407,8 +424,9 @@ cudaError_t pressure_projection(pnp_ctx* c, double scale, bool update_p) {
   const cplx<TV>* twp = (const cplx<TV>*)(sizeof(TV) == 8 ? c->twp_d : c->twp_f);
   const cplx<TV>* twz = (const cplx<TV>*)(sizeof(TV) == 8 ? c->twz_d : c->twz_f);
   TV* phip = (TV*)c->sreal;
+  const TV* idyT = (const TV*)(sizeof(TV) == 8 ? (const void*)c->idy_d : (const void*)c->mf[0]);
   cudaError_t e = launch_fft_x_fwd<TV, TV>(PoissonSrc::Divergence, f.u, f.v, f.w, nullptr, nullptr, nullptr,
-                                           1.0 / scale, c->g, m, spec, twx, twp, c->stream);
+                                           1.0 / scale, c->g, m, spec, twx, twp, c->stream, nullptr, nullptr, idyT);
   if (e != cudaSuccess) return e;
   mark(c);
   e = spectral_solve<TV>(c, spec, twz, true);
@@ -416,7 +434,8 @@ cudaError_t pressure_projection(pnp_ctx* c, double scale, bool update_p) {
   e = launch_fft_x_inv<TV, TV>(PoissonDst::Plain, spec, c->g, m, twx, twp, 0.0, phip, c->stream);
   if (e != cudaSuccess) return e;
   mark(c);
-  e = launch_project<TV, TV>(f.u, f.v, f.w, f.p, phip, scale, update_p, c->g, m, c->stream);
+  const TV* ihT = (const TV*)(sizeof(TV) == 8 ? (const void*)c->ih_d : (const void*)c->mf[1]);
+  e = launch_project<TV>(f.u, f.v, f.w, f.p, phip, scale, update_p, c->g, ihT, c->stream);
   mark(c);
   return e;
 }
@@ -464,7 +483,7 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
   const MixedRefs R = mixed_refs(c);
   const Metrics m = metrics(c);
   mark(c);
-  cudaError_t e = launch_mixed_rhs(f, sh, R, c->g, metrics_f(c), c->ph, st, l, c->stream);
+  cudaError_t e = launch_mixed_rhs(f, sh, R, c->g, metrics_f(c), coef_f(c, st), l, c->stream);
   if (e != cudaSuccess) return e;
   mark(c);
   e = launch_mixed_cn(f, sh, R, c->g, cn_rows_f(c, l, 0), cn_rows_f(c, l, 1), cn_rows(c, l, 2), c->stream);
@@ -485,7 +504,7 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
   if (e != cudaSuccess) return e;
   mark(c);
   const double scale = 1.0 / ((double)c->g.nx * (double)c->g.nz);
-  e = launch_spec_thomas<float>(spec, c->sreal, c->kx2_d, c->kz2_d, yrows(c, false), c->g, scale, false, c->stream,
+  e = launch_spec_thomas<float>(spec, c->spc_cprD, c->spc_invD, yrows(c, false), c->g, scale, false, c->stream,
                                 c->meanrhs_d, c->meanshift_d, c->delta_d);
   if (e != cudaSuccess) return e;
   mark(c);
@@ -926,7 +945,7 @@ int pnp_eval_explicit(pnp_ctx* c) {
   } else {
     int r = refresh_refs(c, std::isfinite(c->refs_dt) ? c->refs_dt : 1.0);
     if (r) return r;
-    e = launch_mixed_rhs(fields<float>(c), shadows(c), mixed_refs(c), c->g, metrics_f(c), c->ph, st, 0, c->stream);
+    e = launch_mixed_rhs(fields<float>(c), shadows(c), mixed_refs(c), c->g, metrics_f(c), coef_f(c, st), 0, c->stream);
     c->fp64_fresh = false;
   }
   return e == cudaSuccess ? PNP_OK : PNP_ERR_CUDA;

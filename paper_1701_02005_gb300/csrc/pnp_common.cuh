@@ -103,25 +103,29 @@ cudaError_t launch_fft_x_fwd(PoissonSrc src, const TV* u, const TV* v, const TV*
                              const double* cm, const T* plain, double scale, const Geo& g,
                              const Metrics& m, cplx<T>* spec, const cplx<T>* tw_half,
                              const cplx<T>* tw_post, cudaStream_t s, const float* sa = nullptr,
-                             const float* sb = nullptr);
+                             const float* sb = nullptr, const T* idyT = nullptr);
 
 template <typename T>
 cudaError_t launch_fft_z(cplx<T>* spec, const cplx<T>* tw_z, const Geo& g, bool inverse, cudaStream_t s);
 
+// Elimination factors of the spectral y-solves (grid-only, computed once).
+cudaError_t launch_spec_factors(double* cpr, double* inv, const double* kx2, const double* kz2, const YRows& rows,
+                                const Geo& g, bool neumann, cudaStream_t s);
+
 template <typename T>
-cudaError_t launch_spec_thomas(cplx<T>* spec, double* scratch, const double* kx2, const double* kz2,
-                               const YRows& rows, const Geo& g, double scale, bool neumann,
-                               cudaStream_t s, const double* mean_rhs = nullptr,
-                               const double* mean_shift = nullptr, double* mean_out = nullptr);
+cudaError_t launch_spec_thomas(cplx<T>* spec, const double* cpr, const double* inv, const YRows& rows,
+                               const Geo& g, double scale, bool neumann, cudaStream_t s,
+                               const double* mean_rhs = nullptr, const double* mean_shift = nullptr,
+                               double* mean_out = nullptr);
 
 template <typename T, typename TO>
 cudaError_t launch_fft_x_inv(PoissonDst dst, const cplx<T>* spec, const Geo& g, const Metrics& m,
                              const cplx<T>* tw_half, const cplx<T>* tw_post, double V, TO* out,
                              cudaStream_t s, const double* plane_add = nullptr);
 
-template <typename TV, typename TS>
-cudaError_t launch_project(TV* u, TV* v, TV* w, TV* p, const TS* phip, double scale, bool update_p,
-                           const Geo& g, const Metrics& m, cudaStream_t s);
+template <typename T>
+cudaError_t launch_project(T* u, T* v, T* w, T* p, const T* phip, double scale, bool update_p, const Geo& g,
+                           const T* ih, cudaStream_t s);
 
 // Initial condition, diagnostics, conversions.
 template <typename TV>

@@ -10,6 +10,13 @@ struct MetricsF {
   const float *idy, *ih, *lo_c, *hi_c, *lo_f, *hi_f, *wl, *wu;
 };
 
+// FP32 copies of the scalar coefficients of one substage (converted once on
+// the host: per-thread FP64->FP32 conversions run on the FP64 pipe).
+struct CoefF {
+  float idx, idz, nu, D, K, Uw;
+  float dt, gam, zet, alp;
+};
+
 // FP32 elimination factors of the velocity Crank-Nicolson matrices.
 struct CNRowsF {
   const float *a, *c, *m;
@@ -39,7 +46,7 @@ struct MixedRefs {
 };
 
 cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
-                             const MetricsF& m, const Phys& ph, const Stage& st, int l, cudaStream_t s);
+                             const MetricsF& m, const CoefF& cf, int l, cudaStream_t s);
 cudaError_t launch_mixed_cn(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
                             const CNRowsF& cell, const CNRowsF& face, const CNRows& ion, cudaStream_t s);
 cudaError_t launch_plane_means3(const double* a, const double* b, const double* c, int nplanes, size_t P,

@@ -76,6 +76,7 @@ class Solver:
 
     def set_device(self, name, tensor):
         t = tensor.contiguous().to(dtype=self.torch.float64)
+        self.torch.cuda.synchronize(self.device)
         B.check(B.pnp_set_state(self.ctx, FIELD_NAMES[name], C.c_void_p(t.data_ptr()), 1), "pnp_set_state")
         self.stream.synchronize()
 
