@@ -90,26 +90,54 @@ cudaError_t launch_cn_solves(const Fields<TV>& f, const Geo& g, const CNRows& ve
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory Stockham radix-2 FFT of one sequence of length N (power of
-// two) between buffers x and y; nt threads cooperate, this one is t0.
-// tw[t] = exp(-2 pi i t / N).  Returns the buffer that holds the result.
-// Every thread of the block must call it (it synchronises the block).
+// Shared-memory Stockham FFT of one sequence of length N (power of two)
+// between buffers x and y: radix-4 stages, preceded by one radix-2 stage when
+// log2 N is odd.  nt threads cooperate, this one is t0; tw[t] = exp(-2 pi i
+// t / N).  Returns the buffer that holds the result.  Every thread of the
+// block must call it (it synchronises the block).
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ cplx<T> mul_i(cplx<T> z, bool neg) {   // +i z, or -i z when neg
+  return neg ? cplx<T>{z.y, -z.x} : cplx<T>{-z.y, z.x};
+}
+
 template <typename T>
 __device__ cplx<T>* stockham(cplx<T>* x, cplx<T>* y, int N, const cplx<T>* __restrict__ tw, bool inverse,
                              int t0, int nt) {
-  const int half = N >> 1;
-  for (int Ns = 1; Ns < N; Ns <<= 1) {
-    const int tstride = N / (2 * Ns);
+  int Ns = 1;
+  if ((__ffs(N) - 1) & 1) {
+    const int half = N >> 1;
     for (int jj = t0; jj < half; jj += nt) {
+      const cplx<T> a0 = x[jj], a1 = x[jj + half];
+      y[2 * jj] = cadd(a0, a1);
+      y[2 * jj + 1] = csub(a0, a1);
+    }
+    __syncthreads();
+    cplx<T>* t = x;
+    x = y;
+    y = t;
+    Ns = 2;
+  }
+  const int q = N >> 2;
+  for (; Ns < N; Ns <<= 2) {
+    const int tstride = N / (Ns * 4);
+    for (int jj = t0; jj < q; jj += nt) {
       const int k = jj & (Ns - 1);
-      cplx<T> w = tw[k * tstride];
-      if (inverse) w.y = -w.y;
-      const cplx<T> a0 = x[jj];
-      const cplx<T> a1 = cmul(x[jj + half], w);
-      const int d = ((jj - k) << 1) + k;
-      y[d] = cadd(a0, a1);
-      y[d + Ns] = csub(a0, a1);
+      cplx<T> a = x[jj], b = x[jj + q], c = x[jj + 2 * q], d = x[jj + 3 * q];
+      if (k != 0) {
+        cplx<T> w1 = tw[k * tstride], w2 = tw[2 * k * tstride], w3 = tw[3 * k * tstride];
+        if (inverse) { w1.y = -w1.y; w2.y = -w2.y; w3.y = -w3.y; }
+        b = cmul(b, w1);
+        c = cmul(c, w2);
+        d = cmul(d, w3);
+      }
+      const cplx<T> apc = cadd(a, c), amc = csub(a, c), bpd = cadd(b, d), bmd = csub(b, d);
+      const cplx<T> ib = mul_i(bmd, !inverse);   // forward: -i (b - d); inverse: +i (b - d)
+      const int dst = ((jj - k) << 2) + k;
+      y[dst] = cadd(apc, bpd);
+      y[dst + Ns] = cadd(amc, ib);
+      y[dst + 2 * Ns] = csub(apc, bpd);
+      y[dst + 3 * Ns] = csub(amc, ib);
     }
     __syncthreads();
     cplx<T>* t = x;
@@ -190,7 +218,7 @@ __global__ void k_fft_x_fwd(SrcArgs<T, TV> src, Geo g, Metrics m, cplx<T>* __res
 template <typename T>
 static void fft_x_shape(const Geo& g, dim3& blk, dim3& grd, size_t& smem) {
   const int Lh = g.nx >> 1;
-  int tx = Lh / 2 < 1 ? 1 : Lh / 2;
+  int tx = Lh / 4 < 1 ? 1 : Lh / 4;
   if (tx > 128) tx = 128;
   int ry = 128 / tx;
   if (ry < 1) ry = 1;
@@ -315,8 +343,9 @@ __global__ void k_fft_z(cplx<T>* __restrict__ spec, const cplx<T>* __restrict__ 
 
 template <typename T>
 cudaError_t launch_fft_z(cplx<T>* spec, const cplx<T>* tw_z, const Geo& g, bool inverse, cudaStream_t s) {
-  const int TM = 8;
-  int ty = g.nz / 2;
+  int TM = (int)(128 / sizeof(cplx<T>));   // one 128-byte segment of each z-row
+  while (TM > 1 && (size_t)2 * TM * (g.nz + 1) * sizeof(cplx<T>) > 200 * 1024) TM >>= 1;
+  int ty = g.nz / 4;
   if (ty > 32) ty = 32;
   if (ty < 1) ty = 1;
   dim3 blk(TM, ty, 1);
@@ -369,30 +398,83 @@ cudaError_t launch_spec_factors(double* cpr, double* inv, const double* kx2, con
 
 constexpr int kCH = 8;
 
+// The forward sweep runs on the unscaled transform; its FP64 results go to an
+// FP64 scratch (no round trip through the transform's precision), and the
+// normalisation 1/(Nx Nz) is applied once, in the transform's precision, when
+// the solution is stored.  The real and imaginary parts are independent
+// recurrences with the same coefficients, so each runs in its own thread
+// (adjacent threads touch the two halves of one complex value).  The FP64 mean
+// mode (mixed potential) keeps the scaled physical source and never touches
+// spec; it runs in the real-part thread of (0,0).
 template <typename T>
-__global__ void k_spec_thomas(cplx<T>* __restrict__ spec, const double* __restrict__ cpr,
-                              const double* __restrict__ inv, YRows rows, Geo g, double scale, bool neumann,
-                              const double* __restrict__ mean_rhs, const double* __restrict__ mean_shift,
-                              double* __restrict__ mean_out) {
-  const int mm = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_spec_thomas(cplx<T>* __restrict__ spec, cplx<double>* __restrict__ dscr,
+                              const double* __restrict__ cpr, const double* __restrict__ inv, YRows rows, Geo g,
+                              double scale, bool neumann, const double* __restrict__ mean_rhs,
+                              const double* __restrict__ mean_shift, double* __restrict__ mean_out) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int mm = tid >> 1, part = tid & 1;
   const int n = blockIdx.y;
   if (mm >= g.mh) return;
   const size_t P = (size_t)g.nz * g.mp;
   const size_t base = (size_t)n * g.mp + mm;
   const int ny = g.nyc;
+  T* sp = reinterpret_cast<T*>(spec) + part;             // this part of spec[base + j P] at sp[2 (base + j P)]
+  double* dp = reinterpret_cast<double*>(dscr) + part;
   const bool pin = neumann && mm == 0 && n == 0;
-  // FP64 mean mode: the (0,0) source gets the FP64 reference charge and its
-  // elimination runs entirely in FP64 storage (mean_out), never in spec.
   const bool mean_mode = mean_rhs != nullptr && mm == 0 && n == 0;
-  double dre = 0.0, dim = 0.0;
+  if (mean_mode) {
+    if (part == 1) {
+      for (int j = 0; j < ny; ++j) sp[2 * (base + (size_t)j * P)] = T(0);
+      return;
+    }
+    double d = 0.0;
+    for (int j0 = 0; j0 < ny; j0 += kCH) {
+      double rr[kCH], iv[kCH], mr[kCH];
+#pragma unroll
+      for (int u = 0; u < kCH; ++u)
+        if (j0 + u < ny) {
+          const size_t o = base + (size_t)(j0 + u) * P;
+          rr[u] = (double)sp[2 * o];
+          iv[u] = inv[o];
+          mr[u] = mean_rhs[j0 + u];
+        }
+#pragma unroll
+      for (int u = 0; u < kCH; ++u)
+        if (j0 + u < ny) {
+          d = (rr[u] * scale + mr[u] - rows.a[j0 + u] * d) * iv[u];
+          mean_out[j0 + u] = d;
+        }
+    }
+    double x = d;
+    mean_out[ny - 1] = x + mean_shift[ny - 1];
+    sp[2 * (base + (size_t)(ny - 1) * P)] = T(0);
+    for (int j1 = ny - 2; j1 >= 0; j1 -= kCH) {
+      double dd[kCH], cc[kCH], ms[kCH];
+#pragma unroll
+      for (int u = 0; u < kCH; ++u)
+        if (j1 - u >= 0) {
+          dd[u] = mean_out[j1 - u];
+          cc[u] = cpr[base + (size_t)(j1 - u) * P];
+          ms[u] = mean_shift[j1 - u];
+        }
+#pragma unroll
+      for (int u = 0; u < kCH; ++u)
+        if (j1 - u >= 0) {
+          x = dd[u] - cc[u] * x;
+          mean_out[j1 - u] = x + ms[u];
+          sp[2 * (base + (size_t)(j1 - u) * P)] = T(0);
+        }
+    }
+    return;
+  }
+  double d = 0.0;
   for (int j0 = 0; j0 < ny; j0 += kCH) {
-    cplx<T> rr[kCH];
-    double iv[kCH];
+    double rr[kCH], iv[kCH];
 #pragma unroll
     for (int u = 0; u < kCH; ++u) {
       if (j0 + u < ny) {
         const size_t o = base + (size_t)(j0 + u) * P;
-        rr[u] = spec[o];
+        rr[u] = (double)sp[2 * o];
         iv[u] = inv[o];
       }
     }
@@ -400,37 +482,22 @@ __global__ void k_spec_thomas(cplx<T>* __restrict__ spec, const double* __restri
     for (int u = 0; u < kCH; ++u) {
       const int j = j0 + u;
       if (j < ny) {
-        const double a = rows.a[j];
-        double rre = (double)rr[u].x * scale, rim = (double)rr[u].y * scale;
-        if (mean_mode) { rre += mean_rhs[j]; rim = 0.0; }
-        if (pin && j == 0) { rre = 0.0; rim = 0.0; }
-        dre = (rre - a * dre) * iv[u];
-        dim = (rim - a * dim) * iv[u];
-        if (mean_mode) mean_out[j] = dre;
-        else spec[base + (size_t)j * P] = {(T)dre, (T)dim};
+        const double r = (pin && j == 0) ? 0.0 : rr[u];
+        d = (r - rows.a[j] * d) * iv[u];
+        dp[2 * (base + (size_t)j * P)] = d;
       }
     }
   }
-  double xre = dre, xim = dim;
-  if (mean_mode) {
-    mean_out[ny - 1] = xre + mean_shift[ny - 1];
-    spec[base + (size_t)(ny - 1) * P] = {T(0), T(0)};
-    for (int j = ny - 2; j >= 0; --j) {
-      const size_t o = base + (size_t)j * P;
-      xre = mean_out[j] - cpr[o] * xre;
-      mean_out[j] = xre + mean_shift[j];
-      spec[o] = {T(0), T(0)};
-    }
-    return;
-  }
+  const T sc = (T)scale;
+  double x = d;
+  sp[2 * (base + (size_t)(ny - 1) * P)] = (T)x * sc;
   for (int j1 = ny - 2; j1 >= 0; j1 -= kCH) {
-    cplx<T> dd[kCH];
-    double cc[kCH];
+    double dd[kCH], cc[kCH];
 #pragma unroll
     for (int u = 0; u < kCH; ++u) {
       if (j1 - u >= 0) {
         const size_t o = base + (size_t)(j1 - u) * P;
-        dd[u] = spec[o];
+        dd[u] = dp[2 * o];
         cc[u] = cpr[o];
       }
     }
@@ -438,21 +505,20 @@ __global__ void k_spec_thomas(cplx<T>* __restrict__ spec, const double* __restri
     for (int u = 0; u < kCH; ++u) {
       const int j = j1 - u;
       if (j >= 0) {
-        xre = (double)dd[u].x - cc[u] * xre;
-        xim = (double)dd[u].y - cc[u] * xim;
-        spec[base + (size_t)j * P] = {(T)xre, (T)xim};
+        x = dd[u] - cc[u] * x;
+        sp[2 * (base + (size_t)j * P)] = (T)x * sc;
       }
     }
   }
 }
 
 template <typename T>
-cudaError_t launch_spec_thomas(cplx<T>* spec, const double* cpr, const double* inv, const YRows& rows, const Geo& g,
-                               double scale, bool neumann, cudaStream_t s, const double* mean_rhs,
-                               const double* mean_shift, double* mean_out) {
+cudaError_t launch_spec_thomas(cplx<T>* spec, cplx<double>* dscr, const double* cpr, const double* inv,
+                               const YRows& rows, const Geo& g, double scale, bool neumann, cudaStream_t s,
+                               const double* mean_rhs, const double* mean_shift, double* mean_out) {
   const int T_ = 64;
-  dim3 grd((g.mh + T_ - 1) / T_, g.nz, 1);
-  k_spec_thomas<T><<<grd, T_, 0, s>>>(spec, cpr, inv, rows, g, scale, neumann, mean_rhs, mean_shift, mean_out);
+  dim3 grd((2 * g.mh + T_ - 1) / T_, g.nz, 1);
+  k_spec_thomas<T><<<grd, T_, 0, s>>>(spec, dscr, cpr, inv, rows, g, scale, neumann, mean_rhs, mean_shift, mean_out);
   return cudaGetLastError();
 }
 
@@ -511,12 +577,12 @@ template cudaError_t launch_fft_x_fwd<double, float>(PoissonSrc, const float*, c
 template cudaError_t launch_fft_z<double>(cplx<double>*, const cplx<double>*, const Geo&, bool, cudaStream_t);
 template cudaError_t launch_fft_z<float>(cplx<float>*, const cplx<float>*, const Geo&, bool, cudaStream_t);
 
-template cudaError_t launch_spec_thomas<double>(cplx<double>*, const double*, const double*, const YRows&,
-                                                const Geo&, double, bool, cudaStream_t, const double*,
-                                                const double*, double*);
-template cudaError_t launch_spec_thomas<float>(cplx<float>*, const double*, const double*, const YRows&,
-                                               const Geo&, double, bool, cudaStream_t, const double*,
-                                               const double*, double*);
+template cudaError_t launch_spec_thomas<double>(cplx<double>*, cplx<double>*, const double*, const double*,
+                                                const YRows&, const Geo&, double, bool, cudaStream_t,
+                                                const double*, const double*, double*);
+template cudaError_t launch_spec_thomas<float>(cplx<float>*, cplx<double>*, const double*, const double*,
+                                               const YRows&, const Geo&, double, bool, cudaStream_t,
+                                               const double*, const double*, double*);
 
 template cudaError_t launch_fft_x_inv<double, double>(PoissonDst, const cplx<double>*, const Geo&, const Metrics&,
                                                       const cplx<double>*, const cplx<double>*, double, double*,

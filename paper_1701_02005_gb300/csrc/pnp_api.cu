@@ -82,6 +82,7 @@ struct pnp_ctx {
   double *Hrefp_d, *Hrefm_d;
   // spectral elimination factors (grid-only): c'_j and 1/pivot_j per spectral point
   double *spc_cprN, *spc_invN, *spc_cprD, *spc_invD;
+  cplx<double>* dscr;   // FP64 forward-sweep values of the spectral solves
   std::vector<double> href_p, href_m, lyc_p, lyc_m;
   bool refs_valid = false;   // references and shadows match the FP64 fields
   bool fp64_fresh = true;    // FP64 Phi, Hc+- arrays are current (else the shadows are)
@@ -140,7 +141,9 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
   double *Hrp = b.take<double>(ny), *Hrm = b.take<double>(ny);
   double *fcN = b.take<double>(nspec), *fiN = b.take<double>(nspec), *fcD = b.take<double>(nspec),
          *fiD = b.take<double>(nspec);
+  cplx<double>* dscr = b.take<cplx<double>>(nspec);
   if (c) {
+    c->dscr = dscr;
     c->spc_cprN = fcN; c->spc_invN = fiN; c->spc_cprD = fcD; c->spc_invD = fiD;
     c->cpS = cpS; c->cmS = cmS; c->phiS = phiS; c->HcpS = HcpS; c->HcmS = HcmS;
     for (int q = 0; q < 8; ++q) c->mf[q] = mf[q];
@@ -405,7 +408,7 @@ cudaError_t spectral_solve(pnp_ctx* c, cplx<T>* spec, const cplx<T>* twz, bool n
   if (e != cudaSuccess) return e;
   mark(c);
   const double scale = 1.0 / ((double)c->g.nx * (double)c->g.nz);
-  e = launch_spec_thomas<T>(spec, neumann ? c->spc_cprN : c->spc_cprD, neumann ? c->spc_invN : c->spc_invD,
+  e = launch_spec_thomas<T>(spec, c->dscr, neumann ? c->spc_cprN : c->spc_cprD, neumann ? c->spc_invN : c->spc_invD,
                             yrows(c, neumann), c->g, scale, neumann, c->stream);
   if (e != cudaSuccess) return e;
   mark(c);
@@ -504,7 +507,7 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
   if (e != cudaSuccess) return e;
   mark(c);
   const double scale = 1.0 / ((double)c->g.nx * (double)c->g.nz);
-  e = launch_spec_thomas<float>(spec, c->spc_cprD, c->spc_invD, yrows(c, false), c->g, scale, false, c->stream,
+  e = launch_spec_thomas<float>(spec, c->dscr, c->spc_cprD, c->spc_invD, yrows(c, false), c->g, scale, false, c->stream,
                                 c->meanrhs_d, c->meanshift_d, c->delta_d);
   if (e != cudaSuccess) return e;
   mark(c);

@@ -113,8 +113,8 @@ cudaError_t launch_spec_factors(double* cpr, double* inv, const double* kx2, con
                                 const Geo& g, bool neumann, cudaStream_t s);
 
 template <typename T>
-cudaError_t launch_spec_thomas(cplx<T>* spec, const double* cpr, const double* inv, const YRows& rows,
-                               const Geo& g, double scale, bool neumann, cudaStream_t s,
+cudaError_t launch_spec_thomas(cplx<T>* spec, cplx<double>* dscr, const double* cpr, const double* inv,
+                               const YRows& rows, const Geo& g, double scale, bool neumann, cudaStream_t s,
                                const double* mean_rhs = nullptr, const double* mean_shift = nullptr,
                                double* mean_out = nullptr);
 
