@@ -43,7 +43,8 @@ enum {
   PNP_ERR_STATE = -5,        /* parameters or state not set yet                   */
   PNP_ERR_NONFINITE = -6,    /* device check: NaN/Inf in a prognostic field       */
   PNP_ERR_NEGATIVE_C = -7,   /* device check: a concentration went negative       */
-  PNP_ERR_UNSUPPORTED = -8   /* option not available for this precision          */
+  PNP_ERR_UNSUPPORTED = -8,  /* option not available for this precision          */
+  PNP_ERR_TOO_LARGE = -9     /* grid exceeds the static scratch of pnp_poisson_noalloc */
 };
 
 /* Arithmetic precision of a context. */
@@ -147,6 +148,26 @@ int pnp_mean_profile(pnp_ctx* ctx, int field, double* out_host);
  * the wall faces.  rhs and x are device FP64 arrays of (Ny-1)*Nz*Nx values and
  * may alias.  Uses the context's scratch; asynchronous. */
 int pnp_poisson(pnp_ctx* ctx, int bc, const double* rhs_dev, double* x_dev);
+
+/* No counterpart in the paper: a convenience for callers that cannot allocate
+ * device memory (a plug-in inside a framework that owns every allocation, or a
+ * latency-critical path where cudaMalloc may synchronise or fail).  Performs the
+ * same separable Poisson solve as pnp_poisson, but needs no context and
+ * allocates nothing: its scratch is one static device array of about 48 MB
+ * (held by every GPU that loads the library until the process exits), which
+ * serves grids with (Ny-1) * Nz * pitch <= 2^20 spectral points (pitch = Nx/2+1
+ * rounded up to a multiple of 8), Nx, Nz <= 4096 and Ny <= 4097; larger grids
+ * return PNP_ERR_TOO_LARGE.  y_faces_host: Ny host values (the first and last
+ * are taken as -1 and +1); rhs_dev, x_dev: device FP64 arrays of
+ * (Ny-1)*Nz*Nx values in the [y][z][x] layout (they may alias); cuda_stream:
+ * the stream to run on (NULL = legacy default stream).  The first call on a
+ * device looks up the device address of the scratch (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the one
+ * scratch, which keeps the last call's contents: calls that overlap on the GPU
+ * (different streams, or different host threads) race and corrupt each
+ * other's results; serialise them.  Asynchronous; returns PNP_OK or an error. */
+int pnp_poisson_noalloc(int nx, int ny, int nz, double Lx, double Lz, const double* y_faces_host, int bc,
+                        const double* rhs_dev, double* x_dev, void* cuda_stream);
 
 /* Overwrite the stored explicit terms H (fields PNP_HU..PNP_HCM) with those of
  * the current state (advection, x/z diffusion, Coulomb force, migration). */

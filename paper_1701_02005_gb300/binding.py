@@ -20,6 +20,7 @@ PNP_ERR_STATE = -5
 PNP_ERR_NONFINITE = -6
 PNP_ERR_NEGATIVE_C = -7
 PNP_ERR_UNSUPPORTED = -8
+PNP_ERR_TOO_LARGE = -9
 
 PNP_FP64 = 0
 PNP_MIXED = 1
@@ -66,6 +67,8 @@ EXPORTS = {
     "pnp_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(pnp_diag)]),
     "pnp_mean_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "pnp_poisson": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "pnp_poisson_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_double),
+                                      C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pnp_eval_explicit": (C.c_int, [C.c_void_p]),
     "pnp_status": (C.c_int, [C.c_void_p]),
     "pnp_fp64_peak": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -128,6 +131,7 @@ pnp_step = _fwd("pnp_step")
 pnp_diagnostics = _fwd("pnp_diagnostics")
 pnp_mean_profile = _fwd("pnp_mean_profile")
 pnp_poisson = _fwd("pnp_poisson")
+pnp_poisson_noalloc = _fwd("pnp_poisson_noalloc")
 pnp_eval_explicit = _fwd("pnp_eval_explicit")
 pnp_status = _fwd("pnp_status")
 pnp_fp64_peak = _fwd("pnp_fp64_peak")

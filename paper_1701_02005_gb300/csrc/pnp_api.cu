@@ -1034,6 +1034,7 @@ const char* pnp_error_string(int code) {
     case PNP_ERR_NONFINITE: return "non-finite value in a prognostic field";
     case PNP_ERR_NEGATIVE_C: return "negative ion concentration";
     case PNP_ERR_UNSUPPORTED: return "unsupported option";
+    case PNP_ERR_TOO_LARGE: return "grid exceeds the static scratch of pnp_poisson_noalloc (2^20 spectral points)";
     default: return "unknown error";
   }
 }
