@@ -68,6 +68,92 @@ def site_cost(site, precision):
 
 
 # --------------------------------------------------------------------------
+# Ensemble workload: 48 cases on two grids, Re x Debye length x wall potential.
+# Per case: the smallest tanh stretching that keeps the Gouy-Chapman potential
+# drop across the wall cell <= 1 (flagged when even g = 6 cannot), and dt from
+# the explicit limits: advection CFL 0.5, wall-normal migration CFL 0.5 and the
+# dielectric relaxation rate D (c+ + c-)_wall / (2 lam^2) (RK3 real-axis bound).
+# --------------------------------------------------------------------------
+def ensemble_cases():
+    import math as m
+    out = []
+    grids = [(64, 65, 64), (128, 97, 128)]
+    idx = 0
+    for (nx, ny, nz) in grids:
+        for Re in (1000.0, 3000.0):
+            for lam in (0.005, 0.0158, 0.05):
+                for V in (0.0, 2.0, 5.0, 10.0):
+                    bq = 2 * lam * (m.cosh(V / 2) - 1)
+                    sq = 0.5 * (-bq + m.sqrt(bq * bq + 4))
+                    cb = sq * sq
+                    dphi_w = 2 * m.sqrt(cb) * m.sinh(V / 2) / lam
+                    chosen, dy0 = None, None
+                    for g in (1.5, 2.0, 2.5, 3.0, 3.5, 4.0, 4.5, 5.0, 5.5, 6.0):
+                        d0 = 1 - m.tanh(g * (1 - 2.0 / (ny - 1))) / m.tanh(g)
+                        if dphi_w * d0 <= 1.0:
+                            chosen, dy0 = g, d0
+                            break
+                    flagged = chosen is None
+                    if flagged:
+                        chosen = 6.0
+                        dy0 = 1 - m.tanh(chosen * (1 - 2.0 / (ny - 1))) / m.tanh(chosen)
+                    D = 1.0 / Re
+                    dx = 2 * m.pi / nx
+                    dt = 0.5 * dx
+                    if V > 0:
+                        dt = min(dt, 0.5 * dy0 / (D * dphi_w))
+                    cwall = cb * (m.exp(V) + m.exp(-V))
+                    dt = min(dt, 2.0 / (D * cwall / (2 * lam * lam)))
+                    out.append(dict(nx=nx, ny=ny, nz=nz, Re=Re, lam=lam, V=V, stretch=chosen, dt=dt,
+                                    dphi_wall_cell=dphi_w * dy0, flagged=flagged, seed=1703 + idx))
+                    idx += 1
+    return out
+
+
+def run_ensemble(args, B, Solver, torch):
+    from paper_1701_02005_gb300 import autotune
+    from paper_1701_02005_gb300.ensemble import Ensemble
+
+    cases = ensemble_cases()
+    prec = B.PNP_MIXED if args.precision == "mixed" else B.PNP_FP64
+    solvers, tuned = [], {}
+    for c in cases:
+        s = Solver(c["nx"], c["ny"], c["nz"], 2 * math.pi, math.pi, stretch=c["stretch"], precision=prec)
+        s.set_params(c["Re"], c["lam"], 1.0, c["V"], 0.5)
+        cfg, _ = autotune.tune(s, c["dt"])
+        tuned[f'{c["nx"]}x{c["ny"]}x{c["nz"]}'] = cfg
+        s.init_state(B.PNP_IC_PB, c["seed"], 0.1)
+        solvers.append(s)
+    ens = Ensemble(solvers)
+    dts = [c["dt"] for c in cases]
+    Ke, We = args.ensemble_steps, 3
+    ens.step(We, dts)
+    ens.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(ens.stream)
+    ens.step(Ke, dts)
+    e1.record(ens.stream)
+    ens.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    ncells = sum(c["nx"] * (c["ny"] - 1) * c["nz"] for c in cases)
+    bad = []
+    for c, s in zip(cases, solvers):
+        d = s.diagnostics()
+        if d["status"] != 0:
+            bad.append(c["seed"])
+    ens.close()
+    for s in solvers:
+        s.close()
+    return {"cases": len(cases), "cells": ncells, "steps": Ke, "value": ncells * Ke / t, "unit": UNIT,
+            "ms_per_step": 1e3 * t / Ke, "graph_launches_per_step": 1, "precision": args.precision,
+            "autotuned": tuned, "flagged_under_resolved": [c["seed"] for c in cases if c["flagged"]],
+            "nonfinite_or_negative": bad,
+            "recipe": "2 grids (64x65x64, 128x97x128) x Re {1000,3000} x lambda {0.005,0.0158,0.05} x "
+                      "V {0,2,5,10}; Gouy-Chapman ions + 0.1 noise; per-case stretching and dt"}
+
+
+# --------------------------------------------------------------------------
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
 
@@ -333,6 +419,10 @@ def run_ours(args):
                "note": "set_state of all 12 fields from pinned host, then per step pnp_step + pnp_diagnostics "
                        "(D2H, synchronising), then get_state(u) to pinned host"}
 
+    ensemble = None
+    if not args.no_ensemble:
+        ensemble = run_ensemble(args, B, Solver, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -346,6 +436,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (working set ~2 GB vs 129 MB), no flush"},
         "roofline": roof,
         "mixed_vs_fp64": cmp,
+        "ensemble": ensemble,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": lps * K,
@@ -374,6 +465,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--ensemble-steps", type=int, default=20)
     ap.add_argument("--grid", default=None,
                     help="NX,NY,NZ override of the workload grid (small cases for profiler captures only)")
     args = ap.parse_args()

@@ -180,6 +180,36 @@ int pnp_status(pnp_ctx* ctx);
  * on the context's stream): the ALU ceiling of the FP64 kernels. */
 int pnp_fp64_peak(pnp_ctx* ctx, double* flops_out);
 
+/* Autotuner (no counterpart in the paper; launch-shape selection for GB300):
+ * times candidate launch shapes of the stencil kernels (block x-extent 16/32/
+ * 64/128 of 128 threads), the wall-normal CN sweeps (64/128/256 threads), the
+ * spectral y-solves (32/64/128) and the z-transform (8..64 threads per column)
+ * on this context's grid with CUDA events and keeps the fastest.  cfg_out[4]
+ * receives the choice (same order as pnp_set_launch_config), ms_out[4]
+ * (optional) the best time of each.  It runs on the workspace and overwrites
+ * the state: call it after pnp_set_params and before pnp_init_state /
+ * pnp_set_state.  Synchronises the stream. */
+int pnp_autotune(pnp_ctx* ctx, double dt, int* cfg_out, double* ms_out);
+/* Set / read the launch shapes {stencil block x, CN block, spectral block,
+ * z-transform threads per column} (e.g. from a cache of autotuner results). */
+int pnp_set_launch_config(pnp_ctx* ctx, const int* cfg);
+int pnp_get_launch_config(pnp_ctx* ctx, int* cfg);
+
+/* Ensemble of independent cases (no counterpart in the paper: the data-parallel
+ * axis of a parameter sweep, e.g. over wall potential and Debye length on
+ * uneven grids).  Each case is a distinct context with its own workspace,
+ * parameters and state.  pnp_ensemble_step advances every case by nsteps
+ * steps of its own dt[i] with ONE CUDA graph launch per step on `stream` (a
+ * non-default stream): the graph forks each case onto a private branch stream
+ * of the ensemble so that the cases' kernels overlap.  Work issued afterwards
+ * on a case's own stream is ordered after the ensemble's steps.  Each case's
+ * arithmetic is exactly that of pnp_step on the case alone (bitwise equal).
+ * The ensemble borrows the contexts; destroy it before them. */
+typedef struct pnp_ensemble pnp_ensemble;
+int pnp_ensemble_create(pnp_ensemble** out, pnp_ctx* const* cases, int ncases, void* cuda_stream);
+int pnp_ensemble_step(pnp_ensemble* ens, int nsteps, const double* dt);
+void pnp_ensemble_destroy(pnp_ensemble* ens);
+
 /* Launch sites timed by pnp_profile, in launch order within a substage. */
 enum {
   PNP_SITE_RHS = 0,         /* explicit terms + CN right-hand sides            */

@@ -74,6 +74,12 @@ EXPORTS = {
     "pnp_fp64_peak": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "pnp_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_int,
                               C.POINTER(C.c_int)]),
+    "pnp_autotune": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "pnp_set_launch_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "pnp_get_launch_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "pnp_ensemble_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_void_p]),
+    "pnp_ensemble_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    "pnp_ensemble_destroy": (None, [C.c_void_p]),
     "pnp_error_string": (C.c_char_p, [C.c_int]),
     "pnp_destroy": (None, [C.c_void_p]),
 }
@@ -136,5 +142,11 @@ pnp_eval_explicit = _fwd("pnp_eval_explicit")
 pnp_status = _fwd("pnp_status")
 pnp_fp64_peak = _fwd("pnp_fp64_peak")
 pnp_profile = _fwd("pnp_profile")
+pnp_autotune = _fwd("pnp_autotune")
+pnp_set_launch_config = _fwd("pnp_set_launch_config")
+pnp_get_launch_config = _fwd("pnp_get_launch_config")
+pnp_ensemble_create = _fwd("pnp_ensemble_create")
+pnp_ensemble_step = _fwd("pnp_ensemble_step")
+pnp_ensemble_destroy = _fwd("pnp_ensemble_destroy")
 pnp_error_string = _fwd("pnp_error_string")
 pnp_destroy = _fwd("pnp_destroy")

@@ -362,8 +362,9 @@ __global__ void k_from_shadow(const float* __restrict__ s, const double* __restr
 // ---------------------------------------------------------------------------
 cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
                              const MetricsF& m, const CoefF& cf, int l, cudaStream_t s) {
-  dim3 blk(32, 4, 1);
-  dim3 grd((g.nx + 31) / 32, (g.nz + 3) / 4, g.nyc);
+  const int bx = g.lc_rhs_bx ? g.lc_rhs_bx : 32, by = 128 / bx;
+  dim3 blk(bx, by, 1);
+  dim3 grd((g.nx + bx - 1) / bx, (g.nz + by - 1) / by, g.nyc);
   k_mom_mixed<<<grd, blk, 0, s>>>(f, sh, R, g, m, cf);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -374,7 +375,7 @@ cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const Mi
 cudaError_t launch_mixed_cn(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
                             const CNRowsF& cell, const CNRowsF& face, const CNRows& ion, cudaStream_t s) {
   const size_t P = (size_t)g.nz * g.nx;
-  const int T = 128;
+  const int T = g.lc_cn ? g.lc_cn : 128;
   dim3 grd((unsigned)((P + T - 1) / T), 3, 1);
   k_cn_vel_f32<<<grd, T, 0, s>>>(f.u, f.ru, f.v, f.rv, f.w, f.rw, cell, face, g.nyc, P);
   cudaError_t e = cudaGetLastError();

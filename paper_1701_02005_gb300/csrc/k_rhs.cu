@@ -166,8 +166,9 @@ __global__ void __launch_bounds__(128) k_rhs(Fields<TV> f, Geo g, Metrics mt, Ph
 template <typename TV>
 cudaError_t launch_rhs(const Fields<TV>& f, const Geo& g, const Metrics& m, const Phys& ph,
                        const Stage& st, cudaStream_t s) {
-  dim3 blk(32, 4, 1);
-  dim3 grd((g.nx + 31) / 32, (g.nz + 3) / 4, g.nyc);
+  const int bx = g.lc_rhs_bx ? g.lc_rhs_bx : 32, by = 128 / bx;
+  dim3 blk(bx, by, 1);
+  dim3 grd((g.nx + bx - 1) / bx, (g.nz + by - 1) / by, g.nyc);
   k_rhs<TV><<<grd, blk, 0, s>>>(f, g, m, ph, st);
   return cudaGetLastError();
 }

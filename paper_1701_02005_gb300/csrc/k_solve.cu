@@ -76,7 +76,7 @@ template <typename TV>
 cudaError_t launch_cn_solves(const Fields<TV>& f, const Geo& g, const CNRows& vel, const CNRows& face,
                              const CNRows& ion, cudaStream_t s) {
   const size_t P = (size_t)g.nz * g.nx;
-  const int T = 128;
+  const int T = g.lc_cn ? g.lc_cn : 128;
   dim3 grd((unsigned)((P + T - 1) / T), 3, 1);
   // u, w: nyc cells from plane 0; v: the nyc-1 interior faces from plane 1
   k_cn_thomas<TV, TV><<<grd, T, 0, s>>>(f.u, f.ru, f.v, f.rv, f.w, f.rw, vel, face, vel, g.nyc,
@@ -346,7 +346,8 @@ cudaError_t launch_fft_z(cplx<T>* spec, const cplx<T>* tw_z, const Geo& g, bool 
   int TM = (int)(128 / sizeof(cplx<T>));   // one 128-byte segment of each z-row
   while (TM > 1 && (size_t)2 * TM * (g.nz + 1) * sizeof(cplx<T>) > 200 * 1024) TM >>= 1;
   int ty = g.nz / 4;
-  if (ty > 32) ty = 32;
+  const int cap = g.lc_fftz_ty ? g.lc_fftz_ty : 32;
+  if (ty > cap) ty = cap;
   if (ty < 1) ty = 1;
   dim3 blk(TM, ty, 1);
   dim3 grd((g.mh + TM - 1) / TM, g.nyc, 1);
@@ -516,7 +517,7 @@ template <typename T>
 cudaError_t launch_spec_thomas(cplx<T>* spec, cplx<double>* dscr, const double* cpr, const double* inv,
                                const YRows& rows, const Geo& g, double scale, bool neumann, cudaStream_t s,
                                const double* mean_rhs, const double* mean_shift, double* mean_out) {
-  const int T_ = 64;
+  const int T_ = g.lc_spec ? g.lc_spec : 64;
   dim3 grd((2 * g.mh + T_ - 1) / T_, g.nz, 1);
   k_spec_thomas<T><<<grd, T_, 0, s>>>(spec, dscr, cpr, inv, rows, g, scale, neumann, mean_rhs, mean_shift, mean_out);
   return cudaGetLastError();

@@ -1023,6 +1023,265 @@ int pnp_profile(pnp_ctx* c, int nsteps, double dt, double* ms_out, int nsites, i
   return rc;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner: time candidate launch shapes of the stencil, CN-sweep, spectral
+// y-solve and z-transform kernels on this context's grid (CUDA events, best of
+// a few repetitions) and keep the fastest.  Runs on the workspace contents and
+// overwrites them: call it before pnp_init_state / pnp_set_state.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename F>
+float time_launches(pnp_ctx* c, F&& f, int reps) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  f();   // warm-up (and launch-shape validation)
+  float best = 1e30f;
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(a, c->stream);
+    f();
+    cudaEventRecord(b, c->stream);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best) best = ms;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (cudaGetLastError() != cudaSuccess) return 1e30f;
+  return best;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pnp_autotune(pnp_ctx* c, double dt, int* cfg_out, double* ms_out) {
+  if (!c || !cfg_out || !(dt > 0)) return PNP_ERR_ARG;
+  if (!c->have_params) return PNP_ERR_STATE;
+  if (c->cn_dt != dt) {
+    int r = upload_cn(c, dt);
+    if (r) return r;
+  }
+  if (c->precision == PNP_MIXED) {
+    c->fp64_fresh = true;
+    c->refs_valid = false;
+    int r = refresh_refs(c, dt);
+    if (r) return r;
+  }
+  const Stage st{dt, kGam[0], kZet[0], kGam[0] + kZet[0]};
+  const int reps = 3;
+  float best[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+  int pick[4] = {32, 128, 64, 32};
+  // 1: stencil block shape
+  for (int bx : {32, 64, 128, 16}) {
+    if (bx > 2 * c->g.nx && bx != 32) continue;
+    c->g.lc_rhs_bx = bx;
+    float t = time_launches(c, [&] {
+      if (c->precision == PNP_FP64) launch_rhs<double>(fields<double>(c), c->g, metrics(c), c->ph, st, c->stream);
+      else launch_mixed_rhs(fields<float>(c), shadows(c), mixed_refs(c), c->g, metrics_f(c), coef_f(c, st), 0, c->stream);
+    }, reps);
+    if (t < best[0]) { best[0] = t; pick[0] = bx; }
+  }
+  c->g.lc_rhs_bx = pick[0];
+  // 2: CN sweep block size
+  for (int T : {64, 128, 256}) {
+    c->g.lc_cn = T;
+    float t = time_launches(c, [&] {
+      if (c->precision == PNP_FP64)
+        launch_cn_solves<double>(fields<double>(c), c->g, cn_rows(c, 0, 0), cn_rows(c, 0, 1), cn_rows(c, 0, 2), c->stream);
+      else
+        launch_mixed_cn(fields<float>(c), shadows(c), mixed_refs(c), c->g, cn_rows_f(c, 0, 0), cn_rows_f(c, 0, 1),
+                        cn_rows(c, 0, 2), c->stream);
+    }, reps);
+    if (t < best[1]) { best[1] = t; pick[1] = T; }
+  }
+  c->g.lc_cn = pick[1];
+  // 3: spectral y-solve block size, 4: z-transform threads per column
+  const double scale = 1.0 / ((double)c->g.nx * (double)c->g.nz);
+  for (int T : {32, 64, 128}) {
+    c->g.lc_spec = T;
+    float t = time_launches(c, [&] {
+      if (c->precision == PNP_FP64)
+        launch_spec_thomas<double>((cplx<double>*)c->spec, c->dscr, c->spc_cprD, c->spc_invD, yrows(c, false), c->g,
+                                   scale, false, c->stream);
+      else
+        launch_spec_thomas<float>((cplx<float>*)c->spec, c->dscr, c->spc_cprD, c->spc_invD, yrows(c, false), c->g,
+                                  scale, false, c->stream);
+    }, reps);
+    if (t < best[2]) { best[2] = t; pick[2] = T; }
+  }
+  c->g.lc_spec = pick[2];
+  for (int ty : {8, 16, 32, 64}) {
+    if (ty > 8 && ty > c->g.nz / 4) continue;
+    c->g.lc_fftz_ty = ty;
+    float t = time_launches(c, [&] {
+      if (c->precision == PNP_FP64)
+        launch_fft_z<double>((cplx<double>*)c->spec, (const cplx<double>*)c->twz_d, c->g, false, c->stream);
+      else
+        launch_fft_z<float>((cplx<float>*)c->spec, (const cplx<float>*)c->twz_f, c->g, false, c->stream);
+    }, reps);
+    if (t < best[3]) { best[3] = t; pick[3] = ty; }
+  }
+  c->g.lc_fftz_ty = pick[3];
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaGetLastError());
+  for (int i = 0; i < 4; ++i) {
+    cfg_out[i] = pick[i];
+    if (ms_out) ms_out[i] = best[i];
+  }
+  c->have_state = false;   // the timing launches overwrote the workspace
+  drop_graph(c);
+  return PNP_OK;
+}
+
+int pnp_set_launch_config(pnp_ctx* c, const int* cfg) {
+  if (!c || !cfg) return PNP_ERR_ARG;
+  const int bx = cfg[0], cn = cfg[1], sp = cfg[2], ty = cfg[3];
+  if (!(bx == 16 || bx == 32 || bx == 64 || bx == 128)) return PNP_ERR_ARG;
+  if (cn < 32 || cn > 1024 || (cn & (cn - 1))) return PNP_ERR_ARG;
+  if (sp < 32 || sp > 1024 || (sp & (sp - 1))) return PNP_ERR_ARG;
+  if (ty < 1 || ty > 64) return PNP_ERR_ARG;
+  c->g.lc_rhs_bx = bx;
+  c->g.lc_cn = cn;
+  c->g.lc_spec = sp;
+  c->g.lc_fftz_ty = ty;
+  drop_graph(c);
+  return PNP_OK;
+}
+
+int pnp_get_launch_config(pnp_ctx* c, int* cfg) {
+  if (!c || !cfg) return PNP_ERR_ARG;
+  cfg[0] = c->g.lc_rhs_bx ? c->g.lc_rhs_bx : 32;
+  cfg[1] = c->g.lc_cn ? c->g.lc_cn : 128;
+  cfg[2] = c->g.lc_spec ? c->g.lc_spec : 64;
+  cfg[3] = c->g.lc_fftz_ty ? c->g.lc_fftz_ty : 32;
+  return PNP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Ensemble of independent cases (uneven grids and parameters) advanced by ONE
+// CUDA graph launch per step: the capture forks every case onto its own
+// stream branch, so the cases' kernels overlap on the GPU.
+// ---------------------------------------------------------------------------
+struct pnp_ensemble {
+  std::vector<pnp_ctx*> cases;
+  std::vector<cudaStream_t> branch;   // private capture branch per case
+  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<double> dts;
+};
+
+extern "C" {
+
+int pnp_ensemble_create(pnp_ensemble** out, pnp_ctx* const* cases, int ncases, void* stream) {
+  if (!out || !cases || ncases < 1 || !stream) return PNP_ERR_ARG;
+  for (int i = 0; i < ncases; ++i) {
+    if (!cases[i]) return PNP_ERR_ARG;
+    for (int k = 0; k < i; ++k)
+      if (cases[k] == cases[i]) return PNP_ERR_ARG;
+  }
+  pnp_ensemble* e = new (std::nothrow) pnp_ensemble();
+  if (!e) return PNP_ERR_ARG;
+  e->cases.assign(cases, cases + ncases);
+  e->stream = (cudaStream_t)stream;
+  e->join.resize(ncases, nullptr);
+  e->branch.resize(ncases, nullptr);
+  bool ok = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < ncases && ok; ++i) ok = cudaEventCreateWithFlags(&e->join[i], cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < ncases && ok; ++i) ok = cudaStreamCreateWithFlags(&e->branch[i], cudaStreamNonBlocking) == cudaSuccess;
+  if (!ok) {
+    pnp_ensemble_destroy(e);
+    return PNP_ERR_CUDA;
+  }
+  *out = e;
+  return PNP_OK;
+}
+
+int pnp_ensemble_step(pnp_ensemble* e, int nsteps, const double* dt) {
+  if (!e || !dt || nsteps < 0) return PNP_ERR_ARG;
+  const int n = (int)e->cases.size();
+  for (int i = 0; i < n; ++i) {
+    pnp_ctx* c = e->cases[i];
+    if (!(dt[i] > 0) || !std::isfinite(dt[i])) return PNP_ERR_ARG;
+    if (!c->have_params || !c->have_state) return PNP_ERR_STATE;
+  }
+  if (nsteps == 0) return PNP_OK;
+  bool recapture = !e->exec || (int)e->dts.size() != n;
+  for (int i = 0; i < n; ++i) {
+    pnp_ctx* c = e->cases[i];
+    if (c->cn_dt != dt[i]) {
+      int r = upload_cn(c, dt[i]);
+      if (r) return r;
+    }
+    const bool had_refs = c->refs_valid;
+    int r = refresh_refs(c, dt[i]);
+    if (r) return r;
+    if (c->precision == PNP_MIXED) c->fp64_fresh = false;
+    if (!had_refs || (!recapture && e->dts[i] != dt[i])) recapture = true;
+  }
+  // finish every case's pending work (uploads, earlier steps) before the ensemble stream runs
+  for (int i = 0; i < n; ++i) CK(cudaStreamSynchronize(e->cases[i]->stream));
+  if (recapture) {
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    e->exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeRelaxed));
+    cudaError_t err = cudaEventRecord(e->fork, e->stream);
+    for (int i = 0; i < n && err == cudaSuccess; ++i) {
+      pnp_ctx* c = e->cases[i];
+      cudaStream_t own = c->stream;
+      c->stream = e->branch[i];   // the case's launches go to its capture branch
+      err = cudaStreamWaitEvent(c->stream, e->fork, 0);
+      if (err == cudaSuccess) err = one_step(c, dt[i]);
+      if (err == cudaSuccess) err = cudaEventRecord(e->join[i], c->stream);
+      if (err == cudaSuccess) err = cudaStreamWaitEvent(e->stream, e->join[i], 0);
+      c->stream = own;
+    }
+    cudaError_t err2 = cudaStreamEndCapture(e->stream, &graph);
+    if (err != cudaSuccess || err2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return PNP_ERR_CUDA;
+    }
+    err = cudaGraphInstantiate(&e->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (err != cudaSuccess) {
+      e->exec = nullptr;
+      return PNP_ERR_CUDA;
+    }
+    e->dts.assign(dt, dt + n);
+  }
+  for (int s = 0; s < nsteps; ++s) CK(cudaGraphLaunch(e->exec, e->stream));
+  // later work issued on a case's own stream must follow the ensemble's steps
+  CK(cudaEventRecord(e->fork, e->stream));
+  for (int i = 0; i < n; ++i) {
+    if (e->cases[i]->stream) CK(cudaStreamWaitEvent(e->cases[i]->stream, e->fork, 0));
+    else CK(cudaStreamSynchronize(e->stream));
+    e->cases[i]->time += nsteps * dt[i];
+    e->cases[i]->nstep += nsteps;
+  }
+  return PNP_OK;
+}
+
+void pnp_ensemble_destroy(pnp_ensemble* e) {
+  if (!e) return;
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  if (e->fork) cudaEventDestroy(e->fork);
+  for (cudaEvent_t ev : e->join)
+    if (ev) cudaEventDestroy(ev);
+  for (cudaStream_t st : e->branch)
+    if (st) cudaStreamDestroy(st);
+  delete e;
+}
+
 const char* pnp_error_string(int code) {
   switch (code) {
     case PNP_OK: return "ok";

@@ -28,6 +28,11 @@ struct Geo {
   int nx, nz, nyc, ny;   // ny = nyc + 1 face nodes
   int mh, mp;            // nx/2 + 1 spectral columns, padded pitch
   double dx, dz, idx, idz;
+  // launch shapes chosen by the autotuner (0 = built-in default)
+  int lc_rhs_bx;         // x-extent of the 128-thread stencil blocks (16, 32, 64, 128)
+  int lc_cn;             // threads per block of the wall-normal CN sweeps
+  int lc_spec;           // threads per block of the spectral y-solves
+  int lc_fftz_ty;        // threads per column of the z-transform (cap)
 };
 
 // Per-y metric arrays on the device (see pnp_api.cu for definitions).

@@ -1,0 +1,72 @@
+"""Ensemble of uneven cases in one graph launch per step: every case must be
+bitwise equal to the same case advanced alone (the ensemble only changes the
+scheduling, never the arithmetic); tuned launch shapes must not change results."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import pnp_oracle as o
+
+pytestmark = pytest.mark.gpu
+
+CASES = [  # (nx, ny, nz, Re, lam, V, stretch, dt, precision)
+    (16, 13, 8, 200.0, 0.1, 2.0, 2.0, 0.01, 0),
+    (32, 17, 16, 500.0, 0.05, 1.0, 2.2, 0.005, 0),
+    (8, 9, 4, 100.0, 0.2, 0.0, 1.5, 0.02, 1),
+    (16, 21, 16, 300.0, 0.05, 3.0, 2.5, 0.002, 1),
+]
+
+
+def _case(nx, ny, nz, Re, lam, V, stretch, dt, prec, seed):
+    from paper_1701_02005_gb300.solver import Solver
+
+    s = Solver(nx, ny, nz, 2 * math.pi, math.pi, stretch=stretch, precision=prec)
+    s.set_params(Re, lam, 1.0, V, 0.5)
+    s.init_state(1, seed, 0.05)
+    return s
+
+
+def test_ensemble_bitwise_equals_cases_alone():
+    from paper_1701_02005_gb300.ensemble import Ensemble
+
+    ens_solvers = [_case(*c, seed=10 + i) for i, c in enumerate(CASES)]
+    alone = [_case(*c, seed=10 + i) for i, c in enumerate(CASES)]
+    dts = [c[7] for c in CASES]
+    ens = Ensemble(ens_solvers)
+    ens.step(3, dts)
+    ens.step(2, dts)
+    ens.synchronize()
+    for s, dt in zip(alone, dts):
+        s.step(5, dt)
+        s.synchronize()
+    for i, (a, b) in enumerate(zip(ens_solvers, alone)):
+        for name in ("u", "v", "w", "p", "cp", "cm", "Phi"):
+            assert np.array_equal(a.get(name), b.get(name)), (i, name)
+        assert a.diagnostics()["nstep"] == 5
+    ens.close()
+    for s in ens_solvers + alone:
+        s.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_autotuned_shapes_do_not_change_results(prec, tmp_path):
+    from paper_1701_02005_gb300 import autotune
+    from paper_1701_02005_gb300.solver import Solver
+
+    g = o.Grid(64, 33, 32, 2 * math.pi, math.pi, stretch=2.0)
+    runs = []
+    for tuned in (False, True):
+        s = Solver(g.nx, g.ny, g.nz, g.Lx, g.Lz, stretch=2.0, precision=prec)
+        s.set_params(400.0, 0.05, 1.0, 2.0, 0.5)
+        if tuned:
+            cfg, ms = autotune.tune(s, 0.01, cache_path=str(tmp_path / "cache.json"))
+            assert cfg[0] in (16, 32, 64, 128) and cfg[1] in (64, 128, 256) and cfg[2] in (32, 64, 128)
+            cfg2, ms2 = autotune.tune(s, 0.01, cache_path=str(tmp_path / "cache.json"))
+            assert cfg2 == cfg and ms2 is None   # second call served from the cache
+        s.init_state(1, 7, 1e-2)
+        s.step(4, 0.01)
+        runs.append({n: s.get(n) for n in ("u", "v", "w", "cp", "Phi")})
+        s.close()
+    for n in runs[0]:
+        assert np.array_equal(runs[0][n], runs[1][n]), n
