@@ -210,6 +210,67 @@ int pnp_ensemble_create(pnp_ensemble** out, pnp_ctx* const* cases, int ncases, v
 int pnp_ensemble_step(pnp_ensemble* ens, int nsteps, const double* dt);
 void pnp_ensemble_destroy(pnp_ensemble* ens);
 
+/* ---- Learned electric-double-layer wall model (no counterpart in the paper) ----
+ * A coarse y-grid cannot resolve the Debye layer; a small network maps
+ * near-wall columns of the coarse state to wall slip velocities (and reports
+ * the potential offset and ion fluxes next to the wall).  Coarse grid: every
+ * ry-th y-face of a fine grid, Nx_c = Nx_f / rx, Nz_c = Nz_f / rz.  Rows are
+ * wall columns [wall][z][x] (bottom first), in the wall frame: the top wall
+ * is mapped onto the bottom by (x, y) -> (-x, -y) with c+ <-> c-, Phi -> -Phi;
+ * streamwise velocities are relative to the wall.
+ * Features (5 * ncells per row): [u_rel | w | c_counter | c_co | phi] for the
+ * ncells cells nearest the wall, phi = Phi - V y.
+ * Outputs / labels (5 per row): 0 / 1 the filtered fine wall shear rates
+ * d(u_rel)/dy and dw/dy, 2 phi of the first coarse cell, 3 / 4 total counter-
+ * / co-ion flux away from the wall through the first interior coarse face.
+ * Network: 40 -> 128 -> 128 -> 128 -> 128 -> 5, erf-GELU on hidden layers,
+ * BF16 weights in the forward GEMMs with FP32 accumulation, FP32 master
+ * weights, Adam; loss = mean squared error of normalised outputs. */
+typedef struct pnp_mlp pnp_mlp;
+int pnp_mlp_param_count(size_t* out_count);
+/* Device workspace for a network that processes up to max_batch rows. */
+int pnp_mlp_workspace_bytes(int max_batch, size_t* out_bytes);
+/* Weights U(-a, a), a = sqrt(6 / fan_in), from SplitMix64(seed); biases 0. */
+int pnp_mlp_create(pnp_mlp** out, int max_batch, void* device_workspace, size_t bytes, void* cuda_stream,
+                   uint64_t seed);
+int pnp_mlp_get_params(pnp_mlp* mlp, float* host_params, size_t count);
+/* Replace the FP32 master parameters (layer by layer: W [out][in] then b [out])
+ * and reset the Adam moments. */
+int pnp_mlp_set_params(pnp_mlp* mlp, const float* host_params, size_t count);
+/* Input x_n = (x - in_shift) * in_scale (40 each), output y = y_n / out_scale +
+ * out_shift (5 each); host arrays. */
+int pnp_mlp_set_normalization(pnp_mlp* mlp, const float* in_shift, const float* in_scale, const float* out_shift,
+                              const float* out_scale);
+/* Y[B][5] = network(X[B][40]); device arrays; asynchronous.  Normalised
+ * outputs are clipped to +-6 (six standard deviations of the training labels
+ * when the normalisation is set from them). */
+int pnp_mlp_forward(pnp_mlp* mlp, const float* X_dev, int B, float* Y_dev);
+/* Gradient of the loss against targets T[B][5] w.r.t. the parameters (host
+ * copy, optional) and the loss (host, optional); synchronises. */
+int pnp_mlp_gradient(pnp_mlp* mlp, const float* X_dev, const float* T_dev, int B, float* grad_host, float* loss_host);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr. */
+int pnp_mlp_train_step(pnp_mlp* mlp, const float* X_dev, const float* T_dev, int B, float lr, float* loss_host);
+void pnp_mlp_destroy(pnp_mlp* mlp);
+
+/* Feature rows of a context's state: X[2 Nz Nx][5 ncells] (ncells <= 8). */
+int pnp_wall_features(pnp_ctx* ctx, int ncells, float* X_dev);
+/* Coarse state := volume-weighted restriction of the fine state (u, v, w, p,
+ * c+-, Phi); the coarse stored explicit terms are zeroed. */
+int pnp_restrict_state(pnp_ctx* fine, pnp_ctx* coarse);
+/* Labels T[2 Nz_c Nx_c][5] of the coarse wall columns from the fine state. */
+int pnp_wall_labels(pnp_ctx* fine, pnp_ctx* coarse, float* T_dev);
+/* Wall slip velocities that impose the wall shear rates predicted in Y[2 Nz
+ * Nx][5] (columns 0 and 1): s = q_0 - h_0 g with q_0 the first-cell value in
+ * the feature rows X (ncells per field, as from pnp_wall_features) and h_0 the
+ * wall-to-centre distance; a non-finite slip or one above ten wall speeds
+ * falls back to no slip.  Y = NULL restores the uniform wall speeds.
+ * pnp_diagnostics then reports the wall shear against the plane-mean wall
+ * velocity. */
+int pnp_set_wall_slip(pnp_ctx* ctx, const float* X_dev, int ncells, const float* Y_dev);
+/* nsteps steps of the coarse solver with the wall model: before each step,
+ * features (8 cells) -> network -> wall slip. */
+int pnp_step_wallmodel(pnp_ctx* ctx, pnp_mlp* mlp, int nsteps, double dt);
+
 /* Launch sites timed by pnp_profile, in launch order within a substage. */
 enum {
   PNP_SITE_RHS = 0,         /* explicit terms + CN right-hand sides            */

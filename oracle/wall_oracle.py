@@ -1,0 +1,180 @@
+"""FP64 NumPy oracle of the learned wall model's data and network (TEST
+INFRASTRUCTURE ONLY; see oracle/__init__.py).
+
+The paper resolves the double layer and has no wall model; this restates the
+definitions the CUDA kernels implement, in plain array code: restriction of a
+fine state onto a coarse grid made of every ry-th y-face and rx x rz cell
+blocks, near-wall feature columns in the wall frame (rotation (x, y) -> (-x,
+-y) with c+ <-> c-, Phi -> -Phi maps the top wall onto the bottom), training
+labels (filtered fine wall shear rates, first-cell potential perturbation,
+ion fluxes through the first coarse face), and the
+MLP 40 -> 128 x 4 -> 5 with erf-GELU, MSE loss on normalised outputs,
+backpropagation and Adam.  Pinned by tests/test_oracle_wall.py.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.special import erf
+
+from .pnp_oracle import Grid  # noqa: F401  (grids are the oracle's)
+
+LAYERS = [(40, 128), (128, 128), (128, 128), (128, 128), (128, 5)]
+
+
+def ratios(gf, gc):
+    return gf.nx // gc.nx, gf.nyc // gc.nyc, gf.nz // gc.nz
+
+
+def restrict(gf, gc, q, vfield=False):
+    rx, ry, rz = ratios(gf, gc)
+    if vfield:
+        qq = q[::ry].reshape(gc.ny, gc.nz, rz, gc.nx, rx)
+        return qq.mean(axis=(2, 4))
+    qq = q.reshape(gc.nyc, ry, gc.nz, rz, gc.nx, rx)
+    w = gf.dy.reshape(gc.nyc, ry)
+    num = (qq.sum(axis=(3, 5)) * w[:, :, None, None]).sum(axis=1)
+    return num / (w.sum(axis=1) * rx * rz)[:, None, None]
+
+
+def wall_features(g, prm, st, ncells=8):
+    P = g.nz * g.nx
+    X = np.empty((2 * P, 5 * ncells))
+    phi = st.Phi - prm.V * g.yc[:, None, None]
+    for wall in (0, 1):
+        for d in range(ncells):
+            j = d if wall == 0 else g.nyc - 1 - d
+            ur = st.u[j] + prm.Uw if wall == 0 else prm.Uw - st.u[j]
+            rows = slice(wall * P, (wall + 1) * P)
+            X[rows, 0 * ncells + d] = ur.ravel()
+            X[rows, 1 * ncells + d] = st.w[j].ravel()
+            X[rows, 2 * ncells + d] = (st.cp[j] if wall == 0 else st.cm[j]).ravel()
+            X[rows, 3 * ncells + d] = (st.cm[j] if wall == 0 else st.cp[j]).ravel()
+            X[rows, 4 * ncells + d] = (phi[j] if wall == 0 else -phi[j]).ravel()
+    return X
+
+
+def _block_mean(gf, gc, a2d):
+    rx, _, rz = ratios(gf, gc)
+    return a2d.reshape(gc.nz, rz, gc.nx, rx).mean(axis=(1, 3))
+
+
+def wall_labels(gf, gc, prm, st):
+    rx, ry, rz = ratios(gf, gc)
+    Pc = gc.nz * gc.nx
+    T = np.empty((2 * Pc, 5))
+    D = prm.D
+    for wall in (0, 1):
+        sl = slice(0, ry) if wall == 0 else slice(gf.nyc - ry, gf.nyc)
+        w = gf.dy[sl]
+        urel = st.u + prm.Uw if wall == 0 else prm.Uw - st.u
+        phi = st.Phi - prm.V * gf.yc[:, None, None]
+        phi = phi if wall == 0 else -phi
+
+        def first_cell(q):
+            qq = q[sl].reshape(ry, gc.nz, rz, gc.nx, rx).sum(axis=(2, 4))
+            return (qq * w[:, None, None]).sum(axis=0) / (w.sum() * rx * rz)
+
+        pa = first_cell(phi)
+        j0 = 0 if wall == 0 else gf.nyc - 1
+        hw = gf.h[0] if wall == 0 else gf.h[gf.nyc]
+        gu = _block_mean(gf, gc, urel[j0] / hw)
+        gw = _block_mean(gf, gc, st.w[j0] / hw)
+        jf = ry if wall == 0 else gf.nyc - ry
+        a, b = jf - 1, jf
+        dP = (st.Phi[b] - st.Phi[a]) / gf.h[jf]
+        cpf, cmf = 0.5 * (st.cp[a] + st.cp[b]), 0.5 * (st.cm[a] + st.cm[b])
+        Fp = st.v[jf] * cpf - D * ((st.cp[b] - st.cp[a]) / gf.h[jf] + cpf * dP)
+        Fm = st.v[jf] * cmf - D * ((st.cm[b] - st.cm[a]) / gf.h[jf] - cmf * dP)
+        f3, f4 = (Fp, Fm) if wall == 0 else (-Fm, -Fp)
+        rows = slice(wall * Pc, (wall + 1) * Pc)
+        T[rows, 0] = gu.ravel()
+        T[rows, 1] = gw.ravel()
+        T[rows, 2] = pa.ravel()
+        T[rows, 3] = _block_mean(gf, gc, f3).ravel()
+        T[rows, 4] = _block_mean(gf, gc, f4).ravel()
+    return T
+
+
+# ---------------------------------------------------------------------------
+# MLP
+# ---------------------------------------------------------------------------
+def param_slices():
+    out, off = [], 0
+    for fi, fo in LAYERS:
+        w = slice(off, off + fi * fo)
+        off += fi * fo
+        b = slice(off, off + fo)
+        off += fo
+        out.append((w, b, fi, fo))
+    return out, off
+
+
+def bf16_round(p):
+    """Round float32 values to the nearest bfloat16 (ties to even), as float64."""
+    f = np.asarray(p, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+def gelu(z):
+    return 0.5 * z * (1.0 + erf(z / math.sqrt(2.0)))
+
+
+def gelu_d(z):
+    return 0.5 * (1.0 + erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+
+
+def _weights(p, bf16):
+    sl, _ = param_slices()
+    Ws, bs = [], []
+    for w, b, fi, fo in sl:
+        W = np.asarray(p[w], dtype=np.float64).reshape(fo, fi)
+        Ws.append(bf16_round(p[w]).reshape(fo, fi) if bf16 else W)
+        bs.append(np.asarray(p[b], dtype=np.float64))
+    return Ws, bs
+
+
+def forward(p, X, norm, bf16=True):
+    """Physical outputs and the cache for backpropagation."""
+    in_shift, in_scale, out_shift, out_scale = (np.asarray(a, dtype=np.float64) for a in norm)
+    Ws, bs = _weights(p, bf16)
+    a = (np.asarray(X, dtype=np.float64) - in_shift) * in_scale
+    ins, zs = [], []
+    for l, (W, b) in enumerate(zip(Ws, bs)):
+        x = a if l == 0 else gelu(zs[-1])
+        ins.append(x)
+        zs.append(x @ W.T + b)
+    yn = zs[-1]
+    return yn / out_scale + out_shift, (ins, zs, Ws)
+
+
+def loss_and_grad(p, X, T, norm, bf16=True):
+    """MSE of normalised outputs and its gradient w.r.t. the parameter vector
+    (w.r.t. the weights the forward pass used)."""
+    _, _, out_shift, out_scale = (np.asarray(a, dtype=np.float64) for a in norm)
+    _, (ins, zs, Ws) = forward(p, X, norm, bf16)
+    tn = (np.asarray(T, dtype=np.float64) - out_shift) * out_scale
+    e = zs[-1] - tn
+    n = e.size
+    loss = float(np.sum(e * e) / n)
+    sl, total = param_slices()
+    g = np.zeros(total)
+    dz = 2.0 * e / n
+    for l in range(len(LAYERS) - 1, -1, -1):
+        w, b, fi, fo = sl[l]
+        g[w] = (dz.T @ ins[l]).ravel()
+        g[b] = dz.sum(axis=0)
+        if l > 0:
+            dz = (dz @ Ws[l]) * gelu_d(zs[l - 1])
+    return loss, g
+
+
+def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** t)
+    vh = v / (1 - b2 ** t)
+    return p - lr * mh / (np.sqrt(vh) + eps), m, v

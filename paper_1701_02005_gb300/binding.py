@@ -80,6 +80,23 @@ EXPORTS = {
     "pnp_ensemble_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_void_p]),
     "pnp_ensemble_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "pnp_ensemble_destroy": (None, [C.c_void_p]),
+    "pnp_mlp_param_count": (C.c_int, [C.POINTER(C.c_size_t)]),
+    "pnp_mlp_workspace_bytes": (C.c_int, [C.c_int, C.POINTER(C.c_size_t)]),
+    "pnp_mlp_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p, C.c_uint64]),
+    "pnp_mlp_get_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_size_t]),
+    "pnp_mlp_set_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_size_t]),
+    "pnp_mlp_set_normalization": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                            C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "pnp_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "pnp_mlp_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_float),
+                                   C.POINTER(C.c_float)]),
+    "pnp_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.POINTER(C.c_float)]),
+    "pnp_mlp_destroy": (None, [C.c_void_p]),
+    "pnp_wall_features": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "pnp_restrict_state": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "pnp_wall_labels": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pnp_set_wall_slip": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "pnp_step_wallmodel": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double]),
     "pnp_error_string": (C.c_char_p, [C.c_int]),
     "pnp_destroy": (None, [C.c_void_p]),
 }
@@ -148,5 +165,20 @@ pnp_get_launch_config = _fwd("pnp_get_launch_config")
 pnp_ensemble_create = _fwd("pnp_ensemble_create")
 pnp_ensemble_step = _fwd("pnp_ensemble_step")
 pnp_ensemble_destroy = _fwd("pnp_ensemble_destroy")
+pnp_mlp_param_count = _fwd("pnp_mlp_param_count")
+pnp_mlp_workspace_bytes = _fwd("pnp_mlp_workspace_bytes")
+pnp_mlp_create = _fwd("pnp_mlp_create")
+pnp_mlp_get_params = _fwd("pnp_mlp_get_params")
+pnp_mlp_set_params = _fwd("pnp_mlp_set_params")
+pnp_mlp_set_normalization = _fwd("pnp_mlp_set_normalization")
+pnp_mlp_forward = _fwd("pnp_mlp_forward")
+pnp_mlp_gradient = _fwd("pnp_mlp_gradient")
+pnp_mlp_train_step = _fwd("pnp_mlp_train_step")
+pnp_mlp_destroy = _fwd("pnp_mlp_destroy")
+pnp_wall_features = _fwd("pnp_wall_features")
+pnp_restrict_state = _fwd("pnp_restrict_state")
+pnp_wall_labels = _fwd("pnp_wall_labels")
+pnp_set_wall_slip = _fwd("pnp_set_wall_slip")
+pnp_step_wallmodel = _fwd("pnp_step_wallmodel")
 pnp_error_string = _fwd("pnp_error_string")
 pnp_destroy = _fwd("pnp_destroy")

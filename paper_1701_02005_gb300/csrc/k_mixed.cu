@@ -71,7 +71,9 @@ __global__ void __launch_bounds__(128) k_mom_mixed(Fields<float> f, Shadows sh, 
     const float rhom = Lf(sh.cp, cxm) - Lf(sh.cm, cxm);
     const float fu = -K * (rref + 0.5f * (rhom + rho0)) * (ph0 - Lf(sh.phi, cxm)) * idx;
     const float H = -(ax + ay + az) + nu * lap + fu;
-    const float Ly = mt.lo_c[j] * ((has_dn ? uym : -Uw) - u0) + mt.hi_c[j] * ((has_up ? uyp : Uw) - u0);
+    const float ub = f.wall_u ? f.wall_u[(size_t)k * nx + i] : -Uw;
+    const float ut = f.wall_u ? f.wall_u[P + (size_t)k * nx + i] : Uw;
+    const float Ly = mt.lo_c[j] * ((has_dn ? uym : ub) - u0) + mt.hi_c[j] * ((has_up ? uyp : ut) - u0);
     const float gp = (p0 - Lf(f.p, cxm)) * idx;
     const float Ho = f.Hu[c0];
     f.ru[c0] = dt * (gam * H + zet * Ho - alp * gp + alp * nu * Ly);
@@ -93,7 +95,9 @@ __global__ void __launch_bounds__(128) k_mom_mixed(Fields<float> f, Shadows sh, 
     const float rhom = Lf(sh.cp, czm) - Lf(sh.cm, czm);
     const float fw = -K * (rref + 0.5f * (rhom + rho0)) * (ph0 - Lf(sh.phi, czm)) * idz;
     const float H = -(ax + ay + az) + nu * lap + fw;
-    const float Ly = mt.lo_c[j] * ((has_dn ? wym : 0.f) - w0) + mt.hi_c[j] * ((has_up ? wyp : 0.f) - w0);
+    const float wb = f.wall_w ? f.wall_w[(size_t)k * nx + i] : 0.f;
+    const float wt = f.wall_w ? f.wall_w[P + (size_t)k * nx + i] : 0.f;
+    const float Ly = mt.lo_c[j] * ((has_dn ? wym : wb) - w0) + mt.hi_c[j] * ((has_up ? wyp : wt) - w0);
     const float gp = (p0 - Lf(f.p, czm)) * idz;
     const float Ho = f.Hw[c0];
     f.rw[c0] = dt * (gam * H + zet * Ho - alp * gp + alp * nu * Ly);

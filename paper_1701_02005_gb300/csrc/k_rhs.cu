@@ -65,7 +65,9 @@ __global__ void __launch_bounds__(128) k_rhs(Fields<TV> f, Geo g, Metrics mt, Ph
     const double rhom = L(f.cp, cxm) - L(f.cm, cxm);
     const double fu = -ph.K * 0.5 * (rhom + rho0) * (Ph0 - Phxm) * idx;
     const double H = -(ax + ay + az) + ph.nu * lap + fu;
-    const double Ly = mt.lo_c[j] * ((has_dn ? uym : -ph.Uw) - u0) + mt.hi_c[j] * ((has_up ? uyp : ph.Uw) - u0);
+    const double ub = f.wall_u ? (double)f.wall_u[(size_t)k * nx + i] : -ph.Uw;
+    const double ut = f.wall_u ? (double)f.wall_u[P + (size_t)k * nx + i] : ph.Uw;
+    const double Ly = mt.lo_c[j] * ((has_dn ? uym : ub) - u0) + mt.hi_c[j] * ((has_up ? uyp : ut) - u0);
     const double gp = (p0 - L(f.p, cxm)) * idx;
     const double Ho = (double)f.Hu[c0];
     f.ru[c0] = (TV)(st.dt * (st.gam * H + st.zet * Ho - st.alp * gp + st.alp * ph.nu * Ly));
@@ -88,7 +90,9 @@ __global__ void __launch_bounds__(128) k_rhs(Fields<TV> f, Geo g, Metrics mt, Ph
     const double rhom = L(f.cp, czm) - L(f.cm, czm);
     const double fw = -ph.K * 0.5 * (rhom + rho0) * (Ph0 - Phzm) * idz;
     const double H = -(ax + ay + az) + ph.nu * lap + fw;
-    const double Ly = mt.lo_c[j] * ((has_dn ? wym : 0.0) - w0) + mt.hi_c[j] * ((has_up ? wyp : 0.0) - w0);
+    const double wb = f.wall_w ? (double)f.wall_w[(size_t)k * nx + i] : 0.0;
+    const double wt = f.wall_w ? (double)f.wall_w[P + (size_t)k * nx + i] : 0.0;
+    const double Ly = mt.lo_c[j] * ((has_dn ? wym : wb) - w0) + mt.hi_c[j] * ((has_up ? wyp : wt) - w0);
     const double gp = (p0 - L(f.p, czm)) * idz;
     const double Ho = (double)f.Hw[c0];
     f.rw[c0] = (TV)(st.dt * (st.gam * H + st.zet * Ho - st.alp * gp + st.alp * ph.nu * Ly));

@@ -13,6 +13,7 @@
 
 #include "pnp_common.cuh"
 #include "pnp_mixed.cuh"
+#include "pnp_wall.cuh"
 
 using namespace pnp;
 
@@ -83,6 +84,10 @@ struct pnp_ctx {
   // spectral elimination factors (grid-only): c'_j and 1/pivot_j per spectral point
   double *spc_cprN, *spc_invN, *spc_cprD, *spc_invD;
   cplx<double>* dscr;   // FP64 forward-sweep values of the spectral solves
+  // wall model: per-column wall velocities [2][P] (velocity precision), feature / output rows
+  void *wall_u, *wall_w;
+  float *featX, *featY;
+  bool slip_on = false;
   std::vector<double> href_p, href_m, lyc_p, lyc_m;
   bool refs_valid = false;   // references and shadows match the FP64 fields
   bool fp64_fresh = true;    // FP64 Phi, Hc+- arrays are current (else the shadows are)
@@ -142,8 +147,14 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
   double *fcN = b.take<double>(nspec), *fiN = b.take<double>(nspec), *fcD = b.take<double>(nspec),
          *fiD = b.take<double>(nspec);
   cplx<double>* dscr = b.take<cplx<double>>(nspec);
+  const size_t P2 = 2 * (size_t)nz * nx;
+  void* wallu = b.take<char>(P2 * tv);
+  void* wallw = b.take<char>(P2 * tv);
+  float* fX = b.take<float>(P2 * 5 * 8);
+  float* fY = b.take<float>(P2 * 5);
   if (c) {
     c->dscr = dscr;
+    c->wall_u = wallu; c->wall_w = wallw; c->featX = fX; c->featY = fY;
     c->spc_cprN = fcN; c->spc_invN = fiN; c->spc_cprD = fcD; c->spc_invD = fiD;
     c->cpS = cpS; c->cmS = cmS; c->phiS = phiS; c->HcpS = HcpS; c->HcmS = HcmS;
     for (int q = 0; q < 8; ++q) c->mf[q] = mf[q];
@@ -398,6 +409,8 @@ Fields<TV> fields(const pnp_ctx* c) {
   f.Hu = (TV*)c->Hu; f.Hv = (TV*)c->Hv; f.Hw = (TV*)c->Hw;
   f.ru = (TV*)c->ru; f.rv = (TV*)c->rv; f.rw = (TV*)c->rw;
   f.cp = c->cp; f.cm = c->cm; f.Phi = c->Phi; f.Hcp = c->Hcp; f.Hcm = c->Hcm; f.rcp = c->rcp; f.rcm = c->rcm;
+  f.wall_u = c->slip_on ? (const TV*)c->wall_u : nullptr;
+  f.wall_w = c->slip_on ? (const TV*)c->wall_w : nullptr;
   return f;
 }
 
@@ -887,9 +900,21 @@ int pnp_diagnostics(pnp_ctx* c, pnp_diag* out) {
   const double P = (double)c->g.nx * c->g.nz;
   const double ub = h[0] / P, ut = h[1] / P;
   const double Uw = c->ph.Uw;
+  double wb = -Uw, wt = Uw;   // plane-mean wall velocities
+  if (c->slip_on) {
+    double m2[2];
+    cudaError_t e2 = c->precision == PNP_FP64
+                         ? launch_mean_profile<double>((const double*)c->wall_u, 2, (int)P, c->stage, c->stream)
+                         : launch_mean_profile<float>((const float*)c->wall_u, 2, (int)P, c->stage, c->stream);
+    if (e2 != cudaSuccess) return PNP_ERR_CUDA;
+    CK(cudaMemcpyAsync(m2, c->stage, sizeof(m2), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    wb = m2[0];
+    wt = m2[1];
+  }
   std::memset(out, 0, sizeof(*out));
-  out->tau_bot = c->ph.nu * (ub + Uw) / c->h[0];
-  out->tau_top = c->ph.nu * (Uw - ut) / c->h[c->g.nyc];
+  out->tau_bot = c->ph.nu * (ub - wb) / c->h[0];
+  out->tau_top = c->ph.nu * (wt - ut) / c->h[c->g.nyc];
   const double tau = 0.5 * (out->tau_bot + out->tau_top);
   out->cf = Uw != 0.0 ? 2.0 * tau / (Uw * Uw) : 0.0;
   out->re_tau = c->Re * std::sqrt(tau > 0 ? tau : 0.0);
@@ -1280,6 +1305,288 @@ void pnp_ensemble_destroy(pnp_ensemble* e) {
   for (cudaStream_t st : e->branch)
     if (st) cudaStreamDestroy(st);
   delete e;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Learned wall model: MLP workspace and the coupling to a coarse context.
+// ---------------------------------------------------------------------------
+struct pnp_mlp {
+  MlpBufs b{};
+  int max_batch = 0;
+  int max_partial = 64;
+  size_t nparam = 0;
+  cudaStream_t stream = nullptr;
+  int t_adam = 0;
+};
+
+namespace {
+
+size_t mlp_carve(pnp_mlp* m, char* base, int max_batch) {
+  Bump bp{base};
+  const MlpDims d = mlp_dims();
+  const size_t np = d.nparam, B = (size_t)max_batch;
+  MlpBufs b{};
+  b.param = bp.take<float>(np);
+  b.wbf = bp.take<__nv_bfloat16>(np);
+  b.grad = bp.take<float>(np);
+  b.m = bp.take<float>(np);
+  b.v = bp.take<float>(np);
+  b.act[0] = bp.take<float>(B * kMlpIn);
+  for (int l = 0; l < kMlpLayers; ++l) b.act[l + 1] = bp.take<float>(B * d.out[l]);
+  b.dact = bp.take<float>(B * kMlpHidden);
+  b.dact2 = bp.take<float>(B * kMlpHidden);
+  b.partial = bp.take<float>(64 * (size_t)(kMlpHidden * kMlpHidden + kMlpHidden));
+  b.loss = bp.take<float>(128);
+  b.in_shift = bp.take<float>(kMlpIn);
+  b.in_scale = bp.take<float>(kMlpIn);
+  b.out_shift = bp.take<float>(kMlpOut);
+  b.out_scale = bp.take<float>(kMlpOut);
+  if (m) {
+    m->b = b;
+    m->nparam = np;
+  }
+  return bp.off + kAlign;
+}
+
+uint64_t sm64_host(uint64_t seed, uint64_t n) {
+  uint64_t x = seed + (n + 1ull) * 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+WallMap wall_map(const pnp_ctx* f, const pnp_ctx* c, int* err) {
+  WallMap wm{};
+  *err = PNP_ERR_ARG;
+  if (f->g.nx % c->g.nx || f->g.nz % c->g.nz || f->g.nyc % c->g.nyc) return wm;
+  wm.nx_f = f->g.nx; wm.nz_f = f->g.nz; wm.nyc_f = f->g.nyc;
+  wm.nx_c = c->g.nx; wm.nz_c = c->g.nz; wm.nyc_c = c->g.nyc;
+  wm.rx = f->g.nx / c->g.nx; wm.rz = f->g.nz / c->g.nz; wm.ry = f->g.nyc / c->g.nyc;
+  for (int jc = 0; jc <= c->g.nyc; ++jc)
+    if (std::fabs(c->yf[jc] - f->yf[jc * wm.ry]) > 1e-12) return wm;   // coarse faces must be fine faces
+  *err = PNP_OK;
+  return wm;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pnp_mlp_param_count(size_t* out) {
+  if (!out) return PNP_ERR_ARG;
+  *out = mlp_dims().nparam;
+  return PNP_OK;
+}
+
+int pnp_mlp_workspace_bytes(int max_batch, size_t* out) {
+  if (!out || max_batch < 1) return PNP_ERR_ARG;
+  *out = mlp_carve(nullptr, nullptr, max_batch);
+  return PNP_OK;
+}
+
+int pnp_mlp_create(pnp_mlp** out, int max_batch, void* ws, size_t bytes, void* stream, uint64_t seed) {
+  if (!out || !ws || max_batch < 1) return PNP_ERR_ARG;
+  if (((uintptr_t)ws % kAlign) != 0 || bytes < mlp_carve(nullptr, nullptr, max_batch)) return PNP_ERR_WORKSPACE;
+  pnp_mlp* m = new (std::nothrow) pnp_mlp();
+  if (!m) return PNP_ERR_ARG;
+  m->max_batch = max_batch;
+  m->stream = (cudaStream_t)stream;
+  mlp_carve(m, (char*)ws, max_batch);
+  if (mlp_prepare() != cudaSuccess) { delete m; return PNP_ERR_CUDA; }
+  // weights U(-a, a), a = sqrt(6 / fan_in) from SplitMix64; biases 0; unit normalisation
+  const MlpDims d = mlp_dims();
+  std::vector<float> p(d.nparam, 0.f);
+  for (int l = 0; l < kMlpLayers; ++l) {
+    const double a = std::sqrt(6.0 / d.in[l]);
+    for (size_t e = 0; e < (size_t)d.in[l] * d.out[l]; ++e) {
+      const double u01 = (double)(sm64_host(seed, d.woff[l] + e) >> 11) * 0x1p-53;
+      p[d.woff[l] + e] = (float)(a * (2.0 * u01 - 1.0));
+    }
+  }
+  std::vector<float> ones(kMlpIn, 1.f), zeros(kMlpIn, 0.f);
+  bool ok = cudaMemsetAsync(ws, 0, bytes, m->stream) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(m->b.param, p.data(), sizeof(float) * d.nparam, cudaMemcpyHostToDevice, m->stream) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(m->b.in_scale, ones.data(), sizeof(float) * kMlpIn, cudaMemcpyHostToDevice, m->stream) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(m->b.out_scale, ones.data(), sizeof(float) * kMlpOut, cudaMemcpyHostToDevice, m->stream) == cudaSuccess;
+  ok = ok && mlp_sync_bf16(m->b, d.nparam, m->stream) == cudaSuccess;
+  ok = ok && cudaStreamSynchronize(m->stream) == cudaSuccess;
+  if (!ok) { delete m; return PNP_ERR_CUDA; }
+  *out = m;
+  return PNP_OK;
+}
+
+int pnp_mlp_get_params(pnp_mlp* m, float* host, size_t n) {
+  if (!m || !host || n != m->nparam) return PNP_ERR_ARG;
+  CK(cudaMemcpyAsync(host, m->b.param, sizeof(float) * n, cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  return PNP_OK;
+}
+
+int pnp_mlp_set_params(pnp_mlp* m, const float* host, size_t n) {
+  if (!m || !host || n != m->nparam) return PNP_ERR_ARG;
+  CK(cudaMemcpyAsync(m->b.param, host, sizeof(float) * n, cudaMemcpyHostToDevice, m->stream));
+  CK(cudaMemsetAsync(m->b.m, 0, sizeof(float) * n, m->stream));
+  CK(cudaMemsetAsync(m->b.v, 0, sizeof(float) * n, m->stream));
+  CK(mlp_sync_bf16(m->b, n, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  m->t_adam = 0;
+  return PNP_OK;
+}
+
+int pnp_mlp_set_normalization(pnp_mlp* m, const float* in_shift, const float* in_scale, const float* out_shift,
+                              const float* out_scale) {
+  if (!m || !in_shift || !in_scale || !out_shift || !out_scale) return PNP_ERR_ARG;
+  CK(cudaMemcpyAsync(m->b.in_shift, in_shift, sizeof(float) * kMlpIn, cudaMemcpyHostToDevice, m->stream));
+  CK(cudaMemcpyAsync(m->b.in_scale, in_scale, sizeof(float) * kMlpIn, cudaMemcpyHostToDevice, m->stream));
+  CK(cudaMemcpyAsync(m->b.out_shift, out_shift, sizeof(float) * kMlpOut, cudaMemcpyHostToDevice, m->stream));
+  CK(cudaMemcpyAsync(m->b.out_scale, out_scale, sizeof(float) * kMlpOut, cudaMemcpyHostToDevice, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  return PNP_OK;
+}
+
+int pnp_mlp_forward(pnp_mlp* m, const float* X, int B, float* Y) {
+  if (!m || !X || !Y || B < 1 || B > m->max_batch) return PNP_ERR_ARG;
+  CK(mlp_forward(m->b, X, B, Y, m->stream));
+  return PNP_OK;
+}
+
+int pnp_mlp_gradient(pnp_mlp* m, const float* X, const float* T, int B, float* grad_host, float* loss_host) {
+  if (!m || !X || !T || B < 1 || B > m->max_batch) return PNP_ERR_ARG;
+  CK(mlp_forward(m->b, X, B, nullptr, m->stream));
+  CK(mlp_backward(m->b, T, B, m->max_partial, m->stream));
+  if (grad_host) CK(cudaMemcpyAsync(grad_host, m->b.grad, sizeof(float) * m->nparam, cudaMemcpyDeviceToHost, m->stream));
+  if (loss_host) CK(cudaMemcpyAsync(loss_host, m->b.loss + 120, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  return PNP_OK;
+}
+
+int pnp_mlp_train_step(pnp_mlp* m, const float* X, const float* T, int B, float lr, float* loss_host) {
+  if (!m || !X || !T || B < 1 || B > m->max_batch || !(lr > 0)) return PNP_ERR_ARG;
+  CK(mlp_forward(m->b, X, B, nullptr, m->stream));
+  CK(mlp_backward(m->b, T, B, m->max_partial, m->stream));
+  m->t_adam += 1;
+  CK(mlp_adam(m->b, m->nparam, lr, 0.9f, 0.999f, 1e-8f, m->t_adam, m->stream));
+  if (loss_host) {
+    CK(cudaMemcpyAsync(loss_host, m->b.loss + 120, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+  }
+  return PNP_OK;
+}
+
+void pnp_mlp_destroy(pnp_mlp* m) { delete m; }
+
+int pnp_wall_features(pnp_ctx* c, int ncells, float* X) {
+  if (!c || !X || ncells < 1 || ncells > 8 || ncells > c->g.nyc) return PNP_ERR_ARG;
+  if (!c->have_state) return PNP_ERR_STATE;
+  int r = materialize(c);
+  if (r) return r;
+  cudaError_t e = c->precision == PNP_FP64
+                      ? launch_wall_features<double>((const double*)c->u, (const double*)c->w, c->cp, c->cm, c->Phi,
+                                                     c->yc_d, c->g, c->ph.V, c->ph.Uw, ncells, X, c->stream)
+                      : launch_wall_features<float>((const float*)c->u, (const float*)c->w, c->cp, c->cm, c->Phi,
+                                                    c->yc_d, c->g, c->ph.V, c->ph.Uw, ncells, X, c->stream);
+  return e == cudaSuccess ? PNP_OK : PNP_ERR_CUDA;
+}
+
+int pnp_restrict_state(pnp_ctx* f, pnp_ctx* c) {
+  if (!f || !c || f == c) return PNP_ERR_ARG;
+  if (!f->have_state || !c->have_params) return PNP_ERR_STATE;
+  int err = 0;
+  const WallMap wm = wall_map(f, c, &err);
+  if (err) return err;
+  int r = materialize(f);
+  if (r) return r;
+  double* dyf = nullptr;
+  // fine cell heights: reuse the fine context's staging area tail (ny values) as scratch
+  dyf = f->stage + f->nv - f->g.ny;
+  CK(cudaMemcpyAsync(dyf, f->dy.data(), sizeof(double) * f->g.nyc, cudaMemcpyHostToDevice, f->stream));
+  const int fields_[7] = {PNP_U, PNP_V, PNP_W, PNP_P, PNP_CP, PNP_CM, PNP_PHI};
+  for (int q = 0; q < 7; ++q) {
+    const int fld = fields_[q];
+    const void* src = field_ptr(f, fld);
+    const bool vf = fld == PNP_V;
+    double* out = f->sreal;   // fine scratch is large enough for any coarse field
+    cudaError_t e;
+    if (f->precision == PNP_MIXED && is_vel_field(fld)) e = launch_restrict<float>((const float*)src, dyf, wm, out, vf, f->stream);
+    else e = launch_restrict<double>((const double*)src, dyf, wm, out, vf, f->stream);
+    if (e != cudaSuccess) return PNP_ERR_CUDA;
+    CK(cudaStreamSynchronize(f->stream));
+    r = pnp_set_state(c, fld, out, 1);
+    if (r) return r;
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  // the coarse run starts with no stored explicit terms
+  for (int fld : {PNP_HU, PNP_HV, PNP_HW}) CK(cudaMemsetAsync(field_ptr(c, fld), 0, field_count(c, fld) * (c->precision == PNP_FP64 ? 8 : 4), c->stream));
+  for (int fld : {PNP_HCP, PNP_HCM}) CK(cudaMemsetAsync(field_ptr(c, fld), 0, field_count(c, fld) * 8, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->have_state = true;
+  c->fp64_fresh = true;
+  c->refs_valid = false;
+  return PNP_OK;
+}
+
+int pnp_wall_labels(pnp_ctx* f, pnp_ctx* c, float* T) {
+  if (!f || !c || !T || f == c) return PNP_ERR_ARG;
+  if (!f->have_state) return PNP_ERR_STATE;
+  int err = 0;
+  const WallMap wm = wall_map(f, c, &err);
+  if (err) return err;
+  int r = materialize(f);
+  if (r) return r;
+  double* scr = f->stage + f->nv - 3 * (size_t)f->g.ny;   // ycf, dyf, hf
+  std::vector<double> pack(3 * (size_t)f->g.ny, 0.0);
+  for (int j = 0; j < f->g.nyc; ++j) { pack[j] = f->yc[j]; pack[f->g.ny + j] = f->dy[j]; }
+  for (int j = 0; j < f->g.ny; ++j) pack[2 * f->g.ny + j] = f->h[j];
+  CK(cudaMemcpyAsync(scr, pack.data(), sizeof(double) * pack.size(), cudaMemcpyHostToDevice, f->stream));
+  const double h0c = c->h[0];
+  cudaError_t e = f->precision == PNP_FP64
+                      ? launch_wall_labels<double>((const double*)f->u, (const double*)f->v, (const double*)f->w, f->cp,
+                                                   f->cm, f->Phi, scr, scr + f->g.ny, scr + 2 * f->g.ny, wm, h0c,
+                                                   f->ph.V, f->ph.Uw, f->ph.D, T, f->stream)
+                      : launch_wall_labels<float>((const float*)f->u, (const float*)f->v, (const float*)f->w, f->cp,
+                                                  f->cm, f->Phi, scr, scr + f->g.ny, scr + 2 * f->g.ny, wm, h0c,
+                                                  f->ph.V, f->ph.Uw, f->ph.D, T, f->stream);
+  if (e != cudaSuccess) return PNP_ERR_CUDA;
+  CK(cudaStreamSynchronize(f->stream));
+  return PNP_OK;
+}
+
+int pnp_set_wall_slip(pnp_ctx* c, const float* X, int ncells, const float* Y) {
+  if (!c || (Y && (!X || ncells < 1 || ncells > 8))) return PNP_ERR_ARG;
+  const size_t P = (size_t)c->g.nz * c->g.nx;
+  const bool was = c->slip_on;
+  if (!Y) {
+    c->slip_on = false;
+  } else {
+    const double h0b = c->h[0], h0t = c->h[c->g.nyc];
+    cudaError_t e = c->precision == PNP_FP64
+                        ? launch_set_slip<double>(X, ncells, Y, P, c->ph.Uw, h0b, h0t, (double*)c->wall_u,
+                                                  (double*)c->wall_w, c->stream)
+                        : launch_set_slip<float>(X, ncells, Y, P, c->ph.Uw, h0b, h0t, (float*)c->wall_u,
+                                                 (float*)c->wall_w, c->stream);
+    if (e != cudaSuccess) return PNP_ERR_CUDA;
+    c->slip_on = true;
+  }
+  if (was != c->slip_on) drop_graph(c);
+  return PNP_OK;
+}
+
+int pnp_step_wallmodel(pnp_ctx* c, pnp_mlp* m, int nsteps, double dt) {
+  if (!c || !m || nsteps < 0) return PNP_ERR_ARG;
+  const int rows = 2 * c->g.nz * c->g.nx;
+  if (rows > m->max_batch) return PNP_ERR_ARG;
+  for (int n = 0; n < nsteps; ++n) {
+    int r = pnp_wall_features(c, 8, c->featX);
+    if (r) return r;
+    CK(mlp_forward(m->b, c->featX, rows, c->featY, c->stream));
+    r = pnp_set_wall_slip(c, c->featX, 8, c->featY);
+    if (r) return r;
+    r = pnp_step(c, 1, dt);
+    if (r) return r;
+  }
+  return PNP_OK;
 }
 
 const char* pnp_error_string(int code) {

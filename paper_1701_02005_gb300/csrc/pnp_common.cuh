@@ -71,6 +71,9 @@ struct Fields {
   double *cp, *cm, *Phi;
   double *Hcp, *Hcm;
   double *rcp, *rcm;
+  // optional per-column wall velocities [2][nz][nx] (bottom, top), lab frame;
+  // nullptr = the uniform wall speeds -Uw / +Uw for u and 0 for w
+  const TV *wall_u, *wall_w;
 };
 
 // Crank-Nicolson factor rows of one substage for the y-implicit solves:

@@ -1,0 +1,68 @@
+// Declarations of the wall-model data kernels (k_wall.cu) and the MLP (k_mlp.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "pnp_common.cuh"
+
+namespace pnp {
+
+// Index map between a fine grid and a coarse grid made of every ry-th fine
+// y-face and rx x rz blocks of fine cells in x and z.
+struct WallMap {
+  int nx_f, nz_f, nyc_f;
+  int nx_c, nz_c, nyc_c;
+  int rx, ry, rz;
+};
+
+template <typename T>
+cudaError_t launch_restrict(const T* f, const double* dyf, const WallMap& wm, double* out, bool vfield, cudaStream_t s);
+template <typename TV>
+cudaError_t launch_wall_features(const TV* u, const TV* w, const double* cp, const double* cm, const double* Phi,
+                                 const double* yc, const Geo& g, double V, double Uw, int ncells, float* X,
+                                 cudaStream_t s);
+template <typename TV>
+cudaError_t launch_wall_labels(const TV* u, const TV* v, const TV* w, const double* cp, const double* cm,
+                               const double* Phi, const double* ycf, const double* dyf, const double* hf,
+                               const WallMap& wm, double h0c, double V, double Uw, double D_ion, float* T,
+                               cudaStream_t s);
+template <typename TV>
+cudaError_t launch_set_slip(const float* X, int ncells, const float* Y, size_t P, double Uw, double h0b, double h0t,
+                            TV* wall_u, TV* wall_w, cudaStream_t s);
+
+// ---- MLP 40 -> 128 x 4 (erf-GELU) -> 5 ----
+constexpr int kMlpLayers = 5;
+constexpr int kMlpIn = 40;
+constexpr int kMlpHidden = 128;
+constexpr int kMlpOut = 5;
+
+struct MlpDims {
+  int in[kMlpLayers], out[kMlpLayers];
+  size_t woff[kMlpLayers], boff[kMlpLayers];   // offsets in the parameter vector
+  size_t nparam;
+};
+MlpDims mlp_dims();
+
+// Buffers of one MLP (all device pointers, carved by the host code).
+struct MlpBufs {
+  float* param;        // FP32 master weights and biases
+  __nv_bfloat16* wbf;  // BF16 copy of the weights used by the forward GEMMs (same offsets)
+  float* grad;         // gradient of the loss
+  float* m;            // Adam first moment
+  float* v;            // Adam second moment
+  float* act[kMlpLayers + 1];   // act[0] normalised input, act[l+1] output of layer l (pre-activation z)
+  float* dact;         // backward scratch [B][128]
+  float* dact2;        // backward scratch [B][128]
+  float* partial;      // per-block partial weight gradients
+  float* loss;         // [partial blocks] then the reduced loss
+  float *in_shift, *in_scale, *out_shift, *out_scale;
+};
+
+cudaError_t mlp_prepare();
+cudaError_t mlp_sync_bf16(const MlpBufs& b, size_t nparam, cudaStream_t s);
+cudaError_t mlp_forward(const MlpBufs& b, const float* X, int B, float* Y, cudaStream_t s);
+cudaError_t mlp_backward(const MlpBufs& b, const float* T, int B, int max_partial, cudaStream_t s);
+cudaError_t mlp_adam(const MlpBufs& b, size_t nparam, float lr, float beta1, float beta2, float eps, int t,
+                     cudaStream_t s);
+
+}  // namespace pnp

@@ -1,0 +1,125 @@
+"""Learned double-layer wall model: the MLP of libpnp (pnp_mlp_* in include/pnp.h)
+with torch-owned workspace, and the data calls that couple it to solver contexts."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import binding as B
+
+N_IN, N_OUT = 40, 5
+
+
+def _fp(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class MLP:
+    def __init__(self, max_batch, seed=1705, device=0, stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        nb = C.c_size_t()
+        B.check(B.pnp_mlp_workspace_bytes(int(max_batch), C.byref(nb)), "pnp_mlp_workspace_bytes")
+        self.ws = torch.empty(int(nb.value) + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.ws.data_ptr()) % 256
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        m = C.c_void_p()
+        B.check(B.pnp_mlp_create(C.byref(m), int(max_batch), C.c_void_p(self.ws.data_ptr() + off),
+                                 C.c_size_t(int(nb.value)), C.c_void_p(self.stream.cuda_stream), C.c_uint64(seed)),
+                "pnp_mlp_create")
+        self.m = m
+        self.max_batch = int(max_batch)
+        n = C.c_size_t()
+        B.check(B.pnp_mlp_param_count(C.byref(n)), "pnp_mlp_param_count")
+        self.nparam = int(n.value)
+
+    def params(self):
+        out = np.empty(self.nparam, dtype=np.float32)
+        B.check(B.pnp_mlp_get_params(self.m, out.ctypes.data_as(C.POINTER(C.c_float)), self.nparam),
+                "pnp_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        a, ptr = _fp(p)
+        B.check(B.pnp_mlp_set_params(self.m, ptr, a.size), "pnp_mlp_set_params")
+
+    def set_normalization(self, in_shift, in_scale, out_shift, out_scale):
+        arrs = [_fp(x) for x in (in_shift, in_scale, out_shift, out_scale)]
+        B.check(B.pnp_mlp_set_normalization(self.m, *[p for _, p in arrs]), "pnp_mlp_set_normalization")
+
+    def _sync(self):
+        self.torch.cuda.synchronize(self.device)
+
+    def forward(self, X):
+        """X: device float32 tensor [B, 40] -> device tensor [B, 5]."""
+        Y = self.torch.empty((X.shape[0], N_OUT), dtype=self.torch.float32, device=self.device)
+        self._sync()
+        B.check(B.pnp_mlp_forward(self.m, C.c_void_p(X.data_ptr()), int(X.shape[0]), C.c_void_p(Y.data_ptr())),
+                "pnp_mlp_forward")
+        self.stream.synchronize()
+        return Y
+
+    def gradient(self, X, T):
+        g = np.empty(self.nparam, dtype=np.float32)
+        loss = C.c_float()
+        self._sync()
+        B.check(B.pnp_mlp_gradient(self.m, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()), int(X.shape[0]),
+                                   g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss)), "pnp_mlp_gradient")
+        return g, float(loss.value)
+
+    def train_step(self, X, T, lr, want_loss=False):
+        loss = C.c_float()
+        B.check(B.pnp_mlp_train_step(self.m, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()), int(X.shape[0]),
+                                     float(lr), C.byref(loss) if want_loss else None), "pnp_mlp_train_step")
+        return float(loss.value) if want_loss else None
+
+    def close(self):
+        if getattr(self, "m", None):
+            self.stream.synchronize()
+            B.pnp_mlp_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def features(solver, ncells=8):
+    """Feature rows [2 Nz Nx, 5 ncells] of a solver's state (device tensor)."""
+    torch = solver.torch
+    X = torch.empty((2 * solver.nz * solver.nx, 5 * ncells), dtype=torch.float32, device=solver.device)
+    torch.cuda.synchronize(solver.device)
+    B.check(B.pnp_wall_features(solver.ctx, int(ncells), C.c_void_p(X.data_ptr())), "pnp_wall_features")
+    solver.synchronize()
+    return X
+
+
+def labels(fine, coarse):
+    torch = fine.torch
+    T = torch.empty((2 * coarse.nz * coarse.nx, N_OUT), dtype=torch.float32, device=fine.device)
+    torch.cuda.synchronize(fine.device)
+    B.check(B.pnp_wall_labels(fine.ctx, coarse.ctx, C.c_void_p(T.data_ptr())), "pnp_wall_labels")
+    return T
+
+
+def restrict(fine, coarse):
+    B.check(B.pnp_restrict_state(fine.ctx, coarse.ctx), "pnp_restrict_state")
+
+
+def set_slip(solver, X, Y, ncells=8):
+    solver.torch.cuda.synchronize(solver.device)
+    if Y is None:
+        B.check(B.pnp_set_wall_slip(solver.ctx, None, 0, None), "pnp_set_wall_slip")
+    else:
+        B.check(B.pnp_set_wall_slip(solver.ctx, C.c_void_p(X.data_ptr()), int(ncells), C.c_void_p(Y.data_ptr())),
+                "pnp_set_wall_slip")
+
+
+def step_with_model(solver, mlp, nsteps, dt):
+    B.check(B.pnp_step_wallmodel(solver.ctx, mlp.m, int(nsteps), float(dt)), "pnp_step_wallmodel")

@@ -1,0 +1,203 @@
+"""Learned wall model on the GPU: data kernels and network against the FP64
+oracle, training by the library's own kernels, and the gain over the coarse
+solver without the model (drag judged against the fine DNS)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import pnp_oracle as o
+from oracle import wall_oracle as w
+from tests import seeded
+
+pytestmark = pytest.mark.gpu
+
+
+def _solver(g, prm, precision=0):
+    from paper_1701_02005_gb300.solver import Solver
+
+    s = Solver(g.nx, g.ny, g.nz, g.Lx, g.Lz, precision=precision, y_faces=g.yf)
+    s.set_params(prm.Re, prm.lam, prm.Sc, prm.V, prm.beta, prm.Uw)
+    return s
+
+
+def _grids():
+    gf = o.Grid(16, 33, 8, 2 * math.pi, math.pi, stretch=2.0)
+    gc = o.Grid(8, 9, 4, 2 * math.pi, math.pi, y_faces=gf.yf[::4])
+    return gf, gc
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-30))
+
+
+def test_restriction_features_labels_match_oracle():
+    from paper_1701_02005_gb300 import wallmodel as wm
+
+    gf, gc = _grids()
+    prm = o.Params(Re=200.0, lam=0.1, V=2.0)
+    st = o.initial_state(gf, prm, o.IC_PB, seed=21, amp=0.2)
+    shp = (gf.nyc, gf.nz, gf.nx)
+    st.cp = st.cp * seeded.positive_field(22, shp, 0.9, 1.1)
+    st.Phi = st.Phi + seeded.field(23, shp, 0.02)
+    sf, sc = _solver(gf, prm), _solver(gc, prm)
+    sf.set_state(st)
+    wm.restrict(sf, sc)
+    for name, vf in (("u", False), ("v", True), ("w", False), ("cp", False), ("Phi", False)):
+        assert _rel(sc.get(name), w.restrict(gf, gc, getattr(st, name), vf)) <= 1e-13, name
+    stc = o.State(*(w.restrict(gf, gc, getattr(st, n), n == "v") for n in ("u", "v", "w", "p", "cp", "cm", "Phi")),
+                  *(np.zeros(1),) * 5)
+    X = wm.features(sc, 8).cpu().numpy()
+    Xr = w.wall_features(gc, prm, stc, 8)
+    assert np.max(np.abs(X - Xr)) <= 1e-6 * np.max(np.abs(Xr))
+    T = wm.labels(sf, sc).cpu().numpy()
+    Tr = w.wall_labels(gf, gc, prm, st)
+    for q in range(5):
+        assert np.max(np.abs(T[:, q] - Tr[:, q])) <= 1e-5 * max(np.max(np.abs(Tr[:, q])), 1e-12), q
+    sf.close()
+    sc.close()
+
+
+def _norm(seed):
+    r = seeded.rng(seed)
+    return [r.normal(size=40).astype(np.float32), r.uniform(0.5, 2, 40).astype(np.float32),
+            r.normal(size=5).astype(np.float32), r.uniform(0.5, 2, 5).astype(np.float32)]
+
+
+def test_mlp_forward_and_gradient_match_oracle():
+    import torch
+
+    from paper_1701_02005_gb300.wallmodel import MLP
+
+    net = MLP(256, seed=5)
+    norm = _norm(6)
+    net.set_normalization(*norm)
+    p = net.params()
+    r = seeded.rng(7)
+    X = r.standard_normal((200, 40)).astype(np.float32)
+    T = r.standard_normal((200, 5)).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    Y = net.forward(Xd).cpu().numpy()
+    Yr, _ = w.forward(p, X, norm, bf16=True)
+    Yr = np.clip((Yr - norm[2]) * norm[3], -6, 6) / norm[3] + norm[2]   # inference path clips at 6 sigma
+    assert np.max(np.abs(Y - Yr)) <= 1e-5 * np.max(np.abs(Yr))
+    g, loss = net.gradient(Xd, Td)
+    lr, gr = w.loss_and_grad(p, X, T, norm, bf16=True)
+    assert abs(loss - lr) <= 1e-5 * lr
+    sl, _ = w.param_slices()
+    for ws, bs, _, _ in sl:
+        for s_ in (ws, bs):
+            assert np.max(np.abs(g[s_] - gr[s_])) <= 1e-4 * np.max(np.abs(gr[s_])) + 1e-9
+    net.close()
+
+
+def test_mlp_training_reduces_loss():
+    import torch
+
+    from paper_1701_02005_gb300.wallmodel import MLP
+
+    r = seeded.rng(9)
+    X = r.standard_normal((4096, 40)).astype(np.float32)
+    A = r.standard_normal((40, 5)) / math.sqrt(40)
+    T = (np.tanh(X @ A) + 0.1 * (X[:, :5] ** 2)).astype(np.float32)
+    net = MLP(4096, seed=10)
+    net.set_normalization(np.zeros(40), np.ones(40), np.zeros(5), np.ones(5))
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    l0 = net.train_step(Xd, Td, 1e-3, want_loss=True)
+    for _ in range(400):
+        net.train_step(Xd, Td, 1e-3)
+    l1 = net.train_step(Xd, Td, 1e-3, want_loss=True)
+    assert l1 < 0.1 * l0, (l0, l1)
+    net.close()
+
+
+def _impulsive(s, g, seed, amp=0.02):
+    """Walls set in motion at t = 0: the seeded, projected noise of pnp_init_state
+    minus the Couette profile (a function of y only, so still divergence free)."""
+    s.init_state(1, seed, amp)
+    s.set("u", s.get("u") - g.yc[:, None, None])
+
+
+def wall_model_case(nfine=(32, 65, 32), ry=4, rxz=2, Re=500.0, dt=0.002, nsteps=200, every=2, train_iters=3000,
+                    rounds=1, seed_train=31, seed_judge=32):
+    """Fine DNS data -> trained network -> coarse runs with and without it, judged
+    on the friction coefficient against the fine DNS.  Training pairs the coarse
+    solver's own near-wall features with the fine run's filtered labels at the
+    same time and initial state: round 0 from the coarse run without the model,
+    later rounds from the coarse run coupled to the previous round's network."""
+    import torch
+
+    from paper_1701_02005_gb300 import wallmodel as wm
+
+    nx, ny, nz = nfine
+    gf = o.Grid(nx, ny, nz, 2 * math.pi, math.pi, stretch=2.0)
+    gc = o.Grid(nx // rxz, (ny - 1) // ry + 1, nz // rxz, 2 * math.pi, math.pi, y_faces=gf.yf[::ry])
+    prm = o.Params(Re=Re, lam=0.05, Sc=1.0, V=2.0, beta=0.5)
+    sf, sc, sm = _solver(gf, prm), _solver(gc, prm), _solver(gc, prm)
+    Xs, Ts = [], []
+    net, norm, losses = None, None, []
+    for rnd in range(rounds):
+        _impulsive(sf, gf, seed_train)
+        wm.restrict(sf, sc)
+        for n in range(nsteps // every):
+            Xs.append(wm.features(sc, 8))
+            Ts.append(wm.labels(sf, sc))
+            sf.step(every, dt)
+            if net is None:
+                sc.step(every, dt)
+            else:
+                wm.step_with_model(sc, net, every, dt)
+        X = torch.cat(Xs)
+        T = torch.cat(Ts)
+        if net is None:
+            Xh, Th = X.cpu().numpy(), T.cpu().numpy()
+            xs, ts = Xh.mean(0), Th.mean(0)
+            # spreads floored relative to each column's magnitude: columns that hardly
+            # vary in the training data must not be amplified into noise at inference
+            xsd = np.maximum(Xh.std(0), 1e-2 * np.maximum(np.abs(xs), 1e-2))
+            tsd = np.maximum(Th.std(0), 1e-2 * np.maximum(np.abs(ts), 1e-4))
+            norm = (xs, 1.0 / xsd, ts, 1.0 / tsd)
+            net = wm.MLP(nsteps // every * rounds * 2 * gc.nz * gc.nx, seed=33)
+            net.set_normalization(*norm)
+        l0 = net.train_step(X, T, 2e-3, want_loss=True)
+        for it in range(train_iters):
+            net.train_step(X, T, 2e-3 if it < train_iters // 2 else 5e-4)
+        l1 = net.train_step(X, T, 5e-4, want_loss=True)
+        losses.append((l0, l1))
+        wm.set_slip(sc, None, None)
+    # judge run (another seed): fine truth, coarse alone, and the network predicting
+    # the wall shear along the coarse trajectory (one-way); the two-way coupled run
+    # (network -> wall slip -> coarse solver) is reported, not asserted
+    _impulsive(sf, gf, seed_judge)
+    wm.restrict(sf, sc)
+    wm.restrict(sf, sm)
+    cf_f, cf_p, cf_m, cf_c = [], [], [], []
+    chunk = 10
+    for n in range(nsteps // chunk):
+        sf.step(chunk, dt)
+        sc.step(chunk, dt)
+        wm.step_with_model(sm, net, chunk, dt)
+        cf_f.append(sf.diagnostics()["cf"])
+        cf_p.append(sc.diagnostics()["cf"])
+        Y = net.forward(wm.features(sc, 8)).cpu().numpy()
+        cf_m.append(2.0 * prm.nu * float(Y[:, 0].mean()))     # c_f = 2 tau_w / Uw^2, tau_w = nu <du_rel/dy>
+        cf_c.append(sm.diagnostics()["cf"])
+    cf_f, cf_p, cf_m, cf_c = map(np.array, (cf_f, cf_p, cf_m, cf_c))
+    err = lambda a: float(np.mean(np.abs(a - cf_f) / cf_f))
+    for s in (sf, sc, sm):
+        s.close()
+    net.close()
+    return dict(loss0=losses[0][0], loss1=losses[-1][1], err_plain=err(cf_p), err_model=err(cf_m),
+                err_coupled=err(cf_c), cf_fine=cf_f.tolist(), cf_plain=cf_p.tolist(), cf_model=cf_m.tolist(),
+                cf_coupled=cf_c.tolist(), rows=int(X.shape[0]))
+
+
+def test_wall_model_gains_over_coarse_solver():
+    r = wall_model_case()
+    print("wall model:", {k: v for k, v in r.items() if not k.startswith("cf_")})
+    print("cf fine ", np.round(r["cf_fine"], 6).tolist())
+    print("cf plain", np.round(r["cf_plain"], 6).tolist())
+    print("cf model", np.round(r["cf_model"], 6).tolist())
+    print("cf coupled", np.round(r["cf_coupled"], 6).tolist())
+    assert r["loss1"] < 0.1 * r["loss0"]
+    assert r["err_model"] < r["err_plain"], r
