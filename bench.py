@@ -269,6 +269,24 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
+def reduce_times(t, dist):
+    """Max of the per-rank timed-region durations (every rank runs its own replica)."""
+    if dist is None:
+        return t
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    tt = torch.tensor([t], dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_value(cells_per_rank, steps, world, t_max):
+    """Cell-steps/s of all ranks together: every rank advances its own case."""
+    return world * cells_per_rank * steps / t_max
+
+
+# --------------------------------------------------------------------------
 def run_ours(args):
     import numpy as np
     import torch
@@ -310,14 +328,10 @@ def run_ours(args):
     s.synchronize()
     barrier()
     clocks = clk.stop()
-    t = e0.elapsed_time(e1) / 1e3
-    if dist is not None:
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = reduce_times(e0.elapsed_time(e1) / 1e3, dist)
     diag = s.diagnostics()
     n_cells = cells()
-    value = world * n_cells * K / t
+    value = whole_job_value(n_cells, K, world, t)
 
     # per-launch-site timing with CUDA events on the library's stream
     nprof = max(2, min(5, K))

@@ -134,8 +134,10 @@ __global__ void __launch_bounds__(128) k_mom_mixed(Fields<float> f, Shadows sh, 
 }
 
 // ---------------------------------------------------------------------------
-// Ion right-hand sides: FP32 fluctuation fluxes + FP64 per-plane reference
-// constant, r_c = Rref(j) + dt [gam H' + zet H'_old + alp D L_y c'] in FP64.
+// Ion right-hand sides: FP32 fluctuation fluxes; the CN right-hand side is
+// split as r_c = Rref(j) + r', Rref the per-plane FP64 reference part (solved
+// once per substage on the host, see k_cn_ion_mixed) and
+// r' = dt [gam H' + zet H'_old + alp D L_y c'] stored in FP32.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_ion_mixed(Fields<float> f, double* __restrict__ rcp, double* __restrict__ rcm,
                                                    Shadows sh, MixedRefs R, Geo g, MetricsF mt, CoefF cf, int l) {
@@ -193,32 +195,36 @@ __global__ void __launch_bounds__(128) k_ion_mixed(Fields<float> f, double* __re
     const float H = -((Fx_ip - Fx_i) * idx + (Fy_jp - Fy_j) * idyj + (Fz_kp - Fz_k) * idz);
     const float Ly = (has_dn ? lo * (cym_ - cc) : 0.f) + (has_up ? hi * (cyp_ - cc) : 0.f);
     float* Hc = ion == 0 ? sh.Hcp : sh.Hcm;
-    double* rc = ion == 0 ? rcp : rcm;
-    const double* Rref = (ion == 0 ? R.Rref_p : R.Rref_m) + (size_t)l * nyc;
+    float* rc = reinterpret_cast<float*>(ion == 0 ? rcp : rcm);
     const float Ho = Hc[c0];
-    rc[c0] = Rref[j] + (double)(dt * (gam * H + zet * Ho + alp * D * Ly));
+    rc[c0] = dt * (gam * H + zet * Ho + alp * D * Ly);
     Hc[c0] = H;
   }
 }
 
 // ---------------------------------------------------------------------------
-// FP64 ion Crank-Nicolson solve with the FP32 shadow written back:
-// c <- c + x (FP64), c' <- (float)(c - c_ref).
+// Ion Crank-Nicolson solve.  (I - s L_y) dc = Rref + r' is linear, so
+// dc = dC_ref + (I - s L_y)^-1 r' with dC_ref the FP64 reference increment of
+// the substage (a 1-D solve done on the host).  The fluctuation part runs in
+// FP32; only the state update c <- c + dC_ref + x' (and the shadow
+// c' = c - c_ref) is FP64.
 // ---------------------------------------------------------------------------
-__global__ void k_cn_ion_mixed(double* __restrict__ cp, double* __restrict__ rcp, float* __restrict__ sp,
-                               double* __restrict__ cm, double* __restrict__ rcm, float* __restrict__ sm,
-                               CNRows rows, MixedRefs R, int n, size_t P) {
+__global__ void k_cn_ion_mixed(double* __restrict__ cp, float* __restrict__ rcp, float* __restrict__ sp,
+                               double* __restrict__ cm, float* __restrict__ rcm, float* __restrict__ sm,
+                               CNRowsF rows, const double* __restrict__ dCp, const double* __restrict__ dCm,
+                               MixedRefs R, int n, size_t P) {
   constexpr int CH = 8;   // planes loaded ahead per sweep step
   const size_t line = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (line >= P) return;
   const bool plus = blockIdx.y == 0;
   double* q = plus ? cp : cm;
-  double* r = plus ? rcp : rcm;
+  float* r = plus ? rcp : rcm;
   float* s = plus ? sp : sm;
   const double* cref = plus ? R.cref64_p : R.cref64_m;
-  double d = 0.0;
+  const double* dC = plus ? dCp : dCm;
+  float d = 0.f;
   for (int jb = 0; jb < n; jb += CH) {
-    double rr[CH];
+    float rr[CH];
 #pragma unroll
     for (int u = 0; u < CH; ++u)
       if (jb + u < n) rr[u] = r[(size_t)(jb + u) * P + line];
@@ -231,9 +237,10 @@ __global__ void k_cn_ion_mixed(double* __restrict__ cp, double* __restrict__ rcp
       }
     }
   }
-  double x = 0.0;
+  float x = 0.f;
   for (int jb = n - 1; jb >= 0; jb -= CH) {
-    double dd[CH], qq[CH];
+    float dd[CH];
+    double qq[CH];
 #pragma unroll
     for (int u = 0; u < CH; ++u)
       if (jb - u >= 0) {
@@ -247,7 +254,7 @@ __global__ void k_cn_ion_mixed(double* __restrict__ cp, double* __restrict__ rcp
       if (j >= 0) {
         const size_t o = (size_t)j * P + line;
         x = dd[u] - rows.c[j] * x;
-        const double cn = qq[u] + x;
+        const double cn = (qq[u] + dC[j]) + (double)x;
         q[o] = cn;
         s[o] = (float)(cn - cref[j]);
       }
@@ -377,7 +384,7 @@ cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const Mi
 }
 
 cudaError_t launch_mixed_cn(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
-                            const CNRowsF& cell, const CNRowsF& face, const CNRows& ion, cudaStream_t s) {
+                            const CNRowsF& cell, const CNRowsF& face, const CNRowsF& ion, int l, cudaStream_t s) {
   const size_t P = (size_t)g.nz * g.nx;
   const int T = g.lc_cn ? g.lc_cn : 128;
   dim3 grd((unsigned)((P + T - 1) / T), 3, 1);
@@ -385,7 +392,8 @@ cudaError_t launch_mixed_cn(const Fields<float>& f, const Shadows& sh, const Mix
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 grd2((unsigned)((P + T - 1) / T), 2, 1);
-  k_cn_ion_mixed<<<grd2, T, 0, s>>>(f.cp, f.rcp, sh.cp, f.cm, f.rcm, sh.cm, ion, R, g.nyc, P);
+  k_cn_ion_mixed<<<grd2, T, 0, s>>>(f.cp, reinterpret_cast<float*>(f.rcp), sh.cp, f.cm, reinterpret_cast<float*>(f.rcm),
+                                    sh.cm, ion, R.Rref_p + (size_t)l * g.nyc, R.Rref_m + (size_t)l * g.nyc, R, g.nyc, P);
   return cudaGetLastError();
 }
 

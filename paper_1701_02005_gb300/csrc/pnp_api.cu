@@ -77,7 +77,7 @@ struct pnp_ctx {
   // mixed-precision path: FP32 shadows, FP32 metrics / velocity CN rows, reference profiles
   float *cpS, *cmS, *phiS, *HcpS, *HcmS;
   float* mf[8];      // idy, ih, lo_c, hi_c, lo_f, hi_f, wl, wu
-  float* cnF_d;      // [3 substages][2 kinds][a, c, m][ny]
+  float* cnF_d;      // [3 substages][3 kinds][a, c, m][ny]
   float *crefp_f, *crefm_f, *crfp_f, *crfm_f, *rhoref_f, *rhorf_f, *dPref_f, *Fvref_f;
   double *Rrefp_d, *Rrefm_d, *cref64p_d, *cref64m_d, *Phiref64_d, *meanrhs_d, *meanshift_d, *delta_d;
   double *Hrefp_d, *Hrefm_d;
@@ -137,7 +137,7 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
   float *HcpS = b.take<float>(nc), *HcmS = b.take<float>(nc);
   float* mf[8];
   for (int q = 0; q < 8; ++q) mf[q] = b.take<float>(ny);
-  float* cnF = b.take<float>(18 * (size_t)ny);
+  float* cnF = b.take<float>(27 * (size_t)ny);
   float *crefp = b.take<float>(ny), *crefm = b.take<float>(ny), *crfp = b.take<float>(ny), *crfm = b.take<float>(ny);
   float *rhoref = b.take<float>(ny), *rhorf = b.take<float>(ny), *dPref = b.take<float>(ny), *Fvref = b.take<float>(ny);
   double *Rrefp = b.take<double>(3 * (size_t)ny), *Rrefm = b.take<double>(3 * (size_t)ny);
@@ -353,12 +353,8 @@ int upload_cn(pnp_ctx* c, double dt) {
       }
     }
   }
-  std::vector<float> cnf(18 * (size_t)ny, 0.f);
-  for (int l = 0; l < 3; ++l)
-    for (int kind = 0; kind < 2; ++kind)
-      for (int a = 0; a < 3; ++a)
-        for (int j = 0; j < ny; ++j)
-          cnf[((size_t)(l * 2 + kind) * 3 + a) * ny + j] = (float)c->cn_h[((size_t)(l * 3 + kind) * 3 + a) * ny + j];
+  std::vector<float> cnf(27 * (size_t)ny, 0.f);
+  for (size_t q = 0; q < cnf.size(); ++q) cnf[q] = (float)c->cn_h[q];
   CK(cudaMemcpyAsync(c->cn_d, c->cn_h.data(), sizeof(double) * c->cn_h.size(), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->cnF_d, cnf.data(), sizeof(float) * cnf.size(), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -375,7 +371,7 @@ CNRows cn_rows(const pnp_ctx* c, int l, int kind) {
 
 CNRowsF cn_rows_f(const pnp_ctx* c, int l, int kind) {
   const size_t ny = c->g.ny;
-  const float* base = c->cnF_d + (size_t)(l * 2 + kind) * 3 * ny;
+  const float* base = c->cnF_d + (size_t)(l * 3 + kind) * 3 * ny;
   return CNRowsF{base, base + ny, base + 2 * ny};
 }
 
@@ -502,7 +498,7 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
   cudaError_t e = launch_mixed_rhs(f, sh, R, c->g, metrics_f(c), coef_f(c, st), l, c->stream);
   if (e != cudaSuccess) return e;
   mark(c);
-  e = launch_mixed_cn(f, sh, R, c->g, cn_rows_f(c, l, 0), cn_rows_f(c, l, 1), cn_rows(c, l, 2), c->stream);
+  e = launch_mixed_cn(f, sh, R, c->g, cn_rows_f(c, l, 0), cn_rows_f(c, l, 1), cn_rows_f(c, l, 2), l, c->stream);
   if (e != cudaSuccess) return e;
   mark(c);
   e = pressure_projection<float>(c, st.alp * dt, true);
@@ -626,13 +622,35 @@ int refresh_refs(pnp_ctx* c, double dt) {
     drop_graph(c);
   }
   if (!(c->refs_dt == dt)) {
-    // Rref(l, j) = dt alp_l (H_ref + D L_y c_ref): the reference part of the ion CN right-hand side
+    // the reference increments below need this dt's elimination factors
+    if (!(c->cn_dt == dt) || c->cn_h.size() != 27 * (size_t)ny) {
+      int r = upload_cn(c, dt);
+      if (r) return r;
+    }
+    // Rref(l, j) = dt alp_l (H_ref + D L_y c_ref): the reference part of the ion
+    // CN right-hand side; stored solved, dC_ref = (I - s_l L_y)^-1 Rref, with the
+    // substage's FP64 elimination factors (same as every ion line uses)
     std::vector<double> Rp(3 * (size_t)ny, 0.0), Rm(3 * (size_t)ny, 0.0);
     for (int l = 0; l < 3; ++l) {
       const double alp = kGam[l] + kZet[l];
-      for (int j = 0; j < nyc; ++j) {
-        Rp[(size_t)l * nyc + j] = dt * alp * (c->href_p[j] + c->ph.D * c->lyc_p[j]);
-        Rm[(size_t)l * nyc + j] = dt * alp * (c->href_m[j] + c->ph.D * c->lyc_m[j]);
+      const double* A = c->cn_h.data() + ((size_t)(l * 3 + 2) * 3 + 0) * ny;
+      const double* Cp = c->cn_h.data() + ((size_t)(l * 3 + 2) * 3 + 1) * ny;
+      const double* M = c->cn_h.data() + ((size_t)(l * 3 + 2) * 3 + 2) * ny;
+      for (int ion = 0; ion < 2; ++ion) {
+        const std::vector<double>& hr = ion == 0 ? c->href_p : c->href_m;
+        const std::vector<double>& ly = ion == 0 ? c->lyc_p : c->lyc_m;
+        double* out = (ion == 0 ? Rp.data() : Rm.data()) + (size_t)l * nyc;
+        double d = 0.0;
+        for (int j = 0; j < nyc; ++j) {
+          const double r = dt * alp * (hr[j] + c->ph.D * ly[j]);
+          d = (r - A[j] * d) * M[j];
+          out[j] = d;
+        }
+        double x = 0.0;
+        for (int j = nyc - 1; j >= 0; --j) {
+          x = out[j] - Cp[j] * x;
+          out[j] = x;
+        }
       }
     }
     CK(cudaMemcpyAsync(c->Rrefp_d, Rp.data(), sizeof(double) * 3 * nyc, cudaMemcpyHostToDevice, c->stream));
@@ -1120,7 +1138,7 @@ int pnp_autotune(pnp_ctx* c, double dt, int* cfg_out, double* ms_out) {
         launch_cn_solves<double>(fields<double>(c), c->g, cn_rows(c, 0, 0), cn_rows(c, 0, 1), cn_rows(c, 0, 2), c->stream);
       else
         launch_mixed_cn(fields<float>(c), shadows(c), mixed_refs(c), c->g, cn_rows_f(c, 0, 0), cn_rows_f(c, 0, 1),
-                        cn_rows(c, 0, 2), c->stream);
+                        cn_rows_f(c, 0, 2), 0, c->stream);
     }, reps);
     if (t < best[1]) { best[1] = t; pick[1] = T; }
   }

@@ -38,7 +38,7 @@ struct MixedRefs {
   const float* rhorf;             // face mean of rho_ref [ny]
   const float* dPref;             // Phi_ref_j - Phi_ref_{j-1} per interior face [ny]
   const float* Fvref;             // -K rhorf dPref / h: reference Coulomb force on v [ny]
-  const double *Rref_p, *Rref_m;  // [3][nyc]: dt alp_l (H_ref + D L_y c_ref)
+  const double *Rref_p, *Rref_m;  // [3][nyc]: reference increments (I - s_l L_y)^-1 dt alp_l (H_ref + D L_y c_ref)
   const double *cref64_p, *cref64_m, *Phiref64;   // exact references [nyc]
   const double* mean_rhs;         // -q rho_ref [nyc]: FP64 (0,0) mode source of Eq. (4)
   const double* mean_shift;       // V y_c - Phi_ref [nyc]
@@ -48,7 +48,7 @@ struct MixedRefs {
 cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
                              const MetricsF& m, const CoefF& cf, int l, cudaStream_t s);
 cudaError_t launch_mixed_cn(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
-                            const CNRowsF& cell, const CNRowsF& face, const CNRows& ion, cudaStream_t s);
+                            const CNRowsF& cell, const CNRowsF& face, const CNRowsF& ion, int l, cudaStream_t s);
 cudaError_t launch_plane_means3(const double* a, const double* b, const double* c, int nplanes, size_t P,
                                 double* oa, double* ob, double* oc, cudaStream_t s);
 cudaError_t launch_make_shadows(const double* cp, const double* cm, const double* Phi, const double* Hcp,
