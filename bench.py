@@ -57,7 +57,7 @@ def site_cost(site, precision):
         }
     else:
         table = {
-            "rhs": (120, 4), "cn_thomas": (148, 12),
+            "rhs": (112, 0), "cn_thomas": (124, 10),
             "p_fftx": (12 + 8 * half, 0), "p_fftz": (16 * half, 0), "p_thomas": (48 * half, 14 * half),
             "p_ifftz": (16 * half, 0), "p_ifftx": (8 * half + 4, 0), "project": (36, 0),
             "e_fftx": (8 + 8 * half, 0), "e_fftz": (16 * half, 0), "e_thomas": (48 * half, 14 * half),
