@@ -23,10 +23,15 @@ namespace pnp {
 __device__ __forceinline__ float Lf(const float* p, size_t i) { return __ldg(p + i); }
 
 // ---------------------------------------------------------------------------
-// Momentum right-hand sides, FP32 (u, w on every cell; v on faces j >= 1).
+// Right-hand sides in FP32, one pass per cell: momentum (u, w on every cell;
+// v on faces j >= 1), then both ions, reusing the loaded velocities and
+// shadows.  For the ions the CN right-hand side is split as r_c = Rref(j) + r',
+// Rref the per-plane FP64 reference part (solved once per substage on the
+// host, see k_cn_ion_mixed) and r' = dt [gam H' + zet H'_old + alp D L_y c']
+// stored in FP32.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_mom_mixed(Fields<float> f, Shadows sh, MixedRefs R, Geo g, MetricsF mt,
-                                                   CoefF cf) {
+__global__ void __launch_bounds__(128) k_rhs_mixed(Fields<float> f, float* __restrict__ rcp, float* __restrict__ rcm,
+                                                   Shadows sh, MixedRefs R, Geo g, MetricsF mt, CoefF cf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y * blockDim.y + threadIdx.y;
   const int j = blockIdx.z;
@@ -51,8 +56,11 @@ __global__ void __launch_bounds__(128) k_mom_mixed(Fields<float> f, Shadows sh, 
   const float wym = has_dn ? Lf(f.w, c0 - P) : 0.f, wyp = has_up ? Lf(f.w, c0 + P) : 0.f;
   const float vb = Lf(f.v, c0), vt = Lf(f.v, c0 + P);
   const float p0 = Lf(f.p, c0);
-  const float ph0 = Lf(sh.phi, c0);
-  const float rho0 = Lf(sh.cp, c0) - Lf(sh.cm, c0);   // rho' at the centre
+  const float ph0 = Lf(sh.phi, c0), phxm = Lf(sh.phi, cxm), phxp = Lf(sh.phi, cxp);
+  const float phzm = Lf(sh.phi, czm), phzp = Lf(sh.phi, czp);
+  const float phym = has_dn ? Lf(sh.phi, c0 - P) : 0.f, phyp = has_up ? Lf(sh.phi, c0 + P) : 0.f;
+  const float cp0 = Lf(sh.cp, c0), cm0 = Lf(sh.cm, c0);
+  const float rho0 = cp0 - cm0;   // rho' at the centre
   const float rref = R.rho_ref[j];
 
   // u at (x-face i, y-centre j, z-centre k)
@@ -69,7 +77,7 @@ __global__ void __launch_bounds__(128) k_mom_mixed(Fields<float> f, Shadows sh, 
     const float az = (wfkp * 0.5f * (u0 + uzp) - wfk * 0.5f * (uzm + u0)) * idz;
     const float lap = (uxp - 2.f * u0 + uxm) * idx2 + (uzp - 2.f * u0 + uzm) * idz2;
     const float rhom = Lf(sh.cp, cxm) - Lf(sh.cm, cxm);
-    const float fu = -K * (rref + 0.5f * (rhom + rho0)) * (ph0 - Lf(sh.phi, cxm)) * idx;
+    const float fu = -K * (rref + 0.5f * (rhom + rho0)) * (ph0 - phxm) * idx;
     const float H = -(ax + ay + az) + nu * lap + fu;
     const float ub = f.wall_u ? f.wall_u[(size_t)k * nx + i] : -Uw;
     const float ut = f.wall_u ? f.wall_u[P + (size_t)k * nx + i] : Uw;
@@ -93,7 +101,7 @@ __global__ void __launch_bounds__(128) k_mom_mixed(Fields<float> f, Shadows sh, 
     const float ax = (ufip * 0.5f * (w0 + wxp) - ufi * 0.5f * (wxm + w0)) * idx;
     const float lap = (wxp - 2.f * w0 + wxm) * idx2 + (wzp - 2.f * w0 + wzm) * idz2;
     const float rhom = Lf(sh.cp, czm) - Lf(sh.cm, czm);
-    const float fw = -K * (rref + 0.5f * (rhom + rho0)) * (ph0 - Lf(sh.phi, czm)) * idz;
+    const float fw = -K * (rref + 0.5f * (rhom + rho0)) * (ph0 - phzm) * idz;
     const float H = -(ax + ay + az) + nu * lap + fw;
     const float wb = f.wall_w ? f.wall_w[(size_t)k * nx + i] : 0.f;
     const float wt = f.wall_w ? f.wall_w[P + (size_t)k * nx + i] : 0.f;
@@ -122,7 +130,7 @@ __global__ void __launch_bounds__(128) k_mom_mixed(Fields<float> f, Shadows sh, 
     // Coulomb force: reference-reference part is the FP64 constant Fvref
     const float rhod = Lf(sh.cp, d0) - Lf(sh.cm, d0);
     const float rpf = 0.5f * (rhod + rho0);                 // rho' on the face
-    const float dphi = ph0 - Lf(sh.phi, d0);                // phi' difference
+    const float dphi = ph0 - phym;                          // phi' difference
     const float fv = R.Fvref[j] - K * ihj * (R.rhorf[j] * dphi + rpf * (R.dPref[j] + dphi));
     const float H = -(ax + ay + az) + nu * lap + fv;
     const float Ly = mt.lo_f[j] * (vym - v0) + mt.hi_f[j] * (vyp - v0);
@@ -131,74 +139,47 @@ __global__ void __launch_bounds__(128) k_mom_mixed(Fields<float> f, Shadows sh, 
     f.rv[c0] = dt * (gam * H + zet * Ho - alp * gp + alp * nu * Ly);
     f.Hv[c0] = H;
   }
-}
 
-// ---------------------------------------------------------------------------
-// Ion right-hand sides: FP32 fluctuation fluxes; the CN right-hand side is
-// split as r_c = Rref(j) + r', Rref the per-plane FP64 reference part (solved
-// once per substage on the host, see k_cn_ion_mixed) and
-// r' = dt [gam H' + zet H'_old + alp D L_y c'] stored in FP32.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_ion_mixed(Fields<float> f, double* __restrict__ rcp, double* __restrict__ rcm,
-                                                   Shadows sh, MixedRefs R, Geo g, MetricsF mt, CoefF cf, int l) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int k = blockIdx.y * blockDim.y + threadIdx.y;
-  const int j = blockIdx.z;
-  if (i >= g.nx || k >= g.nz) return;
-  const int nx = g.nx, nz = g.nz, nyc = g.nyc;
-  const int im = i ? i - 1 : nx - 1, ip = (i + 1 == nx) ? 0 : i + 1;
-  const int km = k ? k - 1 : nz - 1, kp = (k + 1 == nz) ? 0 : k + 1;
-  const bool has_dn = j > 0, has_up = j < nyc - 1;
-  const float idx = cf.idx, idz = cf.idz;
-  const size_t c0 = cidx(j, k, i, nz, nx);
-  const size_t cxm = cidx(j, k, im, nz, nx), cxp = cidx(j, k, ip, nz, nx);
-  const size_t czm = cidx(j, km, i, nz, nx), czp = cidx(j, kp, i, nz, nx);
-  const size_t P = (size_t)nz * nx;
-  const float D = cf.D;
-  const float dt = cf.dt, gam = cf.gam, zet = cf.zet, alp = cf.alp;
-  const float idyj = mt.idy[j], ihj = mt.ih[j], ihjp = mt.ih[j + 1];
-  const float lo = mt.lo_c[j], hi = mt.hi_c[j];
-
-  const float ux_i = Lf(f.u, c0), ux_ip = Lf(f.u, cxp);
-  const float wz_k = Lf(f.w, c0), wz_kp = Lf(f.w, czp);
-  const float vb = Lf(f.v, c0), vt = Lf(f.v, c0 + P);
-  const float p0 = Lf(sh.phi, c0), pxm = Lf(sh.phi, cxm), pxp = Lf(sh.phi, cxp);
-  const float pzm = Lf(sh.phi, czm), pzp = Lf(sh.phi, czp);
-  const float pym = has_dn ? Lf(sh.phi, c0 - P) : 0.f, pyp = has_up ? Lf(sh.phi, c0 + P) : 0.f;
-
+  // ---- ions: FP32 fluctuation fluxes (the reference-reference part is in Rref) ----
+  {
+    const float D = cf.D;
+    const float ihj = mt.ih[j], ihjp = mt.ih[j + 1];
+    const float lo = mt.lo_c[j], hi = mt.hi_c[j];
 #pragma unroll
-  for (int ion = 0; ion < 2; ++ion) {
-    const float* c = ion == 0 ? sh.cp : sh.cm;
-    const float s = ion == 0 ? 1.f : -1.f;
-    const float cr = ion == 0 ? R.cref_p[j] : R.cref_m[j];
-    const float* crf = ion == 0 ? R.crf_p : R.crf_m;
-    const float cc = Lf(c, c0), cxm_ = Lf(c, cxm), cxp_ = Lf(c, cxp), czm_ = Lf(c, czm), czp_ = Lf(c, czp);
-    const float cym_ = has_dn ? Lf(c, c0 - P) : 0.f, cyp_ = has_up ? Lf(c, c0 + P) : 0.f;
-    // x and z faces: the reference is uniform in the plane, so only c', phi' differences appear
-    float ca = cr + 0.5f * (cxm_ + cc), cb = cr + 0.5f * (cc + cxp_);
-    const float Fx_i = ux_i * ca - D * (cc - cxm_) * idx - s * D * ca * (p0 - pxm) * idx;
-    const float Fx_ip = ux_ip * cb - D * (cxp_ - cc) * idx - s * D * cb * (pxp - p0) * idx;
-    ca = cr + 0.5f * (czm_ + cc);
-    cb = cr + 0.5f * (cc + czp_);
-    const float Fz_k = wz_k * ca - D * (cc - czm_) * idz - s * D * ca * (p0 - pzm) * idz;
-    const float Fz_kp = wz_kp * cb - D * (czp_ - cc) * idz - s * D * cb * (pzp - p0) * idz;
-    // y faces (advection + migration; the reference-reference migration is in Rref)
-    float Fy_j = 0.f, Fy_jp = 0.f;
-    if (has_dn) {
-      const float cpf = 0.5f * (cym_ + cc), dph = p0 - pym;
-      Fy_j = vb * (crf[j] + cpf) - s * D * (crf[j] * dph + cpf * (R.dPref[j] + dph)) * ihj;
+    for (int ion = 0; ion < 2; ++ion) {
+      const float* c = ion == 0 ? sh.cp : sh.cm;
+      const float s = ion == 0 ? 1.f : -1.f;
+      const float cr = ion == 0 ? R.cref_p[j] : R.cref_m[j];
+      const float* crf = ion == 0 ? R.crf_p : R.crf_m;
+      const float cc = ion == 0 ? cp0 : cm0;
+      const float cxm_ = Lf(c, cxm), cxp_ = Lf(c, cxp), czm_ = Lf(c, czm), czp_ = Lf(c, czp);
+      const float cym_ = has_dn ? Lf(c, c0 - P) : 0.f, cyp_ = has_up ? Lf(c, c0 + P) : 0.f;
+      // x and z faces: the reference is uniform in the plane, so only c', phi' differences appear
+      float ca = cr + 0.5f * (cxm_ + cc), cb = cr + 0.5f * (cc + cxp_);
+      const float Fx_i = u0 * ca - D * (cc - cxm_) * idx - s * D * ca * (ph0 - phxm) * idx;
+      const float Fx_ip = uxp * cb - D * (cxp_ - cc) * idx - s * D * cb * (phxp - ph0) * idx;
+      ca = cr + 0.5f * (czm_ + cc);
+      cb = cr + 0.5f * (cc + czp_);
+      const float Fz_k = w0 * ca - D * (cc - czm_) * idz - s * D * ca * (ph0 - phzm) * idz;
+      const float Fz_kp = wzp * cb - D * (czp_ - cc) * idz - s * D * cb * (phzp - ph0) * idz;
+      // y faces: advection + migration
+      float Fy_j = 0.f, Fy_jp = 0.f;
+      if (has_dn) {
+        const float cpf = 0.5f * (cym_ + cc), dph = ph0 - phym;
+        Fy_j = vb * (crf[j] + cpf) - s * D * (crf[j] * dph + cpf * (R.dPref[j] + dph)) * ihj;
+      }
+      if (has_up) {
+        const float cpf = 0.5f * (cc + cyp_), dph = phyp - ph0;
+        Fy_jp = vt * (crf[j + 1] + cpf) - s * D * (crf[j + 1] * dph + cpf * (R.dPref[j + 1] + dph)) * ihjp;
+      }
+      const float H = -((Fx_ip - Fx_i) * idx + (Fy_jp - Fy_j) * idyj + (Fz_kp - Fz_k) * idz);
+      const float Ly = (has_dn ? lo * (cym_ - cc) : 0.f) + (has_up ? hi * (cyp_ - cc) : 0.f);
+      float* Hc = ion == 0 ? sh.Hcp : sh.Hcm;
+      float* rc = ion == 0 ? rcp : rcm;
+      const float Ho = Hc[c0];
+      rc[c0] = dt * (gam * H + zet * Ho + alp * D * Ly);
+      Hc[c0] = H;
     }
-    if (has_up) {
-      const float cpf = 0.5f * (cc + cyp_), dph = pyp - p0;
-      Fy_jp = vt * (crf[j + 1] + cpf) - s * D * (crf[j + 1] * dph + cpf * (R.dPref[j + 1] + dph)) * ihjp;
-    }
-    const float H = -((Fx_ip - Fx_i) * idx + (Fy_jp - Fy_j) * idyj + (Fz_kp - Fz_k) * idz);
-    const float Ly = (has_dn ? lo * (cym_ - cc) : 0.f) + (has_up ? hi * (cyp_ - cc) : 0.f);
-    float* Hc = ion == 0 ? sh.Hcp : sh.Hcm;
-    float* rc = reinterpret_cast<float*>(ion == 0 ? rcp : rcm);
-    const float Ho = Hc[c0];
-    rc[c0] = dt * (gam * H + zet * Ho + alp * D * Ly);
-    Hc[c0] = H;
   }
 }
 
@@ -376,10 +357,8 @@ cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const Mi
   const int bx = g.lc_rhs_bx ? g.lc_rhs_bx : 32, by = 128 / bx;
   dim3 blk(bx, by, 1);
   dim3 grd((g.nx + bx - 1) / bx, (g.nz + by - 1) / by, g.nyc);
-  k_mom_mixed<<<grd, blk, 0, s>>>(f, sh, R, g, m, cf);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_ion_mixed<<<grd, blk, 0, s>>>(f, f.rcp, f.rcm, sh, R, g, m, cf, l);
+  (void)l;
+  k_rhs_mixed<<<grd, blk, 0, s>>>(f, reinterpret_cast<float*>(f.rcp), reinterpret_cast<float*>(f.rcm), sh, R, g, m, cf);
   return cudaGetLastError();
 }
 

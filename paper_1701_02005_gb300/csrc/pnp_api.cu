@@ -84,6 +84,12 @@ struct pnp_ctx {
   // spectral elimination factors (grid-only): c'_j and 1/pivot_j per spectral point
   double *spc_cprN, *spc_invN, *spc_cprD, *spc_invD;
   cplx<double>* dscr;   // FP64 forward-sweep values of the spectral solves
+  // the potential pipeline runs concurrently with the pressure pipeline on an
+  // auxiliary stream, with its own spectral buffers
+  void* spec2 = nullptr;
+  cplx<double>* dscr2 = nullptr;
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // wall model: per-column wall velocities [2][P] (velocity precision), feature / output rows
   void *wall_u, *wall_w;
   float *featX, *featY;
@@ -147,6 +153,8 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
   double *fcN = b.take<double>(nspec), *fiN = b.take<double>(nspec), *fcD = b.take<double>(nspec),
          *fiD = b.take<double>(nspec);
   cplx<double>* dscr = b.take<cplx<double>>(nspec);
+  void* spec2 = b.take<cplx<double>>(nspec);
+  cplx<double>* dscr2 = b.take<cplx<double>>(nspec);
   const size_t P2 = 2 * (size_t)nz * nx;
   void* wallu = b.take<char>(P2 * tv);
   void* wallw = b.take<char>(P2 * tv);
@@ -154,6 +162,8 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
   float* fY = b.take<float>(P2 * 5);
   if (c) {
     c->dscr = dscr;
+    c->spec2 = spec2;
+    c->dscr2 = dscr2;
     c->wall_u = wallu; c->wall_w = wallw; c->featX = fX; c->featY = fY;
     c->spc_cprN = fcN; c->spc_invN = fiN; c->spc_cprD = fcD; c->spc_invD = fiD;
     c->cpS = cpS; c->cmS = cmS; c->phiS = phiS; c->HcpS = HcpS; c->HcmS = HcmS;
@@ -412,18 +422,24 @@ Fields<TV> fields(const pnp_ctx* c) {
 
 // Spectral part of a separable Poisson solve: z-FFT, Thomas per (m, n), inverse z-FFT.
 template <typename T>
-cudaError_t spectral_solve(pnp_ctx* c, cplx<T>* spec, const cplx<T>* twz, bool neumann) {
-  cudaError_t e = launch_fft_z<T>(spec, twz, c->g, false, c->stream);
+cudaError_t spectral_solve(pnp_ctx* c, cplx<T>* spec, const cplx<T>* twz, bool neumann, cudaStream_t st,
+                           cplx<double>* dscr) {
+  cudaError_t e = launch_fft_z<T>(spec, twz, c->g, false, st);
   if (e != cudaSuccess) return e;
   mark(c);
   const double scale = 1.0 / ((double)c->g.nx * (double)c->g.nz);
-  e = launch_spec_thomas<T>(spec, c->dscr, neumann ? c->spc_cprN : c->spc_cprD, neumann ? c->spc_invN : c->spc_invD,
-                            yrows(c, neumann), c->g, scale, neumann, c->stream);
+  e = launch_spec_thomas<T>(spec, dscr, neumann ? c->spc_cprN : c->spc_cprD, neumann ? c->spc_invN : c->spc_invD,
+                            yrows(c, neumann), c->g, scale, neumann, st);
   if (e != cudaSuccess) return e;
   mark(c);
-  e = launch_fft_z<T>(spec, twz, c->g, true, c->stream);
+  e = launch_fft_z<T>(spec, twz, c->g, true, st);
   mark(c);
   return e;
+}
+
+template <typename T>
+cudaError_t spectral_solve(pnp_ctx* c, cplx<T>* spec, const cplx<T>* twz, bool neumann) {
+  return spectral_solve<T>(c, spec, twz, neumann, c->stream, c->dscr);
 }
 
 // Pressure correction (Neumann) from div(u_hat) / scale and the projection.
@@ -454,22 +470,79 @@ cudaError_t pressure_projection(pnp_ctx* c, double scale, bool update_p) {
 
 // Eq. (4): L phi = -(c+ - c-) / (2 lam^2), phi = 0 on the walls; Phi = V y + phi (FP64).
 template <typename TV>
-cudaError_t potential_solve(pnp_ctx* c) {
+cudaError_t potential_solve(pnp_ctx* c, cudaStream_t st, void* spec_buf, cplx<double>* dscr) {
   const Metrics m = metrics(c);
-  cplx<double>* spec = (cplx<double>*)c->spec;
+  cplx<double>* spec = (cplx<double>*)spec_buf;
   const cplx<double>* twx = (const cplx<double>*)c->twx_d;
   const cplx<double>* twp = (const cplx<double>*)c->twp_d;
   const cplx<double>* twz = (const cplx<double>*)c->twz_d;
   cudaError_t e = launch_fft_x_fwd<double, TV>(PoissonSrc::Charge, nullptr, nullptr, nullptr, c->cp, c->cm, nullptr,
-                                               c->ph.q, c->g, m, spec, twx, twp, c->stream);
+                                               c->ph.q, c->g, m, spec, twx, twp, st);
   if (e != cudaSuccess) return e;
   mark(c);
-  e = spectral_solve<double>(c, spec, twz, false);
+  e = spectral_solve<double>(c, spec, twz, false, st, dscr);
   if (e != cudaSuccess) return e;
-  e = launch_fft_x_inv<double, double>(PoissonDst::Potential, spec, c->g, m, twx, twp, c->ph.V, c->Phi, c->stream);
+  e = launch_fft_x_inv<double, double>(PoissonDst::Potential, spec, c->g, m, twx, twp, c->ph.V, c->Phi, st);
   mark(c);
   return e;
 }
+
+template <typename TV>
+cudaError_t potential_solve(pnp_ctx* c) {
+  return potential_solve<TV>(c, c->stream, c->spec, c->dscr);
+}
+
+// Mixed potential: FP32 FFT of the fluctuating charge, FP64 y-solves and (0,0) mode.
+cudaError_t potential_mixed(pnp_ctx* c, cudaStream_t st, void* spec_buf, cplx<double>* dscr) {
+  const Shadows sh = shadows(c);
+  const Metrics m = metrics(c);
+  cplx<float>* spec = (cplx<float>*)spec_buf;
+  const cplx<float>* twx = (const cplx<float>*)c->twx_f;
+  const cplx<float>* twp = (const cplx<float>*)c->twp_f;
+  const cplx<float>* twz = (const cplx<float>*)c->twz_f;
+  cudaError_t e = launch_fft_x_fwd<float, float>(PoissonSrc::ChargeShadow, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                 nullptr, c->ph.q, c->g, m, spec, twx, twp, st, sh.cp, sh.cm);
+  if (e != cudaSuccess) return e;
+  mark(c);
+  e = launch_fft_z<float>(spec, twz, c->g, false, st);
+  if (e != cudaSuccess) return e;
+  mark(c);
+  const double scale = 1.0 / ((double)c->g.nx * (double)c->g.nz);
+  e = launch_spec_thomas<float>(spec, dscr, c->spc_cprD, c->spc_invD, yrows(c, false), c->g, scale, false, st,
+                                c->meanrhs_d, c->meanshift_d, c->delta_d);
+  if (e != cudaSuccess) return e;
+  mark(c);
+  e = launch_fft_z<float>(spec, twz, c->g, true, st);
+  if (e != cudaSuccess) return e;
+  mark(c);
+  e = launch_fft_x_inv<float, float>(PoissonDst::PotentialShadow, spec, c->g, m, twx, twp, 0.0, sh.phi, st, c->delta_d);
+  mark(c);
+  return e;
+}
+
+// Pressure projection on the main stream and the potential solve, which
+// depends only on the ions of this substage, on the auxiliary stream; joined
+// before the substage ends.  Sequential when profiling (site timing).
+template <typename TV>
+cudaError_t poisson_pair(pnp_ctx* c, double scale) {
+  auto pot = [&](cudaStream_t st, void* spec, cplx<double>* dscr) {
+    return c->precision == PNP_FP64 ? potential_solve<TV>(c, st, spec, dscr) : potential_mixed(c, st, spec, dscr);
+  };
+  if (c->prof) {
+    cudaError_t e = pressure_projection<TV>(c, scale, true);
+    if (e != cudaSuccess) return e;
+    return pot(c->stream, c->spec, c->dscr);
+  }
+  cudaError_t e = cudaEventRecord(c->ev_fork, c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+  if (e == cudaSuccess) e = pot(c->aux, c->spec2, c->dscr2);
+  if (e == cudaSuccess) e = pressure_projection<TV>(c, scale, true);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->aux);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+  return e;
+}
+
+
 
 template <typename TV>
 cudaError_t substage(pnp_ctx* c, double dt, int l) {
@@ -482,9 +555,7 @@ cudaError_t substage(pnp_ctx* c, double dt, int l) {
   e = launch_cn_solves<TV>(f, c->g, cn_rows(c, l, 0), cn_rows(c, l, 1), cn_rows(c, l, 2), c->stream);
   if (e != cudaSuccess) return e;
   mark(c);
-  e = pressure_projection<TV>(c, st.alp * dt, true);
-  if (e != cudaSuccess) return e;
-  return potential_solve<TV>(c);
+  return poisson_pair<TV>(c, st.alp * dt);
 }
 
 // Mixed-precision substage (policy in k_mixed.cu).
@@ -501,32 +572,7 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
   e = launch_mixed_cn(f, sh, R, c->g, cn_rows_f(c, l, 0), cn_rows_f(c, l, 1), cn_rows_f(c, l, 2), l, c->stream);
   if (e != cudaSuccess) return e;
   mark(c);
-  e = pressure_projection<float>(c, st.alp * dt, true);
-  if (e != cudaSuccess) return e;
-  // potential: FP32 FFT of the fluctuating charge, FP64 y-solves and (0,0) mode
-  cplx<float>* spec = (cplx<float>*)c->spec;
-  const cplx<float>* twx = (const cplx<float>*)c->twx_f;
-  const cplx<float>* twp = (const cplx<float>*)c->twp_f;
-  const cplx<float>* twz = (const cplx<float>*)c->twz_f;
-  e = launch_fft_x_fwd<float, float>(PoissonSrc::ChargeShadow, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                     c->ph.q, c->g, m, spec, twx, twp, c->stream, sh.cp, sh.cm);
-  if (e != cudaSuccess) return e;
-  mark(c);
-  e = launch_fft_z<float>(spec, twz, c->g, false, c->stream);
-  if (e != cudaSuccess) return e;
-  mark(c);
-  const double scale = 1.0 / ((double)c->g.nx * (double)c->g.nz);
-  e = launch_spec_thomas<float>(spec, c->dscr, c->spc_cprD, c->spc_invD, yrows(c, false), c->g, scale, false, c->stream,
-                                c->meanrhs_d, c->meanshift_d, c->delta_d);
-  if (e != cudaSuccess) return e;
-  mark(c);
-  e = launch_fft_z<float>(spec, twz, c->g, true, c->stream);
-  if (e != cudaSuccess) return e;
-  mark(c);
-  e = launch_fft_x_inv<float, float>(PoissonDst::PotentialShadow, spec, c->g, m, twx, twp, 0.0, sh.phi, c->stream,
-                                     c->delta_d);
-  mark(c);
-  return e;
+  return poisson_pair<float>(c, st.alp * dt);
 }
 
 cudaError_t one_step(pnp_ctx* c, double dt) {
@@ -737,8 +783,14 @@ int pnp_init_grid(pnp_ctx** out, int nx, int ny, int nz, double Lx, double Lz, d
     const double s = j * 2.0 / (ny - 1) - 1.0;
     c->yf[j] = stretch == 0.0 ? s : std::tanh(stretch * s) / std::tanh(stretch);
   }
+  if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    pnp_destroy(c);
+    return PNP_ERR_CUDA;
+  }
   r = upload_metrics(c);
-  if (r) { delete c; return r; }
+  if (r) { pnp_destroy(c); return r; }
   *out = c;
   return PNP_OK;
 }
@@ -1626,6 +1678,12 @@ const char* pnp_error_string(int code) {
 void pnp_destroy(pnp_ctx* c) {
   if (!c) return;
   drop_graph(c);
+  if (c->aux) {
+    cudaStreamSynchronize(c->aux);
+    cudaStreamDestroy(c->aux);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
 }
 
