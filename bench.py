@@ -57,10 +57,10 @@ def site_cost(site, precision):
         }
     else:
         table = {
-            "rhs": (112, 0), "cn_thomas": (124, 10),
-            "p_fftx": (12 + 8 * half, 0), "p_fftz": (16 * half, 0), "p_thomas": (48 * half, 14 * half),
+            "rhs": (88, 0), "cn_thomas": (116, 0),
+            "p_fftx": (12 + 8 * half, 0), "p_fftz": (16 * half, 0), "p_thomas": (64 * half, 0),
             "p_ifftz": (16 * half, 0), "p_ifftx": (8 * half + 4, 0), "project": (36, 0),
-            "e_fftx": (8 + 8 * half, 0), "e_fftz": (16 * half, 0), "e_thomas": (48 * half, 14 * half),
+            "e_fftx": (8 + 8 * half, 0), "e_fftz": (16 * half, 0), "e_thomas": (64 * half, 0),
             "e_ifftz": (16 * half, 0), "e_ifftx": (8 * half + 4, 0.25),
         }
     b, f = table[site]
@@ -453,7 +453,8 @@ def run_ours(args):
         "ensemble": ensemble,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": lps * K,
+        "gpu_launches": lps * K if lps > 0 else None,
+        "gpu_launches_per_step": lps if lps > 0 else None,
         "clocks": clocks,
         "sites": sites,
         "status": diag["status"],

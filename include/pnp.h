@@ -274,7 +274,7 @@ int pnp_step_wallmodel(pnp_ctx* ctx, pnp_mlp* mlp, int nsteps, double dt);
 /* Launch sites timed by pnp_profile, in launch order within a substage. */
 enum {
   PNP_SITE_RHS = 0,         /* explicit terms + CN right-hand sides            */
-  PNP_SITE_CN = 1,          /* wall-normal CN Thomas solves (2 launches)       */
+  PNP_SITE_CN = 1,          /* wall-normal CN Thomas solves                    */
   PNP_SITE_P_FFTX = 2,      /* divergence + forward real x-FFT                 */
   PNP_SITE_P_FFTZ = 3,      /* forward z-FFT                                   */
   PNP_SITE_P_THOMAS = 4,    /* spectral Thomas, Neumann                        */
@@ -292,7 +292,8 @@ enum {
 /* Advance nsteps steps without a CUDA graph, timing every launch site with
  * CUDA events on the context's stream.  ms_out[site] receives the summed
  * milliseconds over all 3*nsteps substages (nsites >= PNP_PROFILE_SITES);
- * *launches_per_step the number of kernel launches of one step. */
+ * *launches_per_step the number of kernels one step launches, counted from a
+ * capture of the step's CUDA graph (-1 when the context has no stream). */
 int pnp_profile(pnp_ctx* ctx, int nsteps, double dt, double* ms_out, int nsites, int* launches_per_step);
 
 const char* pnp_error_string(int code);

@@ -12,6 +12,7 @@
 // split into the N/2 + 1 non-negative frequencies.  Forward transforms carry
 // no normalisation; the spectral solve multiplies by 1/(Nx Nz).
 #include "pnp_common.cuh"
+#include "pnp_df.cuh"
 
 namespace pnp {
 
@@ -399,6 +400,59 @@ cudaError_t launch_spec_factors(double* cpr, double* inv, const double* kx2, con
 
 constexpr int kCH = 8;
 
+// FP64 (0,0) mode of the mixed potential: the FP32 transform's mean of the
+// fluctuating charge, scaled, plus the FP64 reference source; the solution goes
+// to mean_out (plus mean_shift) and the transform slot is zeroed.  Runs in the
+// real-part thread; the imaginary-part thread only zeroes its slots.
+template <typename T>
+__device__ void spec_mean_mode(T* sp, const double* __restrict__ cpr, const double* __restrict__ inv,
+                               const YRows& rows, size_t base, size_t P, int ny, int part, double scale,
+                               const double* __restrict__ mean_rhs, const double* __restrict__ mean_shift,
+                               double* __restrict__ mean_out) {
+  if (part == 1) {
+    for (int j = 0; j < ny; ++j) sp[2 * (base + (size_t)j * P)] = T(0);
+    return;
+  }
+  double d = 0.0;
+  for (int j0 = 0; j0 < ny; j0 += kCH) {
+    double rr[kCH], iv[kCH], mr[kCH];
+#pragma unroll
+    for (int u = 0; u < kCH; ++u)
+      if (j0 + u < ny) {
+        const size_t o = base + (size_t)(j0 + u) * P;
+        rr[u] = (double)sp[2 * o];
+        iv[u] = inv[o];
+        mr[u] = mean_rhs[j0 + u];
+      }
+#pragma unroll
+    for (int u = 0; u < kCH; ++u)
+      if (j0 + u < ny) {
+        d = (rr[u] * scale + mr[u] - rows.a[j0 + u] * d) * iv[u];
+        mean_out[j0 + u] = d;
+      }
+  }
+  double x = d;
+  mean_out[ny - 1] = x + mean_shift[ny - 1];
+  sp[2 * (base + (size_t)(ny - 1) * P)] = T(0);
+  for (int j1 = ny - 2; j1 >= 0; j1 -= kCH) {
+    double dd[kCH], cc[kCH], ms[kCH];
+#pragma unroll
+    for (int u = 0; u < kCH; ++u)
+      if (j1 - u >= 0) {
+        dd[u] = mean_out[j1 - u];
+        cc[u] = cpr[base + (size_t)(j1 - u) * P];
+        ms[u] = mean_shift[j1 - u];
+      }
+#pragma unroll
+    for (int u = 0; u < kCH; ++u)
+      if (j1 - u >= 0) {
+        x = dd[u] - cc[u] * x;
+        mean_out[j1 - u] = x + ms[u];
+        sp[2 * (base + (size_t)(j1 - u) * P)] = T(0);
+      }
+  }
+}
+
 // The forward sweep runs on the unscaled transform; its FP64 results go to an
 // FP64 scratch (no round trip through the transform's precision), and the
 // normalisation 1/(Nx Nz) is applied once, in the transform's precision, when
@@ -424,48 +478,7 @@ __global__ void k_spec_thomas(cplx<T>* __restrict__ spec, cplx<double>* __restri
   const bool pin = neumann && mm == 0 && n == 0;
   const bool mean_mode = mean_rhs != nullptr && mm == 0 && n == 0;
   if (mean_mode) {
-    if (part == 1) {
-      for (int j = 0; j < ny; ++j) sp[2 * (base + (size_t)j * P)] = T(0);
-      return;
-    }
-    double d = 0.0;
-    for (int j0 = 0; j0 < ny; j0 += kCH) {
-      double rr[kCH], iv[kCH], mr[kCH];
-#pragma unroll
-      for (int u = 0; u < kCH; ++u)
-        if (j0 + u < ny) {
-          const size_t o = base + (size_t)(j0 + u) * P;
-          rr[u] = (double)sp[2 * o];
-          iv[u] = inv[o];
-          mr[u] = mean_rhs[j0 + u];
-        }
-#pragma unroll
-      for (int u = 0; u < kCH; ++u)
-        if (j0 + u < ny) {
-          d = (rr[u] * scale + mr[u] - rows.a[j0 + u] * d) * iv[u];
-          mean_out[j0 + u] = d;
-        }
-    }
-    double x = d;
-    mean_out[ny - 1] = x + mean_shift[ny - 1];
-    sp[2 * (base + (size_t)(ny - 1) * P)] = T(0);
-    for (int j1 = ny - 2; j1 >= 0; j1 -= kCH) {
-      double dd[kCH], cc[kCH], ms[kCH];
-#pragma unroll
-      for (int u = 0; u < kCH; ++u)
-        if (j1 - u >= 0) {
-          dd[u] = mean_out[j1 - u];
-          cc[u] = cpr[base + (size_t)(j1 - u) * P];
-          ms[u] = mean_shift[j1 - u];
-        }
-#pragma unroll
-      for (int u = 0; u < kCH; ++u)
-        if (j1 - u >= 0) {
-          x = dd[u] - cc[u] * x;
-          mean_out[j1 - u] = x + ms[u];
-          sp[2 * (base + (size_t)(j1 - u) * P)] = T(0);
-        }
-    }
+    spec_mean_mode(sp, cpr, inv, rows, base, P, ny, part, scale, mean_rhs, mean_shift, mean_out);
     return;
   }
   double d = 0.0;
@@ -520,6 +533,157 @@ cudaError_t launch_spec_thomas(cplx<T>* spec, cplx<double>* dscr, const double* 
   const int T_ = g.lc_spec ? g.lc_spec : 64;
   dim3 grd((2 * g.mh + T_ - 1) / T_, g.nz, 1);
   k_spec_thomas<T><<<grd, T_, 0, s>>>(spec, dscr, cpr, inv, rows, g, scale, neumann, mean_rhs, mean_shift, mean_out);
+  return cudaGetLastError();
+}
+
+// Mixed path: the same elimination in double-float arithmetic on the FP32 pipe
+// (pnp_df.cuh).  The low wavenumbers are ill-conditioned on the stretched grid
+// (the near-wall rows dominate |A| |x| by orders of magnitude over A x), so the
+// recurrence needs more than FP32; df carries a 48-bit significand at a small
+// fraction of the FP64 pipe time.  Factors c'_j, 1/pivot_j and the
+// sub-diagonal a_j arrive as df pairs (converted once from the FP64 factors);
+// the forward-sweep values go to the scratch as df pairs; the (0,0) mode of the
+// mixed potential keeps its FP64 path.
+__global__ void k_spec_thomas_df(cplx<float>* __restrict__ spec, float2* __restrict__ dscr,
+                                 const float2* __restrict__ cprF, const float2* __restrict__ invF,
+                                 const float2* __restrict__ aF, const double* __restrict__ cpr,
+                                 const double* __restrict__ inv, YRows rows, Geo g, double scale, float sc,
+                                 bool neumann, const double* __restrict__ mean_rhs,
+                                 const double* __restrict__ mean_shift, double* __restrict__ mean_out) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int mm = tid >> 1, part = tid & 1;
+  const int n = blockIdx.y;
+  if (mm >= g.mh) return;
+  const size_t P = (size_t)g.nz * g.mp;
+  const size_t base = (size_t)n * g.mp + mm;
+  const int ny = g.nyc;
+  float* sp = reinterpret_cast<float*>(spec) + part;   // this part of spec[base + j P] at sp[2 (base + j P)]
+  float2* dp = dscr + part;                             // its df forward value at dp[2 (base + j P)]
+  const bool pin = neumann && mm == 0 && n == 0;
+  if (mean_rhs != nullptr && mm == 0 && n == 0) return;   // k_spec_mean handles the (0,0) mode
+  dfl d{0.f, 0.f};
+  for (int j0 = 0; j0 < ny; j0 += kCH) {
+    float rr[kCH];
+    float2 iv[kCH];
+#pragma unroll
+    for (int u = 0; u < kCH; ++u)
+      if (j0 + u < ny) {
+        const size_t o = base + (size_t)(j0 + u) * P;
+        rr[u] = sp[2 * o];
+        iv[u] = invF[o];
+      }
+#pragma unroll
+    for (int u = 0; u < kCH; ++u) {
+      const int j = j0 + u;
+      if (j < ny) {
+        const float r = (pin && j == 0) ? 0.f : rr[u];
+        const float2 a = aF[j];
+        d = df_mul(df_sub_mul(r, dfl{a.x, a.y}, d), dfl{iv[u].x, iv[u].y});
+        if (j < ny - 1) dp[2 * (base + (size_t)j * P)] = make_float2(d.h, d.l);
+      }
+    }
+  }
+  dfl x = d;
+  sp[2 * (base + (size_t)(ny - 1) * P)] = x.h * sc;
+  for (int j1 = ny - 2; j1 >= 0; j1 -= kCH) {
+    float2 dd[kCH], cc[kCH];
+#pragma unroll
+    for (int u = 0; u < kCH; ++u)
+      if (j1 - u >= 0) {
+        const size_t o = base + (size_t)(j1 - u) * P;
+        dd[u] = dp[2 * o];
+        cc[u] = cprF[o];
+      }
+#pragma unroll
+    for (int u = 0; u < kCH; ++u) {
+      const int j = j1 - u;
+      if (j >= 0) {
+        x = df_sub_mul(dfl{dd[u].x, dd[u].y}, dfl{cc[u].x, cc[u].y}, x);
+        sp[2 * (base + (size_t)j * P)] = x.h * sc;
+      }
+    }
+  }
+}
+
+// The FP64 (0,0) mode of the mixed potential as one block: the column and its
+// coefficients are staged in shared memory by all threads (one memory latency
+// instead of one per serial step), thread 0 runs both sweeps there, and all
+// threads write the result and zero the transform slots.
+constexpr int kMeanSmemRows = 640;   // 6 doubles per row: 30 KB of static shared memory
+__global__ void __launch_bounds__(256) k_spec_mean(cplx<float>* __restrict__ spec, const double* __restrict__ cpr,
+                                                   const double* __restrict__ inv, YRows rows, Geo g, double scale,
+                                                   const double* __restrict__ mean_rhs,
+                                                   const double* __restrict__ mean_shift,
+                                                   double* __restrict__ mean_out) {
+  const size_t P = (size_t)g.nz * g.mp;
+  const int ny = g.nyc;
+  float* sp = reinterpret_cast<float*>(spec);   // (0,0) mode, real part at sp[2 j P], imaginary at sp[2 j P + 1]
+  if (ny > kMeanSmemRows) {
+    if (threadIdx.x < 2)
+      spec_mean_mode(sp + threadIdx.x, cpr, inv, rows, 0, P, ny, (int)threadIdx.x, scale, mean_rhs, mean_shift,
+                     mean_out);
+    return;
+  }
+  __shared__ double src[kMeanSmemRows], iv[kMeanSmemRows], cp[kMeanSmemRows], a[kMeanSmemRows],
+      ms[kMeanSmemRows], out[kMeanSmemRows];
+  for (int j = threadIdx.x; j < ny; j += blockDim.x) {
+    const size_t o = (size_t)j * P;
+    src[j] = (double)sp[2 * o] * scale + mean_rhs[j];
+    iv[j] = inv[o];
+    cp[j] = cpr[o];
+    a[j] = rows.a[j];
+    ms[j] = mean_shift[j];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double d = 0.0;
+    for (int j = 0; j < ny; ++j) {
+      d = (src[j] - a[j] * d) * iv[j];
+      out[j] = d;
+    }
+    double x = d;
+    for (int j = ny - 2; j >= 0; --j) {
+      x = out[j] - cp[j] * x;
+      out[j] = x;
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < ny; j += blockDim.x) {
+    const size_t o = (size_t)j * P;
+    mean_out[j] = out[j] + ms[j];
+    sp[2 * o] = 0.f;
+    sp[2 * o + 1] = 0.f;
+  }
+}
+
+cudaError_t launch_spec_thomas_df(cplx<float>* spec, void* dscr, const SpecDF& f, const double* cpr,
+                                  const double* inv, const YRows& rows, const Geo& g, double scale, bool neumann,
+                                  cudaStream_t s, const double* mean_rhs, const double* mean_shift,
+                                  double* mean_out) {
+  if (mean_rhs != nullptr) {
+    k_spec_mean<<<1, 256, 0, s>>>(spec, cpr, inv, rows, g, scale, mean_rhs, mean_shift, mean_out);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const int T_ = g.lc_spec ? g.lc_spec : 64;
+  dim3 grd((2 * g.mh + T_ - 1) / T_, g.nz, 1);
+  k_spec_thomas_df<<<grd, T_, 0, s>>>(spec, reinterpret_cast<float2*>(dscr), f.cpr, f.inv, f.a, cpr, inv, rows, g,
+                                      scale, (float)scale, neumann, mean_rhs, mean_shift, mean_out);
+  return cudaGetLastError();
+}
+
+// x -> (hi, lo) float pairs, hi the nearest float.
+__global__ void k_to_df(const double* __restrict__ x, float2* __restrict__ out, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  const float h = (float)v;
+  out[i] = make_float2(h, (float)(v - (double)h));
+}
+
+cudaError_t launch_to_df(const double* x, float2* out, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_to_df<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, out, n);
   return cudaGetLastError();
 }
 

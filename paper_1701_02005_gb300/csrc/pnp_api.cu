@@ -13,6 +13,7 @@
 
 #include "pnp_common.cuh"
 #include "pnp_mixed.cuh"
+#include "pnp_df.cuh"
 #include "pnp_wall.cuh"
 
 using namespace pnp;
@@ -83,6 +84,12 @@ struct pnp_ctx {
   double *Hrefp_d, *Hrefm_d;
   // spectral elimination factors (grid-only): c'_j and 1/pivot_j per spectral point
   double *spc_cprN, *spc_invN, *spc_cprD, *spc_invD;
+  // mixed path: their double-float copies and the y-operator sub-diagonals as df
+  float2 *spf_cprN = nullptr, *spf_invN = nullptr, *spf_cprD = nullptr, *spf_invD = nullptr;
+  float2 *spf_aN = nullptr, *spf_aD = nullptr;
+  // mixed path: low parts of the ion fluctuations (c = c_ref + S + L, S the shadow)
+  float *cpL = nullptr, *cmL = nullptr;
+  float2 *dCp_f2 = nullptr, *dCm_f2 = nullptr;   // [3][ny] reference increments as df pairs
   cplx<double>* dscr;   // FP64 forward-sweep values of the spectral solves
   // the potential pipeline runs concurrently with the pressure pipeline on an
   // auxiliary stream, with its own spectral buffers
@@ -96,7 +103,7 @@ struct pnp_ctx {
   bool slip_on = false;
   std::vector<double> href_p, href_m, lyc_p, lyc_m;
   bool refs_valid = false;   // references and shadows match the FP64 fields
-  bool fp64_fresh = true;    // FP64 Phi, Hc+- arrays are current (else the shadows are)
+  bool fp64_fresh = true;    // FP64 c+-, Phi, Hc+- arrays are current (else the shadows are)
   double refs_dt = NAN;
   std::vector<double> yf, yc, dy, h, cn_h;
   Phys ph{};
@@ -160,7 +167,17 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
   void* wallw = b.take<char>(P2 * tv);
   float* fX = b.take<float>(P2 * 5 * 8);
   float* fY = b.take<float>(P2 * 5);
+  const bool mixed = precision == PNP_MIXED;
+  float2 *sfcN = b.take<float2>(mixed ? nspec : 0), *sfiN = b.take<float2>(mixed ? nspec : 0);
+  float2 *sfcD = b.take<float2>(mixed ? nspec : 0), *sfiD = b.take<float2>(mixed ? nspec : 0);
+  float2 *sfaN = b.take<float2>(mixed ? ny : 0), *sfaD = b.take<float2>(mixed ? ny : 0);
+  float *cpL = b.take<float>(mixed ? nc : 0), *cmL = b.take<float>(mixed ? nc : 0);
+  float2 *dCp2 = b.take<float2>(3 * (size_t)ny), *dCm2 = b.take<float2>(3 * (size_t)ny);
   if (c) {
+    c->dCp_f2 = dCp2; c->dCm_f2 = dCm2;
+    c->spf_cprN = sfcN; c->spf_invN = sfiN; c->spf_cprD = sfcD; c->spf_invD = sfiD;
+    c->spf_aN = sfaN; c->spf_aD = sfaD;
+    c->cpL = cpL; c->cmL = cmL;
     c->dscr = dscr;
     c->spec2 = spec2;
     c->dscr2 = dscr2;
@@ -309,6 +326,15 @@ int upload_metrics(pnp_ctx* c) {
     const YRows rd{c->rowsD_d, c->rowsD_d + ny, c->rowsD_d + 2 * ny};
     CK(launch_spec_factors(c->spc_cprN, c->spc_invN, c->kx2_d, c->kz2_d, rn, c->g, true, s));
     CK(launch_spec_factors(c->spc_cprD, c->spc_invD, c->kx2_d, c->kz2_d, rd, c->g, false, s));
+    if (c->precision == PNP_MIXED) {
+      const size_t nspec = (size_t)c->g.nyc * c->g.nz * c->g.mp;
+      CK(launch_to_df(c->spc_cprN, c->spf_cprN, nspec, s));
+      CK(launch_to_df(c->spc_invN, c->spf_invN, nspec, s));
+      CK(launch_to_df(c->spc_cprD, c->spf_cprD, nspec, s));
+      CK(launch_to_df(c->spc_invD, c->spf_invD, nspec, s));
+      CK(launch_to_df(c->rowsN_d, c->spf_aN, (size_t)ny, s));
+      CK(launch_to_df(c->rowsD_d, c->spf_aD, (size_t)ny, s));
+    }
   }
   CK(cudaStreamSynchronize(s));   // host vectors above are temporaries
   c->refs_valid = false;
@@ -394,12 +420,16 @@ CoefF coef_f(const pnp_ctx* c, const Stage& st) {
                (float)st.dt, (float)st.gam, (float)st.zet, (float)st.alp};
 }
 
-Shadows shadows(const pnp_ctx* c) { return Shadows{c->cpS, c->cmS, c->phiS, c->HcpS, c->HcmS}; }
+Shadows shadows(const pnp_ctx* c) { return Shadows{c->cpS, c->cmS, c->phiS, c->HcpS, c->HcmS, c->cpL, c->cmL}; }
 
 MixedRefs mixed_refs(const pnp_ctx* c) {
   return MixedRefs{c->crefp_f, c->crefm_f, c->crfp_f, c->crfm_f, c->rhoref_f, c->rhorf_f, c->dPref_f, c->Fvref_f,
                    c->Rrefp_d, c->Rrefm_d, c->cref64p_d, c->cref64m_d, c->Phiref64_d, c->meanrhs_d,
-                   c->meanshift_d, c->delta_d};
+                   c->meanshift_d, c->delta_d, c->dCp_f2, c->dCm_f2};
+}
+
+SpecDF spec_df(const pnp_ctx* c, bool neumann) {
+  return neumann ? SpecDF{c->spf_cprN, c->spf_invN, c->spf_aN} : SpecDF{c->spf_cprD, c->spf_invD, c->spf_aD};
 }
 
 YRows yrows(const pnp_ctx* c, bool neumann) {
@@ -428,8 +458,12 @@ cudaError_t spectral_solve(pnp_ctx* c, cplx<T>* spec, const cplx<T>* twz, bool n
   if (e != cudaSuccess) return e;
   mark(c);
   const double scale = 1.0 / ((double)c->g.nx * (double)c->g.nz);
-  e = launch_spec_thomas<T>(spec, dscr, neumann ? c->spc_cprN : c->spc_cprD, neumann ? c->spc_invN : c->spc_invD,
-                            yrows(c, neumann), c->g, scale, neumann, st);
+  if constexpr (sizeof(T) == sizeof(float))
+    e = launch_spec_thomas_df(spec, dscr, spec_df(c, neumann), neumann ? c->spc_cprN : c->spc_cprD,
+                              neumann ? c->spc_invN : c->spc_invD, yrows(c, neumann), c->g, scale, neumann, st);
+  else
+    e = launch_spec_thomas<T>(spec, dscr, neumann ? c->spc_cprN : c->spc_cprD, neumann ? c->spc_invN : c->spc_invD,
+                              yrows(c, neumann), c->g, scale, neumann, st);
   if (e != cudaSuccess) return e;
   mark(c);
   e = launch_fft_z<T>(spec, twz, c->g, true, st);
@@ -508,8 +542,8 @@ cudaError_t potential_mixed(pnp_ctx* c, cudaStream_t st, void* spec_buf, cplx<do
   if (e != cudaSuccess) return e;
   mark(c);
   const double scale = 1.0 / ((double)c->g.nx * (double)c->g.nz);
-  e = launch_spec_thomas<float>(spec, dscr, c->spc_cprD, c->spc_invD, yrows(c, false), c->g, scale, false, st,
-                                c->meanrhs_d, c->meanshift_d, c->delta_d);
+  e = launch_spec_thomas_df(spec, dscr, spec_df(c, false), c->spc_cprD, c->spc_invD, yrows(c, false), c->g, scale,
+                            false, st, c->meanrhs_d, c->meanshift_d, c->delta_d);
   if (e != cudaSuccess) return e;
   mark(c);
   e = launch_fft_z<float>(spec, twz, c->g, true, st);
@@ -589,6 +623,8 @@ void drop_graph(pnp_ctx* c);
 int materialize(pnp_ctx* c) {
   if (c->precision != PNP_MIXED || c->fp64_fresh) return PNP_OK;
   const size_t P = (size_t)c->g.nz * c->g.nx;
+  CK(launch_from_shadow_df(c->cpS, c->cpL, c->cref64p_d, c->cp, P, c->nc, c->stream));
+  CK(launch_from_shadow_df(c->cmS, c->cmL, c->cref64m_d, c->cm, P, c->nc, c->stream));
   CK(launch_from_shadow(c->phiS, c->Phiref64_d, c->Phi, P, c->nc, c->stream));
   CK(launch_from_shadow(c->HcpS, c->Hrefp_d, c->Hcp, P, c->nc, c->stream));
   CK(launch_from_shadow(c->HcmS, c->Hrefm_d, c->Hcm, P, c->nc, c->stream));
@@ -701,6 +737,14 @@ int refresh_refs(pnp_ctx* c, double dt) {
     }
     CK(cudaMemcpyAsync(c->Rrefp_d, Rp.data(), sizeof(double) * 3 * nyc, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->Rrefm_d, Rm.data(), sizeof(double) * 3 * nyc, cudaMemcpyHostToDevice, c->stream));
+    std::vector<float2> Pp(3 * (size_t)nyc), Pm(3 * (size_t)nyc);
+    for (size_t q = 0; q < Pp.size(); ++q) {
+      const dfl a = df_split_host(Rp[q]), b = df_split_host(Rm[q]);
+      Pp[q] = make_float2(a.h, a.l);
+      Pm[q] = make_float2(b.h, b.l);
+    }
+    CK(cudaMemcpyAsync(c->dCp_f2, Pp.data(), sizeof(float2) * 3 * nyc, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->dCm_f2, Pm.data(), sizeof(float2) * 3 * nyc, cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->refs_dt = dt;
   }
@@ -1076,6 +1120,43 @@ int pnp_fp64_peak(pnp_ctx* c, double* flops) {
   return PNP_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Kernel launches of one step: capture the step into a graph (nothing runs)
+// and count its kernel nodes.  -1 when the context has no stream to capture on.
+int count_step_kernels(pnp_ctx* c, double dt) {
+  if (c->stream == nullptr) return -1;
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) return -1;
+  const cudaError_t e = one_step(c, dt);
+  const cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return -1;
+  }
+  size_t n = 0;
+  int kernels = -1;
+  if (cudaGraphGetNodes(graph, nullptr, &n) == cudaSuccess) {
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(graph, nodes.data(), &n) == cudaSuccess) {
+      kernels = 0;
+      for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+      }
+    }
+  }
+  cudaGraphDestroy(graph);
+  return kernels;
+}
+
+}  // namespace
+
+extern "C" {
+
 int pnp_profile(pnp_ctx* c, int nsteps, double dt, double* ms_out, int nsites, int* launches_per_step) {
   if (!c || !ms_out || nsites < PNP_PROFILE_SITES || nsteps < 1 || !(dt > 0)) return PNP_ERR_ARG;
   if (!c->have_params || !c->have_state) return PNP_ERR_STATE;
@@ -1088,6 +1169,7 @@ int pnp_profile(pnp_ctx* c, int nsteps, double dt, double* ms_out, int nsites, i
     if (r) return r;
   }
   if (c->precision == PNP_MIXED) c->fp64_fresh = false;
+  const int kernels = count_step_kernels(c, dt);
   Prof prof;
   for (int i = 0; i < Prof::kMax; ++i) CK(cudaEventCreate(&prof.ev[i]));
   for (int i = 0; i < PNP_PROFILE_SITES; ++i) ms_out[i] = 0.0;
@@ -1114,7 +1196,7 @@ int pnp_profile(pnp_ctx* c, int nsteps, double dt, double* ms_out, int nsites, i
     c->time += nsteps * dt;
     c->nstep += nsteps;
   }
-  if (launches_per_step) *launches_per_step = 3 * (PNP_PROFILE_SITES + 1);
+  if (launches_per_step) *launches_per_step = kernels;
   return rc;
 }
 
@@ -1174,6 +1256,7 @@ int pnp_autotune(pnp_ctx* c, double dt, int* cfg_out, double* ms_out) {
   // 1: stencil block shape
   for (int bx : {32, 64, 128, 16}) {
     if (bx > 2 * c->g.nx && bx != 32) continue;
+    if (c->precision == PNP_MIXED && bx > 32) continue;   // the tiled mixed stencil is at most 32 wide
     c->g.lc_rhs_bx = bx;
     float t = time_launches(c, [&] {
       if (c->precision == PNP_FP64) launch_rhs<double>(fields<double>(c), c->g, metrics(c), c->ph, st, c->stream);
@@ -1204,8 +1287,8 @@ int pnp_autotune(pnp_ctx* c, double dt, int* cfg_out, double* ms_out) {
         launch_spec_thomas<double>((cplx<double>*)c->spec, c->dscr, c->spc_cprD, c->spc_invD, yrows(c, false), c->g,
                                    scale, false, c->stream);
       else
-        launch_spec_thomas<float>((cplx<float>*)c->spec, c->dscr, c->spc_cprD, c->spc_invD, yrows(c, false), c->g,
-                                  scale, false, c->stream);
+        launch_spec_thomas_df((cplx<float>*)c->spec, c->dscr, spec_df(c, false), c->spc_cprD, c->spc_invD,
+                              yrows(c, false), c->g, scale, false, c->stream);
     }, reps);
     if (t < best[2]) { best[2] = t; pick[2] = T; }
   }

@@ -120,6 +120,16 @@ cudaError_t launch_fft_z(cplx<T>* spec, const cplx<T>* tw_z, const Geo& g, bool 
 cudaError_t launch_spec_factors(double* cpr, double* inv, const double* kx2, const double* kz2, const YRows& rows,
                                 const Geo& g, bool neumann, cudaStream_t s);
 
+// Double-float copies of the spectral elimination factors (mixed path).
+struct SpecDF {
+  const float2 *cpr, *inv;   // per spectral point, same layout as the FP64 factors
+  const float2* a;           // sub-diagonal of the y-operator per plane
+};
+cudaError_t launch_spec_thomas_df(cplx<float>* spec, void* dscr, const SpecDF& f, const double* cpr,
+                                  const double* inv, const YRows& rows, const Geo& g, double scale, bool neumann,
+                                  cudaStream_t s, const double* mean_rhs = nullptr,
+                                  const double* mean_shift = nullptr, double* mean_out = nullptr);
+cudaError_t launch_to_df(const double* x, float2* out, size_t n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_spec_thomas(cplx<T>* spec, cplx<double>* dscr, const double* cpr, const double* inv,
                                const YRows& rows, const Geo& g, double scale, bool neumann, cudaStream_t s,

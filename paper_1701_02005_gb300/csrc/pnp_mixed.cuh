@@ -24,9 +24,10 @@ struct CNRowsF {
 
 // FP32 fluctuation shadows (relative to the reference profiles).
 struct Shadows {
-  float *cp, *cm;    // c+' , c-'
+  float *cp, *cm;    // c+' , c-' (high parts of the df ion fluctuations)
   float *phi;        // phi' = Phi - Phi_ref
   float *Hcp, *Hcm;  // explicit ion terms minus their reference part
+  float *cpL, *cmL;  // low parts: c = c_ref + cp + cpL exactly to the df resolution
 };
 
 // Per-plane reference data.  FP32 arrays feed the FP32 stencils; FP64 arrays
@@ -43,6 +44,7 @@ struct MixedRefs {
   const double* mean_rhs;         // -q rho_ref [nyc]: FP64 (0,0) mode source of Eq. (4)
   const double* mean_shift;       // V y_c - Phi_ref [nyc]
   double* delta;                  // [nyc] written each solve: V y_c + phi_mean - Phi_ref
+  const float2 *dC_p, *dC_m;      // [3][nyc]: Rref_p, Rref_m as df pairs (the ion update adds them)
 };
 
 cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
@@ -54,6 +56,8 @@ cudaError_t launch_plane_means3(const double* a, const double* b, const double* 
 cudaError_t launch_make_shadows(const double* cp, const double* cm, const double* Phi, const double* Hcp,
                                 const double* Hcm, const Shadows& sh, const MixedRefs& R, const double* Href_p,
                                 const double* Href_m, size_t P, size_t n, cudaStream_t s);
+cudaError_t launch_from_shadow_df(const float* S, const float* L, const double* ref, double* out, size_t P, size_t n,
+                                  cudaStream_t s);
 cudaError_t launch_from_shadow(const float* sh, const double* ref, double* out, size_t P, size_t n, cudaStream_t s);
 
 
