@@ -306,8 +306,12 @@ def run_ours(args):
     prec = B.PNP_MIXED if args.precision == "mixed" else B.PNP_FP64
     s = Solver(WL["nx"], WL["ny"], WL["nz"], WL["Lx"], WL["Lz"], stretch=WL["stretch"], precision=prec, device=local)
     s.set_params(WL["Re"], WL["lam"], WL["Sc"], WL["V"], WL["beta"])
-    s.init_state(B.PNP_IC_PB, WL["seed"] + rank, WL["amp"])
     dt = WL["dt"]
+    launch_cfg = None
+    if not args.no_autotune:
+        from paper_1701_02005_gb300 import autotune
+        launch_cfg, _ = autotune.tune(s, dt)   # before the state: tuning overwrites the workspace
+    s.init_state(B.PNP_IC_PB, WL["seed"] + rank, WL["amp"])
     K, W = args.steps, args.warmup
     s.step(W, dt)
     s.synchronize()
@@ -453,6 +457,7 @@ def run_ours(args):
         "ensemble": ensemble,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "launch_config": launch_cfg,
         "gpu_launches": lps * K if lps > 0 else None,
         "gpu_launches_per_step": lps if lps > 0 else None,
         "clocks": clocks,
@@ -481,6 +486,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--ensemble-steps", type=int, default=20)
     ap.add_argument("--grid", default=None,
                     help="NX,NY,NZ override of the workload grid (small cases for profiler captures only)")

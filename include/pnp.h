@@ -44,7 +44,8 @@ enum {
   PNP_ERR_NONFINITE = -6,    /* device check: NaN/Inf in a prognostic field       */
   PNP_ERR_NEGATIVE_C = -7,   /* device check: a concentration went negative       */
   PNP_ERR_UNSUPPORTED = -8,  /* option not available for this precision          */
-  PNP_ERR_TOO_LARGE = -9     /* grid exceeds the static scratch of pnp_poisson_noalloc */
+  PNP_ERR_TOO_LARGE = -9,    /* grid exceeds the static scratch of pnp_poisson_noalloc */
+  PNP_ERR_TIMEOUT = -10      /* device check: an asynchronous copy did not complete in time */
 };
 
 /* Arithmetic precision of a context. */

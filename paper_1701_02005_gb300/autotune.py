@@ -17,10 +17,14 @@ from .build import BUILD
 DEFAULT_CACHE = os.environ.get("PNP_AUTOTUNE_CACHE", os.path.join(BUILD, "autotune_cache.json"))
 
 
+# bumped whenever the set of candidate kernels behind a launch-shape code changes
+KERNEL_REV = 2
+
+
 def _key(solver):
     name = solver.torch.cuda.get_device_name(solver.device)
     prec = "fp64" if solver.precision == B.PNP_FP64 else "mixed"
-    return f"{name}|{solver.nx}x{solver.ny}x{solver.nz}|{prec}"
+    return f"{name}|{solver.nx}x{solver.ny}x{solver.nz}|{prec}|rev{KERNEL_REV}"
 
 
 def tune(solver, dt, cache_path=DEFAULT_CACHE, force=False):

@@ -21,6 +21,7 @@ PNP_ERR_NONFINITE = -6
 PNP_ERR_NEGATIVE_C = -7
 PNP_ERR_UNSUPPORTED = -8
 PNP_ERR_TOO_LARGE = -9
+PNP_ERR_TIMEOUT = -10
 
 PNP_FP64 = 0
 PNP_MIXED = 1

@@ -1,0 +1,728 @@
+// Explicit right-hand sides of the mixed-precision fractional step
+// (arXiv:1701.02005, Eqs. (1)-(3), Numerical methods; staggering of Fig. 1).
+//
+// FP32, one pass per cell: momentum (u, w on every cell; v on faces j >= 1),
+// then both ions, reusing the loaded velocities and shadows.  For the ions the
+// CN right-hand side is split as r_c = Rref(j) + r', Rref the per-plane FP64
+// reference part (solved once per substage on the host and added by the ion
+// CN update) and r' = dt [gam H' + zet H'_old + alp D L_y c'] stored in FP32.
+//
+// Both kernels march a chunk of y-planes per block and keep the seven stencil
+// inputs (u, w, v, p, phi', c+', c-') of planes j-1, j, j+1 in a ring of four
+// plane slots in shared memory while plane j+2 lands in the fourth:
+//   * k_rhs_mixed_tma: a block owns TZB full x-rows; each row of each array
+//     arrives by one TMA tensor copy (cp.async.bulk.tensor, issued by one
+//     warp, completion on an mbarrier per slot).  The z-halo rows are row
+//     copies at the wrapped z, and after a plane lands its rows get a
+//     one-float periodic x-halo from inside shared memory, so no copy ever
+//     leaves the array.  nx in {32, 64, 128, 256}.
+//   * k_rhs_mixed_tile: TX x TZ tiles with a one-cell periodic halo, filled by
+//     per-thread cp.async; any grid.
+// Tile geometry is compile-time in both, so every neighbour read is a
+// shared-memory load at a constant offset from one of three slot pointers.
+// The arithmetic of a cell is one routine (rhs_cell), specialised at compile
+// time for interior planes and for the wall planes; the y-face products and
+// ion fluxes at face j+1 are carried in registers to the next plane, where
+// the same expression would be re-evaluated from the same operands.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+
+#include "pnp_common.cuh"
+#include "pnp_mixed.cuh"
+
+namespace pnp {
+
+namespace {
+
+constexpr int AU = 0, AW = 1, AV = 2, AP = 3, APH = 4, ACP = 5, ACM = 6, NA = 7, NH = 5;
+
+// Per-plane constants of plane j (and of face j + 1 where a cell needs both faces).
+struct PlaneC {
+  float idy, ih, ihp, lo_c, hi_c, lo_f, hi_f, wl, wu;
+  float rho_ref, Fvref, rhorf, dPref, dPrefp;
+  float cref_p, cref_m, crf_p, crf_pp, crf_m, crf_mp;
+  float Dih, Dihp;   // D / h_j, D / h_{j+1}
+};
+constexpr int kPlaneC = 22;   // fields of PlaneC
+constexpr int kPlaneLd = 24;  // table row length (16-byte rows)
+
+// One field of PlaneC of plane j, by index.
+__device__ __forceinline__ float plane_const(const MetricsF& mt, const MixedRefs& R, float D, int which, int j) {
+  switch (which) {
+    case 0: return mt.idy[j];
+    case 1: return mt.ih[j];
+    case 2: return mt.ih[j + 1];
+    case 3: return mt.lo_c[j];
+    case 4: return mt.hi_c[j];
+    case 5: return mt.lo_f[j];
+    case 6: return mt.hi_f[j];
+    case 7: return mt.wl[j];
+    case 8: return mt.wu[j];
+    case 9: return R.rho_ref[j];
+    case 10: return R.Fvref[j];
+    case 11: return R.rhorf[j];
+    case 12: return R.dPref[j];
+    case 13: return R.dPref[j + 1];
+    case 14: return R.cref_p[j];
+    case 15: return R.cref_m[j];
+    case 16: return R.crf_p[j];
+    case 17: return R.crf_p[j + 1];
+    case 18: return R.crf_m[j];
+    case 19: return R.crf_m[j + 1];
+    case 20: return D * mt.ih[j];
+    default: return D * mt.ih[j + 1];
+  }
+}
+
+// A block's table of per-plane constants: t[p * kPlaneLd + field], plane jb + p.
+__device__ __forceinline__ void fill_plane_table(float* t, const MetricsF& mt, const MixedRefs& R, float D, int jb,
+                                                 int je, int jchunk, int tid, int nthr) {
+  for (int e = tid; e < kPlaneLd * jchunk; e += nthr) {
+    const int p = e / kPlaneLd, which = e % kPlaneLd;
+    t[e] = (which < kPlaneC && jb + p < je) ? plane_const(mt, R, D, which, jb + p) : 0.f;
+  }
+}
+
+__device__ __forceinline__ PlaneC plane_consts(const float* t) {
+  PlaneC q;
+  q.idy = t[0]; q.ih = t[1]; q.ihp = t[2];
+  q.lo_c = t[3]; q.hi_c = t[4]; q.lo_f = t[5]; q.hi_f = t[6];
+  q.wl = t[7]; q.wu = t[8];
+  q.rho_ref = t[9]; q.Fvref = t[10]; q.rhorf = t[11]; q.dPref = t[12]; q.dPrefp = t[13];
+  q.cref_p = t[14]; q.cref_m = t[15];
+  q.crf_p = t[16]; q.crf_pp = t[17]; q.crf_m = t[18]; q.crf_mp = t[19];
+  q.Dih = t[20]; q.Dihp = t[21];
+  return q;
+}
+
+struct CellOut {
+  float ru, Hu, rw, Hw, rv, Hv, rcp, Hcp, rcm, Hcm;
+};
+
+// Values at face j+1 computed for plane j and reused as the face-j values of
+// plane j+1: advective products of u, w, v and the ion fluxes.
+struct YCarry {
+  float tu, tw, tv, fp, fm;
+};
+
+// Column wall velocities and the substage scalars folded once per kernel.
+struct CellK {
+  float idx, idz, idx2, idz2, nu, K, Kx, Kz, D, Dx, Dz, dt, gam, zet, alp, anu, aD;
+  float ub, ut, wb, wt;
+};
+
+__device__ __forceinline__ CellK cell_consts(const CoefF& cf, float ub, float ut, float wb, float wt) {
+  CellK k;
+  k.idx = cf.idx; k.idz = cf.idz; k.idx2 = cf.idx * cf.idx; k.idz2 = cf.idz * cf.idz;
+  k.nu = cf.nu; k.K = cf.K; k.Kx = cf.K * cf.idx; k.Kz = cf.K * cf.idz;
+  k.D = cf.D; k.Dx = cf.D * cf.idx; k.Dz = cf.D * cf.idz;
+  k.dt = cf.dt; k.gam = cf.gam; k.zet = cf.zet; k.alp = cf.alp; k.anu = cf.alp * cf.nu; k.aD = cf.alp * cf.D;
+  k.ub = ub; k.ut = ut; k.wb = wb; k.wt = wt;
+  return k;
+}
+
+// The FP32 explicit terms and CN right-hand sides of one cell (and of the
+// v-face below it when DN).  bm, bo, bp: this cell in array 0 of the slots of
+// planes j-1, j, j+1; arrays are AS floats apart, z-rows SZ floats apart.
+// DN / UP: a cell plane below / above exists; CIN: cy holds face j's values.
+template <int AS, int SZ, bool DN, bool UP, bool CIN>
+__device__ __forceinline__ CellOut rhs_cell(const float* __restrict__ bm, const float* __restrict__ bo,
+                                            const float* __restrict__ bp, const float Ho[5], const PlaneC& q,
+                                            const CellK& k, YCarry& cy) {
+#define LM(a, off) bm[(a) * AS + (off)]
+#define LO(a, off) bo[(a) * AS + (off)]
+#define LP(a, off) bp[(a) * AS + (off)]
+  constexpr int XM = -1, XP = 1, ZM = -SZ, ZP = SZ;
+  CellOut o;
+  const float u0 = LO(AU, 0), uxm = LO(AU, XM), uxp = LO(AU, XP), uzm = LO(AU, ZM), uzp = LO(AU, ZP);
+  const float w0 = LO(AW, 0), wxm = LO(AW, XM), wxp = LO(AW, XP), wzm = LO(AW, ZM), wzp = LO(AW, ZP);
+  const float vb = LO(AV, 0), vt = LP(AV, 0);
+  const float p0 = LO(AP, 0);
+  const float ph0 = LO(APH, 0), phxm = LO(APH, XM), phxp = LO(APH, XP), phzm = LO(APH, ZM), phzp = LO(APH, ZP);
+  const float cp0 = LO(ACP, 0), cm0 = LO(ACM, 0);
+  const float rho0 = cp0 - cm0;   // rho' at the centre
+  const float dphxm = ph0 - phxm, dphxp = phxp - ph0, dphzm = ph0 - phzm, dphzp = phzp - ph0;
+  float uym = 0.f, wym = 0.f, phym = 0.f, uyp = 0.f, wyp = 0.f, phyp = 0.f;
+  if constexpr (DN) {
+    uym = LM(AU, 0);
+    wym = LM(AW, 0);
+    phym = LM(APH, 0);
+  }
+  if constexpr (UP) {
+    uyp = LP(AU, 0);
+    wyp = LP(AW, 0);
+    phyp = LP(APH, 0);
+  }
+
+  // u at (x-face i, y-centre j, z-centre k)
+  {
+    const float ubp = 0.5f * (u0 + uxp), ubm = 0.5f * (uxm + u0);
+    const float ax = (ubp * ubp - ubm * ubm) * k.idx;
+    float ttop = 0.f, tbot = 0.f;
+    if constexpr (UP) ttop = (0.5f * (LP(AV, XM) + vt)) * (0.5f * (u0 + uyp));
+    if constexpr (DN) tbot = CIN ? cy.tu : (0.5f * (LO(AV, XM) + vb)) * (0.5f * (uym + u0));
+    cy.tu = ttop;
+    const float ay = (ttop - tbot) * q.idy;
+    const float wfk = 0.5f * (wxm + w0);
+    const float wfkp = 0.5f * (LO(AW, ZP + XM) + wzp);
+    const float az = (wfkp * 0.5f * (u0 + uzp) - wfk * 0.5f * (uzm + u0)) * k.idz;
+    const float lap = (uxp - 2.f * u0 + uxm) * k.idx2 + (uzp - 2.f * u0 + uzm) * k.idz2;
+    const float rhom = LO(ACP, XM) - LO(ACM, XM);
+    const float fu = -k.Kx * (q.rho_ref + 0.5f * (rhom + rho0)) * dphxm;
+    const float H = -(ax + ay + az) + k.nu * lap + fu;
+    const float Ly = q.lo_c * ((DN ? uym : k.ub) - u0) + q.hi_c * ((UP ? uyp : k.ut) - u0);
+    const float gp = (p0 - LO(AP, XM)) * k.idx;
+    o.ru = k.dt * (k.gam * H + k.zet * Ho[0] - k.alp * gp + k.anu * Ly);
+    o.Hu = H;
+  }
+  // w at (x-centre i, y-centre j, z-face k)
+  {
+    const float wbp = 0.5f * (w0 + wzp), wbm = 0.5f * (wzm + w0);
+    const float az = (wbp * wbp - wbm * wbm) * k.idz;
+    float ttop = 0.f, tbot = 0.f;
+    if constexpr (UP) ttop = (0.5f * (LP(AV, ZM) + vt)) * (0.5f * (w0 + wyp));
+    if constexpr (DN) tbot = CIN ? cy.tw : (0.5f * (LO(AV, ZM) + vb)) * (0.5f * (wym + w0));
+    cy.tw = ttop;
+    const float ay = (ttop - tbot) * q.idy;
+    const float ufi = 0.5f * (uzm + u0);
+    const float ufip = 0.5f * (LO(AU, ZM + XP) + uxp);
+    const float ax = (ufip * 0.5f * (w0 + wxp) - ufi * 0.5f * (wxm + w0)) * k.idx;
+    const float lap = (wxp - 2.f * w0 + wxm) * k.idx2 + (wzp - 2.f * w0 + wzm) * k.idz2;
+    const float rhom = LO(ACP, ZM) - LO(ACM, ZM);
+    const float fw = -k.Kz * (q.rho_ref + 0.5f * (rhom + rho0)) * dphzm;
+    const float H = -(ax + ay + az) + k.nu * lap + fw;
+    const float Ly = q.lo_c * ((DN ? wym : k.wb) - w0) + q.hi_c * ((UP ? wyp : k.wt) - w0);
+    const float gp = (p0 - LO(AP, ZM)) * k.idz;
+    o.rw = k.dt * (k.gam * H + k.zet * Ho[1] - k.alp * gp + k.anu * Ly);
+    o.Hw = H;
+  }
+  // v at (x-centre i, y-face j, z-centre k), 1 <= j <= nyc-1; the centre
+  // product (v_j + v_j+1)^2 / 4 is the face-j product of the next plane
+  {
+    const float vbu = 0.5f * (vb + vt);
+    const float ttop = vbu * vbu;
+    o.rv = 0.f;
+    o.Hv = 0.f;
+    if constexpr (DN) {
+      const float v0 = vb;
+      const float vxm = LO(AV, XM), vxp = LO(AV, XP), vzm = LO(AV, ZM), vzp = LO(AV, ZP);
+      const float vym = LM(AV, 0), vyp = vt;
+      float tbot;
+      if constexpr (CIN) {
+        tbot = cy.tv;
+      } else {
+        const float vbd = 0.5f * (vym + v0);
+        tbot = vbd * vbd;
+      }
+      const float Ui = q.wl * uym + q.wu * u0;
+      const float Uip = q.wl * LM(AU, XP) + q.wu * uxp;
+      const float ax = (Uip * 0.5f * (v0 + vxp) - Ui * 0.5f * (vxm + v0)) * k.idx;
+      const float ay = (ttop - tbot) * q.ih;
+      const float Wk = q.wl * wym + q.wu * w0;
+      const float Wkp = q.wl * LM(AW, ZP) + q.wu * wzp;
+      const float az = (Wkp * 0.5f * (v0 + vzp) - Wk * 0.5f * (vzm + v0)) * k.idz;
+      const float lap = (vxp - 2.f * v0 + vxm) * k.idx2 + (vzp - 2.f * v0 + vzm) * k.idz2;
+      // Coulomb force: reference-reference part is the FP64 constant Fvref
+      const float rhod = LM(ACP, 0) - LM(ACM, 0);
+      const float rpf = 0.5f * (rhod + rho0);   // rho' on the face
+      const float dphi = ph0 - phym;            // phi' difference
+      const float fv = q.Fvref - k.K * q.ih * (q.rhorf * dphi + rpf * (q.dPref + dphi));
+      const float H = -(ax + ay + az) + k.nu * lap + fv;
+      const float Ly = q.lo_f * (vym - v0) + q.hi_f * (vyp - v0);
+      const float gp = (p0 - LM(AP, 0)) * q.ih;
+      o.rv = k.dt * (k.gam * H + k.zet * Ho[2] - k.alp * gp + k.anu * Ly);
+      o.Hv = H;
+    }
+    cy.tv = ttop;
+  }
+  // ions: FP32 fluctuation fluxes (the reference-reference part is in Rref);
+  // F = c_face u - D (dc/dn + s c_face dphi/dn), D/dn folded into one factor
+#pragma unroll
+  for (int ion = 0; ion < 2; ++ion) {
+    const int A = ion == 0 ? ACP : ACM;
+    const float s = ion == 0 ? 1.f : -1.f;
+    const float cr = ion == 0 ? q.cref_p : q.cref_m;
+    const float cc = ion == 0 ? cp0 : cm0;
+    const float cxm_ = LO(A, XM), cxp_ = LO(A, XP), czm_ = LO(A, ZM), czp_ = LO(A, ZP);
+    float ca = cr + 0.5f * (cxm_ + cc), cb = cr + 0.5f * (cc + cxp_);
+    const float Fx_i = u0 * ca - k.Dx * ((cc - cxm_) + s * ca * dphxm);
+    const float Fx_ip = uxp * cb - k.Dx * ((cxp_ - cc) + s * cb * dphxp);
+    ca = cr + 0.5f * (czm_ + cc);
+    cb = cr + 0.5f * (cc + czp_);
+    const float Fz_k = w0 * ca - k.Dz * ((cc - czm_) + s * ca * dphzm);
+    const float Fz_kp = wzp * cb - k.Dz * ((czp_ - cc) + s * cb * dphzp);
+    // y faces: advection + migration
+    float Fy_j = 0.f, Fy_jp = 0.f, Ly = 0.f;
+    if constexpr (DN) {
+      const float cym_ = LM(A, 0);
+      Ly = q.lo_c * (cym_ - cc);
+      if constexpr (CIN) {
+        Fy_j = ion == 0 ? cy.fp : cy.fm;
+      } else {
+        const float crf = ion == 0 ? q.crf_p : q.crf_m;
+        const float cpf = 0.5f * (cym_ + cc), dph = ph0 - phym;
+        Fy_j = vb * (crf + cpf) - s * q.Dih * (crf * dph + cpf * (q.dPref + dph));
+      }
+    }
+    if constexpr (UP) {
+      const float cyp_ = LP(A, 0);
+      Ly += q.hi_c * (cyp_ - cc);
+      const float crfp = ion == 0 ? q.crf_pp : q.crf_mp;
+      const float cpf = 0.5f * (cc + cyp_), dph = phyp - ph0;
+      Fy_jp = vt * (crfp + cpf) - s * q.Dihp * (crfp * dph + cpf * (q.dPrefp + dph));
+    }
+    if (ion == 0) cy.fp = Fy_jp;
+    else cy.fm = Fy_jp;
+    const float H = -((Fx_ip - Fx_i) * k.idx + (Fy_jp - Fy_j) * q.idy + (Fz_kp - Fz_k) * k.idz);
+    const float r = k.dt * (k.gam * H + k.zet * Ho[3 + ion] + k.aD * Ly);
+    if (ion == 0) {
+      o.rcp = r;
+      o.Hcp = H;
+    } else {
+      o.rcm = r;
+      o.Hcm = H;
+    }
+  }
+  return o;
+#undef LM
+#undef LO
+#undef LP
+}
+
+// Plane j of a chunk starting at jb: the specialisation for its position.
+template <int AS, int SZ>
+__device__ __forceinline__ CellOut rhs_cell_at(int j, int jb, int nyc, const float* bm, const float* bo,
+                                               const float* bp, const float Ho[5], const PlaneC& q, const CellK& k,
+                                               YCarry& cy) {
+  if (j > jb) {
+    if (j < nyc - 1) return rhs_cell<AS, SZ, true, true, true>(bm, bo, bp, Ho, q, k, cy);
+    return rhs_cell<AS, SZ, true, false, true>(bm, bo, bp, Ho, q, k, cy);
+  }
+  if (j > 0) {
+    if (j < nyc - 1) return rhs_cell<AS, SZ, true, true, false>(bm, bo, bp, Ho, q, k, cy);
+    return rhs_cell<AS, SZ, true, false, false>(bm, bo, bp, Ho, q, k, cy);
+  }
+  if (j < nyc - 1) return rhs_cell<AS, SZ, false, true, false>(bm, bo, bp, Ho, q, k, cy);
+  return rhs_cell<AS, SZ, false, false, false>(bm, bo, bp, Ho, q, k, cy);
+}
+
+__device__ __forceinline__ void store_cell(const Fields<float>& f, float* rcp, float* rcm, const Shadows& sh,
+                                           size_t c0, bool has_dn, const CellOut& o) {
+  f.ru[c0] = o.ru;
+  f.Hu[c0] = o.Hu;
+  f.rw[c0] = o.rw;
+  f.Hw[c0] = o.Hw;
+  if (has_dn) {
+    f.rv[c0] = o.rv;
+    f.Hv[c0] = o.Hv;
+  }
+  rcp[c0] = o.rcp;
+  sh.Hcp[c0] = o.Hcp;
+  rcm[c0] = o.rcm;
+  sh.Hcm[c0] = o.Hcm;
+}
+
+__device__ __forceinline__ void wall_values(const Fields<float>& f, size_t P, size_t ck, float Uw, float& ub,
+                                            float& ut, float& wb, float& wt) {
+  ub = f.wall_u ? f.wall_u[ck] : -Uw;
+  ut = f.wall_u ? f.wall_u[P + ck] : Uw;
+  wb = f.wall_w ? f.wall_w[ck] : 0.f;
+  wt = f.wall_w ? f.wall_w[P + ck] : 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// cp.async tile kernel (any grid)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Shared memory of the tile kernel (floats): tiles [4 slots][7 arrays][NT],
+// old H [3 slots][5 arrays][TX * TZ], then the per-plane table [jchunk][kPlaneLd].
+__host__ __device__ constexpr size_t rhs_tile_floats(int tx, int tz) {
+  return 4 * 7 * (size_t)(tx + 2) * (tz + 2) + 3 * 5 * (size_t)tx * tz;
+}
+
+template <int TX, int TZ>
+__global__ void __launch_bounds__(TX * TZ, 768 / (TX * TZ))
+    k_rhs_mixed_tile(Fields<float> f, float* __restrict__ rcp, float* __restrict__ rcm, Shadows sh, MixedRefs R,
+                     Geo g, MetricsF mt, CoefF cf, int jchunk) {
+  constexpr int TW = TX + 2, NT = TW * (TZ + 2), NTH = TX * TZ, E = (NT + NTH - 1) / NTH;
+  extern __shared__ __align__(16) float rhs_smem[];
+  float* tiles = rhs_smem;                           // [4][NA][NT]
+  float* holds = rhs_smem + 4 * NA * NT;             // [3][NH][NTH]
+  float* pct = rhs_smem + rhs_tile_floats(TX, TZ);   // [jchunk][kPlaneLd]
+  const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * TX + tx;
+  const int nx = g.nx, nz = g.nz, nyc = g.nyc;
+  const int i0 = blockIdx.x * TX, k0 = blockIdx.y * TZ;
+  const int jb = blockIdx.z * jchunk, je = min(nyc, jb + jchunk);
+  const size_t P = (size_t)nz * nx;
+  const size_t ck = (size_t)(k0 + tz) * nx + i0 + tx;   // in-plane offset of this thread's cell
+
+  int off[E];   // in-plane offsets of this thread's tile elements (periodic in x and z)
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int el = tid + e * NTH;
+    const int kz = el / TW - 1, ix = el % TW - 1;
+    off[e] = ((k0 + kz) & (nz - 1)) * nx + ((i0 + ix) & (nx - 1));
+  }
+  const float* src[NA] = {f.u, f.w, f.v, f.p, sh.phi, sh.cp, sh.cm};
+  const float* hsrc[NH] = {f.Hu, f.Hw, f.Hv, sh.Hcp, sh.Hcm};
+  // plane q (tiles into slot q & 3, old H into slot q mod 3); one commit group
+  // per plane, empty when q is outside the chunk's window or the array
+  auto issue_plane = [&](int q) {
+    if (q >= jb - 1 && q <= je) {
+      float* ts = tiles + (size_t)(q & 3) * NA * NT;
+      const size_t qP = (size_t)q * P;
+#pragma unroll
+      for (int a = 0; a < NA; ++a) {
+        if (q < 0 || q >= (a == AV ? nyc + 1 : nyc)) continue;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (tid + e * NTH < NT) cp_async4(ts + a * NT + tid + e * NTH, src[a] + qP + off[e]);
+      }
+      if (q >= jb && q < je) {
+        float* hs = holds + (size_t)(q % 3) * NH * NTH;
+#pragma unroll
+        for (int h = 0; h < NH; ++h) cp_async4(hs + h * NTH + tid, hsrc[h] + qP + ck);
+      }
+    }
+    cp_async_commit();
+  };
+  issue_plane(jb - 1);
+  issue_plane(jb);
+  issue_plane(jb + 1);
+  fill_plane_table(pct, mt, R, cf.D, jb, je, jchunk, tid, NTH);
+
+  float ub, ut, wb, wt;
+  wall_values(f, P, ck, cf.Uw, ub, ut, wb, wt);
+  const CellK kc = cell_consts(cf, ub, ut, wb, wt);
+  const int c = (tz + 1) * TW + tx + 1;
+  YCarry cy{0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int j = jb; j < je; ++j) {
+    issue_plane(j + 2);
+    cp_async_wait_all_but_one();   // planes up to j + 1 have landed (this thread's copies)
+    __syncthreads();               // ... and every thread's (and the plane table)
+    const float* bm = tiles + (size_t)((j + 3) & 3) * NA * NT + c;
+    const float* bo = tiles + (size_t)(j & 3) * NA * NT + c;
+    const float* bp = tiles + (size_t)((j + 1) & 3) * NA * NT + c;
+    const float* hs = holds + (size_t)(j % 3) * NH * NTH + tid;
+    const float Ho[5] = {hs[0], hs[NTH], hs[2 * NTH], hs[3 * NTH], hs[4 * NTH]};
+    const PlaneC q = plane_consts(pct + (size_t)(j - jb) * kPlaneLd);
+    const CellOut o = rhs_cell_at<NT, TW>(j, jb, nyc, bm, bo, bp, Ho, q, kc, cy);
+    store_cell(f, rcp, rcm, sh, (size_t)j * P + ck, j > 0, o);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// TMA row kernel
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned sm_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sm_addr(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sm_addr(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(sm_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for a phase of an mbarrier: gives up after about two seconds
+// (or 2^26 polls), so a copy that never completes cannot hang the GPU.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+  if (mbar_try_wait(b, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (int it = 0; it < (1 << 26); ++it) {
+    if (mbar_try_wait(b, parity)) return true;
+    if ((it & 255) == 0 && global_ns() - t0 > 2000000000ull) break;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_row(float* dst, const CUtensorMap* m, int x, int z, int y,
+                                        unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(sm_addr(dst)),
+      "l"(reinterpret_cast<unsigned long long>(m)), "r"(x), "r"(z), "r"(y), "r"(sm_addr(bar))
+      : "memory");
+}
+
+// Geometry of the TMA kernel for nx = NX, TZB rows per block:
+//   row stride S = NX + 32 floats: row data at [32, 32 + NX) (128-byte aligned
+//   for the TMA destination), x-halo at 31 and 32 + NX (= 0 of the next row);
+//   an array-slot region holds TZB + 2 rows (z = k0-1 .. k0+TZB, wrapped) plus
+//   the last row's right halo.  Then old H [4 slots][5][TZB][NX], the
+//   per-plane table [jchunk][kPlaneLd] and four 8-byte mbarriers.
+template <int NX, int TZB>
+struct TmaGeo {
+  static constexpr int S = NX + 32, ROWS = TZB + 2, AS = ROWS * S + 32, SLOT = NA * AS;
+  static constexpr int BW = NX < 256 ? NX : 256, NBOX = NX / BW;
+  static constexpr int HS = NH * TZB * NX;   // old-H slot
+  static constexpr int NTHR = NX * TZB;
+  static constexpr size_t floats(int jchunk) { return 4 * (size_t)SLOT + 4 * (size_t)HS + (size_t)kPlaneLd * jchunk; }
+  static constexpr size_t bytes(int jchunk) { return floats(jchunk) * sizeof(float) + 4 * sizeof(unsigned long long); }
+};
+
+template <int NX, int TZB>
+__global__ void __launch_bounds__(NX * TZB, 1)
+    k_rhs_mixed_tma(const __grid_constant__ RhsMaps maps, Fields<float> f, float* __restrict__ rcp,
+                    float* __restrict__ rcm, Shadows sh, MixedRefs R, Geo g, MetricsF mt, CoefF cf, int jchunk,
+                    int* __restrict__ err) {
+  using G = TmaGeo<NX, TZB>;
+  extern __shared__ __align__(1024) float rhs_tma_smem[];
+  float* tiles = rhs_tma_smem;                  // [4 slots][NA][AS]
+  float* holds = tiles + 4 * (size_t)G::SLOT;   // [4 slots][NH][TZB][NX]
+  float* pct = holds + 4 * (size_t)G::HS;       // [jchunk][kPlaneLd]
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(pct + (size_t)kPlaneLd * jchunk);
+  const int nz = g.nz, nyc = g.nyc;
+  const int tx = threadIdx.x, tz = threadIdx.y;
+  const int tid = tz * NX + tx, lane = tid & 31, warp = tid >> 5;
+  const int k0 = blockIdx.x * TZB;
+  const int jb = blockIdx.y * jchunk, je = min(nyc, jb + jchunk);
+  const size_t P = (size_t)nz * NX;
+
+  if (tid == 0) {
+    for (int s = 0; s < 4; ++s) mbar_init(&bars[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fill_plane_table(pct, mt, R, cf.D, jb, je, jchunk, tid, G::NTHR);
+  __syncthreads();
+
+  // plane q of the window [jb - 1, je] into slot n & 3, n = q - jb + 1 (warp 0)
+  auto issue = [&](int q) {
+    const int slot = (q - jb + 1) & 3;
+    const bool hq = q >= jb && q < je;
+    unsigned bytes = 0;
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+      if (q >= 0 && q < (a == AV ? nyc + 1 : nyc)) bytes += G::ROWS * NX * sizeof(float);
+    if (hq) bytes += G::HS * sizeof(float);
+    if (lane == 0) mbar_arrive_expect_tx(&bars[slot], bytes);
+    __syncwarp();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    constexpr int NTILE = NA * G::ROWS * G::NBOX;
+    const int nall = NTILE + (hq ? NH * TZB * G::NBOX : 0);
+    for (int c = lane; c < nall; c += 32) {
+      if (c < NTILE) {
+        const int a = c / (G::ROWS * G::NBOX), rr = (c / G::NBOX) % G::ROWS, bx = c % G::NBOX;
+        if (q < 0 || q >= (a == AV ? nyc + 1 : nyc)) continue;
+        float* dst = tiles + ((size_t)slot * NA + a) * G::AS + rr * G::S + 32 + bx * G::BW;
+        tma_row(dst, &maps.t[a], bx * G::BW, (k0 - 1 + rr) & (nz - 1), q, &bars[slot]);
+      } else {
+        const int c2 = c - NTILE;
+        const int h = c2 / (TZB * G::NBOX), rr = (c2 / G::NBOX) % TZB, bx = c2 % G::NBOX;
+        float* dst = holds + (size_t)slot * G::HS + (h * TZB + rr) * NX + bx * G::BW;
+        tma_row(dst, &maps.h[h], bx * G::BW, k0 + rr, q, &bars[slot]);
+      }
+    }
+  };
+  // periodic x-halo of every row of plane q's slot, from inside shared memory
+  auto halo = [&](int q) {
+    float* ts = tiles + (size_t)((q - jb + 1) & 3) * G::SLOT;
+    for (int e = tid; e < NA * G::ROWS * 2; e += G::NTHR) {
+      float* row = ts + (e / (2 * G::ROWS)) * G::AS + ((e >> 1) % G::ROWS) * G::S;
+      if (e & 1) row[32 + NX] = row[32];
+      else row[31] = row[32 + NX - 1];
+    }
+  };
+  if (warp == 0)
+    for (int q = jb - 1; q <= min(jb + 2, je); ++q) issue(q);
+  int issued = min(jb + 2, je);   // last plane issued (uniform across the block)
+
+  const size_t ck = (size_t)(k0 + tz) * NX + tx;
+  float ub, ut, wb, wt;
+  wall_values(f, P, ck, cf.Uw, ub, ut, wb, wt);
+  const CellK kc = cell_consts(cf, ub, ut, wb, wt);
+  const int co = (tz + 1) * G::S + 32 + tx;   // this cell in array 0 of a slot
+  YCarry cy{0.f, 0.f, 0.f, 0.f, 0.f};
+  int waited = jb - 2;   // last plane this thread has seen land
+  bool bad = false;
+  for (int j = jb; j < je; ++j) {
+    for (int q = waited + 1; q <= j + 1; ++q) {
+      const int n = q - jb + 1;
+      if (!mbar_wait(&bars[n & 3], (n >> 2) & 1)) {
+        bad = true;
+        break;
+      }
+      waited = q;
+      halo(q);
+    }
+    if (__syncthreads_or(bad)) {
+      bad = true;
+      break;
+    }
+    const int n0 = j - jb + 1;
+    const float* bm = tiles + (size_t)((n0 + 3) & 3) * G::SLOT + co;
+    const float* bo = tiles + (size_t)(n0 & 3) * G::SLOT + co;
+    const float* bp = tiles + (size_t)((n0 + 1) & 3) * G::SLOT + co;
+    const float* hs = holds + (size_t)(n0 & 3) * G::HS + tz * NX + tx;
+    const float Ho[5] = {hs[0], hs[TZB * NX], hs[2 * TZB * NX], hs[3 * TZB * NX], hs[4 * TZB * NX]};
+    const PlaneC q = plane_consts(pct + (size_t)(j - jb) * kPlaneLd);
+    const CellOut o = rhs_cell_at<G::AS, G::S>(j, jb, nyc, bm, bo, bp, Ho, q, kc, cy);
+    store_cell(f, rcp, rcm, sh, (size_t)j * P + ck, j > 0, o);
+    __syncthreads();   // slot of plane j - 1 is free
+    if (j + 3 <= je) {
+      if (warp == 0) issue(j + 3);
+      issued = j + 3;
+    }
+  }
+  if (bad) {
+    if (tid == 0) {
+      atomicExch(err, PNP_ERR_TIMEOUT);
+      // let the copies still in flight land before the shared memory is released
+      for (int q = jb - 1; q <= issued; ++q) {
+        const int n = q - jb + 1;
+        mbar_wait(&bars[n & 3], (n >> 2) & 1);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Rows per block of the TMA kernel for this nx (512 threads), 0 when unsupported.
+int rhs_tma_rows(int nx) {
+  switch (nx) {
+    case 32: return 16;
+    case 64: return 8;
+    case 128: return 4;
+    case 256: return 2;
+    default: return 0;
+  }
+}
+
+}  // namespace
+
+bool rhs_tma_eligible(const Geo& g) {
+  const int tzb = rhs_tma_rows(g.nx);
+  return tzb > 0 && g.nz % tzb == 0;
+}
+
+cudaError_t build_rhs_maps(RhsMaps* m, const Fields<float>& f, const Shadows& sh, const Geo& g) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult qr;
+    void* fn = nullptr;
+    const cudaError_t e =
+        cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr);
+    if (e != cudaSuccess || qr != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const int bw = g.nx < 256 ? g.nx : 256;
+  auto make = [&](CUtensorMap* t, const float* p, int planes) {
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.nz, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.nx * sizeof(float), (cuuint64_t)g.nx * g.nz * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, 1, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return encode(t, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(p), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  const float* tin[7] = {f.u, f.w, f.v, f.p, sh.phi, sh.cp, sh.cm};
+  const float* hin[5] = {f.Hu, f.Hw, f.Hv, sh.Hcp, sh.Hcm};
+  for (int a = 0; a < 7; ++a)
+    if (!make(&m->t[a], tin[a], a == AV ? g.ny : g.nyc)) return cudaErrorInvalidValue;
+  for (int h = 0; h < 5; ++h)
+    if (!make(&m->h[h], hin[h], h == 2 ? g.ny : g.nyc)) return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
+cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
+                             const MetricsF& m, const CoefF& cf, const RhsMaps* maps, int* err, cudaStream_t s) {
+  float* rp = reinterpret_cast<float*>(f.rcp);
+  float* rm = reinterpret_cast<float*>(f.rcm);
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      nsm = 152;
+  }
+  // y-chunk length: the best product of wave efficiency (blocks over the
+  // resident slots, rounded up to whole waves) and chunk efficiency (each
+  // chunk also loads the planes below and above it), chunks of >= 8 planes
+  auto chunk = [&](int nxz, int per_sm) {
+    const int slots = nsm * per_sm;
+    int best = g.nyc;
+    double best_eff = -1.0;
+    for (int nch = 1; nch <= (g.nyc + 7) / 8; ++nch) {
+      const int jc = (g.nyc + nch - 1) / nch;
+      const double blocks = (double)nxz * ((g.nyc + jc - 1) / jc);
+      const double waves = blocks / slots;
+      const double eff = waves / std::ceil(waves) * jc / (jc + 2.0);
+      if (eff > best_eff + 1e-9) {
+        best_eff = eff;
+        best = jc;
+      }
+    }
+    return best;
+  };
+  // TMA rows: lc_rhs_bx 64 / 128; cp.async tiles: the default and 32 / 16
+  if (maps && (g.lc_rhs_bx == 64 || g.lc_rhs_bx == 128) && rhs_tma_eligible(g)) {
+    auto go = [&](auto kern, auto geo, int tzb) {
+      using G = decltype(geo);
+      const int jc = chunk(g.nz / tzb, 1);
+      const size_t smem = G::bytes(jc);
+      if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      const dim3 grd((unsigned)(g.nz / tzb), (unsigned)((g.nyc + jc - 1) / jc));
+      kern<<<grd, dim3(g.nx, tzb), smem, s>>>(*maps, f, rp, rm, sh, R, g, m, cf, jc, err);
+      return cudaGetLastError();
+    };
+    switch (g.nx) {
+      case 32: return go(k_rhs_mixed_tma<32, 16>, TmaGeo<32, 16>{}, 16);
+      case 64: return go(k_rhs_mixed_tma<64, 8>, TmaGeo<64, 8>{}, 8);
+      case 128: return go(k_rhs_mixed_tma<128, 4>, TmaGeo<128, 4>{}, 4);
+      default: return go(k_rhs_mixed_tma<256, 2>, TmaGeo<256, 2>{}, 2);
+    }
+  }
+  // tile width: 32 or 16, at most nx; TZ = 8 when nz allows and the tile is
+  // wide, else 4 (nx, nz are powers of two >= 4)
+  int tx = g.lc_rhs_bx == 16 ? 16 : 32;
+  if (tx > g.nx) tx = g.nx;
+  if (g.nz < 8 && tx > 8) tx = 8;
+  const int tz = tx >= 16 ? 8 : 4;
+  const int nxz = (g.nx / tx) * (g.nz / tz);
+  const int jc = chunk(nxz, 3 * 256 / (tx * tz));
+  const dim3 grd((unsigned)(g.nx / tx), (unsigned)(g.nz / tz), (unsigned)((g.nyc + jc - 1) / jc));
+  auto go = [&](auto kern, int bx, int bz) {
+    const size_t smem = sizeof(float) * (rhs_tile_floats(bx, bz) + (size_t)kPlaneLd * jc);
+    if (smem > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<grd, dim3(bx, bz), smem, s>>>(f, rp, rm, sh, R, g, m, cf, jc);
+    return cudaGetLastError();
+  };
+  switch (tx) {
+    case 32: return go(k_rhs_mixed_tile<32, 8>, 32, 8);
+    case 16: return go(k_rhs_mixed_tile<16, 8>, 16, 8);
+    case 8: return go(k_rhs_mixed_tile<8, 4>, 8, 4);
+    default: return go(k_rhs_mixed_tile<4, 4>, 4, 4);
+  }
+}
+
+}  // namespace pnp

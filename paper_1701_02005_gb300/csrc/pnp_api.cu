@@ -90,6 +90,9 @@ struct pnp_ctx {
   // mixed path: low parts of the ion fluctuations (c = c_ref + S + L, S the shadow)
   float *cpL = nullptr, *cmL = nullptr;
   float2 *dCp_f2 = nullptr, *dCm_f2 = nullptr;   // [3][ny] reference increments as df pairs
+  // mixed path: TMA descriptors of the stencil inputs (built once the workspace is carved)
+  RhsMaps rhs_maps{};
+  bool rhs_maps_ok = false;
   cplx<double>* dscr;   // FP64 forward-sweep values of the spectral solves
   // the potential pipeline runs concurrently with the pressure pipeline on an
   // auxiliary stream, with its own spectral buffers
@@ -420,6 +423,8 @@ CoefF coef_f(const pnp_ctx* c, const Stage& st) {
                (float)st.dt, (float)st.gam, (float)st.zet, (float)st.alp};
 }
 
+const RhsMaps* rhs_maps(const pnp_ctx* c) { return c->rhs_maps_ok ? &c->rhs_maps : nullptr; }
+
 Shadows shadows(const pnp_ctx* c) { return Shadows{c->cpS, c->cmS, c->phiS, c->HcpS, c->HcmS, c->cpL, c->cmL}; }
 
 MixedRefs mixed_refs(const pnp_ctx* c) {
@@ -600,7 +605,7 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
   const MixedRefs R = mixed_refs(c);
   const Metrics m = metrics(c);
   mark(c);
-  cudaError_t e = launch_mixed_rhs(f, sh, R, c->g, metrics_f(c), coef_f(c, st), l, c->stream);
+  cudaError_t e = launch_mixed_rhs(f, sh, R, c->g, metrics_f(c), coef_f(c, st), rhs_maps(c), c->status_d + 1, c->stream);
   if (e != cudaSuccess) return e;
   mark(c);
   e = launch_mixed_cn(f, sh, R, c->g, cn_rows_f(c, l, 0), cn_rows_f(c, l, 1), cn_rows_f(c, l, 2), l, c->stream);
@@ -822,6 +827,10 @@ int pnp_init_grid(pnp_ctx** out, int nx, int ny, int nz, double Lx, double Lz, d
   c->g.idz = 1.0 / c->g.dz;
   carve(c, c->ws, nx, ny, nz, precision);
   if (cudaMemsetAsync(c->ws, 0, bytes, c->stream) != cudaSuccess) { delete c; return PNP_ERR_CUDA; }
+  // the TMA stencil needs whole x-rows of at most 512 floats in 128-byte multiples;
+  // otherwise (or without the driver's tensor-map encoder) the cp.async tiles run
+  if (precision == PNP_MIXED && rhs_tma_eligible(c->g))
+    c->rhs_maps_ok = build_rhs_maps(&c->rhs_maps, fields<float>(c), shadows(c), c->g) == cudaSuccess;
   c->yf.assign(ny, 0.0);
   for (int j = 0; j < ny; ++j) {
     const double s = j * 2.0 / (ny - 1) - 1.0;
@@ -1007,10 +1016,11 @@ int pnp_diagnostics(pnp_ctx* c, pnp_diag* out) {
                                                   kDiagBlocks, c->diag_out, c->status_d, c->stream);
   if (e != cudaSuccess) return PNP_ERR_CUDA;
   double h[8];
-  int st = 0;
+  int st2[2] = {0, 0};
   CK(cudaMemcpyAsync(h, c->diag_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(&st, c->status_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(st2, c->status_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  const int st = st2[1] ? st2[1] : st2[0];
   const double P = (double)c->g.nx * c->g.nz;
   const double ub = h[0] / P, ut = h[1] / P;
   const double Uw = c->ph.Uw;
@@ -1087,7 +1097,8 @@ int pnp_eval_explicit(pnp_ctx* c) {
   } else {
     int r = refresh_refs(c, std::isfinite(c->refs_dt) ? c->refs_dt : 1.0);
     if (r) return r;
-    e = launch_mixed_rhs(fields<float>(c), shadows(c), mixed_refs(c), c->g, metrics_f(c), coef_f(c, st), 0, c->stream);
+    e = launch_mixed_rhs(fields<float>(c), shadows(c), mixed_refs(c), c->g, metrics_f(c), coef_f(c, st), rhs_maps(c),
+                         c->status_d + 1, c->stream);
     c->fp64_fresh = false;
   }
   return e == cudaSuccess ? PNP_OK : PNP_ERR_CUDA;
@@ -1095,10 +1106,10 @@ int pnp_eval_explicit(pnp_ctx* c) {
 
 int pnp_status(pnp_ctx* c) {
   if (!c) return PNP_ERR_ARG;
-  int st = 0;
-  CK(cudaMemcpyAsync(&st, c->status_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  int st[2] = {0, 0};
+  CK(cudaMemcpyAsync(st, c->status_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  return st;
+  return st[1] ? st[1] : st[0];   // a copy timeout is sticky and takes precedence
 }
 
 int pnp_fp64_peak(pnp_ctx* c, double* flops) {
@@ -1255,12 +1266,14 @@ int pnp_autotune(pnp_ctx* c, double dt, int* cfg_out, double* ms_out) {
   int pick[4] = {32, 128, 64, 32};
   // 1: stencil block shape
   for (int bx : {32, 64, 128, 16}) {
-    if (bx > 2 * c->g.nx && bx != 32) continue;
-    if (c->precision == PNP_MIXED && bx > 32) continue;   // the tiled mixed stencil is at most 32 wide
+    // FP64: block x-extents; mixed: 128 / 64 = TMA rows x2 / x1 (when available), 32 / 16 = cp.async tiles
+    if (c->precision == PNP_FP64 && bx > 2 * c->g.nx && bx != 32) continue;
+    if (c->precision == PNP_MIXED && bx > 32 && !c->rhs_maps_ok) continue;
     c->g.lc_rhs_bx = bx;
     float t = time_launches(c, [&] {
       if (c->precision == PNP_FP64) launch_rhs<double>(fields<double>(c), c->g, metrics(c), c->ph, st, c->stream);
-      else launch_mixed_rhs(fields<float>(c), shadows(c), mixed_refs(c), c->g, metrics_f(c), coef_f(c, st), 0, c->stream);
+      else launch_mixed_rhs(fields<float>(c), shadows(c), mixed_refs(c), c->g, metrics_f(c), coef_f(c, st), rhs_maps(c),
+                            c->status_d + 1, c->stream);
     }, reps);
     if (t < best[0]) { best[0] = t; pick[0] = bx; }
   }
@@ -1753,6 +1766,7 @@ const char* pnp_error_string(int code) {
     case PNP_ERR_NONFINITE: return "non-finite value in a prognostic field";
     case PNP_ERR_NEGATIVE_C: return "negative ion concentration";
     case PNP_ERR_UNSUPPORTED: return "unsupported option";
+    case PNP_ERR_TIMEOUT: return "an asynchronous copy did not complete within the kernel's wait limit";
     case PNP_ERR_TOO_LARGE: return "grid exceeds the static scratch of pnp_poisson_noalloc (2^20 spectral points)";
     default: return "unknown error";
   }

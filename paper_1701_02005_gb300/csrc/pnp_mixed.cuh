@@ -1,6 +1,8 @@
 // Declarations of the mixed-precision path (see k_mixed.cu for the policy).
 #pragma once
 
+#include <cuda.h>
+
 #include "pnp_common.cuh"
 
 namespace pnp {
@@ -47,8 +49,19 @@ struct MixedRefs {
   const float2 *dC_p, *dC_m;      // [3][nyc]: Rref_p, Rref_m as df pairs (the ion update adds them)
 };
 
+// TMA descriptors of the stencil inputs and old H arrays of one context
+// (3-D {nx, nz, planes} float tensors, one x-row per copy).
+struct RhsMaps {
+  CUtensorMap t[7];   // u, w, v, p, phi', c+', c-'
+  CUtensorMap h[5];   // Hu, Hw, Hv, Hc+', Hc-'
+};
+
+bool rhs_tma_eligible(const Geo& g);
+cudaError_t build_rhs_maps(RhsMaps* m, const Fields<float>& f, const Shadows& sh, const Geo& g);
+// maps == nullptr selects the cp.async tile kernel; err receives PNP_ERR_TIMEOUT
+// if a TMA copy does not complete within the kernel's wait limit.
 cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
-                             const MetricsF& m, const CoefF& cf, int l, cudaStream_t s);
+                             const MetricsF& m, const CoefF& cf, const RhsMaps* maps, int* err, cudaStream_t s);
 cudaError_t launch_mixed_cn(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
                             const CNRowsF& cell, const CNRowsF& face, const CNRowsF& ion, int l, cudaStream_t s);
 cudaError_t launch_plane_means3(const double* a, const double* b, const double* c, int nplanes, size_t P,

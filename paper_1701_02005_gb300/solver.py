@@ -120,6 +120,10 @@ class Solver:
         self.stream.synchronize()
         return out.cpu().numpy()
 
+    def status(self):
+        """Device error word: PNP_OK, a field check (NaN, negative c) or a copy timeout."""
+        return int(B.pnp_status(self.ctx))
+
     def eval_explicit(self):
         B.check(B.pnp_eval_explicit(self.ctx), "pnp_eval_explicit")
         self.stream.synchronize()

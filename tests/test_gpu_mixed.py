@@ -99,3 +99,31 @@ def test_mixed_laminar_couette_exact():
     assert abs(d["tau_bot"] - 1 / 400) <= 1e-5 * (1 / 400)
     assert np.max(np.abs(s.get("u") - g.yc[:, None, None])) <= 1e-6
     s.close()
+
+
+def test_mixed_stencil_kernels_agree():
+    # the TMA row kernel (x2 and x1 rows per block) and the cp.async tile kernels
+    # (32 and 16 wide) run the same per-cell arithmetic: identical to FP32 rounding
+    import ctypes as C
+
+    from paper_1701_02005_gb300 import binding as B
+
+    g = o.Grid(64, 41, 32, 2 * math.pi, math.pi, stretch=2.0)
+    prm = o.Params(Re=300.0, lam=0.05, Sc=1.0, V=2.0, beta=0.5)
+    st = o.initial_state(g, prm, o.IC_PB, seed=15, amp=0.1)
+    shp = (g.nyc, g.nz, g.nx)
+    st.cp = st.cp * seeded.positive_field(16, shp, 0.98, 1.02)
+    st.cm = st.cm * seeded.positive_field(17, shp, 0.98, 1.02)
+    st.Phi = o.potential_from_ions(g, prm, st.cp, st.cm)
+    s = _mixed(g, prm)
+    out = {}
+    for bx in (128, 64, 32, 16):
+        B.check(B.pnp_set_launch_config(s.ctx, (C.c_int * 4)(bx, 128, 64, 32)), "pnp_set_launch_config")
+        s.set_state(st)
+        s.eval_explicit()
+        out[bx] = {n: s.get(n) for n in ("Hu", "Hv", "Hw", "Hcp", "Hcm")}
+    assert s.status() == 0
+    for bx in (64, 32, 16):
+        for n in out[128]:
+            assert _rel(out[bx][n], out[128][n]) <= 1e-6, (bx, n)
+    s.close()
