@@ -45,6 +45,14 @@ def cells(wl=WL):
 # (FP64 arithmetic and FP64<->FP32 conversions), counted from the kernel
 # sources.  ``half`` = spectral points per real point ((Nx/2+1)/Nx).
 # --------------------------------------------------------------------------
+# dram__bytes_read.sum + dram__bytes_write.sum per launch, turbulent Couette
+# 256x193x256, from the one-pass ncu capture summarised under profiles/
+# (shape = the stencil's tuned launch code the capture ran with)
+NCU_TRAFFIC = {
+    ("mixed", "rhs"): {"kernel": "k_rhs_mixed_tile<32, 8>", "shape": 32, "cells": 12582912, "bytes": 1072.2e6},
+}
+
+
 def site_cost(site, precision):
     half = (WL["nx"] // 2 + 1) / WL["nx"]
     if precision == "fp64":
@@ -374,6 +382,13 @@ def run_ours(args):
                 "traffic": None, "kernel": dom, "peak_source": hbm_src,
                 "per_unit": f"{cst['bytes']:.1f} B per cell x {n_cells} cells per launch"}
     roof["share"] = per_launch[dom] / total
+    # DRAM bytes (read + write) per launch of the dominant kernel from the committed
+    # one-pass ncu capture of this workload (profiles/, DRAM traffic summary), valid
+    # only for the kernel and launch shape that capture measured
+    t = NCU_TRAFFIC.get((pname, dom))
+    if t and t["cells"] == n_cells and (t["shape"] is None or (launch_cfg and launch_cfg[0] == t["shape"])):
+        roof["traffic"] = t["bytes"]
+        roof["traffic_kernel"] = t["kernel"]
 
     # the FP64 path on the same workload, and the mixed-vs-FP64 error from one initial state
     cmp = None

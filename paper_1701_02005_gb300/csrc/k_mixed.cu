@@ -1,20 +1,24 @@
 // Mixed-precision kernels of the fractional step (arXiv:1701.02005, Eqs. (1)-(4),
 // Numerical methods; staggering of Fig. 1).
 //
-// Precision policy.  Ion concentrations c+- stay FP64 in memory and every
-// wall-normal solve (ion Crank-Nicolson, both Poisson y-solves, the (0,0)
-// mean mode of the potential) runs in FP64.  The stencils run in FP32 on
-// shadows relative to FP64 reference profiles of y:
-//     c = c_ref(y) + c',   Phi = Phi_ref(y) + phi',
-// c_ref, Phi_ref being plane means taken when the state is loaded.  Every
-// product of two reference quantities (the 1-D double-layer migration flux,
-// its divergence, the implicit diffusion of c_ref and the osmotic Coulomb
-// force on v) is a per-plane FP64 constant folded in exactly; only terms that
-// contain a fluctuation are rounded to FP32, so the near-cancellation of
-// diffusion and migration inside the Debye layer happens in FP64.
-// Velocities, pressure and the momentum stencils are FP32; the velocity
-// Crank-Nicolson matrix is I - s L_y with s L_y = O(1) (well conditioned) and
-// runs in FP32.
+// Precision policy.  The parts that need FP64 accuracy keep a 48-bit or wider
+// significand; on this GPU the per-cell ones get it from double-float pairs on
+// the FP32 pipe (pnp_df.cuh), the 1-D ones from FP64:
+//   * ion concentrations: an FP64 reference profile c_ref(y) plus a per-cell
+//     double-float fluctuation (S, L), c = c_ref + S + L; S is the FP32 shadow
+//     c' the stencils read;
+//   * the potential: Phi = Phi_ref(y) + phi', phi' FP32 from the FP32 transform
+//     of the fluctuating charge, its (0,0) mode from an FP64 source in FP64;
+//   * every spectral y-solve in double-float (k_solve.cu);
+//   * every product of two reference quantities (the 1-D double-layer
+//     migration flux, its divergence, the implicit diffusion of c_ref and the
+//     osmotic Coulomb force on v) is a per-plane FP64 constant folded in
+//     exactly, so the near-cancellation of diffusion and migration inside the
+//     Debye layer happens in FP64; only terms that contain a fluctuation are
+//     rounded to FP32.
+// c_ref, Phi_ref are plane means taken when the state is loaded.  Velocities,
+// pressure and the momentum stencils are FP32; the velocity Crank-Nicolson
+// matrix is I - s L_y with s L_y = O(1) (well conditioned) and runs in FP32.
 #include "pnp_common.cuh"
 #include "pnp_mixed.cuh"
 #include "pnp_df.cuh"
