@@ -385,10 +385,10 @@ def run_ours(args):
     # DRAM bytes (read + write) per launch of the dominant kernel from the committed
     # one-pass ncu capture of this workload (profiles/, DRAM traffic summary), valid
     # only for the kernel and launch shape that capture measured
-    t = NCU_TRAFFIC.get((pname, dom))
-    if t and t["cells"] == n_cells and (t["shape"] is None or (launch_cfg and launch_cfg[0] == t["shape"])):
-        roof["traffic"] = t["bytes"]
-        roof["traffic_kernel"] = t["kernel"]
+    nt = NCU_TRAFFIC.get((pname, dom))
+    if nt and nt["cells"] == n_cells and (nt["shape"] is None or (launch_cfg and launch_cfg[0] == nt["shape"])):
+        roof["traffic"] = nt["bytes"]
+        roof["traffic_kernel"] = nt["kernel"]
 
     # the FP64 path on the same workload, and the mixed-vs-FP64 error from one initial state
     cmp = None

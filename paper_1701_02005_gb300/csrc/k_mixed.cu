@@ -208,18 +208,24 @@ __global__ void k_from_shadow_df(const float* __restrict__ S, const float* __res
 
 // ---------------------------------------------------------------------------
 cudaError_t launch_mixed_cn(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
-                            const CNRowsF& cell, const CNRowsF& face, const CNRowsF& ion, int l, cudaStream_t s) {
+                            const CNRowsF& cell, const CNRowsF& face, const CNRowsF& ion, int l, unsigned parts,
+                            cudaStream_t s) {
   const size_t P = (size_t)g.nz * g.nx;
   const int T = g.lc_cn ? g.lc_cn : 128;
-  dim3 grd((unsigned)((P + T - 1) / T), 3, 1);
-  k_cn_vel_f32<<<grd, T, 0, s>>>(f.u, f.ru, f.v, f.rv, f.w, f.rw, cell, face, g.nyc, P);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  dim3 grd2((unsigned)((P + T - 1) / T), 2, 1);
-  k_cn_ion_mixed<<<grd2, T, 0, s>>>(reinterpret_cast<float*>(f.rcp), sh.cp, sh.cpL, reinterpret_cast<float*>(f.rcm),
-                                    sh.cm, sh.cmL, ion, R.dC_p + (size_t)l * g.nyc, R.dC_m + (size_t)l * g.nyc,
-                                    g.nyc, P);
-  return cudaGetLastError();
+  if (parts & kCnIons) {
+    dim3 grd2((unsigned)((P + T - 1) / T), 2, 1);
+    k_cn_ion_mixed<<<grd2, T, 0, s>>>(reinterpret_cast<float*>(f.rcp), sh.cp, sh.cpL,
+                                      reinterpret_cast<float*>(f.rcm), sh.cm, sh.cmL, ion,
+                                      R.dC_p + (size_t)l * g.nyc, R.dC_m + (size_t)l * g.nyc, g.nyc, P);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (parts & kCnVelocity) {
+    dim3 grd((unsigned)((P + T - 1) / T), 3, 1);
+    k_cn_vel_f32<<<grd, T, 0, s>>>(f.u, f.ru, f.v, f.rv, f.w, f.rw, cell, face, g.nyc, P);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_plane_means3(const double* a, const double* b, const double* c, int nplanes, size_t P,

@@ -608,10 +608,25 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
   cudaError_t e = launch_mixed_rhs(f, sh, R, c->g, metrics_f(c), coef_f(c, st), rhs_maps(c), c->status_d + 1, c->stream);
   if (e != cudaSuccess) return e;
   mark(c);
-  e = launch_mixed_cn(f, sh, R, c->g, cn_rows_f(c, l, 0), cn_rows_f(c, l, 1), cn_rows_f(c, l, 2), l, c->stream);
-  if (e != cudaSuccess) return e;
-  mark(c);
-  return poisson_pair<float>(c, st.alp * dt);
+  const CNRowsF cell = cn_rows_f(c, l, 0), face = cn_rows_f(c, l, 1), ion = cn_rows_f(c, l, 2);
+  if (c->prof) {   // site timing: everything in order on the main stream
+    e = launch_mixed_cn(f, sh, R, c->g, cell, face, ion, l, kCnIons | kCnVelocity, c->stream);
+    if (e != cudaSuccess) return e;
+    mark(c);
+    return poisson_pair<float>(c, st.alp * dt);
+  }
+  // The potential depends only on the ions: their CN solve goes first and the
+  // potential pipeline forks onto the auxiliary stream, overlapping the
+  // velocity CN solve, the pressure pipeline and the projection.
+  e = launch_mixed_cn(f, sh, R, c->g, cell, face, ion, l, kCnIons, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork, c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+  if (e == cudaSuccess) e = potential_mixed(c, c->aux, c->spec2, c->dscr2);
+  if (e == cudaSuccess) e = launch_mixed_cn(f, sh, R, c->g, cell, face, ion, l, kCnVelocity, c->stream);
+  if (e == cudaSuccess) e = pressure_projection<float>(c, st.alp * dt, true);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->aux);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+  return e;
 }
 
 cudaError_t one_step(pnp_ctx* c, double dt) {
@@ -1286,7 +1301,7 @@ int pnp_autotune(pnp_ctx* c, double dt, int* cfg_out, double* ms_out) {
         launch_cn_solves<double>(fields<double>(c), c->g, cn_rows(c, 0, 0), cn_rows(c, 0, 1), cn_rows(c, 0, 2), c->stream);
       else
         launch_mixed_cn(fields<float>(c), shadows(c), mixed_refs(c), c->g, cn_rows_f(c, 0, 0), cn_rows_f(c, 0, 1),
-                        cn_rows_f(c, 0, 2), 0, c->stream);
+                        cn_rows_f(c, 0, 2), 0, kCnIons | kCnVelocity, c->stream);
     }, reps);
     if (t < best[1]) { best[1] = t; pick[1] = T; }
   }

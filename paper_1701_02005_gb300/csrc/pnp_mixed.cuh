@@ -62,8 +62,11 @@ cudaError_t build_rhs_maps(RhsMaps* m, const Fields<float>& f, const Shadows& sh
 // if a TMA copy does not complete within the kernel's wait limit.
 cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
                              const MetricsF& m, const CoefF& cf, const RhsMaps* maps, int* err, cudaStream_t s);
+// Wall-normal CN solves of substage l: the ion families and / or the velocity families.
+constexpr unsigned kCnIons = 1, kCnVelocity = 2;
 cudaError_t launch_mixed_cn(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
-                            const CNRowsF& cell, const CNRowsF& face, const CNRowsF& ion, int l, cudaStream_t s);
+                            const CNRowsF& cell, const CNRowsF& face, const CNRowsF& ion, int l, unsigned parts,
+                            cudaStream_t s);
 cudaError_t launch_plane_means3(const double* a, const double* b, const double* c, int nplanes, size_t P,
                                 double* oa, double* ob, double* oc, cudaStream_t s);
 cudaError_t launch_make_shadows(const double* cp, const double* cm, const double* Phi, const double* Hcp,
