@@ -342,27 +342,32 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Shared memory of the tile kernel (floats): tiles [4 slots][7 arrays][NT],
-// old H [3 slots][5 arrays][TX * TZ], then the per-plane table [jchunk][kPlaneLd].
-__host__ __device__ constexpr size_t rhs_tile_floats(int tx, int tz) {
-  return 4 * 7 * (size_t)(tx + 2) * (tz + 2) + 3 * 5 * (size_t)tx * tz;
+// Shared memory of the tile kernel (floats): tiles [4 slots][7 arrays][NT]
+// with NT = (TX + 2) (TZ CZ + 2), then (HSM) old H [3 slots][5 arrays][TX TZ],
+// then the per-plane table [jchunk][kPlaneLd].
+__host__ __device__ constexpr size_t rhs_tile_floats(int tx, int tz, int cz, bool hsm) {
+  return 4 * 7 * (size_t)(tx + 2) * (tz * cz + 2) + (hsm ? 3 * 5 * (size_t)tx * tz : 0);
 }
 
-template <int TX, int TZ>
-__global__ void __launch_bounds__(TX * TZ, 768 / (TX * TZ))
+// TX x TZ threads own a TX x (TZ CZ) tile of cells; each thread computes CZ
+// cells stacked in z.  HSM: the previous substage's H arrives by cp.async with
+// the planes (else each thread loads it at the top of the iteration).
+template <int TX, int TZ, int CZ, bool HSM>
+__global__ void __launch_bounds__(TX * TZ, (CZ == 1 ? 768 : 512) / (TX * TZ))
     k_rhs_mixed_tile(Fields<float> f, float* __restrict__ rcp, float* __restrict__ rcm, Shadows sh, MixedRefs R,
                      Geo g, MetricsF mt, CoefF cf, int jchunk) {
-  constexpr int TW = TX + 2, NT = TW * (TZ + 2), NTH = TX * TZ, E = (NT + NTH - 1) / NTH;
+  constexpr int TW = TX + 2, NT = TW * (TZ * CZ + 2), NTH = TX * TZ, E = (NT + NTH - 1) / NTH;
   extern __shared__ __align__(16) float rhs_smem[];
-  float* tiles = rhs_smem;                           // [4][NA][NT]
-  float* holds = rhs_smem + 4 * NA * NT;             // [3][NH][NTH]
-  float* pct = rhs_smem + rhs_tile_floats(TX, TZ);   // [jchunk][kPlaneLd]
+  float* tiles = rhs_smem;                                    // [4][NA][NT]
+  float* holds = rhs_smem + 4 * NA * NT;                      // [3][NH][NTH] (HSM)
+  float* pct = rhs_smem + rhs_tile_floats(TX, TZ, CZ, HSM);   // [jchunk][kPlaneLd]
   const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * TX + tx;
   const int nx = g.nx, nz = g.nz, nyc = g.nyc;
-  const int i0 = blockIdx.x * TX, k0 = blockIdx.y * TZ;
+  const int i0 = blockIdx.x * TX, k0 = blockIdx.y * (TZ * CZ);
   const int jb = blockIdx.z * jchunk, je = min(nyc, jb + jchunk);
   const size_t P = (size_t)nz * nx;
-  const size_t ck = (size_t)(k0 + tz) * nx + i0 + tx;   // in-plane offset of this thread's cell
+  // in-plane offset of this thread's first cell; the others are nx apart
+  const size_t ck = (size_t)(k0 + tz * CZ) * nx + i0 + tx;
 
   int off[E];   // in-plane offsets of this thread's tile elements (periodic in x and z)
 #pragma unroll
@@ -386,10 +391,12 @@ __global__ void __launch_bounds__(TX * TZ, 768 / (TX * TZ))
         for (int e = 0; e < E; ++e)
           if (tid + e * NTH < NT) cp_async4(ts + a * NT + tid + e * NTH, src[a] + qP + off[e]);
       }
-      if (q >= jb && q < je) {
-        float* hs = holds + (size_t)(q % 3) * NH * NTH;
+      if constexpr (HSM) {
+        if (q >= jb && q < je) {
+          float* hs = holds + (size_t)(q % 3) * NH * NTH;
 #pragma unroll
-        for (int h = 0; h < NH; ++h) cp_async4(hs + h * NTH + tid, hsrc[h] + qP + ck);
+          for (int h = 0; h < NH; ++h) cp_async4(hs + h * NTH + tid, hsrc[h] + qP + ck);
+        }
       }
     }
     cp_async_commit();
@@ -399,23 +406,46 @@ __global__ void __launch_bounds__(TX * TZ, 768 / (TX * TZ))
   issue_plane(jb + 1);
   fill_plane_table(pct, mt, R, cf.D, jb, je, jchunk, tid, NTH);
 
-  float ub, ut, wb, wt;
-  wall_values(f, P, ck, cf.Uw, ub, ut, wb, wt);
-  const CellK kc = cell_consts(cf, ub, ut, wb, wt);
-  const int c = (tz + 1) * TW + tx + 1;
-  YCarry cy{0.f, 0.f, 0.f, 0.f, 0.f};
+  CellK kc[CZ];
+#pragma unroll
+  for (int cz = 0; cz < CZ; ++cz) {
+    float ub, ut, wb, wt;
+    wall_values(f, P, ck + (size_t)cz * nx, cf.Uw, ub, ut, wb, wt);
+    kc[cz] = cell_consts(cf, ub, ut, wb, wt);
+  }
+  const int c = (tz * CZ + 1) * TW + tx + 1;   // first cell in a tile
+  YCarry cy[CZ];
+#pragma unroll
+  for (int cz = 0; cz < CZ; ++cz) cy[cz] = YCarry{0.f, 0.f, 0.f, 0.f, 0.f};
   for (int j = jb; j < je; ++j) {
+    const size_t c0 = (size_t)j * P + ck;
+    float Ho[CZ][5];
+    if constexpr (!HSM) {
+#pragma unroll
+      for (int cz = 0; cz < CZ; ++cz) {
+        const size_t o = c0 + (size_t)cz * nx;
+#pragma unroll
+        for (int h = 0; h < NH; ++h) Ho[cz][h] = __ldg(hsrc[h] + o);
+      }
+    }
     issue_plane(j + 2);
     cp_async_wait_all_but_one();   // planes up to j + 1 have landed (this thread's copies)
     __syncthreads();               // ... and every thread's (and the plane table)
+    if constexpr (HSM) {
+      const float* hs = holds + (size_t)(j % 3) * NH * NTH + tid;
+#pragma unroll
+      for (int h = 0; h < NH; ++h) Ho[0][h] = hs[h * NTH];
+    }
     const float* bm = tiles + (size_t)((j + 3) & 3) * NA * NT + c;
     const float* bo = tiles + (size_t)(j & 3) * NA * NT + c;
     const float* bp = tiles + (size_t)((j + 1) & 3) * NA * NT + c;
-    const float* hs = holds + (size_t)(j % 3) * NH * NTH + tid;
-    const float Ho[5] = {hs[0], hs[NTH], hs[2 * NTH], hs[3 * NTH], hs[4 * NTH]};
     const PlaneC q = plane_consts(pct + (size_t)(j - jb) * kPlaneLd);
-    const CellOut o = rhs_cell_at<NT, TW>(j, jb, nyc, bm, bo, bp, Ho, q, kc, cy);
-    store_cell(f, rcp, rcm, sh, (size_t)j * P + ck, j > 0, o);
+#pragma unroll
+    for (int cz = 0; cz < CZ; ++cz) {
+      const CellOut o =
+          rhs_cell_at<NT, TW>(j, jb, nyc, bm + cz * TW, bo + cz * TW, bp + cz * TW, Ho[cz], q, kc[cz], cy[cz]);
+      store_cell(f, rcp, rcm, sh, c0 + (size_t)cz * nx, j > 0, o);
+    }
     __syncthreads();
   }
 }
@@ -699,17 +729,13 @@ cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const Mi
       default: return go(k_rhs_mixed_tma<256, 2>, TmaGeo<256, 2>{}, 2);
     }
   }
-  // tile width: 32 or 16, at most nx; TZ = 8 when nz allows and the tile is
-  // wide, else 4 (nx, nz are powers of two >= 4)
-  int tx = g.lc_rhs_bx == 16 ? 16 : 32;
-  if (tx > g.nx) tx = g.nx;
-  if (g.nz < 8 && tx > 8) tx = 8;
-  const int tz = tx >= 16 ? 8 : 4;
-  const int nxz = (g.nx / tx) * (g.nz / tz);
-  const int jc = chunk(nxz, 3 * 256 / (tx * tz));
-  const dim3 grd((unsigned)(g.nx / tx), (unsigned)(g.nz / tz), (unsigned)((g.nyc + jc - 1) / jc));
-  auto go = [&](auto kern, int bx, int bz) {
-    const size_t smem = sizeof(float) * (rhs_tile_floats(bx, bz) + (size_t)kPlaneLd * jc);
+  // cp.async tiles.  lc_rhs_bx: 0 / 32 = 32 x 8 threads with two cells each in z,
+  // 16 = 32 x 8 threads with one cell each; narrower grids fall back to 8 x 4 / 4 x 4
+  auto go = [&](auto kern, int bx, int bz, int cz, bool hsm, int per_sm) {
+    const int nxz = (g.nx / bx) * (g.nz / (bz * cz));
+    const int jc = chunk(nxz, per_sm);
+    const dim3 grd((unsigned)(g.nx / bx), (unsigned)(g.nz / (bz * cz)), (unsigned)((g.nyc + jc - 1) / jc));
+    const size_t smem = sizeof(float) * (rhs_tile_floats(bx, bz, cz, hsm) + (size_t)kPlaneLd * jc);
     if (smem > 48 * 1024) {
       const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
@@ -717,12 +743,10 @@ cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const Mi
     kern<<<grd, dim3(bx, bz), smem, s>>>(f, rp, rm, sh, R, g, m, cf, jc);
     return cudaGetLastError();
   };
-  switch (tx) {
-    case 32: return go(k_rhs_mixed_tile<32, 8>, 32, 8);
-    case 16: return go(k_rhs_mixed_tile<16, 8>, 16, 8);
-    case 8: return go(k_rhs_mixed_tile<8, 4>, 8, 4);
-    default: return go(k_rhs_mixed_tile<4, 4>, 4, 4);
-  }
+  if (g.nx >= 32 && g.nz >= 16 && g.lc_rhs_bx != 16) return go(k_rhs_mixed_tile<32, 8, 2, false>, 32, 8, 2, false, 2);
+  if (g.nx >= 32 && g.nz >= 8) return go(k_rhs_mixed_tile<32, 8, 1, true>, 32, 8, 1, true, 3);
+  if (g.nx >= 8) return go(k_rhs_mixed_tile<8, 4, 1, true>, 8, 4, 1, true, 24);
+  return go(k_rhs_mixed_tile<4, 4, 1, true>, 4, 4, 1, true, 48);
 }
 
 }  // namespace pnp

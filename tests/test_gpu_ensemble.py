@@ -69,4 +69,13 @@ def test_autotuned_shapes_do_not_change_results(prec, tmp_path):
         runs.append({n: s.get(n) for n in ("u", "v", "w", "cp", "Phi")})
         s.close()
     for n in runs[0]:
-        assert np.array_equal(runs[0][n], runs[1][n]), n
+        if prec == 0:
+            # FP64: launch shapes only regroup the same operations
+            assert np.array_equal(runs[0][n], runs[1][n]), n
+        else:
+            # mixed: the stencil candidates are different kernels over the same
+            # per-cell routine; FMA contraction may round the last FP32 bit
+            # differently, so the results agree to FP32 rounding of the O(1)
+            # fields (wall speed 1, concentrations ~1), not bitwise
+            a, b = runs[0][n], runs[1][n]
+            assert np.max(np.abs(a - b)) <= 1e-6 * max(1.0, np.max(np.abs(b))), n
