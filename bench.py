@@ -53,8 +53,11 @@ NCU_TRAFFIC = {
 }
 
 
-def site_cost(site, precision):
+def site_cost(site, precision, launch_cfg=None):
     half = (WL["nx"] // 2 + 1) / WL["nx"]
+    # mixed CN: the shared-memory line tiles (launch code 0 / 32) keep the forward
+    # elimination values on chip (76 B per cell); the line kernels write and re-read them (116 B)
+    cn_tiled = launch_cfg is None or launch_cfg[1] in (0, 32)
     if precision == "fp64":
         table = {
             "rhs": (176, 220), "cn_thomas": (200, 20),
@@ -65,7 +68,7 @@ def site_cost(site, precision):
         }
     else:
         table = {
-            "rhs": (88, 0), "cn_thomas": (116, 0),
+            "rhs": (88, 0), "cn_thomas": (76 if cn_tiled else 116, 0),
             "p_fftx": (12 + 8 * half, 0), "p_fftz": (16 * half, 0), "p_thomas": (64 * half, 0),
             "p_ifftz": (16 * half, 0), "p_ifftx": (8 * half + 4, 0), "project": (36, 0),
             "e_fftx": (8 + 8 * half, 0), "e_fftz": (16 * half, 0), "e_thomas": (64 * half, 0),
@@ -362,13 +365,13 @@ def run_ours(args):
     hbm_src = "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
     sites = {}
     for k, v in per_launch.items():
-        cst = site_cost(k, pname)
+        cst = site_cost(k, pname, launch_cfg)
         d = v * 1e-3
         gbs = cst["bytes"] * n_cells / d / 1e9
         tf = 2.0 * cst["fp64_ops"] * n_cells / d / 1e12   # FP64 ops counted as FMA-equivalent flops
         sites[k] = {"ms": round(v, 4), "share": round(v / total, 4), "hbm_frac": round(gbs / hbm_peak, 4),
                     "fp64_frac": round(tf / (fp64_peak / 1e12), 4)}
-    cst = site_cost(dom, pname)
+    cst = site_cost(dom, pname, launch_cfg)
     dur = per_launch[dom] * 1e-3
     hbm_gbs = cst["bytes"] * n_cells / dur / 1e9
     alu_tf = 2.0 * cst["fp64_ops"] * n_cells / dur / 1e12

@@ -139,6 +139,120 @@ __global__ void k_cn_vel_f32(float* __restrict__ u, float* __restrict__ ru, floa
 }
 
 // ---------------------------------------------------------------------------
+// Wall-normal CN solves with the right-hand sides in shared memory.  A block
+// (one warp) owns 32 consecutive lines of one family.  The whole column block
+// r[0..n)[32] arrives by 16-byte cp.async (every row in flight at once) and the
+// forward elimination overwrites it with d in shared memory; the back
+// substitution streams the state through a two-chunk ring of 16 planes (also
+// cp.async, the first two chunks landing during the forward sweep) and writes
+// it back with coalesced stores.  Against the line kernels above this drops
+// the write and re-read of d in HBM (8 of the 20 / 28 bytes per cell of a
+// velocity / ion family) and keeps ~7 warps' worth of rows in flight per SM.
+// ---------------------------------------------------------------------------
+struct CnFamily {
+  const float* r;       // right-hand side at the family's first plane
+  float* q0;            // state (velocity, or the high part S of an ion fluctuation)
+  float* q1;            // low part L of an ion fluctuation (ion families)
+  const float2* add;    // per-plane reference increment dC_ref (ion families)
+  CNRowsF rows;
+  int n;                // line length
+};
+struct CnTileArgs {
+  CnFamily f[3];
+  size_t P;
+};
+
+constexpr int kCnChunk = 16;   // planes per state chunk of the back substitution
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+
+// Shared memory (floats): d [n][32], state ring [2][NS][kCnChunk][32],
+// factors a, m, c [n] each, then (ions) dC_ref [n] float2.
+__host__ __device__ inline size_t cn_tile_floats(int n, int ns) {
+  return (size_t)n * 32 + 2 * (size_t)ns * kCnChunk * 32 + 3 * (size_t)n + (n & 1) + (ns == 2 ? 2 * (size_t)n : 0);
+}
+
+// NS = state arrays per family: 1 (velocity) or 2 (ions, double-float update).
+template <int NS>
+__global__ void __launch_bounds__(32) k_cn_tile(CnTileArgs args) {
+  extern __shared__ __align__(16) float cn_smem[];
+  const CnFamily& F = args.f[blockIdx.y];
+  const int n = F.n, t = threadIdx.x;
+  const size_t P = args.P, line0 = (size_t)blockIdx.x * 32;
+  float* sr = cn_smem;                                    // [n][32]: r, then d
+  float* ring = sr + (size_t)n * 32;                      // [2][NS][kCnChunk][32]
+  float* ca = ring + 2 * NS * kCnChunk * 32;              // [n] sub-diagonal factor a
+  float* cm = ca + n;                                     // [n] 1 / pivot
+  float* cc = cm + n;                                     // [n] c'
+  float2* cadd = reinterpret_cast<float2*>(cc + n + (n & 1));   // [n] (ions)
+  const int nchunks = (n + kCnChunk - 1) / kCnChunk;
+  // chunk k of the back substitution: planes [hi - kCnChunk, hi), hi = n - k kCnChunk
+  auto issue_chunk = [&](int k) {
+    if (k < nchunks) {
+      const int hi = n - k * kCnChunk, lo = max(0, hi - kCnChunk);
+      float* buf = ring + (size_t)(k & 1) * NS * kCnChunk * 32;
+      for (int e = t; e < (hi - lo) * 8; e += 32) {
+        const int jj = e >> 3, c4 = (e & 7) * 4, j = hi - 1 - jj;
+        cp_async16(buf + jj * 32 + c4, F.q0 + (size_t)j * P + line0 + c4);
+        if constexpr (NS == 2) cp_async16(buf + kCnChunk * 32 + jj * 32 + c4, F.q1 + (size_t)j * P + line0 + c4);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  for (int e = t; e < n * 8; e += 32) {
+    const int j = e >> 3, c4 = (e & 7) * 4;
+    cp_async16(sr + j * 32 + c4, F.r + (size_t)j * P + line0 + c4);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  issue_chunk(0);
+  issue_chunk(1);
+  for (int j = t; j < n; j += 32) {
+    ca[j] = F.rows.a[j];
+    cm[j] = F.rows.m[j];
+    cc[j] = F.rows.c[j];
+    if constexpr (NS == 2) cadd[j] = F.add[j];
+  }
+  asm volatile("cp.async.wait_group 2;" ::: "memory");   // r has landed (this lane's copies)
+  __syncwarp();                                         // ... and every lane's, with the factors
+  float d = 0.f;
+#pragma unroll 8
+  for (int j = 0; j < n; ++j) {
+    d = (sr[j * 32 + t] - ca[j] * d) * cm[j];
+    sr[j * 32 + t] = d;
+  }
+  float x = 0.f;
+  for (int k = 0; k < nchunks; ++k) {
+    asm volatile("cp.async.wait_group 1;" ::: "memory");   // chunk k has landed
+    __syncwarp();
+    const float* buf = ring + (size_t)(k & 1) * NS * kCnChunk * 32;
+    const int hi = n - k * kCnChunk, lo = max(0, hi - kCnChunk);
+#pragma unroll 4
+    for (int j = hi - 1; j >= lo; --j) {
+      const int jj = hi - 1 - j;
+      x = sr[j * 32 + t] - cc[j] * x;
+      float* q0 = F.q0 + (size_t)j * P + line0 + t;
+      if constexpr (NS == 1) {
+        *q0 = buf[jj * 32 + t] + x;
+      } else {
+        const float2 inc = cadd[j];
+        const dfl v = df_add2(dfl{buf[jj * 32 + t], buf[kCnChunk * 32 + jj * 32 + t]}, dfl{inc.x, inc.y}, x);
+        *q0 = v.h;
+        F.q1[(size_t)j * P + line0 + t] = v.l;
+      }
+    }
+    __syncwarp();          // every lane is done with this buffer
+    issue_chunk(k + 2);    // into the buffer just consumed
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+size_t cn_tile_smem(int n, int ns) { return sizeof(float) * cn_tile_floats(n, ns); }
+
+
+// ---------------------------------------------------------------------------
 // Reference profiles: deterministic FP64 plane means (one block per plane).
 // ---------------------------------------------------------------------------
 __global__ void k_plane_means3(const double* __restrict__ a, const double* __restrict__ b,
@@ -211,7 +325,42 @@ cudaError_t launch_mixed_cn(const Fields<float>& f, const Shadows& sh, const Mix
                             const CNRowsF& cell, const CNRowsF& face, const CNRowsF& ion, int l, unsigned parts,
                             cudaStream_t s) {
   const size_t P = (size_t)g.nz * g.nx;
-  const int T = g.lc_cn ? g.lc_cn : 128;
+  // shared-memory line tiles (the default, and lc_cn 32) when 32 lines divide a
+  // plane and a column block fits; lc_cn 64 / 128 / 256: one thread per line
+  const bool tiled = (g.lc_cn == 0 || g.lc_cn == 32) && P % 32 == 0 && cn_tile_smem(g.nyc, 2) <= 227 * 1024;
+  if (tiled) {
+    const dim3 blk(32);
+    if (parts & kCnIons) {
+      CnTileArgs a{};
+      a.P = P;
+      a.f[0] = CnFamily{reinterpret_cast<const float*>(f.rcp), sh.cp, sh.cpL, R.dC_p + (size_t)l * g.nyc, ion, g.nyc};
+      a.f[1] = CnFamily{reinterpret_cast<const float*>(f.rcm), sh.cm, sh.cmL, R.dC_m + (size_t)l * g.nyc, ion, g.nyc};
+      const size_t smem = cn_tile_smem(g.nyc, 2);
+      if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_cn_tile<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+      }
+      k_cn_tile<2><<<dim3((unsigned)(P / 32), 2), blk, smem, s>>>(a);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    if (parts & kCnVelocity) {
+      CnTileArgs a{};
+      a.P = P;
+      a.f[0] = CnFamily{f.ru, f.u, nullptr, nullptr, cell, g.nyc};
+      a.f[1] = CnFamily{f.rv + P, f.v + P, nullptr, nullptr, face, g.nyc - 1};   // interior faces 1 .. nyc-1
+      a.f[2] = CnFamily{f.rw, f.w, nullptr, nullptr, cell, g.nyc};
+      const size_t smem = cn_tile_smem(g.nyc, 1);
+      if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_cn_tile<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+      }
+      k_cn_tile<1><<<dim3((unsigned)(P / 32), 3), blk, smem, s>>>(a);
+      return cudaGetLastError();
+    }
+    return cudaSuccess;
+  }
+  const int T = g.lc_cn > 32 ? g.lc_cn : 128;
   if (parts & kCnIons) {
     dim3 grd2((unsigned)((P + T - 1) / T), 2, 1);
     k_cn_ion_mixed<<<grd2, T, 0, s>>>(reinterpret_cast<float*>(f.rcp), sh.cp, sh.cpL,

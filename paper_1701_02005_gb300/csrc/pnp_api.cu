@@ -1294,7 +1294,7 @@ int pnp_autotune(pnp_ctx* c, double dt, int* cfg_out, double* ms_out) {
   }
   c->g.lc_rhs_bx = pick[0];
   // 2: CN sweep block size
-  for (int T : {64, 128, 256}) {
+  for (int T : {32, 64, 128, 256}) {   // mixed: 32 = shared-memory line tiles
     c->g.lc_cn = T;
     float t = time_launches(c, [&] {
       if (c->precision == PNP_FP64)

@@ -31,7 +31,7 @@ struct Geo {
   // launch shapes chosen by the autotuner (0 = built-in default)
   int lc_rhs_bx;         // FP64 stencil: x-extent of the 128-thread blocks (16, 32, 64, 128);
                          // mixed stencil: 128 TMA rows x2, 64 TMA rows x1, 32 / 16 cp.async tiles
-  int lc_cn;             // threads per block of the wall-normal CN sweeps
+  int lc_cn;             // threads per block of the wall-normal CN sweeps (mixed: 0 / 32 = shared-memory line tiles)
   int lc_spec;           // threads per block of the spectral y-solves
   int lc_fftz_ty;        // threads per column of the z-transform (cap)
 };
