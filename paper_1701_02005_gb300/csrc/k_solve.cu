@@ -708,9 +708,77 @@ __global__ void k_project(T* __restrict__ u, T* __restrict__ v, T* __restrict__ 
   if (update_p) p[c] = p[c] + s0;
 }
 
+// FP32 projection for x-rows of 128 cells: a warp owns 128 consecutive x-cells
+// (a float4 per lane) of one z-row and marches a chunk of y-planes, carrying
+// Phi_p of the plane below in registers; the x-neighbour of a lane's first cell
+// is the previous lane's last (a shuffle; lane 0 wraps or loads it).
+__global__ void __launch_bounds__(128) k_project_rows(float* __restrict__ u, float* __restrict__ v,
+                                                     float* __restrict__ w, float* __restrict__ p,
+                                                     const float* __restrict__ s, float cx, float cz, float sc,
+                                                     const float* __restrict__ ih, bool update_p, Geo g, int jchunk) {
+  const int lane = threadIdx.x, nx = g.nx, nz = g.nz;
+  const int i0 = blockIdx.x * 128 + lane * 4;
+  const int k = blockIdx.y * blockDim.y + threadIdx.y;
+  const int jb = blockIdx.z * jchunk, je = min(g.nyc, jb + jchunk);
+  const int km = k ? k - 1 : nz - 1;
+  const size_t P = (size_t)nz * nx;
+  const size_t row = (size_t)k * nx + i0, rowm = (size_t)km * nx + i0;
+  // wrapped x-neighbour of the warp's first cell
+  const size_t xwrap = (size_t)k * nx + (blockIdx.x == 0 ? nx - 1 : blockIdx.x * 128 - 1);
+  float4 sb = make_float4(0.f, 0.f, 0.f, 0.f);   // Phi_p of plane j - 1
+  if (jb > 0) sb = *reinterpret_cast<const float4*>(s + (size_t)(jb - 1) * P + row);
+  for (int j = jb; j < je; ++j) {
+    const size_t o = (size_t)j * P;
+    const float4 s0 = *reinterpret_cast<const float4*>(s + o + row);
+    const float4 sz = *reinterpret_cast<const float4*>(s + o + rowm);
+    float sx = __shfl_up_sync(0xffffffffu, s0.w, 1);
+    if (lane == 0) sx = s[o + xwrap];
+    float4 uu = *reinterpret_cast<const float4*>(u + o + row);
+    float4 ww = *reinterpret_cast<const float4*>(w + o + row);
+    uu.x -= cx * (s0.x - sx);
+    uu.y -= cx * (s0.y - s0.x);
+    uu.z -= cx * (s0.z - s0.y);
+    uu.w -= cx * (s0.w - s0.z);
+    ww.x -= cz * (s0.x - sz.x);
+    ww.y -= cz * (s0.y - sz.y);
+    ww.z -= cz * (s0.z - sz.z);
+    ww.w -= cz * (s0.w - sz.w);
+    *reinterpret_cast<float4*>(u + o + row) = uu;
+    *reinterpret_cast<float4*>(w + o + row) = ww;
+    if (j > 0) {
+      const float hj = ih[j];
+      float4 vv = *reinterpret_cast<const float4*>(v + o + row);
+      vv.x -= sc * (s0.x - sb.x) * hj;
+      vv.y -= sc * (s0.y - sb.y) * hj;
+      vv.z -= sc * (s0.z - sb.z) * hj;
+      vv.w -= sc * (s0.w - sb.w) * hj;
+      *reinterpret_cast<float4*>(v + o + row) = vv;
+    }
+    if (update_p) {
+      float4 pp = *reinterpret_cast<const float4*>(p + o + row);
+      pp.x += s0.x;
+      pp.y += s0.y;
+      pp.z += s0.z;
+      pp.w += s0.w;
+      *reinterpret_cast<float4*>(p + o + row) = pp;
+    }
+    sb = s0;
+  }
+}
+
 template <typename T>
 cudaError_t launch_project(T* u, T* v, T* w, T* p, const T* phip, double scale, bool update_p, const Geo& g,
                            const T* ih, cudaStream_t s) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (g.nx % 128 == 0 && g.nz % 4 == 0) {
+      // y-chunks of about 16 planes: enough blocks to fill the GPU several times
+      const int nch = (g.nyc + 15) / 16, jc = (g.nyc + nch - 1) / nch;
+      const dim3 grd((unsigned)(g.nx / 128), (unsigned)(g.nz / 4), (unsigned)((g.nyc + jc - 1) / jc));
+      k_project_rows<<<grd, dim3(32, 4), 0, s>>>(u, v, w, p, phip, (float)(scale * g.idx), (float)(scale * g.idz),
+                                                 (float)scale, ih, update_p, g, jc);
+      return cudaGetLastError();
+    }
+  }
   dim3 blk(32, 4, 1);
   dim3 grd((g.nx + 31) / 32, (g.nz + 3) / 4, g.nyc);
   k_project<T><<<grd, blk, 0, s>>>(u, v, w, p, phip, (T)(scale * g.idx), (T)(scale * g.idz), (T)scale, ih, update_p, g);
