@@ -13,6 +13,7 @@
 // no normalisation; the spectral solve multiplies by 1/(Nx Nz).
 #include "pnp_common.cuh"
 #include "pnp_df.cuh"
+#include "pnp_regfft.cuh"
 
 namespace pnp {
 
@@ -342,8 +343,88 @@ __global__ void k_fft_z(cplx<T>* __restrict__ spec, const cplx<T>* __restrict__ 
   for (int n = threadIdx.y; n < nz; n += blockDim.y) plane[(size_t)n * g.mp + m] = Z[n];
 }
 
+// FP32 z-transform with the two-pass register FFT (pnp_regfft.cuh): a block
+// owns TM consecutive m-columns of one y-plane; thread (tm, g) loads the
+// samples n = g + G r of column tm (TM-wide coalesced rows), does the R1-point
+// DFT in registers, multiplies by W_N^{g k1} and exchanges through shared
+// memory; thread g then does the G-point DFTs of its R1 / G values of k1 and
+// stores X[k1 + R1 k2].
+template <int N, int R1, int TM, bool INV>
+__global__ void __launch_bounds__(TM*(N / R1)) k_fft_z_reg(cplx<float>* __restrict__ spec,
+                                                           const cplx<float>* __restrict__ tw, Geo g) {
+  constexpr int G = N / R1, PER = R1 / G;
+  static_assert(R1 % G == 0, "each thread takes whole G-point transforms");
+  extern __shared__ __align__(16) float fz_smem[];
+  cplx<float>* xs = reinterpret_cast<cplx<float>*>(fz_smem);   // [TM][N + 1] (padded against bank conflicts)
+  cplx<float>* twl = xs + TM * (N + 1);                          // [N]
+  const int tm = threadIdx.x, gi = threadIdx.y, tid = gi * TM + tm;
+  for (int e = tid; e < N; e += TM * G) {
+    cplx<float> t = tw[e];
+    if (INV) t.y = -t.y;
+    twl[e] = t;
+  }
+  const int m = blockIdx.x * TM + tm;
+  const bool live = m < g.mh;
+  cplx<float>* col = spec + (size_t)blockIdx.y * N * g.mp + (live ? m : 0);
+  cplx<float> v[R1];
+#pragma unroll
+  for (int r = 0; r < R1; ++r) v[r] = live ? col[(size_t)(gi + G * r) * g.mp] : cplx<float>{0.f, 0.f};
+  __syncthreads();   // the twiddle table
+  rfft::dft<INV, R1>(v);
+  cplx<float>* xm = xs + tm * (N + 1);
+  rfft::static_for<0, R1>([&](auto kc) {
+    constexpr int k1 = decltype(kc)::value;
+    xm[k1 * G + gi] = cmul(v[rfft::bitrev(k1, R1)], twl[gi * k1]);
+  });
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int k1 = gi * PER + p;
+    cplx<float> w[G];
+#pragma unroll
+    for (int q = 0; q < G; ++q) w[q] = xm[k1 * G + q];
+    rfft::dft<INV, G>(w);
+    if (live) {
+      rfft::static_for<0, G>([&](auto kc) {
+        constexpr int k2 = decltype(kc)::value;
+        col[(size_t)(k1 + R1 * k2) * g.mp] = w[rfft::bitrev(k2, G)];
+      });
+    }
+  }
+}
+
+template <int N, int R1, int TM>
+cudaError_t launch_fft_z_reg(cplx<float>* spec, const cplx<float>* tw, const Geo& g, bool inverse, cudaStream_t s) {
+  constexpr int G = N / R1;
+  const size_t smem = sizeof(cplx<float>) * ((size_t)TM * (N + 1) + N);
+  const dim3 grd((unsigned)((g.mh + TM - 1) / TM), (unsigned)g.nyc);
+  auto go = [&](auto kern) {
+    if (smem > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<grd, dim3(TM, G), smem, s>>>(spec, tw, g);
+    return cudaGetLastError();
+  };
+  return inverse ? go(k_fft_z_reg<N, R1, TM, true>) : go(k_fft_z_reg<N, R1, TM, false>);
+}
+
 template <typename T>
 cudaError_t launch_fft_z(cplx<T>* spec, const cplx<T>* tw_z, const Geo& g, bool inverse, cudaStream_t s) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    // register transforms for 16 <= Nz <= 512 unless the stage-by-stage kernel is asked for
+    if (g.lc_fftz_ty != 64) {
+      switch (g.nz) {
+        case 16: return launch_fft_z_reg<16, 4, 32>(spec, tw_z, g, inverse, s);
+        case 32: return launch_fft_z_reg<32, 8, 32>(spec, tw_z, g, inverse, s);
+        case 64: return launch_fft_z_reg<64, 8, 32>(spec, tw_z, g, inverse, s);
+        case 128: return launch_fft_z_reg<128, 16, 32>(spec, tw_z, g, inverse, s);
+        case 256: return launch_fft_z_reg<256, 16, 16>(spec, tw_z, g, inverse, s);
+        case 512: return launch_fft_z_reg<512, 32, 8>(spec, tw_z, g, inverse, s);
+        default: break;
+      }
+    }
+  }
   int TM = (int)(128 / sizeof(cplx<T>));   // one 128-byte segment of each z-row
   while (TM > 1 && (size_t)2 * TM * (g.nz + 1) * sizeof(cplx<T>) > 200 * 1024) TM >>= 1;
   int ty = g.nz / 4;
