@@ -217,6 +217,193 @@ __global__ void k_fft_x_fwd(SrcArgs<T, TV> src, Geo g, Metrics m, cplx<T>* __res
   }
 }
 
+// FP32 real x-transforms with the two-pass register FFT (pnp_regfft.cuh) of
+// the half-length complex sequence z_t = x_2t + i x_2t+1.  G = NH / R1 threads
+// own a row (consecutive lanes of one warp, so every exchange inside a row
+// needs only a warp barrier); ROWS rows per block.
+//
+// Forward: thread g forms z_t for t = g + G r from the source, does the
+// R1-point DFT, twiddles, exchanges, does its G-point DFTs, writes Z to the
+// row buffer in natural order, and the row's threads split the real-FFT
+// post-processing X_m = E_m + W_N^m O_m over m = 0 .. NH.
+template <int NH, int R1, typename TV>
+__global__ void __launch_bounds__(256) k_fft_x_fwd_reg(SrcArgs<float, TV> src, Geo g, Metrics mt,
+                                                       cplx<float>* __restrict__ spec,
+                                                       const cplx<float>* __restrict__ tw_half,
+                                                       const cplx<float>* __restrict__ tw_post) {
+  constexpr int G = NH / R1, PER = R1 / G;
+  static_assert(R1 % G == 0 && 32 % G == 0, "row of whole transforms inside one warp");
+  extern __shared__ __align__(16) float fx_smem[];
+  cplx<float>* twh = reinterpret_cast<cplx<float>*>(fx_smem);   // [NH]
+  cplx<float>* twp = twh + NH;                                   // [NH + 1]
+  cplx<float>* rows = twp + NH + 1;                              // [ROWS][NH + 1]
+  const int gi = threadIdx.x, ry = threadIdx.y, tid = ry * G + gi;
+  const int nthr = G * blockDim.y;
+  for (int e = tid; e < NH; e += nthr) twh[e] = tw_half[e];
+  for (int e = tid; e <= NH; e += nthr) twp[e] = tw_post[e];
+  const int nrows = g.nyc * g.nz;
+  const int row = blockIdx.x * blockDim.y + ry;
+  const bool live = row < nrows;
+  const int j = live ? row / g.nz : 0, k = live ? row % g.nz : 0;
+  cplx<float> v[R1];
+  const size_t rbase = ((size_t)j * g.nz + k) * g.nx;   // this row's first cell
+  if (live && src.kind == PoissonSrc::Divergence) {
+    // both samples of z_t from float2 loads: x-faces 2t, 2t+1, 2t+2 (periodic),
+    // v on the faces below / above, w on the z-faces k, k+1
+    const size_t P = (size_t)g.nz * g.nx;
+    const int kp = (k + 1 == g.nz) ? 0 : k + 1;
+    const size_t rbp = ((size_t)j * g.nz + kp) * g.nx;
+    const float sy = src.idyT[j] * src.ss;
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      const int i = 2 * (gi + G * r);
+      const float2 u01 = *reinterpret_cast<const float2*>(src.u + rbase + i);
+      const float u2 = src.u[rbase + (i + 2 == g.nx ? 0 : i + 2)];
+      const float2 vb = *reinterpret_cast<const float2*>(src.v + rbase + i);
+      const float2 vt = *reinterpret_cast<const float2*>(src.v + rbase + P + i);
+      const float2 wk = *reinterpret_cast<const float2*>(src.w + rbase + i);
+      const float2 wkp = *reinterpret_cast<const float2*>(src.w + rbp + i);
+      v[r] = {(u01.y - u01.x) * src.sx + (vt.x - vb.x) * sy + (wkp.x - wk.x) * src.sz,
+              (u2 - u01.y) * src.sx + (vt.y - vb.y) * sy + (wkp.y - wk.y) * src.sz};
+    }
+  } else if (live && src.kind == PoissonSrc::ChargeShadow) {
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      const int i = 2 * (gi + G * r);
+      const float2 a = *reinterpret_cast<const float2*>(src.sa + rbase + i);
+      const float2 b = *reinterpret_cast<const float2*>(src.sb + rbase + i);
+      v[r] = {(-(a.x - b.x)) * src.ss, (-(a.y - b.y)) * src.ss};
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      const int t = gi + G * r;
+      v[r] = live ? cplx<float>{src_value(src, g, mt, j, k, 2 * t), src_value(src, g, mt, j, k, 2 * t + 1)}
+                  : cplx<float>{0.f, 0.f};
+    }
+  }
+  __syncthreads();   // twiddle tables
+  rfft::dft<false, R1>(v);
+  cplx<float>* xr = rows + (size_t)ry * (NH + 1);
+  rfft::static_for<0, R1>([&](auto kc) {
+    constexpr int k1 = decltype(kc)::value;
+    xr[k1 * G + gi] = cmul(v[rfft::bitrev(k1, R1)], twh[gi * k1]);
+  });
+  __syncwarp();
+  cplx<float> w[PER][G];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int k1 = gi * PER + p;
+#pragma unroll
+    for (int q = 0; q < G; ++q) w[p][q] = xr[k1 * G + q];
+    rfft::dft<false, G>(w[p]);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int k1 = gi * PER + p;
+    rfft::static_for<0, G>([&](auto kc) {
+      constexpr int k2 = decltype(kc)::value;
+      xr[k1 + R1 * k2] = w[p][rfft::bitrev(k2, G)];
+    });
+  }
+  __syncwarp();
+  if (!live) return;
+  cplx<float>* out = spec + (size_t)row * g.mp;
+  for (int mm = gi; mm <= NH; mm += G) {
+    const cplx<float> zm = xr[mm == NH ? 0 : mm];
+    const cplx<float> zc = cconj(xr[mm == 0 ? 0 : NH - mm]);
+    const cplx<float> E = {0.5f * (zm.x + zc.x), 0.5f * (zm.y + zc.y)};
+    const cplx<float> dd = csub(zm, zc);
+    const cplx<float> O = {0.5f * dd.y, -0.5f * dd.x};   // (zm - zc) / (2i)
+    out[mm] = cadd(E, cmul(twp[mm], O));
+  }
+}
+
+// Inverse: thread g forms the pre-processed z_t (from X_t and conj X_{NH-t})
+// for t = g + G r straight from the spectrum, runs the inverse transform and
+// writes x_2t, x_2t+1 of t = k1 + R1 k2.
+template <int NH, int R1, typename TO>
+__global__ void __launch_bounds__(256) k_fft_x_inv_reg(PoissonDst dst, const cplx<float>* __restrict__ spec, Geo g,
+                                                       Metrics mt, const cplx<float>* __restrict__ tw_half,
+                                                       const cplx<float>* __restrict__ tw_post, double V,
+                                                       TO* __restrict__ out, const double* __restrict__ plane_add) {
+  constexpr int G = NH / R1, PER = R1 / G;
+  static_assert(R1 % G == 0 && 32 % G == 0, "row of whole transforms inside one warp");
+  extern __shared__ __align__(16) float fx_smem[];
+  cplx<float>* twh = reinterpret_cast<cplx<float>*>(fx_smem);   // [NH] (conjugated)
+  cplx<float>* twp = twh + NH;                                   // [NH]
+  cplx<float>* rows = twp + NH;                                  // [ROWS][NH + 1]
+  const int gi = threadIdx.x, ry = threadIdx.y, tid = ry * G + gi;
+  const int nthr = G * blockDim.y;
+  for (int e = tid; e < NH; e += nthr) {
+    const cplx<float> a = tw_half[e];
+    twh[e] = {a.x, -a.y};
+    twp[e] = tw_post[e];
+  }
+  const int nrows = g.nyc * g.nz;
+  const int row = blockIdx.x * blockDim.y + ry;
+  const bool live = row < nrows;
+  const cplx<float>* in = spec + (size_t)(live ? row : 0) * g.mp;
+  __syncthreads();   // twiddle tables
+  cplx<float> v[R1];
+#pragma unroll
+  for (int r = 0; r < R1; ++r) {
+    const int t = gi + G * r;
+    cplx<float> z = {0.f, 0.f};
+    if (live) {
+      const cplx<float> Xm = in[t];
+      const cplx<float> Xc = cconj(in[NH - t]);
+      const cplx<float> sum = cadd(Xm, Xc);
+      const cplx<float> dif = csub(Xm, Xc);
+      const cplx<float> tt = cmul(cconj(twp[t]), dif);
+      z = {sum.x - tt.y, sum.y + tt.x};   // sum + i * tt
+    }
+    v[r] = z;
+  }
+  rfft::dft<true, R1>(v);
+  cplx<float>* xr = rows + (size_t)ry * (NH + 1);
+  rfft::static_for<0, R1>([&](auto kc) {
+    constexpr int k1 = decltype(kc)::value;
+    xr[k1 * G + gi] = cmul(v[rfft::bitrev(k1, R1)], twh[gi * k1]);
+  });
+  __syncwarp();
+  if (!live) return;
+  const int j = row / g.nz;
+  const size_t base = (size_t)row * g.nx;
+  const double add = dst == PoissonDst::Potential ? V * mt.yc[j] : 0.0;
+  const float addT = dst == PoissonDst::PotentialShadow ? (float)plane_add[j] : 0.f;
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int k1 = gi * PER + p;
+    cplx<float> w[G];
+#pragma unroll
+    for (int q = 0; q < G; ++q) w[q] = xr[k1 * G + q];
+    rfft::dft<true, G>(w);
+    rfft::static_for<0, G>([&](auto kc) {
+      constexpr int k2 = decltype(kc)::value;
+      const cplx<float> z = w[rfft::bitrev(k2, G)];
+      const size_t o = base + 2 * (size_t)(k1 + R1 * k2);
+      if (dst == PoissonDst::PotentialShadow) {
+        out[o] = (TO)(addT + z.x);
+        out[o + 1] = (TO)(addT + z.y);
+      } else if (dst == PoissonDst::Potential) {
+        out[o] = (TO)(add + (double)z.x);
+        out[o + 1] = (TO)(add + (double)z.y);
+      } else {
+        out[o] = (TO)z.x;
+        out[o + 1] = (TO)z.y;
+      }
+    });
+  }
+}
+
+// Rows per 256-thread block of the register x-transforms, and shared memory.
+template <int NH, int R1>
+constexpr int fx_rows() { return 256 / (NH / R1); }
+template <int NH, int R1>
+constexpr size_t fx_smem() { return sizeof(cplx<float>) * ((size_t)2 * NH + 1 + (size_t)fx_rows<NH, R1>() * (NH + 1)); }
+
 template <typename T>
 static void fft_x_shape(const Geo& g, dim3& blk, dim3& grd, size_t& smem) {
   const int Lh = g.nx >> 1;
@@ -238,6 +425,26 @@ cudaError_t launch_fft_x_fwd(PoissonSrc kind, const TV* u, const TV* v, const TV
                              const T* idyT) {
   SrcArgs<T, TV> a{kind, u, v, w, cp, cm, plain, scale, sa, sb, (T)(scale * g.idx), (T)(scale * g.idz), idyT,
                    (T)scale};
+  if constexpr (sizeof(T) == sizeof(float)) {
+    auto go = [&](auto kern, int G, int rows, size_t smem) {
+      if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+      }
+      const int nrows = g.nyc * g.nz;
+      kern<<<(nrows + rows - 1) / rows, dim3(G, rows), smem, s>>>(a, g, m, spec, tw_half, tw_post);
+      return cudaGetLastError();
+    };
+    switch (g.nx / 2) {
+      case 16: return go(k_fft_x_fwd_reg<16, 4, TV>, 4, fx_rows<16, 4>(), fx_smem<16, 4>());
+      case 32: return go(k_fft_x_fwd_reg<32, 8, TV>, 4, fx_rows<32, 8>(), fx_smem<32, 8>());
+      case 64: return go(k_fft_x_fwd_reg<64, 8, TV>, 8, fx_rows<64, 8>(), fx_smem<64, 8>());
+      case 128: return go(k_fft_x_fwd_reg<128, 16, TV>, 8, fx_rows<128, 16>(), fx_smem<128, 16>());
+      case 256: return go(k_fft_x_fwd_reg<256, 16, TV>, 16, fx_rows<256, 16>(), fx_smem<256, 16>());
+      case 512: return go(k_fft_x_fwd_reg<512, 32, TV>, 16, fx_rows<512, 32>(), fx_smem<512, 32>());
+      default: break;
+    }
+  }
   dim3 blk, grd;
   size_t smem;
   fft_x_shape<T>(g, blk, grd, smem);
@@ -301,6 +508,26 @@ template <typename T, typename TO>
 cudaError_t launch_fft_x_inv(PoissonDst dst, const cplx<T>* spec, const Geo& g, const Metrics& m,
                              const cplx<T>* tw_half, const cplx<T>* tw_post, double V, TO* out,
                              cudaStream_t s, const double* plane_add) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    auto go = [&](auto kern, int G, int rows, size_t smem) {
+      if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+      }
+      const int nrows = g.nyc * g.nz;
+      kern<<<(nrows + rows - 1) / rows, dim3(G, rows), smem, s>>>(dst, spec, g, m, tw_half, tw_post, V, out, plane_add);
+      return cudaGetLastError();
+    };
+    switch (g.nx / 2) {
+      case 16: return go(k_fft_x_inv_reg<16, 4, TO>, 4, fx_rows<16, 4>(), fx_smem<16, 4>());
+      case 32: return go(k_fft_x_inv_reg<32, 8, TO>, 4, fx_rows<32, 8>(), fx_smem<32, 8>());
+      case 64: return go(k_fft_x_inv_reg<64, 8, TO>, 8, fx_rows<64, 8>(), fx_smem<64, 8>());
+      case 128: return go(k_fft_x_inv_reg<128, 16, TO>, 8, fx_rows<128, 16>(), fx_smem<128, 16>());
+      case 256: return go(k_fft_x_inv_reg<256, 16, TO>, 16, fx_rows<256, 16>(), fx_smem<256, 16>());
+      case 512: return go(k_fft_x_inv_reg<512, 32, TO>, 16, fx_rows<512, 32>(), fx_smem<512, 32>());
+      default: break;
+    }
+  }
   dim3 blk, grd;
   size_t smem;
   fft_x_shape<T>(g, blk, grd, smem);
