@@ -107,20 +107,13 @@ struct YCarry {
   float tu, tw, tv, fp, fm;
 };
 
-// Column wall velocities and the substage scalars folded once per kernel.
+// Column wall velocities of a cell.
 struct CellK {
-  float idx, idz, idx2, idz2, nu, K, Kx, Kz, D, Dx, Dz, dt, gam, zet, alp, anu, aD;
   float ub, ut, wb, wt;
 };
 
-__device__ __forceinline__ CellK cell_consts(const CoefF& cf, float ub, float ut, float wb, float wt) {
-  CellK k;
-  k.idx = cf.idx; k.idz = cf.idz; k.idx2 = cf.idx * cf.idx; k.idz2 = cf.idz * cf.idz;
-  k.nu = cf.nu; k.K = cf.K; k.Kx = cf.K * cf.idx; k.Kz = cf.K * cf.idz;
-  k.D = cf.D; k.Dx = cf.D * cf.idx; k.Dz = cf.D * cf.idz;
-  k.dt = cf.dt; k.gam = cf.gam; k.zet = cf.zet; k.alp = cf.alp; k.anu = cf.alp * cf.nu; k.aD = cf.alp * cf.D;
-  k.ub = ub; k.ut = ut; k.wb = wb; k.wt = wt;
-  return k;
+__device__ __forceinline__ CellK cell_consts(const CoefF&, float ub, float ut, float wb, float wt) {
+  return CellK{ub, ut, wb, wt};
 }
 
 // The FP32 explicit terms and CN right-hand sides of one cell (and of the
@@ -130,7 +123,7 @@ __device__ __forceinline__ CellK cell_consts(const CoefF& cf, float ub, float ut
 template <int AS, int SZ, bool DN, bool UP, bool CIN>
 __device__ __forceinline__ CellOut rhs_cell(const float* __restrict__ bm, const float* __restrict__ bo,
                                             const float* __restrict__ bp, const float Ho[5], const PlaneC& q,
-                                            const CellK& k, YCarry& cy) {
+                                            const CellK& kw, const CoefF& k, YCarry& cy) {
 #define LM(a, off) bm[(a) * AS + (off)]
 #define LO(a, off) bo[(a) * AS + (off)]
 #define LP(a, off) bp[(a) * AS + (off)]
@@ -172,7 +165,7 @@ __device__ __forceinline__ CellOut rhs_cell(const float* __restrict__ bm, const 
     const float rhom = LO(ACP, XM) - LO(ACM, XM);
     const float fu = -k.Kx * (q.rho_ref + 0.5f * (rhom + rho0)) * dphxm;
     const float H = -(ax + ay + az) + k.nu * lap + fu;
-    const float Ly = q.lo_c * ((DN ? uym : k.ub) - u0) + q.hi_c * ((UP ? uyp : k.ut) - u0);
+    const float Ly = q.lo_c * ((DN ? uym : kw.ub) - u0) + q.hi_c * ((UP ? uyp : kw.ut) - u0);
     const float gp = (p0 - LO(AP, XM)) * k.idx;
     o.ru = k.dt * (k.gam * H + k.zet * Ho[0] - k.alp * gp + k.anu * Ly);
     o.Hu = H;
@@ -193,7 +186,7 @@ __device__ __forceinline__ CellOut rhs_cell(const float* __restrict__ bm, const 
     const float rhom = LO(ACP, ZM) - LO(ACM, ZM);
     const float fw = -k.Kz * (q.rho_ref + 0.5f * (rhom + rho0)) * dphzm;
     const float H = -(ax + ay + az) + k.nu * lap + fw;
-    const float Ly = q.lo_c * ((DN ? wym : k.wb) - w0) + q.hi_c * ((UP ? wyp : k.wt) - w0);
+    const float Ly = q.lo_c * ((DN ? wym : kw.wb) - w0) + q.hi_c * ((UP ? wyp : kw.wt) - w0);
     const float gp = (p0 - LO(AP, ZM)) * k.idz;
     o.rw = k.dt * (k.gam * H + k.zet * Ho[1] - k.alp * gp + k.anu * Ly);
     o.Hw = H;
@@ -294,18 +287,18 @@ __device__ __forceinline__ CellOut rhs_cell(const float* __restrict__ bm, const 
 // Plane j of a chunk starting at jb: the specialisation for its position.
 template <int AS, int SZ>
 __device__ __forceinline__ CellOut rhs_cell_at(int j, int jb, int nyc, const float* bm, const float* bo,
-                                               const float* bp, const float Ho[5], const PlaneC& q, const CellK& k,
-                                               YCarry& cy) {
+                                               const float* bp, const float Ho[5], const PlaneC& q, const CellK& kw,
+                                               const CoefF& k, YCarry& cy) {
   if (j > jb) {
-    if (j < nyc - 1) return rhs_cell<AS, SZ, true, true, true>(bm, bo, bp, Ho, q, k, cy);
-    return rhs_cell<AS, SZ, true, false, true>(bm, bo, bp, Ho, q, k, cy);
+    if (j < nyc - 1) return rhs_cell<AS, SZ, true, true, true>(bm, bo, bp, Ho, q, kw, k, cy);
+    return rhs_cell<AS, SZ, true, false, true>(bm, bo, bp, Ho, q, kw, k, cy);
   }
   if (j > 0) {
-    if (j < nyc - 1) return rhs_cell<AS, SZ, true, true, false>(bm, bo, bp, Ho, q, k, cy);
-    return rhs_cell<AS, SZ, true, false, false>(bm, bo, bp, Ho, q, k, cy);
+    if (j < nyc - 1) return rhs_cell<AS, SZ, true, true, false>(bm, bo, bp, Ho, q, kw, k, cy);
+    return rhs_cell<AS, SZ, true, false, false>(bm, bo, bp, Ho, q, kw, k, cy);
   }
-  if (j < nyc - 1) return rhs_cell<AS, SZ, false, true, false>(bm, bo, bp, Ho, q, k, cy);
-  return rhs_cell<AS, SZ, false, false, false>(bm, bo, bp, Ho, q, k, cy);
+  if (j < nyc - 1) return rhs_cell<AS, SZ, false, true, false>(bm, bo, bp, Ho, q, kw, k, cy);
+  return rhs_cell<AS, SZ, false, false, false>(bm, bo, bp, Ho, q, kw, k, cy);
 }
 
 __device__ __forceinline__ void store_cell(const Fields<float>& f, float* rcp, float* rcm, const Shadows& sh,
@@ -352,8 +345,8 @@ __host__ __device__ constexpr size_t rhs_tile_floats(int tx, int tz, int cz, boo
 // TX x TZ threads own a TX x (TZ CZ) tile of cells; each thread computes CZ
 // cells stacked in z.  HSM: the previous substage's H arrives by cp.async with
 // the planes (else each thread loads it at the top of the iteration).
-template <int TX, int TZ, int CZ, bool HSM>
-__global__ void __launch_bounds__(TX * TZ, (CZ == 1 ? 768 : 512) / (TX * TZ))
+template <int TX, int TZ, int CZ, bool HSM, int MINB>
+__global__ void __launch_bounds__(TX * TZ, MINB)
     k_rhs_mixed_tile(Fields<float> f, float* __restrict__ rcp, float* __restrict__ rcm, Shadows sh, MixedRefs R,
                      Geo g, MetricsF mt, CoefF cf, int jchunk) {
   constexpr int TW = TX + 2, NT = TW * (TZ * CZ + 2), NTH = TX * TZ, E = (NT + NTH - 1) / NTH;
@@ -443,7 +436,7 @@ __global__ void __launch_bounds__(TX * TZ, (CZ == 1 ? 768 : 512) / (TX * TZ))
 #pragma unroll
     for (int cz = 0; cz < CZ; ++cz) {
       const CellOut o =
-          rhs_cell_at<NT, TW>(j, jb, nyc, bm + cz * TW, bo + cz * TW, bp + cz * TW, Ho[cz], q, kc[cz], cy[cz]);
+          rhs_cell_at<NT, TW>(j, jb, nyc, bm + cz * TW, bo + cz * TW, bp + cz * TW, Ho[cz], q, kc[cz], cf, cy[cz]);
       store_cell(f, rcp, rcm, sh, c0 + (size_t)cz * nx, j > 0, o);
     }
     __syncthreads();
@@ -611,7 +604,7 @@ __global__ void __launch_bounds__(NX * TZB, 1)
     const float* hs = holds + (size_t)(n0 & 3) * G::HS + tz * NX + tx;
     const float Ho[5] = {hs[0], hs[TZB * NX], hs[2 * TZB * NX], hs[3 * TZB * NX], hs[4 * TZB * NX]};
     const PlaneC q = plane_consts(pct + (size_t)(j - jb) * kPlaneLd);
-    const CellOut o = rhs_cell_at<G::AS, G::S>(j, jb, nyc, bm, bo, bp, Ho, q, kc, cy);
+    const CellOut o = rhs_cell_at<G::AS, G::S>(j, jb, nyc, bm, bo, bp, Ho, q, kc, cf, cy);
     store_cell(f, rcp, rcm, sh, (size_t)j * P + ck, j > 0, o);
     __syncthreads();   // slot of plane j - 1 is free
     if (j + 3 <= je) {
@@ -709,8 +702,8 @@ cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const Mi
     }
     return best;
   };
-  // TMA rows: lc_rhs_bx 64 / 128; cp.async tiles: the default and 32 / 16
-  if (maps && (g.lc_rhs_bx == 64 || g.lc_rhs_bx == 128) && rhs_tma_eligible(g)) {
+  // TMA rows: lc_rhs_bx 128; cp.async tiles: the default and 64 / 32 / 16
+  if (maps && g.lc_rhs_bx == 128 && rhs_tma_eligible(g)) {
     auto go = [&](auto kern, auto geo, int tzb) {
       using G = decltype(geo);
       const int jc = chunk(g.nz / tzb, 1);
@@ -729,8 +722,9 @@ cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const Mi
       default: return go(k_rhs_mixed_tma<256, 2>, TmaGeo<256, 2>{}, 2);
     }
   }
-  // cp.async tiles.  lc_rhs_bx: 0 / 32 = 32 x 8 threads with two cells each in z,
-  // 16 = 32 x 8 threads with one cell each; narrower grids fall back to 8 x 4 / 4 x 4
+  // cp.async tiles.  lc_rhs_bx: 0 / 32 = 32 x 8 threads with two cells each in z
+  // (two blocks per SM), 64 = the same capped to three blocks per SM, 16 = 32 x 8
+  // threads with one cell each; narrower grids fall back to 8 x 4 / 4 x 4
   auto go = [&](auto kern, int bx, int bz, int cz, bool hsm, int per_sm) {
     const int nxz = (g.nx / bx) * (g.nz / (bz * cz));
     const int jc = chunk(nxz, per_sm);
@@ -743,10 +737,12 @@ cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const Mi
     kern<<<grd, dim3(bx, bz), smem, s>>>(f, rp, rm, sh, R, g, m, cf, jc);
     return cudaGetLastError();
   };
-  if (g.nx >= 32 && g.nz >= 16 && g.lc_rhs_bx != 16) return go(k_rhs_mixed_tile<32, 8, 2, false>, 32, 8, 2, false, 2);
-  if (g.nx >= 32 && g.nz >= 8) return go(k_rhs_mixed_tile<32, 8, 1, true>, 32, 8, 1, true, 3);
-  if (g.nx >= 8) return go(k_rhs_mixed_tile<8, 4, 1, true>, 8, 4, 1, true, 24);
-  return go(k_rhs_mixed_tile<4, 4, 1, true>, 4, 4, 1, true, 48);
+  if (g.nx >= 32 && g.nz >= 16 && g.lc_rhs_bx == 64)   // two cells, three blocks per SM (registers capped)
+    return go(k_rhs_mixed_tile<32, 8, 2, false, 3>, 32, 8, 2, false, 3);
+  if (g.nx >= 32 && g.nz >= 16 && g.lc_rhs_bx != 16) return go(k_rhs_mixed_tile<32, 8, 2, false, 2>, 32, 8, 2, false, 2);
+  if (g.nx >= 32 && g.nz >= 8) return go(k_rhs_mixed_tile<32, 8, 1, true, 3>, 32, 8, 1, true, 3);
+  if (g.nx >= 8) return go(k_rhs_mixed_tile<8, 4, 1, true, 24>, 8, 4, 1, true, 24);
+  return go(k_rhs_mixed_tile<4, 4, 1, true, 32>, 4, 4, 1, true, 48);
 }
 
 }  // namespace pnp

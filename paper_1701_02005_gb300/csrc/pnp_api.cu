@@ -419,8 +419,17 @@ MetricsF metrics_f(const pnp_ctx* c) {
 }
 
 CoefF coef_f(const pnp_ctx* c, const Stage& st) {
-  return CoefF{(float)c->g.idx, (float)c->g.idz, (float)c->ph.nu, (float)c->ph.D, (float)c->ph.K, (float)c->ph.Uw,
-               (float)st.dt, (float)st.gam, (float)st.zet, (float)st.alp};
+  CoefF f{(float)c->g.idx, (float)c->g.idz, (float)c->ph.nu, (float)c->ph.D, (float)c->ph.K, (float)c->ph.Uw,
+          (float)st.dt, (float)st.gam, (float)st.zet, (float)st.alp};
+  f.idx2 = f.idx * f.idx;
+  f.idz2 = f.idz * f.idz;
+  f.Kx = f.K * f.idx;
+  f.Kz = f.K * f.idz;
+  f.Dx = f.D * f.idx;
+  f.Dz = f.D * f.idz;
+  f.anu = f.alp * f.nu;
+  f.aD = f.alp * f.D;
+  return f;
 }
 
 const RhsMaps* rhs_maps(const pnp_ctx* c) { return c->rhs_maps_ok ? &c->rhs_maps : nullptr; }
@@ -1281,9 +1290,9 @@ int pnp_autotune(pnp_ctx* c, double dt, int* cfg_out, double* ms_out) {
   int pick[4] = {32, 128, 64, 32};
   // 1: stencil block shape
   for (int bx : {32, 64, 128, 16}) {
-    // FP64: block x-extents; mixed: 128 / 64 = TMA rows x2 / x1 (when available), 32 / 16 = cp.async tiles
+    // FP64: block x-extents; mixed: 128 = TMA rows (when available), 64 / 32 / 16 = cp.async tiles
     if (c->precision == PNP_FP64 && bx > 2 * c->g.nx && bx != 32) continue;
-    if (c->precision == PNP_MIXED && bx > 32 && !c->rhs_maps_ok) continue;
+    if (c->precision == PNP_MIXED && bx == 128 && !c->rhs_maps_ok) continue;
     c->g.lc_rhs_bx = bx;
     float t = time_launches(c, [&] {
       if (c->precision == PNP_FP64) launch_rhs<double>(fields<double>(c), c->g, metrics(c), c->ph, st, c->stream);

@@ -17,6 +17,8 @@ struct MetricsF {
 struct CoefF {
   float idx, idz, nu, D, K, Uw;
   float dt, gam, zet, alp;
+  // products used per cell, formed once in FP32 on the host
+  float idx2, idz2, Kx, Kz, Dx, Dz, anu, aD;
 };
 
 // FP32 elimination factors of the velocity Crank-Nicolson matrices.
