@@ -182,10 +182,14 @@ int pnp_status(pnp_ctx* ctx);
 int pnp_fp64_peak(pnp_ctx* ctx, double* flops_out);
 
 /* Autotuner (no counterpart in the paper; launch-shape selection for GB300):
- * times candidate launch shapes of the stencil kernels (block x-extent 16/32/
- * 64/128 of 128 threads), the wall-normal CN sweeps (64/128/256 threads), the
- * spectral y-solves (32/64/128) and the z-transform (8..64 threads per column)
- * on this context's grid with CUDA events and keeps the fastest.  cfg_out[4]
+ * times candidate launch codes of the stencil (FP64: block x-extent 16/32/64/128
+ * of 128 threads; mixed: 16 one-cell tiles, 32 / 64 two-cell tiles at two /
+ * three blocks per SM, 128 TMA rows), the wall-normal CN sweeps (32 = mixed
+ * shared-memory line tiles, else 64/128/256 threads per block), the spectral
+ * y-solves (16 = mixed shared-memory tiles, else 32/64/128 threads) and the
+ * z-transform (8..64 threads per column; mixed: 64 = stage-by-stage kernel,
+ * else register FFT) on this context's grid with CUDA events and keeps the
+ * fastest.  cfg_out[4]
  * receives the choice (same order as pnp_set_launch_config), ms_out[4]
  * (optional) the best time of each.  It runs on the workspace and overwrites
  * the state: call it after pnp_set_params and before pnp_init_state /

@@ -1317,7 +1317,7 @@ int pnp_autotune(pnp_ctx* c, double dt, int* cfg_out, double* ms_out) {
   c->g.lc_cn = pick[1];
   // 3: spectral y-solve block size, 4: z-transform threads per column
   const double scale = 1.0 / ((double)c->g.nx * (double)c->g.nz);
-  for (int T : {32, 64, 128}) {
+  for (int T : {16, 32, 64, 128}) {   // mixed: 16 = shared-memory tiles
     c->g.lc_spec = T;
     float t = time_launches(c, [&] {
       if (c->precision == PNP_FP64)
@@ -1358,7 +1358,7 @@ int pnp_set_launch_config(pnp_ctx* c, const int* cfg) {
   const int bx = cfg[0], cn = cfg[1], sp = cfg[2], ty = cfg[3];
   if (!(bx == 16 || bx == 32 || bx == 64 || bx == 128)) return PNP_ERR_ARG;
   if (cn < 32 || cn > 1024 || (cn & (cn - 1))) return PNP_ERR_ARG;
-  if (sp < 32 || sp > 1024 || (sp & (sp - 1))) return PNP_ERR_ARG;
+  if (sp < 16 || sp > 1024 || (sp & (sp - 1))) return PNP_ERR_ARG;
   if (ty < 1 || ty > 64) return PNP_ERR_ARG;
   c->g.lc_rhs_bx = bx;
   c->g.lc_cn = cn;

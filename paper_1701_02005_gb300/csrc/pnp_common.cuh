@@ -33,7 +33,7 @@ struct Geo {
                          // mixed stencil: 128 TMA rows, 64 / 32 two-cell cp.async tiles (3 / 2
                          // blocks per SM), 16 one-cell tiles
   int lc_cn;             // threads per block of the wall-normal CN sweeps (mixed: 0 / 32 = shared-memory line tiles)
-  int lc_spec;           // threads per block of the spectral y-solves
+  int lc_spec;           // threads per block of the spectral y-solves (mixed: 16 = shared-memory tiles)
   int lc_fftz_ty;        // threads per column of the z-transform (cap)
 };
 
