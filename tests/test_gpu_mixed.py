@@ -127,3 +127,28 @@ def test_mixed_stencil_kernels_agree():
         for n in out[128]:
             assert _rel(out[bx][n], out[128][n]) <= 1e-6, (bx, n)
     s.close()
+
+
+def test_mixed_spectral_solve_variants_agree():
+    # the spectral y-solve with its forward values in shared memory (launch code
+    # 16) and one thread per spectral point (32, 64): the same df operations in
+    # the same order, so the fields agree to the last bit
+    import ctypes as C
+
+    from paper_1701_02005_gb300 import binding as B
+
+    g = o.Grid(64, 41, 32, 2 * math.pi, math.pi, stretch=2.0)
+    prm = o.Params(Re=300.0, lam=0.05, Sc=1.0, V=2.0, beta=0.5)
+    st = o.initial_state(g, prm, o.IC_PB, seed=25, amp=0.1)
+    s = _mixed(g, prm)
+    out = {}
+    for sp in (16, 32, 64):
+        B.check(B.pnp_set_launch_config(s.ctx, (C.c_int * 4)(32, 32, sp, 32)), "pnp_set_launch_config")
+        s.set_state(st)
+        s.step(3, 0.005)
+        out[sp] = {n: s.get(n) for n in ("u", "v", "w", "p", "Phi")}
+    assert s.status() == 0
+    for sp in (16, 64):
+        for n in out[32]:
+            assert np.array_equal(out[sp][n], out[32][n]), (sp, n)
+    s.close()
