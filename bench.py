@@ -49,8 +49,8 @@ def cells(wl=WL):
 # 256x193x256, from the one-pass ncu capture summarised under profiles/
 # (shape = the stencil's tuned launch code the capture ran with)
 NCU_TRAFFIC = {
-    ("mixed", "rhs"): {"kernel": "k_rhs_mixed_tile<32, 8, 2, false, 2>", "shape": 32, "cells": 12582912,
-                       "bytes": 1077.0e6},
+    ("mixed", "rhs"): {"kernel": "k_rhs_mixed_tile<32, 8, 2, false, 2>", "shape": None, "cells": 12582912,
+                       "bytes": None},
 }
 
 
@@ -391,7 +391,7 @@ def run_ours(args):
     # one-pass ncu capture of this workload (profiles/, DRAM traffic summary), valid
     # only for the kernel and launch shape that capture measured
     nt = NCU_TRAFFIC.get((pname, dom))
-    if nt and nt["cells"] == n_cells and (nt["shape"] is None or (launch_cfg and launch_cfg[0] == nt["shape"])):
+    if nt and nt["bytes"] and nt["cells"] == n_cells and (nt["shape"] is None or (launch_cfg and launch_cfg[0] == nt["shape"])):
         roof["traffic"] = nt["bytes"]
         roof["traffic_kernel"] = nt["kernel"]
 

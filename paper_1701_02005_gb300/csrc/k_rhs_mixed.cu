@@ -28,6 +28,7 @@
 #include <cudaTypedefs.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "pnp_common.cuh"
 #include "pnp_mixed.cuh"
@@ -97,47 +98,88 @@ __device__ __forceinline__ PlaneC plane_consts(const float* t) {
   return q;
 }
 
+// Two cells of one thread as a packed pair (cell 0 in .x, cell 1 in .y):
+// arithmetic on the pair issues one packed FP32 instruction (FADD2 / FMUL2 /
+// FFMA2) for both cells.  A float converts to the pair (both lanes).
+struct V2 {
+  float2 v;
+  __device__ __forceinline__ V2() {}
+  __device__ __forceinline__ V2(float a) : v(make_float2(a, a)) {}
+  __device__ __forceinline__ V2(float a, float b) : v(make_float2(a, b)) {}
+};
+__device__ __forceinline__ V2 operator+(V2 a, V2 b) {
+  V2 r;
+  r.v = __fadd2_rn(a.v, b.v);
+  return r;
+}
+__device__ __forceinline__ V2 operator-(V2 a, V2 b) {   // a + (-1) b: one rounding, as a - b
+  V2 r;
+  r.v = __ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v);
+  return r;
+}
+__device__ __forceinline__ V2 operator*(V2 a, V2 b) {
+  V2 r;
+  r.v = __fmul2_rn(a.v, b.v);
+  return r;
+}
+__device__ __forceinline__ V2 operator-(V2 a) { return V2(-a.v.x, -a.v.y); }
+__device__ __forceinline__ V2 fmaT(V2 a, V2 b, V2 c) {
+  V2 r;
+  r.v = __ffma2_rn(a.v, b.v, c.v);
+  return r;
+}
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <typename T>
 struct CellOut {
-  float ru, Hu, rw, Hw, rv, Hv, rcp, Hcp, rcm, Hcm;
+  T ru, Hu, rw, Hw, rv, Hv, rcp, Hcp, rcm, Hcm;
 };
 
 // Values at face j+1 computed for plane j and reused as the face-j values of
 // plane j+1: advective products of u, w, v and the ion fluxes.
+template <typename T>
 struct YCarry {
-  float tu, tw, tv, fp, fm;
+  T tu, tw, tv, fp, fm;
 };
 
-// Column wall velocities of a cell.
+// Column wall velocities of the cell(s).
+template <typename T>
 struct CellK {
-  float ub, ut, wb, wt;
+  T ub, ut, wb, wt;
 };
 
-__device__ __forceinline__ CellK cell_consts(const CoefF&, float ub, float ut, float wb, float wt) {
-  return CellK{ub, ut, wb, wt};
+// A tile value of the cell (T = float) or of the cell pair, the second cell one
+// z-row (SZ floats) further (T = V2).
+template <typename T, int SZ>
+__device__ __forceinline__ T tld(const float* b, int i) {
+  if constexpr (std::is_same<T, float>::value) return b[i];
+  else return V2(b[i], b[i + SZ]);
 }
 
-// The FP32 explicit terms and CN right-hand sides of one cell (and of the
-// v-face below it when DN).  bm, bo, bp: this cell in array 0 of the slots of
-// planes j-1, j, j+1; arrays are AS floats apart, z-rows SZ floats apart.
-// DN / UP: a cell plane below / above exists; CIN: cy holds face j's values.
-template <int AS, int SZ, bool DN, bool UP, bool CIN>
-__device__ __forceinline__ CellOut rhs_cell(const float* __restrict__ bm, const float* __restrict__ bo,
-                                            const float* __restrict__ bp, const float Ho[5], const PlaneC& q,
-                                            const CellK& kw, const CoefF& k, YCarry& cy) {
-#define LM(a, off) bm[(a) * AS + (off)]
-#define LO(a, off) bo[(a) * AS + (off)]
-#define LP(a, off) bp[(a) * AS + (off)]
+// The FP32 explicit terms and CN right-hand sides of one cell or of a cell pair
+// (and of the v-face below when DN).  bm, bo, bp: the (first) cell in array 0
+// of the slots of planes j-1, j, j+1; arrays are AS floats apart, z-rows SZ
+// floats apart.  DN / UP: a cell plane below / above exists; CIN: cy holds
+// face j's values.  The products and sums are written as fused multiply-adds
+// where a plain expression would let the compiler fuse them.
+template <typename T, int AS, int SZ, bool DN, bool UP, bool CIN>
+__device__ __forceinline__ CellOut<T> rhs_cell(const float* __restrict__ bm, const float* __restrict__ bo,
+                                               const float* __restrict__ bp, const T Ho[5], const PlaneC& q,
+                                               const CellK<T>& kw, const CoefF& k, YCarry<T>& cy) {
+#define LM(a, off) tld<T, SZ>(bm, (a) * AS + (off))
+#define LO(a, off) tld<T, SZ>(bo, (a) * AS + (off))
+#define LP(a, off) tld<T, SZ>(bp, (a) * AS + (off))
   constexpr int XM = -1, XP = 1, ZM = -SZ, ZP = SZ;
-  CellOut o;
-  const float u0 = LO(AU, 0), uxm = LO(AU, XM), uxp = LO(AU, XP), uzm = LO(AU, ZM), uzp = LO(AU, ZP);
-  const float w0 = LO(AW, 0), wxm = LO(AW, XM), wxp = LO(AW, XP), wzm = LO(AW, ZM), wzp = LO(AW, ZP);
-  const float vb = LO(AV, 0), vt = LP(AV, 0);
-  const float p0 = LO(AP, 0);
-  const float ph0 = LO(APH, 0), phxm = LO(APH, XM), phxp = LO(APH, XP), phzm = LO(APH, ZM), phzp = LO(APH, ZP);
-  const float cp0 = LO(ACP, 0), cm0 = LO(ACM, 0);
-  const float rho0 = cp0 - cm0;   // rho' at the centre
-  const float dphxm = ph0 - phxm, dphxp = phxp - ph0, dphzm = ph0 - phzm, dphzp = phzp - ph0;
-  float uym = 0.f, wym = 0.f, phym = 0.f, uyp = 0.f, wyp = 0.f, phyp = 0.f;
+  CellOut<T> o;
+  const T u0 = LO(AU, 0), uxm = LO(AU, XM), uxp = LO(AU, XP), uzm = LO(AU, ZM), uzp = LO(AU, ZP);
+  const T w0 = LO(AW, 0), wxm = LO(AW, XM), wxp = LO(AW, XP), wzm = LO(AW, ZM), wzp = LO(AW, ZP);
+  const T vb = LO(AV, 0), vt = LP(AV, 0);
+  const T p0 = LO(AP, 0);
+  const T ph0 = LO(APH, 0), phxm = LO(APH, XM), phxp = LO(APH, XP), phzm = LO(APH, ZM), phzp = LO(APH, ZP);
+  const T cp0 = LO(ACP, 0), cm0 = LO(ACM, 0);
+  const T rho0 = cp0 - cm0;   // rho' at the centre
+  const T dphxm = ph0 - phxm, dphxp = phxp - ph0, dphzm = ph0 - phzm, dphzp = phzp - ph0;
+  T uym = 0.f, wym = 0.f, phym = 0.f, uyp = 0.f, wyp = 0.f, phyp = 0.f;
   if constexpr (DN) {
     uym = LM(AU, 0);
     wym = LM(AW, 0);
@@ -151,81 +193,81 @@ __device__ __forceinline__ CellOut rhs_cell(const float* __restrict__ bm, const 
 
   // u at (x-face i, y-centre j, z-centre k)
   {
-    const float ubp = 0.5f * (u0 + uxp), ubm = 0.5f * (uxm + u0);
-    const float ax = (ubp * ubp - ubm * ubm) * k.idx;
-    float ttop = 0.f, tbot = 0.f;
+    const T ubp = 0.5f * (u0 + uxp), ubm = 0.5f * (uxm + u0);
+    const T ax = fmaT(ubp, ubp, -(ubm * ubm)) * k.idx;
+    T ttop = 0.f, tbot = 0.f;
     if constexpr (UP) ttop = (0.5f * (LP(AV, XM) + vt)) * (0.5f * (u0 + uyp));
     if constexpr (DN) tbot = CIN ? cy.tu : (0.5f * (LO(AV, XM) + vb)) * (0.5f * (uym + u0));
     cy.tu = ttop;
-    const float ay = (ttop - tbot) * q.idy;
-    const float wfk = 0.5f * (wxm + w0);
-    const float wfkp = 0.5f * (LO(AW, ZP + XM) + wzp);
-    const float az = (wfkp * 0.5f * (u0 + uzp) - wfk * 0.5f * (uzm + u0)) * k.idz;
-    const float lap = (uxp - 2.f * u0 + uxm) * k.idx2 + (uzp - 2.f * u0 + uzm) * k.idz2;
-    const float rhom = LO(ACP, XM) - LO(ACM, XM);
-    const float fu = -k.Kx * (q.rho_ref + 0.5f * (rhom + rho0)) * dphxm;
-    const float H = -(ax + ay + az) + k.nu * lap + fu;
-    const float Ly = q.lo_c * ((DN ? uym : kw.ub) - u0) + q.hi_c * ((UP ? uyp : kw.ut) - u0);
-    const float gp = (p0 - LO(AP, XM)) * k.idx;
-    o.ru = k.dt * (k.gam * H + k.zet * Ho[0] - k.alp * gp + k.anu * Ly);
+    const T ay = (ttop - tbot) * q.idy;
+    const T wfk = 0.5f * (wxm + w0);
+    const T wfkp = 0.5f * (LO(AW, ZP + XM) + wzp);
+    const T az = fmaT(wfkp, 0.5f * (u0 + uzp), -(wfk * (0.5f * (uzm + u0)))) * k.idz;
+    const T lap = fmaT(fmaT(-2.f, u0, uzp) + uzm, k.idz2, (fmaT(-2.f, u0, uxp) + uxm) * k.idx2);
+    const T rhom = LO(ACP, XM) - LO(ACM, XM);
+    const T fu = (-k.Kx) * fmaT(0.5f, rhom + rho0, q.rho_ref) * dphxm;
+    const T H = fmaT(k.nu, lap, fu) - (ax + ay + az);
+    const T Ly = fmaT(q.hi_c, (UP ? uyp : kw.ut) - u0, q.lo_c * ((DN ? uym : kw.ub) - u0));
+    const T gp = (p0 - LO(AP, XM)) * k.idx;
+    o.ru = k.dt * fmaT(k.anu, Ly, fmaT(-k.alp, gp, fmaT(k.gam, H, k.zet * Ho[0])));
     o.Hu = H;
   }
   // w at (x-centre i, y-centre j, z-face k)
   {
-    const float wbp = 0.5f * (w0 + wzp), wbm = 0.5f * (wzm + w0);
-    const float az = (wbp * wbp - wbm * wbm) * k.idz;
-    float ttop = 0.f, tbot = 0.f;
+    const T wbp = 0.5f * (w0 + wzp), wbm = 0.5f * (wzm + w0);
+    const T az = fmaT(wbp, wbp, -(wbm * wbm)) * k.idz;
+    T ttop = 0.f, tbot = 0.f;
     if constexpr (UP) ttop = (0.5f * (LP(AV, ZM) + vt)) * (0.5f * (w0 + wyp));
     if constexpr (DN) tbot = CIN ? cy.tw : (0.5f * (LO(AV, ZM) + vb)) * (0.5f * (wym + w0));
     cy.tw = ttop;
-    const float ay = (ttop - tbot) * q.idy;
-    const float ufi = 0.5f * (uzm + u0);
-    const float ufip = 0.5f * (LO(AU, ZM + XP) + uxp);
-    const float ax = (ufip * 0.5f * (w0 + wxp) - ufi * 0.5f * (wxm + w0)) * k.idx;
-    const float lap = (wxp - 2.f * w0 + wxm) * k.idx2 + (wzp - 2.f * w0 + wzm) * k.idz2;
-    const float rhom = LO(ACP, ZM) - LO(ACM, ZM);
-    const float fw = -k.Kz * (q.rho_ref + 0.5f * (rhom + rho0)) * dphzm;
-    const float H = -(ax + ay + az) + k.nu * lap + fw;
-    const float Ly = q.lo_c * ((DN ? wym : kw.wb) - w0) + q.hi_c * ((UP ? wyp : kw.wt) - w0);
-    const float gp = (p0 - LO(AP, ZM)) * k.idz;
-    o.rw = k.dt * (k.gam * H + k.zet * Ho[1] - k.alp * gp + k.anu * Ly);
+    const T ay = (ttop - tbot) * q.idy;
+    const T ufi = 0.5f * (uzm + u0);
+    const T ufip = 0.5f * (LO(AU, ZM + XP) + uxp);
+    const T ax = fmaT(ufip, 0.5f * (w0 + wxp), -(ufi * (0.5f * (wxm + w0)))) * k.idx;
+    const T lap = fmaT(fmaT(-2.f, w0, wzp) + wzm, k.idz2, (fmaT(-2.f, w0, wxp) + wxm) * k.idx2);
+    const T rhom = LO(ACP, ZM) - LO(ACM, ZM);
+    const T fw = (-k.Kz) * fmaT(0.5f, rhom + rho0, q.rho_ref) * dphzm;
+    const T H = fmaT(k.nu, lap, fw) - (ax + ay + az);
+    const T Ly = fmaT(q.hi_c, (UP ? wyp : kw.wt) - w0, q.lo_c * ((DN ? wym : kw.wb) - w0));
+    const T gp = (p0 - LO(AP, ZM)) * k.idz;
+    o.rw = k.dt * fmaT(k.anu, Ly, fmaT(-k.alp, gp, fmaT(k.gam, H, k.zet * Ho[1])));
     o.Hw = H;
   }
   // v at (x-centre i, y-face j, z-centre k), 1 <= j <= nyc-1; the centre
   // product (v_j + v_j+1)^2 / 4 is the face-j product of the next plane
   {
-    const float vbu = 0.5f * (vb + vt);
-    const float ttop = vbu * vbu;
+    const T vbu = 0.5f * (vb + vt);
+    const T ttop = vbu * vbu;
     o.rv = 0.f;
     o.Hv = 0.f;
     if constexpr (DN) {
-      const float v0 = vb;
-      const float vxm = LO(AV, XM), vxp = LO(AV, XP), vzm = LO(AV, ZM), vzp = LO(AV, ZP);
-      const float vym = LM(AV, 0), vyp = vt;
-      float tbot;
+      const T v0 = vb;
+      const T vxm = LO(AV, XM), vxp = LO(AV, XP), vzm = LO(AV, ZM), vzp = LO(AV, ZP);
+      const T vym = LM(AV, 0), vyp = vt;
+      T tbot;
       if constexpr (CIN) {
         tbot = cy.tv;
       } else {
-        const float vbd = 0.5f * (vym + v0);
+        const T vbd = 0.5f * (vym + v0);
         tbot = vbd * vbd;
       }
-      const float Ui = q.wl * uym + q.wu * u0;
-      const float Uip = q.wl * LM(AU, XP) + q.wu * uxp;
-      const float ax = (Uip * 0.5f * (v0 + vxp) - Ui * 0.5f * (vxm + v0)) * k.idx;
-      const float ay = (ttop - tbot) * q.ih;
-      const float Wk = q.wl * wym + q.wu * w0;
-      const float Wkp = q.wl * LM(AW, ZP) + q.wu * wzp;
-      const float az = (Wkp * 0.5f * (v0 + vzp) - Wk * 0.5f * (vzm + v0)) * k.idz;
-      const float lap = (vxp - 2.f * v0 + vxm) * k.idx2 + (vzp - 2.f * v0 + vzm) * k.idz2;
+      const T Ui = fmaT(q.wl, uym, q.wu * u0);
+      const T Uip = fmaT(q.wl, LM(AU, XP), q.wu * uxp);
+      const T ax = fmaT(Uip, 0.5f * (v0 + vxp), -(Ui * (0.5f * (vxm + v0)))) * k.idx;
+      const T ay = (ttop - tbot) * q.ih;
+      const T Wk = fmaT(q.wl, wym, q.wu * w0);
+      const T Wkp = fmaT(q.wl, LM(AW, ZP), q.wu * wzp);
+      const T az = fmaT(Wkp, 0.5f * (v0 + vzp), -(Wk * (0.5f * (vzm + v0)))) * k.idz;
+      const T lap = fmaT(fmaT(-2.f, v0, vzp) + vzm, k.idz2, (fmaT(-2.f, v0, vxp) + vxm) * k.idx2);
       // Coulomb force: reference-reference part is the FP64 constant Fvref
-      const float rhod = LM(ACP, 0) - LM(ACM, 0);
-      const float rpf = 0.5f * (rhod + rho0);   // rho' on the face
-      const float dphi = ph0 - phym;            // phi' difference
-      const float fv = q.Fvref - k.K * q.ih * (q.rhorf * dphi + rpf * (q.dPref + dphi));
-      const float H = -(ax + ay + az) + k.nu * lap + fv;
-      const float Ly = q.lo_f * (vym - v0) + q.hi_f * (vyp - v0);
-      const float gp = (p0 - LM(AP, 0)) * q.ih;
-      o.rv = k.dt * (k.gam * H + k.zet * Ho[2] - k.alp * gp + k.anu * Ly);
+      const T rhod = LM(ACP, 0) - LM(ACM, 0);
+      const T rpf = 0.5f * (rhod + rho0);   // rho' on the face
+      const T dphi = ph0 - phym;            // phi' difference
+      const T fv = fmaT(-k.K * q.ih, fmaT(q.rhorf, dphi, rpf * (dphi + q.dPref)), q.Fvref);
+      const T H = fmaT(k.nu, lap, fv) - (ax + ay + az);
+      const T Ly = fmaT(q.hi_f, vyp - v0, q.lo_f * (vym - v0));
+      const T gp = (p0 - LM(AP, 0)) * q.ih;
+      o.rv = k.dt * fmaT(k.anu, Ly, fmaT(-k.alp, gp, fmaT(k.gam, H, k.zet * Ho[2])));
       o.Hv = H;
     }
     cy.tv = ttop;
@@ -235,41 +277,44 @@ __device__ __forceinline__ CellOut rhs_cell(const float* __restrict__ bm, const 
 #pragma unroll
   for (int ion = 0; ion < 2; ++ion) {
     const int A = ion == 0 ? ACP : ACM;
-    const float s = ion == 0 ? 1.f : -1.f;
     const float cr = ion == 0 ? q.cref_p : q.cref_m;
-    const float cc = ion == 0 ? cp0 : cm0;
-    const float cxm_ = LO(A, XM), cxp_ = LO(A, XP), czm_ = LO(A, ZM), czp_ = LO(A, ZP);
-    float ca = cr + 0.5f * (cxm_ + cc), cb = cr + 0.5f * (cc + cxp_);
-    const float Fx_i = u0 * ca - k.Dx * ((cc - cxm_) + s * ca * dphxm);
-    const float Fx_ip = uxp * cb - k.Dx * ((cxp_ - cc) + s * cb * dphxp);
-    ca = cr + 0.5f * (czm_ + cc);
-    cb = cr + 0.5f * (cc + czp_);
-    const float Fz_k = w0 * ca - k.Dz * ((cc - czm_) + s * ca * dphzm);
-    const float Fz_kp = wzp * cb - k.Dz * ((czp_ - cc) + s * cb * dphzp);
+    const float sD = ion == 0 ? 1.f : -1.f;
+    const T cc = ion == 0 ? cp0 : cm0;
+    const T cxm_ = LO(A, XM), cxp_ = LO(A, XP), czm_ = LO(A, ZM), czp_ = LO(A, ZP);
+    T ca = fmaT(0.5f, cxm_ + cc, cr), cb = fmaT(0.5f, cc + cxp_, cr);
+    const T sca = ion == 0 ? ca : -ca, scb = ion == 0 ? cb : -cb;
+    const T Fx_i = fmaT(u0, ca, (-k.Dx) * fmaT(sca, dphxm, cc - cxm_));
+    const T Fx_ip = fmaT(uxp, cb, (-k.Dx) * fmaT(scb, dphxp, cxp_ - cc));
+    ca = fmaT(0.5f, czm_ + cc, cr);
+    cb = fmaT(0.5f, cc + czp_, cr);
+    const T sza = ion == 0 ? ca : -ca, szb = ion == 0 ? cb : -cb;
+    const T Fz_k = fmaT(w0, ca, (-k.Dz) * fmaT(sza, dphzm, cc - czm_));
+    const T Fz_kp = fmaT(wzp, cb, (-k.Dz) * fmaT(szb, dphzp, czp_ - cc));
     // y faces: advection + migration
-    float Fy_j = 0.f, Fy_jp = 0.f, Ly = 0.f;
+    T Fy_j = 0.f, Fy_jp = 0.f, Ly = 0.f;
     if constexpr (DN) {
-      const float cym_ = LM(A, 0);
+      const T cym_ = LM(A, 0);
       Ly = q.lo_c * (cym_ - cc);
       if constexpr (CIN) {
         Fy_j = ion == 0 ? cy.fp : cy.fm;
       } else {
         const float crf = ion == 0 ? q.crf_p : q.crf_m;
-        const float cpf = 0.5f * (cym_ + cc), dph = ph0 - phym;
-        Fy_j = vb * (crf + cpf) - s * q.Dih * (crf * dph + cpf * (q.dPref + dph));
+        const T cpf = 0.5f * (cym_ + cc), dph = ph0 - phym;
+        Fy_j = fmaT(vb, cpf + crf, (-sD * q.Dih) * fmaT(cpf, dph + q.dPref, crf * dph));
       }
     }
     if constexpr (UP) {
-      const float cyp_ = LP(A, 0);
-      Ly += q.hi_c * (cyp_ - cc);
+      const T cyp_ = LP(A, 0);
+      Ly = fmaT(q.hi_c, cyp_ - cc, Ly);
       const float crfp = ion == 0 ? q.crf_pp : q.crf_mp;
-      const float cpf = 0.5f * (cc + cyp_), dph = phyp - ph0;
-      Fy_jp = vt * (crfp + cpf) - s * q.Dihp * (crfp * dph + cpf * (q.dPrefp + dph));
+      const T cpf = 0.5f * (cc + cyp_), dph = phyp - ph0;
+      Fy_jp = fmaT(vt, cpf + crfp, (-sD * q.Dihp) * fmaT(cpf, dph + q.dPrefp, crfp * dph));
     }
     if (ion == 0) cy.fp = Fy_jp;
     else cy.fm = Fy_jp;
-    const float H = -((Fx_ip - Fx_i) * k.idx + (Fy_jp - Fy_j) * q.idy + (Fz_kp - Fz_k) * k.idz);
-    const float r = k.dt * (k.gam * H + k.zet * Ho[3 + ion] + k.aD * Ly);
+    const T div = fmaT(Fz_kp - Fz_k, k.idz, fmaT(Fy_jp - Fy_j, q.idy, (Fx_ip - Fx_i) * k.idx));
+    const T H = -div;
+    const T r = k.dt * fmaT(k.aD, Ly, fmaT(-k.gam, div, k.zet * Ho[3 + ion]));
     if (ion == 0) {
       o.rcp = r;
       o.Hcp = H;
@@ -285,24 +330,24 @@ __device__ __forceinline__ CellOut rhs_cell(const float* __restrict__ bm, const 
 }
 
 // Plane j of a chunk starting at jb: the specialisation for its position.
-template <int AS, int SZ>
-__device__ __forceinline__ CellOut rhs_cell_at(int j, int jb, int nyc, const float* bm, const float* bo,
-                                               const float* bp, const float Ho[5], const PlaneC& q, const CellK& kw,
-                                               const CoefF& k, YCarry& cy) {
+template <typename T, int AS, int SZ>
+__device__ __forceinline__ CellOut<T> rhs_cell_at(int j, int jb, int nyc, const float* bm, const float* bo,
+                                                  const float* bp, const T Ho[5], const PlaneC& q,
+                                                  const CellK<T>& kw, const CoefF& k, YCarry<T>& cy) {
   if (j > jb) {
-    if (j < nyc - 1) return rhs_cell<AS, SZ, true, true, true>(bm, bo, bp, Ho, q, kw, k, cy);
-    return rhs_cell<AS, SZ, true, false, true>(bm, bo, bp, Ho, q, kw, k, cy);
+    if (j < nyc - 1) return rhs_cell<T, AS, SZ, true, true, true>(bm, bo, bp, Ho, q, kw, k, cy);
+    return rhs_cell<T, AS, SZ, true, false, true>(bm, bo, bp, Ho, q, kw, k, cy);
   }
   if (j > 0) {
-    if (j < nyc - 1) return rhs_cell<AS, SZ, true, true, false>(bm, bo, bp, Ho, q, kw, k, cy);
-    return rhs_cell<AS, SZ, true, false, false>(bm, bo, bp, Ho, q, kw, k, cy);
+    if (j < nyc - 1) return rhs_cell<T, AS, SZ, true, true, false>(bm, bo, bp, Ho, q, kw, k, cy);
+    return rhs_cell<T, AS, SZ, true, false, false>(bm, bo, bp, Ho, q, kw, k, cy);
   }
-  if (j < nyc - 1) return rhs_cell<AS, SZ, false, true, false>(bm, bo, bp, Ho, q, kw, k, cy);
-  return rhs_cell<AS, SZ, false, false, false>(bm, bo, bp, Ho, q, kw, k, cy);
+  if (j < nyc - 1) return rhs_cell<T, AS, SZ, false, true, false>(bm, bo, bp, Ho, q, kw, k, cy);
+  return rhs_cell<T, AS, SZ, false, false, false>(bm, bo, bp, Ho, q, kw, k, cy);
 }
 
 __device__ __forceinline__ void store_cell(const Fields<float>& f, float* rcp, float* rcm, const Shadows& sh,
-                                           size_t c0, bool has_dn, const CellOut& o) {
+                                           size_t c0, bool has_dn, const CellOut<float>& o) {
   f.ru[c0] = o.ru;
   f.Hu[c0] = o.Hu;
   f.rw[c0] = o.rw;
@@ -315,6 +360,33 @@ __device__ __forceinline__ void store_cell(const Fields<float>& f, float* rcp, f
   sh.Hcp[c0] = o.Hcp;
   rcm[c0] = o.rcm;
   sh.Hcm[c0] = o.Hcm;
+}
+
+// The pair: cell 0 at c0, cell 1 at c1.
+__device__ __forceinline__ void store_cell(const Fields<float>& f, float* rcp, float* rcm, const Shadows& sh,
+                                           size_t c0, size_t c1, bool has_dn, const CellOut<V2>& o) {
+  f.ru[c0] = o.ru.v.x;
+  f.ru[c1] = o.ru.v.y;
+  f.Hu[c0] = o.Hu.v.x;
+  f.Hu[c1] = o.Hu.v.y;
+  f.rw[c0] = o.rw.v.x;
+  f.rw[c1] = o.rw.v.y;
+  f.Hw[c0] = o.Hw.v.x;
+  f.Hw[c1] = o.Hw.v.y;
+  if (has_dn) {
+    f.rv[c0] = o.rv.v.x;
+    f.rv[c1] = o.rv.v.y;
+    f.Hv[c0] = o.Hv.v.x;
+    f.Hv[c1] = o.Hv.v.y;
+  }
+  rcp[c0] = o.rcp.v.x;
+  rcp[c1] = o.rcp.v.y;
+  sh.Hcp[c0] = o.Hcp.v.x;
+  sh.Hcp[c1] = o.Hcp.v.y;
+  rcm[c0] = o.rcm.v.x;
+  rcm[c1] = o.rcm.v.y;
+  sh.Hcm[c0] = o.Hcm.v.x;
+  sh.Hcm[c1] = o.Hcm.v.y;
 }
 
 __device__ __forceinline__ void wall_values(const Fields<float>& f, size_t P, size_t ck, float Uw, float& ub,
@@ -339,7 +411,7 @@ __device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.a
 // with NT = (TX + 2) (TZ CZ + 2), then (HSM) old H [3 slots][5 arrays][TX TZ],
 // then the per-plane table [jchunk][kPlaneLd].
 __host__ __device__ constexpr size_t rhs_tile_floats(int tx, int tz, int cz, bool hsm) {
-  return 4 * 7 * (size_t)(tx + 2) * (tz * cz + 2) + (hsm ? 3 * 5 * (size_t)tx * tz : 0);
+  return 4 * 7 * (size_t)(tx + 2) * (tz * cz + 2) + (hsm ? 3 * 5 * (size_t)tx * tz * cz : 0);
 }
 
 // TX x TZ threads own a TX x (TZ CZ) tile of cells; each thread computes CZ
@@ -352,7 +424,7 @@ __global__ void __launch_bounds__(TX * TZ, MINB)
   constexpr int TW = TX + 2, NT = TW * (TZ * CZ + 2), NTH = TX * TZ, E = (NT + NTH - 1) / NTH;
   extern __shared__ __align__(16) float rhs_smem[];
   float* tiles = rhs_smem;                                    // [4][NA][NT]
-  float* holds = rhs_smem + 4 * NA * NT;                      // [3][NH][NTH] (HSM)
+  float* holds = rhs_smem + 4 * NA * NT;                      // [3][NH][CZ][NTH] (HSM)
   float* pct = rhs_smem + rhs_tile_floats(TX, TZ, CZ, HSM);   // [jchunk][kPlaneLd]
   const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * TX + tx;
   const int nx = g.nx, nz = g.nz, nyc = g.nyc;
@@ -386,9 +458,12 @@ __global__ void __launch_bounds__(TX * TZ, MINB)
       }
       if constexpr (HSM) {
         if (q >= jb && q < je) {
-          float* hs = holds + (size_t)(q % 3) * NH * NTH;
+          float* hs = holds + (size_t)(q % 3) * NH * CZ * NTH;
 #pragma unroll
-          for (int h = 0; h < NH; ++h) cp_async4(hs + h * NTH + tid, hsrc[h] + qP + ck);
+          for (int h = 0; h < NH; ++h)
+#pragma unroll
+            for (int cz = 0; cz < CZ; ++cz)
+              cp_async4(hs + (h * CZ + cz) * NTH + tid, hsrc[h] + qP + ck + (size_t)cz * nx);
         }
       }
     }
@@ -399,46 +474,54 @@ __global__ void __launch_bounds__(TX * TZ, MINB)
   issue_plane(jb + 1);
   fill_plane_table(pct, mt, R, cf.D, jb, je, jchunk, tid, NTH);
 
-  CellK kc[CZ];
+  // CZ = 1: one cell in FP32 scalars; CZ = 2: the cell pair in packed FP32
+  using T = typename std::conditional<CZ == 2, V2, float>::type;
+  static_assert(CZ == 1 || CZ == 2, "one cell or a packed pair per thread");
+  // wall velocities of the column(s), read only on the two wall planes
+  auto walls = [&]() {
+    float ub[CZ], ut[CZ], wb[CZ], wt[CZ];
 #pragma unroll
-  for (int cz = 0; cz < CZ; ++cz) {
-    float ub, ut, wb, wt;
-    wall_values(f, P, ck + (size_t)cz * nx, cf.Uw, ub, ut, wb, wt);
-    kc[cz] = cell_consts(cf, ub, ut, wb, wt);
-  }
+    for (int cz = 0; cz < CZ; ++cz) wall_values(f, P, ck + (size_t)cz * nx, cf.Uw, ub[cz], ut[cz], wb[cz], wt[cz]);
+    if constexpr (CZ == 2) return CellK<T>{V2(ub[0], ub[1]), V2(ut[0], ut[1]), V2(wb[0], wb[1]), V2(wt[0], wt[1])};
+    else return CellK<T>{ub[0], ut[0], wb[0], wt[0]};
+  };
   const int c = (tz * CZ + 1) * TW + tx + 1;   // first cell in a tile
-  YCarry cy[CZ];
-#pragma unroll
-  for (int cz = 0; cz < CZ; ++cz) cy[cz] = YCarry{0.f, 0.f, 0.f, 0.f, 0.f};
+  YCarry<T> cy{0.f, 0.f, 0.f, 0.f, 0.f};
   for (int j = jb; j < je; ++j) {
     const size_t c0 = (size_t)j * P + ck;
-    float Ho[CZ][5];
+    float Hf[CZ][NH];
     if constexpr (!HSM) {
 #pragma unroll
       for (int cz = 0; cz < CZ; ++cz) {
         const size_t o = c0 + (size_t)cz * nx;
 #pragma unroll
-        for (int h = 0; h < NH; ++h) Ho[cz][h] = __ldg(hsrc[h] + o);
+        for (int h = 0; h < NH; ++h) Hf[cz][h] = __ldg(hsrc[h] + o);
       }
     }
     issue_plane(j + 2);
     cp_async_wait_all_but_one();   // planes up to j + 1 have landed (this thread's copies)
     __syncthreads();               // ... and every thread's (and the plane table)
     if constexpr (HSM) {
-      const float* hs = holds + (size_t)(j % 3) * NH * NTH + tid;
+      const float* hs = holds + (size_t)(j % 3) * NH * CZ * NTH + tid;
 #pragma unroll
-      for (int h = 0; h < NH; ++h) Ho[0][h] = hs[h * NTH];
+      for (int h = 0; h < NH; ++h)
+#pragma unroll
+        for (int cz = 0; cz < CZ; ++cz) Hf[cz][h] = hs[(h * CZ + cz) * NTH];
+    }
+    T Ho[NH];
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+      if constexpr (CZ == 2) Ho[h] = V2(Hf[0][h], Hf[1][h]);
+      else Ho[h] = Hf[0][h];
     }
     const float* bm = tiles + (size_t)((j + 3) & 3) * NA * NT + c;
     const float* bo = tiles + (size_t)(j & 3) * NA * NT + c;
     const float* bp = tiles + (size_t)((j + 1) & 3) * NA * NT + c;
     const PlaneC q = plane_consts(pct + (size_t)(j - jb) * kPlaneLd);
-#pragma unroll
-    for (int cz = 0; cz < CZ; ++cz) {
-      const CellOut o =
-          rhs_cell_at<NT, TW>(j, jb, nyc, bm + cz * TW, bo + cz * TW, bp + cz * TW, Ho[cz], q, kc[cz], cf, cy[cz]);
-      store_cell(f, rcp, rcm, sh, c0 + (size_t)cz * nx, j > 0, o);
-    }
+    const CellK<T> kc = (j == 0 || j == nyc - 1) ? walls() : CellK<T>{0.f, 0.f, 0.f, 0.f};
+    const CellOut<T> o = rhs_cell_at<T, NT, TW>(j, jb, nyc, bm, bo, bp, Ho, q, kc, cf, cy);
+    if constexpr (CZ == 2) store_cell(f, rcp, rcm, sh, c0, c0 + nx, j > 0, o);
+    else store_cell(f, rcp, rcm, sh, c0, j > 0, o);
     __syncthreads();
   }
 }
@@ -578,9 +661,9 @@ __global__ void __launch_bounds__(NX * TZB, 1)
   const size_t ck = (size_t)(k0 + tz) * NX + tx;
   float ub, ut, wb, wt;
   wall_values(f, P, ck, cf.Uw, ub, ut, wb, wt);
-  const CellK kc = cell_consts(cf, ub, ut, wb, wt);
+  const CellK<float> kc{ub, ut, wb, wt};
   const int co = (tz + 1) * G::S + 32 + tx;   // this cell in array 0 of a slot
-  YCarry cy{0.f, 0.f, 0.f, 0.f, 0.f};
+  YCarry<float> cy{0.f, 0.f, 0.f, 0.f, 0.f};
   int waited = jb - 2;   // last plane this thread has seen land
   bool bad = false;
   for (int j = jb; j < je; ++j) {
@@ -604,7 +687,7 @@ __global__ void __launch_bounds__(NX * TZB, 1)
     const float* hs = holds + (size_t)(n0 & 3) * G::HS + tz * NX + tx;
     const float Ho[5] = {hs[0], hs[TZB * NX], hs[2 * TZB * NX], hs[3 * TZB * NX], hs[4 * TZB * NX]};
     const PlaneC q = plane_consts(pct + (size_t)(j - jb) * kPlaneLd);
-    const CellOut o = rhs_cell_at<G::AS, G::S>(j, jb, nyc, bm, bo, bp, Ho, q, kc, cf, cy);
+    const CellOut<float> o = rhs_cell_at<float, G::AS, G::S>(j, jb, nyc, bm, bo, bp, Ho, q, kc, cf, cy);
     store_cell(f, rcp, rcm, sh, (size_t)j * P + ck, j > 0, o);
     __syncthreads();   // slot of plane j - 1 is free
     if (j + 3 <= je) {
@@ -722,9 +805,10 @@ cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const Mi
       default: return go(k_rhs_mixed_tma<256, 2>, TmaGeo<256, 2>{}, 2);
     }
   }
-  // cp.async tiles.  lc_rhs_bx: 0 / 32 = 32 x 8 threads with two cells each in z
-  // (two blocks per SM), 64 = the same capped to three blocks per SM, 16 = 32 x 8
-  // threads with one cell each; narrower grids fall back to 8 x 4 / 4 x 4
+  // cp.async tiles.  lc_rhs_bx: 0 / 32 = 32 x 8 threads with a packed pair of
+  // cells each in z, old H by direct loads; 64 = the same with old H on the
+  // cp.async plane ring; 16 = 32 x 8 threads with one cell each; narrower grids
+  // fall back to 8 x 4 / 4 x 4
   auto go = [&](auto kern, int bx, int bz, int cz, bool hsm, int per_sm) {
     const int nxz = (g.nx / bx) * (g.nz / (bz * cz));
     const int jc = chunk(nxz, per_sm);
@@ -737,8 +821,8 @@ cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const Mi
     kern<<<grd, dim3(bx, bz), smem, s>>>(f, rp, rm, sh, R, g, m, cf, jc);
     return cudaGetLastError();
   };
-  if (g.nx >= 32 && g.nz >= 16 && g.lc_rhs_bx == 64)   // two cells, three blocks per SM (registers capped)
-    return go(k_rhs_mixed_tile<32, 8, 2, false, 3>, 32, 8, 2, false, 3);
+  if (g.nx >= 32 && g.nz >= 16 && g.lc_rhs_bx == 64)   // two cells, old H on the cp.async ring
+    return go(k_rhs_mixed_tile<32, 8, 2, true, 2>, 32, 8, 2, true, 2);
   if (g.nx >= 32 && g.nz >= 16 && g.lc_rhs_bx != 16) return go(k_rhs_mixed_tile<32, 8, 2, false, 2>, 32, 8, 2, false, 2);
   if (g.nx >= 32 && g.nz >= 8) return go(k_rhs_mixed_tile<32, 8, 1, true, 3>, 32, 8, 1, true, 3);
   if (g.nx >= 8) return go(k_rhs_mixed_tile<8, 4, 1, true, 24>, 8, 4, 1, true, 24);
