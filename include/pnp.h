@@ -174,8 +174,19 @@ int pnp_poisson_noalloc(int nx, int ny, int nz, double Lx, double Lz, const doub
  * the current state (advection, x/z diffusion, Coulomb force, migration). */
 int pnp_eval_explicit(pnp_ctx* ctx);
 
-/* Device error word of the last diagnostics (synchronises). */
+/* Device error word of the last diagnostics, or PNP_ERR_TIMEOUT when a bounded
+ * copy wait of a kernel ran out (sticky, takes precedence); synchronises. */
 int pnp_status(pnp_ctx* ctx);
+
+/* Zero the device error words (synchronises). */
+int pnp_clear_status(pnp_ctx* ctx);
+
+/* Failure-path self-test (no counterpart in the paper): one block waits, with
+ * the same bounded mbarrier wait the TMA stencil uses, on a barrier that no
+ * copy completes; after limit_s seconds (0 < limit_s <= 10) the wait gives up
+ * and records PNP_ERR_TIMEOUT.  Faults and hangs nothing; returns pnp_status
+ * (PNP_ERR_TIMEOUT on a working GPU).  Clear with pnp_clear_status. */
+int pnp_selftest_wait_timeout(pnp_ctx* ctx, double limit_s);
 
 /* Measured FP64 FMA throughput of this device in FLOP/s (bounded microbenchmark
  * on the context's stream): the ALU ceiling of the FP64 kernels. */

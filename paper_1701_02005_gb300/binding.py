@@ -72,6 +72,8 @@ EXPORTS = {
                                       C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pnp_eval_explicit": (C.c_int, [C.c_void_p]),
     "pnp_status": (C.c_int, [C.c_void_p]),
+    "pnp_clear_status": (C.c_int, [C.c_void_p]),
+    "pnp_selftest_wait_timeout": (C.c_int, [C.c_void_p, C.c_double]),
     "pnp_fp64_peak": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "pnp_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_int,
                               C.POINTER(C.c_int)]),
@@ -158,6 +160,8 @@ pnp_poisson = _fwd("pnp_poisson")
 pnp_poisson_noalloc = _fwd("pnp_poisson_noalloc")
 pnp_eval_explicit = _fwd("pnp_eval_explicit")
 pnp_status = _fwd("pnp_status")
+pnp_clear_status = _fwd("pnp_clear_status")
+pnp_selftest_wait_timeout = _fwd("pnp_selftest_wait_timeout")
 pnp_fp64_peak = _fwd("pnp_fp64_peak")
 pnp_profile = _fwd("pnp_profile")
 pnp_autotune = _fwd("pnp_autotune")

@@ -555,16 +555,32 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Bounded wait for a phase of an mbarrier: gives up after about two seconds
-// (or 2^26 polls), so a copy that never completes cannot hang the GPU.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+// Bounded wait for a phase of an mbarrier: gives up after limit_ns (two
+// seconds for the stencil's copies) or 2^26 polls, so a copy that never
+// completes cannot hang the GPU; the caller records the failure.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity,
+                                          unsigned long long limit_ns = 2000000000ull) {
   if (mbar_try_wait(b, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (int it = 0; it < (1 << 26); ++it) {
     if (mbar_try_wait(b, parity)) return true;
-    if ((it & 255) == 0 && global_ns() - t0 > 2000000000ull) break;
+    if ((it & 255) == 0 && global_ns() - t0 > limit_ns) break;
   }
   return false;
+}
+
+// Self-test of the failure path: one thread promises 16 bytes on an mbarrier
+// that no copy ever completes and waits with the bounded wait above; the wait
+// runs out and the timeout is recorded in the context's error word.  Nothing
+// is in flight when the block exits.
+__global__ void k_wait_selftest(int* __restrict__ err, unsigned long long limit_ns) {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_arrive_expect_tx(&bar, 16);
+    if (!mbar_wait(&bar, 0, limit_ns)) atomicExch(err, PNP_ERR_TIMEOUT);
+  }
 }
 
 __device__ __forceinline__ void tma_row(float* dst, const CUtensorMap* m, int x, int z, int y,
@@ -720,6 +736,11 @@ int rhs_tma_rows(int nx) {
 }
 
 }  // namespace
+
+cudaError_t launch_wait_selftest(int* err, double limit_s, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(err, (unsigned long long)(limit_s * 1e9));
+  return cudaGetLastError();
+}
 
 bool rhs_tma_eligible(const Geo& g) {
   const int tzb = rhs_tma_rows(g.nx);

@@ -1128,6 +1128,19 @@ int pnp_eval_explicit(pnp_ctx* c) {
   return e == cudaSuccess ? PNP_OK : PNP_ERR_CUDA;
 }
 
+int pnp_clear_status(pnp_ctx* c) {
+  if (!c) return PNP_ERR_ARG;
+  CK(cudaMemsetAsync(c->status_d, 0, 2 * sizeof(int), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PNP_OK;
+}
+
+int pnp_selftest_wait_timeout(pnp_ctx* c, double limit_s) {
+  if (!c || !(limit_s > 0.0) || limit_s > 10.0) return PNP_ERR_ARG;
+  CK(launch_wait_selftest(c->status_d + 1, limit_s, c->stream));
+  return pnp_status(c);
+}
+
 int pnp_status(pnp_ctx* c) {
   if (!c) return PNP_ERR_ARG;
   int st[2] = {0, 0};

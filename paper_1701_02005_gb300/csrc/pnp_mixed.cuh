@@ -59,6 +59,8 @@ struct RhsMaps {
 };
 
 bool rhs_tma_eligible(const Geo& g);
+// One bounded mbarrier wait that cannot complete (failure-path self-test).
+cudaError_t launch_wait_selftest(int* err, double limit_s, cudaStream_t s);
 cudaError_t build_rhs_maps(RhsMaps* m, const Fields<float>& f, const Shadows& sh, const Geo& g);
 // maps == nullptr selects the cp.async tile kernel; err receives PNP_ERR_TIMEOUT
 // if a TMA copy does not complete within the kernel's wait limit.

@@ -100,7 +100,7 @@ class Solver:
     def diagnostics(self):
         d = B.pnp_diag()
         code = B.pnp_diagnostics(self.ctx, C.byref(d))
-        if code not in (B.PNP_OK, B.PNP_ERR_NONFINITE, B.PNP_ERR_NEGATIVE_C):
+        if code not in (B.PNP_OK, B.PNP_ERR_NONFINITE, B.PNP_ERR_NEGATIVE_C, B.PNP_ERR_TIMEOUT):
             B.check(code, "pnp_diagnostics")
         return d.as_dict()
 

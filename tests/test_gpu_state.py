@@ -64,3 +64,26 @@ def test_unstable_step_is_reported_not_faulted():
     s.step(2, 0.001)
     assert s.diagnostics()["status"] == B.PNP_OK
     s.close()
+
+
+def test_copy_wait_timeout_is_reported_and_cleared():
+    # the bounded mbarrier wait of the TMA stencil, run on a barrier no copy
+    # completes: it gives up after the limit, records PNP_ERR_TIMEOUT, and the
+    # context keeps working once the status is cleared
+    import math
+
+    from paper_1701_02005_gb300 import binding as B
+    from paper_1701_02005_gb300.solver import Solver
+
+    s = Solver(32, 33, 32, 2 * math.pi, math.pi, stretch=2.0, precision=B.PNP_MIXED)
+    s.set_params(400.0, 0.05, 1.0, 2.0, 0.5)
+    s.init_state(B.PNP_IC_PB, 3, 1e-2)
+    s.step(2, 0.01)
+    assert s.status() == 0
+    assert B.pnp_selftest_wait_timeout(s.ctx, 0.05) == B.PNP_ERR_TIMEOUT
+    assert s.status() == B.PNP_ERR_TIMEOUT          # sticky until cleared
+    assert s.diagnostics()["status"] == B.PNP_ERR_TIMEOUT
+    B.check(B.pnp_clear_status(s.ctx), "pnp_clear_status")
+    s.step(2, 0.01)
+    assert s.status() == 0 and s.diagnostics()["status"] == 0
+    s.close()
