@@ -217,6 +217,18 @@ __global__ void k_fft_x_fwd(SrcArgs<T, TV> src, Geo g, Metrics m, cplx<T>* __res
   }
 }
 
+// Row buffer of the register x-transforms: the exchange is laid out
+// [k1][g] with a stride of G + 1 (so the G-point reads of pass 2, one run of G
+// values per thread, fall in distinct banks), the natural-order row reuses it,
+// and the row stride is 8 mod 16 complex values so that the two rows served
+// by one half-warp of 64-bit accesses use opposite halves of the banks.
+template <int NH, int R1>
+constexpr int fx_row_stride() {
+  constexpr int G = NH / R1;
+  constexpr int need = R1 * (G + 1) > NH + 1 ? R1 * (G + 1) : NH + 1;
+  return need + ((8 - need % 16) + 16) % 16;
+}
+
 // FP32 real x-transforms with the two-pass register FFT (pnp_regfft.cuh) of
 // the half-length complex sequence z_t = x_2t + i x_2t+1.  G = NH / R1 threads
 // own a row (consecutive lanes of one warp, so every exchange inside a row
@@ -236,7 +248,7 @@ __global__ void __launch_bounds__(256) k_fft_x_fwd_reg(SrcArgs<float, TV> src, G
   extern __shared__ __align__(16) float fx_smem[];
   cplx<float>* twh = reinterpret_cast<cplx<float>*>(fx_smem);   // [NH]
   cplx<float>* twp = twh + NH;                                   // [NH + 1]
-  cplx<float>* rows = twp + NH + 1;                              // [ROWS][NH + 1]
+  cplx<float>* rows = twp + NH + 1;                              // [ROWS][row stride]
   const int gi = threadIdx.x, ry = threadIdx.y, tid = ry * G + gi;
   const int nthr = G * blockDim.y;
   for (int e = tid; e < NH; e += nthr) twh[e] = tw_half[e];
@@ -284,10 +296,10 @@ __global__ void __launch_bounds__(256) k_fft_x_fwd_reg(SrcArgs<float, TV> src, G
   }
   __syncthreads();   // twiddle tables
   rfft::dft<false, R1>(v);
-  cplx<float>* xr = rows + (size_t)ry * (NH + 1);
+  cplx<float>* xr = rows + (size_t)ry * fx_row_stride<NH, R1>();
   rfft::static_for<0, R1>([&](auto kc) {
     constexpr int k1 = decltype(kc)::value;
-    xr[k1 * G + gi] = cmul(v[rfft::bitrev(k1, R1)], twh[gi * k1]);
+    xr[k1 * (G + 1) + gi] = cmul(v[rfft::bitrev(k1, R1)], twh[gi * k1]);
   });
   __syncwarp();
   cplx<float> w[PER][G];
@@ -295,7 +307,7 @@ __global__ void __launch_bounds__(256) k_fft_x_fwd_reg(SrcArgs<float, TV> src, G
   for (int p = 0; p < PER; ++p) {
     const int k1 = gi * PER + p;
 #pragma unroll
-    for (int q = 0; q < G; ++q) w[p][q] = xr[k1 * G + q];
+    for (int q = 0; q < G; ++q) w[p][q] = xr[k1 * (G + 1) + q];
     rfft::dft<false, G>(w[p]);
   }
   __syncwarp();
@@ -333,7 +345,7 @@ __global__ void __launch_bounds__(256) k_fft_x_inv_reg(PoissonDst dst, const cpl
   extern __shared__ __align__(16) float fx_smem[];
   cplx<float>* twh = reinterpret_cast<cplx<float>*>(fx_smem);   // [NH] (conjugated)
   cplx<float>* twp = twh + NH;                                   // [NH]
-  cplx<float>* rows = twp + NH;                                  // [ROWS][NH + 1]
+  cplx<float>* rows = twp + NH;                                  // [ROWS][row stride]
   const int gi = threadIdx.x, ry = threadIdx.y, tid = ry * G + gi;
   const int nthr = G * blockDim.y;
   for (int e = tid; e < NH; e += nthr) {
@@ -362,10 +374,10 @@ __global__ void __launch_bounds__(256) k_fft_x_inv_reg(PoissonDst dst, const cpl
     v[r] = z;
   }
   rfft::dft<true, R1>(v);
-  cplx<float>* xr = rows + (size_t)ry * (NH + 1);
+  cplx<float>* xr = rows + (size_t)ry * fx_row_stride<NH, R1>();
   rfft::static_for<0, R1>([&](auto kc) {
     constexpr int k1 = decltype(kc)::value;
-    xr[k1 * G + gi] = cmul(v[rfft::bitrev(k1, R1)], twh[gi * k1]);
+    xr[k1 * (G + 1) + gi] = cmul(v[rfft::bitrev(k1, R1)], twh[gi * k1]);
   });
   __syncwarp();
   if (!live) return;
@@ -378,7 +390,7 @@ __global__ void __launch_bounds__(256) k_fft_x_inv_reg(PoissonDst dst, const cpl
     const int k1 = gi * PER + p;
     cplx<float> w[G];
 #pragma unroll
-    for (int q = 0; q < G; ++q) w[q] = xr[k1 * G + q];
+    for (int q = 0; q < G; ++q) w[q] = xr[k1 * (G + 1) + q];
     rfft::dft<true, G>(w);
     rfft::static_for<0, G>([&](auto kc) {
       constexpr int k2 = decltype(kc)::value;
@@ -402,7 +414,9 @@ __global__ void __launch_bounds__(256) k_fft_x_inv_reg(PoissonDst dst, const cpl
 template <int NH, int R1>
 constexpr int fx_rows() { return 256 / (NH / R1); }
 template <int NH, int R1>
-constexpr size_t fx_smem() { return sizeof(cplx<float>) * ((size_t)2 * NH + 1 + (size_t)fx_rows<NH, R1>() * (NH + 1)); }
+constexpr size_t fx_smem() {
+  return sizeof(cplx<float>) * ((size_t)2 * NH + 1 + (size_t)fx_rows<NH, R1>() * fx_row_stride<NH, R1>());
+}
 
 template <typename T>
 static void fft_x_shape(const Geo& g, dim3& blk, dim3& grd, size_t& smem) {
