@@ -63,6 +63,11 @@ enum {
   PNP_HCP = 10, PNP_HCM = 11,
   PNP_NFIELDS = 12
 };
+/* The next step's first RK3 substage has zeta = 0 and never reads H, so after
+ * pnp_step in PNP_MIXED the H fields hold the second substage's explicit terms
+ * (the third substage's are not written); PNP_FP64 keeps the third's. Either
+ * way the continuation of the run is the same. pnp_eval_explicit always
+ * stores them. */
 
 /* Initial conditions for pnp_init_state. */
 enum {

@@ -347,46 +347,50 @@ __device__ __forceinline__ CellOut<T> rhs_cell_at(int j, int jb, int nyc, const 
 }
 
 __device__ __forceinline__ void store_cell(const Fields<float>& f, float* rcp, float* rcm, const Shadows& sh,
-                                           size_t c0, bool has_dn, const CellOut<float>& o) {
+                                           size_t c0, bool has_dn, bool keep_h, const CellOut<float>& o) {
   f.ru[c0] = o.ru;
-  f.Hu[c0] = o.Hu;
   f.rw[c0] = o.rw;
-  f.Hw[c0] = o.Hw;
-  if (has_dn) {
-    f.rv[c0] = o.rv;
-    f.Hv[c0] = o.Hv;
-  }
+  if (has_dn) f.rv[c0] = o.rv;
   rcp[c0] = o.rcp;
-  sh.Hcp[c0] = o.Hcp;
   rcm[c0] = o.rcm;
-  sh.Hcm[c0] = o.Hcm;
+  if (keep_h) {
+    f.Hu[c0] = o.Hu;
+    f.Hw[c0] = o.Hw;
+    if (has_dn) f.Hv[c0] = o.Hv;
+    sh.Hcp[c0] = o.Hcp;
+    sh.Hcm[c0] = o.Hcm;
+  }
 }
 
 // The pair: cell 0 at c0, cell 1 at c1.
 __device__ __forceinline__ void store_cell(const Fields<float>& f, float* rcp, float* rcm, const Shadows& sh,
-                                           size_t c0, size_t c1, bool has_dn, const CellOut<V2>& o) {
+                                           size_t c0, size_t c1, bool has_dn, bool keep_h, const CellOut<V2>& o) {
   f.ru[c0] = o.ru.v.x;
   f.ru[c1] = o.ru.v.y;
-  f.Hu[c0] = o.Hu.v.x;
-  f.Hu[c1] = o.Hu.v.y;
   f.rw[c0] = o.rw.v.x;
   f.rw[c1] = o.rw.v.y;
-  f.Hw[c0] = o.Hw.v.x;
-  f.Hw[c1] = o.Hw.v.y;
   if (has_dn) {
     f.rv[c0] = o.rv.v.x;
     f.rv[c1] = o.rv.v.y;
-    f.Hv[c0] = o.Hv.v.x;
-    f.Hv[c1] = o.Hv.v.y;
   }
   rcp[c0] = o.rcp.v.x;
   rcp[c1] = o.rcp.v.y;
-  sh.Hcp[c0] = o.Hcp.v.x;
-  sh.Hcp[c1] = o.Hcp.v.y;
   rcm[c0] = o.rcm.v.x;
   rcm[c1] = o.rcm.v.y;
-  sh.Hcm[c0] = o.Hcm.v.x;
-  sh.Hcm[c1] = o.Hcm.v.y;
+  if (keep_h) {
+    f.Hu[c0] = o.Hu.v.x;
+    f.Hu[c1] = o.Hu.v.y;
+    f.Hw[c0] = o.Hw.v.x;
+    f.Hw[c1] = o.Hw.v.y;
+    if (has_dn) {
+      f.Hv[c0] = o.Hv.v.x;
+      f.Hv[c1] = o.Hv.v.y;
+    }
+    sh.Hcp[c0] = o.Hcp.v.x;
+    sh.Hcp[c1] = o.Hcp.v.y;
+    sh.Hcm[c0] = o.Hcm.v.x;
+    sh.Hcm[c1] = o.Hcm.v.y;
+  }
 }
 
 __device__ __forceinline__ void wall_values(const Fields<float>& f, size_t P, size_t ck, float Uw, float& ub,
@@ -443,6 +447,7 @@ __global__ void __launch_bounds__(TX * TZ, MINB)
   }
   const float* src[NA] = {f.u, f.w, f.v, f.p, sh.phi, sh.cp, sh.cm};
   const float* hsrc[NH] = {f.Hu, f.Hw, f.Hv, sh.Hcp, sh.Hcm};
+  const bool read_h = cf.zet != 0.f, keep_h = cf.keep_h != 0;   // uniform per launch
   // plane q (tiles into slot q & 3, old H into slot q mod 3); one commit group
   // per plane, empty when q is outside the chunk's window or the array
   auto issue_plane = [&](int q) {
@@ -457,7 +462,7 @@ __global__ void __launch_bounds__(TX * TZ, MINB)
           if (tid + e * NTH < NT) cp_async4(ts + a * NT + tid + e * NTH, src[a] + qP + off[e]);
       }
       if constexpr (HSM) {
-        if (q >= jb && q < je) {
+        if (read_h && q >= jb && q < je) {
           float* hs = holds + (size_t)(q % 3) * NH * CZ * NTH;
 #pragma unroll
           for (int h = 0; h < NH; ++h)
@@ -490,23 +495,31 @@ __global__ void __launch_bounds__(TX * TZ, MINB)
   for (int j = jb; j < je; ++j) {
     const size_t c0 = (size_t)j * P + ck;
     float Hf[CZ][NH];
+#pragma unroll
+    for (int cz = 0; cz < CZ; ++cz)
+#pragma unroll
+      for (int h = 0; h < NH; ++h) Hf[cz][h] = 0.f;
     if constexpr (!HSM) {
+      if (read_h) {
 #pragma unroll
-      for (int cz = 0; cz < CZ; ++cz) {
-        const size_t o = c0 + (size_t)cz * nx;
+        for (int cz = 0; cz < CZ; ++cz) {
+          const size_t o = c0 + (size_t)cz * nx;
 #pragma unroll
-        for (int h = 0; h < NH; ++h) Hf[cz][h] = __ldg(hsrc[h] + o);
+          for (int h = 0; h < NH; ++h) Hf[cz][h] = __ldg(hsrc[h] + o);
+        }
       }
     }
     issue_plane(j + 2);
     cp_async_wait_all_but_one();   // planes up to j + 1 have landed (this thread's copies)
     __syncthreads();               // ... and every thread's (and the plane table)
     if constexpr (HSM) {
-      const float* hs = holds + (size_t)(j % 3) * NH * CZ * NTH + tid;
+      if (read_h) {
+        const float* hs = holds + (size_t)(j % 3) * NH * CZ * NTH + tid;
 #pragma unroll
-      for (int h = 0; h < NH; ++h)
+        for (int h = 0; h < NH; ++h)
 #pragma unroll
-        for (int cz = 0; cz < CZ; ++cz) Hf[cz][h] = hs[(h * CZ + cz) * NTH];
+          for (int cz = 0; cz < CZ; ++cz) Hf[cz][h] = hs[(h * CZ + cz) * NTH];
+      }
     }
     T Ho[NH];
 #pragma unroll
@@ -520,8 +533,8 @@ __global__ void __launch_bounds__(TX * TZ, MINB)
     const PlaneC q = plane_consts(pct + (size_t)(j - jb) * kPlaneLd);
     const CellK<T> kc = (j == 0 || j == nyc - 1) ? walls() : CellK<T>{0.f, 0.f, 0.f, 0.f};
     const CellOut<T> o = rhs_cell_at<T, NT, TW>(j, jb, nyc, bm, bo, bp, Ho, q, kc, cf, cy);
-    if constexpr (CZ == 2) store_cell(f, rcp, rcm, sh, c0, c0 + nx, j > 0, o);
-    else store_cell(f, rcp, rcm, sh, c0, j > 0, o);
+    if constexpr (CZ == 2) store_cell(f, rcp, rcm, sh, c0, c0 + nx, j > 0, keep_h, o);
+    else store_cell(f, rcp, rcm, sh, c0, j > 0, keep_h, o);
     __syncthreads();
   }
 }
@@ -633,10 +646,11 @@ __global__ void __launch_bounds__(NX * TZB, 1)
   fill_plane_table(pct, mt, R, cf.D, jb, je, jchunk, tid, G::NTHR);
   __syncthreads();
 
+  const bool read_h = cf.zet != 0.f, keep_h = cf.keep_h != 0;   // uniform per launch
   // plane q of the window [jb - 1, je] into slot n & 3, n = q - jb + 1 (warp 0)
   auto issue = [&](int q) {
     const int slot = (q - jb + 1) & 3;
-    const bool hq = q >= jb && q < je;
+    const bool hq = read_h && q >= jb && q < je;
     unsigned bytes = 0;
 #pragma unroll
     for (int a = 0; a < NA; ++a)
@@ -701,10 +715,14 @@ __global__ void __launch_bounds__(NX * TZB, 1)
     const float* bo = tiles + (size_t)(n0 & 3) * G::SLOT + co;
     const float* bp = tiles + (size_t)((n0 + 1) & 3) * G::SLOT + co;
     const float* hs = holds + (size_t)(n0 & 3) * G::HS + tz * NX + tx;
-    const float Ho[5] = {hs[0], hs[TZB * NX], hs[2 * TZB * NX], hs[3 * TZB * NX], hs[4 * TZB * NX]};
+    float Ho[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (read_h) {
+#pragma unroll
+      for (int h = 0; h < 5; ++h) Ho[h] = hs[h * TZB * NX];
+    }
     const PlaneC q = plane_consts(pct + (size_t)(j - jb) * kPlaneLd);
     const CellOut<float> o = rhs_cell_at<float, G::AS, G::S>(j, jb, nyc, bm, bo, bp, Ho, q, kc, cf, cy);
-    store_cell(f, rcp, rcm, sh, (size_t)j * P + ck, j > 0, o);
+    store_cell(f, rcp, rcm, sh, (size_t)j * P + ck, j > 0, keep_h, o);
     __syncthreads();   // slot of plane j - 1 is free
     if (j + 3 <= je) {
       if (warp == 0) issue(j + 3);

@@ -418,7 +418,7 @@ MetricsF metrics_f(const pnp_ctx* c) {
   return MetricsF{c->mf[0], c->mf[1], c->mf[2], c->mf[3], c->mf[4], c->mf[5], c->mf[6], c->mf[7]};
 }
 
-CoefF coef_f(const pnp_ctx* c, const Stage& st) {
+CoefF coef_f(const pnp_ctx* c, const Stage& st, bool keep_h = true) {
   CoefF f{(float)c->g.idx, (float)c->g.idz, (float)c->ph.nu, (float)c->ph.D, (float)c->ph.K, (float)c->ph.Uw,
           (float)st.dt, (float)st.gam, (float)st.zet, (float)st.alp};
   f.idx2 = f.idx * f.idx;
@@ -429,6 +429,7 @@ CoefF coef_f(const pnp_ctx* c, const Stage& st) {
   f.Dz = f.D * f.idz;
   f.anu = f.alp * f.nu;
   f.aD = f.alp * f.D;
+  f.keep_h = keep_h ? 1 : 0;
   return f;
 }
 
@@ -614,7 +615,8 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
   const MixedRefs R = mixed_refs(c);
   const Metrics m = metrics(c);
   mark(c);
-  cudaError_t e = launch_mixed_rhs(f, sh, R, c->g, metrics_f(c), coef_f(c, st), rhs_maps(c), c->status_d + 1, c->stream);
+  cudaError_t e =
+      launch_mixed_rhs(f, sh, R, c->g, metrics_f(c), coef_f(c, st, l < 2), rhs_maps(c), c->status_d + 1, c->stream);
   if (e != cudaSuccess) return e;
   mark(c);
   const CNRowsF cell = cn_rows_f(c, l, 0), face = cn_rows_f(c, l, 1), ion = cn_rows_f(c, l, 2);
@@ -624,12 +626,12 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
     mark(c);
     return poisson_pair<float>(c, st.alp * dt);
   }
-  // The potential depends only on the ions: their CN solve goes first and the
-  // potential pipeline forks onto the auxiliary stream, overlapping the
-  // velocity CN solve, the pressure pipeline and the projection.
-  e = launch_mixed_cn(f, sh, R, c->g, cell, face, ion, l, kCnIons, c->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork, c->stream);
+  // The ion CN solve and the potential depend only on the ions: both fork onto
+  // the auxiliary stream right after the stencil and overlap the velocity CN
+  // solve, the pressure pipeline and the projection.
+  e = cudaEventRecord(c->ev_fork, c->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+  if (e == cudaSuccess) e = launch_mixed_cn(f, sh, R, c->g, cell, face, ion, l, kCnIons, c->aux);
   if (e == cudaSuccess) e = potential_mixed(c, c->aux, c->spec2, c->dscr2);
   if (e == cudaSuccess) e = launch_mixed_cn(f, sh, R, c->g, cell, face, ion, l, kCnVelocity, c->stream);
   if (e == cudaSuccess) e = pressure_projection<float>(c, st.alp * dt, true);

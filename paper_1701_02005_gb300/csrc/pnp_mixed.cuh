@@ -19,6 +19,10 @@ struct CoefF {
   float dt, gam, zet, alp;
   // products used per cell, formed once in FP32 on the host
   float idx2, idz2, Kx, Kz, Dx, Dz, anu, aD;
+  // 0: the explicit terms H of this substage are not stored (the low-storage
+  // RK3's last substage: the next step's first substage has zeta = 0 and never
+  // reads them); the previous H is read only when zet != 0
+  int keep_h;
 };
 
 // FP32 elimination factors of the velocity Crank-Nicolson matrices.
