@@ -8,8 +8,9 @@
 // CN update) and r' = dt [gam H' + zet H'_old + alp D L_y c'] stored in FP32.
 //
 // Both kernels march a chunk of y-planes per block and keep the seven stencil
-// inputs (u, w, v, p, phi', c+', c-') of planes j-1, j, j+1 in a ring of four
-// plane slots in shared memory while plane j+2 lands in the fourth:
+// inputs (u, w, v, p, phi', c+', c-') of planes j-1, j, j+1 in a ring of plane
+// slots in shared memory while the next planes land (four slots and one plane
+// ahead for the TMA rows, five slots and two planes ahead for the tiles):
 //   * k_rhs_mixed_tma: a block owns TZB full x-rows; each row of each array
 //     arrives by one TMA tensor copy (cp.async.bulk.tensor, issued by one
 //     warp, completion on an mbarrier per slot).  The z-halo rows are row
@@ -17,7 +18,8 @@
 //     one-float periodic x-halo from inside shared memory, so no copy ever
 //     leaves the array.  nx in {32, 64, 128, 256}.
 //   * k_rhs_mixed_tile: TX x TZ tiles with a one-cell periodic halo, filled by
-//     per-thread cp.async; any grid.
+//     per-thread cp.async (16-byte chunks for the rows, 4 bytes for the x-halo);
+//     any grid.
 // Tile geometry is compile-time in both, so every neighbour read is a
 // shared-memory load at a constant offset from one of three slot pointers.
 // The arithmetic of a cell is one routine (rhs_cell), specialised at compile
@@ -411,25 +413,53 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Shared memory of the tile kernel (floats): tiles [4 slots][7 arrays][NT]
-// with NT = (TX + 2) (TZ CZ + 2), then (HSM) old H [3 slots][5 arrays][TX TZ],
-// then the per-plane table [jchunk][kPlaneLd].
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+
+// Tile geometry in shared memory.  A tile row holds the TX cells of one z-row
+// from column 0 (16-byte aligned, so the interior lands by 16-byte copies), the
+// +x halo at column TX and the -x halo of the NEXT row at column RS - 1; the
+// array starts with a 4-float pad that holds row 0's -x halo.  Neighbours are
+// therefore at -1 / +1 (x) and -RS / +RS (z) from every cell.
+template <int TX, int TZ, int CZ>
+struct TileGeo {
+  static constexpr int PAD = 4, RS = TX + 4, ROWS = TZ * CZ + 2;
+  static constexpr int NT = PAD + ROWS * RS;   // floats per array, a multiple of 4
+  static constexpr int QX = TX / 4;            // 16-byte chunks per row
+  static constexpr int TASKS = ROWS * (QX + 2);   // copies per array and plane
+  static_assert(TX % 4 == 0, "16-byte interior copies");
+};
+
+// Plane ring: NSLOT slots, planes j-1, j, j+1 read while j+2 and j+3 land.
+constexpr int kTileSlots = 5, kHoldSlots = 4;
+
+// Shared memory of the tile kernel (floats): tiles [kTileSlots][7 arrays][NT],
+// then (HSM) old H [kHoldSlots][5 arrays][CZ][TX TZ], then the per-plane
+// table [jchunk][kPlaneLd].
 __host__ __device__ constexpr size_t rhs_tile_floats(int tx, int tz, int cz, bool hsm) {
-  return 4 * 7 * (size_t)(tx + 2) * (tz * cz + 2) + (hsm ? 3 * 5 * (size_t)tx * tz * cz : 0);
+  return (size_t)kTileSlots * 7 * (4 + (size_t)(tz * cz + 2) * (tx + 4)) +
+         (hsm ? (size_t)kHoldSlots * 5 * tx * tz * cz : 0);
 }
 
 // TX x TZ threads own a TX x (TZ CZ) tile of cells; each thread computes CZ
 // cells stacked in z.  HSM: the previous substage's H arrives by cp.async with
 // the planes (else each thread loads it at the top of the iteration).
+//
+// One barrier per plane: after it every thread has finished the previous
+// plane, so the slot of plane j-2 is free for plane j+3, which is issued right
+// behind the barrier and has two plane times to land.
 template <int TX, int TZ, int CZ, bool HSM, int MINB>
 __global__ void __launch_bounds__(TX * TZ, MINB)
     k_rhs_mixed_tile(Fields<float> f, float* __restrict__ rcp, float* __restrict__ rcm, Shadows sh, MixedRefs R,
                      Geo g, MetricsF mt, CoefF cf, int jchunk) {
-  constexpr int TW = TX + 2, NT = TW * (TZ * CZ + 2), NTH = TX * TZ, E = (NT + NTH - 1) / NTH;
+  using TG = TileGeo<TX, TZ, CZ>;
+  constexpr int NT = TG::NT, RS = TG::RS, NTH = TX * TZ, E = (TG::TASKS + NTH - 1) / NTH;
   extern __shared__ __align__(16) float rhs_smem[];
-  float* tiles = rhs_smem;                                    // [4][NA][NT]
-  float* holds = rhs_smem + 4 * NA * NT;                      // [3][NH][CZ][NTH] (HSM)
-  float* pct = rhs_smem + rhs_tile_floats(TX, TZ, CZ, HSM);   // [jchunk][kPlaneLd]
+  float* tiles = rhs_smem;                                          // [kTileSlots][NA][NT]
+  float* holds = rhs_smem + (size_t)kTileSlots * NA * NT;            // [kHoldSlots][NH][CZ][NTH] (HSM)
+  float* pct = rhs_smem + rhs_tile_floats(TX, TZ, CZ, HSM);         // [jchunk][kPlaneLd]
   const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * TX + tx;
   const int nx = g.nx, nz = g.nz, nyc = g.nyc;
   const int i0 = blockIdx.x * TX, k0 = blockIdx.y * (TZ * CZ);
@@ -438,32 +468,51 @@ __global__ void __launch_bounds__(TX * TZ, MINB)
   // in-plane offset of this thread's first cell; the others are nx apart
   const size_t ck = (size_t)(k0 + tz * CZ) * nx + i0 + tx;
 
-  int off[E];   // in-plane offsets of this thread's tile elements (periodic in x and z)
+  // this thread's copies of every array's tile: task t < ROWS QX is the 16-byte
+  // chunk t % QX of row t / QX; the next 2 ROWS tasks are the x-halo floats
+  // (periodic in x and z); kind 16 / 4 bytes, 0 = none
+  int goff[E], soff[E], kind[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int el = tid + e * NTH;
-    const int kz = el / TW - 1, ix = el % TW - 1;
-    off[e] = ((k0 + kz) & (nz - 1)) * nx + ((i0 + ix) & (nx - 1));
+    const int t = tid + e * NTH;
+    kind[e] = 0;
+    goff[e] = 0;
+    soff[e] = 0;
+    if (t < TG::ROWS * TG::QX) {
+      const int r = t / TG::QX, qx = t % TG::QX;
+      goff[e] = ((k0 - 1 + r) & (nz - 1)) * nx + i0 + 4 * qx;
+      soff[e] = TG::PAD + r * RS + 4 * qx;
+      kind[e] = 16;
+    } else if (t < TG::TASKS) {
+      const int h = t - TG::ROWS * TG::QX, r = h >> 1, side = h & 1;
+      goff[e] = ((k0 - 1 + r) & (nz - 1)) * nx + ((side ? i0 + TX : i0 - 1) & (nx - 1));
+      soff[e] = TG::PAD + r * RS + (side ? TX : -1);
+      kind[e] = 4;
+    }
   }
   const float* src[NA] = {f.u, f.w, f.v, f.p, sh.phi, sh.cp, sh.cm};
   const float* hsrc[NH] = {f.Hu, f.Hw, f.Hv, sh.Hcp, sh.Hcm};
   const bool read_h = cf.zet != 0.f, keep_h = cf.keep_h != 0;   // uniform per launch
-  // plane q (tiles into slot q & 3, old H into slot q mod 3); one commit group
-  // per plane, empty when q is outside the chunk's window or the array
+  // ring position of plane q (q >= jb - 1)
+  auto slot_of = [&](int q) { return (q - jb + 1) % kTileSlots; };
+  // plane q (tiles into its slot, old H into slot (q - jb + 1) & 3); one commit
+  // group per plane, empty when q is outside the chunk's window or the array
   auto issue_plane = [&](int q) {
     if (q >= jb - 1 && q <= je) {
-      float* ts = tiles + (size_t)(q & 3) * NA * NT;
+      float* ts = tiles + (size_t)slot_of(q) * NA * NT;
       const size_t qP = (size_t)q * P;
 #pragma unroll
       for (int a = 0; a < NA; ++a) {
         if (q < 0 || q >= (a == AV ? nyc + 1 : nyc)) continue;
 #pragma unroll
-        for (int e = 0; e < E; ++e)
-          if (tid + e * NTH < NT) cp_async4(ts + a * NT + tid + e * NTH, src[a] + qP + off[e]);
+        for (int e = 0; e < E; ++e) {
+          if (kind[e] == 16) cp_async16(ts + a * NT + soff[e], src[a] + qP + goff[e]);
+          else if (kind[e] == 4) cp_async4(ts + a * NT + soff[e], src[a] + qP + goff[e]);
+        }
       }
       if constexpr (HSM) {
         if (read_h && q >= jb && q < je) {
-          float* hs = holds + (size_t)(q % 3) * NH * CZ * NTH;
+          float* hs = holds + (size_t)((q - jb + 1) & (kHoldSlots - 1)) * NH * CZ * NTH;
 #pragma unroll
           for (int h = 0; h < NH; ++h)
 #pragma unroll
@@ -477,6 +526,7 @@ __global__ void __launch_bounds__(TX * TZ, MINB)
   issue_plane(jb - 1);
   issue_plane(jb);
   issue_plane(jb + 1);
+  issue_plane(jb + 2);
   fill_plane_table(pct, mt, R, cf.D, jb, je, jchunk, tid, NTH);
 
   // CZ = 1: one cell in FP32 scalars; CZ = 2: the cell pair in packed FP32
@@ -490,7 +540,7 @@ __global__ void __launch_bounds__(TX * TZ, MINB)
     if constexpr (CZ == 2) return CellK<T>{V2(ub[0], ub[1]), V2(ut[0], ut[1]), V2(wb[0], wb[1]), V2(wt[0], wt[1])};
     else return CellK<T>{ub[0], ut[0], wb[0], wt[0]};
   };
-  const int c = (tz * CZ + 1) * TW + tx + 1;   // first cell in a tile
+  const int c = TG::PAD + (tz * CZ + 1) * RS + tx;   // first cell in a tile
   YCarry<T> cy{0.f, 0.f, 0.f, 0.f, 0.f};
   for (int j = jb; j < je; ++j) {
     const size_t c0 = (size_t)j * P + ck;
@@ -509,12 +559,12 @@ __global__ void __launch_bounds__(TX * TZ, MINB)
         }
       }
     }
-    issue_plane(j + 2);
     cp_async_wait_all_but_one();   // planes up to j + 1 have landed (this thread's copies)
-    __syncthreads();               // ... and every thread's (and the plane table)
+    __syncthreads();               // ... every thread's; and every thread is done with plane j - 2
+    issue_plane(j + 3);            // into the slot of plane j - 2
     if constexpr (HSM) {
       if (read_h) {
-        const float* hs = holds + (size_t)(j % 3) * NH * CZ * NTH + tid;
+        const float* hs = holds + (size_t)((j - jb + 1) & (kHoldSlots - 1)) * NH * CZ * NTH + tid;
 #pragma unroll
         for (int h = 0; h < NH; ++h)
 #pragma unroll
@@ -527,16 +577,16 @@ __global__ void __launch_bounds__(TX * TZ, MINB)
       if constexpr (CZ == 2) Ho[h] = V2(Hf[0][h], Hf[1][h]);
       else Ho[h] = Hf[0][h];
     }
-    const float* bm = tiles + (size_t)((j + 3) & 3) * NA * NT + c;
-    const float* bo = tiles + (size_t)(j & 3) * NA * NT + c;
-    const float* bp = tiles + (size_t)((j + 1) & 3) * NA * NT + c;
+    const float* bm = tiles + (size_t)slot_of(j - 1) * NA * NT + c;
+    const float* bo = tiles + (size_t)slot_of(j) * NA * NT + c;
+    const float* bp = tiles + (size_t)slot_of(j + 1) * NA * NT + c;
     const PlaneC q = plane_consts(pct + (size_t)(j - jb) * kPlaneLd);
     const CellK<T> kc = (j == 0 || j == nyc - 1) ? walls() : CellK<T>{0.f, 0.f, 0.f, 0.f};
-    const CellOut<T> o = rhs_cell_at<T, NT, TW>(j, jb, nyc, bm, bo, bp, Ho, q, kc, cf, cy);
+    const CellOut<T> o = rhs_cell_at<T, NT, RS>(j, jb, nyc, bm, bo, bp, Ho, q, kc, cf, cy);
     if constexpr (CZ == 2) store_cell(f, rcp, rcm, sh, c0, c0 + nx, j > 0, keep_h, o);
     else store_cell(f, rcp, rcm, sh, c0, j > 0, keep_h, o);
-    __syncthreads();
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");   // no copy outlives the block
 }
 
 // ---------------------------------------------------------------------------
