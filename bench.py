@@ -51,7 +51,7 @@ def cells(wl=WL):
 NCU_TRAFFIC = {
     # mean of three consecutive launches (one per RK3 substage), launch code 0 / 32
     ("mixed", "rhs"): {"kernel": "k_rhs_mixed_tile<32, 8, 2, false, 2>", "shape": (0, 32), "cells": 12582912,
-                       "bytes": None},
+                       "bytes": 916035413},
 }
 
 

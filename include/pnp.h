@@ -206,11 +206,13 @@ int pnp_fp64_peak(pnp_ctx* ctx, double* flops_out);
  * y-solves (16 = mixed shared-memory tiles, else 32/64/128 threads) and the
  * z-transform (8..64 threads per column; mixed: 64 = stage-by-stage kernel,
  * else register FFT) on this context's grid with CUDA events and keeps the
- * fastest.  cfg_out[4]
- * receives the choice (same order as pnp_set_launch_config), ms_out[4]
- * (optional) the best time of each.  It runs on the workspace and overwrites
- * the state: call it after pnp_set_params and before pnp_init_state /
- * pnp_set_state.  Synchronises the stream. */
+ * fastest; then re-checks each choice, one code at a time, on the time of
+ * whole steps of size dt (pnp_step from a Poisson-Boltzmann initial state),
+ * since launch shapes interact inside a step.  cfg_out[4] receives the choice
+ * (same order as pnp_set_launch_config), ms_out[4] (optional) the best time of
+ * each site alone.  It runs on the workspace and overwrites the state: call it
+ * after pnp_set_params and before pnp_init_state / pnp_set_state.
+ * Synchronises the stream. */
 int pnp_autotune(pnp_ctx* ctx, double dt, int* cfg_out, double* ms_out);
 /* Set / read the launch shapes {stencil block x, CN block, spectral block,
  * z-transform threads per column} (e.g. from a cache of autotuner results). */

@@ -1,7 +1,7 @@
 """Launch-shape autotuning with a JSON cache.
 
-pnp_autotune (C++) times candidate launch shapes on a context's grid; the
-result is cached per (device, grid, precision) so later contexts reuse it via
+pnp_autotune (C++) times candidate launch shapes on a context's grid, site by
+site and then on whole steps; the result is cached per (device, grid, precision) so later contexts reuse it via
 pnp_set_launch_config.  Tuning overwrites the workspace, so it runs before the
 state is initialised.
 """
@@ -18,7 +18,7 @@ DEFAULT_CACHE = os.environ.get("PNP_AUTOTUNE_CACHE", os.path.join(BUILD, "autotu
 
 
 # bumped whenever the set of candidate kernels behind a launch-shape code changes
-KERNEL_REV = 2
+KERNEL_REV = 3
 
 
 def _key(solver):

@@ -1359,6 +1359,62 @@ int pnp_autotune(pnp_ctx* c, double dt, int* cfg_out, double* ms_out) {
   c->g.lc_fftz_ty = pick[3];
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaGetLastError());
+  // 5: the whole step.  Timed alone, the sites cannot show how their launch
+  // shapes interact inside a step (the two streams share HBM and SMs), and
+  // candidates a few percent apart alone can order differently there.  So each
+  // choice is re-checked, one code at a time (coordinate descent from the
+  // per-site picks), on the time of whole steps from a Poisson-Boltzmann
+  // initial state, and a candidate replaces the pick only if it is faster by
+  // more than 0.5%.
+  {
+    int r = pnp_init_state(c, PNP_IC_PB, 1, 1e-2);
+    if (r) return r;
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    auto step_ms = [&]() -> float {
+      drop_graph(c);
+      if (pnp_step(c, 2, dt) != PNP_OK) return 1e30f;   // warm-up (and graph capture)
+      constexpr int kSteps = 8;
+      float bestm = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(a, c->stream);
+        if (pnp_step(c, kSteps, dt) != PNP_OK) return 1e30f;
+        cudaEventRecord(b, c->stream);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        bestm = std::min(bestm, ms / kSteps);
+      }
+      return bestm;
+    };
+    auto set = [&](int i, int v) {
+      int* f[4] = {&c->g.lc_rhs_bx, &c->g.lc_cn, &c->g.lc_spec, &c->g.lc_fftz_ty};
+      *f[i] = v;
+    };
+    float cur = step_ms();
+    const std::vector<int> cands[4] = {{32, 64, 128, 16}, {32, 64, 128, 256}, {16, 32, 64, 128}, {8, 16, 32, 64}};
+    for (int i = 0; i < 4; ++i) {
+      for (int v : cands[i]) {
+        if (v == pick[i]) continue;
+        if (i == 0 && c->precision == PNP_FP64 && v > 2 * c->g.nx && v != 32) continue;
+        if (i == 0 && c->precision == PNP_MIXED && v == 128 && !c->rhs_maps_ok) continue;
+        if (i == 3 && v > 8 && v > c->g.nz / 4) continue;
+        set(i, v);
+        const float t = step_ms();
+        if (t < 0.995f * cur) {
+          cur = t;
+          pick[i] = v;
+        }
+        set(i, pick[i]);
+      }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    drop_graph(c);
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaGetLastError());
+  }
   for (int i = 0; i < 4; ++i) {
     cfg_out[i] = pick[i];
     if (ms_out) ms_out[i] = best[i];
