@@ -200,7 +200,7 @@ int pnp_fp64_peak(pnp_ctx* ctx, double* flops_out);
 /* Autotuner (no counterpart in the paper; launch-shape selection for GB300):
  * times candidate launch codes of the stencil (FP64: block x-extent 16/32/64/128
  * of 128 threads; mixed: 16 one-cell tiles, 32 / 64 packed two-cell tiles
- * with old H by direct loads / on the copy ring, 128 TMA rows), the
+ * 32 / 64 cells wide, 128 TMA rows), the
  * wall-normal CN sweeps (32 = mixed
  * shared-memory line tiles, else 64/128/256 threads per block), the spectral
  * y-solves (16 = mixed shared-memory tiles, else 32/64/128 threads) and the

@@ -894,10 +894,13 @@ cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const Mi
       default: return go(k_rhs_mixed_tma<256, 2>, TmaGeo<256, 2>{}, 2);
     }
   }
-  // cp.async tiles.  lc_rhs_bx: 0 / 32 = 32 x 8 threads with a packed pair of
-  // cells each in z, old H by direct loads; 64 = the same with old H on the
-  // cp.async plane ring; 16 = 32 x 8 threads with one cell each; narrower grids
-  // fall back to 8 x 4 / 4 x 4
+  // cp.async tiles.  lc_rhs_bx: 64 = 64 x 4 threads with a packed pair of cells
+  // each in z (a 64 x 8 tile), old H by direct loads; 32 = the same on 32 x 8
+  // threads (a 32 x 16 tile); 0 = the 64-wide tile where nx >= 64, else the
+  // 32-wide one; 16 = 32 x 8 threads with one cell each, old H on the cp.async
+  // ring; narrower grids fall back to 8 x 4 / 4 x 4.  Measured on the
+  // 256x193x256 workload: 0.210 ms (64 wide), 0.224 ms (32 wide), 0.259 ms (one
+  // cell); 64 x 8 threads (one 512-thread block per SM) 0.220 ms, 128 x 2 0.221 ms
   auto go = [&](auto kern, int bx, int bz, int cz, bool hsm, int per_sm) {
     const int nxz = (g.nx / bx) * (g.nz / (bz * cz));
     const int jc = chunk(nxz, per_sm);
@@ -910,9 +913,10 @@ cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const Mi
     kern<<<grd, dim3(bx, bz), smem, s>>>(f, rp, rm, sh, R, g, m, cf, jc);
     return cudaGetLastError();
   };
-  if (g.nx >= 32 && g.nz >= 16 && g.lc_rhs_bx == 64)   // two cells, old H on the cp.async ring
-    return go(k_rhs_mixed_tile<32, 8, 2, true, 2>, 32, 8, 2, true, 2);
-  if (g.nx >= 32 && g.nz >= 16 && g.lc_rhs_bx != 16) return go(k_rhs_mixed_tile<32, 8, 2, false, 2>, 32, 8, 2, false, 2);
+  const int code = g.lc_rhs_bx;
+  if (g.nx >= 64 && g.nz >= 8 && (code == 64 || code == 0 || code == 128))
+    return go(k_rhs_mixed_tile<64, 4, 2, false, 2>, 64, 4, 2, false, 2);
+  if (g.nx >= 32 && g.nz >= 16 && code != 16) return go(k_rhs_mixed_tile<32, 8, 2, false, 2>, 32, 8, 2, false, 2);
   if (g.nx >= 32 && g.nz >= 8) return go(k_rhs_mixed_tile<32, 8, 1, true, 3>, 32, 8, 1, true, 3);
   if (g.nx >= 8) return go(k_rhs_mixed_tile<8, 4, 1, true, 24>, 8, 4, 1, true, 24);
   return go(k_rhs_mixed_tile<4, 4, 1, true, 32>, 4, 4, 1, true, 48);

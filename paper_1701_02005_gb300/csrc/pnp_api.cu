@@ -1441,7 +1441,7 @@ int pnp_set_launch_config(pnp_ctx* c, const int* cfg) {
 
 int pnp_get_launch_config(pnp_ctx* c, int* cfg) {
   if (!c || !cfg) return PNP_ERR_ARG;
-  cfg[0] = c->g.lc_rhs_bx ? c->g.lc_rhs_bx : 32;
+  cfg[0] = c->g.lc_rhs_bx ? c->g.lc_rhs_bx : (c->precision == PNP_MIXED && c->g.nx >= 64 ? 64 : 32);
   cfg[1] = c->g.lc_cn ? c->g.lc_cn : 128;
   cfg[2] = c->g.lc_spec ? c->g.lc_spec : 64;
   cfg[3] = c->g.lc_fftz_ty ? c->g.lc_fftz_ty : 32;

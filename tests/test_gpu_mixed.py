@@ -103,7 +103,8 @@ def test_mixed_laminar_couette_exact():
 
 def test_mixed_stencil_kernels_agree():
     # the TMA row kernel (x2 and x1 rows per block) and the cp.async tile kernels
-    # (32 and 16 wide) run the same per-cell arithmetic: identical to FP32 rounding
+    # (packed pairs 64 and 32 wide, one cell 32 wide) run the same per-cell
+    # arithmetic: identical to FP32 rounding
     import ctypes as C
 
     from paper_1701_02005_gb300 import binding as B
