@@ -77,6 +77,8 @@ EXPORTS = {
     "pnp_fp64_peak": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "pnp_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_int,
                               C.POINTER(C.c_int)]),
+    "pnp_timeline": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                               C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "pnp_autotune": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "pnp_set_launch_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "pnp_get_launch_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
@@ -164,6 +166,7 @@ pnp_clear_status = _fwd("pnp_clear_status")
 pnp_selftest_wait_timeout = _fwd("pnp_selftest_wait_timeout")
 pnp_fp64_peak = _fwd("pnp_fp64_peak")
 pnp_profile = _fwd("pnp_profile")
+pnp_timeline = _fwd("pnp_timeline")
 pnp_autotune = _fwd("pnp_autotune")
 pnp_set_launch_config = _fwd("pnp_set_launch_config")
 pnp_get_launch_config = _fwd("pnp_get_launch_config")

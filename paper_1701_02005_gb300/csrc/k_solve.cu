@@ -1163,14 +1163,31 @@ __global__ void __launch_bounds__(128) k_project_rows(float* __restrict__ u, flo
   const size_t xwrap = (size_t)k * nx + (blockIdx.x == 0 ? nx - 1 : blockIdx.x * 128 - 1);
   float4 sb = make_float4(0.f, 0.f, 0.f, 0.f);   // Phi_p of plane j - 1
   if (jb > 0) sb = *reinterpret_cast<const float4*>(s + (size_t)(jb - 1) * P + row);
-  for (int j = jb; j < je; ++j) {
+  // every operand of plane j; the loads of plane j + 1 are issued before plane
+  // j's arithmetic, so each thread keeps two planes of loads in flight
+  struct Plane {
+    float4 s0, sz, uu, ww, vv, pp;
+    float sxw;
+  };
+  auto load = [&](int j, Plane& q) {
     const size_t o = (size_t)j * P;
-    const float4 s0 = *reinterpret_cast<const float4*>(s + o + row);
-    const float4 sz = *reinterpret_cast<const float4*>(s + o + rowm);
+    q.s0 = *reinterpret_cast<const float4*>(s + o + row);
+    q.sz = *reinterpret_cast<const float4*>(s + o + rowm);
+    q.sxw = lane == 0 ? s[o + xwrap] : 0.f;
+    q.uu = *reinterpret_cast<const float4*>(u + o + row);
+    q.ww = *reinterpret_cast<const float4*>(w + o + row);
+    if (j > 0) q.vv = *reinterpret_cast<const float4*>(v + o + row);
+    if (update_p) q.pp = *reinterpret_cast<const float4*>(p + o + row);
+  };
+  Plane cur, nxt;
+  if (jb < je) load(jb, cur);
+  for (int j = jb; j < je; ++j) {
+    if (j + 1 < je) load(j + 1, nxt);
+    const size_t o = (size_t)j * P;
+    const float4 s0 = cur.s0, sz = cur.sz;
     float sx = __shfl_up_sync(0xffffffffu, s0.w, 1);
-    if (lane == 0) sx = s[o + xwrap];
-    float4 uu = *reinterpret_cast<const float4*>(u + o + row);
-    float4 ww = *reinterpret_cast<const float4*>(w + o + row);
+    if (lane == 0) sx = cur.sxw;
+    float4 uu = cur.uu, ww = cur.ww;
     uu.x -= cx * (s0.x - sx);
     uu.y -= cx * (s0.y - s0.x);
     uu.z -= cx * (s0.z - s0.y);
@@ -1183,7 +1200,7 @@ __global__ void __launch_bounds__(128) k_project_rows(float* __restrict__ u, flo
     *reinterpret_cast<float4*>(w + o + row) = ww;
     if (j > 0) {
       const float hj = ih[j];
-      float4 vv = *reinterpret_cast<const float4*>(v + o + row);
+      float4 vv = cur.vv;
       vv.x -= sc * (s0.x - sb.x) * hj;
       vv.y -= sc * (s0.y - sb.y) * hj;
       vv.z -= sc * (s0.z - sb.z) * hj;
@@ -1191,7 +1208,7 @@ __global__ void __launch_bounds__(128) k_project_rows(float* __restrict__ u, flo
       *reinterpret_cast<float4*>(v + o + row) = vv;
     }
     if (update_p) {
-      float4 pp = *reinterpret_cast<const float4*>(p + o + row);
+      float4 pp = cur.pp;
       pp.x += s0.x;
       pp.y += s0.y;
       pp.z += s0.z;
@@ -1199,6 +1216,7 @@ __global__ void __launch_bounds__(128) k_project_rows(float* __restrict__ u, flo
       *reinterpret_cast<float4*>(p + o + row) = pp;
     }
     sb = s0;
+    cur = nxt;
   }
 }
 

@@ -45,9 +45,11 @@ struct Bump {
 
 // Optional per-launch-site event timing (pnp_profile).
 struct Prof {
-  static constexpr int kMax = 16;
+  static constexpr int kMax = 64;
   cudaEvent_t ev[kMax];
+  int site[kMax], on_aux[kMax];
   int n = 0;
+  bool timeline = false;   // record on each site's own stream, keep the concurrent schedule
 };
 
 struct pnp_ctx {
@@ -220,10 +222,18 @@ int check_grid(int nx, int ny, int nz) {
     if ((__VA_ARGS__) != cudaSuccess) return PNP_ERR_CUDA; \
   } while (0)
 
-// Records the next site-boundary event when profiling (no-op otherwise).
-inline void mark(pnp_ctx* c) {
-  if (c->prof && c->prof->n < Prof::kMax) cudaEventRecord(c->prof->ev[c->prof->n++], c->stream);
+// Records the next site-boundary event when profiling or tracing (no-op
+// otherwise): the end of site `site` (-1: a start) on stream st.
+inline void mark(pnp_ctx* c, cudaStream_t st, int site) {
+  if (c->prof && c->prof->n < Prof::kMax) {
+    const int i = c->prof->n++;
+    c->prof->site[i] = site;
+    c->prof->on_aux[i] = st == c->aux;
+    cudaEventRecord(c->prof->ev[i], st);
+  }
 }
+// site timing or tracing with the concurrent schedule off
+inline bool serial_sites(const pnp_ctx* c) { return c->prof && !c->prof->timeline; }
 
 Metrics metrics(const pnp_ctx* c) {
   return Metrics{c->yc_d, c->idy_d, c->ih_d, c->lo_c_d, c->hi_c_d, c->lo_f_d, c->hi_f_d, c->wl_d, c->wu_d};
@@ -471,7 +481,7 @@ cudaError_t spectral_solve(pnp_ctx* c, cplx<T>* spec, const cplx<T>* twz, bool n
                            cplx<double>* dscr) {
   cudaError_t e = launch_fft_z<T>(spec, twz, c->g, false, st);
   if (e != cudaSuccess) return e;
-  mark(c);
+  mark(c, st, neumann ? PNP_SITE_P_FFTZ : PNP_SITE_E_FFTZ);
   const double scale = 1.0 / ((double)c->g.nx * (double)c->g.nz);
   if constexpr (sizeof(T) == sizeof(float))
     e = launch_spec_thomas_df(spec, dscr, spec_df(c, neumann), neumann ? c->spc_cprN : c->spc_cprD,
@@ -480,9 +490,9 @@ cudaError_t spectral_solve(pnp_ctx* c, cplx<T>* spec, const cplx<T>* twz, bool n
     e = launch_spec_thomas<T>(spec, dscr, neumann ? c->spc_cprN : c->spc_cprD, neumann ? c->spc_invN : c->spc_invD,
                               yrows(c, neumann), c->g, scale, neumann, st);
   if (e != cudaSuccess) return e;
-  mark(c);
+  mark(c, st, neumann ? PNP_SITE_P_THOMAS : PNP_SITE_E_THOMAS);
   e = launch_fft_z<T>(spec, twz, c->g, true, st);
-  mark(c);
+  mark(c, st, neumann ? PNP_SITE_P_IFFTZ : PNP_SITE_E_IFFTZ);
   return e;
 }
 
@@ -505,15 +515,15 @@ cudaError_t pressure_projection(pnp_ctx* c, double scale, bool update_p) {
   cudaError_t e = launch_fft_x_fwd<TV, TV>(PoissonSrc::Divergence, f.u, f.v, f.w, nullptr, nullptr, nullptr,
                                            1.0 / scale, c->g, m, spec, twx, twp, c->stream, nullptr, nullptr, idyT);
   if (e != cudaSuccess) return e;
-  mark(c);
+  mark(c, c->stream, PNP_SITE_P_FFTX);
   e = spectral_solve<TV>(c, spec, twz, true);
   if (e != cudaSuccess) return e;
   e = launch_fft_x_inv<TV, TV>(PoissonDst::Plain, spec, c->g, m, twx, twp, 0.0, phip, c->stream);
   if (e != cudaSuccess) return e;
-  mark(c);
+  mark(c, c->stream, PNP_SITE_P_IFFTX);
   const TV* ihT = (const TV*)(sizeof(TV) == 8 ? (const void*)c->ih_d : (const void*)c->mf[1]);
   e = launch_project<TV>(f.u, f.v, f.w, f.p, phip, scale, update_p, c->g, ihT, c->stream);
-  mark(c);
+  mark(c, c->stream, PNP_SITE_PROJECT);
   return e;
 }
 
@@ -528,11 +538,11 @@ cudaError_t potential_solve(pnp_ctx* c, cudaStream_t st, void* spec_buf, cplx<do
   cudaError_t e = launch_fft_x_fwd<double, TV>(PoissonSrc::Charge, nullptr, nullptr, nullptr, c->cp, c->cm, nullptr,
                                                c->ph.q, c->g, m, spec, twx, twp, st);
   if (e != cudaSuccess) return e;
-  mark(c);
+  mark(c, st, PNP_SITE_E_FFTX);
   e = spectral_solve<double>(c, spec, twz, false, st, dscr);
   if (e != cudaSuccess) return e;
   e = launch_fft_x_inv<double, double>(PoissonDst::Potential, spec, c->g, m, twx, twp, c->ph.V, c->Phi, st);
-  mark(c);
+  mark(c, st, PNP_SITE_E_IFFTX);
   return e;
 }
 
@@ -552,20 +562,20 @@ cudaError_t potential_mixed(pnp_ctx* c, cudaStream_t st, void* spec_buf, cplx<do
   cudaError_t e = launch_fft_x_fwd<float, float>(PoissonSrc::ChargeShadow, nullptr, nullptr, nullptr, nullptr, nullptr,
                                                  nullptr, c->ph.q, c->g, m, spec, twx, twp, st, sh.cp, sh.cm);
   if (e != cudaSuccess) return e;
-  mark(c);
+  mark(c, st, PNP_SITE_E_FFTX);
   e = launch_fft_z<float>(spec, twz, c->g, false, st);
   if (e != cudaSuccess) return e;
-  mark(c);
+  mark(c, st, PNP_SITE_E_FFTZ);
   const double scale = 1.0 / ((double)c->g.nx * (double)c->g.nz);
   e = launch_spec_thomas_df(spec, dscr, spec_df(c, false), c->spc_cprD, c->spc_invD, yrows(c, false), c->g, scale,
                             false, st, c->meanrhs_d, c->meanshift_d, c->delta_d);
   if (e != cudaSuccess) return e;
-  mark(c);
+  mark(c, st, PNP_SITE_E_THOMAS);
   e = launch_fft_z<float>(spec, twz, c->g, true, st);
   if (e != cudaSuccess) return e;
-  mark(c);
+  mark(c, st, PNP_SITE_E_IFFTZ);
   e = launch_fft_x_inv<float, float>(PoissonDst::PotentialShadow, spec, c->g, m, twx, twp, 0.0, sh.phi, st, c->delta_d);
-  mark(c);
+  mark(c, st, PNP_SITE_E_IFFTX);
   return e;
 }
 
@@ -577,7 +587,7 @@ cudaError_t poisson_pair(pnp_ctx* c, double scale) {
   auto pot = [&](cudaStream_t st, void* spec, cplx<double>* dscr) {
     return c->precision == PNP_FP64 ? potential_solve<TV>(c, st, spec, dscr) : potential_mixed(c, st, spec, dscr);
   };
-  if (c->prof) {
+  if (serial_sites(c)) {
     cudaError_t e = pressure_projection<TV>(c, scale, true);
     if (e != cudaSuccess) return e;
     return pot(c->stream, c->spec, c->dscr);
@@ -597,13 +607,13 @@ template <typename TV>
 cudaError_t substage(pnp_ctx* c, double dt, int l) {
   const Stage st{dt, kGam[l], kZet[l], kGam[l] + kZet[l]};
   const Fields<TV> f = fields<TV>(c);
-  mark(c);
+  mark(c, c->stream, -1);
   cudaError_t e = launch_rhs<TV>(f, c->g, metrics(c), c->ph, st, c->stream);
   if (e != cudaSuccess) return e;
-  mark(c);
+  mark(c, c->stream, PNP_SITE_RHS);
   e = launch_cn_solves<TV>(f, c->g, cn_rows(c, l, 0), cn_rows(c, l, 1), cn_rows(c, l, 2), c->stream);
   if (e != cudaSuccess) return e;
-  mark(c);
+  mark(c, c->stream, PNP_SITE_CN);
   return poisson_pair<TV>(c, st.alp * dt);
 }
 
@@ -614,16 +624,16 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
   const Shadows sh = shadows(c);
   const MixedRefs R = mixed_refs(c);
   const Metrics m = metrics(c);
-  mark(c);
+  mark(c, c->stream, -1);
   cudaError_t e =
       launch_mixed_rhs(f, sh, R, c->g, metrics_f(c), coef_f(c, st, l < 2), rhs_maps(c), c->status_d + 1, c->stream);
   if (e != cudaSuccess) return e;
-  mark(c);
+  mark(c, c->stream, PNP_SITE_RHS);
   const CNRowsF cell = cn_rows_f(c, l, 0), face = cn_rows_f(c, l, 1), ion = cn_rows_f(c, l, 2);
-  if (c->prof) {   // site timing: everything in order on the main stream
+  if (serial_sites(c)) {   // site timing: everything in order on the main stream
     e = launch_mixed_cn(f, sh, R, c->g, cell, face, ion, l, kCnIons | kCnVelocity, c->stream);
     if (e != cudaSuccess) return e;
-    mark(c);
+    mark(c, c->stream, PNP_SITE_CN);
     return poisson_pair<float>(c, st.alp * dt);
   }
   // The ion CN solve and the potential depend only on the ions: both fork onto
@@ -632,8 +642,10 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
   e = cudaEventRecord(c->ev_fork, c->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
   if (e == cudaSuccess) e = launch_mixed_cn(f, sh, R, c->g, cell, face, ion, l, kCnIons, c->aux);
+  if (e == cudaSuccess) mark(c, c->aux, PNP_SITE_CN);
   if (e == cudaSuccess) e = potential_mixed(c, c->aux, c->spec2, c->dscr2);
   if (e == cudaSuccess) e = launch_mixed_cn(f, sh, R, c->g, cell, face, ion, l, kCnVelocity, c->stream);
+  if (e == cudaSuccess) mark(c, c->stream, PNP_SITE_CN);
   if (e == cudaSuccess) e = pressure_projection<float>(c, st.alp * dt, true);
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->aux);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
@@ -1247,6 +1259,52 @@ int pnp_profile(pnp_ctx* c, int nsteps, double dt, double* ms_out, int nsites, i
     c->nstep += nsteps;
   }
   if (launches_per_step) *launches_per_step = kernels;
+  return rc;
+}
+
+int pnp_timeline(pnp_ctx* c, double dt, int cap, int* site_out, int* stream_out, double* t_ms_out, int* n_out) {
+  if (!c || !site_out || !stream_out || !t_ms_out || !n_out || cap < 1 || !(dt > 0)) return PNP_ERR_ARG;
+  if (!c->have_params || !c->have_state) return PNP_ERR_STATE;
+  if (c->cn_dt != dt) {
+    int r = upload_cn(c, dt);
+    if (r) return r;
+  }
+  {
+    int r = refresh_refs(c, dt);
+    if (r) return r;
+  }
+  if (c->precision == PNP_MIXED) c->fp64_fresh = false;
+  CK(cudaStreamSynchronize(c->stream));
+  Prof prof;
+  prof.timeline = true;
+  for (int i = 0; i < Prof::kMax; ++i) CK(cudaEventCreate(&prof.ev[i]));
+  c->prof = &prof;
+  int rc = PNP_OK;
+  for (int l = 0; l < 3 && rc == PNP_OK; ++l) {
+    cudaError_t e = c->precision == PNP_FP64 ? substage<double>(c, dt, l) : substage_mixed(c, dt, l);
+    if (e != cudaSuccess) rc = PNP_ERR_CUDA;
+  }
+  c->prof = nullptr;
+  if (rc == PNP_OK && (cudaStreamSynchronize(c->stream) != cudaSuccess || cudaStreamSynchronize(c->aux) != cudaSuccess))
+    rc = PNP_ERR_CUDA;
+  int n = 0;
+  for (int i = 0; i < prof.n && n < cap && rc == PNP_OK; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, prof.ev[0], prof.ev[i]) != cudaSuccess) {
+      rc = PNP_ERR_CUDA;
+      break;
+    }
+    site_out[n] = prof.site[i];
+    stream_out[n] = prof.on_aux[i];
+    t_ms_out[n] = ms;
+    ++n;
+  }
+  *n_out = n;
+  for (int i = 0; i < Prof::kMax; ++i) cudaEventDestroy(prof.ev[i]);
+  if (rc == PNP_OK) {
+    c->time += dt;
+    c->nstep += 1;
+  }
   return rc;
 }
 

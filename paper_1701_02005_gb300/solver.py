@@ -145,6 +145,18 @@ class Solver:
             pass
 
 
+def timeline(solver, dt, cap=64):
+    """One traced step via pnp_timeline: a list of (site, stream, ms) in launch
+    order; site is a PROFILE_SITES name or "start", stream "main" or "aux"."""
+    site = (C.c_int * cap)()
+    stream = (C.c_int * cap)()
+    t = (C.c_double * cap)()
+    n = C.c_int()
+    B.check(B.pnp_timeline(solver.ctx, float(dt), cap, site, stream, t, C.byref(n)), "pnp_timeline")
+    return [(B.PROFILE_SITES[site[i]] if site[i] >= 0 else "start", "aux" if stream[i] else "main", t[i])
+            for i in range(n.value)]
+
+
 def profile(solver, nsteps, dt):
     """Per-launch-site milliseconds (summed) and launches per step via pnp_profile."""
     n = len(B.PROFILE_SITES)
