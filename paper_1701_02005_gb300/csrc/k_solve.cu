@@ -858,6 +858,9 @@ cudaError_t launch_spec_thomas(cplx<T>* spec, cplx<double>* dscr, const double* 
   return cudaGetLastError();
 }
 
+// Rows per batch of the df line sweeps (two batches in flight per thread).
+constexpr int kDfCH = 4;
+
 // Mixed path: the same elimination in double-float arithmetic on the FP32 pipe
 // (pnp_df.cuh).  The low wavenumbers are ill-conditioned on the stretched grid
 // (the near-wall rows dominate |A| |x| by orders of magnitude over A x), so the
@@ -883,19 +886,20 @@ __global__ void k_spec_thomas_df(cplx<float>* __restrict__ spec, float2* __restr
   float2* dp = dscr + part;                             // its df forward value at dp[2 (base + j P)]
   const bool pin = neumann && mm == 0 && n == 0;
   if (mean_rhs != nullptr && mm == 0 && n == 0) return;   // k_spec_mean handles the (0,0) mode
-  dfl d{0.f, 0.f};
-  for (int j0 = 0; j0 < ny; j0 += kCH) {
-    float rr[kCH];
-    float2 iv[kCH];
+  // Both sweeps run in kDfCH-row batches, double-buffered: the loads of batch
+  // b + 1 are in flight while batch b's recurrence runs.
+  auto load_f = [&](int j0, float (&rr)[kDfCH], float2 (&iv)[kDfCH]) {
 #pragma unroll
-    for (int u = 0; u < kCH; ++u)
+    for (int u = 0; u < kDfCH; ++u)
       if (j0 + u < ny) {
         const size_t o = base + (size_t)(j0 + u) * P;
         rr[u] = sp[2 * o];
         iv[u] = invF[o];
       }
+  };
+  auto comp_f = [&](int j0, const float (&rr)[kDfCH], const float2 (&iv)[kDfCH], dfl d) {
 #pragma unroll
-    for (int u = 0; u < kCH; ++u) {
+    for (int u = 0; u < kDfCH; ++u) {
       const int j = j0 + u;
       if (j < ny) {
         const float r = (pin && j == 0) ? 0.f : rr[u];
@@ -904,24 +908,54 @@ __global__ void k_spec_thomas_df(cplx<float>* __restrict__ spec, float2* __restr
         if (j < ny - 1) dp[2 * (base + (size_t)j * P)] = make_float2(d.h, d.l);
       }
     }
+    return d;
+  };
+  dfl d{0.f, 0.f};
+  {
+    float rA[kDfCH], rB[kDfCH];
+    float2 iA[kDfCH], iB[kDfCH];
+    load_f(0, rA, iA);
+    for (int j0 = 0; j0 < ny; j0 += 2 * kDfCH) {
+      if (j0 + kDfCH < ny) load_f(j0 + kDfCH, rB, iB);
+      d = comp_f(j0, rA, iA, d);
+      if (j0 + kDfCH < ny) {
+        if (j0 + 2 * kDfCH < ny) load_f(j0 + 2 * kDfCH, rA, iA);
+        d = comp_f(j0 + kDfCH, rB, iB, d);
+      }
+    }
   }
   dfl x = d;
   sp[2 * (base + (size_t)(ny - 1) * P)] = x.h * sc;
-  for (int j1 = ny - 2; j1 >= 0; j1 -= kCH) {
-    float2 dd[kCH], cc[kCH];
+  // back substitution over rows j1, j1 - 1, ..., j1 - kDfCH + 1 (those >= 0)
+  auto load_b = [&](int j1, float2 (&dd)[kDfCH], float2 (&cc)[kDfCH]) {
 #pragma unroll
-    for (int u = 0; u < kCH; ++u)
+    for (int u = 0; u < kDfCH; ++u)
       if (j1 - u >= 0) {
         const size_t o = base + (size_t)(j1 - u) * P;
         dd[u] = dp[2 * o];
         cc[u] = cprF[o];
       }
+  };
+  auto comp_b = [&](int j1, const float2 (&dd)[kDfCH], const float2 (&cc)[kDfCH], dfl x) {
 #pragma unroll
-    for (int u = 0; u < kCH; ++u) {
+    for (int u = 0; u < kDfCH; ++u) {
       const int j = j1 - u;
       if (j >= 0) {
         x = df_sub_mul(dfl{dd[u].x, dd[u].y}, dfl{cc[u].x, cc[u].y}, x);
         sp[2 * (base + (size_t)j * P)] = x.h * sc;
+      }
+    }
+    return x;
+  };
+  {
+    float2 dA[kDfCH], dB[kDfCH], cA[kDfCH], cB[kDfCH];
+    load_b(ny - 2, dA, cA);
+    for (int j1 = ny - 2; j1 >= 0; j1 -= 2 * kDfCH) {
+      if (j1 - kDfCH >= 0) load_b(j1 - kDfCH, dB, cB);
+      x = comp_b(j1, dA, cA, x);
+      if (j1 - kDfCH >= 0) {
+        if (j1 - 2 * kDfCH >= 0) load_b(j1 - 2 * kDfCH, dA, cA);
+        x = comp_b(j1 - kDfCH, dB, cB, x);
       }
     }
   }
