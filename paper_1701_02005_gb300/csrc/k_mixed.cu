@@ -38,7 +38,7 @@ __global__ void k_cn_ion_mixed(float* __restrict__ rcp, float* __restrict__ Sp, 
                                float* __restrict__ rcm, float* __restrict__ Sm, float* __restrict__ Lm,
                                CNRowsF rows, const float2* __restrict__ dCp, const float2* __restrict__ dCm, int n,
                                size_t P) {
-  constexpr int CH = 8;   // planes loaded ahead per sweep step
+  constexpr int CH = 4;   // planes per batch; two batches in flight
   const size_t line = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (line >= P) return;
   const bool plus = blockIdx.y == 0;
@@ -46,12 +46,14 @@ __global__ void k_cn_ion_mixed(float* __restrict__ rcp, float* __restrict__ Sp, 
   float* S = plus ? Sp : Sm;
   float* L = plus ? Lp : Lm;
   const float2* dC = plus ? dCp : dCm;
-  float d = 0.f;
-  for (int jb = 0; jb < n; jb += CH) {
-    float rr[CH];
+  // forward sweep over batches [jb, jb + CH): the next batch's loads are
+  // issued before this batch's recurrence
+  auto load_f = [&](int jb, float (&rr)[CH]) {
 #pragma unroll
     for (int u = 0; u < CH; ++u)
       if (jb + u < n) rr[u] = r[(size_t)(jb + u) * P + line];
+  };
+  auto comp_f = [&](int jb, const float (&rr)[CH], float d) {
 #pragma unroll
     for (int u = 0; u < CH; ++u) {
       const int j = jb + u;
@@ -60,10 +62,23 @@ __global__ void k_cn_ion_mixed(float* __restrict__ rcp, float* __restrict__ Sp, 
         r[(size_t)j * P + line] = d;
       }
     }
+    return d;
+  };
+  float d = 0.f;
+  {
+    float rA[CH], rB[CH];
+    load_f(0, rA);
+    for (int jb = 0; jb < n; jb += 2 * CH) {
+      if (jb + CH < n) load_f(jb + CH, rB);
+      d = comp_f(jb, rA, d);
+      if (jb + CH < n) {
+        if (jb + 2 * CH < n) load_f(jb + 2 * CH, rA);
+        d = comp_f(jb + CH, rB, d);
+      }
+    }
   }
-  float x = 0.f;
-  for (int jb = n - 1; jb >= 0; jb -= CH) {
-    float dd[CH], sh[CH], sl[CH];
+  // back substitution over batches jb, jb - 1, ..., jb - CH + 1, likewise
+  auto load_b = [&](int jb, float (&dd)[CH], float (&sh)[CH], float (&sl)[CH]) {
 #pragma unroll
     for (int u = 0; u < CH; ++u)
       if (jb - u >= 0) {
@@ -72,6 +87,8 @@ __global__ void k_cn_ion_mixed(float* __restrict__ rcp, float* __restrict__ Sp, 
         sh[u] = S[o];
         sl[u] = L[o];
       }
+  };
+  auto comp_b = [&](int jb, const float (&dd)[CH], const float (&sh)[CH], const float (&sl)[CH], float x) {
 #pragma unroll
     for (int u = 0; u < CH; ++u) {
       const int j = jb - u;
@@ -84,6 +101,20 @@ __global__ void k_cn_ion_mixed(float* __restrict__ rcp, float* __restrict__ Sp, 
         L[o] = c.l;
       }
     }
+    return x;
+  };
+  float x = 0.f;
+  {
+    float dA[CH], hA[CH], lA[CH], dB[CH], hB[CH], lB[CH];
+    load_b(n - 1, dA, hA, lA);
+    for (int jb = n - 1; jb >= 0; jb -= 2 * CH) {
+      if (jb - CH >= 0) load_b(jb - CH, dB, hB, lB);
+      x = comp_b(jb, dA, hA, lA, x);
+      if (jb - CH >= 0) {
+        if (jb - 2 * CH >= 0) load_b(jb - 2 * CH, dA, hA, lA);
+        x = comp_b(jb - CH, dB, hB, lB, x);
+      }
+    }
   }
 }
 
@@ -91,7 +122,7 @@ __global__ void k_cn_ion_mixed(float* __restrict__ rcp, float* __restrict__ Sp, 
 __global__ void k_cn_vel_f32(float* __restrict__ u, float* __restrict__ ru, float* __restrict__ v,
                              float* __restrict__ rv, float* __restrict__ w, float* __restrict__ rw,
                              CNRowsF cell, CNRowsF face, int nyc, size_t P) {
-  constexpr int CH = 8;
+  constexpr int CH = 4;   // planes per batch; two batches in flight
   const size_t line = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (line >= P) return;
   float* q;
@@ -103,12 +134,14 @@ __global__ void k_cn_vel_f32(float* __restrict__ u, float* __restrict__ ru, floa
   else { q = w; r = rw; rw_ = cell; n = nyc; j0 = 0; }
   float* rl = r + (size_t)j0 * P + line;
   float* ql = q + (size_t)j0 * P + line;
-  float d = 0.f;
-  for (int jb = 0; jb < n; jb += CH) {
-    float rr[CH];
+  // both sweeps in CH-plane batches, the next batch's loads issued before this
+  // batch's recurrence
+  auto load_f = [&](int jb, float (&rr)[CH]) {
 #pragma unroll
     for (int k = 0; k < CH; ++k)
       if (jb + k < n) rr[k] = rl[(size_t)(jb + k) * P];
+  };
+  auto comp_f = [&](int jb, const float (&rr)[CH], float d) {
 #pragma unroll
     for (int k = 0; k < CH; ++k) {
       const int j = jb + k;
@@ -117,22 +150,50 @@ __global__ void k_cn_vel_f32(float* __restrict__ u, float* __restrict__ ru, floa
         rl[(size_t)j * P] = d;
       }
     }
+    return d;
+  };
+  float d = 0.f;
+  {
+    float rA[CH], rB[CH];
+    load_f(0, rA);
+    for (int jb = 0; jb < n; jb += 2 * CH) {
+      if (jb + CH < n) load_f(jb + CH, rB);
+      d = comp_f(jb, rA, d);
+      if (jb + CH < n) {
+        if (jb + 2 * CH < n) load_f(jb + 2 * CH, rA);
+        d = comp_f(jb + CH, rB, d);
+      }
+    }
   }
-  float x = 0.f;
-  for (int jb = n - 1; jb >= 0; jb -= CH) {
-    float dd[CH], qq[CH];
+  auto load_b = [&](int jb, float (&dd)[CH], float (&qq)[CH]) {
 #pragma unroll
     for (int k = 0; k < CH; ++k)
       if (jb - k >= 0) {
         dd[k] = rl[(size_t)(jb - k) * P];
         qq[k] = ql[(size_t)(jb - k) * P];
       }
+  };
+  auto comp_b = [&](int jb, const float (&dd)[CH], const float (&qq)[CH], float x) {
 #pragma unroll
     for (int k = 0; k < CH; ++k) {
       const int j = jb - k;
       if (j >= 0) {
         x = dd[k] - rw_.c[j] * x;
         ql[(size_t)j * P] = qq[k] + x;
+      }
+    }
+    return x;
+  };
+  float x = 0.f;
+  {
+    float dA[CH], qA[CH], dB[CH], qB[CH];
+    load_b(n - 1, dA, qA);
+    for (int jb = n - 1; jb >= 0; jb -= 2 * CH) {
+      if (jb - CH >= 0) load_b(jb - CH, dB, qB);
+      x = comp_b(jb, dA, qA, x);
+      if (jb - CH >= 0) {
+        if (jb - 2 * CH >= 0) load_b(jb - 2 * CH, dA, qA);
+        x = comp_b(jb - CH, dB, qB, x);
       }
     }
   }
