@@ -359,7 +359,11 @@ def run_ours(args):
     ms, lps = profile(s, nprof, dt)
     per_launch = {k: v / (3 * nprof) for k, v in ms.items()}
     total = sum(per_launch.values())
-    dom = max(per_launch, key=per_launch.get)
+    # the dominant kernel: a site's time per kernel launch (the mixed CN site is
+    # two kernels, ions and velocities; the potential y-solve site the FP64 mean
+    # mode and the df lines)
+    kernels_per_site = {"cn_thomas": 2, "e_thomas": 2} if prec == B.PNP_MIXED else {}
+    dom = max(per_launch, key=lambda k: per_launch[k] / kernels_per_site.get(k, 1))
     pname = "fp64" if prec == B.PNP_FP64 else "mixed"
     fp64_peak = max(s.fp64_peak(), s.fp64_peak())   # measured now, at working clocks
     peaks = {}
