@@ -141,7 +141,12 @@ int pnp_field_size(pnp_ctx* ctx, int field, size_t* out_count);
  * step is captured once per dt into a CUDA graph and replayed. */
 int pnp_step(pnp_ctx* ctx, int nsteps, double dt);
 
-/* Deterministic FP64 reductions of the current state; synchronises the stream. */
+/* Deterministic reductions of the current state (fixed order; FP64 block
+ * sums); synchronises the stream.  PNP_MIXED after a step reads the FP32
+ * fields and the double-float ion state directly: per-thread sums in
+ * double-float (squares exact, weights dy, h and the divergence coefficients
+ * as double-float pairs), no FP64 copy of the state; the ion numbers and
+ * energies agree with their FP64 evaluation to ~1e-13 relative. */
 int pnp_diagnostics(pnp_ctx* ctx, pnp_diag* out);
 
 /* Plane average <q>(y) of a field into host memory (Ny-1 values, Ny for v). */

@@ -6,6 +6,8 @@
 // divergence (Eq. (2)).  All sums are FP64 with a fixed reduction order
 // (deterministic across runs for a given grid).
 #include "pnp_common.cuh"
+#include "pnp_df.cuh"
+#include "pnp_mixed.cuh"
 
 namespace pnp {
 
@@ -150,6 +152,71 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Fields<TV> f, Geo
     for (int q = 0; q < kDiagSlots; ++q) partial[(size_t)blockIdx.x * kDiagSlots + q] = sh[q * kDiagThreads];
 }
 
+// Mixed precision: the same partial sums straight from the FP32 fields and the
+// df ion state c = c_ref + S + L, with no FP64 copy of the state and no FP64
+// arithmetic per cell.  Each thread sums in df on the FP32 pipe (squares by
+// TwoProduct, weights dy_j and h_j as df pairs), converts its sums to FP64 once
+// and the block reduces them in FP64 in a fixed order; the reference part of
+// the ion numbers, sum_j c_ref(j) dy_j over the plane, is added on the host.
+// The divergence is summed in df from exact differences (TwoSum) times df
+// coefficients, so that its small value keeps its FP64 accuracy; the minimum
+// concentration is FP32; a value is counted non-finite when any input read for
+// it is.
+__global__ void __launch_bounds__(kDiagThreads) k_diag_partial_mixed(Fields<float> f, Shadows sh,
+                                                                     const float* __restrict__ cref_p,
+                                                                     const float* __restrict__ cref_m,
+                                                                     const float* __restrict__ idyF,
+                                                                     const float2* __restrict__ wgt, Geo g,
+                                                                     double* partial) {
+  __shared__ double shr[kDiagSlots * kDiagThreads];
+  dfl sum[6] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};   // slots 0-3, 5
+  float maxdiv = 0.f, bad = 0.f, cmin = 3.0e38f;
+  const size_t P = (size_t)g.nz * g.nx;
+  const size_t nc = (size_t)g.nyc * P, nv = (size_t)g.ny * P;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  // 1/dx, 1/dz as df pairs (per thread, once)
+  const float idxh = (float)g.idx, idzh = (float)g.idz;
+  const dfl idx{idxh, (float)(g.idx - (double)idxh)}, idz{idzh, (float)(g.idz - (double)idzh)};
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += stride) {
+    const int j = (int)(c / P);
+    const int rem = (int)(c - (size_t)j * P);
+    const int k = rem / g.nx, i = rem - k * g.nx;
+    const int ip = (i + 1 == g.nx) ? 0 : i + 1, kp = (k + 1 == g.nz) ? 0 : k + 1;
+    const float u = f.u[c], w = f.w[c], p = f.p[c], ph = sh.phi[c];
+    const float Sp = sh.cp[c], Lp = sh.cpL[c], Sm = sh.cm[c], Lm = sh.cmL[c];
+    const float2 dyw = wgt[j];
+    const dfl dy{dyw.x, dyw.y};
+    if (j == 0) sum[0] = df_add(sum[0], dfl{u, 0.f});
+    if (j == g.nyc - 1) sum[1] = df_add(sum[1], dfl{u, 0.f});
+    sum[2] = df_add(sum[2], df_mul(dfl{Sp, Lp}, dy));
+    sum[3] = df_add(sum[3], df_mul(dfl{Sm, Lm}, dy));
+    const float2 iyw = wgt[2 * g.ny + j];
+    const dfl dv = df_add(df_add(df_mul(df_two_sum(f.u[cidx(j, k, ip, g.nz, g.nx)], -u), idx),
+                                 df_mul(df_two_sum(f.v[c + P], -f.v[c]), dfl{iyw.x, iyw.y})),
+                          df_mul(df_two_sum(f.w[cidx(j, kp, i, g.nz, g.nx)], -w), idz));
+    const float div = __fadd_rn(dv.h, dv.l);
+    maxdiv = fmaxf(maxdiv, fabsf(div));
+    sum[4] = df_add(sum[4], df_mul(df_add(df_prod(u, u), df_prod(w, w)), dy));
+    if (!isfinite(u) || !isfinite(w) || !isfinite(Sp) || !isfinite(Sm) || !isfinite(p) || !isfinite(ph) ||
+        !isfinite(div))
+      bad += 1.f;
+    cmin = fminf(cmin, fminf(cref_p[j] + Sp, cref_m[j] + Sm));
+  }
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < nv; c += stride) {
+    const int j = (int)(c / P);
+    const float v = f.v[c];
+    const float2 hw = wgt[g.ny + j];
+    sum[4] = df_add(sum[4], df_mul(df_prod(v, v), dfl{hw.x, hw.y}));
+    if (!isfinite(v)) bad += 1.f;
+  }
+  auto d = [](dfl x) { return (double)x.h + (double)x.l; };
+  double acc[kDiagSlots] = {d(sum[0]), d(sum[1]), d(sum[2]), d(sum[3]), (double)maxdiv, d(sum[4]), (double)bad,
+                            (double)cmin};
+  block_reduce(shr, acc, threadIdx.x);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < kDiagSlots; ++q) partial[(size_t)blockIdx.x * kDiagSlots + q] = shr[q * kDiagThreads];
+}
+
 __global__ void __launch_bounds__(kDiagThreads) k_diag_final(const double* partial, int npartial, double* out,
                                                             int* status) {
   __shared__ double sh[kDiagSlots * kDiagThreads];
@@ -175,6 +242,16 @@ cudaError_t launch_diagnostics(const Fields<TV>& f, const Geo& g, const Metrics&
                                double* partial, int npartial, double* out, int* status, cudaStream_t s) {
   (void)ph;
   k_diag_partial<TV><<<npartial, kDiagThreads, 0, s>>>(f, g, m, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_diag_final<<<1, kDiagThreads, 0, s>>>(partial, npartial, out, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics_mixed(const Fields<float>& f, const Shadows& sh, const float* cref_p,
+                                     const float* cref_m, const float* idyF, const float2* wgt, const Geo& g,
+                                     double* partial, int npartial, double* out, int* status, cudaStream_t s) {
+  k_diag_partial_mixed<<<npartial, kDiagThreads, 0, s>>>(f, sh, cref_p, cref_m, idyF, wgt, g, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_diag_final<<<1, kDiagThreads, 0, s>>>(partial, npartial, out, status);

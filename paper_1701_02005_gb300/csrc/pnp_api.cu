@@ -25,7 +25,7 @@ const double kGam[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
 const double kZet[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
 
 constexpr size_t kAlign = 256;
-constexpr int kDiagBlocks = 304;   // 2 x 152 SMs
+constexpr int kDiagBlocks = 760;   // 5 x 152 SMs of 256-thread blocks: one resident wave
 constexpr int kProbeBlocks = 152 * 8;
 
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
@@ -80,6 +80,8 @@ struct pnp_ctx {
   // mixed-precision path: FP32 shadows, FP32 metrics / velocity CN rows, reference profiles
   float *cpS, *cmS, *phiS, *HcpS, *HcmS;
   float* mf[8];      // idy, ih, lo_c, hi_c, lo_f, hi_f, wl, wu
+  float2* diag_w = nullptr;            // dy_j, h_j, 1/dy_j ([ny] each) as df pairs (mixed diagnostics)
+  double refN_p = 0.0, refN_m = 0.0;   // sum over cells of c_ref(j) dy_j (reference part of N+-)
   float* cnF_d;      // [3 substages][3 kinds][a, c, m][ny]
   float *crefp_f, *crefm_f, *crfp_f, *crfm_f, *rhoref_f, *rhorf_f, *dPref_f, *Fvref_f;
   double *Rrefp_d, *Rrefm_d, *cref64p_d, *cref64m_d, *Phiref64_d, *meanrhs_d, *meanshift_d, *delta_d;
@@ -155,6 +157,7 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
   float *HcpS = b.take<float>(nc), *HcmS = b.take<float>(nc);
   float* mf[8];
   for (int q = 0; q < 8; ++q) mf[q] = b.take<float>(ny);
+  float2* dgw = b.take<float2>(3 * (size_t)ny);
   float* cnF = b.take<float>(27 * (size_t)ny);
   float *crefp = b.take<float>(ny), *crefm = b.take<float>(ny), *crfp = b.take<float>(ny), *crfm = b.take<float>(ny);
   float *rhoref = b.take<float>(ny), *rhorf = b.take<float>(ny), *dPref = b.take<float>(ny), *Fvref = b.take<float>(ny);
@@ -190,6 +193,7 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
     c->spc_cprN = fcN; c->spc_invN = fiN; c->spc_cprD = fcD; c->spc_invD = fiD;
     c->cpS = cpS; c->cmS = cmS; c->phiS = phiS; c->HcpS = HcpS; c->HcmS = HcmS;
     for (int q = 0; q < 8; ++q) c->mf[q] = mf[q];
+    c->diag_w = dgw;
     c->cnF_d = cnF;
     c->crefp_f = crefp; c->crefm_f = crefm; c->crfp_f = crfp; c->crfm_f = crfm;
     c->rhoref_f = rhoref; c->rhorf_f = rhorf; c->dPref_f = dPref; c->Fvref_f = Fvref;
@@ -332,6 +336,12 @@ int upload_metrics(pnp_ctx* c) {
     for (int q = 0; q < 8; ++q)
       for (int j = 0; j < ny; ++j) tmp[(size_t)q * ny + j] = (float)(*src[q])[j];
     for (int q = 0; q < 8; ++q) CK(up(c->mf[q], tmp.data() + (size_t)q * ny, sizeof(float) * ny));
+    std::vector<float2> w(3 * (size_t)ny, make_float2(0.f, 0.f));
+    auto split = [](double x) { return make_float2((float)x, (float)(x - (double)(float)x)); };
+    for (int j = 0; j < nyc; ++j) w[j] = split(c->dy[j]);
+    for (int j = 0; j < ny; ++j) w[ny + j] = split(c->h[j]);
+    for (int j = 0; j < nyc; ++j) w[2 * (size_t)ny + j] = split(1.0 / c->dy[j]);
+    CK(up(c->diag_w, w.data(), sizeof(float2) * 3 * ny));
     CK(cudaStreamSynchronize(s));
   }
   {
@@ -690,6 +700,11 @@ int refresh_refs(pnp_ctx* c, double dt) {
     CK(cudaMemcpyAsync(cm.data(), c->cref64m_d, sizeof(double) * nyc, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(Ph.data(), c->Phiref64_d, sizeof(double) * nyc, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    c->refN_p = c->refN_m = 0.0;
+    for (int j = 0; j < nyc; ++j) {
+      c->refN_p += (double)P * cp[j] * c->dy[j];
+      c->refN_m += (double)P * cm[j] * c->dy[j];
+    }
     const double D = c->ph.D, K = c->ph.K, q = c->ph.q, V = c->ph.V;
     std::vector<float> crefp(ny, 0.f), crefm(ny, 0.f), crfp(ny, 0.f), crfm(ny, 0.f), rhoref(ny, 0.f), rhorf(ny, 0.f),
         dPref(ny, 0.f), Fvref(ny, 0.f);
@@ -1043,21 +1058,33 @@ int pnp_step(pnp_ctx* c, int nsteps, double dt) {
 int pnp_diagnostics(pnp_ctx* c, pnp_diag* out) {
   if (!c || !out) return PNP_ERR_ARG;
   if (!c->have_params || !c->have_state) return PNP_ERR_STATE;
-  {
+  // mixed precision with valid shadows: straight from the FP32 fields and the
+  // df ion state; otherwise from the FP64 arrays (current after pnp_init_state /
+  // pnp_set_state, or brought up to date here)
+  const bool from_shadows = c->precision == PNP_MIXED && c->refs_valid;
+  if (!from_shadows) {
     int r = materialize(c);
     if (r) return r;
   }
-  cudaError_t e = c->precision == PNP_FP64
-                      ? launch_diagnostics<double>(fields<double>(c), c->g, metrics(c), c->ph, c->diag_partial,
-                                                   kDiagBlocks, c->diag_out, c->status_d, c->stream)
-                      : launch_diagnostics<float>(fields<float>(c), c->g, metrics(c), c->ph, c->diag_partial,
-                                                  kDiagBlocks, c->diag_out, c->status_d, c->stream);
+  cudaError_t e =
+      from_shadows ? launch_diagnostics_mixed(fields<float>(c), shadows(c), c->crefp_f, c->crefm_f, c->mf[0],
+                                              c->diag_w, c->g, c->diag_partial, kDiagBlocks, c->diag_out,
+                                              c->status_d, c->stream)
+      : c->precision == PNP_FP64
+          ? launch_diagnostics<double>(fields<double>(c), c->g, metrics(c), c->ph, c->diag_partial, kDiagBlocks,
+                                       c->diag_out, c->status_d, c->stream)
+          : launch_diagnostics<float>(fields<float>(c), c->g, metrics(c), c->ph, c->diag_partial, kDiagBlocks,
+                                      c->diag_out, c->status_d, c->stream);
   if (e != cudaSuccess) return PNP_ERR_CUDA;
   double h[8];
   int st2[2] = {0, 0};
   CK(cudaMemcpyAsync(h, c->diag_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(st2, c->status_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (from_shadows) {   // the reference part of the ion numbers
+    h[2] += c->refN_p;
+    h[3] += c->refN_m;
+  }
   const int st = st2[1] ? st2[1] : st2[0];
   const double P = (double)c->g.nx * c->g.nz;
   const double ub = h[0] / P, ut = h[1] / P;

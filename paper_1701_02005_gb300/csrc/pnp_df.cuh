@@ -65,6 +65,22 @@ __device__ __forceinline__ dfl df_add2(dfl x, dfl d, float f) {
   return df_two_sum(s2.h, t);
 }
 
+// x + y for df operands, with both the leading and the trailing parts summed
+// by TwoSum (the accurate df sum: valid when x and y have opposite signs and
+// cancel).
+__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
+  dfl s = df_two_sum(x.h, y.h);
+  const dfl t = df_two_sum(x.l, y.l);
+  s = df_fast_two_sum(s.h, __fadd_rn(s.l, t.h));
+  return df_fast_two_sum(s.h, __fadd_rn(s.l, t.l));
+}
+
+// a * b exactly, for float operands (TwoProduct).
+__device__ __forceinline__ dfl df_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
 // Host-side split of a double into a df pair (hi = nearest float).
 inline dfl df_split_host(double x) {
   const float h = (float)x;

@@ -153,3 +153,27 @@ def test_mixed_spectral_solve_variants_agree():
         for n in out[32]:
             assert np.array_equal(out[sp][n], out[32][n]), (sp, n)
     s.close()
+
+
+def test_mixed_diagnostics_from_shadows_match_the_definition():
+    # after steps the mixed diagnostics come straight from the FP32 fields and
+    # the double-float ion state; they must match the definitions evaluated in
+    # FP64 on the materialised state (read back through pnp_get_state)
+    g = o.Grid(64, 41, 32, 2 * math.pi, math.pi, stretch=2.0)
+    prm = o.Params(Re=300.0, lam=0.05, Sc=1.0, V=2.0, beta=0.5)
+    s = _mixed(g, prm)
+    s.set_state(o.initial_state(g, prm, o.IC_PB, seed=21, amp=0.05))
+    s.step(6, 0.01)
+    for _ in range(2):   # twice: the second call sees the same state
+        d = s.diagnostics()
+        st = o.State(*(s.get(n) for n in ("u", "v", "w", "p", "cp", "cm", "Phi", "Hu", "Hv", "Hw", "Hcp", "Hcm")))
+        ref = o.diagnostics(g, prm, st)
+        for k in ("n_plus", "n_minus"):
+            assert abs(d[k] - ref[k]) <= 1e-13 * abs(ref[k]), (k, d[k], ref[k])
+        assert abs(d["net_charge"] - ref["net_charge"]) <= 1e-13 * abs(ref["n_plus"])
+        for k in ("tau_bot", "tau_top", "ke"):
+            assert abs(d[k] - ref[k]) <= 1e-12 * abs(ref[k]), (k, d[k], ref[k])
+        # the divergence summed in double-float against its FP64 evaluation
+        assert abs(d["max_div"] - ref["max_div"]) <= 1e-6 * ref["max_div"] + 1e-15
+        assert d["status"] == 0
+    s.close()
