@@ -5,6 +5,8 @@
 // ion numbers (conserved: zero wall flux, Fig. 1 caption), net charge, max
 // divergence (Eq. (2)).  All sums are FP64 with a fixed reduction order
 // (deterministic across runs for a given grid).
+#include <algorithm>
+
 #include "pnp_common.cuh"
 #include "pnp_df.cuh"
 #include "pnp_mixed.cuh"
@@ -159,10 +161,11 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Fields<TV> f, Geo
 // and the block reduces them in FP64 in a fixed order; the reference part of
 // the ion numbers, sum_j c_ref(j) dy_j over the plane, is added on the host.
 // The divergence is summed in df from exact differences (TwoSum) times df
-// coefficients, so that its small value keeps its FP64 accuracy; the minimum
-// concentration is FP32; a value is counted non-finite when any input read for
-// it is.
-__global__ void __launch_bounds__(kDiagThreads) k_diag_partial_mixed(Fields<float> f, Shadows sh,
+// coefficients, so that its small value keeps its FP64 accuracy -- evaluated
+// only where an FP32 estimate plus its rounding bound could reach the running
+// maximum, which gives the same maximum; the minimum concentration is FP32; a
+// value is counted non-finite when any input read for it is.
+__global__ void __launch_bounds__(kDiagThreads, 4) k_diag_partial_mixed(Fields<float> f, Shadows sh,
                                                                      const float* __restrict__ cref_p,
                                                                      const float* __restrict__ cref_m,
                                                                      const float* __restrict__ idyF,
@@ -177,35 +180,41 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial_mixed(Fields<floa
   // 1/dx, 1/dz as df pairs (per thread, once)
   const float idxh = (float)g.idx, idzh = (float)g.idz;
   const dfl idx{idxh, (float)(g.idx - (double)idxh)}, idz{idzh, (float)(g.idz - (double)idzh)};
+  // cells (and the v faces 0 .. nyc-1 below them); then the top wall face
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += stride) {
     const int j = (int)(c / P);
     const int rem = (int)(c - (size_t)j * P);
     const int k = rem / g.nx, i = rem - k * g.nx;
     const int ip = (i + 1 == g.nx) ? 0 : i + 1, kp = (k + 1 == g.nz) ? 0 : k + 1;
-    const float u = f.u[c], w = f.w[c], p = f.p[c], ph = sh.phi[c];
+    const float u = f.u[c], w = f.w[c], p = f.p[c], ph = sh.phi[c], v0 = f.v[c], v1 = f.v[c + P];
+    const float ue = f.u[cidx(j, k, ip, g.nz, g.nx)], wn = f.w[cidx(j, kp, i, g.nz, g.nx)];
     const float Sp = sh.cp[c], Lp = sh.cpL[c], Sm = sh.cm[c], Lm = sh.cmL[c];
-    const float2 dyw = wgt[j];
+    const float2 dyw = wgt[j], hw = wgt[g.ny + j], iyw = wgt[2 * g.ny + j];
     const dfl dy{dyw.x, dyw.y};
     if (j == 0) sum[0] = df_add(sum[0], dfl{u, 0.f});
     if (j == g.nyc - 1) sum[1] = df_add(sum[1], dfl{u, 0.f});
     sum[2] = df_add(sum[2], df_mul(dfl{Sp, Lp}, dy));
     sum[3] = df_add(sum[3], df_mul(dfl{Sm, Lm}, dy));
-    const float2 iyw = wgt[2 * g.ny + j];
-    const dfl dv = df_add(df_add(df_mul(df_two_sum(f.u[cidx(j, k, ip, g.nz, g.nx)], -u), idx),
-                                 df_mul(df_two_sum(f.v[c + P], -f.v[c]), dfl{iyw.x, iyw.y})),
-                          df_mul(df_two_sum(f.w[cidx(j, kp, i, g.nz, g.nx)], -w), idz));
-    const float div = __fadd_rn(dv.h, dv.l);
-    maxdiv = fmaxf(maxdiv, fabsf(div));
-    sum[4] = df_add(sum[4], df_mul(df_add(df_prod(u, u), df_prod(w, w)), dy));
+    sum[4] = df_add(sum[4], df_add(df_mul(df_add(df_prod(u, u), df_prod(w, w)), dy),
+                                   df_mul(df_prod(v0, v0), dfl{hw.x, hw.y})));
+    // the divergence: an FP32 estimate with a bound on its rounding error; the
+    // exact (df) value only where the estimate could reach the running maximum
+    const float t1 = (ue - u) * idxh, t2 = (v1 - v0) * iyw.x, t3 = (wn - w) * idzh;
+    const float est = t1 + t2 + t3;
+    const float bound = 4e-7f * (fabsf(t1) + fabsf(t2) + fabsf(t3)) + 1e-30f;
+    if (!(fabsf(est) + bound < maxdiv)) {
+      const dfl dv = df_add(df_add(df_mul(df_two_sum(ue, -u), idx), df_mul(df_two_sum(v1, -v0), dfl{iyw.x, iyw.y})),
+                            df_mul(df_two_sum(wn, -w), idz));
+      maxdiv = fmaxf(maxdiv, fabsf(__fadd_rn(dv.h, dv.l)));
+    }
     if (!isfinite(u) || !isfinite(w) || !isfinite(Sp) || !isfinite(Sm) || !isfinite(p) || !isfinite(ph) ||
-        !isfinite(div))
+        !isfinite(v0) || !isfinite(est))
       bad += 1.f;
     cmin = fminf(cmin, fminf(cref_p[j] + Sp, cref_m[j] + Sm));
   }
-  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < nv; c += stride) {
-    const int j = (int)(c / P);
+  for (size_t c = nc + (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < nv; c += stride) {
     const float v = f.v[c];
-    const float2 hw = wgt[g.ny + j];
+    const float2 hw = wgt[g.ny + g.nyc];
     sum[4] = df_add(sum[4], df_mul(df_prod(v, v), dfl{hw.x, hw.y}));
     if (!isfinite(v)) bad += 1.f;
   }
@@ -251,10 +260,16 @@ cudaError_t launch_diagnostics(const Fields<TV>& f, const Geo& g, const Metrics&
 cudaError_t launch_diagnostics_mixed(const Fields<float>& f, const Shadows& sh, const float* cref_p,
                                      const float* cref_m, const float* idyF, const float2* wgt, const Geo& g,
                                      double* partial, int npartial, double* out, int* status, cudaStream_t s) {
-  k_diag_partial_mixed<<<npartial, kDiagThreads, 0, s>>>(f, sh, cref_p, cref_m, idyF, wgt, g, partial);
-  cudaError_t e = cudaGetLastError();
+  // one resident wave: four 256-thread blocks per SM (64 registers a thread)
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  k_diag_final<<<1, kDiagThreads, 0, s>>>(partial, npartial, out, status);
+  const int nb = std::max(1, std::min(npartial, 4 * sms));
+  k_diag_partial_mixed<<<nb, kDiagThreads, 0, s>>>(f, sh, cref_p, cref_m, idyF, wgt, g, partial);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_diag_final<<<1, kDiagThreads, 0, s>>>(partial, nb, out, status);
   return cudaGetLastError();
 }
 
