@@ -156,65 +156,89 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Fields<TV> f, Geo
 
 // Mixed precision: the same partial sums straight from the FP32 fields and the
 // df ion state c = c_ref + S + L, with no FP64 copy of the state and no FP64
-// arithmetic per cell.  Each thread sums in df on the FP32 pipe (squares by
-// TwoProduct, weights dy_j and h_j as df pairs), converts its sums to FP64 once
-// and the block reduces them in FP64 in a fixed order; the reference part of
-// the ion numbers, sum_j c_ref(j) dy_j over the plane, is added on the host.
-// The divergence is summed in df from exact differences (TwoSum) times df
-// coefficients, so that its small value keeps its FP64 accuracy -- evaluated
-// only where an FP32 estimate plus its rounding bound could reach the running
-// maximum, which gives the same maximum; the minimum concentration is FP32; a
-// value is counted non-finite when any input read for it is.
+// arithmetic per cell.  A block takes a contiguous range of x-rows, so a
+// thread's rows share their plane j for long runs: per run it sums u^2 + w^2,
+// v^2 (exact squares) and the ion fluctuations S + L in df on the FP32 pipe and
+// weights the run's sums by dy_j and h_j (df pairs) once.  The per-thread sums
+// go to FP64 once and the block reduces them in FP64 in a fixed order; the
+// reference part of the ion numbers, sum_j c_ref(j) dy_j over the plane, is
+// added on the host.  The divergence is summed in df from exact differences
+// (TwoSum) times df coefficients, so that its small value keeps its FP64
+// accuracy -- evaluated only where an FP32 estimate plus its rounding bound
+// could reach the running maximum, which gives the same maximum; the minimum
+// concentration is FP32; a value is counted non-finite when any input read for
+// it is.  Nx and Nz are powers of two.
 __global__ void __launch_bounds__(kDiagThreads, 4) k_diag_partial_mixed(Fields<float> f, Shadows sh,
-                                                                     const float* __restrict__ cref_p,
-                                                                     const float* __restrict__ cref_m,
-                                                                     const float* __restrict__ idyF,
-                                                                     const float2* __restrict__ wgt, Geo g,
-                                                                     double* partial) {
+                                                                        const float* __restrict__ cref_p,
+                                                                        const float* __restrict__ cref_m,
+                                                                        const float2* __restrict__ wgt, Geo g,
+                                                                        double* partial) {
   __shared__ double shr[kDiagSlots * kDiagThreads];
-  dfl sum[6] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};   // slots 0-3, 5
+  dfl sum[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};   // slots 0-3, 5
   float maxdiv = 0.f, bad = 0.f, cmin = 3.0e38f;
-  const size_t P = (size_t)g.nz * g.nx;
-  const size_t nc = (size_t)g.nyc * P, nv = (size_t)g.ny * P;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const int nx = g.nx, nz = g.nz, lnz = __ffs(nz) - 1;
+  const size_t P = (size_t)nz * nx;
+  const int rows = g.nyc * nz, per = (rows + gridDim.x - 1) / gridDim.x;
+  const int r0 = blockIdx.x * per, r1 = min(rows, r0 + per);
   // 1/dx, 1/dz as df pairs (per thread, once)
   const float idxh = (float)g.idx, idzh = (float)g.idz;
   const dfl idx{idxh, (float)(g.idx - (double)idxh)}, idz{idzh, (float)(g.idz - (double)idzh)};
-  // cells (and the v faces 0 .. nyc-1 below them); then the top wall face
-  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += stride) {
-    const int j = (int)(c / P);
-    const int rem = (int)(c - (size_t)j * P);
-    const int k = rem / g.nx, i = rem - k * g.nx;
-    const int ip = (i + 1 == g.nx) ? 0 : i + 1, kp = (k + 1 == g.nz) ? 0 : k + 1;
-    const float u = f.u[c], w = f.w[c], p = f.p[c], ph = sh.phi[c], v0 = f.v[c], v1 = f.v[c + P];
-    const float ue = f.u[cidx(j, k, ip, g.nz, g.nx)], wn = f.w[cidx(j, kp, i, g.nz, g.nx)];
-    const float Sp = sh.cp[c], Lp = sh.cpL[c], Sm = sh.cm[c], Lm = sh.cmL[c];
-    const float2 dyw = wgt[j], hw = wgt[g.ny + j], iyw = wgt[2 * g.ny + j];
-    const dfl dy{dyw.x, dyw.y};
-    if (j == 0) sum[0] = df_add(sum[0], dfl{u, 0.f});
-    if (j == g.nyc - 1) sum[1] = df_add(sum[1], dfl{u, 0.f});
-    sum[2] = df_add(sum[2], df_mul(dfl{Sp, Lp}, dy));
-    sum[3] = df_add(sum[3], df_mul(dfl{Sm, Lm}, dy));
-    sum[4] = df_add(sum[4], df_add(df_mul(df_add(df_prod(u, u), df_prod(w, w)), dy),
-                                   df_mul(df_prod(v0, v0), dfl{hw.x, hw.y})));
-    // the divergence: an FP32 estimate with a bound on its rounding error; the
-    // exact (df) value only where the estimate could reach the running maximum
-    const float t1 = (ue - u) * idxh, t2 = (v1 - v0) * iyw.x, t3 = (wn - w) * idzh;
-    const float est = t1 + t2 + t3;
-    const float bound = 4e-7f * (fabsf(t1) + fabsf(t2) + fabsf(t3)) + 1e-30f;
-    if (!(fabsf(est) + bound < maxdiv)) {
-      const dfl dv = df_add(df_add(df_mul(df_two_sum(ue, -u), idx), df_mul(df_two_sum(v1, -v0), dfl{iyw.x, iyw.y})),
-                            df_mul(df_two_sum(wn, -w), idz));
-      maxdiv = fmaxf(maxdiv, fabsf(__fadd_rn(dv.h, dv.l)));
+  // the current run of rows in plane jr: sums still to be weighted
+  int jr = r0 >> lnz;
+  dfl ruw{0.f, 0.f}, rv{0.f, 0.f}, rcp{0.f, 0.f}, rcm{0.f, 0.f}, ru{0.f, 0.f};
+  auto flush = [&]() {
+    const float2 dyw = wgt[jr], hw = wgt[g.ny + jr];
+    const dfl dy{dyw.x, dyw.y}, h{hw.x, hw.y};
+    sum[4] = df_add(sum[4], df_add(df_mul(ruw, dy), df_mul(rv, h)));
+    sum[2] = df_add(sum[2], df_mul(rcp, dy));
+    sum[3] = df_add(sum[3], df_mul(rcm, dy));
+    if (jr == 0) sum[0] = df_add(sum[0], ru);
+    if (jr == g.nyc - 1) sum[1] = df_add(sum[1], ru);
+    ruw = rv = rcp = rcm = ru = dfl{0.f, 0.f};
+  };
+  for (int r = r0; r < r1; ++r) {
+    const int j = r >> lnz, k = r & (nz - 1);
+    if (j != jr) {
+      flush();
+      jr = j;
     }
-    if (!isfinite(u) || !isfinite(w) || !isfinite(Sp) || !isfinite(Sm) || !isfinite(p) || !isfinite(ph) ||
-        !isfinite(v0) || !isfinite(est))
-      bad += 1.f;
-    cmin = fminf(cmin, fminf(cref_p[j] + Sp, cref_m[j] + Sm));
+    const int kp = (k + 1) & (nz - 1);
+    const float2 iyw = wgt[2 * g.ny + j];
+    const float crp = cref_p[j], crm = cref_m[j];
+    const size_t rowo = (size_t)r * nx, rowkp = ((size_t)j * nz + kp) * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const size_t c = rowo + i;
+      const int ip = (i + 1) & (nx - 1);
+      const float u = f.u[c], w = f.w[c], p = f.p[c], ph = sh.phi[c], v0 = f.v[c], v1 = f.v[c + P];
+      const float ue = f.u[rowo + ip], wn = f.w[rowkp + i];
+      const float Sp = sh.cp[c], Lp = sh.cpL[c], Sm = sh.cm[c], Lm = sh.cmL[c];
+      ru = df_add_fast(ru, dfl{u, 0.f});
+      ruw = df_add_fast(ruw, df_add_fast(df_prod(u, u), df_prod(w, w)));
+      rv = df_add_fast(rv, df_prod(v0, v0));
+      rcp = df_add_fast(rcp, dfl{Sp, Lp});
+      rcm = df_add_fast(rcm, dfl{Sm, Lm});
+      // the divergence: an FP32 estimate with a bound on its rounding error; the
+      // exact (df) value only where the estimate could reach the running maximum
+      const float t1 = (ue - u) * idxh, t2 = (v1 - v0) * iyw.x, t3 = (wn - w) * idzh;
+      const float est = t1 + t2 + t3;
+      const float bound = 4e-7f * (fabsf(t1) + fabsf(t2) + fabsf(t3)) + 1e-30f;
+      if (!(fabsf(est) + bound < maxdiv)) {
+        const dfl dv = df_add(df_add(df_mul(df_two_sum(ue, -u), idx), df_mul(df_two_sum(v1, -v0), dfl{iyw.x, iyw.y})),
+                              df_mul(df_two_sum(wn, -w), idz));
+        maxdiv = fmaxf(maxdiv, fabsf(__fadd_rn(dv.h, dv.l)));
+      }
+      if (!isfinite(u) || !isfinite(w) || !isfinite(Sp) || !isfinite(Sm) || !isfinite(p) || !isfinite(ph) ||
+          !isfinite(v0) || !isfinite(est))
+        bad += 1.f;
+      cmin = fminf(cmin, fminf(crp + Sp, crm + Sm));
+    }
   }
-  for (size_t c = nc + (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < nv; c += stride) {
+  if (r0 < r1) flush();
+  // the top wall face of v
+  const size_t nc = (size_t)g.nyc * P;
+  const float2 hw = wgt[g.ny + g.nyc];
+  for (size_t c = nc + (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc + P; c += (size_t)gridDim.x * blockDim.x) {
     const float v = f.v[c];
-    const float2 hw = wgt[g.ny + g.nyc];
     sum[4] = df_add(sum[4], df_mul(df_prod(v, v), dfl{hw.x, hw.y}));
     if (!isfinite(v)) bad += 1.f;
   }
@@ -266,7 +290,8 @@ cudaError_t launch_diagnostics_mixed(const Fields<float>& f, const Shadows& sh, 
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   const int nb = std::max(1, std::min(npartial, 4 * sms));
-  k_diag_partial_mixed<<<nb, kDiagThreads, 0, s>>>(f, sh, cref_p, cref_m, idyF, wgt, g, partial);
+  (void)idyF;
+  k_diag_partial_mixed<<<nb, kDiagThreads, 0, s>>>(f, sh, cref_p, cref_m, wgt, g, partial);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_diag_final<<<1, kDiagThreads, 0, s>>>(partial, nb, out, status);

@@ -75,6 +75,14 @@ __device__ __forceinline__ dfl df_add(dfl x, dfl y) {
   return df_fast_two_sum(s.h, __fadd_rn(s.l, t.l));
 }
 
+// x + y for df operands with the trailing parts added in FP32 (Dekker's
+// sum): error about 2^-47 (|x| + |y|), enough for running sums whose terms do
+// not cancel to far below their own size.
+__device__ __forceinline__ dfl df_add_fast(dfl x, dfl y) {
+  const dfl s = df_two_sum(x.h, y.h);
+  return df_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
+}
+
 // a * b exactly, for float operands (TwoProduct).
 __device__ __forceinline__ dfl df_prod(float a, float b) {
   const float p = __fmul_rn(a, b);
