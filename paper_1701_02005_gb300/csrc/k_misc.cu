@@ -282,15 +282,14 @@ cudaError_t launch_diagnostics(const Fields<TV>& f, const Geo& g, const Metrics&
 }
 
 cudaError_t launch_diagnostics_mixed(const Fields<float>& f, const Shadows& sh, const float* cref_p,
-                                     const float* cref_m, const float* idyF, const float2* wgt, const Geo& g,
-                                     double* partial, int npartial, double* out, int* status, cudaStream_t s) {
+                                     const float* cref_m, const float2* wgt, const Geo& g, double* partial,
+                                     int npartial, double* out, int* status, cudaStream_t s) {
   // one resident wave: four 256-thread blocks per SM (64 registers a thread)
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   const int nb = std::max(1, std::min(npartial, 4 * sms));
-  (void)idyF;
   k_diag_partial_mixed<<<nb, kDiagThreads, 0, s>>>(f, sh, cref_p, cref_m, wgt, g, partial);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -1067,9 +1067,9 @@ int pnp_diagnostics(pnp_ctx* c, pnp_diag* out) {
     if (r) return r;
   }
   cudaError_t e =
-      from_shadows ? launch_diagnostics_mixed(fields<float>(c), shadows(c), c->crefp_f, c->crefm_f, c->mf[0],
-                                              c->diag_w, c->g, c->diag_partial, kDiagBlocks, c->diag_out,
-                                              c->status_d, c->stream)
+      from_shadows ? launch_diagnostics_mixed(fields<float>(c), shadows(c), c->crefp_f, c->crefm_f, c->diag_w,
+                                              c->g, c->diag_partial, kDiagBlocks, c->diag_out, c->status_d,
+                                              c->stream)
       : c->precision == PNP_FP64
           ? launch_diagnostics<double>(fields<double>(c), c->g, metrics(c), c->ph, c->diag_partial, kDiagBlocks,
                                        c->diag_out, c->status_d, c->stream)

@@ -68,8 +68,8 @@ bool rhs_tma_eligible(const Geo& g);
 // copy); wgt[j] = dy_j and wgt[2 ny + j] = 1/dy_j (j < nyc), wgt[ny + j] = h_j,
 // as df pairs.  The reference part of the ion numbers is not included.
 cudaError_t launch_diagnostics_mixed(const Fields<float>& f, const Shadows& sh, const float* cref_p,
-                                     const float* cref_m, const float* idyF, const float2* wgt, const Geo& g,
-                                     double* partial, int npartial, double* out, int* status, cudaStream_t s);
+                                     const float* cref_m, const float2* wgt, const Geo& g, double* partial,
+                                     int npartial, double* out, int* status, cudaStream_t s);
 cudaError_t launch_wait_selftest(int* err, double limit_s, cudaStream_t s);
 cudaError_t build_rhs_maps(RhsMaps* m, const Fields<float>& f, const Shadows& sh, const Geo& g);
 // maps == nullptr selects the cp.async tile kernel; err receives PNP_ERR_TIMEOUT
