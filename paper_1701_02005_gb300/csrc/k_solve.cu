@@ -961,11 +961,48 @@ __global__ void k_spec_thomas_df(cplx<float>* __restrict__ spec, float2* __restr
   }
 }
 
-// The FP64 (0,0) mode of the mixed potential as one block: the column and its
-// coefficients are staged in shared memory by all threads (one memory latency
-// instead of one per serial step), thread 0 runs both sweeps there, and all
-// threads write the result and zero the transform slots.
-constexpr int kMeanSmemRows = 640;   // 6 doubles per row: 30 KB of static shared memory
+// The FP64 (0,0) mode of the mixed potential as one block.  All threads stage
+// the column in shared memory; both Thomas sweeps are first-order linear
+// recurrences x_j = A_j + B_j x_(j-1) (forward: A = src_j / pivot_j,
+// B = -a_j / pivot_j; back substitution, run from the top: A = d_j, B = -c'_j),
+// so the first warp solves each as a scan of affine maps: every lane composes
+// the maps of its chunk of rows, a Kogge-Stone scan over the 32 lanes composes
+// the chunks, and every lane re-runs its chunk from the value entering it.
+// The dependent FP64 chain shrinks from two steps per row to ~2 n / 32 + 10
+// steps.  |B| < 1 on the diagonally dominant y-operator, so the composed
+// products only shrink.  Then all threads write the result and zero the
+// transform slots.
+constexpr int kMeanSmemRows = 640;   // 5 doubles per row: 25 KB of static shared memory
+
+// x_j = A_j + B_j x_(j-1) for j = 0 .. n-1 with x_(-1) = 0, by the first warp;
+// A(s), B(s) give the maps in sweep order s, x(s, value) stores the result
+template <typename FA, typename FB, typename FX>
+__device__ __forceinline__ void affine_scan_warp(int n, FA A, FB B, FX x) {
+  const int lane = threadIdx.x & 31, per = (n + 31) / 32;
+  const int lo = min(n, lane * per), hi = min(n, lo + per);
+  double bc = 1.0, ac = 0.0;   // this chunk's composed map
+  for (int s = lo; s < hi; ++s) {
+    const double b = B(s);
+    ac = fma(b, ac, A(s));
+    bc *= b;
+  }
+  // inclusive scan over lanes: (b, a) of lanes <= lane composed, earlier first
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const double bp = __shfl_up_sync(0xffffffffu, bc, off), ap = __shfl_up_sync(0xffffffffu, ac, off);
+    if (lane >= off) {
+      ac = fma(bc, ap, ac);
+      bc *= bp;
+    }
+  }
+  double v = __shfl_up_sync(0xffffffffu, ac, 1);   // the value entering this chunk
+  if (lane == 0) v = 0.0;
+  for (int s = lo; s < hi; ++s) {
+    v = fma(B(s), v, A(s));
+    x(s, v);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_spec_mean(cplx<float>* __restrict__ spec, const double* __restrict__ cpr,
                                                    const double* __restrict__ inv, YRows rows, Geo g, double scale,
                                                    const double* __restrict__ mean_rhs,
@@ -980,28 +1017,26 @@ __global__ void __launch_bounds__(256) k_spec_mean(cplx<float>* __restrict__ spe
                      mean_out);
     return;
   }
-  __shared__ double src[kMeanSmemRows], iv[kMeanSmemRows], cp[kMeanSmemRows], a[kMeanSmemRows],
-      ms[kMeanSmemRows], out[kMeanSmemRows];
+  __shared__ double e[kMeanSmemRows], fa[kMeanSmemRows], cp[kMeanSmemRows], ms[kMeanSmemRows],
+      out[kMeanSmemRows];
   for (int j = threadIdx.x; j < ny; j += blockDim.x) {
     const size_t o = (size_t)j * P;
-    src[j] = (double)sp[2 * o] * scale + mean_rhs[j];
-    iv[j] = inv[o];
+    const double iv = inv[o];
+    e[j] = ((double)sp[2 * o] * scale + mean_rhs[j]) * iv;
+    fa[j] = rows.a[j] * iv;
     cp[j] = cpr[o];
-    a[j] = rows.a[j];
     ms[j] = mean_shift[j];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double d = 0.0;
-    for (int j = 0; j < ny; ++j) {
-      d = (src[j] - a[j] * d) * iv[j];
-      out[j] = d;
-    }
-    double x = d;
-    for (int j = ny - 2; j >= 0; --j) {
-      x = out[j] - cp[j] * x;
-      out[j] = x;
-    }
+  if (threadIdx.x < 32) {
+    // forward: d_j = e_j - (a_j / pivot_j) d_(j-1)
+    affine_scan_warp(ny, [&](int s) { return e[s]; }, [&](int s) { return -fa[s]; },
+                     [&](int s, double v) { out[s] = v; });
+    __syncwarp();
+    // back substitution from the top: x_(n-1) = d_(n-1), x_j = d_j - c'_j x_(j+1)
+    affine_scan_warp(ny, [&](int s) { return out[ny - 1 - s]; },
+                     [&](int s) { return s == 0 ? 0.0 : -cp[ny - 1 - s]; },
+                     [&](int s, double v) { out[ny - 1 - s] = v; });
   }
   __syncthreads();
   for (int j = threadIdx.x; j < ny; j += blockDim.x) {
