@@ -57,9 +57,9 @@ NCU_TRAFFIC = {
 
 def site_cost(site, precision, launch_cfg=None):
     half = (WL["nx"] // 2 + 1) / WL["nx"]
-    # mixed CN: the shared-memory line tiles (launch code 0 / 32) keep the forward
+    # mixed CN: the shared-memory line tiles (launch code 32) keep the forward
     # elimination values on chip (76 B per cell); the line kernels write and re-read them (116 B)
-    cn_tiled = launch_cfg is None or launch_cfg[1] in (0, 32)
+    cn_tiled = launch_cfg is not None and launch_cfg[1] == 32
     if precision == "fp64":
         table = {
             "rhs": (176, 220), "cn_thomas": (200, 20),

@@ -386,9 +386,13 @@ cudaError_t launch_mixed_cn(const Fields<float>& f, const Shadows& sh, const Mix
                             const CNRowsF& cell, const CNRowsF& face, const CNRowsF& ion, int l, unsigned parts,
                             cudaStream_t s) {
   const size_t P = (size_t)g.nz * g.nx;
-  // shared-memory line tiles (the default, and lc_cn 32) when 32 lines divide a
-  // plane and a column block fits; lc_cn 64 / 128 / 256: one thread per line
-  const bool tiled = (g.lc_cn == 0 || g.lc_cn == 32) && P % 32 == 0 && cn_tile_smem(g.nyc, 2) <= 227 * 1024;
+  // lc_cn 32: shared-memory line tiles, when 32 lines divide a plane and a column
+  // block fits; otherwise one thread per line, lc_cn threads per block (0: 128).
+  // In the two-stream step the line kernels win (2.62 against 2.72 ms on the
+  // 256x193x256 workload, although the tiles move 76 B per cell against 116 B
+  // and are faster alone): the tiles' shared memory keeps the SMs from the
+  // kernels of the other stream
+  const bool tiled = g.lc_cn == 32 && P % 32 == 0 && cn_tile_smem(g.nyc, 2) <= 227 * 1024;
   if (tiled) {
     const dim3 blk(32);
     if (parts & kCnIons) {

@@ -32,7 +32,7 @@ struct Geo {
   int lc_rhs_bx;         // FP64 stencil: x-extent of the 128-thread blocks (16, 32, 64, 128);
                          // mixed stencil: 128 TMA rows, 64 / 32 packed-pair cp.async tiles 64 / 32
                          // cells wide, 16 one-cell tiles
-  int lc_cn;             // threads per block of the wall-normal CN sweeps (mixed: 0 / 32 = shared-memory line tiles)
+  int lc_cn;             // threads per block of the wall-normal CN sweeps (mixed: 32 = shared-memory line tiles)
   int lc_spec;           // threads per block of the spectral y-solves (mixed: 16 = shared-memory tiles)
   int lc_fftz_ty;        // threads per column of the z-transform (cap)
 };
