@@ -155,6 +155,32 @@ def test_mixed_spectral_solve_variants_agree():
     s.close()
 
 
+def test_mixed_cn_variants_agree():
+    # the wall-normal CN solves as one thread per line (launch codes 64, 128, 256;
+    # the default) and as shared-memory line tiles (32): the same recurrences on
+    # the same operands, so the stepped fields agree to FP32 rounding
+    import ctypes as C
+
+    from paper_1701_02005_gb300 import binding as B
+
+    g = o.Grid(64, 41, 32, 2 * math.pi, math.pi, stretch=2.0)
+    prm = o.Params(Re=300.0, lam=0.05, Sc=1.0, V=2.0, beta=0.5)
+    st = o.initial_state(g, prm, o.IC_PB, seed=27, amp=0.1)
+    s = _mixed(g, prm)
+    out = {}
+    for cn in (32, 64, 128, 256):
+        B.check(B.pnp_set_launch_config(s.ctx, (C.c_int * 4)(64, cn, 32, 32)), "pnp_set_launch_config")
+        s.set_state(st)
+        s.step(3, 0.005)
+        out[cn] = {n: s.get(n) for n in ("u", "v", "w", "cp", "cm", "Phi")}
+    assert s.status() == 0
+    for cn in (64, 128, 256):
+        assert all(np.array_equal(out[cn][n], out[64][n]) for n in out[64]), cn   # same kernel, other block size
+        for n in out[32]:
+            assert _rel(out[cn][n], out[32][n]) <= 1e-6, (cn, n)
+    s.close()
+
+
 def test_mixed_diagnostics_from_shadows_match_the_definition():
     # after steps the mixed diagnostics come straight from the FP32 fields and
     # the double-float ion state; they must match the definitions evaluated in
