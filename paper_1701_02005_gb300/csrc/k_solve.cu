@@ -410,9 +410,11 @@ __global__ void __launch_bounds__(256) k_fft_x_inv_reg(PoissonDst dst, const cpl
   }
 }
 
-// Rows per 256-thread block of the register x-transforms, and shared memory.
+// Rows per 128-thread block of the register x-transforms (smaller blocks share
+// the GPU better with the other stream: 2.583 against 2.593 ms per step with
+// 256 threads on the 256x193x256 workload), and shared memory.
 template <int NH, int R1>
-constexpr int fx_rows() { return 256 / (NH / R1); }
+constexpr int fx_rows() { return 128 / (NH / R1); }
 template <int NH, int R1>
 constexpr size_t fx_smem() {
   return sizeof(cplx<float>) * ((size_t)2 * NH + 1 + (size_t)fx_rows<NH, R1>() * fx_row_stride<NH, R1>());
