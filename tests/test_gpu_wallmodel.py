@@ -119,12 +119,12 @@ def _impulsive(s, g, seed, amp=0.02):
 
 
 def wall_model_case(nfine=(32, 65, 32), ry=4, rxz=2, Re=500.0, dt=0.002, nsteps=200, every=2, train_iters=3000,
-                    rounds=1, seed_train=31, seed_judge=32):
+                    passes=1, seed_train=31, seed_judge=32):
     """Fine DNS data -> trained network -> coarse runs with and without it, judged
     on the friction coefficient against the fine DNS.  Training pairs the coarse
     solver's own near-wall features with the fine run's filtered labels at the
-    same time and initial state: round 0 from the coarse run without the model,
-    later rounds from the coarse run coupled to the previous round's network."""
+    same time and initial state: data pass 0 from the coarse run without the
+    model, later passes from the coarse run coupled to the previous pass's network."""
     import torch
 
     from paper_1701_02005_gb300 import wallmodel as wm
@@ -136,7 +136,7 @@ def wall_model_case(nfine=(32, 65, 32), ry=4, rxz=2, Re=500.0, dt=0.002, nsteps=
     sf, sc, sm = _solver(gf, prm), _solver(gc, prm), _solver(gc, prm)
     Xs, Ts = [], []
     net, norm, losses = None, None, []
-    for rnd in range(rounds):
+    for rnd in range(passes):
         _impulsive(sf, gf, seed_train)
         wm.restrict(sf, sc)
         for n in range(nsteps // every):
@@ -157,7 +157,7 @@ def wall_model_case(nfine=(32, 65, 32), ry=4, rxz=2, Re=500.0, dt=0.002, nsteps=
             xsd = np.maximum(Xh.std(0), 1e-2 * np.maximum(np.abs(xs), 1e-2))
             tsd = np.maximum(Th.std(0), 1e-2 * np.maximum(np.abs(ts), 1e-4))
             norm = (xs, 1.0 / xsd, ts, 1.0 / tsd)
-            net = wm.MLP(nsteps // every * rounds * 2 * gc.nz * gc.nx, seed=33)
+            net = wm.MLP(nsteps // every * passes * 2 * gc.nz * gc.nx, seed=33)
             net.set_normalization(*norm)
         l0 = net.train_step(X, T, 2e-3, want_loss=True)
         for it in range(train_iters):
