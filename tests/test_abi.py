@@ -58,6 +58,20 @@ def test_null_context_is_rejected(lib):
     assert B.pnp_diagnostics(None, C.byref(d)) == B.PNP_ERR_ARG
 
 
+def test_tracing_and_tuning_validate_arguments(lib):
+    from paper_1701_02005_gb300 import binding as B
+
+    site, stream, n = (C.c_int * 8)(), (C.c_int * 8)(), C.c_int()
+    t = (C.c_double * 8)()
+    assert B.pnp_timeline(None, 0.01, 8, site, stream, t, C.byref(n)) == B.PNP_ERR_ARG
+    cfg, ms = (C.c_int * 4)(), (C.c_double * 4)()
+    assert B.pnp_autotune(None, 0.01, cfg, ms) == B.PNP_ERR_ARG
+    assert B.pnp_set_launch_config(None, cfg) == B.PNP_ERR_ARG
+    out = (C.c_double * 13)()
+    lps = C.c_int()
+    assert B.pnp_profile(None, 1, 0.01, out, 13, C.byref(lps)) == B.PNP_ERR_ARG
+
+
 def test_no_device_fails_loudly(lib):
     import torch
 
