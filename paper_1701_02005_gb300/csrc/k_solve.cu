@@ -1296,10 +1296,11 @@ cudaError_t launch_project(T* u, T* v, T* w, T* p, const T* phip, double scale, 
                            const T* ih, cudaStream_t s) {
   if constexpr (sizeof(T) == sizeof(float)) {
     if (g.nx % 128 == 0 && g.nz % 4 == 0) {
-      // y-chunks of about 4 planes: many short blocks, which share the GPU best
-      // with the other stream's kernels (swept over 4-48 planes on the
-      // 256x193x256 workload: 4 best, 2.593 against 2.605 ms per step at 16)
-      const int nch = (g.nyc + 3) / 4, jc = (g.nyc + nch - 1) / nch;
+      // y-chunks of about 2 planes: many short blocks, which share the GPU best
+      // with the other stream's kernels (swept over 2-48 planes on the
+      // 256x193x256 workload: 2 best, 2.592 against 2.595 ms per step at 4 and
+      // 2.605 at 16)
+      const int nch = (g.nyc + 1) / 2, jc = (g.nyc + nch - 1) / nch;
       const dim3 grd((unsigned)(g.nx / 128), (unsigned)(g.nz / 4), (unsigned)((g.nyc + jc - 1) / jc));
       k_project_rows<<<grd, dim3(32, 4), 0, s>>>(u, v, w, p, phip, (float)(scale * g.idx), (float)(scale * g.idz),
                                                  (float)scale, ih, update_p, g, jc);
