@@ -326,16 +326,18 @@ enum {
 int pnp_profile(pnp_ctx* ctx, int nsteps, double dt, double* ms_out, int nsites, int* launches_per_step);
 
 /* Trace of one step (no counterpart in the paper; a tracing aid): runs one
- * full RK3 step of size dt eagerly, in the step's own concurrent schedule
- * (two streams, no graph), with a timing event after every launch site on the
- * stream that ran it.  For each event i < *n_out (at most cap; about 15 per
+ * full RK3 step of size dt in the step's own concurrent schedule (two
+ * streams), with a timing event after every launch site on the stream that
+ * ran it: launched eagerly (in_graph = 0), or captured with the events as
+ * event-record nodes into one CUDA graph and launched once (in_graph != 0;
+ * needs a context stream), which times the step as pnp_step runs it.  For each event i < *n_out (at most cap; about 15 per
  * substage): site_out[i] = its PNP_SITE_* (-1: the start of a substage),
  * stream_out[i] = 0 for the context's stream, 1 for the auxiliary stream,
  * t_ms_out[i] = milliseconds since the first event.  The wall-normal CN solve
  * appears twice per mixed substage (ions on the auxiliary stream, velocities
  * on the main one).  Advances the state by one step; synchronises. */
-int pnp_timeline(pnp_ctx* ctx, double dt, int cap, int* site_out, int* stream_out, double* t_ms_out,
-                 int* n_out);
+int pnp_timeline(pnp_ctx* ctx, double dt, int in_graph, int cap, int* site_out, int* stream_out,
+                 double* t_ms_out, int* n_out);
 
 const char* pnp_error_string(int code);
 

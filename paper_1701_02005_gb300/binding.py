@@ -77,7 +77,7 @@ EXPORTS = {
     "pnp_fp64_peak": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "pnp_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_int,
                               C.POINTER(C.c_int)]),
-    "pnp_timeline": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+    "pnp_timeline": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "pnp_autotune": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "pnp_set_launch_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),

@@ -50,6 +50,7 @@ struct Prof {
   int site[kMax], on_aux[kMax];
   int n = 0;
   bool timeline = false;   // record on each site's own stream, keep the concurrent schedule
+  bool external = false;   // during a stream capture: record as event nodes of the graph
 };
 
 struct pnp_ctx {
@@ -233,7 +234,8 @@ inline void mark(pnp_ctx* c, cudaStream_t st, int site) {
     const int i = c->prof->n++;
     c->prof->site[i] = site;
     c->prof->on_aux[i] = st == c->aux;
-    cudaEventRecord(c->prof->ev[i], st);
+    if (c->prof->external) cudaEventRecordWithFlags(c->prof->ev[i], st, cudaEventRecordExternal);
+    else cudaEventRecord(c->prof->ev[i], st);
   }
 }
 // site timing or tracing with the concurrent schedule off
@@ -1289,8 +1291,10 @@ int pnp_profile(pnp_ctx* c, int nsteps, double dt, double* ms_out, int nsites, i
   return rc;
 }
 
-int pnp_timeline(pnp_ctx* c, double dt, int cap, int* site_out, int* stream_out, double* t_ms_out, int* n_out) {
+int pnp_timeline(pnp_ctx* c, double dt, int in_graph, int cap, int* site_out, int* stream_out, double* t_ms_out,
+                 int* n_out) {
   if (!c || !site_out || !stream_out || !t_ms_out || !n_out || cap < 1 || !(dt > 0)) return PNP_ERR_ARG;
+  if (in_graph && !c->stream) return PNP_ERR_ARG;   // a capture needs a stream of its own
   if (!c->have_params || !c->have_state) return PNP_ERR_STATE;
   if (c->cn_dt != dt) {
     int r = upload_cn(c, dt);
@@ -1304,12 +1308,24 @@ int pnp_timeline(pnp_ctx* c, double dt, int cap, int* site_out, int* stream_out,
   CK(cudaStreamSynchronize(c->stream));
   Prof prof;
   prof.timeline = true;
+  prof.external = in_graph != 0;
   for (int i = 0; i < Prof::kMax; ++i) CK(cudaEventCreate(&prof.ev[i]));
   c->prof = &prof;
   int rc = PNP_OK;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (in_graph && cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) rc = PNP_ERR_CUDA;
   for (int l = 0; l < 3 && rc == PNP_OK; ++l) {
     cudaError_t e = c->precision == PNP_FP64 ? substage<double>(c, dt, l) : substage_mixed(c, dt, l);
     if (e != cudaSuccess) rc = PNP_ERR_CUDA;
+  }
+  if (in_graph) {
+    // the traced step as one graph (the events as its event-record nodes), launched once
+    const cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+    if (rc == PNP_OK && (e2 != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess ||
+                         cudaGraphLaunch(exec, c->stream) != cudaSuccess))
+      rc = PNP_ERR_CUDA;
+    cudaGetLastError();
   }
   c->prof = nullptr;
   if (rc == PNP_OK && (cudaStreamSynchronize(c->stream) != cudaSuccess || cudaStreamSynchronize(c->aux) != cudaSuccess))
@@ -1328,6 +1344,8 @@ int pnp_timeline(pnp_ctx* c, double dt, int cap, int* site_out, int* stream_out,
   }
   *n_out = n;
   for (int i = 0; i < Prof::kMax; ++i) cudaEventDestroy(prof.ev[i]);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
   if (rc == PNP_OK) {
     c->time += dt;
     c->nstep += 1;

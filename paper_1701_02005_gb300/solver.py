@@ -145,14 +145,16 @@ class Solver:
             pass
 
 
-def timeline(solver, dt, cap=64):
-    """One traced step via pnp_timeline: a list of (site, stream, ms) in launch
-    order; site is a PROFILE_SITES name or "start", stream "main" or "aux"."""
+def timeline(solver, dt, in_graph=False, cap=64):
+    """One traced step via pnp_timeline (eager, or as one CUDA graph): a list of
+    (site, stream, ms) in launch order; site is a PROFILE_SITES name or "start",
+    stream "main" or "aux"."""
     site = (C.c_int * cap)()
     stream = (C.c_int * cap)()
     t = (C.c_double * cap)()
     n = C.c_int()
-    B.check(B.pnp_timeline(solver.ctx, float(dt), cap, site, stream, t, C.byref(n)), "pnp_timeline")
+    B.check(B.pnp_timeline(solver.ctx, float(dt), int(bool(in_graph)), cap, site, stream, t, C.byref(n)),
+            "pnp_timeline")
     return [(B.PROFILE_SITES[site[i]] if site[i] >= 0 else "start", "aux" if stream[i] else "main", t[i])
             for i in range(n.value)]
 

@@ -63,7 +63,7 @@ def test_tracing_and_tuning_validate_arguments(lib):
 
     site, stream, n = (C.c_int * 8)(), (C.c_int * 8)(), C.c_int()
     t = (C.c_double * 8)()
-    assert B.pnp_timeline(None, 0.01, 8, site, stream, t, C.byref(n)) == B.PNP_ERR_ARG
+    assert B.pnp_timeline(None, 0.01, 0, 8, site, stream, t, C.byref(n)) == B.PNP_ERR_ARG
     cfg, ms = (C.c_int * 4)(), (C.c_double * 4)()
     assert B.pnp_autotune(None, 0.01, cfg, ms) == B.PNP_ERR_ARG
     assert B.pnp_set_launch_config(None, cfg) == B.PNP_ERR_ARG

@@ -1,4 +1,5 @@
-"""pnp_timeline: one traced step in the step's concurrent schedule.
+"""pnp_timeline: one traced step in the step's concurrent schedule, launched
+eagerly or as one CUDA graph with the timing events as graph nodes.
 
 The trace lists every launch site once per substage on the stream that ran
 it (the ion CN solve and the potential pipeline on the auxiliary stream, the
@@ -24,7 +25,8 @@ def _mixed(g, prm):
     return s
 
 
-def test_timeline_covers_every_site_and_matches_a_step():
+@pytest.mark.parametrize("in_graph", [False, True])
+def test_timeline_covers_every_site_and_matches_a_step(in_graph):
     from paper_1701_02005_gb300 import binding as B
     from paper_1701_02005_gb300.solver import timeline
 
@@ -35,7 +37,7 @@ def test_timeline_covers_every_site_and_matches_a_step():
         s.init_state(B.PNP_IC_PB, 11, 1e-2)
         s.step(2, 0.01)
     a.step(1, 0.01)
-    tr = timeline(b, 0.01)
+    tr = timeline(b, 0.01, in_graph=in_graph)
     assert [e[0] for e in tr].count("start") == 3
     per = len(tr) // 3
     assert len(tr) == 3 * per == 45
