@@ -31,3 +31,26 @@ def test_ensemble_recipe():
     assert len(cases) == 48
     assert sum(bench.cells(c) for c in cases) == 44_040_192
     assert {(c["nx"], c["ny"], c["nz"]) for c in cases} == {(64, 65, 64), (128, 97, 128)}
+
+
+def test_reference_arm_prints_one_contract_line():
+    # bench.py --impl reference times the oracle on the host: one JSON line with
+    # the contract's keys (a tiny grid override keeps it to a few seconds)
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--grid", "16,17,16",
+                          "--steps", "1", "--warmup", "3"], capture_output=True, text=True, timeout=300, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
