@@ -167,16 +167,19 @@ int pnp_poisson(pnp_ctx* ctx, int bc, const double* rhs_dev, double* x_dev);
  * allocates nothing: its scratch is one static device array of about 48 MB
  * (held by every GPU that loads the library until the process exits), which
  * serves grids with (Ny-1) * Nz * pitch <= 2^20 spectral points (pitch = Nx/2+1
- * rounded up to a multiple of 8), Nx, Nz <= 4096 and Ny <= 4097; larger grids
- * return PNP_ERR_TOO_LARGE.  y_faces_host: Ny host values (the first and last
- * are taken as -1 and +1); rhs_dev, x_dev: device FP64 arrays of
+ * rounded up to a multiple of 8), Nx, Nz <= 4096 and Ny <= 2049; larger grids
+ * return PNP_ERR_TOO_LARGE.  y_faces_host: Ny increasing host values (the first
+ * and last are taken as -1 and +1), read before the call returns: they travel
+ * to the GPU as a kernel argument, which also builds the grid constants in the
+ * scratch, in stream order; rhs_dev, x_dev: device FP64 arrays of
  * (Ny-1)*Nz*Nx values in the [y][z][x] layout (they may alias); cuda_stream:
  * the stream to run on (NULL = legacy default stream).  The first call on a
  * device looks up the device address of the scratch (cudaGetSymbolAddress);
  * make that first call before any stream capture.  All calls share the one
- * scratch, which keeps the last call's contents: calls that overlap on the GPU
- * (different streams, or different host threads) race and corrupt each
- * other's results; serialise them.  Asynchronous; returns PNP_OK or an error. */
+ * scratch, which keeps the last call's contents: calls queued on one stream
+ * run one after the other, but calls that overlap on the GPU (different
+ * streams, or different host threads) race and corrupt each other's results;
+ * serialise them.  Asynchronous; returns PNP_OK or an error. */
 int pnp_poisson_noalloc(int nx, int ny, int nz, double Lx, double Lz, const double* y_faces_host, int bc,
                         const double* rhs_dev, double* x_dev, void* cuda_stream);
 

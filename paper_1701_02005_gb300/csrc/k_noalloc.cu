@@ -11,6 +11,7 @@
 // rows, wavenumbers, FFT tables) is one file-scope static device array of
 // fixed size, which every GPU that loads the library holds until the process
 // exits.  The caller still passes the right-hand side and the solution array.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -23,7 +24,7 @@ namespace {
 
 // Maximum sizes served by the static scratch.
 constexpr size_t kNaMaxSpec = (size_t)1 << 20;   // spectral points (Ny-1) * Nz * pitch(Nx/2+1)
-constexpr int kNaMaxNy = 4097;                   // y face nodes
+constexpr int kNaMaxNy = 2049;                   // y face nodes (the faces travel as a kernel argument)
 constexpr int kNaMaxN = 4096;                    // Nx and Nz
 
 // Layout of the scratch, in doubles; every block starts on a 256-byte boundary.
@@ -32,7 +33,7 @@ constexpr size_t kOffSpec = 0;                                      // complex<d
 constexpr size_t kOffDscr = kOffSpec + 2 * kNaMaxSpec;              // complex<double> [kNaMaxSpec]
 constexpr size_t kOffCpr = kOffDscr + 2 * kNaMaxSpec;               // double [kNaMaxSpec]
 constexpr size_t kOffInv = kOffCpr + kNaMaxSpec;                    // double [kNaMaxSpec]
-constexpr size_t kOffConst = kOffInv + kNaMaxSpec;                  // host-computed constants below
+constexpr size_t kOffConst = kOffInv + kNaMaxSpec;                  // grid constants below
 constexpr size_t kConstRows = al32(3 * (size_t)kNaMaxNy);           // a, b, c of the y-operator
 constexpr size_t kConstKx = al32(kNaMaxN / 2 + 8);                  // kx2 (padded pitch)
 constexpr size_t kConstKz = al32(kNaMaxN);                          // kz2
@@ -42,6 +43,13 @@ constexpr size_t kConstTwz = al32(2 * kNaMaxN);                     // complex e
 constexpr size_t kConstTotal = kConstRows + kConstKx + kConstKz + kConstTwx + kConstTwp + kConstTwz;
 constexpr size_t kScratchDoubles = kOffConst + kConstTotal;         // ~48.3 MB
 
+// The y faces passed by value: a kernel argument is copied when the launch is
+// issued, so no host buffer has to outlive the call (16,392 bytes, inside the
+// 32,764-byte parameter limit).
+struct NaFaces {
+  double y[kNaMaxNy];
+};
+
 }  // namespace
 
 static __device__ __align__(256) double g_poisson_scratch[kScratchDoubles];
@@ -49,11 +57,8 @@ static __device__ __align__(256) double g_poisson_scratch[kScratchDoubles];
 namespace {
 
 constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;   // guards the per-device addresses and the static host buffers below
+std::mutex g_setup_mutex;   // guards the per-device addresses below
 double* g_scratch_ptr[kMaxDevices] = {nullptr};
-// host-side work buffers (static, so that the call allocates no host memory either)
-double g_host_const[kConstTotal];
-double g_host_dy[kNaMaxNy], g_host_yc[kNaMaxNy], g_host_h[kNaMaxNy];
 
 // Device address of the static scratch for the current device (looked up once
 // per device; the name g_poisson_scratch is only a host-side stand-in).
@@ -72,6 +77,48 @@ int scratch_address(double** out) {
 
 bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
+// Grid constants of one solve, written into the scratch in stream order (so a
+// later call on the same stream cannot overwrite them while this one runs):
+// the rows (a, b, c) of the finite-volume second difference in y (walls at
+// the first and last face, forced to -1 and +1; Dirichlet: the wall value
+// sits on the wall face, Neumann: no flux through it), the modified
+// wavenumbers (2 - 2 cos(2 pi m / N)) / d^2, and the twiddles of the real
+// x-transform and the complex z-transform.  Every entry the solve reads is
+// written, padding included.
+__global__ void k_na_constants(NaFaces f, int ny, int nx, int nz, double dx, double dz, int dirichlet,
+                               double* __restrict__ cst) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nyc = ny - 1, mh = nx / 2 + 1, mp = (mh + 7) / 8 * 8, Lh = nx / 2;
+  double* rows = cst;
+  double* kx2 = rows + kConstRows;
+  double* kz2 = kx2 + kConstKx;
+  double* twx = kz2 + kConstKz;
+  double* twp = twx + kConstTwx;
+  double* twz = twp + kConstTwp;
+  auto face = [&](int j) { return j == 0 ? -1.0 : (j == ny - 1 ? 1.0 : f.y[j]); };
+  auto centre = [&](int j) { return 0.5 * (face(j) + face(j + 1)); };
+  if (t < nyc) {
+    const double dyj = face(t + 1) - face(t);
+    const double hlo = t == 0 ? 0.5 * dyj : centre(t) - centre(t - 1);
+    const double hhi = t == nyc - 1 ? 0.5 * dyj : centre(t + 1) - centre(t);
+    const double lo = 1.0 / (hlo * dyj), hi = 1.0 / (hhi * dyj);
+    double a = 0.0, b = 0.0, c = 0.0;
+    if (t > 0) { a = lo; b -= lo; }
+    else if (dirichlet) b -= lo;
+    if (t < nyc - 1) { c = hi; b -= hi; }
+    else if (dirichlet) b -= hi;
+    rows[t] = a;
+    rows[ny + t] = b;
+    rows[2 * ny + t] = c;
+  }
+  if (t < mp) kx2[t] = t < mh ? (2.0 - 2.0 * cospi(2.0 * t / nx)) / (dx * dx) : 0.0;
+  if (t < nz) kz2[t] = (2.0 - 2.0 * cospi(2.0 * t / nz)) / (dz * dz);
+  double sn, cs;
+  if (t < Lh) { sincospi(2.0 * t / Lh, &sn, &cs); twx[2 * t] = cs; twx[2 * t + 1] = -sn; }
+  if (t <= Lh) { sincospi(2.0 * t / nx, &sn, &cs); twp[2 * t] = cs; twp[2 * t + 1] = -sn; }
+  if (t < nz) { sincospi(2.0 * t / nz, &sn, &cs); twz[2 * t] = cs; twz[2 * t + 1] = -sn; }
+}
+
 }  // namespace
 
 extern "C" int pnp_poisson_noalloc(int nx, int ny, int nz, double Lx, double Lz, const double* y_faces_host, int bc,
@@ -84,57 +131,30 @@ extern "C" int pnp_poisson_noalloc(int nx, int ny, int nz, double Lx, double Lz,
   const int mp = (mh + 7) / 8 * 8;
   const size_t nspec = (size_t)nyc * nz * mp;
   if (nx > kNaMaxN || nz > kNaMaxN || ny > kNaMaxNy || nspec > kNaMaxSpec) return PNP_ERR_TOO_LARGE;
-  std::lock_guard<std::mutex> lk(g_setup_mutex);
-  double* base = nullptr;
-  int r = scratch_address(&base);
-  if (r) return r;
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  // grid metrics from the y faces (the same finite-volume definitions as pnp_init_grid)
-  double* dy = g_host_dy;
-  double* yc = g_host_yc;
-  double* h = g_host_h;
-  for (int j = 0; j < nyc; ++j) {
+  // the faces must increase; the walls are taken as -1 and +1
+  for (int j = 0; j < ny - 1; ++j) {
     const double y0 = j == 0 ? -1.0 : y_faces_host[j];
     const double y1 = j + 1 == ny - 1 ? 1.0 : y_faces_host[j + 1];
-    dy[j] = y1 - y0;
-    yc[j] = 0.5 * (y0 + y1);
-    if (!(dy[j] > 0.0)) return PNP_ERR_GRID;
+    if (!(y1 - y0 > 0.0)) return PNP_ERR_GRID;
   }
-  h[0] = 0.5 * dy[0];
-  for (int j = 1; j < nyc; ++j) h[j] = yc[j] - yc[j - 1];
-  h[nyc] = 0.5 * dy[nyc - 1];
-  // host-computed constants, packed as in the scratch layout
-  double* cst = g_host_const;
-  std::memset(cst, 0, sizeof(g_host_const));
-  double* rows = cst;
-  double* kx2 = rows + kConstRows;
-  double* kz2 = kx2 + kConstKx;
-  double* twx = kz2 + kConstKz;
-  double* twp = twx + kConstTwx;
-  double* twz = twp + kConstTwp;
+  double* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_setup_mutex);
+    int r = scratch_address(&base);
+    if (r) return r;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
   const bool dir = bc == PNP_DIRICHLET;
-  for (int j = 0; j < nyc; ++j) {
-    const double lo = 1.0 / (h[j] * dy[j]);
-    const double hi = 1.0 / (h[j + 1] * dy[j]);
-    double b = 0.0;
-    if (j > 0) { rows[j] = lo; b -= lo; }
-    else if (dir) b -= lo;
-    if (j < nyc - 1) { rows[2 * ny + j] = hi; b -= hi; }
-    else if (dir) b -= hi;
-    rows[ny + j] = b;
-  }
   const double dx = Lx / nx, dz = Lz / nz;
-  for (int m = 0; m < mh; ++m) kx2[m] = (2.0 - 2.0 * std::cos(2.0 * M_PI * m / nx)) / (dx * dx);
-  for (int n = 0; n < nz; ++n) kz2[n] = (2.0 - 2.0 * std::cos(2.0 * M_PI * n / nz)) / (dz * dz);
-  const int Lh = nx / 2;
-  for (int t = 0; t < Lh; ++t) { twx[2 * t] = std::cos(2.0 * M_PI * t / Lh); twx[2 * t + 1] = -std::sin(2.0 * M_PI * t / Lh); }
-  for (int t = 0; t <= Lh; ++t) { twp[2 * t] = std::cos(2.0 * M_PI * t / nx); twp[2 * t + 1] = -std::sin(2.0 * M_PI * t / nx); }
-  for (int t = 0; t < nz; ++t) { twz[2 * t] = std::cos(2.0 * M_PI * t / nz); twz[2 * t + 1] = -std::sin(2.0 * M_PI * t / nz); }
   double* dconst = base + kOffConst;
-  // a pageable source is staged before cudaMemcpyAsync returns, so the static
-  // host buffer may be reused by the next call as soon as this one returns
-  if (cudaMemcpyAsync(dconst, cst, sizeof(g_host_const), cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return PNP_ERR_CUDA;
+  NaFaces faces;
+  std::memset(&faces, 0, sizeof(faces));
+  std::memcpy(faces.y, y_faces_host, sizeof(double) * (size_t)ny);
+  {
+    const int need = std::max(std::max(nyc, mp), std::max(nz, nx / 2 + 1));
+    k_na_constants<<<(need + 127) / 128, 128, 0, s>>>(faces, ny, nx, nz, dx, dz, dir ? 1 : 0, dconst);
+    if (cudaGetLastError() != cudaSuccess) return PNP_ERR_CUDA;
+  }
 
   Geo g{};
   g.nx = nx; g.nz = nz; g.nyc = nyc; g.ny = ny; g.mh = mh; g.mp = mp;

@@ -128,3 +128,122 @@ def test_labels_identity_on_identical_grids():
     assert np.allclose(T[:, 0], X[:, 0] / g.h[0], rtol=1e-13)
     assert np.allclose(T[:, 1], X[:, 1] / g.h[0], rtol=1e-13, atol=1e-14)
     assert np.allclose(T[:, 2], X[:, 4], atol=1e-14)   # first-cell phi
+
+
+# ---------------------------------------------------------------------------
+# Top-wall mapping and the sign / species of the ion-flux labels
+# ---------------------------------------------------------------------------
+def _symmetric_grid(nx, ny, nz, stretch):
+    """tanh faces made exactly antisymmetric, so that the mirror image of a
+    state lives on the same grid to the last bit."""
+    g = o.Grid(nx, ny, nz, 2 * math.pi, math.pi, stretch=stretch)
+    yf = 0.5 * (g.yf - g.yf[::-1])
+    return o.Grid(nx, ny, nz, 2 * math.pi, math.pi, y_faces=yf)
+
+
+def _mirror(g, st):
+    """Image of a state under the half turn about the z-axis, (x, y) -> (-x, -y),
+    with c+ <-> c- and Phi -> -Phi: it maps the top wall (speed +Uw, potential
+    +V) onto the bottom one (-Uw, -V), so the image solves the same problem.
+    x: centres i -> nx-1-i, x-faces i -> (nx-i) mod nx; y: cells j -> nyc-1-j,
+    faces j -> ny-1-j; z unchanged.  u and v change sign, w does not."""
+    xc = (g.nx - 1 - np.arange(g.nx))
+    xf = (g.nx - np.arange(g.nx)) % g.nx
+    img = st.copy()
+    img.u = -st.u[::-1][:, :, xf]
+    img.v = -st.v[::-1][:, :, xc]
+    img.w = st.w[::-1][:, :, xc]
+    img.cp = st.cm[::-1][:, :, xc]
+    img.cm = st.cp[::-1][:, :, xc]
+    img.Phi = -st.Phi[::-1][:, :, xc]
+    return img
+
+
+def _random_wall_state(g, prm, seed):
+    shp = (g.nyc, g.nz, g.nx)
+    st = o.initial_state(g, prm, o.IC_LAMINAR)
+    st.u = seeded.field(seed, shp, 0.3) + g.yc[:, None, None]
+    st.v = seeded.wall_zero_faces(seed + 1, (g.ny, g.nz, g.nx), 0.1)
+    st.w = seeded.field(seed + 2, shp, 0.2)
+    st.cp = seeded.positive_field(seed + 3, shp, 0.5, 2.0)
+    st.cm = seeded.positive_field(seed + 4, shp, 0.2, 3.0)
+    st.Phi = prm.V * g.yc[:, None, None] + seeded.field(seed + 5, shp, 0.4)
+    return st
+
+
+def test_top_wall_features_are_the_bottom_features_of_the_mirror_image():
+    g = _symmetric_grid(8, 17, 4, 1.8)
+    prm = o.Params(Re=100.0, lam=0.1, V=1.5)
+    st = _random_wall_state(g, prm, 61)
+    img = _mirror(g, st)
+    nc = 6
+    X = w.wall_features(g, prm, st, nc)
+    Xi = w.wall_features(g, prm, img, nc)
+    P = g.nz * g.nx
+    top = X[P:].reshape(g.nz, g.nx, 5 * nc)
+    bot_img = Xi[:P].reshape(g.nz, g.nx, 5 * nc)
+    xc = g.nx - 1 - np.arange(g.nx)
+    xf = (g.nx - np.arange(g.nx)) % g.nx
+    # u (x-faces) maps its own way in x; the centred quantities another
+    assert np.allclose(top[:, :, :nc], bot_img[:, xf, :nc], rtol=0, atol=1e-14)
+    assert np.allclose(top[:, :, nc:], bot_img[:, xc, nc:], rtol=0, atol=1e-14)
+    # the mapping is not trivially satisfied: the species and the sign matter
+    assert np.max(np.abs(top[:, :, 2 * nc:3 * nc] - top[:, :, 3 * nc:4 * nc])) > 0.1
+    assert np.max(np.abs(top[:, :, 4 * nc:])) > 0.1
+
+
+def test_top_wall_labels_are_the_bottom_labels_of_the_mirror_image():
+    gf = _symmetric_grid(8, 33, 8, 1.8)
+    gc = o.Grid(8, 9, 4, 2 * math.pi, math.pi, y_faces=gf.yf[::4])   # rx = 1 keeps the x-face map block-aligned
+    prm = o.Params(Re=100.0, lam=0.1, V=1.5)
+    st = _random_wall_state(gf, prm, 71)
+    img = _mirror(gf, st)
+    T = w.wall_labels(gf, gc, prm, st)
+    Ti = w.wall_labels(gf, gc, prm, img)
+    Pc = gc.nz * gc.nx
+    top = T[Pc:].reshape(gc.nz, gc.nx, 5)
+    bot_img = Ti[:Pc].reshape(gc.nz, gc.nx, 5)
+    xc = gc.nx - 1 - np.arange(gc.nx)
+    xf = (gc.nx - np.arange(gc.nx)) % gc.nx
+    assert np.allclose(top[:, :, 0], bot_img[:, xf, 0], rtol=1e-13, atol=1e-13)
+    assert np.allclose(top[:, :, 1:], bot_img[:, xc, 1:], rtol=1e-13, atol=1e-13)
+    assert np.max(np.abs(top[:, :, 3] - top[:, :, 4])) > 1e-3
+
+
+def test_flux_labels_of_linear_profiles_have_closed_forms():
+    """Uniform gradients give face fluxes known in closed form: diffusion of
+    c = a + b y carries -D b in +y, migration in Phi = E y carries -/+ D c E
+    for c+/c-, advection by a uniform v carries v c.  Column 3 is the counter-
+    ion (c- at the top wall, held at +V), column 4 the co-ion, both counted
+    away from their wall; distinct values per species catch a swap."""
+    gf = o.Grid(8, 33, 4, 2 * math.pi, math.pi, stretch=1.6)
+    gc = o.Grid(4, 9, 2, 2 * math.pi, math.pi, y_faces=gf.yf[::4])
+    shp = (gf.nyc, gf.nz, gf.nx)
+    prm = o.Params(Re=50.0, lam=0.1, V=0.0, Sc=2.0, Uw=0.0)
+    D = prm.D
+    P = gc.nz * gc.nx
+
+    def labels(cp, cm, Phi, v0=0.0):
+        st = o.initial_state(gf, prm, o.IC_LAMINAR)
+        st.u[...] = 0.0
+        st.cp, st.cm, st.Phi = cp, cm, Phi
+        st.v = np.zeros((gf.ny, gf.nz, gf.nx))
+        st.v[1:-1] = v0
+        T = w.wall_labels(gf, gc, prm, st)
+        return T[:P], T[P:]
+
+    ones = np.ones(shp)
+    y = gf.yc[:, None, None] * ones
+    # diffusion: c+ = 1 + 0.3 y, c- = 2 - 0.7 y
+    bot, top = labels(1.0 + 0.3 * y, 2.0 - 0.7 * y, 0.0 * ones)
+    assert np.allclose(bot[:, 3], -D * 0.3, rtol=1e-12) and np.allclose(bot[:, 4], -D * -0.7, rtol=1e-12)
+    assert np.allclose(top[:, 3], +D * -0.7, rtol=1e-12) and np.allclose(top[:, 4], +D * 0.3, rtol=1e-12)
+    # migration in a uniform field E = 0.4 with c+ = 1.5, c- = 0.5
+    E = 0.4
+    bot, top = labels(1.5 * ones, 0.5 * ones, E * y)
+    assert np.allclose(bot[:, 3], -D * 1.5 * E, rtol=1e-12) and np.allclose(bot[:, 4], +D * 0.5 * E, rtol=1e-12)
+    assert np.allclose(top[:, 3], -D * 0.5 * E, rtol=1e-12) and np.allclose(top[:, 4], +D * 1.5 * E, rtol=1e-12)
+    # advection by v = 0.05 with c+ = 1.5, c- = 0.5
+    bot, top = labels(1.5 * ones, 0.5 * ones, 0.0 * ones, v0=0.05)
+    assert np.allclose(bot[:, 3], 0.05 * 1.5, rtol=1e-12) and np.allclose(bot[:, 4], 0.05 * 0.5, rtol=1e-12)
+    assert np.allclose(top[:, 3], -0.05 * 0.5, rtol=1e-12) and np.allclose(top[:, 4], -0.05 * 1.5, rtol=1e-12)
