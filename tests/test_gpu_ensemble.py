@@ -1,6 +1,7 @@
 """Ensemble of uneven cases in one graph launch per step: every case must be
 bitwise equal to the same case advanced alone (the ensemble only changes the
-scheduling, never the arithmetic); tuned launch shapes must not change results."""
+scheduling, never the arithmetic) and match the FP64 oracle, on the grids of
+the 48-case sweep as well; tuned launch shapes must not change results."""
 import math
 
 import numpy as np
@@ -79,3 +80,57 @@ def test_autotuned_shapes_do_not_change_results(prec, tmp_path):
             # fields (wall speed 1, concentrations ~1), not bitwise
             a, b = runs[0][n], runs[1][n]
             assert np.max(np.abs(a - b)) <= 1e-6 * max(1.0, np.max(np.abs(b))), n
+
+
+def test_ensemble_cases_match_the_oracle():
+    """Each case of one graph-launched ensemble step against the FP64 oracle:
+    one case on each grid of the 48-case sweep (64 x 65 x 64 and 128 x 97 x
+    128, with the sweep's stretching and dt) plus two small ones, in FP64
+    (1e-10 relative per field) and mixed precision (fields 1e-5 of their
+    scale, velocities at least the wall speed; <u>(y) 1e-4, wall shear 1e-4)."""
+    import bench
+    from paper_1701_02005_gb300.ensemble import Ensemble
+    from paper_1701_02005_gb300.solver import Solver
+
+    sweep = {(c["nx"], c["Re"], c["lam"], c["V"]): c for c in bench.ensemble_cases()}
+    picks = [(sweep[(64, 1000.0, 0.05, 2.0)], 0), (sweep[(128, 3000.0, 0.0158, 5.0)], 1),
+             (dict(nx=16, ny=13, nz=8, Re=200.0, lam=0.1, V=2.0, stretch=2.0, dt=0.01, seed=5), 1),
+             (dict(nx=32, ny=17, nz=16, Re=500.0, lam=0.05, V=1.0, stretch=2.2, dt=0.005, seed=6), 0)]
+    names = ("u", "v", "w", "p", "cp", "cm", "Phi", "Hu", "Hv", "Hw", "Hcp", "Hcm")
+    solvers, grids, prms, starts = [], [], [], []
+    for c, prec in picks:
+        g = o.Grid(c["nx"], c["ny"], c["nz"], 2 * math.pi, math.pi, stretch=c["stretch"])
+        prm = o.Params(Re=c["Re"], lam=c["lam"], Sc=1.0, V=c["V"], beta=0.5)
+        s = Solver(g.nx, g.ny, g.nz, g.Lx, g.Lz, precision=prec, y_faces=g.yf)
+        s.set_params(prm.Re, prm.lam, prm.Sc, prm.V, prm.beta)
+        s.init_state(1, c["seed"], 0.1)
+        starts.append(o.State(*(s.get(n) for n in names)))
+        solvers.append(s)
+        grids.append(g)
+        prms.append(prm)
+    nsteps = 2
+    ens = Ensemble(solvers)
+    ens.step(nsteps, [c["dt"] for c, _ in picks])
+    ens.synchronize()
+    for i, ((c, prec), s, g, prm, st0) in enumerate(zip(picks, solvers, grids, prms, starts)):
+        ref = o.step(g, prm, st0, c["dt"], nsteps)
+        errs = {}
+        for n in ("u", "v", "w", "cp", "cm", "Phi"):
+            r = getattr(ref, n)
+            sc = max(float(np.max(np.abs(r))), 1.0 if (prec == 1 and n in ("u", "v", "w")) else 1e-300)
+            errs[n] = float(np.max(np.abs(s.get(n) - r))) / sc
+        d = s.diagnostics()
+        assert d["status"] == 0 and d["nstep"] == nsteps, (i, d)
+        print("ensemble case", i, (g.nx, g.ny, g.nz), "precision", prec, errs)
+        if prec == 0:
+            assert all(e <= 1e-10 for e in errs.values()), (i, errs)
+        else:
+            assert all(e <= 1e-5 for e in errs.values()), (i, errs)
+            du = float(np.max(np.abs(s.mean_profile("u") - o.mean_profile(ref.u))))
+            dr = o.diagnostics(g, prm, ref)
+            tau = max(abs(d["tau_bot"] - dr["tau_bot"]) / abs(dr["tau_bot"]),
+                      abs(d["tau_top"] - dr["tau_top"]) / abs(dr["tau_top"]))
+            assert du <= 1e-4 and tau <= 1e-4, (i, du, tau)
+    ens.close()
+    for s in solvers:
+        s.close()
