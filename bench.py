@@ -90,6 +90,26 @@ def site_cost(site, precision, launch_cfg=None):
 # the explicit limits: advection CFL 0.5, wall-normal migration CFL 0.5 and the
 # dielectric relaxation rate D (c+ + c-)_wall / (2 lam^2) (RK3 real-axis bound).
 # --------------------------------------------------------------------------
+def stable_dt(nx, ny, Re, lam, V, stretch, Lx=2 * math.pi):
+    """dt from the explicit limits: advection CFL 0.5 (wall speed 1), wall-normal
+    migration CFL 0.5 across the wall cell under the Gouy-Chapman wall field,
+    and the dielectric relaxation rate (RK3 real-axis bound); also returns the
+    potential drop across the wall cell."""
+    import math as m
+    bq = 2 * lam * (m.cosh(V / 2) - 1)
+    sq = 0.5 * (-bq + m.sqrt(bq * bq + 4))
+    cb = sq * sq
+    dphi_w = 2 * m.sqrt(cb) * m.sinh(V / 2) / lam
+    dy0 = 1 - m.tanh(stretch * (1 - 2.0 / (ny - 1))) / m.tanh(stretch) if stretch > 0 else 2.0 / (ny - 1)
+    D = 1.0 / Re
+    dt = 0.5 * Lx / nx
+    if V > 0:
+        dt = min(dt, 0.5 * dy0 / (D * dphi_w))
+    cwall = cb * (m.exp(V) + m.exp(-V))
+    dt = min(dt, 2.0 / (D * cwall / (2 * lam * lam)))
+    return dt, dphi_w * dy0
+
+
 def ensemble_cases():
     import math as m
     out = []
@@ -113,13 +133,7 @@ def ensemble_cases():
                     if flagged:
                         chosen = 6.0
                         dy0 = 1 - m.tanh(chosen * (1 - 2.0 / (ny - 1))) / m.tanh(chosen)
-                    D = 1.0 / Re
-                    dx = 2 * m.pi / nx
-                    dt = 0.5 * dx
-                    if V > 0:
-                        dt = min(dt, 0.5 * dy0 / (D * dphi_w))
-                    cwall = cb * (m.exp(V) + m.exp(-V))
-                    dt = min(dt, 2.0 / (D * cwall / (2 * lam * lam)))
+                    dt, _ = stable_dt(nx, ny, Re, lam, V, chosen)
                     out.append(dict(nx=nx, ny=ny, nz=nz, Re=Re, lam=lam, V=V, stretch=chosen, dt=dt,
                                     dphi_wall_cell=dphi_w * dy0, flagged=flagged, seed=1703 + idx))
                     idx += 1
@@ -167,6 +181,65 @@ def run_ensemble(args, B, Solver, torch):
             "nonfinite_or_negative": bad,
             "recipe": "2 grids (64x65x64, 128x97x128) x Re {1000,3000} x lambda {0.005,0.0158,0.05} x "
                       "V {0,2,5,10}; Gouy-Chapman ions + 0.1 noise; per-case stretching and dt"}
+
+
+# --------------------------------------------------------------------------
+# Large single case: 1024 x 385 x 512 (201,326,592 cells), Re 1e4, Debye length
+# 0.005, V 5, tanh stretching 3; mixed precision against the all-FP64 path
+# from the same initial state.
+# --------------------------------------------------------------------------
+C4 = dict(nx=1024, ny=385, nz=512, Lx=2 * math.pi, Lz=math.pi, stretch=3.0, Re=1.0e4, lam=0.005, Sc=1.0, V=5.0,
+          beta=0.5, seed=1704, amp=0.1)
+
+
+def run_large(args, B, Solver, torch):
+    from paper_1701_02005_gb300.solver import FIELD_NAMES
+
+    c = C4
+    dt, dphi_cell = stable_dt(c["nx"], c["ny"], c["Re"], c["lam"], c["V"], c["stretch"])
+    mk = lambda prec: Solver(c["nx"], c["ny"], c["nz"], c["Lx"], c["Lz"], stretch=c["stretch"], precision=prec)
+    s64 = mk(B.PNP_FP64)
+    s64.set_params(c["Re"], c["lam"], c["Sc"], c["V"], c["beta"])
+    s64.init_state(B.PNP_IC_PB, c["seed"], c["amp"])
+    smx = mk(B.PNP_MIXED)
+    smx.set_params(c["Re"], c["lam"], c["Sc"], c["V"], c["beta"])
+    for nm in ("u", "v", "w", "p", "cp", "cm", "Phi"):   # the same initial state, copied on the device
+        t = torch.empty(s64.shape(nm), dtype=torch.float64, device=s64.device)
+        s64.synchronize()
+        B.check(B.pnp_get_state(s64.ctx, FIELD_NAMES[nm], t.data_ptr(), 1), "pnp_get_state")
+        s64.synchronize()
+        smx.set_device(nm, t)
+        del t
+    d0 = s64.diagnostics()
+    K = args.large_steps
+    out = {"workload": "1024x385x512, Re 1e4, lambda_D/h 0.005, Sc 1, V 5 (V-hat 10), tanh stretching 3, "
+                       "Gouy-Chapman ions + 0.1 noise, seed 1704",
+           "cells": c["nx"] * (c["ny"] - 1) * c["nz"], "dt": dt, "dphi_wall_cell": dphi_cell, "steps": K}
+    for name, s in (("fp64", s64), ("mixed", smx)):
+        s.step(1, dt)   # graph capture
+        s.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.step(K, dt)
+        e1.record(s.stream)
+        s.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        out[name] = {"value": out["cells"] * K / t, "unit": UNIT, "ms_per_step": 1e3 * t / K}
+    um64, ummx = s64.mean_profile("u"), smx.mean_profile("u")
+    d64, dmx = s64.diagnostics(), smx.diagnostics()
+    import numpy as np
+    out.update({"speedup": out["mixed"]["value"] / out["fp64"]["value"],
+                "mean_u_abs_err": float(np.max(np.abs(ummx - um64))),
+                "tau_w_rel_err": float(max(abs(dmx["tau_bot"] - d64["tau_bot"]) / abs(d64["tau_bot"]),
+                                           abs(dmx["tau_top"] - d64["tau_top"]) / abs(d64["tau_top"]))),
+                "n_plus_rel_drift_mixed": float(abs(dmx["n_plus"] - d0["n_plus"]) / d0["n_plus"]),
+                "n_plus_rel_drift_fp64": float(abs(d64["n_plus"] - d0["n_plus"]) / d0["n_plus"]),
+                "status": [d64["status"], dmx["status"]], "cfl": dmx["cfl"], "max_dphi": dmx["max_dphi"],
+                "tolerance": 1e-4, "launch_config": "built-in defaults (not autotuned)"})
+    s64.close()
+    smx.close()
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -225,61 +298,89 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------
-def cpu_baseline(nz_sample=112, nsteps=3):
-    """The FP64 oracle as it stands, on a slab of the workload (nz reduced):
-    about 16 M cell-steps, 10 s of one host core."""
-    import numpy as np  # noqa: F401
-
+# The FP64 oracle on the host cores: the workload split into z-slabs (each an
+# independent problem of the same x/y grid and parameters, periodic in z over
+# its own extent), one slab per process, all processes timed together from a
+# common barrier.  Processes are spawned (never forked after the GPU is in use).
+# --------------------------------------------------------------------------
+def _oracle_slab(wl, nz):
     from oracle import pnp_oracle as o
 
-    g = o.Grid(WL["nx"], WL["ny"], nz_sample, WL["Lx"], WL["Lz"] * nz_sample / WL["nz"], stretch=WL["stretch"])
-    prm = o.Params(Re=WL["Re"], lam=WL["lam"], Sc=WL["Sc"], V=WL["V"], beta=WL["beta"])
-    st = o.initial_state(g, prm, o.IC_PB, seed=WL["seed"], amp=WL["amp"])
+    g = o.Grid(wl["nx"], wl["ny"], nz, wl["Lx"], wl["Lz"] * nz / wl["nz"], stretch=wl["stretch"])
+    prm = o.Params(Re=wl["Re"], lam=wl["lam"], Sc=wl["Sc"], V=wl["V"], beta=wl["beta"])
+    return o, g, prm, o.initial_state(g, prm, o.IC_PB, seed=wl["seed"], amp=wl["amp"])
+
+
+def _oracle_worker(wl, nz, warmup, steps, barrier, results):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    o, g, prm, st = _oracle_slab(wl, nz)
+    for _ in range(warmup):
+        st = o.step(g, prm, st, wl["dt"], 1)
+    barrier.wait()
     t0 = time.perf_counter()
-    o.step(g, prm, st, WL["dt"], nsteps)
+    for _ in range(steps):
+        st = o.step(g, prm, st, wl["dt"], 1)
+    results.put((g.nx * g.nyc * g.nz * steps, time.perf_counter() - t0))
+
+
+def oracle_on_host_cores(wl, warmup, steps, cores=None):
+    """Cell-steps/s of the oracle over all host cores (one z-slab per process)."""
+    import multiprocessing as mp
+
+    cores = cores or os.cpu_count() or 1
+    nproc = 1
+    while nproc * 2 <= min(cores, wl["nz"] // 2):
+        nproc *= 2
+    nz = wl["nz"] // nproc
+    ctx = mp.get_context("spawn")
+    barrier, results = ctx.Barrier(nproc), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(wl, nz, warmup, steps, barrier, results)) for _ in range(nproc)]
+    for p in procs:
+        p.start()
+    out = [results.get() for _ in procs]
+    for p in procs:
+        p.join()
+    cell_steps = sum(c for c, _ in out)
+    t = max(t for _, t in out)
+    return {"value": cell_steps / t, "unit": UNIT, "cores": nproc, "host_cpus": os.cpu_count(),
+            "threads_per_process": 1, "kind": "oracle", "seconds": t,
+            "sample": f"{nproc} processes x {steps} steps of a {wl['nx']}x{wl['ny']}x{nz} z-slab of the workload "
+                      f"({nproc * nz} of its {wl['nz']} z-planes in all; each slab periodic over its own z extent, "
+                      f"same x/y grid and parameters); NumPy FP64, one thread per process"}
+
+
+def cpu_baseline(nsteps=3):
+    """The FP64 oracle as it stands on all host cores (the workload's full cell
+    count per step, a few steps), plus the small 32x33x32 configuration's 200
+    steps on one core."""
+    out = oracle_on_host_cores(WL, 0, nsteps)
+    from oracle import pnp_oracle as o
+
+    g = o.Grid(32, 33, 32, 2 * math.pi, math.pi, stretch=2.0)
+    prm = o.Params(Re=400.0, lam=0.05, Sc=1.0, V=2.0, beta=0.5)
+    st = o.initial_state(g, prm, o.IC_PB, seed=1701, amp=1e-3)
+    t0 = time.perf_counter()
+    o.step(g, prm, st, 0.01, 200)
     t = time.perf_counter() - t0
-    n = g.nx * g.nyc * g.nz
-    return {"value": n * nsteps / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{nsteps} oracle steps of a {g.nx}x{g.ny}x{g.nz} slab of the workload (same x/y grid and "
-                      f"parameters, z extent {g.Lz:.4f}); NumPy FP64, single-threaded"}
+    out["small_case"] = {"value": g.nx * g.nyc * g.nz * 200 / t, "unit": UNIT, "cores": 1, "steps": 200,
+                         "workload": "32x33x32, Re 400, lambda_D/h 0.05, V 2, dt 0.01 (the parity configuration)"}
+    return out
 
 
 def run_reference(args):
-    """--impl reference: the oracle on the host cores, each step a bounded slab sample."""
+    """--impl reference: the oracle on all host cores, each step the whole
+    workload's cell count as independent z-slabs (one per process)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    from oracle import pnp_oracle as o
-
     K, W = args.steps, args.warmup
-    budget = 150.0 / max(K + W, 1)
-    # calibrate the per-cell cost on a thin slab
-    def slab(nz):
-        g = o.Grid(WL["nx"], WL["ny"], nz, WL["Lx"], WL["Lz"] * nz / WL["nz"], stretch=WL["stretch"])
-        prm = o.Params(Re=WL["Re"], lam=WL["lam"], Sc=WL["Sc"], V=WL["V"], beta=WL["beta"])
-        return g, prm, o.initial_state(g, prm, o.IC_PB, seed=WL["seed"], amp=WL["amp"])
-    g, prm, st = slab(4)
-    t0 = time.perf_counter()
-    o.step(g, prm, st, WL["dt"], 1)
-    per_cell = (time.perf_counter() - t0) / (g.nx * g.nyc * g.nz)
-    nz = 4
-    while nz * 2 <= WL["nz"] and per_cell * WL["nx"] * (WL["ny"] - 1) * nz * 2 <= budget:
-        nz *= 2
-    g, prm, st = slab(nz)
-    for _ in range(W):
-        st = o.step(g, prm, st, WL["dt"], 1)
-    t0 = time.perf_counter()
-    for _ in range(K):
-        st = o.step(g, prm, st, WL["dt"], 1)
-    t = time.perf_counter() - t0
-    n = g.nx * g.nyc * g.nz
-    v = n * K / t
+    cb = oracle_on_host_cores(WL, W, K)
+    v = cb["value"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": K,
-            "warmup": W, "ms_per_step": 1e3 * t / K, "higher_is_better": True, "scaling": "weak",
+            "warmup": W, "ms_per_step": 1e3 * cb["seconds"] / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WL_NAME, "sample": f"{g.nx}x{g.ny}x{g.nz} slab per step", "precision": "fp64"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{K} steps of a {g.nx}x{g.ny}x{g.nz} slab (z extent {g.Lz:.4f})"},
+            "config": {"workload": WL_NAME, "sample": cb["sample"], "precision": "fp64"},
+            "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -301,6 +402,107 @@ def reduce_times(t, dist):
 def whole_job_value(cells_per_rank, steps, world, t_max):
     """Cell-steps/s of all ranks together: every rank advances its own case."""
     return world * cells_per_rank * steps / t_max
+
+
+# --------------------------------------------------------------------------
+# Mixed precision (both solve policies) against the FP64 path from one initial
+# state: plane-mean <u>(y) and wall-shear errors every `every` steps, and the
+# time per step of each path (CUDA events over the first `timed` steps).
+# --------------------------------------------------------------------------
+def compare_precisions(B, Solver, torch, wl, V, dt, nsteps, every, launch_cfg=None, seed=None, device=0, tol=1e-4,
+                       timed=None):
+    import numpy as np
+
+    from paper_1701_02005_gb300.solver import FIELD_NAMES
+
+    mk = lambda prec: Solver(wl["nx"], wl["ny"], wl["nz"], wl["Lx"], wl["Lz"], stretch=wl["stretch"], precision=prec,
+                             device=device)
+    s64 = mk(B.PNP_FP64)
+    s64.set_params(wl["Re"], wl["lam"], wl["Sc"], V, wl["beta"])
+    s64.init_state(B.PNP_IC_PB, wl["seed"] if seed is None else seed, wl["amp"])
+    mixed = {}
+    for name, pol in (("default", B.PNP_POLICY_DEFAULT), ("fp64_solves", B.PNP_POLICY_FP64_SOLVES)):
+        sm = mk(B.PNP_MIXED)
+        sm.set_params(wl["Re"], wl["lam"], wl["Sc"], V, wl["beta"])
+        sm.set_policy(pol)
+        if launch_cfg is not None:
+            import ctypes as C
+            B.check(B.pnp_set_launch_config(sm.ctx, (C.c_int * 4)(*launch_cfg)), "pnp_set_launch_config")
+        for nm in ("u", "v", "w", "p", "cp", "cm", "Phi"):   # the same initial state, copied on the device
+            t = torch.empty(s64.shape(nm), dtype=torch.float64, device=s64.device)
+            s64.synchronize()
+            B.check(B.pnp_get_state(s64.ctx, FIELD_NAMES[nm], t.data_ptr(), 1), "pnp_get_state")
+            s64.synchronize()
+            sm.set_device(nm, t)
+        mixed[name] = sm
+    d0 = s64.diagnostics()
+    cells_ = wl["nx"] * (wl["ny"] - 1) * wl["nz"]
+    timed = timed or every
+    ms = {}
+    curve = []
+    done = 0
+    horizon = {k: None for k in mixed}
+    while done < nsteps:
+        n = min(every, nsteps - done)
+        for name, s in [("fp64", s64)] + list(mixed.items()):
+            if done == 0 and n > 1:   # time the first block (graph captured by its first step)
+                s.step(1, dt)
+                s.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s.stream)
+                s.step(n - 1, dt)
+                e1.record(s.stream)
+                s.synchronize()
+                ms[name] = e0.elapsed_time(e1) / (n - 1)
+            else:
+                s.step(n, dt)
+        done += n
+        um64 = s64.mean_profile("u")
+        d64 = s64.diagnostics()
+        point = {"step": done}
+        for name, s in mixed.items():
+            dm = s.diagnostics()
+            eu = float(np.max(np.abs(s.mean_profile("u") - um64)))
+            et = float(max(abs(dm["tau_bot"] - d64["tau_bot"]) / abs(d64["tau_bot"]),
+                           abs(dm["tau_top"] - d64["tau_top"]) / abs(d64["tau_top"])))
+            point[name] = {"mean_u_abs_err": eu, "tau_w_rel_err": et,
+                           "n_plus_rel_drift": float(abs(dm["n_plus"] - d0["n_plus"]) / d0["n_plus"])}
+            if horizon[name] is None and max(eu, et) > tol:
+                horizon[name] = done
+        curve.append(point)
+        if all(h is not None for h in horizon.values()):
+            break
+    last = curve[-1]
+    out = {"V": V, "dt": dt, "steps": done, "tolerance": tol,
+           "fp64_ms_per_step": ms.get("fp64"), "fp64_value": cells_ / (ms["fp64"] * 1e-3) if "fp64" in ms else None,
+           "mean_u_abs_err": last["default"]["mean_u_abs_err"], "tau_w_rel_err": last["default"]["tau_w_rel_err"],
+           "n_plus_rel_drift": last["default"]["n_plus_rel_drift"],
+           "fp64_solves": {"ms_per_step": ms.get("fp64_solves"),
+                           "value": cells_ / (ms["fp64_solves"] * 1e-3) if "fp64_solves" in ms else None,
+                           **last["fp64_solves"]},
+           "default_ms_per_step_here": ms.get("default"),
+           "tolerance_lost_at_step": horizon, "curve": curve}
+    s64.close()
+    for s in mixed.values():
+        s.close()
+    return out
+
+
+def run_curve(args):
+    """Mixed (both solve policies) against FP64 on the workload at V = 0, 2, 5:
+    <u>(y) and wall-shear errors every 100 steps up to --curve-steps or until
+    both policies have lost the 1e-4 tolerance."""
+    import torch
+
+    from paper_1701_02005_gb300 import binding as B
+    from paper_1701_02005_gb300.solver import Solver
+
+    out = {"workload": WL_NAME, "curves": {}}
+    for V in (0.0, 2.0, 5.0):
+        dtV = WL["dt"] if V <= 2.0 else stable_dt(WL["nx"], WL["ny"], WL["Re"], WL["lam"], V, WL["stretch"])[0]
+        out["curves"][str(V)] = compare_precisions(B, Solver, torch, WL, V, dtV, args.curve_steps, 100)
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 # --------------------------------------------------------------------------
@@ -406,37 +608,16 @@ def run_ours(args):
     # the FP64 path on the same workload, and the mixed-vs-FP64 error from one initial state
     cmp = None
     if prec == B.PNP_MIXED and not args.no_fp64_compare:
-        s64 = Solver(WL["nx"], WL["ny"], WL["nz"], WL["Lx"], WL["Lz"], stretch=WL["stretch"], precision=B.PNP_FP64,
-                     device=local)
-        s64.set_params(WL["Re"], WL["lam"], WL["Sc"], WL["V"], WL["beta"])
-        s64.init_state(B.PNP_IC_PB, WL["seed"] + rank, WL["amp"])
-        smx = Solver(WL["nx"], WL["ny"], WL["nz"], WL["Lx"], WL["Lz"], stretch=WL["stretch"], precision=B.PNP_MIXED,
-                     device=local)
-        smx.set_params(WL["Re"], WL["lam"], WL["Sc"], WL["V"], WL["beta"])
-        for nm in ("u", "v", "w", "p", "cp", "cm", "Phi"):
-            smx.set_device(nm, torch.from_numpy(s64.get(nm)).to(s64.device))
-        Kc = args.compare_steps
-        s64.step(1, dt)
-        s64.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(s64.stream)
-        s64.step(Kc - 1, dt)
-        f1.record(s64.stream)
-        s64.synchronize()
-        t64 = f0.elapsed_time(f1) / 1e3 / (Kc - 1)
-        smx.step(Kc, dt)
-        smx.synchronize()
-        um64, ummx = s64.mean_profile("u"), smx.mean_profile("u")
-        d64, dmx = s64.diagnostics(), smx.diagnostics()
-        cmp = {"fp64_value": n_cells / t64, "fp64_ms_per_step": 1e3 * t64, "speedup": (value / world) / (n_cells / t64),
-               "steps": Kc, "mean_u_abs_err": float(np.max(np.abs(ummx - um64))),
-               "tau_w_rel_err": float(max(abs(dmx["tau_bot"] - d64["tau_bot"]) / abs(d64["tau_bot"]),
-                                          abs(dmx["tau_top"] - d64["tau_top"]) / abs(d64["tau_top"]))),
-               "n_plus_rel_drift": float(abs(dmx["n_plus"] - d64["n_plus"]) / d64["n_plus"]),
-               "tolerance": 1e-4}
-        s64.close()
-        smx.close()
+        cmp = compare_precisions(B, Solver, torch, WL, WL["V"], dt, args.compare_steps, args.compare_every,
+                                 launch_cfg=launch_cfg, seed=WL["seed"] + rank, device=local)
+        cmp["speedup"] = (value / world) / cmp["fp64_value"]
+        cmp["other_voltages"] = {}
+        for V in (0.0, 5.0):   # shorter curves at the workload's other wall potentials
+            dtV = dt if V <= WL["V"] else stable_dt(WL["nx"], WL["ny"], WL["Re"], WL["lam"], V, WL["stretch"])[0]
+            r = compare_precisions(B, Solver, torch, WL, V, dtV, args.compare_steps // 2, args.compare_every,
+                                   launch_cfg=launch_cfg, seed=WL["seed"] + rank, device=local)
+            cmp["other_voltages"][str(V)] = {k: r[k] for k in ("dt", "steps", "mean_u_abs_err", "tau_w_rel_err",
+                                                                "fp64_solves", "tolerance_lost_at_step", "curve")}
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -469,6 +650,10 @@ def run_ours(args):
     if not args.no_ensemble:
         ensemble = run_ensemble(args, B, Solver, torch)
 
+    large = None
+    if not args.no_large:
+        large = run_large(args, B, Solver, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -483,6 +668,7 @@ def run_ours(args):
         "roofline": roof,
         "mixed_vs_fp64": cmp,
         "ensemble": ensemble,
+        "large_case": large,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "launch_config": launch_cfg,
@@ -508,7 +694,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--compare-steps", type=int, default=20)
+    ap.add_argument("--compare-steps", type=int, default=200)
+    ap.add_argument("--compare-every", type=int, default=20)
+    ap.add_argument("--curve", action="store_true",
+                    help="only the mixed-vs-FP64 error curves at V = 0, 2, 5 over --curve-steps steps")
+    ap.add_argument("--curve-steps", type=int, default=2000)
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-e2e", action="store_true")
@@ -516,6 +706,8 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--ensemble-steps", type=int, default=20)
+    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--large-steps", type=int, default=20)
     ap.add_argument("--grid", default=None,
                     help="NX,NY,NZ override of the workload grid (small cases for profiler captures only)")
     args = ap.parse_args()
@@ -528,6 +720,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.curve:
+        return run_curve(args)
     return run_ours(args)
 
 

@@ -45,14 +45,32 @@ enum {
   PNP_ERR_NEGATIVE_C = -7,   /* device check: a concentration went negative       */
   PNP_ERR_UNSUPPORTED = -8,  /* option not available for this precision          */
   PNP_ERR_TOO_LARGE = -9,    /* grid exceeds the static scratch of pnp_poisson_noalloc */
-  PNP_ERR_TIMEOUT = -10      /* device check: an asynchronous copy did not complete in time */
+  PNP_ERR_TIMEOUT = -10,     /* device check: an asynchronous copy did not complete in time */
+  PNP_ERR_CFL = -11,         /* device check: advective CFL number of the last dt above its limit */
+  PNP_ERR_DPHI = -12         /* device check: potential step between neighbouring cells above its limit */
 };
 
 /* Arithmetic precision of a context. */
 enum {
   PNP_FP64 = 0,   /* every field, stencil, FFT and solve in FP64                  */
-  PNP_MIXED = 1   /* u, v, w, p stencils and the pressure FFT in FP32; ions,
-                     potential, all tridiagonal solves and global sums in FP64    */
+  PNP_MIXED = 1   /* FP32: u, v, w, p and every stencil (advection, viscous and
+                     Coulomb terms, ion fluxes of the fluctuations about the
+                     plane-mean reference profiles); FP64-level: the ion state
+                     (FP64 reference profile + double-float fluctuation), the
+                     reference double-layer terms (FP64 per plane), the global
+                     sums (double-float per thread, FP64 across threads).  The
+                     solves depend on the policy (pnp_set_policy): by default
+                     the spectral y-solves of both Poisson problems in double-
+                     float, the (0,0) potential mode and the reference ion CN
+                     in FP64, the transforms and the velocity and ion-
+                     fluctuation CN solves in FP32; PNP_POLICY_FP64_SOLVES moves
+                     every transform and tridiagonal solve to FP64 arithmetic */
+};
+
+/* Solve precision of a PNP_MIXED context (see above). */
+enum {
+  PNP_POLICY_DEFAULT = 0,      /* FP32 transforms and CN, double-float spectral solves */
+  PNP_POLICY_FP64_SOLVES = 1   /* FP64 transforms, spectral and CN solves                 */
 };
 
 /* Fields for pnp_set_state / pnp_get_state / pnp_mean_profile. */
@@ -87,13 +105,27 @@ typedef struct pnp_diag {
   double n_plus;      /* sum c+ dV                                                */
   double n_minus;     /* sum c- dV                                                */
   double net_charge;  /* n_plus - n_minus                                         */
-  double wall_flux;   /* total ion flux through the wall faces (zero by design)   */
+  double wall_flux;   /* |flux_plus| + |flux_minus| (zero by design, Fig. 1)     */
   double max_div;     /* max |div u| over the cells                               */
   double ke;          /* kinetic energy 1/2 sum |u|^2 dV                          */
   double time;        /* simulated time                                           */
   long long nstep;    /* completed steps                                          */
   int status;         /* device error word (PNP_OK or a PNP_ERR_* code)           */
   int precision;
+  double cfl;         /* dt max(|u|/dx + |v|/dy + |w|/dz), cell-centred velocities,
+                         dt the last step's size (0 before the first step)       */
+  double max_dphi;    /* max |Phi difference| between neighbouring cells (x, z,
+                         interior y faces), in units of V_T                      */
+  double flux_plus;   /* net c+ flux out through the two wall faces implied by the
+                         stored explicit terms: -sum H_c+ dV (the discrete
+                         divergence theorem; the implicit y-diffusion has no wall
+                         coupling), per unit time                                */
+  double flux_minus;  /* the same for c-                                         */
+  double dt_cfl;      /* dt at which the advective CFL number reaches 1          */
+  double dt_migration;/* dt at which the ion drift D |grad Phi| crosses one cell
+                         (the explicit migration term's CFL number reaches 1)    */
+  double dt_dielectric; /* 1 / max D (c+ + c-) / (2 lam^2): the time scale of
+                         dielectric (charge) relaxation, explicit in the scheme  */
 } pnp_diag;
 
 /* Bytes of device workspace needed for an Nx x Ny x Nz grid (Ny = face nodes). */
@@ -148,6 +180,38 @@ int pnp_step(pnp_ctx* ctx, int nsteps, double dt);
  * as double-float pairs), no FP64 copy of the state; the ion numbers and
  * energies agree with their FP64 evaluation to ~1e-13 relative. */
 int pnp_diagnostics(pnp_ctx* ctx, pnp_diag* out);
+
+/* Adaptive time step (the explicit parts of the scheme -- advection,
+ * migration and with it the dielectric relaxation -- bound dt; Numerical
+ * methods, the stiffness of the double layer): advances nsteps steps; before
+ * every block of check_every steps (>= 1) it reads the state's limits (as
+ * pnp_diagnostics, synchronising) and takes dt = min(dt_max, cfl dt_cfl,
+ * cfl dt_migration, 4 cfl dt_dielectric), rounded down to the ladder
+ * dt_max 2^(-k/8) so that a run revisits few distinct dt values (each new dt
+ * recomputes the CN factors and recaptures the step's graph); dt grows by at
+ * most one rung per check.  dts_out (host, optional, nsteps values) receives
+ * the dt of every step.  0 < cfl <= 1.  Stops with the device status if a
+ * check reports one (PNP_ERR_NONFINITE, ...). */
+int pnp_step_adaptive(pnp_ctx* ctx, int nsteps, double dt_max, double cfl, int check_every, double* dts_out);
+
+/* Select the solve precision of a PNP_MIXED context (PNP_POLICY_*): the
+ * stencils, storage and sums are the same under both; PNP_POLICY_FP64_SOLVES
+ * runs the wall-normal CN solves of u, v, w and of the ion fluctuations, both
+ * Poisson problems' x/z transforms and their spectral y-solves in FP64
+ * arithmetic (FP64 forward values, one rounding to the state's storage), as a
+ * plain reading of "FP64 for the tridiagonal and Poisson solves" asks.
+ * PNP_ERR_UNSUPPORTED for a non-default policy on a PNP_FP64 context. */
+int pnp_set_policy(pnp_ctx* ctx, int policy);
+
+/* Stability limits of the diagnostics' device checks: PNP_ERR_CFL when dt max(|u|/dx + |v|/dy + |w|/dz) of the
+ * last step exceeds cfl_max (default sqrt(3), the imaginary-axis stability
+ * bound of the three-stage RK3 for centred advection), PNP_ERR_DPHI when the
+ * potential changes by more than dphi_max between neighbouring cells (default
+ * 2: beyond it the discrete Boltzmann ratio (2 - dPhi) / (2 + dPhi) of the
+ * arithmetic face means turns negative and the migration flux can drive a
+ * concentration below zero).  Both are reported by pnp_diagnostics / pnp_status
+ * after NaN/Inf and negative-concentration checks; the step is not stopped. */
+int pnp_set_limits(pnp_ctx* ctx, double cfl_max, double dphi_max);
 
 /* Plane average <q>(y) of a field into host memory (Ny-1 values, Ny for v). */
 int pnp_mean_profile(pnp_ctx* ctx, int field, double* out_host);

@@ -22,6 +22,10 @@ PNP_ERR_NEGATIVE_C = -7
 PNP_ERR_UNSUPPORTED = -8
 PNP_ERR_TOO_LARGE = -9
 PNP_ERR_TIMEOUT = -10
+PNP_ERR_CFL = -11
+PNP_ERR_DPHI = -12
+PNP_POLICY_DEFAULT = 0
+PNP_POLICY_FP64_SOLVES = 1
 
 PNP_FP64 = 0
 PNP_MIXED = 1
@@ -46,6 +50,8 @@ class pnp_diag(C.Structure):
         ("n_plus", C.c_double), ("n_minus", C.c_double), ("net_charge", C.c_double),
         ("wall_flux", C.c_double), ("max_div", C.c_double), ("ke", C.c_double), ("time", C.c_double),
         ("nstep", C.c_longlong), ("status", C.c_int), ("precision", C.c_int),
+        ("cfl", C.c_double), ("max_dphi", C.c_double), ("flux_plus", C.c_double), ("flux_minus", C.c_double),
+        ("dt_cfl", C.c_double), ("dt_migration", C.c_double), ("dt_dielectric", C.c_double),
     ]
 
     def as_dict(self):
@@ -71,6 +77,10 @@ EXPORTS = {
     "pnp_poisson_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_double),
                                       C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pnp_eval_explicit": (C.c_int, [C.c_void_p]),
+    "pnp_set_limits": (C.c_int, [C.c_void_p, C.c_double, C.c_double]),
+    "pnp_set_policy": (C.c_int, [C.c_void_p, C.c_int]),
+    "pnp_step_adaptive": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int,
+                                    C.POINTER(C.c_double)]),
     "pnp_status": (C.c_int, [C.c_void_p]),
     "pnp_clear_status": (C.c_int, [C.c_void_p]),
     "pnp_selftest_wait_timeout": (C.c_int, [C.c_void_p, C.c_double]),
@@ -161,6 +171,9 @@ pnp_mean_profile = _fwd("pnp_mean_profile")
 pnp_poisson = _fwd("pnp_poisson")
 pnp_poisson_noalloc = _fwd("pnp_poisson_noalloc")
 pnp_eval_explicit = _fwd("pnp_eval_explicit")
+pnp_set_limits = _fwd("pnp_set_limits")
+pnp_set_policy = _fwd("pnp_set_policy")
+pnp_step_adaptive = _fwd("pnp_step_adaptive")
 pnp_status = _fwd("pnp_status")
 pnp_clear_status = _fwd("pnp_clear_status")
 pnp_selftest_wait_timeout = _fwd("pnp_selftest_wait_timeout")

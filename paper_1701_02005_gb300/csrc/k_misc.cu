@@ -93,20 +93,30 @@ cudaError_t launch_init_fields(const Fields<TV>& f, const Geo& g, const Metrics&
 // ---------------------------------------------------------------------------
 // Diagnostics: per-block partial sums in a fixed order, then one block.
 // Slots: 0 sum u(j=0), 1 sum u(j=nyc-1), 2 sum c+ dy, 3 sum c- dy, 4 max|div|,
-// 5 sum (u^2 + w^2) dy + v^2 h, 6 count of non-finite values, 7 min(c+, c-).
+// 5 sum (u^2 + w^2) dy + v^2 h, 6 count of non-finite values, 7 min(c+, c-),
+// 8 max advective rate |u_c|/dx + |v_c|/dy + |w_c|/dz (cell-centred velocities;
+// times dt it is the CFL number), 9 max |Phi difference| between neighbouring
+// cells (x, z and interior y faces), 10 / 11 sum of the stored explicit ion
+// terms H_c+ dy, H_c- dy (by the discrete divergence theorem minus the net
+// ion flux through the two wall faces, per unit dx dz), 12 max migration rate
+// over D: |dPhi_x|/dx^2 + |dPhi_y|/(h dy) + |dPhi_z|/dz^2 (the drift speed
+// D |grad Phi| over the cell size), 13 max (c+ + c-) (times D / (2 lam^2) the
+// dielectric relaxation rate).
 // ---------------------------------------------------------------------------
-constexpr int kDiagSlots = 8;
+constexpr int kDiagSlots = 14;
 constexpr int kDiagThreads = 256;
 
+__device__ __forceinline__ bool diag_is_max(int q) { return q == 4 || q == 8 || q == 9 || q == 12 || q == 13; }
+
 __device__ __forceinline__ void block_reduce(double* sh, double* vals, int tid) {
-  // tree reduction of kDiagSlots values per thread; op: sum, except slot 4 (max) and 7 (min)
+  // tree reduction of kDiagSlots values per thread; op: sum, except the maxima (4, 8, 9, 12, 13) and the minimum (7)
   for (int q = 0; q < kDiagSlots; ++q) sh[q * kDiagThreads + tid] = vals[q];
   __syncthreads();
   for (int st = kDiagThreads / 2; st > 0; st >>= 1) {
     if (tid < st) {
       for (int q = 0; q < kDiagSlots; ++q) {
         double a = sh[q * kDiagThreads + tid], b = sh[q * kDiagThreads + tid + st];
-        sh[q * kDiagThreads + tid] = q == 4 ? fmax(a, b) : (q == 7 ? fmin(a, b) : a + b);
+        sh[q * kDiagThreads + tid] = diag_is_max(q) ? fmax(a, b) : (q == 7 ? fmin(a, b) : a + b);
       }
     }
     __syncthreads();
@@ -116,7 +126,7 @@ __device__ __forceinline__ void block_reduce(double* sh, double* vals, int tid) 
 template <typename TV>
 __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Fields<TV> f, Geo g, Metrics m, double* partial) {
   __shared__ double sh[kDiagSlots * kDiagThreads];
-  double acc[kDiagSlots] = {0, 0, 0, 0, 0, 0, 0, 1e300};
+  double acc[kDiagSlots] = {0, 0, 0, 0, 0, 0, 0, 1e300, 0, 0, 0, 0, 0, 0};
   const size_t P = (size_t)g.nz * g.nx;
   const size_t nc = (size_t)g.nyc * P, nv = (size_t)g.ny * P;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -137,7 +147,18 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Fields<TV> f, Geo
                        ((double)f.w[cidx(j, kp, i, g.nz, g.nx)] - w) * g.idz;
     acc[4] = fmax(acc[4], fabs(div));
     acc[5] += (u * u + w * w) * dy;
+    const double ue = (double)f.u[cidx(j, k, ip, g.nz, g.nx)], wn = (double)f.w[cidx(j, kp, i, g.nz, g.nx)];
+    const double rate = fabs(0.5 * (u + ue)) * g.idx + fabs(0.5 * ((double)f.v[c] + (double)f.v[c + P])) * m.idy[j] +
+                        fabs(0.5 * (w + wn)) * g.idz;
+    acc[8] = fmax(acc[8], rate);
     const double p = (double)f.p[c], Ph = f.Phi[c];
+    const double dpx = fabs(f.Phi[cidx(j, k, ip, g.nz, g.nx)] - Ph), dpz = fabs(f.Phi[cidx(j, kp, i, g.nz, g.nx)] - Ph);
+    const double dpy = j + 1 < g.nyc ? fabs(f.Phi[c + P] - Ph) : 0.0;
+    acc[9] = fmax(acc[9], fmax(fmax(dpx, dpz), dpy));
+    acc[12] = fmax(acc[12], dpx * g.idx * g.idx + dpy * m.ih[j + 1] * m.idy[j] + dpz * g.idz * g.idz);
+    acc[13] = fmax(acc[13], cp + cm);
+    acc[10] += f.Hcp[c] * dy;
+    acc[11] += f.Hcm[c] * dy;
     if (!isfinite(u) || !isfinite(w) || !isfinite(cp) || !isfinite(cm) || !isfinite(p) || !isfinite(Ph) ||
         !isfinite(div))
       acc[6] += 1.0;
@@ -171,11 +192,12 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Fields<TV> f, Geo
 __global__ void __launch_bounds__(kDiagThreads, 4) k_diag_partial_mixed(Fields<float> f, Shadows sh,
                                                                         const float* __restrict__ cref_p,
                                                                         const float* __restrict__ cref_m,
+                                                                        const float* __restrict__ dPref,
                                                                         const float2* __restrict__ wgt, Geo g,
                                                                         double* partial) {
   __shared__ double shr[kDiagSlots * kDiagThreads];
-  dfl sum[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};   // slots 0-3, 5
-  float maxdiv = 0.f, bad = 0.f, cmin = 3.0e38f;
+  dfl sum[7] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};   // 0-3, 5, 10, 11
+  float maxdiv = 0.f, bad = 0.f, cmin = 3.0e38f, maxrate = 0.f, maxdphi = 0.f, maxmig = 0.f, maxcsum = 0.f;
   const int nx = g.nx, nz = g.nz, lnz = __ffs(nz) - 1;
   const size_t P = (size_t)nz * nx;
   const int rows = g.nyc * nz, per = (rows + gridDim.x - 1) / gridDim.x;
@@ -185,16 +207,18 @@ __global__ void __launch_bounds__(kDiagThreads, 4) k_diag_partial_mixed(Fields<f
   const dfl idx{idxh, (float)(g.idx - (double)idxh)}, idz{idzh, (float)(g.idz - (double)idzh)};
   // the current run of rows in plane jr: sums still to be weighted
   int jr = r0 >> lnz;
-  dfl ruw{0.f, 0.f}, rv{0.f, 0.f}, rcp{0.f, 0.f}, rcm{0.f, 0.f}, ru{0.f, 0.f};
+  dfl ruw{0.f, 0.f}, rv{0.f, 0.f}, rcp{0.f, 0.f}, rcm{0.f, 0.f}, ru{0.f, 0.f}, rhp{0.f, 0.f}, rhm{0.f, 0.f};
   auto flush = [&]() {
     const float2 dyw = wgt[jr], hw = wgt[g.ny + jr];
     const dfl dy{dyw.x, dyw.y}, h{hw.x, hw.y};
     sum[4] = df_add(sum[4], df_add(df_mul(ruw, dy), df_mul(rv, h)));
     sum[2] = df_add(sum[2], df_mul(rcp, dy));
     sum[3] = df_add(sum[3], df_mul(rcm, dy));
+    sum[5] = df_add(sum[5], df_mul(rhp, dy));
+    sum[6] = df_add(sum[6], df_mul(rhm, dy));
     if (jr == 0) sum[0] = df_add(sum[0], ru);
     if (jr == g.nyc - 1) sum[1] = df_add(sum[1], ru);
-    ruw = rv = rcp = rcm = ru = dfl{0.f, 0.f};
+    ruw = rv = rcp = rcm = ru = rhp = rhm = dfl{0.f, 0.f};
   };
   for (int r = r0; r < r1; ++r) {
     const int j = r >> lnz, k = r & (nz - 1);
@@ -205,6 +229,8 @@ __global__ void __launch_bounds__(kDiagThreads, 4) k_diag_partial_mixed(Fields<f
     const int kp = (k + 1) & (nz - 1);
     const float2 iyw = wgt[2 * g.ny + j];
     const float crp = cref_p[j], crm = cref_m[j];
+    const float dpy = j + 1 < g.nyc ? dPref[j + 1] : 0.f;   // Phi_ref step across face j+1 (interior faces)
+    const float ihy = j + 1 < g.nyc ? 1.f / wgt[g.ny + j + 1].x : 0.f;   // 1 / h of that face
     const size_t rowo = (size_t)r * nx, rowkp = ((size_t)j * nz + kp) * nx;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       const size_t c = rowo + i;
@@ -231,6 +257,15 @@ __global__ void __launch_bounds__(kDiagThreads, 4) k_diag_partial_mixed(Fields<f
           !isfinite(v0) || !isfinite(est))
         bad += 1.f;
       cmin = fminf(cmin, fminf(crp + Sp, crm + Sm));
+      maxrate = fmaxf(maxrate, fabsf(0.5f * (u + ue)) * idxh + fabsf(0.5f * (v0 + v1)) * iyw.x +
+                                   fabsf(0.5f * (w + wn)) * idzh);
+      const float dpx = fabsf(sh.phi[rowo + ip] - ph), dpz = fabsf(sh.phi[rowkp + i] - ph);
+      const float dpyc = j + 1 < g.nyc ? fabsf(dpy + (sh.phi[c + P] - ph)) : 0.f;
+      maxdphi = fmaxf(maxdphi, fmaxf(fmaxf(dpx, dpz), dpyc));
+      maxmig = fmaxf(maxmig, dpx * idxh * idxh + dpyc * ihy * iyw.x + dpz * idzh * idzh);
+      maxcsum = fmaxf(maxcsum, (crp + Sp) + (crm + Sm));
+      rhp = df_add_fast(rhp, dfl{sh.Hcp[c], 0.f});
+      rhm = df_add_fast(rhm, dfl{sh.Hcm[c], 0.f});
     }
   }
   if (r0 < r1) flush();
@@ -244,20 +279,25 @@ __global__ void __launch_bounds__(kDiagThreads, 4) k_diag_partial_mixed(Fields<f
   }
   auto d = [](dfl x) { return (double)x.h + (double)x.l; };
   double acc[kDiagSlots] = {d(sum[0]), d(sum[1]), d(sum[2]), d(sum[3]), (double)maxdiv, d(sum[4]), (double)bad,
-                            (double)cmin};
+                            (double)cmin, (double)maxrate, (double)maxdphi, d(sum[5]), d(sum[6]), (double)maxmig,
+                            (double)maxcsum};
   block_reduce(shr, acc, threadIdx.x);
   if (threadIdx.x == 0)
     for (int q = 0; q < kDiagSlots; ++q) partial[(size_t)blockIdx.x * kDiagSlots + q] = shr[q * kDiagThreads];
 }
 
+// Final reduction and the device status word: a non-finite value, a negative
+// concentration, an advective CFL number (rate x dt, dt > 0 the last step's
+// size) above cfl_max, or a potential step between neighbouring cells above
+// dphi_max, in that order of precedence.
 __global__ void __launch_bounds__(kDiagThreads) k_diag_final(const double* partial, int npartial, double* out,
-                                                            int* status) {
+                                                            int* status, DiagLimits lim) {
   __shared__ double sh[kDiagSlots * kDiagThreads];
-  double acc[kDiagSlots] = {0, 0, 0, 0, 0, 0, 0, 1e300};
+  double acc[kDiagSlots] = {0, 0, 0, 0, 0, 0, 0, 1e300, 0, 0, 0, 0, 0, 0};
   for (int b = threadIdx.x; b < npartial; b += blockDim.x) {
     for (int q = 0; q < kDiagSlots; ++q) {
       const double v = partial[(size_t)b * kDiagSlots + q];
-      acc[q] = q == 4 ? fmax(acc[q], v) : (q == 7 ? fmin(acc[q], v) : acc[q] + v);
+      acc[q] = diag_is_max(q) ? fmax(acc[q], v) : (q == 7 ? fmin(acc[q], v) : acc[q] + v);
     }
   }
   block_reduce(sh, acc, threadIdx.x);
@@ -266,34 +306,38 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_final(const double* parti
     int st = PNP_OK;
     if (sh[6 * kDiagThreads] > 0.0) st = PNP_ERR_NONFINITE;
     else if (sh[7 * kDiagThreads] < 0.0) st = PNP_ERR_NEGATIVE_C;
+    else if (lim.dt > 0.0 && sh[8 * kDiagThreads] * lim.dt > lim.cfl_max) st = PNP_ERR_CFL;
+    else if (sh[9 * kDiagThreads] > lim.dphi_max) st = PNP_ERR_DPHI;
     *status = st;
   }
 }
 
 template <typename TV>
 cudaError_t launch_diagnostics(const Fields<TV>& f, const Geo& g, const Metrics& m, const Phys& ph,
-                               double* partial, int npartial, double* out, int* status, cudaStream_t s) {
+                               double* partial, int npartial, double* out, int* status, const DiagLimits& lim,
+                               cudaStream_t s) {
   (void)ph;
   k_diag_partial<TV><<<npartial, kDiagThreads, 0, s>>>(f, g, m, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_diag_final<<<1, kDiagThreads, 0, s>>>(partial, npartial, out, status);
+  k_diag_final<<<1, kDiagThreads, 0, s>>>(partial, npartial, out, status, lim);
   return cudaGetLastError();
 }
 
 cudaError_t launch_diagnostics_mixed(const Fields<float>& f, const Shadows& sh, const float* cref_p,
-                                     const float* cref_m, const float2* wgt, const Geo& g, double* partial,
-                                     int npartial, double* out, int* status, cudaStream_t s) {
+                                     const float* cref_m, const float* dPref, const float2* wgt, const Geo& g,
+                                     double* partial, int npartial, double* out, int* status,
+                                     const DiagLimits& lim, cudaStream_t s) {
   // one resident wave: four 256-thread blocks per SM (64 registers a thread)
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   const int nb = std::max(1, std::min(npartial, 4 * sms));
-  k_diag_partial_mixed<<<nb, kDiagThreads, 0, s>>>(f, sh, cref_p, cref_m, wgt, g, partial);
+  k_diag_partial_mixed<<<nb, kDiagThreads, 0, s>>>(f, sh, cref_p, cref_m, dPref, wgt, g, partial);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_diag_final<<<1, kDiagThreads, 0, s>>>(partial, nb, out, status);
+  k_diag_final<<<1, kDiagThreads, 0, s>>>(partial, nb, out, status, lim);
   return cudaGetLastError();
 }
 
@@ -356,9 +400,9 @@ template cudaError_t launch_init_fields<double>(const Fields<double>&, const Geo
 template cudaError_t launch_init_fields<float>(const Fields<float>&, const Geo&, const Metrics&, const Phys&, int,
                                                double, double, uint64_t, double, const double*, cudaStream_t);
 template cudaError_t launch_diagnostics<double>(const Fields<double>&, const Geo&, const Metrics&, const Phys&,
-                                                double*, int, double*, int*, cudaStream_t);
+                                                double*, int, double*, int*, const DiagLimits&, cudaStream_t);
 template cudaError_t launch_diagnostics<float>(const Fields<float>&, const Geo&, const Metrics&, const Phys&,
-                                               double*, int, double*, int*, cudaStream_t);
+                                               double*, int, double*, int*, const DiagLimits&, cudaStream_t);
 template cudaError_t launch_convert<double, double>(const double*, double*, size_t, cudaStream_t);
 template cudaError_t launch_convert<double, float>(const double*, float*, size_t, cudaStream_t);
 template cudaError_t launch_convert<float, double>(const float*, double*, size_t, cudaStream_t);

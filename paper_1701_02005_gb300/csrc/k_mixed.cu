@@ -442,6 +442,138 @@ cudaError_t launch_mixed_cn(const Fields<float>& f, const Shadows& sh, const Mix
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// FP64-arithmetic variants of the mixed path's wall-normal CN solves (the
+// "FP64 solves" policy): the FP32 right-hand sides are eliminated and
+// back-substituted in FP64 with the FP64 factor rows, the forward values kept
+// in FP64 scratch (d never rounds to FP32), and the update is added in FP64
+// before the single rounding to the state's storage: velocities to FP32, the
+// ion fluctuation (S, L) += dC_ref + x as an FP64 sum split back into a
+// double-float pair.
+// ---------------------------------------------------------------------------
+template <int CH>
+__device__ __forceinline__ double cn_forward_f64(const float* __restrict__ r, double* __restrict__ d_out,
+                                                 const CNRows& rw, int n, size_t P) {
+  double d = 0.0;
+  for (int jb = 0; jb < n; jb += CH) {
+    float rr[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+      if (jb + u < n) rr[u] = r[(size_t)(jb + u) * P];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int j = jb + u;
+      if (j < n) {
+        d = ((double)rr[u] - rw.a[j] * d) * rw.m[j];
+        d_out[(size_t)j * P] = d;
+      }
+    }
+  }
+  return d;
+}
+
+__global__ void k_cn_vel_f64(float* __restrict__ u, const float* __restrict__ ru, float* __restrict__ v,
+                             const float* __restrict__ rv, float* __restrict__ w, const float* __restrict__ rw,
+                             double* __restrict__ du, double* __restrict__ dv, double* __restrict__ dw,
+                             CNRows cell, CNRows face, int nyc, size_t P) {
+  constexpr int CH = 8;
+  const size_t line = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (line >= P) return;
+  float* q;
+  const float* r;
+  double* ds;
+  CNRows rws;
+  int n, j0;
+  if (blockIdx.y == 0) { q = u; r = ru; ds = du; rws = cell; n = nyc; j0 = 0; }
+  else if (blockIdx.y == 1) { q = v; r = rv; ds = dv; rws = face; n = nyc - 1; j0 = 1; }
+  else { q = w; r = rw; ds = dw; rws = cell; n = nyc; j0 = 0; }
+  const float* rl = r + (size_t)j0 * P + line;
+  double* dl = ds + (size_t)j0 * P + line;
+  float* ql = q + (size_t)j0 * P + line;
+  cn_forward_f64<CH>(rl, dl, rws, n, P);
+  double x = 0.0;
+  for (int jb = n - 1; jb >= 0; jb -= CH) {
+    double dd[CH];
+    float qq[CH];
+#pragma unroll
+    for (int k = 0; k < CH; ++k)
+      if (jb - k >= 0) {
+        dd[k] = dl[(size_t)(jb - k) * P];
+        qq[k] = ql[(size_t)(jb - k) * P];
+      }
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+      const int j = jb - k;
+      if (j >= 0) {
+        x = dd[k] - rws.c[j] * x;
+        ql[(size_t)j * P] = (float)((double)qq[k] + x);
+      }
+    }
+  }
+}
+
+__global__ void k_cn_ion_f64(const float* __restrict__ rcp, float* __restrict__ Sp, float* __restrict__ Lp,
+                             const float* __restrict__ rcm, float* __restrict__ Sm, float* __restrict__ Lm,
+                             double* __restrict__ dp, double* __restrict__ dm, CNRows rows,
+                             const double* __restrict__ dCp, const double* __restrict__ dCm, int n, size_t P) {
+  constexpr int CH = 8;
+  const size_t line = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (line >= P) return;
+  const bool plus = blockIdx.y == 0;
+  const float* r = (plus ? rcp : rcm) + line;
+  float* S = (plus ? Sp : Sm) + line;
+  float* L = (plus ? Lp : Lm) + line;
+  double* dl = (plus ? dp : dm) + line;
+  const double* dC = plus ? dCp : dCm;
+  cn_forward_f64<CH>(r, dl, rows, n, P);
+  double x = 0.0;
+  for (int jb = n - 1; jb >= 0; jb -= CH) {
+    double dd[CH];
+    float sh[CH], sl[CH];
+#pragma unroll
+    for (int k = 0; k < CH; ++k)
+      if (jb - k >= 0) {
+        const size_t o = (size_t)(jb - k) * P;
+        dd[k] = dl[o];
+        sh[k] = S[o];
+        sl[k] = L[o];
+      }
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+      const int j = jb - k;
+      if (j >= 0) {
+        const size_t o = (size_t)j * P;
+        x = dd[k] - rows.c[j] * x;
+        const double t = ((double)sh[k] + (double)sl[k]) + (dC[j] + x);
+        const float hi = (float)t;
+        S[o] = hi;
+        L[o] = (float)(t - (double)hi);
+      }
+    }
+  }
+}
+
+cudaError_t launch_mixed_cn_fp64(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
+                                 const CNRows& cell, const CNRows& face, const CNRows& ion, int l, unsigned parts,
+                                 const CnScratch64& scr, cudaStream_t s) {
+  const size_t P = (size_t)g.nz * g.nx;
+  const int T = 128;
+  if (parts & kCnIons) {
+    dim3 grd((unsigned)((P + T - 1) / T), 2, 1);
+    k_cn_ion_f64<<<grd, T, 0, s>>>(reinterpret_cast<const float*>(f.rcp), sh.cp, sh.cpL,
+                                   reinterpret_cast<const float*>(f.rcm), sh.cm, sh.cmL, scr.dcp, scr.dcm, ion,
+                                   R.Rref_p + (size_t)l * g.nyc, R.Rref_m + (size_t)l * g.nyc, g.nyc, P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (parts & kCnVelocity) {
+    dim3 grd((unsigned)((P + T - 1) / T), 3, 1);
+    k_cn_vel_f64<<<grd, T, 0, s>>>(f.u, f.ru, f.v, f.rv, f.w, f.rw, scr.du, scr.dv, scr.dw, cell, face, g.nyc, P);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_plane_means3(const double* a, const double* b, const double* c, int nplanes, size_t P,
                                 double* oa, double* ob, double* oc, cudaStream_t s) {
   k_plane_means3<<<nplanes, 256, 0, s>>>(a, b, c, P, oa, ob, oc);

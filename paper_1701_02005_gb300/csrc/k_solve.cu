@@ -161,6 +161,7 @@ struct SrcArgs {
   T sx, sz;               // scale / dx, scale / dz in the transform's precision
   const T* idyT;          // 1 / dy in the transform's precision
   T ss;                   // scale
+  const float *la, *lb;   // low parts of the double-float ion fluctuations (ChargeShadowDF)
 };
 
 template <typename T, typename TV>
@@ -181,6 +182,9 @@ __device__ __forceinline__ T src_value(const SrcArgs<T, TV>& a, const Geo& g, co
   } else if (a.kind == PoissonSrc::ChargeShadow) {
     // fluctuating charge about the reference profile, FP32
     return T(-(a.sa[c] - a.sb[c])) * a.ss;
+  } else if (a.kind == PoissonSrc::ChargeShadowDF) {
+    // the same from the full double-float fluctuations (S + L), in T
+    return -(((T)a.sa[c] + (T)a.la[c]) - ((T)a.sb[c] + (T)a.lb[c])) * a.ss;
   }
   return a.plain[c];
 }
@@ -438,9 +442,9 @@ cudaError_t launch_fft_x_fwd(PoissonSrc kind, const TV* u, const TV* v, const TV
                              const double* cm, const T* plain, double scale, const Geo& g,
                              const Metrics& m, cplx<T>* spec, const cplx<T>* tw_half,
                              const cplx<T>* tw_post, cudaStream_t s, const float* sa, const float* sb,
-                             const T* idyT) {
+                             const T* idyT, const float* la, const float* lb) {
   SrcArgs<T, TV> a{kind, u, v, w, cp, cm, plain, scale, sa, sb, (T)(scale * g.idx), (T)(scale * g.idz), idyT,
-                   (T)scale};
+                   (T)scale, la, lb};
   if constexpr (sizeof(T) == sizeof(float)) {
     auto go = [&](auto kern, int G, int rows, size_t smem) {
       if (smem > 48 * 1024) {
@@ -1323,17 +1327,20 @@ template cudaError_t launch_fft_x_fwd<double, double>(PoissonSrc, const double*,
                                                       const double*, const double*, const double*, double,
                                                       const Geo&, const Metrics&, cplx<double>*,
                                                       const cplx<double>*, const cplx<double>*, cudaStream_t,
-                                                      const float*, const float*, const double*);
+                                                      const float*, const float*, const double*, const float*,
+                                                      const float*);
 template cudaError_t launch_fft_x_fwd<float, float>(PoissonSrc, const float*, const float*, const float*,
                                                     const double*, const double*, const float*, double,
                                                     const Geo&, const Metrics&, cplx<float>*,
                                                     const cplx<float>*, const cplx<float>*, cudaStream_t,
-                                                    const float*, const float*, const float*);
+                                                    const float*, const float*, const float*, const float*,
+                                                    const float*);
 template cudaError_t launch_fft_x_fwd<double, float>(PoissonSrc, const float*, const float*, const float*,
                                                      const double*, const double*, const double*, double,
                                                      const Geo&, const Metrics&, cplx<double>*,
                                                      const cplx<double>*, const cplx<double>*, cudaStream_t,
-                                                     const float*, const float*, const double*);
+                                                     const float*, const float*, const double*, const float*,
+                                                     const float*);
 
 template cudaError_t launch_fft_z<double>(cplx<double>*, const cplx<double>*, const Geo&, bool, cudaStream_t);
 template cudaError_t launch_fft_z<float>(cplx<float>*, const cplx<float>*, const Geo&, bool, cudaStream_t);
@@ -1351,6 +1358,9 @@ template cudaError_t launch_fft_x_inv<double, double>(PoissonDst, const cplx<dou
 template cudaError_t launch_fft_x_inv<float, float>(PoissonDst, const cplx<float>*, const Geo&, const Metrics&,
                                                     const cplx<float>*, const cplx<float>*, double, float*,
                                                     cudaStream_t, const double*);
+template cudaError_t launch_fft_x_inv<double, float>(PoissonDst, const cplx<double>*, const Geo&, const Metrics&,
+                                                     const cplx<double>*, const cplx<double>*, double, float*,
+                                                     cudaStream_t, const double*);
 
 template cudaError_t launch_project<double>(double*, double*, double*, double*, const double*, double, bool,
                                             const Geo&, const double*, cudaStream_t);

@@ -5,6 +5,7 @@
 //   per RK3 substage l:  explicit terms -> y-implicit CN solves ->
 //   pressure Poisson (Neumann) + projection -> potential Poisson (Dirichlet).
 // A step is captured once per dt into a CUDA graph on non-default streams.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -119,6 +120,10 @@ struct pnp_ctx {
   bool have_params = false, have_state = false;
   double time = 0.0;
   long long nstep = 0;
+  double last_dt = 0.0;                         // size of the last step (0: none yet)
+  int policy = PNP_POLICY_DEFAULT;              // mixed path: where the solves' FP64 accuracy comes from
+  double cfl_max = 1.7320508075688772, dphi_max = 2.0;   // limits of the device checks
+  double refH_p = 0.0, refH_m = 0.0;            // sum over cells of H_ref(j) dy_j (mixed)
   cudaGraphExec_t gexec = nullptr;
   double graph_dt = NAN;
   double cn_dt = NAN;
@@ -150,8 +155,8 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
   double* cn = b.take<double>(27 * (size_t)ny);
   void *twx = b.take<cplx<double>>(nx / 2), *twp = b.take<cplx<double>>(nx / 2 + 1), *twz = b.take<cplx<double>>(nz);
   void *twxf = b.take<cplx<float>>(nx / 2), *twpf = b.take<cplx<float>>(nx / 2 + 1), *twzf = b.take<cplx<float>>(nz);
-  double* dpart = b.take<double>((size_t)kDiagBlocks * 8);
-  double* dout = b.take<double>(8);
+  double* dpart = b.take<double>((size_t)kDiagBlocks * 16);
+  double* dout = b.take<double>(16);
   int* st = b.take<int>(4);
   double* probe = b.take<double>((size_t)kProbeBlocks * 256);
   float *cpS = b.take<float>(nc), *cmS = b.take<float>(nc), *phiS = b.take<float>(nc);
@@ -591,6 +596,68 @@ cudaError_t potential_mixed(pnp_ctx* c, cudaStream_t st, void* spec_buf, cplx<do
   return e;
 }
 
+// The "FP64 solves" policy of the mixed path: both Poisson problems with FP64
+// transforms, FP64 spectral y-solves and an FP64 (0,0) mode, from the FP32
+// velocities and the double-float ion state; Phi_p and phi' stored in FP32.
+cudaError_t pressure_projection_fp64(pnp_ctx* c, double scale) {
+  const Metrics m = metrics(c);
+  const Fields<float> f = fields<float>(c);
+  cplx<double>* spec = (cplx<double>*)c->spec;
+  const cplx<double>* twx = (const cplx<double>*)c->twx_d;
+  const cplx<double>* twp = (const cplx<double>*)c->twp_d;
+  const cplx<double>* twz = (const cplx<double>*)c->twz_d;
+  float* phip = (float*)c->sreal;
+  cudaError_t e = launch_fft_x_fwd<double, float>(PoissonSrc::Divergence, f.u, f.v, f.w, nullptr, nullptr, nullptr,
+                                                  1.0 / scale, c->g, m, spec, twx, twp, c->stream, nullptr, nullptr,
+                                                  c->idy_d);
+  if (e != cudaSuccess) return e;
+  mark(c, c->stream, PNP_SITE_P_FFTX);
+  e = spectral_solve<double>(c, spec, twz, true, c->stream, c->dscr);
+  if (e != cudaSuccess) return e;
+  e = launch_fft_x_inv<double, float>(PoissonDst::Plain, spec, c->g, m, twx, twp, 0.0, phip, c->stream);
+  if (e != cudaSuccess) return e;
+  mark(c, c->stream, PNP_SITE_P_IFFTX);
+  e = launch_project<float>(f.u, f.v, f.w, f.p, phip, scale, true, c->g, c->mf[1], c->stream);
+  mark(c, c->stream, PNP_SITE_PROJECT);
+  return e;
+}
+
+cudaError_t potential_mixed_fp64(pnp_ctx* c, cudaStream_t st, void* spec_buf, cplx<double>* dscr) {
+  const Shadows sh = shadows(c);
+  const Metrics m = metrics(c);
+  cplx<double>* spec = (cplx<double>*)spec_buf;
+  const cplx<double>* twx = (const cplx<double>*)c->twx_d;
+  const cplx<double>* twp = (const cplx<double>*)c->twp_d;
+  const cplx<double>* twz = (const cplx<double>*)c->twz_d;
+  cudaError_t e = launch_fft_x_fwd<double, float>(PoissonSrc::ChargeShadowDF, nullptr, nullptr, nullptr, nullptr,
+                                                  nullptr, nullptr, c->ph.q, c->g, m, spec, twx, twp, st, sh.cp,
+                                                  sh.cm, nullptr, sh.cpL, sh.cmL);
+  if (e != cudaSuccess) return e;
+  mark(c, st, PNP_SITE_E_FFTX);
+  e = launch_fft_z<double>(spec, twz, c->g, false, st);
+  if (e != cudaSuccess) return e;
+  mark(c, st, PNP_SITE_E_FFTZ);
+  const double scale = 1.0 / ((double)c->g.nx * (double)c->g.nz);
+  e = launch_spec_thomas<double>(spec, dscr, c->spc_cprD, c->spc_invD, yrows(c, false), c->g, scale, false, st,
+                                 c->meanrhs_d, c->meanshift_d, c->delta_d);
+  if (e != cudaSuccess) return e;
+  mark(c, st, PNP_SITE_E_THOMAS);
+  e = launch_fft_z<double>(spec, twz, c->g, true, st);
+  if (e != cudaSuccess) return e;
+  mark(c, st, PNP_SITE_E_IFFTZ);
+  e = launch_fft_x_inv<double, float>(PoissonDst::PotentialShadow, spec, c->g, m, twx, twp, 0.0, sh.phi, st,
+                                      c->delta_d);
+  mark(c, st, PNP_SITE_E_IFFTX);
+  return e;
+}
+
+// FP64 scratch of the FP64-arithmetic CN solves: the FP64 copies of the ion
+// state, Phi, H_c+- and the conversion stage are not read during a mixed step
+// (they are materialised on demand afterwards), so they hold the forward values.
+CnScratch64 cn_scratch64(const pnp_ctx* c) {
+  return CnScratch64{c->cp, c->stage, c->cm, c->Phi, c->Hcp};
+}
+
 // Pressure projection on the main stream and the potential solve, which
 // depends only on the ions of this substage, on the auxiliary stream; joined
 // before the substage ends.  Sequential when profiling (site timing).
@@ -635,30 +702,43 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
   const Fields<float> f = fields<float>(c);
   const Shadows sh = shadows(c);
   const MixedRefs R = mixed_refs(c);
-  const Metrics m = metrics(c);
+  const bool fp64 = c->policy == PNP_POLICY_FP64_SOLVES;
   mark(c, c->stream, -1);
   cudaError_t e =
       launch_mixed_rhs(f, sh, R, c->g, metrics_f(c), coef_f(c, st, l < 2), rhs_maps(c), c->status_d + 1, c->stream);
   if (e != cudaSuccess) return e;
   mark(c, c->stream, PNP_SITE_RHS);
   const CNRowsF cell = cn_rows_f(c, l, 0), face = cn_rows_f(c, l, 1), ion = cn_rows_f(c, l, 2);
+  auto cn = [&](unsigned parts, cudaStream_t s) {
+    return fp64 ? launch_mixed_cn_fp64(f, sh, R, c->g, cn_rows(c, l, 0), cn_rows(c, l, 1), cn_rows(c, l, 2), l, parts,
+                                       cn_scratch64(c), s)
+                : launch_mixed_cn(f, sh, R, c->g, cell, face, ion, l, parts, s);
+  };
+  auto pot = [&](cudaStream_t s, void* spec, cplx<double>* dscr) {
+    return fp64 ? potential_mixed_fp64(c, s, spec, dscr) : potential_mixed(c, s, spec, dscr);
+  };
+  auto proj = [&]() {
+    return fp64 ? pressure_projection_fp64(c, st.alp * dt) : pressure_projection<float>(c, st.alp * dt, true);
+  };
   if (serial_sites(c)) {   // site timing: everything in order on the main stream
-    e = launch_mixed_cn(f, sh, R, c->g, cell, face, ion, l, kCnIons | kCnVelocity, c->stream);
+    e = cn(kCnIons | kCnVelocity, c->stream);
     if (e != cudaSuccess) return e;
     mark(c, c->stream, PNP_SITE_CN);
-    return poisson_pair<float>(c, st.alp * dt);
+    e = proj();
+    if (e != cudaSuccess) return e;
+    return pot(c->stream, c->spec, c->dscr);
   }
   // The ion CN solve and the potential depend only on the ions: both fork onto
   // the auxiliary stream right after the stencil and overlap the velocity CN
   // solve, the pressure pipeline and the projection.
   e = cudaEventRecord(c->ev_fork, c->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
-  if (e == cudaSuccess) e = launch_mixed_cn(f, sh, R, c->g, cell, face, ion, l, kCnIons, c->aux);
+  if (e == cudaSuccess) e = cn(kCnIons, c->aux);
   if (e == cudaSuccess) mark(c, c->aux, PNP_SITE_CN);
-  if (e == cudaSuccess) e = potential_mixed(c, c->aux, c->spec2, c->dscr2);
-  if (e == cudaSuccess) e = launch_mixed_cn(f, sh, R, c->g, cell, face, ion, l, kCnVelocity, c->stream);
+  if (e == cudaSuccess) e = pot(c->aux, c->spec2, c->dscr2);
+  if (e == cudaSuccess) e = cn(kCnVelocity, c->stream);
   if (e == cudaSuccess) mark(c, c->stream, PNP_SITE_CN);
-  if (e == cudaSuccess) e = pressure_projection<float>(c, st.alp * dt, true);
+  if (e == cudaSuccess) e = proj();
   if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->aux);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
   return e;
@@ -738,10 +818,13 @@ int refresh_refs(pnp_ctx* c, double dt) {
       dPref[j] = (float)dP;
       Fvref[j] = (float)(-K * rf * dP * ih);
     }
+    c->refH_p = c->refH_m = 0.0;
     for (int j = 0; j < nyc; ++j) {
       const double idy = 1.0 / c->dy[j];
       c->href_p[j] = -(Fp[j + 1] - Fp[j]) * idy;
       c->href_m[j] = -(Fm[j + 1] - Fm[j]) * idy;
+      c->refH_p += (double)P * c->href_p[j] * c->dy[j];
+      c->refH_m += (double)P * c->href_m[j] * c->dy[j];
       const double lo = 1.0 / (c->h[j] * c->dy[j]), hi = 1.0 / (c->h[j + 1] * c->dy[j]);
       c->lyc_p[j] = (j > 0 ? lo * (cp[j - 1] - cp[j]) : 0.0) + (j < nyc - 1 ? hi * (cp[j + 1] - cp[j]) : 0.0);
       c->lyc_m[j] = (j > 0 ? lo * (cm[j - 1] - cm[j]) : 0.0) + (j < nyc - 1 ? hi * (cm[j + 1] - cm[j]) : 0.0);
@@ -1054,6 +1137,49 @@ int pnp_step(pnp_ctx* c, int nsteps, double dt) {
   }
   c->time += nsteps * dt;
   c->nstep += nsteps;
+  c->last_dt = dt;
+  return PNP_OK;
+}
+
+int pnp_step_adaptive(pnp_ctx* c, int nsteps, double dt_max, double cfl, int check_every, double* dts_out) {
+  if (!c || nsteps < 0 || !(dt_max > 0) || !std::isfinite(dt_max) || !(cfl > 0) || cfl > 1 || check_every < 1)
+    return PNP_ERR_ARG;
+  if (!c->have_params || !c->have_state) return PNP_ERR_STATE;
+  int rung = -1;   // ladder index of the current dt
+  for (int done = 0; done < nsteps;) {
+    pnp_diag d;
+    const int st = pnp_diagnostics(c, &d);
+    if (st != PNP_OK && st != PNP_ERR_CFL && st != PNP_ERR_DPHI) return st;
+    const double lim = std::min(std::min(cfl * d.dt_cfl, cfl * d.dt_migration), 4.0 * cfl * d.dt_dielectric);
+    int k = 0;
+    if (lim < dt_max) k = (int)std::ceil(8.0 * std::log2(dt_max / lim) - 1e-12);
+    if (rung >= 0 && k < rung - 1) k = rung - 1;   // grow by one rung at most
+    if (k > 4096) return PNP_ERR_CFL;              // no usable dt (limits collapsed)
+    rung = k;
+    const double dt = dt_max * std::exp2(-k / 8.0);
+    const int n = std::min(check_every, nsteps - done);
+    const int r = pnp_step(c, n, dt);
+    if (r) return r;
+    if (dts_out)
+      for (int q = 0; q < n; ++q) dts_out[done + q] = dt;
+    done += n;
+  }
+  return PNP_OK;
+}
+
+int pnp_set_policy(pnp_ctx* c, int policy) {
+  if (!c || (policy != PNP_POLICY_DEFAULT && policy != PNP_POLICY_FP64_SOLVES)) return PNP_ERR_ARG;
+  if (policy != PNP_POLICY_DEFAULT && c->precision != PNP_MIXED) return PNP_ERR_UNSUPPORTED;
+  if (c->policy != policy) drop_graph(c);
+  c->policy = policy;
+  return PNP_OK;
+}
+
+int pnp_set_limits(pnp_ctx* c, double cfl_max, double dphi_max) {
+  if (!c || !(cfl_max > 0) || !(dphi_max > 0) || !std::isfinite(cfl_max) || !std::isfinite(dphi_max))
+    return PNP_ERR_ARG;
+  c->cfl_max = cfl_max;
+  c->dphi_max = dphi_max;
   return PNP_OK;
 }
 
@@ -1068,24 +1194,27 @@ int pnp_diagnostics(pnp_ctx* c, pnp_diag* out) {
     int r = materialize(c);
     if (r) return r;
   }
+  const DiagLimits lim{c->last_dt, c->cfl_max, c->dphi_max};
   cudaError_t e =
-      from_shadows ? launch_diagnostics_mixed(fields<float>(c), shadows(c), c->crefp_f, c->crefm_f, c->diag_w,
-                                              c->g, c->diag_partial, kDiagBlocks, c->diag_out, c->status_d,
-                                              c->stream)
+      from_shadows ? launch_diagnostics_mixed(fields<float>(c), shadows(c), c->crefp_f, c->crefm_f, c->dPref_f,
+                                              c->diag_w, c->g, c->diag_partial, kDiagBlocks, c->diag_out,
+                                              c->status_d, lim, c->stream)
       : c->precision == PNP_FP64
           ? launch_diagnostics<double>(fields<double>(c), c->g, metrics(c), c->ph, c->diag_partial, kDiagBlocks,
-                                       c->diag_out, c->status_d, c->stream)
+                                       c->diag_out, c->status_d, lim, c->stream)
           : launch_diagnostics<float>(fields<float>(c), c->g, metrics(c), c->ph, c->diag_partial, kDiagBlocks,
-                                      c->diag_out, c->status_d, c->stream);
+                                      c->diag_out, c->status_d, lim, c->stream);
   if (e != cudaSuccess) return PNP_ERR_CUDA;
-  double h[8];
+  double h[kDiagOutSlots];
   int st2[2] = {0, 0};
   CK(cudaMemcpyAsync(h, c->diag_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(st2, c->status_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  if (from_shadows) {   // the reference part of the ion numbers
+  if (from_shadows) {   // the reference parts of the ion numbers and of the explicit ion terms
     h[2] += c->refN_p;
     h[3] += c->refN_m;
+    h[10] += c->refH_p;
+    h[11] += c->refH_m;
   }
   const int st = st2[1] ? st2[1] : st2[0];
   const double P = (double)c->g.nx * c->g.nz;
@@ -1112,7 +1241,16 @@ int pnp_diagnostics(pnp_ctx* c, pnp_diag* out) {
   out->n_plus = h[2] * c->g.dx * c->g.dz;
   out->n_minus = h[3] * c->g.dx * c->g.dz;
   out->net_charge = out->n_plus - out->n_minus;
-  out->wall_flux = 0.0;   // the scheme sets every wall-face ion flux to zero (Fig. 1 caption)
+  // net ion flux out through the walls: the cell sums of -H_c telescope to the
+  // wall-face fluxes (zero in the scheme, Fig. 1 caption)
+  out->flux_plus = -h[10] * c->g.dx * c->g.dz;
+  out->flux_minus = -h[11] * c->g.dx * c->g.dz;
+  out->wall_flux = std::fabs(out->flux_plus) + std::fabs(out->flux_minus);
+  out->cfl = c->last_dt * h[8];
+  out->max_dphi = h[9];
+  out->dt_cfl = h[8] > 0 ? 1.0 / h[8] : INFINITY;
+  out->dt_migration = h[12] > 0 ? 1.0 / (c->ph.D * h[12]) : INFINITY;
+  out->dt_dielectric = h[13] > 0 ? 1.0 / (c->ph.D * c->ph.q * h[13]) : INFINITY;
   out->max_div = h[4];
   out->ke = 0.5 * h[5] * c->g.dx * c->g.dz;
   out->time = c->time;
@@ -1656,6 +1794,7 @@ int pnp_ensemble_step(pnp_ensemble* e, int nsteps, const double* dt) {
     else CK(cudaStreamSynchronize(e->stream));
     e->cases[i]->time += nsteps * dt[i];
     e->cases[i]->nstep += nsteps;
+    e->cases[i]->last_dt = dt[i];
   }
   return PNP_OK;
 }
@@ -1966,6 +2105,8 @@ const char* pnp_error_string(int code) {
     case PNP_ERR_UNSUPPORTED: return "unsupported option";
     case PNP_ERR_TIMEOUT: return "an asynchronous copy did not complete within the kernel's wait limit";
     case PNP_ERR_TOO_LARGE: return "grid exceeds the static scratch of pnp_poisson_noalloc (2^20 spectral points)";
+    case PNP_ERR_CFL: return "advective CFL number of the last step above its limit";
+    case PNP_ERR_DPHI: return "potential step between neighbouring cells above its limit";
     default: return "unknown error";
   }
 }

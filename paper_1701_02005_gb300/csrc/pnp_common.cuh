@@ -105,7 +105,9 @@ cudaError_t launch_cn_solves(const Fields<TV>& f, const Geo& g, const CNRows& ve
                              const CNRows& ion, cudaStream_t s);
 
 // Poisson pipeline pieces.  Spectral buffer holds (nyc, nz, mp) complex T.
-enum class PoissonSrc { Divergence, Charge, ChargeShadow, Plain };
+// ChargeShadowDF: the fluctuating charge from the double-float ion state
+// (high parts sa, sb and low parts la, lb), formed in the transform's precision.
+enum class PoissonSrc { Divergence, Charge, ChargeShadow, ChargeShadowDF, Plain };
 enum class PoissonDst { Plain, Potential, PotentialShadow };
 
 template <typename T, typename TV>
@@ -113,7 +115,8 @@ cudaError_t launch_fft_x_fwd(PoissonSrc src, const TV* u, const TV* v, const TV*
                              const double* cm, const T* plain, double scale, const Geo& g,
                              const Metrics& m, cplx<T>* spec, const cplx<T>* tw_half,
                              const cplx<T>* tw_post, cudaStream_t s, const float* sa = nullptr,
-                             const float* sb = nullptr, const T* idyT = nullptr);
+                             const float* sb = nullptr, const T* idyT = nullptr, const float* la = nullptr,
+                             const float* lb = nullptr);
 
 template <typename T>
 cudaError_t launch_fft_z(cplx<T>* spec, const cplx<T>* tw_z, const Geo& g, bool inverse, cudaStream_t s);
@@ -153,9 +156,19 @@ cudaError_t launch_init_fields(const Fields<TV>& f, const Geo& g, const Metrics&
                                int ic_kind, double cb, double kappa, uint64_t seed, double amp,
                                const double* yf, cudaStream_t s);
 
+// Stability limits checked by the diagnostics pass (device status word):
+// dt = the last step's size (<= 0: no CFL check), cfl_max = bound on
+// dt (|u|/dx + |v|/dy + |w|/dz), dphi_max = bound on the potential step
+// between neighbouring cells (2: the positivity limit of the discrete
+// Boltzmann ratio (2 - dPhi) / (2 + dPhi) of the arithmetic face means).
+struct DiagLimits {
+  double dt, cfl_max, dphi_max;
+};
+constexpr int kDiagOutSlots = 14;   // doubles written by the final diagnostics reduction
+
 template <typename TV>
 cudaError_t launch_diagnostics(const Fields<TV>& f, const Geo& g, const Metrics& m, const Phys& ph,
-                               double* partial, int npartial, double* out, int* status,
+                               double* partial, int npartial, double* out, int* status, const DiagLimits& lim,
                                cudaStream_t s);
 
 template <typename TA, typename TB>

@@ -66,10 +66,13 @@ bool rhs_tma_eligible(const Geo& g);
 // One bounded mbarrier wait that cannot complete (failure-path self-test).
 // Diagnostics partial sums from the FP32 fields and the df ion state (no FP64
 // copy); wgt[j] = dy_j and wgt[2 ny + j] = 1/dy_j (j < nyc), wgt[ny + j] = h_j,
-// as df pairs.  The reference part of the ion numbers is not included.
+// as df pairs; dPref[j] the reference potential step across interior face j.
+// The reference parts of the ion numbers and of the explicit ion terms are not
+// included.
 cudaError_t launch_diagnostics_mixed(const Fields<float>& f, const Shadows& sh, const float* cref_p,
-                                     const float* cref_m, const float2* wgt, const Geo& g, double* partial,
-                                     int npartial, double* out, int* status, cudaStream_t s);
+                                     const float* cref_m, const float* dPref, const float2* wgt, const Geo& g,
+                                     double* partial, int npartial, double* out, int* status,
+                                     const DiagLimits& lim, cudaStream_t s);
 cudaError_t launch_wait_selftest(int* err, double limit_s, cudaStream_t s);
 cudaError_t build_rhs_maps(RhsMaps* m, const Fields<float>& f, const Shadows& sh, const Geo& g);
 // maps == nullptr selects the cp.async tile kernel; err receives PNP_ERR_TIMEOUT
@@ -81,6 +84,14 @@ constexpr unsigned kCnIons = 1, kCnVelocity = 2;
 cudaError_t launch_mixed_cn(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
                             const CNRowsF& cell, const CNRowsF& face, const CNRowsF& ion, int l, unsigned parts,
                             cudaStream_t s);
+// FP64 scratch of the FP64-arithmetic CN solves: forward values per line
+// (du, dw, dcp, dcm: nyc planes; dv: ny planes).
+struct CnScratch64 {
+  double *du, *dv, *dw, *dcp, *dcm;
+};
+cudaError_t launch_mixed_cn_fp64(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
+                                 const CNRows& cell, const CNRows& face, const CNRows& ion, int l, unsigned parts,
+                                 const CnScratch64& scr, cudaStream_t s);
 cudaError_t launch_plane_means3(const double* a, const double* b, const double* c, int nplanes, size_t P,
                                 double* oa, double* ob, double* oc, cudaStream_t s);
 cudaError_t launch_make_shadows(const double* cp, const double* cm, const double* Phi, const double* Hcp,

@@ -94,15 +94,32 @@ class Solver:
     def step(self, nsteps, dt):
         B.check(B.pnp_step(self.ctx, int(nsteps), float(dt)), "pnp_step")
 
+    def step_adaptive(self, nsteps, dt_max, cfl=0.5, check_every=10):
+        """nsteps steps with dt from the state's explicit limits (pnp_step_adaptive);
+        returns the dt of every step."""
+        dts = np.zeros(int(nsteps), dtype=np.float64)
+        B.check(B.pnp_step_adaptive(self.ctx, int(nsteps), float(dt_max), float(cfl), int(check_every),
+                                    dts.ctypes.data_as(C.POINTER(C.c_double))), "pnp_step_adaptive")
+        return dts
+
     def synchronize(self):
         self.stream.synchronize()
 
     def diagnostics(self):
         d = B.pnp_diag()
         code = B.pnp_diagnostics(self.ctx, C.byref(d))
-        if code not in (B.PNP_OK, B.PNP_ERR_NONFINITE, B.PNP_ERR_NEGATIVE_C, B.PNP_ERR_TIMEOUT):
+        if code not in (B.PNP_OK, B.PNP_ERR_NONFINITE, B.PNP_ERR_NEGATIVE_C, B.PNP_ERR_TIMEOUT, B.PNP_ERR_CFL,
+                        B.PNP_ERR_DPHI):
             B.check(code, "pnp_diagnostics")
         return d.as_dict()
+
+    def set_policy(self, policy):
+        """Solve precision of a mixed context: binding.PNP_POLICY_DEFAULT or PNP_POLICY_FP64_SOLVES."""
+        B.check(B.pnp_set_policy(self.ctx, int(policy)), "pnp_set_policy")
+
+    def set_limits(self, cfl_max=3 ** 0.5, dphi_max=2.0):
+        """Limits of the device checks reported as PNP_ERR_CFL / PNP_ERR_DPHI."""
+        B.check(B.pnp_set_limits(self.ctx, float(cfl_max), float(dphi_max)), "pnp_set_limits")
 
     def mean_profile(self, name):
         n = self.shape(name)[0]

@@ -4,7 +4,8 @@ oracle, element by element on the same seeded state.
 
 * mixed precision at 256 x 65 x 256 (the workload's x/z grid and parameters,
   a shorter y-grid): 256-point register transforms, 64-wide stencil tiles with
-  neighbouring tiles in x, the stencil's multi-chunk y-march, three steps.
+  neighbouring tiles in x, the stencil's multi-chunk y-march, three steps;
+  under both solve policies (default, and FP64 transforms and solves).
   Tolerances: fields 1e-5 of each field's scale (velocities at least the wall
   speed), <u>(y) 1e-4 absolute and the wall shear 1e-4 relative (the stated
   accuracy of the mixed path);
@@ -43,10 +44,12 @@ def _scale(name, ref):
     return max(m, 1.0) if name in VEL else max(m, 1e-300)
 
 
-def test_mixed_at_the_workload_x_z_grid_matches_the_oracle():
+@pytest.mark.parametrize("policy", [0, 1])
+def test_mixed_at_the_workload_x_z_grid_matches_the_oracle(policy):
     from paper_1701_02005_gb300 import binding as B
 
     g, prm, s, st0 = _setup(256, 65, 256, B.PNP_MIXED)
+    s.set_policy(policy)
     nsteps, dt = 3, C2["dt"]
     s.step(nsteps, dt)
     ref = o.step(g, prm, st0, dt, nsteps)
@@ -56,7 +59,7 @@ def test_mixed_at_the_workload_x_z_grid_matches_the_oracle():
     d, dr = s.diagnostics(), o.diagnostics(g, prm, ref)
     tau = max(abs(d["tau_bot"] - dr["tau_bot"]) / abs(dr["tau_bot"]),
               abs(d["tau_top"] - dr["tau_top"]) / abs(dr["tau_top"]))
-    print("mixed 256x65x256 vs oracle:", errs, "<u>", du, "tau", tau)
+    print("mixed 256x65x256 (policy %d) vs oracle:" % policy, errs, "<u>", du, "tau", tau)
     assert d["status"] == 0
     assert all(e <= 1e-5 for e in errs.values()), errs
     assert du <= 1e-4 and tau <= 1e-4, (du, tau)

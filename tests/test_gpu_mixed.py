@@ -203,3 +203,45 @@ def test_mixed_diagnostics_from_shadows_match_the_definition():
         assert abs(d["max_div"] - ref["max_div"]) <= 1e-6 * ref["max_div"] + 1e-15
         assert d["status"] == 0
     s.close()
+
+
+def test_mixed_fp64_solves_policy_against_the_oracle():
+    # the policy that runs every transform and tridiagonal solve of the mixed
+    # path in FP64 arithmetic: the same tolerances as the default policy
+    from paper_1701_02005_gb300 import binding as B
+
+    g = o.Grid(32, 33, 32, 2 * math.pi, math.pi, stretch=2.0)
+    prm = o.Params(Re=400.0, lam=0.05, Sc=1.0, V=2.0, beta=0.5)
+    st0 = o.initial_state(g, prm, o.IC_PB, seed=1701, amp=1e-2)
+    s = _mixed(g, prm)
+    s.set_policy(B.PNP_POLICY_FP64_SOLVES)
+    s.set_state(st0)
+    nsteps, dt = 100, 0.01
+    s.step(nsteps, dt)
+    ref = o.step(g, prm, st0, dt, nsteps)
+    du = np.max(np.abs(s.mean_profile("u") - o.mean_profile(ref.u)))
+    d, dr, d0 = s.diagnostics(), o.diagnostics(g, prm, ref), o.diagnostics(g, prm, st0)
+    tau_err = max(abs(d["tau_bot"] - dr["tau_bot"]) / abs(dr["tau_bot"]),
+                  abs(d["tau_top"] - dr["tau_top"]) / abs(dr["tau_top"]))
+    field_errs = {n: _rel(s.get(n), getattr(ref, n)) for n in ("u", "v", "w", "cp", "cm", "Phi")}
+    print("mixed (FP64 solves) C1: <u> err", du, "tau err", tau_err, "fields", field_errs)
+    assert du <= 1e-4 and tau_err <= 1e-4, (du, tau_err)
+    assert field_errs["cp"] <= 1e-5 and field_errs["cm"] <= 1e-5 and field_errs["Phi"] <= 1e-5, field_errs
+    assert abs(d["n_plus"] - d0["n_plus"]) <= 1e-10 * d0["n_plus"]
+    assert d["status"] == 0
+    # switching back to the default policy keeps the state and steps on
+    s.set_policy(B.PNP_POLICY_DEFAULT)
+    s.step(2, dt)
+    assert s.diagnostics()["status"] == 0
+    s.close()
+
+
+def test_fp64_solves_policy_needs_a_mixed_context():
+    from paper_1701_02005_gb300 import binding as B
+    from paper_1701_02005_gb300.solver import Solver
+
+    s = Solver(8, 9, 4, 1.0, 1.0, precision=B.PNP_FP64)
+    assert B.pnp_set_policy(s.ctx, B.PNP_POLICY_FP64_SOLVES) == B.PNP_ERR_UNSUPPORTED
+    assert B.pnp_set_policy(s.ctx, 7) == B.PNP_ERR_ARG
+    assert B.pnp_set_policy(s.ctx, B.PNP_POLICY_DEFAULT) == B.PNP_OK
+    s.close()
