@@ -124,6 +124,9 @@ class Params:
     V: float = 0.0
     beta: float = 0.5
     Uw: float = 1.0
+    # optional wall potentials (Phi_bottom, Phi_top), each (nz, nx) values on the
+    # wall faces above / below the cell columns; None = the uniform -V, +V
+    wall: tuple | None = None
 
     @property
     def nu(self):            # momentum diffusivity 1/Re
@@ -435,10 +438,24 @@ def explicit_terms(g, prm, st):
     return Hu, Hv, Hw, Hcp, Hcm
 
 
+def wall_lift(g, prm):
+    """Phi_0: the wall potentials carried into the gap linearly in y,
+    Phi_0 = (1 - y)/2 Phi_bottom(x, z) + (1 + y)/2 Phi_top(x, z); V y for the
+    uniform walls (-V, +V).  The finite-volume y-operator with the wall value
+    on the wall face is exact on it, so only its x/z curvature is left."""
+    if prm.wall is None:
+        return np.broadcast_to(prm.V * _col(g.yc), (g.nyc, g.nz, g.nx)).copy()
+    Pb, Pt = (np.asarray(a, dtype=np.float64).reshape(g.nz, g.nx) for a in prm.wall)
+    return _col(0.5 * (1.0 - g.yc)) * Pb[None] + _col(0.5 * (1.0 + g.yc)) * Pt[None]
+
+
 def potential_from_ions(g, prm, cp, cm):
-    """Eq. (4): L phi = -(c+ - c-) / (2 lam^2), phi = 0 on walls; Phi = V y + phi."""
-    phi = poisson_solve(g, -(cp - cm) * prm.q, DIRICHLET)
-    return prm.V * _col(g.yc) + phi
+    """Eq. (4): L Phi = -(c+ - c-) / (2 lam^2) with Phi given on the walls (the
+    paper's walls carry any potential): Phi = Phi_0 + phi, phi = 0 on the walls,
+    L phi = -(c+ - c-) / (2 lam^2) - (delta_xx + delta_zz) Phi_0."""
+    Phi0 = wall_lift(g, prm)
+    phi = poisson_solve(g, -(cp - cm) * prm.q - lap_xz(g, Phi0), DIRICHLET)
+    return Phi0 + phi
 
 
 def project(g, u, v, w, scale):
