@@ -149,6 +149,20 @@ int pnp_set_yfaces(pnp_ctx* ctx, const double* y_faces_host, int ny);
 int pnp_set_params(pnp_ctx* ctx, double Re, double debye_len, double Sc,
                    double wall_potential, double beta);
 
+/* Wall potentials that vary along the walls (the paper's walls may carry any
+ * potential; Eq. (4) with Dirichlet data): bottom, top = Nz*Nx host values
+ * ([z][x], one per wall face below / above a cell column), in units of V_T.
+ * Phi = Phi_0 + phi with Phi_0 = (1 - y)/2 bottom + (1 + y)/2 top the linear
+ * lift (on which the finite-volume y-operator is exact) and phi = 0 on the
+ * walls solving L phi = -(c+ - c-) / (2 lam^2) - (d_xx + d_zz) Phi_0.  The
+ * context solves the charge-free part of the wall variations once here (one
+ * FP64 Dirichlet solve) and adds it in every potential solve; the plane means
+ * act as the uniform walls (V = (mean top - mean bottom) / 2 plus a constant).
+ * If a state is loaded its potential is re-solved under the new walls at once.
+ * Call again between steps for a time-varying potential; both NULL restore the
+ * uniform walls of pnp_set_params (which also resets them).  Synchronises. */
+int pnp_set_wall_potential(pnp_ctx* ctx, const double* bottom_host, const double* top_host);
+
 /* Wall speed in units of U (default 1; 0 gives the quiescent validation run). */
 int pnp_set_wall_velocity(pnp_ctx* ctx, double Uw);
 
@@ -212,6 +226,20 @@ int pnp_set_policy(pnp_ctx* ctx, int policy);
  * concentration below zero).  Both are reported by pnp_diagnostics / pnp_status
  * after NaN/Inf and negative-concentration checks; the step is not stopped. */
 int pnp_set_limits(pnp_ctx* ctx, double cfl_max, double dphi_max);
+
+/* Time statistics (Results: the mean profiles in wall units, the RMS ion and
+ * potential fluctuations, the friction coefficient c_f): pnp_stats_sample adds
+ * the plane means of q and q^2 of the current state for q = u, v, w, c+, c-,
+ * Phi to FP64 accumulators (asynchronous; call it every few steps);
+ * pnp_stats_get returns, per y-plane, the time-and-plane mean <q>(y) and the
+ * RMS fluctuation sqrt(<q^2> - <q>^2) in mean_out / rms_out (host, 6 x Ny
+ * values: [u, v, w, c+, c-, Phi][Ny], cell quantities in the first Ny-1, v on
+ * all Ny faces), the time-averaged c_f = (tau_bot + tau_top) / Uw^2 of the
+ * mean profile, and the number of samples (synchronises).  pnp_stats_reset
+ * zeroes them. */
+int pnp_stats_reset(pnp_ctx* ctx);
+int pnp_stats_sample(pnp_ctx* ctx);
+int pnp_stats_get(pnp_ctx* ctx, double* mean_out, double* rms_out, double* cf_mean, long long* nsamples);
 
 /* Plane average <q>(y) of a field into host memory (Ny-1 values, Ny for v). */
 int pnp_mean_profile(pnp_ctx* ctx, int field, double* out_host);

@@ -378,6 +378,66 @@ cudaError_t launch_mean_profile(const TQ* q, int nplanes, int plane_size, double
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Statistics: plane means of q and q^2 for u, v, w, c+, c-, Phi of the current
+// state, added to the accumulators acc[(2 q + 0 | 1) ny + j] (one block per
+// plane, fixed reduction order).  The mixed path reads the FP32 velocities,
+// the double-float ion state c = c_ref + S + L and Phi = Phi_ref + phi'; every
+// per-cell value is formed and squared in FP64.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_stats_sample(StatSrc src, Geo g, double* __restrict__ acc) {
+  __shared__ double sh[12 * 256];
+  const int j = blockIdx.x;
+  const size_t P = (size_t)g.nz * g.nx;
+  double a[12];
+#pragma unroll
+  for (int q = 0; q < 12; ++q) a[q] = 0.0;
+  auto vel = [&](const void* p, size_t c) {
+    return src.vel_f32 ? (double)static_cast<const float*>(p)[c] : static_cast<const double*>(p)[c];
+  };
+  for (size_t r = threadIdx.x; r < P; r += blockDim.x) {
+    const size_t c = (size_t)j * P + r;
+    const double v = vel(src.v, c);
+    a[2] += v;
+    a[3] += v * v;
+    if (j < g.nyc) {
+      const double u = vel(src.u, c), w = vel(src.w, c);
+      double cp, cm, ph;
+      if (src.mixed) {
+        cp = src.cref_p[j] + ((double)src.cpS[c] + (double)src.cpL[c]);
+        cm = src.cref_m[j] + ((double)src.cmS[c] + (double)src.cmL[c]);
+        ph = src.phi_ref[j] + (double)src.phiS[c];
+      } else {
+        cp = src.cp[c];
+        cm = src.cm[c];
+        ph = src.Phi[c];
+      }
+      a[0] += u; a[1] += u * u;
+      a[4] += w; a[5] += w * w;
+      a[6] += cp; a[7] += cp * cp;
+      a[8] += cm; a[9] += cm * cm;
+      a[10] += ph; a[11] += ph * ph;
+    }
+  }
+  for (int q = 0; q < 12; ++q) sh[q * 256 + threadIdx.x] = a[q];
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int q = 0; q < 12; ++q) sh[q * 256 + threadIdx.x] += sh[q * 256 + threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x < 12) {
+    const int q = threadIdx.x;   // slot order u, u2, v, v2, w, w2, c+, c+2, c-, c-2, Phi, Phi2
+    const bool cell = q < 2 || q >= 4;
+    if (!cell || j < g.nyc) acc[(size_t)q * g.ny + j] += sh[q * 256] / (double)P;
+  }
+}
+
+cudaError_t launch_stats_sample(const StatSrc& src, const Geo& g, double* acc, cudaStream_t s) {
+  k_stats_sample<<<g.ny, 256, 0, s>>>(src, g, acc);
+  return cudaGetLastError();
+}
+
 // FP64 FMA throughput probe: 8 independent dependency chains per thread.
 __global__ void k_fp64_probe(double* out, int iters) {
   double x0 = threadIdx.x * 1e-3, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
@@ -399,6 +459,55 @@ template cudaError_t launch_init_fields<double>(const Fields<double>&, const Geo
                                                 double, double, uint64_t, double, const double*, cudaStream_t);
 template cudaError_t launch_init_fields<float>(const Fields<float>&, const Geo&, const Metrics&, const Phys&, int,
                                                double, double, uint64_t, double, const double*, cudaStream_t);
+// ---------------------------------------------------------------------------
+// Wall potentials that vary along the walls (the walls may carry any
+// potential): Phi = V y + off + lift + phi, lift = Phi_0' + psi with psi the
+// homogeneous-Dirichlet solution of L psi = -(d_xx + d_zz) Phi_0'.
+// ---------------------------------------------------------------------------
+__global__ void k_wall_lift_source(double* __restrict__ src, const double* __restrict__ B,
+                                   const double* __restrict__ T, const double* __restrict__ yc, Geo g) {
+  const size_t P = (size_t)g.nz * g.nx, n = (size_t)g.nyc * P;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(c / P);
+    const int r = (int)(c - (size_t)j * P), k = r / g.nx, i = r - k * g.nx;
+    const int ip = i + 1 == g.nx ? 0 : i + 1, im = i == 0 ? g.nx - 1 : i - 1;
+    const int kp = k + 1 == g.nz ? 0 : k + 1, km = k == 0 ? g.nz - 1 : k - 1;
+    auto lap = [&](const double* q) {
+      const double q0 = q[r];
+      return (q[k * g.nx + ip] - 2.0 * q0 + q[k * g.nx + im]) * g.idx * g.idx +
+             (q[kp * g.nx + i] - 2.0 * q0 + q[km * g.nx + i]) * g.idz * g.idz;
+    };
+    src[c] = -(0.5 * (1.0 - yc[j]) * lap(B) + 0.5 * (1.0 + yc[j]) * lap(T));
+  }
+}
+
+__global__ void k_wall_lift_finish(double* __restrict__ lift64, float* __restrict__ lift32,
+                                   const double* __restrict__ B, const double* __restrict__ T, double Bm, double Tm,
+                                   double off, const double* __restrict__ yc, Geo g) {
+  const size_t P = (size_t)g.nz * g.nx, n = (size_t)g.nyc * P;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(c / P);
+    const size_t r = c - (size_t)j * P;
+    const double v = lift64[c] + 0.5 * (1.0 - yc[j]) * (B[r] - Bm) + 0.5 * (1.0 + yc[j]) * (T[r] - Tm);
+    lift32[c] = (float)v;
+    lift64[c] = v + off;
+  }
+}
+
+cudaError_t launch_wall_lift_source(double* src, const double* B, const double* T, double Bm, double Tm,
+                                    const double* yc, const Geo& g, cudaStream_t s) {
+  (void)Bm;
+  (void)Tm;   // the x/z second differences of a constant vanish
+  k_wall_lift_source<<<1216, 256, 0, s>>>(src, B, T, yc, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wall_lift_finish(double* lift64, float* lift32, const double* B, const double* T, double Bm,
+                                    double Tm, double off, const double* yc, const Geo& g, cudaStream_t s) {
+  k_wall_lift_finish<<<1216, 256, 0, s>>>(lift64, lift32, B, T, Bm, Tm, off, yc, g);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_diagnostics<double>(const Fields<double>&, const Geo&, const Metrics&, const Phys&,
                                                 double*, int, double*, int*, const DiagLimits&, cudaStream_t);
 template cudaError_t launch_diagnostics<float>(const Fields<float>&, const Geo&, const Metrics&, const Phys&,

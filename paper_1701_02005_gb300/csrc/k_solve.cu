@@ -343,7 +343,8 @@ template <int NH, int R1, typename TO>
 __global__ void __launch_bounds__(256) k_fft_x_inv_reg(PoissonDst dst, const cplx<float>* __restrict__ spec, Geo g,
                                                        Metrics mt, const cplx<float>* __restrict__ tw_half,
                                                        const cplx<float>* __restrict__ tw_post, double V,
-                                                       TO* __restrict__ out, const double* __restrict__ plane_add) {
+                                                       TO* __restrict__ out, const double* __restrict__ plane_add,
+                                                       const TO* __restrict__ cell_add) {
   constexpr int G = NH / R1, PER = R1 / G;
   static_assert(R1 % G == 0 && 32 % G == 0, "row of whole transforms inside one warp");
   extern __shared__ __align__(16) float fx_smem[];
@@ -401,11 +402,15 @@ __global__ void __launch_bounds__(256) k_fft_x_inv_reg(PoissonDst dst, const cpl
       const cplx<float> z = w[rfft::bitrev(k2, G)];
       const size_t o = base + 2 * (size_t)(k1 + R1 * k2);
       if (dst == PoissonDst::PotentialShadow) {
-        out[o] = (TO)(addT + z.x);
-        out[o + 1] = (TO)(addT + z.y);
+        TO a0 = (TO)(addT + z.x), a1 = (TO)(addT + z.y);
+        if (cell_add) { a0 += cell_add[o]; a1 += cell_add[o + 1]; }
+        out[o] = a0;
+        out[o + 1] = a1;
       } else if (dst == PoissonDst::Potential) {
-        out[o] = (TO)(add + (double)z.x);
-        out[o + 1] = (TO)(add + (double)z.y);
+        TO a0 = (TO)(add + (double)z.x), a1 = (TO)(add + (double)z.y);
+        if (cell_add) { a0 += cell_add[o]; a1 += cell_add[o + 1]; }
+        out[o] = a0;
+        out[o + 1] = a1;
       } else {
         out[o] = (TO)z.x;
         out[o + 1] = (TO)z.y;
@@ -480,7 +485,8 @@ cudaError_t launch_fft_x_fwd(PoissonSrc kind, const TV* u, const TV* v, const TV
 template <typename T, typename TO>
 __global__ void k_fft_x_inv(PoissonDst dst, const cplx<T>* __restrict__ spec, Geo g, Metrics m,
                             const cplx<T>* __restrict__ tw_half, const cplx<T>* __restrict__ tw_post,
-                            double V, TO* __restrict__ out, const double* __restrict__ plane_add) {
+                            double V, TO* __restrict__ out, const double* __restrict__ plane_add,
+                            const TO* __restrict__ cell_add) {
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
   const int Lh = g.nx >> 1;
@@ -512,11 +518,15 @@ __global__ void k_fft_x_inv(PoissonDst dst, const cplx<T>* __restrict__ spec, Ge
   for (int t = threadIdx.x; t < Lh; t += blockDim.x) {
     const cplx<T> z = Z[t];
     if (dst == PoissonDst::PotentialShadow) {
-      out[base + 2 * t] = (TO)(addT + z.x);
-      out[base + 2 * t + 1] = (TO)(addT + z.y);
+      TO a0 = (TO)(addT + z.x), a1 = (TO)(addT + z.y);
+      if (cell_add) { a0 += cell_add[base + 2 * t]; a1 += cell_add[base + 2 * t + 1]; }
+      out[base + 2 * t] = a0;
+      out[base + 2 * t + 1] = a1;
     } else if (dst == PoissonDst::Potential) {
-      out[base + 2 * t] = (TO)(add + (double)z.x);
-      out[base + 2 * t + 1] = (TO)(add + (double)z.y);
+      TO a0 = (TO)(add + (double)z.x), a1 = (TO)(add + (double)z.y);
+      if (cell_add) { a0 += cell_add[base + 2 * t]; a1 += cell_add[base + 2 * t + 1]; }
+      out[base + 2 * t] = a0;
+      out[base + 2 * t + 1] = a1;
     } else {
       out[base + 2 * t] = (TO)z.x;
       out[base + 2 * t + 1] = (TO)z.y;
@@ -527,7 +537,7 @@ __global__ void k_fft_x_inv(PoissonDst dst, const cplx<T>* __restrict__ spec, Ge
 template <typename T, typename TO>
 cudaError_t launch_fft_x_inv(PoissonDst dst, const cplx<T>* spec, const Geo& g, const Metrics& m,
                              const cplx<T>* tw_half, const cplx<T>* tw_post, double V, TO* out,
-                             cudaStream_t s, const double* plane_add) {
+                             cudaStream_t s, const double* plane_add, const TO* cell_add) {
   if constexpr (sizeof(T) == sizeof(float)) {
     auto go = [&](auto kern, int G, int rows, size_t smem) {
       if (smem > 48 * 1024) {
@@ -535,7 +545,8 @@ cudaError_t launch_fft_x_inv(PoissonDst dst, const cplx<T>* spec, const Geo& g, 
         if (e != cudaSuccess) return e;
       }
       const int nrows = g.nyc * g.nz;
-      kern<<<(nrows + rows - 1) / rows, dim3(G, rows), smem, s>>>(dst, spec, g, m, tw_half, tw_post, V, out, plane_add);
+      kern<<<(nrows + rows - 1) / rows, dim3(G, rows), smem, s>>>(dst, spec, g, m, tw_half, tw_post, V, out, plane_add,
+                                                                  cell_add);
       return cudaGetLastError();
     };
     switch (g.nx / 2) {
@@ -555,7 +566,7 @@ cudaError_t launch_fft_x_inv(PoissonDst dst, const cplx<T>* spec, const Geo& g, 
     cudaError_t e = cudaFuncSetAttribute(k_fft_x_inv<T, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_fft_x_inv<T, TO><<<grd, blk, smem, s>>>(dst, spec, g, m, tw_half, tw_post, V, out, plane_add);
+  k_fft_x_inv<T, TO><<<grd, blk, smem, s>>>(dst, spec, g, m, tw_half, tw_post, V, out, plane_add, cell_add);
   return cudaGetLastError();
 }
 
@@ -1354,13 +1365,13 @@ template cudaError_t launch_spec_thomas<float>(cplx<float>*, cplx<double>*, cons
 
 template cudaError_t launch_fft_x_inv<double, double>(PoissonDst, const cplx<double>*, const Geo&, const Metrics&,
                                                       const cplx<double>*, const cplx<double>*, double, double*,
-                                                      cudaStream_t, const double*);
+                                                      cudaStream_t, const double*, const double*);
 template cudaError_t launch_fft_x_inv<float, float>(PoissonDst, const cplx<float>*, const Geo&, const Metrics&,
                                                     const cplx<float>*, const cplx<float>*, double, float*,
-                                                    cudaStream_t, const double*);
+                                                    cudaStream_t, const double*, const float*);
 template cudaError_t launch_fft_x_inv<double, float>(PoissonDst, const cplx<double>*, const Geo&, const Metrics&,
                                                      const cplx<double>*, const cplx<double>*, double, float*,
-                                                     cudaStream_t, const double*);
+                                                     cudaStream_t, const double*, const float*);
 
 template cudaError_t launch_project<double>(double*, double*, double*, double*, const double*, double, bool,
                                             const Geo&, const double*, cudaStream_t);

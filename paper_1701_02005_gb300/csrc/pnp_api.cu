@@ -122,6 +122,14 @@ struct pnp_ctx {
   long long nstep = 0;
   double last_dt = 0.0;                         // size of the last step (0: none yet)
   int policy = PNP_POLICY_DEFAULT;              // mixed path: where the solves' FP64 accuracy comes from
+  // wall potentials that vary along the walls: Phi = V y + wall_off + lift + phi
+  bool wall_map = false;
+  double wall_off = 0.0, V_set = 0.0;           // mean offset; the uniform V of pnp_set_params
+  double *wallB_d = nullptr, *wallT_d = nullptr, *lift64 = nullptr;
+  float* lift32 = nullptr;
+  // time statistics: plane means of q and q^2 summed over samples ([12][ny])
+  double* stats_acc = nullptr;
+  long long stats_n = 0;
   double cfl_max = 1.7320508075688772, dphi_max = 2.0;   // limits of the device checks
   double refH_p = 0.0, refH_m = 0.0;            // sum over cells of H_ref(j) dy_j (mixed)
   cudaGraphExec_t gexec = nullptr;
@@ -187,7 +195,13 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
   float2 *sfaN = b.take<float2>(mixed ? ny : 0), *sfaD = b.take<float2>(mixed ? ny : 0);
   float *cpL = b.take<float>(mixed ? nc : 0), *cmL = b.take<float>(mixed ? nc : 0);
   float2 *dCp2 = b.take<float2>(3 * (size_t)ny), *dCm2 = b.take<float2>(3 * (size_t)ny);
+  double *wB = b.take<double>((size_t)nz * nx), *wT = b.take<double>((size_t)nz * nx);
+  double* lift64 = b.take<double>(nc);
+  float* lift32 = b.take<float>(nc);
+  double* sacc = b.take<double>(12 * (size_t)ny);
   if (c) {
+    c->stats_acc = sacc;
+    c->wallB_d = wB; c->wallT_d = wT; c->lift64 = lift64; c->lift32 = lift32;
     c->dCp_f2 = dCp2; c->dCm_f2 = dCm2;
     c->spf_cprN = sfcN; c->spf_invN = sfiN; c->spf_cprD = sfcD; c->spf_invD = sfiD;
     c->spf_aN = sfaN; c->spf_aD = sfaD;
@@ -558,7 +572,8 @@ cudaError_t potential_solve(pnp_ctx* c, cudaStream_t st, void* spec_buf, cplx<do
   mark(c, st, PNP_SITE_E_FFTX);
   e = spectral_solve<double>(c, spec, twz, false, st, dscr);
   if (e != cudaSuccess) return e;
-  e = launch_fft_x_inv<double, double>(PoissonDst::Potential, spec, c->g, m, twx, twp, c->ph.V, c->Phi, st);
+  e = launch_fft_x_inv<double, double>(PoissonDst::Potential, spec, c->g, m, twx, twp, c->ph.V, c->Phi, st, nullptr,
+                                       c->wall_map ? c->lift64 : nullptr);
   mark(c, st, PNP_SITE_E_IFFTX);
   return e;
 }
@@ -591,7 +606,8 @@ cudaError_t potential_mixed(pnp_ctx* c, cudaStream_t st, void* spec_buf, cplx<do
   e = launch_fft_z<float>(spec, twz, c->g, true, st);
   if (e != cudaSuccess) return e;
   mark(c, st, PNP_SITE_E_IFFTZ);
-  e = launch_fft_x_inv<float, float>(PoissonDst::PotentialShadow, spec, c->g, m, twx, twp, 0.0, sh.phi, st, c->delta_d);
+  e = launch_fft_x_inv<float, float>(PoissonDst::PotentialShadow, spec, c->g, m, twx, twp, 0.0, sh.phi, st, c->delta_d,
+                                     c->wall_map ? c->lift32 : nullptr);
   mark(c, st, PNP_SITE_E_IFFTX);
   return e;
 }
@@ -646,7 +662,7 @@ cudaError_t potential_mixed_fp64(pnp_ctx* c, cudaStream_t st, void* spec_buf, cp
   if (e != cudaSuccess) return e;
   mark(c, st, PNP_SITE_E_IFFTZ);
   e = launch_fft_x_inv<double, float>(PoissonDst::PotentialShadow, spec, c->g, m, twx, twp, 0.0, sh.phi, st,
-                                      c->delta_d);
+                                      c->delta_d, c->wall_map ? c->lift32 : nullptr);
   mark(c, st, PNP_SITE_E_IFFTX);
   return e;
 }
@@ -800,7 +816,7 @@ int refresh_refs(pnp_ctx* c, double dt) {
       crefm[j] = (float)cm[j];
       rhoref[j] = (float)(cp[j] - cm[j]);
       mrhs[j] = -q * (cp[j] - cm[j]);
-      mshift[j] = V * c->yc[j] - Ph[j];
+      mshift[j] = V * c->yc[j] + (c->wall_map ? c->wall_off : 0.0) - Ph[j];
     }
     // reference migration flux on interior faces, its divergence, the implicit
     // diffusion of the reference and the reference Coulomb force on v (all FP64)
@@ -1006,6 +1022,9 @@ int pnp_set_params(pnp_ctx* c, double Re, double lam, double Sc, double V, doubl
   c->ph.q = 1.0 / (2.0 * lam * lam);
   c->ph.V = V;
   c->ph.Uw = Uw;
+  c->V_set = V;
+  c->wall_map = false;   // uniform walls -V, +V
+  c->wall_off = 0.0;
   c->have_params = true;
   c->cn_dt = NAN;
   drop_graph(c);
@@ -1164,6 +1183,112 @@ int pnp_step_adaptive(pnp_ctx* c, int nsteps, double dt_max, double cfl, int che
       for (int q = 0; q < n; ++q) dts_out[done + q] = dt;
     done += n;
   }
+  return PNP_OK;
+}
+
+int pnp_stats_reset(pnp_ctx* c) {
+  if (!c) return PNP_ERR_ARG;
+  CK(cudaMemsetAsync(c->stats_acc, 0, 12 * sizeof(double) * c->g.ny, c->stream));
+  c->stats_n = 0;
+  return PNP_OK;
+}
+
+int pnp_stats_sample(pnp_ctx* c) {
+  if (!c) return PNP_ERR_ARG;
+  if (!c->have_params || !c->have_state) return PNP_ERR_STATE;
+  const bool shadows_now = c->precision == PNP_MIXED && c->refs_valid && !c->fp64_fresh;
+  if (!shadows_now) {
+    int r = materialize(c);
+    if (r) return r;
+  }
+  StatSrc src{};
+  src.u = c->u; src.v = c->v; src.w = c->w;
+  src.vel_f32 = c->precision == PNP_MIXED;
+  src.mixed = shadows_now;
+  src.cp = c->cp; src.cm = c->cm; src.Phi = c->Phi;
+  src.cpS = c->cpS; src.cpL = c->cpL; src.cmS = c->cmS; src.cmL = c->cmL; src.phiS = c->phiS;
+  src.cref_p = c->cref64p_d; src.cref_m = c->cref64m_d; src.phi_ref = c->Phiref64_d;
+  CK(launch_stats_sample(src, c->g, c->stats_acc, c->stream));
+  ++c->stats_n;
+  return PNP_OK;
+}
+
+int pnp_stats_get(pnp_ctx* c, double* mean_out, double* rms_out, double* cf_mean, long long* nsamples) {
+  if (!c || !mean_out || !rms_out) return PNP_ERR_ARG;
+  const int ny = c->g.ny, nyc = c->g.nyc;
+  std::vector<double> a(12 * (size_t)ny);
+  CK(cudaMemcpyAsync(a.data(), c->stats_acc, sizeof(double) * a.size(), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const double n = c->stats_n > 0 ? (double)c->stats_n : 1.0;
+  for (int q = 0; q < 6; ++q) {
+    const int planes = q == 1 ? ny : nyc;   // v on the faces
+    for (int j = 0; j < ny; ++j) {
+      double m = 0.0, r = 0.0;
+      if (j < planes && c->stats_n > 0) {
+        m = a[(size_t)(2 * q) * ny + j] / n;
+        const double m2 = a[(size_t)(2 * q + 1) * ny + j] / n;
+        r = std::sqrt(std::max(m2 - m * m, 0.0));
+      }
+      mean_out[(size_t)q * ny + j] = m;
+      rms_out[(size_t)q * ny + j] = r;
+    }
+  }
+  if (cf_mean) {
+    const double Uw = c->ph.Uw;
+    const double tb = c->ph.nu * (mean_out[0] + Uw) / c->h[0];
+    const double tt = c->ph.nu * (Uw - mean_out[nyc - 1]) / c->h[nyc];
+    *cf_mean = (c->stats_n > 0 && Uw != 0.0) ? (tb + tt) / (Uw * Uw) : 0.0;
+  }
+  if (nsamples) *nsamples = c->stats_n;
+  return PNP_OK;
+}
+
+int pnp_set_wall_potential(pnp_ctx* c, const double* bottom, const double* top) {
+  if (!c) return PNP_ERR_ARG;
+  if (!c->have_params) return PNP_ERR_STATE;
+  if ((bottom == nullptr) != (top == nullptr)) return PNP_ERR_ARG;
+  const size_t P = (size_t)c->g.nz * c->g.nx;
+  if (!bottom) {
+    c->wall_map = false;
+    c->wall_off = 0.0;
+    c->ph.V = c->V_set;
+  } else {
+    double sb = 0.0, st = 0.0;
+    for (size_t q = 0; q < P; ++q) {
+      if (!std::isfinite(bottom[q]) || !std::isfinite(top[q])) return PNP_ERR_ARG;
+      sb += bottom[q];
+      st += top[q];
+    }
+    const double Bm = sb / (double)P, Tm = st / (double)P;
+    CK(cudaMemcpyAsync(c->wallB_d, bottom, sizeof(double) * P, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->wallT_d, top, sizeof(double) * P, cudaMemcpyHostToDevice, c->stream));
+    // lift = Phi_0' + psi: the charge-free potential of the zero-mean wall
+    // variations, one FP64 Dirichlet solve (the scratch of the pressure pipeline)
+    const Metrics m = metrics(c);
+    cplx<double>* spec = (cplx<double>*)c->spec;
+    const cplx<double>* twx = (const cplx<double>*)c->twx_d;
+    const cplx<double>* twp = (const cplx<double>*)c->twp_d;
+    const cplx<double>* twz = (const cplx<double>*)c->twz_d;
+    CK(launch_wall_lift_source(c->sreal, c->wallB_d, c->wallT_d, Bm, Tm, c->yc_d, c->g, c->stream));
+    CK(launch_fft_x_fwd<double, double>(PoissonSrc::Plain, nullptr, nullptr, nullptr, nullptr, nullptr, c->sreal, 1.0,
+                                        c->g, m, spec, twx, twp, c->stream));
+    CK(spectral_solve<double>(c, spec, twz, false));
+    CK(launch_fft_x_inv<double, double>(PoissonDst::Plain, spec, c->g, m, twx, twp, 0.0, c->lift64, c->stream));
+    const double off = 0.5 * (Tm + Bm);
+    CK(launch_wall_lift_finish(c->lift64, c->lift32, c->wallB_d, c->wallT_d, Bm, Tm, off, c->yc_d, c->g, c->stream));
+    c->wall_map = true;
+    c->wall_off = off;
+    c->ph.V = 0.5 * (Tm - Bm);
+  }
+  drop_graph(c);
+  if (c->have_state) {   // the potential of the current ions under the new walls
+    int r = materialize(c);
+    if (r) return r;
+    const cudaError_t e = c->precision == PNP_FP64 ? potential_solve<double>(c) : potential_solve<float>(c);
+    if (e != cudaSuccess) return PNP_ERR_CUDA;
+    c->refs_valid = false;
+  }
+  CK(cudaStreamSynchronize(c->stream));
   return PNP_OK;
 }
 

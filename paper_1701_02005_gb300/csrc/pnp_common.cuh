@@ -141,10 +141,22 @@ cudaError_t launch_spec_thomas(cplx<T>* spec, cplx<double>* dscr, const double* 
                                const double* mean_rhs = nullptr, const double* mean_shift = nullptr,
                                double* mean_out = nullptr);
 
+// Potential / PotentialShadow: out = V yc_j (Potential) or plane_add[j]
+// (PotentialShadow) + the transform + cell_add[c] (optional, per cell).
 template <typename T, typename TO>
 cudaError_t launch_fft_x_inv(PoissonDst dst, const cplx<T>* spec, const Geo& g, const Metrics& m,
                              const cplx<T>* tw_half, const cplx<T>* tw_post, double V, TO* out,
-                             cudaStream_t s, const double* plane_add = nullptr);
+                             cudaStream_t s, const double* plane_add = nullptr, const TO* cell_add = nullptr);
+
+// Wall potentials that vary along the walls: the source -(d_xx + d_zz) Phi_0'
+// of the zero-mean part of the linear lift Phi_0' = (1 - y)/2 (B - Bm) +
+// (1 + y)/2 (T - Tm) (B, T the [nz][nx] wall values, Bm, Tm their means),
+// and, after the Dirichlet solve, lift64 += Phi_0' + off and lift32 = the
+// FP32 value without off.
+cudaError_t launch_wall_lift_source(double* src, const double* B, const double* T, double Bm, double Tm,
+                                    const double* yc, const Geo& g, cudaStream_t s);
+cudaError_t launch_wall_lift_finish(double* lift64, float* lift32, const double* B, const double* T, double Bm,
+                                    double Tm, double off, const double* yc, const Geo& g, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_project(T* u, T* v, T* w, T* p, const T* phip, double scale, bool update_p, const Geo& g,

@@ -84,6 +84,17 @@ constexpr unsigned kCnIons = 1, kCnVelocity = 2;
 cudaError_t launch_mixed_cn(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
                             const CNRowsF& cell, const CNRowsF& face, const CNRowsF& ion, int l, unsigned parts,
                             cudaStream_t s);
+// Sources of a statistics sample (FP64 path: the FP64 arrays; mixed: FP32
+// velocities, the double-float ion state and phi' about the FP64 references).
+struct StatSrc {
+  const void *u, *v, *w;
+  bool vel_f32, mixed;
+  const double *cp, *cm, *Phi;
+  const float *cpS, *cpL, *cmS, *cmL, *phiS;
+  const double *cref_p, *cref_m, *phi_ref;
+};
+cudaError_t launch_stats_sample(const StatSrc& src, const Geo& g, double* acc, cudaStream_t s);
+
 // FP64 scratch of the FP64-arithmetic CN solves: forward values per line
 // (du, dw, dcp, dcm: nyc planes; dv: ny planes).
 struct CnScratch64 {

@@ -113,6 +113,40 @@ class Solver:
             B.check(code, "pnp_diagnostics")
         return d.as_dict()
 
+    def set_wall_potential(self, bottom=None, top=None):
+        """Wall potentials along the walls ([nz][nx] arrays, units of V_T); None restores the uniform walls."""
+        if bottom is None and top is None:
+            B.check(B.pnp_set_wall_potential(self.ctx, None, None), "pnp_set_wall_potential")
+            return
+        b = np.ascontiguousarray(bottom, dtype=np.float64).reshape(self.nz, self.nx)
+        t = np.ascontiguousarray(top, dtype=np.float64).reshape(self.nz, self.nx)
+        B.check(B.pnp_set_wall_potential(self.ctx, b.ctypes.data_as(C.POINTER(C.c_double)),
+                                         t.ctypes.data_as(C.POINTER(C.c_double))), "pnp_set_wall_potential")
+
+    # -- time statistics --
+    STAT_FIELDS = ("u", "v", "w", "cp", "cm", "Phi")
+
+    def stats_reset(self):
+        B.check(B.pnp_stats_reset(self.ctx), "pnp_stats_reset")
+
+    def stats_sample(self):
+        B.check(B.pnp_stats_sample(self.ctx), "pnp_stats_sample")
+
+    def stats(self):
+        """Time-and-plane means and RMS fluctuations per field (arrays over y),
+        the time-averaged c_f and the number of samples."""
+        mean = np.zeros((6, self.ny))
+        rms = np.zeros((6, self.ny))
+        cf = C.c_double()
+        n = C.c_longlong()
+        B.check(B.pnp_stats_get(self.ctx, mean.ctypes.data_as(C.POINTER(C.c_double)),
+                                rms.ctypes.data_as(C.POINTER(C.c_double)), C.byref(cf), C.byref(n)), "pnp_stats_get")
+        out = {}
+        for q, name in enumerate(self.STAT_FIELDS):
+            k = self.ny if name == "v" else self.nyc
+            out[name] = (mean[q, :k].copy(), rms[q, :k].copy())
+        return out, cf.value, n.value
+
     def set_policy(self, policy):
         """Solve precision of a mixed context: binding.PNP_POLICY_DEFAULT or PNP_POLICY_FP64_SOLVES."""
         B.check(B.pnp_set_policy(self.ctx, int(policy)), "pnp_set_policy")
