@@ -488,6 +488,84 @@ def compare_precisions(B, Solver, torch, wl, V, dt, nsteps, every, launch_cfg=No
     return out
 
 
+def run_sweep(args):
+    """A reduced version of the paper's drag-vs-voltage experiment (Results):
+    plane Couette at Re 3000 on 64 x 65 x 64 (box 2 pi x 2 x pi), Debye length
+    0.0158, Sc 1, wall potentials V = 0, 0.5, 1, 1.5, 2 (V-hat = 2 V) from one
+    seeded perturbed state, all cases in one ensemble (one graph launch per
+    step, a common dt); time statistics after a spin-up.  Context only: the
+    grid is coarse and the averaging window short."""
+    import numpy as np
+    import torch
+
+    from paper_1701_02005_gb300 import binding as B
+    from paper_1701_02005_gb300.ensemble import Ensemble
+    from paper_1701_02005_gb300.solver import Solver
+
+    nx, ny, nz, Re, lam = 64, 65, 64, 3000.0, 0.0158
+    Vs = (0.0, 0.5, 1.0, 1.5, 2.0)
+    cases = []
+    for V in Vs:
+        chosen = 6.0
+        for gm in (1.5, 2.0, 2.5, 3.0, 3.5, 4.0, 4.5, 5.0, 5.5, 6.0):
+            if stable_dt(nx, ny, Re, lam, V, gm)[1] <= 1.0:
+                chosen = gm
+                break
+        cases.append((V, chosen))
+    stretch = max(g for _, g in cases)   # one grid for all: the finest wall cell any case needs
+    dt = min(stable_dt(nx, ny, Re, lam, V, stretch)[0] for V in Vs)
+    solvers = []
+    for V, _ in cases:
+        s = Solver(nx, ny, nz, 2 * math.pi, math.pi, stretch=stretch, precision=B.PNP_MIXED)
+        s.set_params(Re, lam, 1.0, V, 0.5)
+        s.init_state(B.PNP_IC_PB, 1706, args.sweep_amp)
+        solvers.append(s)
+    ens = Ensemble(solvers)
+    spin, avg, every = args.sweep_spinup, args.sweep_steps, 10
+    t0 = time.perf_counter()
+    ens.step(spin, [dt] * len(solvers))
+    ens.synchronize()
+    for s in solvers:
+        s.stats_reset()
+    cf_hist = [[] for _ in solvers]
+    for _ in range(avg // every):
+        ens.step(every, [dt] * len(solvers))
+        ens.synchronize()
+        for i, s in enumerate(solvers):
+            s.stats_sample()
+            cf_hist[i].append(s.diagnostics()["cf"])
+    wall = time.perf_counter() - t0
+    out = {"workload": f"{nx}x{ny}x{nz}, Re {Re:g}, lambda_D/h {lam}, Sc 1, tanh stretching {stretch}, dt {dt:.4g}, "
+                       f"{spin} spin-up + {avg} averaged steps, noise {args.sweep_amp}, seed 1706",
+           "wall_seconds": wall, "cases": []}
+    cf0 = None
+    for (V, _), s, hist in zip(cases, solvers, cf_hist):
+        st, cf, n = s.stats()
+        d = s.diagnostics()
+        um = st["u"][0]
+        tau = 0.5 * cf
+        ut = math.sqrt(max(tau, 0.0))
+        g = s   # plane data in wall units near the bottom wall
+        yf = np.tanh(stretch * (np.arange(ny) * 2.0 / (ny - 1) - 1.0)) / math.tanh(stretch)
+        yc = 0.5 * (yf[1:] + yf[:-1])
+        yplus = (yc + 1.0) * Re * ut
+        uplus = (um + 1.0) / ut if ut > 0 else um * 0
+        if cf0 is None:
+            cf0 = cf
+        out["cases"].append({"V": V, "V_hat": 2 * V, "cf": cf, "cf_over_cf0": cf / cf0 if cf0 else None,
+                             "re_tau": Re * ut, "cf_laminar": 2.0 / Re, "samples": n, "status": d["status"],
+                             "cf_series_first_last": [hist[0], hist[-1]],
+                             "u_plus_at_y_plus": [[round(float(a), 3), round(float(b), 3)]
+                                                  for a, b in zip(yplus[:12:2], uplus[:12:2])],
+                             "rms_cplus_max": float(np.max(st["cp"][1])), "rms_cminus_max": float(np.max(st["cm"][1])),
+                             "rms_phi_max": float(np.max(st["Phi"][1]))})
+    ens.close()
+    for s in solvers:
+        s.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_curve(args):
     """Mixed (both solve policies) against FP64 on the workload at V = 0, 2, 5:
     <u>(y) and wall-shear errors every 100 steps up to --curve-steps or until
@@ -699,6 +777,10 @@ def main():
     ap.add_argument("--curve", action="store_true",
                     help="only the mixed-vs-FP64 error curves at V = 0, 2, 5 over --curve-steps steps")
     ap.add_argument("--curve-steps", type=int, default=2000)
+    ap.add_argument("--sweep", action="store_true", help="only the reduced drag-vs-voltage sweep (ensemble)")
+    ap.add_argument("--sweep-spinup", type=int, default=4000)
+    ap.add_argument("--sweep-steps", type=int, default=4000)
+    ap.add_argument("--sweep-amp", type=float, default=0.3)
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-e2e", action="store_true")
@@ -722,6 +804,8 @@ def main():
         return run_reference(args)
     if args.curve:
         return run_curve(args)
+    if args.sweep:
+        return run_sweep(args)
     return run_ours(args)
 
 

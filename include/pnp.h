@@ -208,6 +208,17 @@ int pnp_diagnostics(pnp_ctx* ctx, pnp_diag* out);
  * check reports one (PNP_ERR_NONFINITE, ...). */
 int pnp_step_adaptive(pnp_ctx* ctx, int nsteps, double dt_max, double cfl, int check_every, double* dts_out);
 
+/* PNP_MIXED with the default policy: fuse the forward elimination of the
+ * wall-normal CN solves into the explicit-term stencil (on != 0, the default).
+ * The stencil, which marches y in chunks, stores each chunk's forward-
+ * elimination values started from zero instead of the right-hand sides; the CN
+ * kernel recovers every line's true values from the chunk-end values and
+ * per-row products of the factors, then back-substitutes: the right-hand sides
+ * never make an HBM round trip.  Off: the right-hand sides are stored and the
+ * CN kernels eliminate both ways (the shared-memory CN tiles, launch code 32,
+ * always take that path). */
+int pnp_set_fusion(pnp_ctx* ctx, int on);
+
 /* Select the solve precision of a PNP_MIXED context (PNP_POLICY_*): the
  * stencils, storage and sums are the same under both; PNP_POLICY_FP64_SOLVES
  * runs the wall-normal CN solves of u, v, w and of the ion fluctuations, both

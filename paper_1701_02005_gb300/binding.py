@@ -79,6 +79,7 @@ EXPORTS = {
     "pnp_eval_explicit": (C.c_int, [C.c_void_p]),
     "pnp_set_limits": (C.c_int, [C.c_void_p, C.c_double, C.c_double]),
     "pnp_set_policy": (C.c_int, [C.c_void_p, C.c_int]),
+    "pnp_set_fusion": (C.c_int, [C.c_void_p, C.c_int]),
     "pnp_stats_reset": (C.c_int, [C.c_void_p]),
     "pnp_stats_sample": (C.c_int, [C.c_void_p]),
     "pnp_stats_get": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -178,6 +179,7 @@ pnp_poisson_noalloc = _fwd("pnp_poisson_noalloc")
 pnp_eval_explicit = _fwd("pnp_eval_explicit")
 pnp_set_limits = _fwd("pnp_set_limits")
 pnp_set_policy = _fwd("pnp_set_policy")
+pnp_set_fusion = _fwd("pnp_set_fusion")
 pnp_stats_reset = _fwd("pnp_stats_reset")
 pnp_stats_sample = _fwd("pnp_stats_sample")
 pnp_stats_get = _fwd("pnp_stats_get")

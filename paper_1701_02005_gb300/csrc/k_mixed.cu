@@ -443,6 +443,115 @@ cudaError_t launch_mixed_cn(const Fields<float>& f, const Shadows& sh, const Mix
 }
 
 // ---------------------------------------------------------------------------
+// Back substitution after the fused stencil (launch_mixed_rhs with CnFuse):
+// the stencil stored, per y-chunk of its march, d~_j = (r_j - a_j d~_{j-1}) m_j
+// started from zero at the chunk's first row, so the true forward value is
+// d_j = d~_j + G_j d_{s-1}, G_j = prod_{i=s..j} (-a_i m_i) over the chunk
+// (host table).  Per line: the chunk-end values d_{e-1} = d~_{e-1} + G_{e-1}
+// d_{s-1} chunk by chunk (a few strided loads), then x_j = d_j - c_j x_{j+1}
+// from the top, state += x (velocities; ions as the double-float update with
+// the reference increment).  Reads d~ and the state once, writes the state.
+// ---------------------------------------------------------------------------
+struct FusedFam {
+  const float* d;      // d~ at the family's first row
+  float* S;            // state (velocity) or the high part S of an ion fluctuation
+  float* L;            // low part L (ions), else nullptr
+  const float2* add;   // dC_ref per row (ions), else nullptr
+  const float* c;      // super-diagonal factor c per row
+  const float* G;      // chunk products per row
+  int n, j0;           // rows per line; plane of row 0
+};
+struct FusedArgs {
+  FusedFam f[5];       // u, v, w, c+, c-
+  int jc;
+  size_t P;
+};
+
+__global__ void k_cn_backsub_fused(FusedArgs A, int fam0) {
+  constexpr int CH = 8;
+  const FusedFam& F = A.f[fam0 + blockIdx.y];
+  const size_t P = A.P;
+  const size_t line = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (line >= P) return;
+  const int n = F.n, j0 = F.j0, jc = A.jc;
+  const float* d = F.d + line;
+  float* S = F.S + line;
+  float* L = F.L ? F.L + line : nullptr;
+  // chunk ch holds rows [max(ch jc - j0, 0), min((ch + 1) jc - j0, n))
+  const int nch = (n - 1 + j0) / jc + 1;
+  float dend[kFusedMaxChunks];
+  {
+    float dv[kFusedMaxChunks];
+#pragma unroll 8
+    for (int ch = 0; ch < nch; ++ch) dv[ch] = d[(size_t)(min((ch + 1) * jc - j0, n) - 1) * P];
+    float dp = 0.f;
+    for (int ch = 0; ch < nch; ++ch) {
+      dp = fmaf(F.G[min((ch + 1) * jc - j0, n) - 1], dp, dv[ch]);
+      dend[ch] = dp;
+    }
+  }
+  float x = 0.f;
+  int ch = nch - 1;
+  for (int jb = n - 1; jb >= 0; jb -= CH) {
+    float dd[CH], sh[CH], sl[CH];
+#pragma unroll
+    for (int k = 0; k < CH; ++k)
+      if (jb - k >= 0) {
+        const size_t o = (size_t)(jb - k) * P;
+        dd[k] = d[o];
+        sh[k] = S[o];
+        sl[k] = L ? L[o] : 0.f;
+      }
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+      const int r = jb - k;
+      if (r >= 0) {
+        while (ch > 0 && r + j0 < ch * jc) --ch;
+        const float dprev = ch > 0 ? dend[ch - 1] : 0.f;
+        x = fmaf(F.G[r], dprev, dd[k]) - F.c[r] * x;
+        const size_t o = (size_t)r * P;
+        if (L) {
+          const float2 inc = F.add[r];
+          const dfl cv = df_add2(dfl{sh[k], sl[k]}, dfl{inc.x, inc.y}, x);
+          S[o] = cv.h;
+          L[o] = cv.l;
+        } else {
+          S[o] = sh[k] + x;
+        }
+      }
+    }
+  }
+}
+
+cudaError_t launch_mixed_cn_fused(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
+                                  const CNRowsF& cell, const CNRowsF& face, const CNRowsF& ion, const CnFusedG& G,
+                                  int jc, int l, unsigned parts, cudaStream_t s) {
+  const size_t P = (size_t)g.nz * g.nx;
+  if ((g.nyc - 1) / jc + 1 > kFusedMaxChunks) return cudaErrorInvalidValue;
+  FusedArgs A{};
+  A.jc = jc;
+  A.P = P;
+  A.f[0] = FusedFam{f.ru, f.u, nullptr, nullptr, cell.c, G.cell, g.nyc, 0};
+  A.f[1] = FusedFam{f.rv + P, f.v + P, nullptr, nullptr, face.c, G.face, g.nyc - 1, 1};
+  A.f[2] = FusedFam{f.rw, f.w, nullptr, nullptr, cell.c, G.cell, g.nyc, 0};
+  A.f[3] = FusedFam{reinterpret_cast<const float*>(f.rcp), sh.cp, sh.cpL, R.dC_p + (size_t)l * g.nyc, ion.c, G.ion,
+                    g.nyc, 0};
+  A.f[4] = FusedFam{reinterpret_cast<const float*>(f.rcm), sh.cm, sh.cmL, R.dC_m + (size_t)l * g.nyc, ion.c, G.ion,
+                    g.nyc, 0};
+  const int T = g.lc_cn && g.lc_cn != 32 ? g.lc_cn : 128;
+  if (parts & kCnIons) {
+    k_cn_backsub_fused<<<dim3((unsigned)((P + T - 1) / T), 2, 1), T, 0, s>>>(A, 3);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (parts & kCnVelocity) {
+    k_cn_backsub_fused<<<dim3((unsigned)((P + T - 1) / T), 3, 1), T, 0, s>>>(A, 0);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
 // FP64-arithmetic variants of the mixed path's wall-normal CN solves (the
 // "FP64 solves" policy): the FP32 right-hand sides are eliminated and
 // back-substituted in FP64 with the FP64 factor rows, the forward values kept

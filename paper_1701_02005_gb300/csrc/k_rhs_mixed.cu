@@ -47,13 +47,23 @@ struct PlaneC {
   float rho_ref, Fvref, rhorf, dPref, dPrefp;
   float cref_p, cref_m, crf_p, crf_pp, crf_m, crf_mp;
   float Dih, Dihp;   // D / h_j, D / h_{j+1}
+  // forward-elimination factors a, m of the CN rows at plane j (cells: u, w
+  // and the ions; v: row j - 1, its face j), when the stencil eliminates
+  float fa_c, fm_c, fa_f, fm_f, fa_i, fm_i;
 };
-constexpr int kPlaneC = 22;   // fields of PlaneC
-constexpr int kPlaneLd = 24;  // table row length (16-byte rows)
+constexpr int kPlaneC = 28;   // fields of PlaneC
+constexpr int kPlaneLd = 28;  // table row length (16-byte rows)
 
 // One field of PlaneC of plane j, by index.
-__device__ __forceinline__ float plane_const(const MetricsF& mt, const MixedRefs& R, float D, int which, int j) {
+__device__ __forceinline__ float plane_const(const MetricsF& mt, const MixedRefs& R, const CnFuse& fz, float D,
+                                             int which, int j) {
   switch (which) {
+    case 22: return fz.on ? fz.cell.a[j] : 0.f;
+    case 23: return fz.on ? fz.cell.m[j] : 0.f;
+    case 24: return fz.on && j > 0 ? fz.face.a[j - 1] : 0.f;
+    case 25: return fz.on && j > 0 ? fz.face.m[j - 1] : 0.f;
+    case 26: return fz.on ? fz.ion.a[j] : 0.f;
+    case 27: return fz.on ? fz.ion.m[j] : 0.f;
     case 0: return mt.idy[j];
     case 1: return mt.ih[j];
     case 2: return mt.ih[j + 1];
@@ -80,11 +90,11 @@ __device__ __forceinline__ float plane_const(const MetricsF& mt, const MixedRefs
 }
 
 // A block's table of per-plane constants: t[p * kPlaneLd + field], plane jb + p.
-__device__ __forceinline__ void fill_plane_table(float* t, const MetricsF& mt, const MixedRefs& R, float D, int jb,
-                                                 int je, int jchunk, int tid, int nthr) {
+__device__ __forceinline__ void fill_plane_table(float* t, const MetricsF& mt, const MixedRefs& R, const CnFuse& fz,
+                                                 float D, int jb, int je, int jchunk, int tid, int nthr) {
   for (int e = tid; e < kPlaneLd * jchunk; e += nthr) {
     const int p = e / kPlaneLd, which = e % kPlaneLd;
-    t[e] = (which < kPlaneC && jb + p < je) ? plane_const(mt, R, D, which, jb + p) : 0.f;
+    t[e] = (which < kPlaneC && jb + p < je) ? plane_const(mt, R, fz, D, which, jb + p) : 0.f;
   }
 }
 
@@ -97,6 +107,7 @@ __device__ __forceinline__ PlaneC plane_consts(const float* t) {
   q.cref_p = t[14]; q.cref_m = t[15];
   q.crf_p = t[16]; q.crf_pp = t[17]; q.crf_m = t[18]; q.crf_mp = t[19];
   q.Dih = t[20]; q.Dihp = t[21];
+  q.fa_c = t[22]; q.fm_c = t[23]; q.fa_f = t[24]; q.fm_f = t[25]; q.fa_i = t[26]; q.fm_i = t[27];
   return q;
 }
 
@@ -395,6 +406,32 @@ __device__ __forceinline__ void store_cell(const Fields<float>& f, float* rcp, f
   }
 }
 
+// The CN forward elimination fused into the stencil: the right-hand sides of
+// plane j become d~_j = (r_j - a_j d~_{j-1}) m_j, started from d~ = 0 at the
+// chunk's first plane (the first v face for v), so each chunk of the y-march is
+// an independent affine piece d_j = d~_j + G_j d_{s-1} of the line's true
+// elimination; the CN back substitution supplies d_{s-1} (G_j: products of
+// -a m over the chunk up to j, host tables).
+template <typename T>
+struct FwdCarry {
+  T u, w, v, cp, cm;
+};
+
+template <typename T>
+__device__ __forceinline__ void fuse_forward(CellOut<T>& o, const PlaneC& q, int j, int jb, FwdCarry<T>& d) {
+  if (j == jb) d = FwdCarry<T>{0.f, 0.f, 0.f, 0.f, 0.f};
+  d.u = fmaT(-q.fa_c, d.u, o.ru) * q.fm_c;
+  d.w = fmaT(-q.fa_c, d.w, o.rw) * q.fm_c;
+  if (j > 0) d.v = fmaT(-q.fa_f, d.v, o.rv) * q.fm_f;
+  d.cp = fmaT(-q.fa_i, d.cp, o.rcp) * q.fm_i;
+  d.cm = fmaT(-q.fa_i, d.cm, o.rcm) * q.fm_i;
+  o.ru = d.u;
+  o.rw = d.w;
+  o.rv = d.v;
+  o.rcp = d.cp;
+  o.rcm = d.cm;
+}
+
 __device__ __forceinline__ void wall_values(const Fields<float>& f, size_t P, size_t ck, float Uw, float& ub,
                                             float& ut, float& wb, float& wt) {
   ub = f.wall_u ? f.wall_u[ck] : -Uw;
@@ -453,7 +490,7 @@ __host__ __device__ constexpr size_t rhs_tile_floats(int tx, int tz, int cz, boo
 template <int TX, int TZ, int CZ, bool HSM, int MINB>
 __global__ void __launch_bounds__(TX * TZ, MINB)
     k_rhs_mixed_tile(Fields<float> f, float* __restrict__ rcp, float* __restrict__ rcm, Shadows sh, MixedRefs R,
-                     Geo g, MetricsF mt, CoefF cf, int jchunk) {
+                     Geo g, MetricsF mt, CoefF cf, int jchunk, CnFuse fz) {
   using TG = TileGeo<TX, TZ, CZ>;
   constexpr int NT = TG::NT, RS = TG::RS, NTH = TX * TZ, E = (TG::TASKS + NTH - 1) / NTH;
   extern __shared__ __align__(16) float rhs_smem[];
@@ -527,7 +564,8 @@ __global__ void __launch_bounds__(TX * TZ, MINB)
   issue_plane(jb);
   issue_plane(jb + 1);
   issue_plane(jb + 2);
-  fill_plane_table(pct, mt, R, cf.D, jb, je, jchunk, tid, NTH);
+  fill_plane_table(pct, mt, R, fz, cf.D, jb, je, jchunk, tid, NTH);
+  const bool fuse = fz.on != 0;   // uniform per launch
 
   // CZ = 1: one cell in FP32 scalars; CZ = 2: the cell pair in packed FP32
   using T = typename std::conditional<CZ == 2, V2, float>::type;
@@ -542,6 +580,7 @@ __global__ void __launch_bounds__(TX * TZ, MINB)
   };
   const int c = TG::PAD + (tz * CZ + 1) * RS + tx;   // first cell in a tile
   YCarry<T> cy{0.f, 0.f, 0.f, 0.f, 0.f};
+  FwdCarry<T> fd{0.f, 0.f, 0.f, 0.f, 0.f};
   for (int j = jb; j < je; ++j) {
     const size_t c0 = (size_t)j * P + ck;
     float Hf[CZ][NH];
@@ -582,7 +621,8 @@ __global__ void __launch_bounds__(TX * TZ, MINB)
     const float* bp = tiles + (size_t)slot_of(j + 1) * NA * NT + c;
     const PlaneC q = plane_consts(pct + (size_t)(j - jb) * kPlaneLd);
     const CellK<T> kc = (j == 0 || j == nyc - 1) ? walls() : CellK<T>{0.f, 0.f, 0.f, 0.f};
-    const CellOut<T> o = rhs_cell_at<T, NT, RS>(j, jb, nyc, bm, bo, bp, Ho, q, kc, cf, cy);
+    CellOut<T> o = rhs_cell_at<T, NT, RS>(j, jb, nyc, bm, bo, bp, Ho, q, kc, cf, cy);
+    if (fuse) fuse_forward(o, q, j, jb, fd);
     if constexpr (CZ == 2) store_cell(f, rcp, rcm, sh, c0, c0 + nx, j > 0, keep_h, o);
     else store_cell(f, rcp, rcm, sh, c0, j > 0, keep_h, o);
   }
@@ -675,7 +715,7 @@ template <int NX, int TZB>
 __global__ void __launch_bounds__(NX * TZB, 1)
     k_rhs_mixed_tma(const __grid_constant__ RhsMaps maps, Fields<float> f, float* __restrict__ rcp,
                     float* __restrict__ rcm, Shadows sh, MixedRefs R, Geo g, MetricsF mt, CoefF cf, int jchunk,
-                    int* __restrict__ err) {
+                    int* __restrict__ err, CnFuse fz) {
   using G = TmaGeo<NX, TZB>;
   extern __shared__ __align__(1024) float rhs_tma_smem[];
   float* tiles = rhs_tma_smem;                  // [4 slots][NA][AS]
@@ -693,8 +733,10 @@ __global__ void __launch_bounds__(NX * TZB, 1)
     for (int s = 0; s < 4; ++s) mbar_init(&bars[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  fill_plane_table(pct, mt, R, cf.D, jb, je, jchunk, tid, G::NTHR);
+  fill_plane_table(pct, mt, R, fz, cf.D, jb, je, jchunk, tid, G::NTHR);
   __syncthreads();
+  const bool fuse = fz.on != 0;   // uniform per launch
+  FwdCarry<float> fd{0.f, 0.f, 0.f, 0.f, 0.f};
 
   const bool read_h = cf.zet != 0.f, keep_h = cf.keep_h != 0;   // uniform per launch
   // plane q of the window [jb - 1, je] into slot n & 3, n = q - jb + 1 (warp 0)
@@ -771,7 +813,8 @@ __global__ void __launch_bounds__(NX * TZB, 1)
       for (int h = 0; h < 5; ++h) Ho[h] = hs[h * TZB * NX];
     }
     const PlaneC q = plane_consts(pct + (size_t)(j - jb) * kPlaneLd);
-    const CellOut<float> o = rhs_cell_at<float, G::AS, G::S>(j, jb, nyc, bm, bo, bp, Ho, q, kc, cf, cy);
+    CellOut<float> o = rhs_cell_at<float, G::AS, G::S>(j, jb, nyc, bm, bo, bp, Ho, q, kc, cf, cy);
+    if (fuse) fuse_forward(o, q, j, jb, fd);
     store_cell(f, rcp, rcm, sh, (size_t)j * P + ck, j > 0, keep_h, o);
     __syncthreads();   // slot of plane j - 1 is free
     if (j + 3 <= je) {
@@ -844,10 +887,8 @@ cudaError_t build_rhs_maps(RhsMaps* m, const Fields<float>& f, const Shadows& sh
   return cudaSuccess;
 }
 
-cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
-                             const MetricsF& m, const CoefF& cf, const RhsMaps* maps, int* err, cudaStream_t s) {
-  float* rp = reinterpret_cast<float*>(f.rcp);
-  float* rm = reinterpret_cast<float*>(f.rcm);
+namespace {
+int sm_count() {
   static int nsm = 0;
   if (nsm == 0) {
     int dev = 0;
@@ -855,36 +896,81 @@ cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const Mi
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       nsm = 152;
   }
-  // y-chunk length: the best product of wave efficiency (blocks over the
-  // resident slots, rounded up to whole waves) and chunk efficiency (each
-  // chunk also loads the planes below and above it), chunks of >= 8 planes
-  auto chunk = [&](int nxz, int per_sm) {
-    const int slots = nsm * per_sm;
-    int best = g.nyc;
-    double best_eff = -1.0;
-    for (int nch = 1; nch <= (g.nyc + 7) / 8; ++nch) {
-      const int jc = (g.nyc + nch - 1) / nch;
-      const double blocks = (double)nxz * ((g.nyc + jc - 1) / jc);
-      const double waves = blocks / slots;
-      const double eff = waves / std::ceil(waves) * jc / (jc + 2.0);
-      if (eff > best_eff + 1e-9) {
-        best_eff = eff;
-        best = jc;
-      }
+  return nsm;
+}
+
+// The stencil kernel a launch takes and its y-chunk length.
+struct RhsPlan {
+  int kind;   // 0: TMA rows; 1: 64-wide pair tile; 2: 32-wide pair tile; 3: one-cell 32 x 8; 4: 8 x 4; 5: 4 x 4
+  int tzb;    // TMA: rows per block
+  int jc;     // planes per y-chunk
+};
+
+// y-chunk length: the best product of wave efficiency (blocks over the
+// resident slots, rounded up to whole waves) and chunk efficiency (each chunk
+// also loads the planes below and above it), chunks of >= 8 planes
+int chunk_len(const Geo& g, int nxz, int per_sm) {
+  const int slots = sm_count() * per_sm;
+  int best = g.nyc;
+  double best_eff = -1.0;
+  for (int nch = 1; nch <= (g.nyc + 7) / 8; ++nch) {
+    const int jc = (g.nyc + nch - 1) / nch;
+    const double blocks = (double)nxz * ((g.nyc + jc - 1) / jc);
+    const double waves = blocks / slots;
+    const double eff = waves / std::ceil(waves) * jc / (jc + 2.0);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = jc;
     }
-    return best;
+  }
+  return best;
+}
+
+// TMA rows: lc_rhs_bx 128 (when the tensor maps exist); cp.async tiles: the
+// default and 64 / 32 / 16.  lc_rhs_bx: 64 = 64 x 4 threads with a packed pair
+// of cells each in z (a 64 x 8 tile), old H by direct loads; 32 = the same on
+// 32 x 8 threads (a 32 x 16 tile); 0 = the 64-wide tile where nx >= 64, else
+// the 32-wide one; 16 = 32 x 8 threads with one cell each, old H on the
+// cp.async ring; narrower grids fall back to 8 x 4 / 4 x 4.  Measured on the
+// 256x193x256 workload: 0.210 ms (64 wide), 0.224 ms (32 wide), 0.259 ms (one
+// cell); 64 x 8 threads (one 512-thread block per SM) 0.220 ms, 128 x 2 0.221 ms
+RhsPlan plan_for(const Geo& g, bool tma_maps) {
+  const int code = g.lc_rhs_bx;
+  if (tma_maps && code == 128 && rhs_tma_eligible(g)) {
+    const int tzb = rhs_tma_rows(g.nx);
+    return {0, tzb, chunk_len(g, g.nz / tzb, 1)};
+  }
+  auto tile = [&](int kind, int bx, int bz, int cz, int per_sm) {
+    return RhsPlan{kind, 0, chunk_len(g, (g.nx / bx) * (g.nz / (bz * cz)), per_sm)};
   };
-  // TMA rows: lc_rhs_bx 128; cp.async tiles: the default and 64 / 32 / 16
-  if (maps && g.lc_rhs_bx == 128 && rhs_tma_eligible(g)) {
+  if (g.nx >= 64 && g.nz >= 8 && (code == 64 || code == 0 || code == 128)) return tile(1, 64, 4, 2, 2);
+  if (g.nx >= 32 && g.nz >= 16 && code != 16) return tile(2, 32, 8, 2, 2);
+  if (g.nx >= 32 && g.nz >= 8) return tile(3, 32, 8, 1, 3);
+  if (g.nx >= 8) return tile(4, 8, 4, 1, 24);
+  return tile(5, 4, 4, 1, 48);
+}
+}  // namespace
+
+int mixed_rhs_chunk(const Geo& g, bool tma_maps) { return plan_for(g, tma_maps).jc; }
+
+cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
+                             const MetricsF& m, const CoefF& cf, const RhsMaps* maps, int* err, cudaStream_t s,
+                             const CnFuse* fuse) {
+  float* rp = reinterpret_cast<float*>(f.rcp);
+  float* rm = reinterpret_cast<float*>(f.rcm);
+  const CnFuse fz = fuse ? *fuse : CnFuse{};
+  const RhsPlan pl = plan_for(g, maps != nullptr);
+  if (fz.on && fz.jc != pl.jc) return cudaErrorInvalidValue;   // the back substitution's chunks must match
+  const int jc = pl.jc;
+  if (pl.kind == 0) {
     auto go = [&](auto kern, auto geo, int tzb) {
       using G = decltype(geo);
-      const int jc = chunk(g.nz / tzb, 1);
       const size_t smem = G::bytes(jc);
       if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       const dim3 grd((unsigned)(g.nz / tzb), (unsigned)((g.nyc + jc - 1) / jc));
-      kern<<<grd, dim3(g.nx, tzb), smem, s>>>(*maps, f, rp, rm, sh, R, g, m, cf, jc, err);
+      kern<<<grd, dim3(g.nx, tzb), smem, s>>>(*maps, f, rp, rm, sh, R, g, m, cf, jc, err, fz);
       return cudaGetLastError();
     };
     switch (g.nx) {
@@ -894,32 +980,23 @@ cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const Mi
       default: return go(k_rhs_mixed_tma<256, 2>, TmaGeo<256, 2>{}, 2);
     }
   }
-  // cp.async tiles.  lc_rhs_bx: 64 = 64 x 4 threads with a packed pair of cells
-  // each in z (a 64 x 8 tile), old H by direct loads; 32 = the same on 32 x 8
-  // threads (a 32 x 16 tile); 0 = the 64-wide tile where nx >= 64, else the
-  // 32-wide one; 16 = 32 x 8 threads with one cell each, old H on the cp.async
-  // ring; narrower grids fall back to 8 x 4 / 4 x 4.  Measured on the
-  // 256x193x256 workload: 0.210 ms (64 wide), 0.224 ms (32 wide), 0.259 ms (one
-  // cell); 64 x 8 threads (one 512-thread block per SM) 0.220 ms, 128 x 2 0.221 ms
-  auto go = [&](auto kern, int bx, int bz, int cz, bool hsm, int per_sm) {
-    const int nxz = (g.nx / bx) * (g.nz / (bz * cz));
-    const int jc = chunk(nxz, per_sm);
+  auto go = [&](auto kern, int bx, int bz, int cz, bool hsm) {
     const dim3 grd((unsigned)(g.nx / bx), (unsigned)(g.nz / (bz * cz)), (unsigned)((g.nyc + jc - 1) / jc));
     const size_t smem = sizeof(float) * (rhs_tile_floats(bx, bz, cz, hsm) + (size_t)kPlaneLd * jc);
     if (smem > 48 * 1024) {
       const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
     }
-    kern<<<grd, dim3(bx, bz), smem, s>>>(f, rp, rm, sh, R, g, m, cf, jc);
+    kern<<<grd, dim3(bx, bz), smem, s>>>(f, rp, rm, sh, R, g, m, cf, jc, fz);
     return cudaGetLastError();
   };
-  const int code = g.lc_rhs_bx;
-  if (g.nx >= 64 && g.nz >= 8 && (code == 64 || code == 0 || code == 128))
-    return go(k_rhs_mixed_tile<64, 4, 2, false, 2>, 64, 4, 2, false, 2);
-  if (g.nx >= 32 && g.nz >= 16 && code != 16) return go(k_rhs_mixed_tile<32, 8, 2, false, 2>, 32, 8, 2, false, 2);
-  if (g.nx >= 32 && g.nz >= 8) return go(k_rhs_mixed_tile<32, 8, 1, true, 3>, 32, 8, 1, true, 3);
-  if (g.nx >= 8) return go(k_rhs_mixed_tile<8, 4, 1, true, 24>, 8, 4, 1, true, 24);
-  return go(k_rhs_mixed_tile<4, 4, 1, true, 32>, 4, 4, 1, true, 48);
+  switch (pl.kind) {
+    case 1: return go(k_rhs_mixed_tile<64, 4, 2, false, 2>, 64, 4, 2, false);
+    case 2: return go(k_rhs_mixed_tile<32, 8, 2, false, 2>, 32, 8, 2, false);
+    case 3: return go(k_rhs_mixed_tile<32, 8, 1, true, 3>, 32, 8, 1, true);
+    case 4: return go(k_rhs_mixed_tile<8, 4, 1, true, 24>, 8, 4, 1, true);
+    default: return go(k_rhs_mixed_tile<4, 4, 1, true, 32>, 4, 4, 1, true);
+  }
 }
 
 }  // namespace pnp

@@ -127,6 +127,12 @@ struct pnp_ctx {
   double wall_off = 0.0, V_set = 0.0;           // mean offset; the uniform V of pnp_set_params
   double *wallB_d = nullptr, *wallT_d = nullptr, *lift64 = nullptr;
   float* lift32 = nullptr;
+  // the CN forward elimination fused into the mixed stencil: chunk products G
+  // [3 substages][3 kinds][ny] for the dt and chunk length they were made for
+  bool fuse_cn = true;
+  float* fuseG_d = nullptr;
+  double fuse_dt = NAN;
+  int fuse_jc = 0;
   // time statistics: plane means of q and q^2 summed over samples ([12][ny])
   double* stats_acc = nullptr;
   long long stats_n = 0;
@@ -199,8 +205,10 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
   double* lift64 = b.take<double>(nc);
   float* lift32 = b.take<float>(nc);
   double* sacc = b.take<double>(12 * (size_t)ny);
+  float* fuseG = b.take<float>(9 * (size_t)ny);
   if (c) {
     c->stats_acc = sacc;
+    c->fuseG_d = fuseG;
     c->wallB_d = wB; c->wallT_d = wT; c->lift64 = lift64; c->lift32 = lift32;
     c->dCp_f2 = dCp2; c->dCm_f2 = dCm2;
     c->spf_cprN = sfcN; c->spf_invN = sfiN; c->spf_cprD = sfcD; c->spf_invD = sfiD;
@@ -440,6 +448,53 @@ int upload_cn(pnp_ctx* c, double dt) {
   CK(cudaStreamSynchronize(c->stream));
   c->cn_dt = dt;
   c->refs_dt = NAN;
+  c->fuse_dt = NAN;
+  return PNP_OK;
+}
+
+// The stencil eliminates forward chunk by chunk (chunk length jc) when the
+// mixed path runs its default policy with the line back substitution.
+bool cn_fused(const pnp_ctx* c, int* jc_out = nullptr) {
+  if (c->precision != PNP_MIXED || c->policy != PNP_POLICY_DEFAULT || !c->fuse_cn || c->g.lc_cn == 32) return false;
+  const int jc = mixed_rhs_chunk(c->g, c->rhs_maps_ok);
+  if ((c->g.nyc - 1) / jc + 1 > kFusedMaxChunks) return false;
+  if (jc_out) *jc_out = jc;
+  return true;
+}
+
+// Chunk products G_r = prod_{i=s..r} (-a_i m_i) over the rows of each chunk,
+// from the FP32 factor rows the stencil eliminates with (needs upload_cn's dt).
+int upload_fuse(pnp_ctx* c, double dt, int jc) {
+  const int ny = c->g.ny, nyc = c->g.nyc;
+  std::vector<float> G(9 * (size_t)ny, 0.f);
+  for (int l = 0; l < 3; ++l)
+    for (int kind = 0; kind < 3; ++kind) {
+      const double* A = c->cn_h.data() + ((size_t)(l * 3 + kind) * 3 + 0) * ny;
+      const double* M = c->cn_h.data() + ((size_t)(l * 3 + kind) * 3 + 2) * ny;
+      const int n = kind == 1 ? nyc - 1 : nyc, j0 = kind == 1 ? 1 : 0;
+      float* out = G.data() + (size_t)(l * 3 + kind) * ny;
+      double acc = 1.0;
+      for (int r = 0; r < n; ++r) {
+        if (r == 0 || (r + j0) % jc == 0) acc = 1.0;   // first row of a chunk
+        acc *= -(double)(float)A[r] * (double)(float)M[r];
+        out[r] = (float)acc;
+      }
+    }
+  CK(cudaMemcpyAsync(c->fuseG_d, G.data(), sizeof(float) * G.size(), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->fuse_dt = dt;
+  c->fuse_jc = jc;
+  return PNP_OK;
+}
+
+// The factor tables a step of size dt needs (CN rows, fused-chunk products).
+int prepare_tables(pnp_ctx* c, double dt) {
+  if (c->cn_dt != dt) {
+    int r = upload_cn(c, dt);
+    if (r) return r;
+  }
+  int jc = 0;
+  if (cn_fused(c, &jc) && (!(c->fuse_dt == dt) || c->fuse_jc != jc)) return upload_fuse(c, dt, jc);
   return PNP_OK;
 }
 
@@ -719,16 +774,24 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
   const Shadows sh = shadows(c);
   const MixedRefs R = mixed_refs(c);
   const bool fp64 = c->policy == PNP_POLICY_FP64_SOLVES;
+  const CNRowsF cell = cn_rows_f(c, l, 0), face = cn_rows_f(c, l, 1), ion = cn_rows_f(c, l, 2);
+  int jc = 0;
+  const bool fused = cn_fused(c, &jc) && c->fuse_dt == dt && c->fuse_jc == jc;
+  const CnFuse fz{cell, face, ion, jc, fused ? 1 : 0};
   mark(c, c->stream, -1);
-  cudaError_t e =
-      launch_mixed_rhs(f, sh, R, c->g, metrics_f(c), coef_f(c, st, l < 2), rhs_maps(c), c->status_d + 1, c->stream);
+  cudaError_t e = launch_mixed_rhs(f, sh, R, c->g, metrics_f(c), coef_f(c, st, l < 2), rhs_maps(c), c->status_d + 1,
+                                   c->stream, fused ? &fz : nullptr);
   if (e != cudaSuccess) return e;
   mark(c, c->stream, PNP_SITE_RHS);
-  const CNRowsF cell = cn_rows_f(c, l, 0), face = cn_rows_f(c, l, 1), ion = cn_rows_f(c, l, 2);
+  const size_t ny = c->g.ny;
+  const float* Gl = c->fuseG_d + (size_t)l * 3 * ny;
+  const CnFusedG G{Gl, Gl + ny, Gl + 2 * ny};
   auto cn = [&](unsigned parts, cudaStream_t s) {
-    return fp64 ? launch_mixed_cn_fp64(f, sh, R, c->g, cn_rows(c, l, 0), cn_rows(c, l, 1), cn_rows(c, l, 2), l, parts,
-                                       cn_scratch64(c), s)
-                : launch_mixed_cn(f, sh, R, c->g, cell, face, ion, l, parts, s);
+    if (fp64)
+      return launch_mixed_cn_fp64(f, sh, R, c->g, cn_rows(c, l, 0), cn_rows(c, l, 1), cn_rows(c, l, 2), l, parts,
+                                  cn_scratch64(c), s);
+    if (fused) return launch_mixed_cn_fused(f, sh, R, c->g, cell, face, ion, G, jc, l, parts, s);
+    return launch_mixed_cn(f, sh, R, c->g, cell, face, ion, l, parts, s);
   };
   auto pot = [&](cudaStream_t s, void* spec, cplx<double>* dscr) {
     return fp64 ? potential_mixed_fp64(c, s, spec, dscr) : potential_mixed(c, s, spec, dscr);
@@ -1124,12 +1187,9 @@ int pnp_step(pnp_ctx* c, int nsteps, double dt) {
   if (!c || nsteps < 0 || !(dt > 0) || !std::isfinite(dt)) return PNP_ERR_ARG;
   if (!c->have_params || !c->have_state) return PNP_ERR_STATE;
   if (nsteps == 0) return PNP_OK;
-  if (c->cn_dt != dt) {
-    int r = upload_cn(c, dt);
-    if (r) return r;
-  }
   {
     int r = refresh_refs(c, dt);
+    if (!r) r = prepare_tables(c, dt);
     if (r) return r;
   }
   if (c->precision == PNP_MIXED) c->fp64_fresh = false;
@@ -1289,6 +1349,13 @@ int pnp_set_wall_potential(pnp_ctx* c, const double* bottom, const double* top) 
     c->refs_valid = false;
   }
   CK(cudaStreamSynchronize(c->stream));
+  return PNP_OK;
+}
+
+int pnp_set_fusion(pnp_ctx* c, int on) {
+  if (!c) return PNP_ERR_ARG;
+  if ((on != 0) != c->fuse_cn) drop_graph(c);
+  c->fuse_cn = on != 0;
   return PNP_OK;
 }
 
@@ -1514,12 +1581,9 @@ extern "C" {
 int pnp_profile(pnp_ctx* c, int nsteps, double dt, double* ms_out, int nsites, int* launches_per_step) {
   if (!c || !ms_out || nsites < PNP_PROFILE_SITES || nsteps < 1 || !(dt > 0)) return PNP_ERR_ARG;
   if (!c->have_params || !c->have_state) return PNP_ERR_STATE;
-  if (c->cn_dt != dt) {
-    int r = upload_cn(c, dt);
-    if (r) return r;
-  }
   {
     int r = refresh_refs(c, dt);
+    if (!r) r = prepare_tables(c, dt);
     if (r) return r;
   }
   if (c->precision == PNP_MIXED) c->fp64_fresh = false;
@@ -1559,12 +1623,9 @@ int pnp_timeline(pnp_ctx* c, double dt, int in_graph, int cap, int* site_out, in
   if (!c || !site_out || !stream_out || !t_ms_out || !n_out || cap < 1 || !(dt > 0)) return PNP_ERR_ARG;
   if (in_graph && !c->stream) return PNP_ERR_ARG;   // a capture needs a stream of its own
   if (!c->have_params || !c->have_state) return PNP_ERR_STATE;
-  if (c->cn_dt != dt) {
-    int r = upload_cn(c, dt);
-    if (r) return r;
-  }
   {
     int r = refresh_refs(c, dt);
+    if (!r) r = prepare_tables(c, dt);
     if (r) return r;
   }
   if (c->precision == PNP_MIXED) c->fp64_fresh = false;
@@ -1663,6 +1724,10 @@ int pnp_autotune(pnp_ctx* c, double dt, int* cfg_out, double* ms_out) {
     c->fp64_fresh = true;
     c->refs_valid = false;
     int r = refresh_refs(c, dt);
+    if (r) return r;
+  }
+  {
+    int r = prepare_tables(c, dt);
     if (r) return r;
   }
   const Stage st{dt, kGam[0], kZet[0], kGam[0] + kZet[0]};
@@ -1869,12 +1934,9 @@ int pnp_ensemble_step(pnp_ensemble* e, int nsteps, const double* dt) {
   bool recapture = !e->exec || (int)e->dts.size() != n;
   for (int i = 0; i < n; ++i) {
     pnp_ctx* c = e->cases[i];
-    if (c->cn_dt != dt[i]) {
-      int r = upload_cn(c, dt[i]);
-      if (r) return r;
-    }
     const bool had_refs = c->refs_valid;
     int r = refresh_refs(c, dt[i]);
+    if (!r) r = prepare_tables(c, dt[i]);
     if (r) return r;
     if (c->precision == PNP_MIXED) c->fp64_fresh = false;
     if (!had_refs || (!recapture && e->dts[i] != dt[i])) recapture = true;

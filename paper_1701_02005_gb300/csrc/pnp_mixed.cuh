@@ -75,10 +75,34 @@ cudaError_t launch_diagnostics_mixed(const Fields<float>& f, const Shadows& sh, 
                                      const DiagLimits& lim, cudaStream_t s);
 cudaError_t launch_wait_selftest(int* err, double limit_s, cudaStream_t s);
 cudaError_t build_rhs_maps(RhsMaps* m, const Fields<float>& f, const Shadows& sh, const Geo& g);
+// The CN forward elimination fused into the stencil (on != 0): the substage's
+// FP32 factor rows of the three families (cells u, w; v faces; ions) and the
+// y-chunk length the stencil marches, which the back substitution must know.
+struct CnFuse {
+  CNRowsF cell, face, ion;
+  int jc;
+  int on;
+};
+// Planes per y-chunk of the stencil launch_mixed_rhs takes on this grid and
+// launch shape (tma_maps: the context has the TMA tensor maps).
+int mixed_rhs_chunk(const Geo& g, bool tma_maps);
 // maps == nullptr selects the cp.async tile kernel; err receives PNP_ERR_TIMEOUT
-// if a TMA copy does not complete within the kernel's wait limit.
+// if a TMA copy does not complete within the kernel's wait limit.  fuse (optional):
+// store d~ (chunk-local forward elimination) instead of the CN right-hand sides.
 cudaError_t launch_mixed_rhs(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
-                             const MetricsF& m, const CoefF& cf, const RhsMaps* maps, int* err, cudaStream_t s);
+                             const MetricsF& m, const CoefF& cf, const RhsMaps* maps, int* err, cudaStream_t s,
+                             const CnFuse* fuse = nullptr);
+// Back substitution of the wall-normal CN solves after the fused stencil: per
+// line, the chunk-boundary values of the forward elimination from the chunks'
+// d~ and the products G (tables [row] per family: cells, faces, ions), then
+// x_j = d_j - c_j x_{j+1} from the top with d_j = d~_j + G_j d_{s-1}.
+struct CnFusedG {
+  const float *cell, *face, *ion;
+};
+cudaError_t launch_mixed_cn_fused(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,
+                                  const CNRowsF& cell, const CNRowsF& face, const CNRowsF& ion, const CnFusedG& G,
+                                  int jc, int l, unsigned parts, cudaStream_t s);
+constexpr int kFusedMaxChunks = 32;
 // Wall-normal CN solves of substage l: the ion families and / or the velocity families.
 constexpr unsigned kCnIons = 1, kCnVelocity = 2;
 cudaError_t launch_mixed_cn(const Fields<float>& f, const Shadows& sh, const MixedRefs& R, const Geo& g,

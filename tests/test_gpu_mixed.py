@@ -245,3 +245,33 @@ def test_fp64_solves_policy_needs_a_mixed_context():
     assert B.pnp_set_policy(s.ctx, 7) == B.PNP_ERR_ARG
     assert B.pnp_set_policy(s.ctx, B.PNP_POLICY_DEFAULT) == B.PNP_OK
     s.close()
+
+
+@pytest.mark.parametrize("shape", [(64, 97, 32), (16, 257, 8)])
+def test_fused_forward_elimination_matches_the_unfused_solve(shape):
+    # the stencil's chunk-local forward elimination plus the back substitution's
+    # chunk fix-up against right-hand sides stored and eliminated in one sweep:
+    # the same solve up to FP32 rounding, on grids whose y-march has many chunks
+    from paper_1701_02005_gb300 import binding as B
+
+    nx, ny, nz = shape
+    g = o.Grid(nx, ny, nz, 2 * math.pi, math.pi, stretch=2.0)
+    prm = o.Params(Re=300.0, lam=0.05, Sc=1.0, V=2.0, beta=0.5)
+    st = o.initial_state(g, prm, o.IC_PB, seed=37, amp=0.1)
+    out = {}
+    for fused in (1, 0):
+        s = _mixed(g, prm)
+        B.check(B.pnp_set_fusion(s.ctx, fused), "pnp_set_fusion")
+        s.set_state(st)
+        s.step(3, 0.004)
+        out[fused] = {n: s.get(n) for n in ("u", "v", "w", "cp", "cm", "Phi")}
+        assert s.status() == 0
+        s.close()
+    for n in out[0]:
+        scale = max(np.max(np.abs(out[0][n])), 1.0 if n in ("u", "v", "w") else 1e-300)
+        assert np.max(np.abs(out[1][n] - out[0][n])) <= 1e-6 * scale, n
+    ref = o.step(g, prm, st, 0.004, 3)
+    for n in out[1]:
+        r = getattr(ref, n)
+        scale = max(np.max(np.abs(r)), 1.0 if n in ("u", "v", "w") else 1e-300)
+        assert np.max(np.abs(out[1][n] - r)) <= 1e-5 * scale, n
