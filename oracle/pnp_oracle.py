@@ -37,7 +37,8 @@ the CUDA path implements):
   conservation on the stretched y-grid).  Ions: face velocity times the
   arithmetic face mean of c.
 * "Adams-Bashforth for viscous terms" read as Crank-Nicolson in y per
-  substage; x and z viscous / diffusive terms explicit.
+  substage; x and z viscous / diffusive terms explicit, or (Params.af) also
+  Crank-Nicolson, approximately factorised into periodic x and z sweeps.
 * Pressure update p <- p + Phi_p.  The singular (0,0) Neumann mode is pinned
   by replacing its bottom-row equation with Phi_p(0,0,j=0) = 0.
 * Modified wavenumbers (2 - 2 cos(2 pi m / N)) / dx^2: the solver inverts
@@ -127,6 +128,9 @@ class Params:
     # optional wall potentials (Phi_bottom, Phi_top), each (nz, nx) values on the
     # wall faces above / below the cell columns; None = the uniform -V, +V
     wall: tuple | None = None
+    # approximate factorisation: x/z viscous and ion-diffusion terms implicit
+    # as well, (I - s L_x)(I - s L_z)(I - s L_y) dq = r (periodic x, z sweeps)
+    af: bool = False
 
     @property
     def nu(self):            # momentum diffusivity 1/Re
@@ -282,7 +286,7 @@ def body_force(g, prm, cp, cm, Phi):
     return fu, fv, fw
 
 
-def ion_explicit(g, prm, s, c, u, v, w, Phi):
+def ion_explicit(g, prm, s, c, u, v, w, Phi, xz_diffusion=True):
     """Explicit part of Eq. (3) for the ion of valence s = +1 / -1.
 
     Face flux F = u c_face - D grad c - s D c_face grad Phi (advective,
@@ -291,10 +295,11 @@ def ion_explicit(g, prm, s, c, u, v, w, Phi):
     zero (no penetration, Fig. 1 caption).  Returns -div F.
     """
     D = prm.D
+    Dd = D if xz_diffusion else 0.0   # x/z diffusion explicit (CN in y) or implicit (AF)
     cx = 0.5 * (_xm(c) + c)
-    Fx = u * cx - D * (c - _xm(c)) / g.dx - s * D * cx * (Phi - _xm(Phi)) / g.dx
+    Fx = u * cx - Dd * (c - _xm(c)) / g.dx - s * D * cx * (Phi - _xm(Phi)) / g.dx
     cz = 0.5 * (_zm(c) + c)
-    Fz = w * cz - D * (c - _zm(c)) / g.dz - s * D * cz * (Phi - _zm(Phi)) / g.dz
+    Fz = w * cz - Dd * (c - _zm(c)) / g.dz - s * D * cz * (Phi - _zm(Phi)) / g.dz
     Fy = np.zeros((g.ny,) + c.shape[1:])
     cy = 0.5 * (c[:-1] + c[1:])
     Fy[1:-1] = v[1:-1] * cy - s * D * cy * (Phi[1:] - Phi[:-1]) / _col(g.h[1:-1])
@@ -389,6 +394,41 @@ def cn_solve(a, b, c, s, r):
     return thomas(_col(-s * a), _col(1.0 - s * b), _col(-s * c), r)
 
 
+def periodic_solve(lo, di, up, r, axis):
+    """Solve the cyclic tridiagonal system lo x_{i-1} + di x_i + up x_{i+1} = r_i
+    (indices modulo n, constant coefficients) along ``axis``: the Thomas
+    algorithm on the system with its corners removed and the diagonal changed
+    at both ends, plus the Sherman-Morrison correction for the rank-one rest
+    (A = T + u v^T, u = (gam, 0, ..., 0, up), v = (1, 0, ..., 0, lo / gam),
+    gam = -di)."""
+    rr = np.moveaxis(r, axis, 0)
+    n = rr.shape[0]
+    gam = -di
+    a = np.full(n, lo)
+    b = np.full(n, di)
+    c = np.full(n, up)
+    a[0] = 0.0
+    c[-1] = 0.0
+    b[0] = di - gam
+    b[-1] = di - lo * up / gam
+    u = np.zeros(n)
+    u[0] = gam
+    u[-1] = up
+    shape = (n,) + (1,) * (rr.ndim - 1)
+    y = thomas(a.reshape(shape), b.reshape(shape), c.reshape(shape), rr)
+    q = thomas(a, b, c, u)
+    f = (y[0] + (lo / gam) * y[-1]) / (1.0 + q[0] + (lo / gam) * q[-1])
+    x = y - f[None] * q.reshape(shape)
+    return np.moveaxis(x, 0, axis)
+
+
+def xz_factors_solve(g, s, r):
+    """(I - s L_z)^-1 (I - s L_x)^-1 r with the periodic second differences."""
+    bx, bz = s / g.dx ** 2, s / g.dz ** 2
+    t = periodic_solve(-bx, 1.0 + 2.0 * bx, -bx, r, axis=2)
+    return periodic_solve(-bz, 1.0 + 2.0 * bz, -bz, t, axis=1)
+
+
 # --------------------------------------------------------------------------
 # Separable Poisson solver (Numerical methods, potential paragraph)
 # --------------------------------------------------------------------------
@@ -428,13 +468,14 @@ def explicit_terms(g, prm, st):
     """H for u, v, w, c+, c- at the current level: advection, explicit
     x/z diffusion, Coulomb force, Nernst-Planck drift (Eqs. (1), (3))."""
     fu, fv, fw = body_force(g, prm, st.cp, st.cm, st.Phi)
-    Hu = -advection_u(g, st.u, st.v, st.w) + prm.nu * lap_xz(g, st.u) + fu
-    Hv = -advection_v(g, st.u, st.v, st.w) + prm.nu * lap_xz(g, st.v) + fv
+    nxz = 0.0 if prm.af else prm.nu   # x/z viscous terms: explicit (CN in y) or implicit (AF)
+    Hu = -advection_u(g, st.u, st.v, st.w) + nxz * lap_xz(g, st.u) + fu
+    Hv = -advection_v(g, st.u, st.v, st.w) + nxz * lap_xz(g, st.v) + fv
     Hv[0] = 0.0
     Hv[-1] = 0.0
-    Hw = -advection_w(g, st.u, st.v, st.w) + prm.nu * lap_xz(g, st.w) + fw
-    Hcp = ion_explicit(g, prm, +1.0, st.cp, st.u, st.v, st.w, st.Phi)
-    Hcm = ion_explicit(g, prm, -1.0, st.cm, st.u, st.v, st.w, st.Phi)
+    Hw = -advection_w(g, st.u, st.v, st.w) + nxz * lap_xz(g, st.w) + fw
+    Hcp = ion_explicit(g, prm, +1.0, st.cp, st.u, st.v, st.w, st.Phi, not prm.af)
+    Hcm = ion_explicit(g, prm, -1.0, st.cm, st.u, st.v, st.w, st.Phi, not prm.af)
     return Hu, Hv, Hw, Hcp, Hcm
 
 
@@ -490,6 +531,16 @@ def substage(g, prm, st, dt, l):
 
     su = 0.5 * alp * dt * nu
     sc = 0.5 * alp * dt * D
+    if prm.af:
+        # approximate factorisation: the x/z second differences join L_y on the
+        # right-hand side (explicit half) and in the factored operator
+        ru = ru + dt * alp * nu * lap_xz(g, st.u)
+        rv = rv + dt * alp * nu * lap_xz(g, st.v[1:-1])
+        rw = rw + dt * alp * nu * lap_xz(g, st.w)
+        rcp = rcp + dt * alp * D * lap_xz(g, st.cp)
+        rcm = rcm + dt * alp * D * lap_xz(g, st.cm)
+        ru, rv, rw = (xz_factors_solve(g, su, r) for r in (ru, rv, rw))
+        rcp, rcm = (xz_factors_solve(g, sc, r) for r in (rcp, rcm))
     uh = st.u + cn_solve(au, bu, cu, su, ru)
     vh = st.v.copy()
     vh[1:-1] += cn_solve(av, bv, cv, su, rv)
