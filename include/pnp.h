@@ -208,6 +208,17 @@ int pnp_diagnostics(pnp_ctx* ctx, pnp_diag* out);
  * check reports one (PNP_ERR_NONFINITE, ...). */
 int pnp_step_adaptive(pnp_ctx* ctx, int nsteps, double dt_max, double cfl, int check_every, double* dts_out);
 
+/* Time-integration scheme of the viscous and diffusive terms (Numerical
+ * methods: the AFiD fractional step).  PNP_SCHEME_CN: Crank-Nicolson in y
+ * (the wall-normal Thomas solves), x/z terms explicit in the RK3 right-hand
+ * side.  PNP_SCHEME_AF: Crank-Nicolson in all three directions, approximately
+ * factorised, (I - s L_x)(I - s L_z)(I - s L_y) dq = r with r holding the
+ * explicit half of the full Laplacian: periodic (cyclic) tridiagonal sweeps in
+ * x and z before the wall-normal solve, which lifts the x/z viscous and
+ * diffusive stability limits.  Migration and advection stay explicit. */
+enum { PNP_SCHEME_CN = 0, PNP_SCHEME_AF = 1 };
+int pnp_set_scheme(pnp_ctx* ctx, int scheme);
+
 /* PNP_MIXED with the default policy: fuse the forward elimination of the
  * wall-normal CN solves into the explicit-term stencil (on != 0, the default).
  * The stencil, which marches y in chunks, stores each chunk's forward-

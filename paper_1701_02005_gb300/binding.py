@@ -26,6 +26,8 @@ PNP_ERR_CFL = -11
 PNP_ERR_DPHI = -12
 PNP_POLICY_DEFAULT = 0
 PNP_POLICY_FP64_SOLVES = 1
+PNP_SCHEME_CN = 0
+PNP_SCHEME_AF = 1
 
 PNP_FP64 = 0
 PNP_MIXED = 1
@@ -80,6 +82,7 @@ EXPORTS = {
     "pnp_set_limits": (C.c_int, [C.c_void_p, C.c_double, C.c_double]),
     "pnp_set_policy": (C.c_int, [C.c_void_p, C.c_int]),
     "pnp_set_fusion": (C.c_int, [C.c_void_p, C.c_int]),
+    "pnp_set_scheme": (C.c_int, [C.c_void_p, C.c_int]),
     "pnp_stats_reset": (C.c_int, [C.c_void_p]),
     "pnp_stats_sample": (C.c_int, [C.c_void_p]),
     "pnp_stats_get": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -180,6 +183,7 @@ pnp_eval_explicit = _fwd("pnp_eval_explicit")
 pnp_set_limits = _fwd("pnp_set_limits")
 pnp_set_policy = _fwd("pnp_set_policy")
 pnp_set_fusion = _fwd("pnp_set_fusion")
+pnp_set_scheme = _fwd("pnp_set_scheme")
 pnp_stats_reset = _fwd("pnp_stats_reset")
 pnp_stats_sample = _fwd("pnp_stats_sample")
 pnp_stats_get = _fwd("pnp_stats_get")

@@ -64,13 +64,13 @@ __global__ void __launch_bounds__(128) k_rhs(Fields<TV> f, Geo g, Metrics mt, Ph
     const double lap = (uxp - 2.0 * u0 + uxm) * idx2 + (uzp - 2.0 * u0 + uzm) * idz2;
     const double rhom = L(f.cp, cxm) - L(f.cm, cxm);
     const double fu = -ph.K * 0.5 * (rhom + rho0) * (Ph0 - Phxm) * idx;
-    const double H = -(ax + ay + az) + ph.nu * lap + fu;
+    const double H = -(ax + ay + az) + (st.af ? 0.0 : ph.nu * lap) + fu;
     const double ub = f.wall_u ? (double)f.wall_u[(size_t)k * nx + i] : -ph.Uw;
     const double ut = f.wall_u ? (double)f.wall_u[P + (size_t)k * nx + i] : ph.Uw;
     const double Ly = mt.lo_c[j] * ((has_dn ? uym : ub) - u0) + mt.hi_c[j] * ((has_up ? uyp : ut) - u0);
     const double gp = (p0 - L(f.p, cxm)) * idx;
     const double Ho = (double)f.Hu[c0];
-    f.ru[c0] = (TV)(st.dt * (st.gam * H + st.zet * Ho - st.alp * gp + st.alp * ph.nu * Ly));
+    f.ru[c0] = (TV)(st.dt * (st.gam * H + st.zet * Ho - st.alp * gp + st.alp * ph.nu * (st.af ? Ly + lap : Ly)));
     f.Hu[c0] = (TV)H;
   }
 
@@ -89,13 +89,13 @@ __global__ void __launch_bounds__(128) k_rhs(Fields<TV> f, Geo g, Metrics mt, Ph
     const double lap = (wxp - 2.0 * w0 + wxm) * idx2 + (wzp - 2.0 * w0 + wzm) * idz2;
     const double rhom = L(f.cp, czm) - L(f.cm, czm);
     const double fw = -ph.K * 0.5 * (rhom + rho0) * (Ph0 - Phzm) * idz;
-    const double H = -(ax + ay + az) + ph.nu * lap + fw;
+    const double H = -(ax + ay + az) + (st.af ? 0.0 : ph.nu * lap) + fw;
     const double wb = f.wall_w ? (double)f.wall_w[(size_t)k * nx + i] : 0.0;
     const double wt = f.wall_w ? (double)f.wall_w[P + (size_t)k * nx + i] : 0.0;
     const double Ly = mt.lo_c[j] * ((has_dn ? wym : wb) - w0) + mt.hi_c[j] * ((has_up ? wyp : wt) - w0);
     const double gp = (p0 - L(f.p, czm)) * idz;
     const double Ho = (double)f.Hw[c0];
-    f.rw[c0] = (TV)(st.dt * (st.gam * H + st.zet * Ho - st.alp * gp + st.alp * ph.nu * Ly));
+    f.rw[c0] = (TV)(st.dt * (st.gam * H + st.zet * Ho - st.alp * gp + st.alp * ph.nu * (st.af ? Ly + lap : Ly)));
     f.Hw[c0] = (TV)H;
   }
 
@@ -117,11 +117,11 @@ __global__ void __launch_bounds__(128) k_rhs(Fields<TV> f, Geo g, Metrics mt, Ph
     const double lap = (vxp - 2.0 * v0 + vxm) * idx2 + (vzp - 2.0 * v0 + vzm) * idz2;
     const double rhod = L(f.cp, d0) - L(f.cm, d0);
     const double fv = -ph.K * 0.5 * (rhod + rho0) * (Ph0 - Phym) * ihj;
-    const double H = -(ax + ay + az) + ph.nu * lap + fv;
+    const double H = -(ax + ay + az) + (st.af ? 0.0 : ph.nu * lap) + fv;
     const double Ly = mt.lo_f[j] * (vym - v0) + mt.hi_f[j] * (vyp - v0);
     const double gp = (p0 - L(f.p, d0)) * ihj;
     const double Ho = (double)f.Hv[c0];
-    f.rv[c0] = (TV)(st.dt * (st.gam * H + st.zet * Ho - st.alp * gp + st.alp * ph.nu * Ly));
+    f.rv[c0] = (TV)(st.dt * (st.gam * H + st.zet * Ho - st.alp * gp + st.alp * ph.nu * (st.af ? Ly + lap : Ly)));
     f.Hv[c0] = (TV)H;
   }
 
@@ -156,8 +156,13 @@ __global__ void __launch_bounds__(128) k_rhs(Fields<TV> f, Geo g, Metrics mt, Ph
         const double cf = 0.5 * (cc + cyp_);
         Fy_jp = vt * cf - s * D * cf * (Phyp - Ph0) * ihjp;
       }
-      const double H = -((Fx_ip - Fx_i) * idx + (Fy_jp - Fy_j) * idyj + (Fz_kp - Fz_k) * idz);
-      const double Ly = (has_dn ? mt.lo_c[j] * (cym_ - cc) : 0.0) + (has_up ? mt.hi_c[j] * (cyp_ - cc) : 0.0);
+      double H = -((Fx_ip - Fx_i) * idx + (Fy_jp - Fy_j) * idyj + (Fz_kp - Fz_k) * idz);
+      double Ly = (has_dn ? mt.lo_c[j] * (cym_ - cc) : 0.0) + (has_up ? mt.hi_c[j] * (cyp_ - cc) : 0.0);
+      if (st.af) {   // the x/z diffusion leaves H and joins the implicit operator
+        const double lapc = (cxp_ - 2.0 * cc + cxm_) * idx2 + (czp_ - 2.0 * cc + czm_) * idz2;
+        H -= D * lapc;
+        Ly += lapc;
+      }
       double* Hc = ion == 0 ? f.Hcp : f.Hcm;
       double* rc = ion == 0 ? f.rcp : f.rcm;
       const double Ho = Hc[c0];

@@ -219,10 +219,10 @@ __device__ __forceinline__ CellOut<T> rhs_cell(const float* __restrict__ bm, con
     const T lap = fmaT(fmaT(-2.f, u0, uzp) + uzm, k.idz2, (fmaT(-2.f, u0, uxp) + uxm) * k.idx2);
     const T rhom = LO(ACP, XM) - LO(ACM, XM);
     const T fu = (-k.Kx) * fmaT(0.5f, rhom + rho0, q.rho_ref) * dphxm;
-    const T H = fmaT(k.nu, lap, fu) - (ax + ay + az);
+    const T H = fmaT(k.nuH, lap, fu) - (ax + ay + az);
     const T Ly = fmaT(q.hi_c, (UP ? uyp : kw.ut) - u0, q.lo_c * ((DN ? uym : kw.ub) - u0));
     const T gp = (p0 - LO(AP, XM)) * k.idx;
-    o.ru = k.dt * fmaT(k.anu, Ly, fmaT(-k.alp, gp, fmaT(k.gam, H, k.zet * Ho[0])));
+    o.ru = k.dt * fmaT(k.anu, Ly, fmaT(k.anuxz, lap, fmaT(-k.alp, gp, fmaT(k.gam, H, k.zet * Ho[0]))));
     o.Hu = H;
   }
   // w at (x-centre i, y-centre j, z-face k)
@@ -240,10 +240,10 @@ __device__ __forceinline__ CellOut<T> rhs_cell(const float* __restrict__ bm, con
     const T lap = fmaT(fmaT(-2.f, w0, wzp) + wzm, k.idz2, (fmaT(-2.f, w0, wxp) + wxm) * k.idx2);
     const T rhom = LO(ACP, ZM) - LO(ACM, ZM);
     const T fw = (-k.Kz) * fmaT(0.5f, rhom + rho0, q.rho_ref) * dphzm;
-    const T H = fmaT(k.nu, lap, fw) - (ax + ay + az);
+    const T H = fmaT(k.nuH, lap, fw) - (ax + ay + az);
     const T Ly = fmaT(q.hi_c, (UP ? wyp : kw.wt) - w0, q.lo_c * ((DN ? wym : kw.wb) - w0));
     const T gp = (p0 - LO(AP, ZM)) * k.idz;
-    o.rw = k.dt * fmaT(k.anu, Ly, fmaT(-k.alp, gp, fmaT(k.gam, H, k.zet * Ho[1])));
+    o.rw = k.dt * fmaT(k.anu, Ly, fmaT(k.anuxz, lap, fmaT(-k.alp, gp, fmaT(k.gam, H, k.zet * Ho[1]))));
     o.Hw = H;
   }
   // v at (x-centre i, y-face j, z-centre k), 1 <= j <= nyc-1; the centre
@@ -277,10 +277,10 @@ __device__ __forceinline__ CellOut<T> rhs_cell(const float* __restrict__ bm, con
       const T rpf = 0.5f * (rhod + rho0);   // rho' on the face
       const T dphi = ph0 - phym;            // phi' difference
       const T fv = fmaT(-k.K * q.ih, fmaT(q.rhorf, dphi, rpf * (dphi + q.dPref)), q.Fvref);
-      const T H = fmaT(k.nu, lap, fv) - (ax + ay + az);
+      const T H = fmaT(k.nuH, lap, fv) - (ax + ay + az);
       const T Ly = fmaT(q.hi_f, vyp - v0, q.lo_f * (vym - v0));
       const T gp = (p0 - LM(AP, 0)) * q.ih;
-      o.rv = k.dt * fmaT(k.anu, Ly, fmaT(-k.alp, gp, fmaT(k.gam, H, k.zet * Ho[2])));
+      o.rv = k.dt * fmaT(k.anu, Ly, fmaT(k.anuxz, lap, fmaT(-k.alp, gp, fmaT(k.gam, H, k.zet * Ho[2]))));
       o.Hv = H;
     }
     cy.tv = ttop;
@@ -326,8 +326,13 @@ __device__ __forceinline__ CellOut<T> rhs_cell(const float* __restrict__ bm, con
     if (ion == 0) cy.fp = Fy_jp;
     else cy.fm = Fy_jp;
     const T div = fmaT(Fz_kp - Fz_k, k.idz, fmaT(Fy_jp - Fy_j, q.idy, (Fx_ip - Fx_i) * k.idx));
-    const T H = -div;
-    const T r = k.dt * fmaT(k.aD, Ly, fmaT(-k.gam, div, k.zet * Ho[3 + ion]));
+    T H = -div;
+    T r = k.dt * fmaT(k.aD, Ly, fmaT(-k.gam, div, k.zet * Ho[3 + ion]));
+    if (k.af) {   // the x/z diffusion leaves H and joins the implicit operator: r gains dt (alp - gam) D lap
+      const T lapc = fmaT(fmaT(-2.f, cc, czp_) + czm_, k.idz2, (fmaT(-2.f, cc, cxp_) + cxm_) * k.idx2);
+      H = fmaT(-k.D, lapc, H);
+      r = fmaT(k.dt * k.zD, lapc, r);
+    }
     if (ion == 0) {
       o.rcp = r;
       o.Hcp = H;

@@ -1329,6 +1329,85 @@ cudaError_t launch_project(T* u, T* v, T* w, T* p, const T* phip, double scale, 
 }
 
 // ---- explicit instantiations ----
+// ---------------------------------------------------------------------------
+// Periodic x / z sweeps of the approximate factorisation.  A block stages L
+// whole lines of one family in shared memory with coalesced loads (x: L rows
+// of nx contiguous values; z: L adjacent columns of one plane, nz values each,
+// read as L-wide row segments), thread t < L solves line t there (forward
+// elimination, back substitution, Sherman-Morrison correction: the cyclic
+// system's three passes never touch HBM), and the block writes the lines back.
+// ---------------------------------------------------------------------------
+template <typename T, bool ZDIR>
+__global__ void __launch_bounds__(128) k_periodic(PeriodicArgs<T> A, Geo g, int L) {
+  extern __shared__ __align__(16) unsigned char per_smem[];
+  T* tile = reinterpret_cast<T*>(per_smem);
+  const PeriodicFam<T>& F = A.f[blockIdx.y];
+  const int n = ZDIR ? g.nz : g.nx;
+  const int ld = n + 1;
+  const size_t P = (size_t)g.nz * g.nx;
+  // the block's lines: x: rows row0 .. row0 + L - 1 of the family's planes;
+  // z: columns i0 .. i0 + L - 1 of plane j
+  const int blocks_per_plane = ZDIR ? g.nx / L : 0;
+  const int nlines = ZDIR ? F.nplanes * (g.nx / L) : F.nplanes * g.nz / L;
+  if ((int)blockIdx.x >= nlines) return;
+  const int j = ZDIR ? blockIdx.x / blocks_per_plane : 0;
+  const int i0 = ZDIR ? (blockIdx.x % blocks_per_plane) * L : 0;
+  const size_t row0 = ZDIR ? 0 : (size_t)blockIdx.x * L;
+  auto gidx = [&](int line, int pt) -> size_t {
+    return ZDIR ? (size_t)j * P + (size_t)pt * g.nx + i0 + line : (row0 + line) * g.nx + pt;
+  };
+  const int tot = L * n;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int line = ZDIR ? e % L : e / n, pt = ZDIR ? e / L : e % n;
+    tile[line * ld + pt] = F.r[gidx(line, pt)];
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < L) {
+    T* x = tile + threadIdx.x * ld;
+    T d = T(0);
+    for (int i = 0; i < n; ++i) {
+      d = (x[i] - (i ? F.lo * d : T(0))) * F.m[i];
+      x[i] = d;
+    }
+    T y = d;   // y_{n-1} = d_{n-1}
+    const T ylast = y;
+    for (int i = n - 2; i >= 0; --i) {
+      y = x[i] - F.cp[i] * y;
+      x[i] = y;
+    }
+    const T f = (x[0] + F.log * ylast) * F.fac;
+    for (int i = 0; i < n; ++i) x[i] -= f * F.q[i];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int line = ZDIR ? e % L : e / n, pt = ZDIR ? e / L : e % n;
+    F.r[gidx(line, pt)] = tile[line * ld + pt];
+  }
+}
+
+template <typename T>
+cudaError_t launch_periodic(const PeriodicArgs<T>& a, const Geo& g, bool zdir, cudaStream_t s) {
+  const int n = zdir ? g.nz : g.nx;
+  int L = 32;
+  while (L > 1 && (size_t)L * (n + 1) * sizeof(T) > 96 * 1024) L >>= 1;
+  if (zdir && L > g.nx) L = g.nx;
+  if (!zdir && L > g.nz) L = g.nz;
+  const size_t smem = (size_t)L * (n + 1) * sizeof(T);
+  int maxp = 0;
+  for (int q = 0; q < a.nfam; ++q) maxp = a.f[q].nplanes > maxp ? a.f[q].nplanes : maxp;
+  const int nblk = zdir ? maxp * (g.nx / L) : maxp * g.nz / L;
+  auto kern = zdir ? k_periodic<T, true> : k_periodic<T, false>;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<dim3((unsigned)nblk, (unsigned)a.nfam, 1), 128, smem, s>>>(a, g, L);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_periodic<double>(const PeriodicArgs<double>&, const Geo&, bool, cudaStream_t);
+template cudaError_t launch_periodic<float>(const PeriodicArgs<float>&, const Geo&, bool, cudaStream_t);
+
 template cudaError_t launch_cn_solves<double>(const Fields<double>&, const Geo&, const CNRows&, const CNRows&,
                                               const CNRows&, cudaStream_t);
 template cudaError_t launch_cn_solves<float>(const Fields<float>&, const Geo&, const CNRows&, const CNRows&,

@@ -127,6 +127,13 @@ struct pnp_ctx {
   double wall_off = 0.0, V_set = 0.0;           // mean offset; the uniform V of pnp_set_params
   double *wallB_d = nullptr, *wallT_d = nullptr, *lift64 = nullptr;
   float* lift32 = nullptr;
+  // approximate factorisation (x/z implicit): periodic-sweep factors
+  // [3 substages][2 kinds: nu, D][2 dirs: x, z] x {c', m, q} and their scalars
+  int scheme = PNP_SCHEME_CN;
+  double *af_d = nullptr;
+  float* af_f = nullptr;
+  double af_sc[3][2][2][3] = {};
+  double af_dt = NAN;
   // the CN forward elimination fused into the mixed stencil: chunk products G
   // [3 substages][3 kinds][ny] for the dt and chunk length they were made for
   bool fuse_cn = true;
@@ -206,7 +213,11 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
   float* lift32 = b.take<float>(nc);
   double* sacc = b.take<double>(12 * (size_t)ny);
   float* fuseG = b.take<float>(9 * (size_t)ny);
+  double* afd = b.take<double>(36 * (size_t)(nx + nz));
+  float* aff = b.take<float>(36 * (size_t)(nx + nz));
   if (c) {
+    c->af_d = afd;
+    c->af_f = aff;
     c->stats_acc = sacc;
     c->fuseG_d = fuseG;
     c->wallB_d = wB; c->wallT_d = wT; c->lift64 = lift64; c->lift32 = lift32;
@@ -449,13 +460,16 @@ int upload_cn(pnp_ctx* c, double dt) {
   c->cn_dt = dt;
   c->refs_dt = NAN;
   c->fuse_dt = NAN;
+  c->af_dt = NAN;
   return PNP_OK;
 }
 
 // The stencil eliminates forward chunk by chunk (chunk length jc) when the
 // mixed path runs its default policy with the line back substitution.
 bool cn_fused(const pnp_ctx* c, int* jc_out = nullptr) {
-  if (c->precision != PNP_MIXED || c->policy != PNP_POLICY_DEFAULT || !c->fuse_cn || c->g.lc_cn == 32) return false;
+  if (c->precision != PNP_MIXED || c->policy != PNP_POLICY_DEFAULT || !c->fuse_cn || c->g.lc_cn == 32 ||
+      c->scheme == PNP_SCHEME_AF)
+    return false;
   const int jc = mixed_rhs_chunk(c->g, c->rhs_maps_ok);
   if ((c->g.nyc - 1) / jc + 1 > kFusedMaxChunks) return false;
   if (jc_out) *jc_out = jc;
@@ -487,10 +501,109 @@ int upload_fuse(pnp_ctx* c, double dt, int jc) {
   return PNP_OK;
 }
 
-// The factor tables a step of size dt needs (CN rows, fused-chunk products).
+// Offset (in values) of the periodic-sweep factors of (substage l, kind k, dir d).
+size_t af_off(const pnp_ctx* c, int l, int k, int d) {
+  const size_t nx = c->g.nx, nz = c->g.nz;
+  return (size_t)(l * 2 + k) * 3 * (nx + nz) + (d ? 3 * nx : 0);
+}
+
+// Factors of the cyclic systems (I - s L) along x and z, s = alp dt nu / 2 or
+// alp dt D / 2: diagonal 1 + 2 s / h^2, off-diagonals -s / h^2, wrapping.  The
+// Thomas factors of the corner-free system with the two modified end
+// diagonals, the Sherman-Morrison vector q = T^-1 (gam, 0, .., 0, up) and the
+// scalars lo, lo / gam, 1 / (1 + q_0 + (lo / gam) q_{n-1}).
+int upload_af(pnp_ctx* c, double dt) {
+  const size_t tot = 36 * (size_t)(c->g.nx + c->g.nz);
+  std::vector<double> h(tot, 0.0);
+  for (int l = 0; l < 3; ++l) {
+    const double alp = kGam[l] + kZet[l];
+    for (int k = 0; k < 2; ++k) {
+      const double s = 0.5 * alp * dt * (k == 0 ? c->ph.nu : c->ph.D);
+      for (int d = 0; d < 2; ++d) {
+        const int n = d ? c->g.nz : c->g.nx;
+        const double hh = d ? c->g.dz : c->g.dx;
+        const double beta = s / (hh * hh), lo = -beta, up = -beta, di = 1.0 + 2.0 * beta, gam = -di;
+        double* cp = h.data() + af_off(c, l, k, d);
+        double* m = cp + n;
+        double* q = m + n;
+        // forward factors of T (a = lo for i >= 1, b_0 = di - gam, b_{n-1} = di - lo up / gam)
+        double cprev = 0.0;
+        for (int i = 0; i < n; ++i) {
+          const double b = i == 0 ? di - gam : (i == n - 1 ? di - lo * up / gam : di);
+          const double piv = i == 0 ? b : b - lo * cprev;
+          m[i] = 1.0 / piv;
+          cprev = (i < n - 1 ? up : 0.0) * m[i];
+          cp[i] = cprev;
+        }
+        // q = T^-1 u, u = (gam, 0, ..., 0, up)
+        double dd = 0.0;
+        std::vector<double> dv(n);
+        for (int i = 0; i < n; ++i) {
+          const double ui = i == 0 ? gam : (i == n - 1 ? up : 0.0);
+          dd = (ui - (i ? lo * dd : 0.0)) * m[i];
+          dv[i] = dd;
+        }
+        double y = dv[n - 1];
+        q[n - 1] = y;
+        for (int i = n - 2; i >= 0; --i) {
+          y = dv[i] - cp[i] * y;
+          q[i] = y;
+        }
+        c->af_sc[l][k][d][0] = lo;
+        c->af_sc[l][k][d][1] = lo / gam;
+        c->af_sc[l][k][d][2] = 1.0 / (1.0 + q[0] + (lo / gam) * q[n - 1]);
+      }
+    }
+  }
+  std::vector<float> f(tot);
+  for (size_t q = 0; q < tot; ++q) f[q] = (float)h[q];
+  CK(cudaMemcpyAsync(c->af_d, h.data(), sizeof(double) * tot, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->af_f, f.data(), sizeof(float) * tot, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->af_dt = dt;
+  return PNP_OK;
+}
+
+// Periodic sweeps (x, then z) of the approximate factorisation on the CN
+// right-hand sides of substage l: families u, v (interior faces), w (fam bit 1)
+// and c+, c- (fam bit 2), in the context's precision.
+template <typename TR>
+cudaError_t periodic_sweeps(pnp_ctx* c, int l, unsigned fams, TR* ru, TR* rv, TR* rw, TR* rcp, TR* rcm,
+                            cudaStream_t st) {
+  const size_t P = (size_t)c->g.nz * c->g.nx;
+  for (int d = 0; d < 2; ++d) {
+    PeriodicArgs<TR> a{};
+    auto fam = [&](TR* r, int np, int k) {
+      const int n = d ? c->g.nz : c->g.nx;
+      const size_t off = af_off(c, l, k, d);
+      const TR* base = sizeof(TR) == 8 ? (const TR*)(c->af_d + off) : (const TR*)(c->af_f + off);
+      a.f[a.nfam++] = PeriodicFam<TR>{r, np, base, base + n, base + 2 * n, (TR)c->af_sc[l][k][d][0],
+                                      (TR)c->af_sc[l][k][d][1], (TR)c->af_sc[l][k][d][2]};
+    };
+    if (fams & 1u) {
+      fam(ru, c->g.nyc, 0);
+      fam(rv + P, c->g.nyc - 1, 0);
+      fam(rw, c->g.nyc, 0);
+    }
+    if (fams & 2u) {
+      fam(rcp, c->g.nyc, 1);
+      fam(rcm, c->g.nyc, 1);
+    }
+    const cudaError_t e = launch_periodic<TR>(a, c->g, d == 1, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// The factor tables a step of size dt needs (CN rows, fused-chunk products,
+// periodic-sweep factors).
 int prepare_tables(pnp_ctx* c, double dt) {
   if (c->cn_dt != dt) {
     int r = upload_cn(c, dt);
+    if (r) return r;
+  }
+  if (c->scheme == PNP_SCHEME_AF && !(c->af_dt == dt)) {
+    int r = upload_af(c, dt);
     if (r) return r;
   }
   int jc = 0;
@@ -526,6 +639,10 @@ CoefF coef_f(const pnp_ctx* c, const Stage& st, bool keep_h = true) {
   f.anu = f.alp * f.nu;
   f.aD = f.alp * f.D;
   f.keep_h = keep_h ? 1 : 0;
+  f.af = st.af;
+  f.nuH = st.af ? 0.f : f.nu;
+  f.anuxz = st.af ? (float)(st.alp * c->ph.nu) : 0.f;
+  f.zD = st.af ? (float)(st.zet * c->ph.D) : 0.f;
   return f;
 }
 
@@ -755,11 +872,15 @@ cudaError_t poisson_pair(pnp_ctx* c, double scale) {
 
 template <typename TV>
 cudaError_t substage(pnp_ctx* c, double dt, int l) {
-  const Stage st{dt, kGam[l], kZet[l], kGam[l] + kZet[l]};
+  const Stage st{dt, kGam[l], kZet[l], kGam[l] + kZet[l], c->scheme == PNP_SCHEME_AF ? 1 : 0};
   const Fields<TV> f = fields<TV>(c);
   mark(c, c->stream, -1);
   cudaError_t e = launch_rhs<TV>(f, c->g, metrics(c), c->ph, st, c->stream);
   if (e != cudaSuccess) return e;
+  if (st.af) {
+    e = periodic_sweeps<double>(c, l, 3u, (double*)f.ru, (double*)f.rv, (double*)f.rw, f.rcp, f.rcm, c->stream);
+    if (e != cudaSuccess) return e;
+  }
   mark(c, c->stream, PNP_SITE_RHS);
   e = launch_cn_solves<TV>(f, c->g, cn_rows(c, l, 0), cn_rows(c, l, 1), cn_rows(c, l, 2), c->stream);
   if (e != cudaSuccess) return e;
@@ -769,7 +890,7 @@ cudaError_t substage(pnp_ctx* c, double dt, int l) {
 
 // Mixed-precision substage (policy in k_mixed.cu).
 cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
-  const Stage st{dt, kGam[l], kZet[l], kGam[l] + kZet[l]};
+  const Stage st{dt, kGam[l], kZet[l], kGam[l] + kZet[l], c->scheme == PNP_SCHEME_AF ? 1 : 0};
   const Fields<float> f = fields<float>(c);
   const Shadows sh = shadows(c);
   const MixedRefs R = mixed_refs(c);
@@ -787,6 +908,11 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
   const float* Gl = c->fuseG_d + (size_t)l * 3 * ny;
   const CnFusedG G{Gl, Gl + ny, Gl + 2 * ny};
   auto cn = [&](unsigned parts, cudaStream_t s) {
+    if (st.af) {   // the x/z factors first, on the FP32 right-hand sides of these families
+      const cudaError_t ea = periodic_sweeps<float>(c, l, (parts & kCnVelocity ? 1u : 0u) | (parts & kCnIons ? 2u : 0u),
+                                                    f.ru, f.rv, f.rw, (float*)f.rcp, (float*)f.rcm, s);
+      if (ea != cudaSuccess) return ea;
+    }
     if (fp64)
       return launch_mixed_cn_fp64(f, sh, R, c->g, cn_rows(c, l, 0), cn_rows(c, l, 1), cn_rows(c, l, 2), l, parts,
                                   cn_scratch64(c), s);
@@ -1349,6 +1475,14 @@ int pnp_set_wall_potential(pnp_ctx* c, const double* bottom, const double* top) 
     c->refs_valid = false;
   }
   CK(cudaStreamSynchronize(c->stream));
+  return PNP_OK;
+}
+
+int pnp_set_scheme(pnp_ctx* c, int scheme) {
+  if (!c || (scheme != PNP_SCHEME_CN && scheme != PNP_SCHEME_AF)) return PNP_ERR_ARG;
+  if (c->scheme != scheme) drop_graph(c);
+  c->scheme = scheme;
+  c->af_dt = NAN;
   return PNP_OK;
 }
 

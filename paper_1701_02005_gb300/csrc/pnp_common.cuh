@@ -63,7 +63,28 @@ struct Phys {
 // One RK3 substage.
 struct Stage {
   double dt, gam, zet, alp;
+  int af;   // approximate factorisation: x/z viscous / diffusive terms implicit (not in H)
 };
+
+// Periodic (cyclic) tridiagonal sweeps of the approximate factorisation:
+// (I - s L) x = r along x or z with the constant-coefficient periodic second
+// difference, by the Thomas algorithm on the corner-free system and a
+// Sherman-Morrison correction: d_i = (r_i - lo d_{i-1}) m_i, y_i = d_i - c'_i
+// y_{i+1}, x = y - ((y_0 + (lo / gam) y_{n-1}) fac) q.
+template <typename T>
+struct PeriodicFam {
+  T* r;          // right-hand side / solution at the family's first plane
+  int nplanes;   // planes of the family (v: the interior faces)
+  const T *cp, *m, *q;   // [n] factors and the correction vector
+  T lo, log, fac;        // sub-diagonal, lo / gam, 1 / (1 + q_0 + (lo / gam) q_{n-1})
+};
+template <typename T>
+struct PeriodicArgs {
+  PeriodicFam<T> f[5];
+  int nfam;
+};
+template <typename T>
+cudaError_t launch_periodic(const PeriodicArgs<T>& a, const Geo& g, bool zdir, cudaStream_t s);
 
 template <typename TV>
 struct Fields {

@@ -23,6 +23,11 @@ struct CoefF {
   // RK3's last substage: the next step's first substage has zeta = 0 and never
   // reads them); the previous H is read only when zet != 0
   int keep_h;
+  // approximate factorisation (0 = off): x/z viscous / diffusive terms leave H and
+  // join the implicit side: nuH = 0, anuxz = alp nu (momentum r += anuxz lap_xz);
+  // ions H -= D lap_xz c', r += dt zet D lap_xz c'
+  int af;
+  float nuH, anuxz, zD;
 };
 
 // FP32 elimination factors of the velocity Crank-Nicolson matrices.
