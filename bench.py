@@ -55,11 +55,12 @@ NCU_TRAFFIC = {
 }
 
 
-def site_cost(site, precision, launch_cfg=None):
+def site_cost(site, precision, launch_cfg=None, fused=True):
     half = (WL["nx"] // 2 + 1) / WL["nx"]
-    # mixed CN: the shared-memory line tiles (launch code 32) keep the forward
-    # elimination values on chip (76 B per cell); the line kernels write and re-read them (116 B)
-    cn_tiled = launch_cfg is not None and launch_cfg[1] == 32
+    # mixed CN: the back substitution after the stencil's fused forward elimination
+    # (the default) and the shared-memory line tiles (launch code 32) move 76 B per
+    # cell (d in, state in and out); the unfused line kernels also write and re-read d (116 B)
+    cn_tiled = fused or (launch_cfg is not None and launch_cfg[1] == 32)
     if precision == "fp64":
         table = {
             "rhs": (176, 220), "cn_thomas": (200, 20),
@@ -603,6 +604,8 @@ def run_ours(args):
     prec = B.PNP_MIXED if args.precision == "mixed" else B.PNP_FP64
     s = Solver(WL["nx"], WL["ny"], WL["nz"], WL["Lx"], WL["Lz"], stretch=WL["stretch"], precision=prec, device=local)
     s.set_params(WL["Re"], WL["lam"], WL["Sc"], WL["V"], WL["beta"])
+    if args.no_fusion:
+        B.check(B.pnp_set_fusion(s.ctx, 0), "pnp_set_fusion")
     dt = WL["dt"]
     launch_cfg = None
     if not args.no_autotune:
@@ -655,13 +658,13 @@ def run_ours(args):
     hbm_src = "MEASURED_PEAKS.json hbm_gbs (measured copy)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
     sites = {}
     for k, v in per_launch.items():
-        cst = site_cost(k, pname, launch_cfg)
+        cst = site_cost(k, pname, launch_cfg, not args.no_fusion)
         d = v * 1e-3
         gbs = cst["bytes"] * n_cells / d / 1e9
         tf = 2.0 * cst["fp64_ops"] * n_cells / d / 1e12   # FP64 ops counted as FMA-equivalent flops
         sites[k] = {"ms": round(v, 4), "share": round(v / total, 4), "hbm_frac": round(gbs / hbm_peak, 4),
                     "fp64_frac": round(tf / (fp64_peak / 1e12), 4)}
-    cst = site_cost(dom, pname, launch_cfg)
+    cst = site_cost(dom, pname, launch_cfg, not args.no_fusion)
     dur = per_launch[dom] * 1e-3
     hbm_gbs = cst["bytes"] * n_cells / dur / 1e9
     alu_tf = 2.0 * cst["fp64_ops"] * n_cells / dur / 1e12
@@ -787,6 +790,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-fusion", action="store_true",
+                    help="store the CN right-hand sides instead of fusing the forward elimination into the stencil")
     ap.add_argument("--ensemble-steps", type=int, default=20)
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--large-steps", type=int, default=20)

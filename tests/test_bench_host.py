@@ -9,17 +9,19 @@ def test_mixed_byte_model():
     # stencil: 28 B of inputs + 20 B of right-hand sides, plus the previous H
     # (20 B) in two substages of three and the new H (20 B) in two of three
     assert abs(c("rhs") - (28 + 20 + 20 * 2 / 3 + 20 * 2 / 3)) < 1e-12
-    # CN: one thread per line by default (forward values through memory); the
-    # shared-memory tiles (launch code 32) keep them on chip
-    assert c("cn_thomas") == 116 and c("cn_thomas", [64, 32, 32, 16]) == 76
-    assert c("cn_thomas", [64, 64, 32, 16]) == 116
+    # CN: the back substitution after the stencil's fused forward elimination (the
+    # default) and the shared-memory tiles (launch code 32) move 76 B per cell; the
+    # unfused line kernels write and re-read the forward values (116 B)
+    unfused = lambda cfg: bench.site_cost("cn_thomas", "mixed", cfg, False)["bytes"]
+    assert c("cn_thomas") == 76 and c("cn_thomas", [64, 32, 32, 16]) == 76
+    assert unfused([64, 64, 32, 16]) == 116 and unfused([64, 32, 32, 16]) == 76
     # a spectral y-solve: spectrum in / out (8 + 8), df forward values out / in
     # (16 + 16) and the df factors (16) per spectral point
     assert abs(c("p_thomas") - 64 * half) < 1e-12 and abs(c("e_thomas") - 64 * half) < 1e-12
     sites = ("rhs", "cn_thomas", "p_fftx", "p_fftz", "p_thomas", "p_ifftz", "p_ifftx", "project",
              "e_fftx", "e_fftz", "e_thomas", "e_ifftz", "e_ifftx")
     total = sum(c(s) for s in sites)
-    assert 360 < total < 375   # ~368 B per cell and substage with the CN line kernels
+    assert 325 < total < 332   # ~328 B per cell and substage with the fused CN forward elimination
     # the measured stencil traffic is quoted for the default stencil kernel
     nt = bench.NCU_TRAFFIC[("mixed", "rhs")]
     assert nt["shape"] == (0, 64) and nt["cells"] == bench.cells()
