@@ -369,9 +369,10 @@ void pnp_ensemble_destroy(pnp_ensemble* ens);
  * Outputs / labels (5 per row): 0 / 1 the filtered fine wall shear rates
  * d(u_rel)/dy and dw/dy, 2 phi of the first coarse cell, 3 / 4 total counter-
  * / co-ion flux away from the wall through the first interior coarse face.
- * Network: 40 -> 128 -> 128 -> 128 -> 128 -> 5, erf-GELU on hidden layers,
- * BF16 weights in the forward GEMMs with FP32 accumulation, FP32 master
- * weights, Adam; loss = mean squared error of normalised outputs. */
+ * Network: 40 -> 128 -> 128 -> 128 -> 128 -> 5, erf-GELU on hidden layers; every
+ * GEMM (forward, data gradient, weight gradient) on the tensor cores with BF16
+ * operands (weights, activations, output gradients) and FP32 accumulation;
+ * FP32 master weights, Adam; loss = mean squared error of normalised outputs. */
 typedef struct pnp_mlp pnp_mlp;
 int pnp_mlp_param_count(size_t* out_count);
 /* Device workspace for a network that processes up to max_batch rows. */
@@ -396,6 +397,9 @@ int pnp_mlp_forward(pnp_mlp* mlp, const float* X_dev, int B, float* Y_dev);
 int pnp_mlp_gradient(pnp_mlp* mlp, const float* X_dev, const float* T_dev, int B, float* grad_host, float* loss_host);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr. */
 int pnp_mlp_train_step(pnp_mlp* mlp, const float* X_dev, const float* T_dev, int B, float lr, float* loss_host);
+/* Device status of the network's kernels: PNP_OK, or PNP_ERR_TIMEOUT when a
+ * bounded wait for the tensor cores ran out (sticky); synchronises. */
+int pnp_mlp_status(pnp_mlp* mlp);
 void pnp_mlp_destroy(pnp_mlp* mlp);
 
 /* Feature rows of a context's state: X[2 Nz Nx][5 ncells] (ncells <= 8). */

@@ -137,25 +137,32 @@ def _weights(p, bf16):
     return Ws, bs
 
 
-def forward(p, X, norm, bf16=True):
-    """Physical outputs and the cache for backpropagation."""
+def forward(p, X, norm, bf16=True, bf16_act=False):
+    """Physical outputs and the cache for backpropagation.  bf16: the GEMMs use
+    BF16-rounded weights; bf16_act: their activation operands are rounded to
+    BF16 as well (tensor-core GEMMs take both operands in BF16 and accumulate
+    in FP32); biases, GELU and the accumulation stay FP64 here."""
     in_shift, in_scale, out_shift, out_scale = (np.asarray(a, dtype=np.float64) for a in norm)
     Ws, bs = _weights(p, bf16)
     a = (np.asarray(X, dtype=np.float64) - in_shift) * in_scale
     ins, zs = [], []
     for l, (W, b) in enumerate(zip(Ws, bs)):
         x = a if l == 0 else gelu(zs[-1])
+        if bf16_act:
+            x = bf16_round(x)
         ins.append(x)
         zs.append(x @ W.T + b)
     yn = zs[-1]
     return yn / out_scale + out_shift, (ins, zs, Ws)
 
 
-def loss_and_grad(p, X, T, norm, bf16=True):
+def loss_and_grad(p, X, T, norm, bf16=True, bf16_act=False):
     """MSE of normalised outputs and its gradient w.r.t. the parameter vector
-    (w.r.t. the weights the forward pass used)."""
+    (w.r.t. the weights the forward pass used).  bf16_act: the backward GEMMs
+    take the output gradients dz in BF16 as well (the weight gradient pairs
+    them with the BF16 layer inputs; the bias gradient sums them)."""
     _, _, out_shift, out_scale = (np.asarray(a, dtype=np.float64) for a in norm)
-    _, (ins, zs, Ws) = forward(p, X, norm, bf16)
+    _, (ins, zs, Ws) = forward(p, X, norm, bf16, bf16_act)
     tn = (np.asarray(T, dtype=np.float64) - out_shift) * out_scale
     e = zs[-1] - tn
     n = e.size
@@ -165,10 +172,11 @@ def loss_and_grad(p, X, T, norm, bf16=True):
     dz = 2.0 * e / n
     for l in range(len(LAYERS) - 1, -1, -1):
         w, b, fi, fo = sl[l]
-        g[w] = (dz.T @ ins[l]).ravel()
-        g[b] = dz.sum(axis=0)
+        dzo = bf16_round(dz) if bf16_act else dz
+        g[w] = (dzo.T @ ins[l]).ravel()
+        g[b] = dzo.sum(axis=0)
         if l > 0:
-            dz = (dz @ Ws[l]) * gelu_d(zs[l - 1])
+            dz = (dzo @ Ws[l]) * gelu_d(zs[l - 1])
     return loss, g
 
 

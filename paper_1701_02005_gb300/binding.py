@@ -115,6 +115,7 @@ EXPORTS = {
     "pnp_mlp_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_float),
                                    C.POINTER(C.c_float)]),
     "pnp_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.POINTER(C.c_float)]),
+    "pnp_mlp_status": (C.c_int, [C.c_void_p]),
     "pnp_mlp_destroy": (None, [C.c_void_p]),
     "pnp_wall_features": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "pnp_restrict_state": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -210,6 +211,7 @@ pnp_mlp_set_normalization = _fwd("pnp_mlp_set_normalization")
 pnp_mlp_forward = _fwd("pnp_mlp_forward")
 pnp_mlp_gradient = _fwd("pnp_mlp_gradient")
 pnp_mlp_train_step = _fwd("pnp_mlp_train_step")
+pnp_mlp_status = _fwd("pnp_mlp_status")
 pnp_mlp_destroy = _fwd("pnp_mlp_destroy")
 pnp_wall_features = _fwd("pnp_wall_features")
 pnp_restrict_state = _fwd("pnp_restrict_state")

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libpnp.so")
-SOURCES = ["k_rhs.cu", "k_rhs_mixed.cu", "k_solve.cu", "k_misc.cu", "k_mixed.cu", "k_noalloc.cu", "k_wall.cu", "k_mlp.cu", "pnp_api.cu"]
+SOURCES = ["k_rhs.cu", "k_rhs_mixed.cu", "k_solve.cu", "k_misc.cu", "k_mixed.cu", "k_noalloc.cu", "k_wall.cu", "k_mlp.cu", "k_mlp_tc.cu", "pnp_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

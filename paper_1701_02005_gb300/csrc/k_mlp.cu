@@ -1,8 +1,8 @@
 // MLP of the learned wall model: 40 -> 128 -> 128 -> 128 -> 128 -> 5, erf-based
-// GELU on the hidden layers, linear output.  Forward GEMMs use BF16 copies of
-// the weights with FP32 activations and FP32 accumulation; training keeps FP32
-// master weights, computes exact gradients of the mean-squared error of the
-// normalised outputs with respect to the weights the forward pass used, and
+// GELU on the hidden layers, linear output.  The GEMMs run on the tensor cores
+// (k_mlp_tc.cu: BF16 weights and activation operands, FP32 accumulation);
+// training keeps FP32 master weights, forms the gradients of the mean-squared
+// error of the normalised outputs with the same BF16-operand GEMMs, and
 // applies Adam (Kingma & Ba 2015).  Batch reductions (weight gradients, loss)
 // go through per-block partials summed in a fixed order: deterministic.
 // (No counterpart in the paper.)
@@ -33,118 +33,6 @@ MlpDims mlp_dims() {
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_d(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
-}
-
-constexpr int kRB = 32;   // rows per block of the row-parallel GEMMs
-constexpr int kMaxK = 128;
-
-// out[b][n] = sum_k in(b, k) W[n][k] + bias[n]; in = x (layer 0) or gelu(z_prev).
-__global__ void __launch_bounds__(256) k_mlp_fwd(const float* __restrict__ in, int K, bool act_in,
-                                                 const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias,
-                                                 int N, int B, float* __restrict__ out) {
-  extern __shared__ float smem_f[];
-  float* sW = smem_f;                       // [N][K+1]
-  float* sX = smem_f + N * (K + 1);         // [kRB][K+1]
-  const int b0 = blockIdx.x * kRB;
-  for (int t = threadIdx.x; t < N * K; t += blockDim.x) sW[(t / K) * (K + 1) + t % K] = __bfloat162float(W[t]);
-  for (int t = threadIdx.x; t < kRB * K; t += blockDim.x) {
-    const int r = t / K, k = t % K;
-    float x = 0.f;
-    if (b0 + r < B) {
-      x = in[(size_t)(b0 + r) * K + k];
-      if (act_in) x = gelu(x);
-    }
-    sX[r * (K + 1) + k] = x;
-  }
-  __syncthreads();
-  const int r = threadIdx.x % kRB, cg = threadIdx.x / kRB;   // 8 column groups
-  if (b0 + r >= B) return;
-  for (int n = cg; n < N; n += 8) {
-    float acc = bias[n];
-    const float* xw = sX + r * (K + 1);
-    const float* ww = sW + n * (K + 1);
-    for (int k = 0; k < K; ++k) acc = fmaf(xw[k], ww[k], acc);
-    out[(size_t)(b0 + r) * N + n] = acc;
-  }
-}
-
-// da[b][k] = sum_n dz[b][n] W[n][k]; if gate: dz_prev[b][k] = da * gelu'(zprev[b][k]).
-__global__ void __launch_bounds__(256) k_mlp_bwd_data(const float* __restrict__ dz, int N,
-                                                      const __nv_bfloat16* __restrict__ W, int K, int B,
-                                                      const float* __restrict__ zprev, float* __restrict__ out) {
-  extern __shared__ float smem_f[];
-  float* sW = smem_f;                       // [N][K+1]
-  float* sD = smem_f + N * (K + 1);         // [kRB][kMaxK+1]
-  const int b0 = blockIdx.x * kRB;
-  for (int t = threadIdx.x; t < N * K; t += blockDim.x) sW[(t / K) * (K + 1) + t % K] = __bfloat162float(W[t]);
-  for (int t = threadIdx.x; t < kRB * N; t += blockDim.x) {
-    const int r = t / N, n = t % N;
-    sD[r * (kMaxK + 1) + n] = (b0 + r < B) ? dz[(size_t)(b0 + r) * N + n] : 0.f;
-  }
-  __syncthreads();
-  const int r = threadIdx.x % kRB, cg = threadIdx.x / kRB;
-  if (b0 + r >= B) return;
-  for (int k = cg; k < K; k += 8) {
-    float acc = 0.f;
-    const float* dd = sD + r * (kMaxK + 1);
-    for (int n = 0; n < N; ++n) acc = fmaf(dd[n], sW[n * (K + 1) + k], acc);
-    const size_t o = (size_t)(b0 + r) * K + k;
-    out[o] = acc * gelu_d(zprev[o]);
-  }
-}
-
-// Per-block partial weight / bias gradients: partial[blk][n][k] = sum_b dz[b][n] in(b,k),
-// partial[blk][N*K + n] = sum_b dz[b][n].  Rows blk*rows_per_block ...
-constexpr int kWgChunk = 32;
-__global__ void __launch_bounds__(256) k_mlp_wgrad_partial(const float* __restrict__ dz, int N,
-                                                           const float* __restrict__ in, int K, bool act_in, int B,
-                                                           int rows_per_block, float* __restrict__ partial) {
-  __shared__ float sD[kWgChunk * kMaxK];
-  __shared__ float sX[kWgChunk * kMaxK];
-  const int r0 = blockIdx.x * rows_per_block;
-  const int r1 = min(B, r0 + rows_per_block);
-  const int nk = N * K;
-  float acc[64];
-#pragma unroll
-  for (int q = 0; q < 64; ++q) acc[q] = 0.f;
-  float bacc = 0.f;
-  for (int c0 = r0; c0 < r1; c0 += kWgChunk) {
-    const int rows = min(kWgChunk, r1 - c0);
-    __syncthreads();
-    for (int t = threadIdx.x; t < kWgChunk * N; t += blockDim.x) {
-      const int r = t / N, n = t % N;
-      sD[r * N + n] = r < rows ? dz[(size_t)(c0 + r) * N + n] : 0.f;
-    }
-    for (int t = threadIdx.x; t < kWgChunk * K; t += blockDim.x) {
-      const int r = t / K, k = t % K;
-      float x = 0.f;
-      if (r < rows) {
-        x = in[(size_t)(c0 + r) * K + k];
-        if (act_in) x = gelu(x);
-      }
-      sX[r * K + k] = x;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 64; ++q) {
-      const int e = threadIdx.x + q * 256;
-      if (e < nk) {
-        const int n = e / K, k = e % K;
-        float a = acc[q];
-        for (int r = 0; r < rows; ++r) a = fmaf(sD[r * N + n], sX[r * K + k], a);
-        acc[q] = a;
-      }
-    }
-    if (threadIdx.x < N)
-      for (int r = 0; r < rows; ++r) bacc += sD[r * N + threadIdx.x];
-  }
-  float* p = partial + (size_t)blockIdx.x * (nk + N);
-#pragma unroll
-  for (int q = 0; q < 64; ++q) {
-    const int e = threadIdx.x + q * 256;
-    if (e < nk) p[e] = acc[q];
-  }
-  if (threadIdx.x < N) p[nk + threadIdx.x] = bacc;
 }
 
 __global__ void k_mlp_reduce_partial(const float* __restrict__ partial, int nblk, int len, float* __restrict__ gw,
@@ -227,14 +115,6 @@ __global__ void k_mlp_adam(float* __restrict__ p, const float* __restrict__ g, f
 }
 
 // ---------------------------------------------------------------------------
-// Opt the large-tile kernels into more than 48 KB of dynamic shared memory (once per process).
-cudaError_t mlp_prepare() {
-  const int bytes = (int)(sizeof(float) * ((size_t)kMaxK * (kMaxK + 1) + (size_t)kRB * (kMaxK + 1)));
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_mlp_bwd_data, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
-
 cudaError_t mlp_sync_bf16(const MlpBufs& b, size_t nparam, cudaStream_t s) {
   k_mlp_to_bf16<<<(unsigned)((nparam + 255) / 256), 256, 0, s>>>(b.param, b.wbf, nparam);
   return cudaGetLastError();
@@ -244,11 +124,12 @@ cudaError_t mlp_forward(const MlpBufs& b, const float* X, int B, float* Y, cudaS
   const MlpDims d = mlp_dims();
   const size_t ni = (size_t)B * kMlpIn;
   k_mlp_norm_in<<<(unsigned)((ni + 255) / 256), 256, 0, s>>>(X, B, b.in_shift, b.in_scale, b.act[0]);
-  const unsigned nb = (unsigned)((B + kRB - 1) / kRB);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   for (int l = 0; l < kMlpLayers; ++l) {
-    const size_t sm = sizeof(float) * ((size_t)d.out[l] * (d.in[l] + 1) + (size_t)kRB * (d.in[l] + 1));
-    k_mlp_fwd<<<nb, 256, sm, s>>>(b.act[l], d.in[l], l > 0, b.wbf + d.woff[l], b.param + d.boff[l], d.out[l], B,
-                                  b.act[l + 1]);
+    e = mlp_fwd_layer_tc(b.act[l], d.in[l], l > 0, b.wbf + d.woff[l], b.param + d.boff[l], d.out[l], B, b.act[l + 1],
+                         b.err, s);
+    if (e != cudaSuccess) return e;
   }
   if (Y) {
     const size_t no = (size_t)B * kMlpOut;
@@ -263,20 +144,22 @@ cudaError_t mlp_backward(const MlpBufs& b, const float* T, int B, int max_partia
   const int nloss = 120;
   k_mlp_loss<<<nloss, 256, 0, s>>>(b.act[kMlpLayers], T, B, b.out_shift, b.out_scale, b.dact, b.loss);
   k_mlp_loss_final<<<1, 32, 0, s>>>(b.loss, nloss);
+  // rows per weight-gradient CTA: a multiple of the tensor-core chunk (64 rows)
   int rows_per_block = (B + max_partial - 1) / max_partial;
-  rows_per_block = (rows_per_block + kWgChunk - 1) / kWgChunk * kWgChunk;
+  rows_per_block = (rows_per_block + 63) / 64 * 64;
   const int nblk = (B + rows_per_block - 1) / rows_per_block;
   float* dz = b.dact;
   float* other = b.dact2;
   for (int l = kMlpLayers - 1; l >= 0; --l) {
     const int N = d.out[l], K = d.in[l];
-    k_mlp_wgrad_partial<<<nblk, 256, 0, s>>>(dz, N, b.act[l], K, l > 0, B, rows_per_block, b.partial);
+    cudaError_t e = mlp_wgrad_tc(dz, N, b.act[l], K, l > 0, B, rows_per_block, nblk, b.partial, b.err, s);
+    if (e != cudaSuccess) return e;
     const int len = N * K + N;
     k_mlp_reduce_partial<<<(len + 255) / 256, 256, 0, s>>>(b.partial, nblk, len, b.grad + d.woff[l],
                                                            b.grad + d.boff[l], N * K);
     if (l > 0) {
-      const size_t sm = sizeof(float) * ((size_t)N * (K + 1) + (size_t)kRB * (kMaxK + 1));
-      k_mlp_bwd_data<<<(unsigned)((B + kRB - 1) / kRB), 256, sm, s>>>(dz, N, b.wbf + d.woff[l], K, B, b.act[l], other);
+      e = mlp_bwd_data_tc(dz, N, b.wbf + d.woff[l], K, B, b.act[l], other, b.err, s);
+      if (e != cudaSuccess) return e;
       float* t = dz;
       dz = other;
       other = t;

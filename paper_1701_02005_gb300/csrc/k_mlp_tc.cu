@@ -1,0 +1,410 @@
+// Tensor-core GEMMs of the wall-model MLP (no counterpart in the paper):
+// tcgen05.mma (kind::f16, BF16 operands, FP32 accumulation in tensor memory)
+// issued by one thread per CTA on operand tiles staged in shared memory.
+//
+//   forward      z[b][n]  = sum_k a(b, k) W[n][k] + bias[n],  a = x_n or GELU(z_prev)
+//   data grad    da[b][k] = (sum_n dz[b][n] W[n][k]) GELU'(z_prev[b][k])
+//   weight grad  dW[n][k] = sum_b dz[b][n] a(b, k),  dbias[n] = sum_b dz[b][n]
+//
+// Every GEMM is D[M = 128][N] += A[128][K] B[N][K]^T with both operands
+// K-major: a CTA owns 128 rows of D (one per thread of its four warps, which is
+// also the TMEM lane each warp may read), stages A and B as BF16 in the
+// canonical no-swizzle layout (8-row x 16-byte core matrices, the K groups
+// outermost), and one thread issues K/16 MMAs whose completion it commits to
+// an mbarrier; the warps then read their 32 accumulator lanes with tcgen05.ld.
+// The weight gradient reduces over the batch: its M is the layer's outputs,
+// its N the layer's inputs plus a column of ones (the bias gradient), and its K
+// runs over the CTA's batch rows in 64-row chunks accumulated in TMEM.  Waits
+// are bounded: on a timeout a kernel records PNP_ERR_TIMEOUT, waits once more
+// (bounded) for its MMAs, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "pnp_common.cuh"
+#include "pnp_wall.cuh"
+
+namespace pnp {
+
+namespace {
+
+constexpr int kTcRows = 128;      // rows of D per CTA (M of every MMA)
+constexpr int kTcThreads = 128;   // four warps: warp w reads TMEM lanes 32w .. 32w + 31
+constexpr int kWgK = 64;          // batch rows per weight-gradient chunk (four MMAs of K = 16)
+constexpr unsigned long long kTcWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ float gelu_tc(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d_tc(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+// Byte offset of element (r, k) of an R-row K-major tile: core matrix (r / 8,
+// k / 8) of 8 rows x 16 bytes, K groups outermost, so the core matrices
+// adjacent in K are R/8 * 128 bytes apart (the leading-dimension offset) and
+// those adjacent in M/N 128 bytes (the stride-dimension offset).
+__device__ __forceinline__ uint32_t canon(int r, int k, int R) {
+  return (uint32_t)((((k >> 3) * (R >> 3) + (r >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+// Shared-memory matrix descriptor: start address, leading- and stride-
+// dimension byte offsets (each >> 4), the fixed version bits 0b001 at 46-48,
+// no base offset, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t start, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((start >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 at bits
+// 17-22, M / 16 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// the generic-proxy writes of the staged tiles become visible to the tensor cores
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// one full warp; the address lands in *slot
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 16 consecutive FP32 accumulator columns of this thread's lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void mbar_init1(unsigned long long* b) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(b)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(saddr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait for the phase with this parity to complete
+__device__ __forceinline__ bool mbar_wait_tc(unsigned long long* b, unsigned parity) {
+  if (mbar_test(b, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  for (int it = 0; it < (1 << 26); ++it) {
+    if (mbar_test(b, parity)) return true;
+    if ((it & 255) == 0 && now_ns() - t0 > kTcWaitNs) break;
+  }
+  return false;
+}
+
+__device__ __forceinline__ uint32_t tmem_cols(int n) {
+  uint32_t c = 32;
+  while ((int)c < n) c <<= 1;
+  return c;
+}
+
+// The shared tail of every kernel: K / 16 MMAs on the staged tiles (thread 0),
+// the bounded wait for their completion (phase `parity`), true when it came.
+__device__ __forceinline__ bool mma_tiles(uint32_t tmem, const __nv_bfloat16* sA, const __nv_bfloat16* sB, int N,
+                                          int Kdim, bool accumulate, unsigned long long* bar, unsigned parity) {
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (threadIdx.x == 0) {
+    const uint32_t lboA = (kTcRows / 8) * 128, lboB = (uint32_t)(N / 8) * 128;
+    const uint32_t id = idesc_bf16(kTcRows, N);
+    for (int s = 0; s < Kdim / 16; ++s) {
+      const uint64_t a = sdesc(saddr(sA) + 2 * s * lboA, lboA, 128);
+      const uint64_t b = sdesc(saddr(sB) + 2 * s * lboB, lboB, 128);
+      mma_bf16(tmem, a, b, id, (accumulate || s > 0) ? 1u : 0u);
+    }
+    mma_commit(bar);
+  }
+  const bool ok = __syncthreads_and(mbar_wait_tc(bar, parity)) != 0;   // uniform across the CTA
+  fence_after();
+  return ok;
+}
+
+// Shared memory: A [128][K] and B [N][K] BF16 tiles, an mbarrier and the TMEM slot.
+struct TcSmem {
+  __nv_bfloat16* A;
+  __nv_bfloat16* B;
+  unsigned long long* bar;
+  uint32_t* slot;
+};
+__device__ __forceinline__ TcSmem tc_smem(unsigned char* base, int Kdim, int N) {
+  TcSmem t;
+  t.A = reinterpret_cast<__nv_bfloat16*>(base);
+  t.B = t.A + (size_t)kTcRows * Kdim;
+  unsigned char* tail = reinterpret_cast<unsigned char*>(t.B + (size_t)N * Kdim);
+  tail = reinterpret_cast<unsigned char*>(((uintptr_t)tail + 15) & ~(uintptr_t)15);
+  t.bar = reinterpret_cast<unsigned long long*>(tail);
+  t.slot = reinterpret_cast<uint32_t*>(tail + 8);
+  return t;
+}
+__host__ __device__ inline size_t tc_smem_bytes(int Kdim, int N) {
+  return ((size_t)kTcRows * Kdim + (size_t)N * Kdim) * 2 + 16 + 16;
+}
+
+__device__ __forceinline__ void set_bf16(__nv_bfloat16* tile, uint32_t off, float x) {
+  *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(tile) + off) = __float2bfloat16_rn(x);
+}
+
+// Failure path: record the timeout and give the MMAs one more bounded wait
+// before the tensor memory is freed.
+__device__ __forceinline__ void tc_timeout(int* err, unsigned long long* bar, unsigned parity) {
+  if (threadIdx.x == 0) {
+    atomicExch(err, PNP_ERR_TIMEOUT);
+    mbar_wait_tc(bar, parity);
+  }
+}
+
+}  // namespace
+
+// z[b][n] = sum_k a(b, k) W[n][k] + bias[n] for the CTA's 128 rows; Kp, Np: K, N rounded up to 16.
+__global__ void __launch_bounds__(kTcThreads) k_mlp_fwd_tc(const float* __restrict__ in, int K, int act_in,
+                                                           const __nv_bfloat16* __restrict__ W,
+                                                           const float* __restrict__ bias, int N, int B,
+                                                           float* __restrict__ out, int* err) {
+  extern __shared__ __align__(128) unsigned char tc_raw[];
+  const int Kp = (K + 15) & ~15, Np = (N + 15) & ~15;
+  const TcSmem s = tc_smem(tc_raw, Kp, Np);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t ncols = tmem_cols(Np);
+  if (warp == 0) tmem_alloc(s.slot, ncols);
+  if (tid == 0) mbar_init1(s.bar);
+  const int b = blockIdx.x * kTcRows + tid;
+  for (int k = 0; k < Kp; ++k) {
+    float x = 0.f;
+    if (b < B && k < K) {
+      x = in[(size_t)b * K + k];
+      if (act_in) x = gelu_tc(x);
+    }
+    set_bf16(s.A, canon(tid, k, kTcRows), x);
+  }
+  for (int e = tid; e < Np * Kp; e += kTcThreads) {
+    const int n = e / Kp, k = e - n * Kp;
+    const float wv = (n < N && k < K) ? __bfloat162float(W[(size_t)n * K + k]) : 0.f;
+    set_bf16(s.B, canon(n, k, Np), wv);
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *s.slot;
+  if (mma_tiles(tmem, s.A, s.B, Np, Kp, false, s.bar, 0)) {
+    const uint32_t lane = tmem + ((uint32_t)(32 * warp) << 16);
+    for (int c0 = 0; c0 < Np; c0 += 16) {
+      float v[16];
+      tmem_ld16(lane + c0, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int n = c0 + i;
+        if (b < B && n < N) out[(size_t)b * N + n] = v[i] + bias[n];
+      }
+    }
+  } else {
+    tc_timeout(err, s.bar, 0);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+// da[b][k] = (sum_n dz[b][n] W[n][k]) GELU'(zprev[b][k]): A = dz [128][Np], B = W^T [Kq][Np].
+__global__ void __launch_bounds__(kTcThreads) k_mlp_bwd_data_tc(const float* __restrict__ dz, int N,
+                                                                const __nv_bfloat16* __restrict__ W, int K, int B,
+                                                                const float* __restrict__ zprev,
+                                                                float* __restrict__ out, int* err) {
+  extern __shared__ __align__(128) unsigned char tc_raw[];
+  const int Np = (N + 15) & ~15, Kq = (K + 15) & ~15;
+  const TcSmem s = tc_smem(tc_raw, Np, Kq);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t ncols = tmem_cols(Kq);
+  if (warp == 0) tmem_alloc(s.slot, ncols);
+  if (tid == 0) mbar_init1(s.bar);
+  const int b = blockIdx.x * kTcRows + tid;
+  for (int n = 0; n < Np; ++n) {
+    const float g = (b < B && n < N) ? dz[(size_t)b * N + n] : 0.f;
+    set_bf16(s.A, canon(tid, n, kTcRows), g);
+  }
+  for (int e = tid; e < Kq * Np; e += kTcThreads) {
+    const int n = e / Kq, k = e - n * Kq;   // consecutive threads read consecutive W[n][k]
+    const float wv = (n < N && k < K) ? __bfloat162float(W[(size_t)n * K + k]) : 0.f;
+    set_bf16(s.B, canon(k, n, Kq), wv);
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *s.slot;
+  if (mma_tiles(tmem, s.A, s.B, Kq, Np, false, s.bar, 0)) {
+    const uint32_t lane = tmem + ((uint32_t)(32 * warp) << 16);
+    for (int c0 = 0; c0 < Kq; c0 += 16) {
+      float v[16];
+      tmem_ld16(lane + c0, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int k = c0 + i;
+        if (b < B && k < K) {
+          const size_t o = (size_t)b * K + k;
+          out[o] = v[i] * gelu_d_tc(zprev[o]);
+        }
+      }
+    }
+  } else {
+    tc_timeout(err, s.bar, 0);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+// Per-CTA partial weight and bias gradients over rows [blk r, min(B, (blk+1) r)):
+// D[n][k] = sum_b dz[b][n] a(b, k) (k < K), D[n][K] = sum_b dz[b][n]; the batch
+// is the K of the MMAs, in 64-row chunks accumulated in TMEM.  partial[blk] =
+// [N][K] weights, then [N] biases.
+__global__ void __launch_bounds__(kTcThreads) k_mlp_wgrad_tc(const float* __restrict__ dz, int N,
+                                                             const float* __restrict__ in, int K, int act_in, int B,
+                                                             int rows_per_block, float* __restrict__ partial,
+                                                             int* err) {
+  extern __shared__ __align__(128) unsigned char tc_raw[];
+  const int Nw = ((K + 1) + 15) & ~15;   // inputs and the ones column of the bias
+  const TcSmem s = tc_smem(tc_raw, kWgK, Nw);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t ncols = tmem_cols(Nw);
+  if (warp == 0) tmem_alloc(s.slot, ncols);
+  if (tid == 0) mbar_init1(s.bar);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *s.slot;
+  const int r0 = blockIdx.x * rows_per_block, r1 = min(B, r0 + rows_per_block);
+  bool ok = true;
+  unsigned phase = 0;
+  for (int c0 = r0; c0 < r1 && ok; c0 += kWgK, phase ^= 1u) {
+    const int rows = min(kWgK, r1 - c0);
+    if (c0 > r0) {   // the previous chunk's MMAs read the tiles until their commit arrived
+      fence_before();
+      __syncthreads();
+    }
+    for (int e = tid; e < kTcRows * kWgK; e += kTcThreads) {
+      const int n = e / kWgK, bb = e - n * kWgK;
+      const float g = (n < N && bb < rows) ? dz[(size_t)(c0 + bb) * N + n] : 0.f;
+      set_bf16(s.A, canon(n, bb, kTcRows), g);
+    }
+    for (int e = tid; e < Nw * kWgK; e += kTcThreads) {
+      const int k = e / kWgK, bb = e - k * kWgK;
+      float x = 0.f;
+      if (bb < rows) {
+        if (k < K) {
+          x = in[(size_t)(c0 + bb) * K + k];
+          if (act_in) x = gelu_tc(x);
+        } else if (k == K) {
+          x = 1.f;
+        }
+      }
+      set_bf16(s.B, canon(k, bb, Nw), x);
+    }
+    ok = mma_tiles(tmem, s.A, s.B, Nw, kWgK, c0 > r0, s.bar, phase);
+  }
+  float* p = partial + (size_t)blockIdx.x * ((size_t)N * K + N);
+  if (ok && r0 < r1) {
+    const uint32_t lane = tmem + ((uint32_t)(32 * warp) << 16);
+    const int n = tid;   // this thread's TMEM lane is output row n
+    for (int c0 = 0; c0 < Nw; c0 += 16) {
+      float v[16];
+      tmem_ld16(lane + c0, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int k = c0 + i;
+        if (n < N && k < K) p[(size_t)n * K + k] = v[i];
+        else if (n < N && k == K) p[(size_t)N * K + n] = v[i];
+      }
+    }
+  } else if (!ok) {
+    tc_timeout(err, s.bar, phase ^ 1u);
+  } else {   // no rows: zero partials
+    for (int e = tid; e < N * K + N; e += kTcThreads) p[e] = 0.f;
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+// ---- launchers ----
+// Dynamic shared memory of at least 80 KB per CTA keeps at most two CTAs (and
+// at most 2 x 256 tensor-memory columns) on an SM, so an allocation never waits
+// for a CTA that is not running.
+constexpr size_t kTcMinSmem = 80 * 1024;
+
+template <typename Kern, typename... Args>
+cudaError_t tc_launch(Kern kern, unsigned grid, size_t smem_need, cudaStream_t s, Args... args) {
+  const size_t smem = smem_need > kTcMinSmem ? smem_need : kTcMinSmem;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kTcThreads, smem, s>>>(args...);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_fwd_layer_tc(const float* in, int K, bool act_in, const __nv_bfloat16* W, const float* bias, int N,
+                             int B, float* out, int* err, cudaStream_t s) {
+  if (K > 256 || N > 256) return cudaErrorInvalidValue;
+  const int Kp = (K + 15) & ~15, Np = (N + 15) & ~15;
+  return tc_launch(k_mlp_fwd_tc, (unsigned)((B + kTcRows - 1) / kTcRows), tc_smem_bytes(Kp, Np), s, in, K,
+                   act_in ? 1 : 0, W, bias, N, B, out, err);
+}
+
+cudaError_t mlp_bwd_data_tc(const float* dz, int N, const __nv_bfloat16* W, int K, int B, const float* zprev,
+                            float* out, int* err, cudaStream_t s) {
+  if (K > 256 || N > 256) return cudaErrorInvalidValue;
+  const int Np = (N + 15) & ~15, Kq = (K + 15) & ~15;
+  return tc_launch(k_mlp_bwd_data_tc, (unsigned)((B + kTcRows - 1) / kTcRows), tc_smem_bytes(Np, Kq), s, dz, N, W,
+                   K, B, zprev, out, err);
+}
+
+cudaError_t mlp_wgrad_tc(const float* dz, int N, const float* in, int K, bool act_in, int B, int rows_per_block,
+                         int nblk, float* partial, int* err, cudaStream_t s) {
+  if (N > kTcRows || K + 1 > 256) return cudaErrorInvalidValue;
+  const int Nw = ((K + 1) + 15) & ~15;
+  return tc_launch(k_mlp_wgrad_tc, (unsigned)nblk, tc_smem_bytes(kWgK, Nw), s, dz, N, in, K, act_in ? 1 : 0, B,
+                   rows_per_block, partial, err);
+}
+
+}  // namespace pnp

@@ -2167,6 +2167,7 @@ size_t mlp_carve(pnp_mlp* m, char* base, int max_batch) {
   b.in_scale = bp.take<float>(kMlpIn);
   b.out_shift = bp.take<float>(kMlpOut);
   b.out_scale = bp.take<float>(kMlpOut);
+  b.err = bp.take<int>(4);
   if (m) {
     m->b = b;
     m->nparam = np;
@@ -2218,7 +2219,6 @@ int pnp_mlp_create(pnp_mlp** out, int max_batch, void* ws, size_t bytes, void* s
   m->max_batch = max_batch;
   m->stream = (cudaStream_t)stream;
   mlp_carve(m, (char*)ws, max_batch);
-  if (mlp_prepare() != cudaSuccess) { delete m; return PNP_ERR_CUDA; }
   // weights U(-a, a), a = sqrt(6 / fan_in) from SplitMix64; biases 0; unit normalisation
   const MlpDims d = mlp_dims();
   std::vector<float> p(d.nparam, 0.f);
@@ -2297,6 +2297,14 @@ int pnp_mlp_train_step(pnp_mlp* m, const float* X, const float* T, int B, float 
     CK(cudaStreamSynchronize(m->stream));
   }
   return PNP_OK;
+}
+
+int pnp_mlp_status(pnp_mlp* m) {
+  if (!m) return PNP_ERR_ARG;
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, m->b.err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  return st;
 }
 
 void pnp_mlp_destroy(pnp_mlp* m) { delete m; }

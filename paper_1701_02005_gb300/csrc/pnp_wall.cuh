@@ -56,9 +56,17 @@ struct MlpBufs {
   float* partial;      // per-block partial weight gradients
   float* loss;         // [partial blocks] then the reduced loss
   float *in_shift, *in_scale, *out_shift, *out_scale;
+  int* err;            // device status word (PNP_ERR_TIMEOUT from a bounded tensor-core wait)
 };
 
-cudaError_t mlp_prepare();
+// Tensor-core (tcgen05) GEMMs of the MLP (k_mlp_tc.cu).
+cudaError_t mlp_fwd_layer_tc(const float* in, int K, bool act_in, const __nv_bfloat16* W, const float* bias, int N,
+                             int B, float* out, int* err, cudaStream_t s);
+cudaError_t mlp_bwd_data_tc(const float* dz, int N, const __nv_bfloat16* W, int K, int B, const float* zprev,
+                            float* out, int* err, cudaStream_t s);
+cudaError_t mlp_wgrad_tc(const float* dz, int N, const float* in, int K, bool act_in, int B, int rows_per_block,
+                         int nblk, float* partial, int* err, cudaStream_t s);
+
 cudaError_t mlp_sync_bf16(const MlpBufs& b, size_t nparam, cudaStream_t s);
 cudaError_t mlp_forward(const MlpBufs& b, const float* X, int B, float* Y, cudaStream_t s);
 cudaError_t mlp_backward(const MlpBufs& b, const float* T, int B, int max_partial, cudaStream_t s);

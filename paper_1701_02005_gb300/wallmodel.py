@@ -77,6 +77,10 @@ class MLP:
                                      float(lr), C.byref(loss) if want_loss else None), "pnp_mlp_train_step")
         return float(loss.value) if want_loss else None
 
+    def status(self):
+        """Device status of the network's kernels (PNP_ERR_TIMEOUT if a tensor-core wait ran out)."""
+        return int(B.pnp_mlp_status(self.m))
+
     def close(self):
         if getattr(self, "m", None):
             self.stream.synchronize()

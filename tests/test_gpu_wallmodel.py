@@ -77,17 +77,26 @@ def test_mlp_forward_and_gradient_match_oracle():
     X = r.standard_normal((200, 40)).astype(np.float32)
     T = r.standard_normal((200, 5)).astype(np.float32)
     Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    # the tensor-core GEMMs take weights and activation operands in BF16 and
+    # accumulate in FP32: against the oracle's BF16-operand reading the results
+    # differ by the FP32 accumulation order and by the rare operand whose BF16
+    # rounding flips between the two GELU evaluations (one BF16 ulp, 2^-8)
     Y = net.forward(Xd).cpu().numpy()
-    Yr, _ = w.forward(p, X, norm, bf16=True)
+    Yr, _ = w.forward(p, X, norm, bf16=True, bf16_act=True)
     Yr = np.clip((Yr - norm[2]) * norm[3], -6, 6) / norm[3] + norm[2]   # inference path clips at 6 sigma
-    assert np.max(np.abs(Y - Yr)) <= 1e-5 * np.max(np.abs(Yr))
+    assert np.max(np.abs(Y - Yr)) <= 2e-3 * np.max(np.abs(Yr)), np.max(np.abs(Y - Yr)) / np.max(np.abs(Yr))
+    Yx, _ = w.forward(p, X, norm, bf16=True)
+    Yx = np.clip((Yx - norm[2]) * norm[3], -6, 6) / norm[3] + norm[2]
+    assert np.max(np.abs(Y - Yx)) <= 3e-2 * np.max(np.abs(Yx))   # and to BF16 accuracy of the FP32-operand net
     g, loss = net.gradient(Xd, Td)
-    lr, gr = w.loss_and_grad(p, X, T, norm, bf16=True)
-    assert abs(loss - lr) <= 1e-5 * lr
+    lr, gr = w.loss_and_grad(p, X, T, norm, bf16=True, bf16_act=True)
+    assert abs(loss - lr) <= 2e-3 * lr, (loss, lr)
     sl, _ = w.param_slices()
     for ws, bs, _, _ in sl:
         for s_ in (ws, bs):
-            assert np.max(np.abs(g[s_] - gr[s_])) <= 1e-4 * np.max(np.abs(gr[s_])) + 1e-9
+            err = np.max(np.abs(g[s_] - gr[s_])) / (np.max(np.abs(gr[s_])) + 1e-12)
+            assert err <= 5e-3, err
+    assert net.status() == 0
     net.close()
 
 

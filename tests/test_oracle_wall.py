@@ -247,3 +247,32 @@ def test_flux_labels_of_linear_profiles_have_closed_forms():
     bot, top = labels(1.5 * ones, 0.5 * ones, 0.0 * ones, v0=0.05)
     assert np.allclose(bot[:, 3], 0.05 * 1.5, rtol=1e-12) and np.allclose(bot[:, 4], 0.05 * 0.5, rtol=1e-12)
     assert np.allclose(top[:, 3], -0.05 * 0.5, rtol=1e-12) and np.allclose(top[:, 4], -0.05 * 1.5, rtol=1e-12)
+
+
+def test_bf16_operand_reading_is_exact_on_representable_values():
+    # with weights, inputs and every intermediate GEMM operand exactly
+    # representable in BF16 the BF16-operand reading equals the exact network;
+    # on random values it differs by the BF16 rounding of the operands only
+    _, total = w.param_slices()
+    p = np.zeros(total)
+    sl, _ = w.param_slices()
+    r = seeded.rng(11)
+    for ws, bs, fi, fo in sl:   # weights k / 8 (k small), zero biases
+        p[ws] = r.integers(-2, 3, size=ws.stop - ws.start) / 8.0
+    X = r.integers(-2, 3, size=(6, 40)).astype(np.float64)
+    norm = (np.zeros(40), np.ones(40), np.zeros(5), np.ones(5))
+    # the first layer's pre-activations are small integers / 8: representable;
+    # GELU of them is not, so compare only the first layer's GEMM
+    _, (ins_a, zs_a, _) = w.forward(p, X, norm, bf16=True, bf16_act=True)
+    _, (ins_b, zs_b, _) = w.forward(p, X, norm, bf16=True, bf16_act=False)
+    assert np.array_equal(zs_a[0], zs_b[0])
+    # random values: the two readings agree to the BF16 operand rounding
+    p2 = 0.1 * r.standard_normal(total)
+    X2 = r.standard_normal((20, 40))
+    ya, _ = w.forward(p2, X2, norm, bf16=True, bf16_act=True)
+    yb, _ = w.forward(p2, X2, norm, bf16=True, bf16_act=False)
+    rel = np.max(np.abs(ya - yb)) / np.max(np.abs(yb))
+    assert 0 < rel < 3e-2, rel
+    la, ga = w.loss_and_grad(p2, X2, X2[:, :5], norm, bf16=True, bf16_act=True)
+    lb, gb = w.loss_and_grad(p2, X2, X2[:, :5], norm, bf16=True, bf16_act=False)
+    assert abs(la - lb) <= 3e-2 * lb and np.max(np.abs(ga - gb)) <= 5e-2 * np.max(np.abs(gb))
