@@ -49,9 +49,10 @@ def cells(wl=WL):
 # 256x193x256, from the one-pass ncu capture summarised under profiles/
 # (shape = the stencil's tuned launch code the capture ran with)
 NCU_TRAFFIC = {
-    # mean of three consecutive launches (one per RK3 substage), launch code 0 / 32
-    ("mixed", "rhs"): {"kernel": "k_rhs_mixed_tile<64, 4, 2, false, 2>", "shape": (0, 64), "cells": 12582912,
-                       "bytes": 912572587},
+    # mean of three consecutive launches (one per RK3 substage) of the stencil with
+    # the fused CN forward elimination, launch code 0 / 64
+    ("mixed", "rhs"): {"kernel": "k_rhs_mixed_tile<64, 4, 2, false, 2> (fused CN forward elimination)",
+                       "shape": (0, 64), "cells": 12582912, "bytes": 913655040},
 }
 
 
