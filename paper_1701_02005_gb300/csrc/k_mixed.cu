@@ -467,7 +467,8 @@ struct FusedArgs {
   size_t P;
 };
 
-__global__ void k_cn_backsub_fused(FusedArgs A, int fam0) {
+template <bool ION>
+__global__ void __launch_bounds__(128) k_cn_backsub_fused(FusedArgs A, int fam0) {
   constexpr int CH = 8;
   const FusedFam& F = A.f[fam0 + blockIdx.y];
   const size_t P = A.P;
@@ -476,7 +477,7 @@ __global__ void k_cn_backsub_fused(FusedArgs A, int fam0) {
   const int n = F.n, j0 = F.j0, jc = A.jc;
   const float* d = F.d + line;
   float* S = F.S + line;
-  float* L = F.L ? F.L + line : nullptr;
+  float* L = ION ? F.L + line : nullptr;
   // chunk ch holds rows [max(ch jc - j0, 0), min((ch + 1) jc - j0, n))
   const int nch = (n - 1 + j0) / jc + 1;
   float dend[kFusedMaxChunks];
@@ -490,8 +491,12 @@ __global__ void k_cn_backsub_fused(FusedArgs A, int fam0) {
       dend[ch] = dp;
     }
   }
+  // back substitution from the top; the true d of the chunk below the current
+  // row changes only when the sweep crosses into the next chunk down
   float x = 0.f;
   int ch = nch - 1;
+  int first = max(ch * jc - j0, 0);
+  float dprev = ch > 0 ? dend[ch - 1] : 0.f;
   for (int jb = n - 1; jb >= 0; jb -= CH) {
     float dd[CH], sh[CH], sl[CH];
 #pragma unroll
@@ -500,17 +505,20 @@ __global__ void k_cn_backsub_fused(FusedArgs A, int fam0) {
         const size_t o = (size_t)(jb - k) * P;
         dd[k] = d[o];
         sh[k] = S[o];
-        sl[k] = L ? L[o] : 0.f;
+        if (ION) sl[k] = L[o];
       }
 #pragma unroll
     for (int k = 0; k < CH; ++k) {
       const int r = jb - k;
       if (r >= 0) {
-        while (ch > 0 && r + j0 < ch * jc) --ch;
-        const float dprev = ch > 0 ? dend[ch - 1] : 0.f;
+        if (r < first) {
+          --ch;
+          first = max(ch * jc - j0, 0);
+          dprev = ch > 0 ? dend[ch - 1] : 0.f;
+        }
         x = fmaf(F.G[r], dprev, dd[k]) - F.c[r] * x;
         const size_t o = (size_t)r * P;
-        if (L) {
+        if (ION) {
           const float2 inc = F.add[r];
           const dfl cv = df_add2(dfl{sh[k], sl[k]}, dfl{inc.x, inc.y}, x);
           S[o] = cv.h;
@@ -540,12 +548,12 @@ cudaError_t launch_mixed_cn_fused(const Fields<float>& f, const Shadows& sh, con
                     g.nyc, 0};
   const int T = g.lc_cn && g.lc_cn != 32 ? g.lc_cn : 128;
   if (parts & kCnIons) {
-    k_cn_backsub_fused<<<dim3((unsigned)((P + T - 1) / T), 2, 1), T, 0, s>>>(A, 3);
+    k_cn_backsub_fused<true><<<dim3((unsigned)((P + T - 1) / T), 2, 1), T, 0, s>>>(A, 3);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   if (parts & kCnVelocity) {
-    k_cn_backsub_fused<<<dim3((unsigned)((P + T - 1) / T), 3, 1), T, 0, s>>>(A, 0);
+    k_cn_backsub_fused<false><<<dim3((unsigned)((P + T - 1) / T), 3, 1), T, 0, s>>>(A, 0);
     return cudaGetLastError();
   }
   return cudaSuccess;
