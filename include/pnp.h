@@ -417,8 +417,18 @@ int pnp_wall_labels(pnp_ctx* fine, pnp_ctx* coarse, float* T_dev);
  * pnp_diagnostics then reports the wall shear against the plane-mean wall
  * velocity. */
 int pnp_set_wall_slip(pnp_ctx* ctx, const float* X_dev, int ncells, const float* Y_dev);
+/* The same wall values as a prescribed wall stress: the explicit terms see the
+ * wall flux nu g the slip implies, and the wall-normal implicit solves of u
+ * and w drop their wall coupling (zero-flux rows), so the near-wall cells are
+ * not pulled towards the slip value within a step. */
+int pnp_set_wall_stress(pnp_ctx* ctx, const float* X_dev, int ncells, const float* Y_dev);
+/* How pnp_step_wallmodel couples the network to the solver: mode 0 = wall slip
+ * (pnp_set_wall_slip), 1 = wall stress (pnp_set_wall_stress); relax in (0, 1]:
+ * the wall-shear rates used each step move that fraction of the way from the
+ * previous step's to the new prediction (1 = no relaxation). */
+int pnp_set_wallmodel_coupling(pnp_ctx* ctx, int mode, double relax);
 /* nsteps steps of the coarse solver with the wall model: before each step,
- * features (8 cells) -> network -> wall slip. */
+ * features (8 cells) -> network -> (relaxed) wall rates -> wall slip or stress. */
 int pnp_step_wallmodel(pnp_ctx* ctx, pnp_mlp* mlp, int nsteps, double dt);
 
 /* Launch sites timed by pnp_profile, in launch order within a substage. */

@@ -122,6 +122,8 @@ EXPORTS = {
     "pnp_wall_labels": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "pnp_set_wall_slip": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "pnp_step_wallmodel": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double]),
+    "pnp_set_wall_stress": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "pnp_set_wallmodel_coupling": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
     "pnp_error_string": (C.c_char_p, [C.c_int]),
     "pnp_destroy": (None, [C.c_void_p]),
 }
@@ -218,5 +220,7 @@ pnp_restrict_state = _fwd("pnp_restrict_state")
 pnp_wall_labels = _fwd("pnp_wall_labels")
 pnp_set_wall_slip = _fwd("pnp_set_wall_slip")
 pnp_step_wallmodel = _fwd("pnp_step_wallmodel")
+pnp_set_wall_stress = _fwd("pnp_set_wall_stress")
+pnp_set_wallmodel_coupling = _fwd("pnp_set_wallmodel_coupling")
 pnp_error_string = _fwd("pnp_error_string")
 pnp_destroy = _fwd("pnp_destroy")

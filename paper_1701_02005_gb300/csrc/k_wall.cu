@@ -192,6 +192,25 @@ __global__ void k_set_slip(const float* __restrict__ X, int ncells, const float*
   wall_w[P + c] = (TV)guard_slip(swt, lim);
 }
 
+// Under-relaxed wall-shear rates: prev += w (Y - prev) for the two rate
+// columns of every row, and Y takes the relaxed value.
+__global__ void k_relax_rates(float* __restrict__ Y, float* __restrict__ prev, int rows, float w) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const size_t o = (size_t)r * 5 + q;
+    const float v = prev[o] + w * (Y[o] - prev[o]);
+    prev[o] = v;
+    Y[o] = v;
+  }
+}
+
+cudaError_t launch_relax_rates(float* Y, float* prev, int rows, float w, cudaStream_t s) {
+  k_relax_rates<<<(rows + 255) / 256, 256, 0, s>>>(Y, prev, rows, w);
+  return cudaGetLastError();
+}
+
 // ---- launchers ----
 template <typename T>
 cudaError_t launch_restrict(const T* f, const double* dyf, const WallMap& wm, double* out, bool vfield, cudaStream_t s) {

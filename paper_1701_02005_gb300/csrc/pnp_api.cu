@@ -26,6 +26,10 @@ const double kGam[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
 const double kZet[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
 
 constexpr size_t kAlign = 256;
+// CN factor-row families: 0 u, w (Dirichlet wall values); 1 v (interior faces);
+// 2 ions (zero wall flux, D); 3 u, w with a prescribed wall stress (zero wall
+// coupling in the implicit operator, nu) for the wall model's stress coupling
+constexpr int kCnKinds = 4;
 constexpr int kDiagBlocks = 760;   // 5 x 152 SMs of 256-thread blocks: one resident wave
 constexpr int kProbeBlocks = 152 * 8;
 
@@ -110,6 +114,14 @@ struct pnp_ctx {
   void *wall_u, *wall_w;
   float *featX, *featY;
   bool slip_on = false;
+  // wall-model coupling: 0 slip (the slip velocity is a Dirichlet wall value of
+  // the implicit solve), 1 stress (the wall flux it implies is imposed, the
+  // implicit operator has no wall coupling); relaxation of the predicted rates
+  bool wall_stress = false;
+  int wm_mode = 0;
+  float wm_relax = 1.f;
+  bool wm_have_prev = false;
+  float* featYprev = nullptr;
   std::vector<double> href_p, href_m, lyc_p, lyc_m;
   bool refs_valid = false;   // references and shadows match the FP64 fields
   bool fp64_fresh = true;    // FP64 c+-, Phi, Hc+- arrays are current (else the shadows are)
@@ -173,7 +185,7 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
   double *wl = b.take<double>(ny), *wu = b.take<double>(ny);
   double *kx2 = b.take<double>(mp), *kz2 = b.take<double>(nz);
   double *rowsN = b.take<double>(3 * (size_t)ny), *rowsD = b.take<double>(3 * (size_t)ny);
-  double* cn = b.take<double>(27 * (size_t)ny);
+  double* cn = b.take<double>(9 * kCnKinds * (size_t)ny);
   void *twx = b.take<cplx<double>>(nx / 2), *twp = b.take<cplx<double>>(nx / 2 + 1), *twz = b.take<cplx<double>>(nz);
   void *twxf = b.take<cplx<float>>(nx / 2), *twpf = b.take<cplx<float>>(nx / 2 + 1), *twzf = b.take<cplx<float>>(nz);
   double* dpart = b.take<double>((size_t)kDiagBlocks * 16);
@@ -185,7 +197,7 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
   float* mf[8];
   for (int q = 0; q < 8; ++q) mf[q] = b.take<float>(ny);
   float2* dgw = b.take<float2>(3 * (size_t)ny);
-  float* cnF = b.take<float>(27 * (size_t)ny);
+  float* cnF = b.take<float>(9 * kCnKinds * (size_t)ny);
   float *crefp = b.take<float>(ny), *crefm = b.take<float>(ny), *crfp = b.take<float>(ny), *crfm = b.take<float>(ny);
   float *rhoref = b.take<float>(ny), *rhorf = b.take<float>(ny), *dPref = b.take<float>(ny), *Fvref = b.take<float>(ny);
   double *Rrefp = b.take<double>(3 * (size_t)ny), *Rrefm = b.take<double>(3 * (size_t)ny);
@@ -202,6 +214,7 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
   void* wallw = b.take<char>(P2 * tv);
   float* fX = b.take<float>(P2 * 5 * 8);
   float* fY = b.take<float>(P2 * 5);
+  float* fYp = b.take<float>(P2 * 5);
   const bool mixed = precision == PNP_MIXED;
   float2 *sfcN = b.take<float2>(mixed ? nspec : 0), *sfiN = b.take<float2>(mixed ? nspec : 0);
   float2 *sfcD = b.take<float2>(mixed ? nspec : 0), *sfiD = b.take<float2>(mixed ? nspec : 0);
@@ -212,7 +225,7 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
   double* lift64 = b.take<double>(nc);
   float* lift32 = b.take<float>(nc);
   double* sacc = b.take<double>(12 * (size_t)ny);
-  float* fuseG = b.take<float>(9 * (size_t)ny);
+  float* fuseG = b.take<float>(3 * kCnKinds * (size_t)ny);
   double* afd = b.take<double>(36 * (size_t)(nx + nz));
   float* aff = b.take<float>(36 * (size_t)(nx + nz));
   if (c) {
@@ -228,7 +241,7 @@ size_t carve(pnp_ctx* c, char* base, int nx, int ny, int nz, int precision) {
     c->dscr = dscr;
     c->spec2 = spec2;
     c->dscr2 = dscr2;
-    c->wall_u = wallu; c->wall_w = wallw; c->featX = fX; c->featY = fY;
+    c->wall_u = wallu; c->wall_w = wallw; c->featX = fX; c->featY = fY; c->featYprev = fYp;
     c->spc_cprN = fcN; c->spc_invN = fiN; c->spc_cprD = fcD; c->spc_invD = fiD;
     c->cpS = cpS; c->cmS = cmS; c->phiS = phiS; c->HcpS = HcpS; c->HcmS = HcmS;
     for (int q = 0; q < 8; ++q) c->mf[q] = mf[q];
@@ -411,10 +424,10 @@ int upload_metrics(pnp_ctx* c) {
 // 2: ions, zero wall flux), s = alp dt nu / 2 (nu = 1/Re or 1/(Re Sc)).
 int upload_cn(pnp_ctx* c, double dt) {
   const int ny = c->g.ny, nyc = c->g.nyc;
-  c->cn_h.assign(27 * (size_t)ny, 0.0);
+  c->cn_h.assign(9 * kCnKinds * (size_t)ny, 0.0);
   for (int l = 0; l < 3; ++l) {
     const double alp = kGam[l] + kZet[l];
-    for (int kind = 0; kind < 3; ++kind) {
+    for (int kind = 0; kind < kCnKinds; ++kind) {
       const double diff = kind == 2 ? c->ph.D : c->ph.nu;
       const double sfac = 0.5 * alp * dt * diff;
       const int n = kind == 1 ? nyc - 1 : nyc;
@@ -438,9 +451,9 @@ int upload_cn(pnp_ctx* c, double dt) {
           else if (dir) b[j] -= hi;
         }
       }
-      double* A = c->cn_h.data() + ((size_t)(l * 3 + kind) * 3 + 0) * ny;
-      double* Cp = c->cn_h.data() + ((size_t)(l * 3 + kind) * 3 + 1) * ny;
-      double* M = c->cn_h.data() + ((size_t)(l * 3 + kind) * 3 + 2) * ny;
+      double* A = c->cn_h.data() + ((size_t)(l * kCnKinds + kind) * 3 + 0) * ny;
+      double* Cp = c->cn_h.data() + ((size_t)(l * kCnKinds + kind) * 3 + 1) * ny;
+      double* M = c->cn_h.data() + ((size_t)(l * kCnKinds + kind) * 3 + 2) * ny;
       double cprev = 0.0;
       for (int idx = 0; idx < n; ++idx) {
         const double Aj = -sfac * a[idx], Bj = 1.0 - sfac * b[idx], Cj = -sfac * cc[idx];
@@ -452,7 +465,7 @@ int upload_cn(pnp_ctx* c, double dt) {
       }
     }
   }
-  std::vector<float> cnf(27 * (size_t)ny, 0.f);
+  std::vector<float> cnf(9 * kCnKinds * (size_t)ny, 0.f);
   for (size_t q = 0; q < cnf.size(); ++q) cnf[q] = (float)c->cn_h[q];
   CK(cudaMemcpyAsync(c->cn_d, c->cn_h.data(), sizeof(double) * c->cn_h.size(), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->cnF_d, cnf.data(), sizeof(float) * cnf.size(), cudaMemcpyHostToDevice, c->stream));
@@ -480,13 +493,13 @@ bool cn_fused(const pnp_ctx* c, int* jc_out = nullptr) {
 // from the FP32 factor rows the stencil eliminates with (needs upload_cn's dt).
 int upload_fuse(pnp_ctx* c, double dt, int jc) {
   const int ny = c->g.ny, nyc = c->g.nyc;
-  std::vector<float> G(9 * (size_t)ny, 0.f);
+  std::vector<float> G(3 * kCnKinds * (size_t)ny, 0.f);
   for (int l = 0; l < 3; ++l)
-    for (int kind = 0; kind < 3; ++kind) {
-      const double* A = c->cn_h.data() + ((size_t)(l * 3 + kind) * 3 + 0) * ny;
-      const double* M = c->cn_h.data() + ((size_t)(l * 3 + kind) * 3 + 2) * ny;
+    for (int kind = 0; kind < kCnKinds; ++kind) {
+      const double* A = c->cn_h.data() + ((size_t)(l * kCnKinds + kind) * 3 + 0) * ny;
+      const double* M = c->cn_h.data() + ((size_t)(l * kCnKinds + kind) * 3 + 2) * ny;
       const int n = kind == 1 ? nyc - 1 : nyc, j0 = kind == 1 ? 1 : 0;
-      float* out = G.data() + (size_t)(l * 3 + kind) * ny;
+      float* out = G.data() + (size_t)(l * kCnKinds + kind) * ny;
       double acc = 1.0;
       for (int r = 0; r < n; ++r) {
         if (r == 0 || (r + j0) % jc == 0) acc = 1.0;   // first row of a chunk
@@ -613,13 +626,13 @@ int prepare_tables(pnp_ctx* c, double dt) {
 
 CNRows cn_rows(const pnp_ctx* c, int l, int kind) {
   const size_t ny = c->g.ny;
-  const double* base = c->cn_d + (size_t)(l * 3 + kind) * 3 * ny;
+  const double* base = c->cn_d + (size_t)(l * kCnKinds + kind) * 3 * ny;
   return CNRows{base, base + ny, base + 2 * ny};
 }
 
 CNRowsF cn_rows_f(const pnp_ctx* c, int l, int kind) {
   const size_t ny = c->g.ny;
-  const float* base = c->cnF_d + (size_t)(l * 3 + kind) * 3 * ny;
+  const float* base = c->cnF_d + (size_t)(l * kCnKinds + kind) * 3 * ny;
   return CNRowsF{base, base + ny, base + 2 * ny};
 }
 
@@ -882,7 +895,8 @@ cudaError_t substage(pnp_ctx* c, double dt, int l) {
     if (e != cudaSuccess) return e;
   }
   mark(c, c->stream, PNP_SITE_RHS);
-  e = launch_cn_solves<TV>(f, c->g, cn_rows(c, l, 0), cn_rows(c, l, 1), cn_rows(c, l, 2), c->stream);
+  e = launch_cn_solves<TV>(f, c->g, cn_rows(c, l, c->wall_stress ? 3 : 0), cn_rows(c, l, 1), cn_rows(c, l, 2),
+                           c->stream);
   if (e != cudaSuccess) return e;
   mark(c, c->stream, PNP_SITE_CN);
   return poisson_pair<TV>(c, st.alp * dt);
@@ -895,7 +909,8 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
   const Shadows sh = shadows(c);
   const MixedRefs R = mixed_refs(c);
   const bool fp64 = c->policy == PNP_POLICY_FP64_SOLVES;
-  const CNRowsF cell = cn_rows_f(c, l, 0), face = cn_rows_f(c, l, 1), ion = cn_rows_f(c, l, 2);
+  const int kc = c->wall_stress ? 3 : 0;   // u, w rows: Dirichlet wall values, or the wall-stress coupling
+  const CNRowsF cell = cn_rows_f(c, l, kc), face = cn_rows_f(c, l, 1), ion = cn_rows_f(c, l, 2);
   int jc = 0;
   const bool fused = cn_fused(c, &jc) && c->fuse_dt == dt && c->fuse_jc == jc;
   const CnFuse fz{cell, face, ion, jc, fused ? 1 : 0};
@@ -905,8 +920,8 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
   if (e != cudaSuccess) return e;
   mark(c, c->stream, PNP_SITE_RHS);
   const size_t ny = c->g.ny;
-  const float* Gl = c->fuseG_d + (size_t)l * 3 * ny;
-  const CnFusedG G{Gl, Gl + ny, Gl + 2 * ny};
+  const float* Gl = c->fuseG_d + (size_t)l * kCnKinds * ny;
+  const CnFusedG G{Gl + (size_t)kc * ny, Gl + ny, Gl + 2 * ny};
   auto cn = [&](unsigned parts, cudaStream_t s) {
     if (st.af) {   // the x/z factors first, on the FP32 right-hand sides of these families
       const cudaError_t ea = periodic_sweeps<float>(c, l, (parts & kCnVelocity ? 1u : 0u) | (parts & kCnIons ? 2u : 0u),
@@ -914,7 +929,7 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
       if (ea != cudaSuccess) return ea;
     }
     if (fp64)
-      return launch_mixed_cn_fp64(f, sh, R, c->g, cn_rows(c, l, 0), cn_rows(c, l, 1), cn_rows(c, l, 2), l, parts,
+      return launch_mixed_cn_fp64(f, sh, R, c->g, cn_rows(c, l, kc), cn_rows(c, l, 1), cn_rows(c, l, 2), l, parts,
                                   cn_scratch64(c), s);
     if (fused) return launch_mixed_cn_fused(f, sh, R, c->g, cell, face, ion, G, jc, l, parts, s);
     return launch_mixed_cn(f, sh, R, c->g, cell, face, ion, l, parts, s);
@@ -1053,7 +1068,7 @@ int refresh_refs(pnp_ctx* c, double dt) {
   }
   if (!(c->refs_dt == dt)) {
     // the reference increments below need this dt's elimination factors
-    if (!(c->cn_dt == dt) || c->cn_h.size() != 27 * (size_t)ny) {
+    if (!(c->cn_dt == dt) || c->cn_h.size() != 9 * kCnKinds * (size_t)ny) {
       int r = upload_cn(c, dt);
       if (r) return r;
     }
@@ -1063,9 +1078,9 @@ int refresh_refs(pnp_ctx* c, double dt) {
     std::vector<double> Rp(3 * (size_t)ny, 0.0), Rm(3 * (size_t)ny, 0.0);
     for (int l = 0; l < 3; ++l) {
       const double alp = kGam[l] + kZet[l];
-      const double* A = c->cn_h.data() + ((size_t)(l * 3 + 2) * 3 + 0) * ny;
-      const double* Cp = c->cn_h.data() + ((size_t)(l * 3 + 2) * 3 + 1) * ny;
-      const double* M = c->cn_h.data() + ((size_t)(l * 3 + 2) * 3 + 2) * ny;
+      const double* A = c->cn_h.data() + ((size_t)(l * kCnKinds + 2) * 3 + 0) * ny;
+      const double* Cp = c->cn_h.data() + ((size_t)(l * kCnKinds + 2) * 3 + 1) * ny;
+      const double* M = c->cn_h.data() + ((size_t)(l * kCnKinds + 2) * 3 + 2) * ny;
       for (int ion = 0; ion < 2; ++ion) {
         const std::vector<double>& hr = ion == 0 ? c->href_p : c->href_m;
         const std::vector<double>& ly = ion == 0 ? c->lyc_p : c->lyc_m;
@@ -2385,12 +2400,14 @@ int pnp_wall_labels(pnp_ctx* f, pnp_ctx* c, float* T) {
   return PNP_OK;
 }
 
-int pnp_set_wall_slip(pnp_ctx* c, const float* X, int ncells, const float* Y) {
+namespace {
+int set_wall_values(pnp_ctx* c, const float* X, int ncells, const float* Y, bool stress) {
   if (!c || (Y && (!X || ncells < 1 || ncells > 8))) return PNP_ERR_ARG;
   const size_t P = (size_t)c->g.nz * c->g.nx;
-  const bool was = c->slip_on;
+  const bool was = c->slip_on, was_stress = c->wall_stress;
   if (!Y) {
     c->slip_on = false;
+    c->wall_stress = false;
   } else {
     const double h0b = c->h[0], h0t = c->h[c->g.nyc];
     cudaError_t e = c->precision == PNP_FP64
@@ -2400,8 +2417,26 @@ int pnp_set_wall_slip(pnp_ctx* c, const float* X, int ncells, const float* Y) {
                                                  (float*)c->wall_w, c->stream);
     if (e != cudaSuccess) return PNP_ERR_CUDA;
     c->slip_on = true;
+    c->wall_stress = stress;
   }
-  if (was != c->slip_on) drop_graph(c);
+  if (was != c->slip_on || was_stress != c->wall_stress) drop_graph(c);
+  return PNP_OK;
+}
+}  // namespace
+
+int pnp_set_wall_slip(pnp_ctx* c, const float* X, int ncells, const float* Y) {
+  return set_wall_values(c, X, ncells, Y, false);
+}
+
+int pnp_set_wall_stress(pnp_ctx* c, const float* X, int ncells, const float* Y) {
+  return set_wall_values(c, X, ncells, Y, true);
+}
+
+int pnp_set_wallmodel_coupling(pnp_ctx* c, int mode, double relax) {
+  if (!c || (mode != 0 && mode != 1) || !(relax > 0.0) || relax > 1.0) return PNP_ERR_ARG;
+  c->wm_mode = mode;
+  c->wm_relax = (float)relax;
+  c->wm_have_prev = false;
   return PNP_OK;
 }
 
@@ -2413,7 +2448,11 @@ int pnp_step_wallmodel(pnp_ctx* c, pnp_mlp* m, int nsteps, double dt) {
     int r = pnp_wall_features(c, 8, c->featX);
     if (r) return r;
     CK(mlp_forward(m->b, c->featX, rows, c->featY, c->stream));
-    r = pnp_set_wall_slip(c, c->featX, 8, c->featY);
+    if (c->wm_relax < 1.f) {   // the rates used move a fraction of the way to the prediction
+      CK(launch_relax_rates(c->featY, c->featYprev, rows, c->wm_have_prev ? c->wm_relax : 1.f, c->stream));
+      c->wm_have_prev = true;
+    }
+    r = set_wall_values(c, c->featX, 8, c->featY, c->wm_mode == 1);
     if (r) return r;
     r = pnp_step(c, 1, dt);
     if (r) return r;

@@ -30,6 +30,9 @@ template <typename TV>
 cudaError_t launch_set_slip(const float* X, int ncells, const float* Y, size_t P, double Uw, double h0b, double h0t,
                             TV* wall_u, TV* wall_w, cudaStream_t s);
 
+// prev += w (Y - prev), Y = prev on the two wall-shear-rate columns of each row
+cudaError_t launch_relax_rates(float* Y, float* prev, int rows, float w, cudaStream_t s);
+
 // ---- MLP 40 -> 128 x 4 (erf-GELU) -> 5 ----
 constexpr int kMlpLayers = 5;
 constexpr int kMlpIn = 40;
