@@ -468,7 +468,7 @@ struct FusedArgs {
 };
 
 template <bool ION>
-__global__ void __launch_bounds__(128) k_cn_backsub_fused(FusedArgs A, int fam0) {
+__global__ void __launch_bounds__(256) k_cn_backsub_fused(FusedArgs A, int fam0) {
   constexpr int CH = 8;
   const FusedFam& F = A.f[fam0 + blockIdx.y];
   const size_t P = A.P;

@@ -206,6 +206,38 @@ __global__ void k_relax_rates(float* __restrict__ Y, float* __restrict__ prev, i
   }
 }
 
+// Plane means of the two wall-shear-rate columns of each wall's rows (rows
+// [0, P) bottom, [P, 2P) top), written back to every row of that wall.
+__global__ void k_mean_rates(float* __restrict__ Y, int P) {
+  __shared__ float sh[2][256];
+  const int wall = blockIdx.x;
+  float a = 0.f, b = 0.f;
+  for (int r = threadIdx.x; r < P; r += blockDim.x) {
+    a += Y[(size_t)(wall * P + r) * 5 + 0];
+    b += Y[(size_t)(wall * P + r) * 5 + 1];
+  }
+  sh[0][threadIdx.x] = a;
+  sh[1][threadIdx.x] = b;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + st];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  const float ma = sh[0][0] / (float)P, mb = sh[1][0] / (float)P;
+  for (int r = threadIdx.x; r < P; r += blockDim.x) {
+    Y[(size_t)(wall * P + r) * 5 + 0] = ma;
+    Y[(size_t)(wall * P + r) * 5 + 1] = mb;
+  }
+}
+
+cudaError_t launch_mean_rates(float* Y, int P, cudaStream_t s) {
+  k_mean_rates<<<2, 256, 0, s>>>(Y, P);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_relax_rates(float* Y, float* prev, int rows, float w, cudaStream_t s) {
   k_relax_rates<<<(rows + 255) / 256, 256, 0, s>>>(Y, prev, rows, w);
   return cudaGetLastError();

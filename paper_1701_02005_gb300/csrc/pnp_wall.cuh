@@ -32,6 +32,8 @@ cudaError_t launch_set_slip(const float* X, int ncells, const float* Y, size_t P
 
 // prev += w (Y - prev), Y = prev on the two wall-shear-rate columns of each row
 cudaError_t launch_relax_rates(float* Y, float* prev, int rows, float w, cudaStream_t s);
+// plane means of the wall-shear-rate columns, per wall, broadcast to its rows
+cudaError_t launch_mean_rates(float* Y, int P, cudaStream_t s);
 
 // ---- MLP 40 -> 128 x 4 (erf-GELU) -> 5 ----
 constexpr int kMlpLayers = 5;
