@@ -233,7 +233,20 @@ constexpr int fx_row_stride() {
   return need + ((8 - need % 16) + 16) % 16;
 }
 
-// FP32 real x-transforms with the two-pass register FFT (pnp_regfft.cuh) of
+// Two consecutive values p[0], p[1] (p 8-byte aligned for FP32, 16-byte for
+// FP64) as one vector load, converted to T.
+template <typename T, typename S>
+__device__ __forceinline__ cplx<T> ld_pair(const S* p) {
+  if constexpr (sizeof(S) == sizeof(float)) {
+    const float2 a = *reinterpret_cast<const float2*>(p);
+    return {(T)a.x, (T)a.y};
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    return {(T)a.x, (T)a.y};
+  }
+}
+
+// Real x-transforms (FP32 or FP64) with the two-pass register FFT (pnp_regfft.cuh) of
 // the half-length complex sequence z_t = x_2t + i x_2t+1.  G = NH / R1 threads
 // own a row (consecutive lanes of one warp, so every exchange inside a row
 // needs only a warp barrier); ROWS rows per block.
@@ -242,17 +255,17 @@ constexpr int fx_row_stride() {
 // R1-point DFT, twiddles, exchanges, does its G-point DFTs, writes Z to the
 // row buffer in natural order, and the row's threads split the real-FFT
 // post-processing X_m = E_m + W_N^m O_m over m = 0 .. NH.
-template <int NH, int R1, typename TV>
-__global__ void __launch_bounds__(256) k_fft_x_fwd_reg(SrcArgs<float, TV> src, Geo g, Metrics mt,
-                                                       cplx<float>* __restrict__ spec,
-                                                       const cplx<float>* __restrict__ tw_half,
-                                                       const cplx<float>* __restrict__ tw_post) {
+template <int NH, int R1, typename T, typename TV>
+__global__ void __launch_bounds__(256) k_fft_x_fwd_reg(SrcArgs<T, TV> src, Geo g, Metrics mt,
+                                                       cplx<T>* __restrict__ spec,
+                                                       const cplx<T>* __restrict__ tw_half,
+                                                       const cplx<T>* __restrict__ tw_post) {
   constexpr int G = NH / R1, PER = R1 / G;
   static_assert(R1 % G == 0 && 32 % G == 0, "row of whole transforms inside one warp");
-  extern __shared__ __align__(16) float fx_smem[];
-  cplx<float>* twh = reinterpret_cast<cplx<float>*>(fx_smem);   // [NH]
-  cplx<float>* twp = twh + NH;                                   // [NH + 1]
-  cplx<float>* rows = twp + NH + 1;                              // [ROWS][row stride]
+  extern __shared__ __align__(16) unsigned char fx_smem[];
+  cplx<T>* twh = reinterpret_cast<cplx<T>*>(fx_smem);   // [NH]
+  cplx<T>* twp = twh + NH;                               // [NH + 1]
+  cplx<T>* rows = twp + NH + 1;                          // [ROWS][row stride]
   const int gi = threadIdx.x, ry = threadIdx.y, tid = ry * G + gi;
   const int nthr = G * blockDim.y;
   for (int e = tid; e < NH; e += nthr) twh[e] = tw_half[e];
@@ -261,24 +274,24 @@ __global__ void __launch_bounds__(256) k_fft_x_fwd_reg(SrcArgs<float, TV> src, G
   const int row = blockIdx.x * blockDim.y + ry;
   const bool live = row < nrows;
   const int j = live ? row / g.nz : 0, k = live ? row % g.nz : 0;
-  cplx<float> v[R1];
+  cplx<T> v[R1];
   const size_t rbase = ((size_t)j * g.nz + k) * g.nx;   // this row's first cell
   if (live && src.kind == PoissonSrc::Divergence) {
-    // both samples of z_t from float2 loads: x-faces 2t, 2t+1, 2t+2 (periodic),
+    // both samples of z_t from paired loads: x-faces 2t, 2t+1, 2t+2 (periodic),
     // v on the faces below / above, w on the z-faces k, k+1
     const size_t P = (size_t)g.nz * g.nx;
     const int kp = (k + 1 == g.nz) ? 0 : k + 1;
     const size_t rbp = ((size_t)j * g.nz + kp) * g.nx;
-    const float sy = src.idyT[j] * src.ss;
+    const T sy = src.idyT[j] * src.ss;
 #pragma unroll
     for (int r = 0; r < R1; ++r) {
       const int i = 2 * (gi + G * r);
-      const float2 u01 = *reinterpret_cast<const float2*>(src.u + rbase + i);
-      const float u2 = src.u[rbase + (i + 2 == g.nx ? 0 : i + 2)];
-      const float2 vb = *reinterpret_cast<const float2*>(src.v + rbase + i);
-      const float2 vt = *reinterpret_cast<const float2*>(src.v + rbase + P + i);
-      const float2 wk = *reinterpret_cast<const float2*>(src.w + rbase + i);
-      const float2 wkp = *reinterpret_cast<const float2*>(src.w + rbp + i);
+      const cplx<T> u01 = ld_pair<T>(src.u + rbase + i);
+      const T u2 = (T)src.u[rbase + (i + 2 == g.nx ? 0 : i + 2)];
+      const cplx<T> vb = ld_pair<T>(src.v + rbase + i);
+      const cplx<T> vt = ld_pair<T>(src.v + rbase + P + i);
+      const cplx<T> wk = ld_pair<T>(src.w + rbase + i);
+      const cplx<T> wkp = ld_pair<T>(src.w + rbp + i);
       v[r] = {(u01.y - u01.x) * src.sx + (vt.x - vb.x) * sy + (wkp.x - wk.x) * src.sz,
               (u2 - u01.y) * src.sx + (vt.y - vb.y) * sy + (wkp.y - wk.y) * src.sz};
     }
@@ -286,27 +299,27 @@ __global__ void __launch_bounds__(256) k_fft_x_fwd_reg(SrcArgs<float, TV> src, G
 #pragma unroll
     for (int r = 0; r < R1; ++r) {
       const int i = 2 * (gi + G * r);
-      const float2 a = *reinterpret_cast<const float2*>(src.sa + rbase + i);
-      const float2 b = *reinterpret_cast<const float2*>(src.sb + rbase + i);
+      const cplx<T> a = ld_pair<T>(src.sa + rbase + i);
+      const cplx<T> b = ld_pair<T>(src.sb + rbase + i);
       v[r] = {(-(a.x - b.x)) * src.ss, (-(a.y - b.y)) * src.ss};
     }
   } else {
 #pragma unroll
     for (int r = 0; r < R1; ++r) {
       const int t = gi + G * r;
-      v[r] = live ? cplx<float>{src_value(src, g, mt, j, k, 2 * t), src_value(src, g, mt, j, k, 2 * t + 1)}
-                  : cplx<float>{0.f, 0.f};
+      v[r] = live ? cplx<T>{src_value(src, g, mt, j, k, 2 * t), src_value(src, g, mt, j, k, 2 * t + 1)}
+                  : cplx<T>{T(0), T(0)};
     }
   }
   __syncthreads();   // twiddle tables
   rfft::dft<false, R1>(v);
-  cplx<float>* xr = rows + (size_t)ry * fx_row_stride<NH, R1>();
+  cplx<T>* xr = rows + (size_t)ry * fx_row_stride<NH, R1>();
   rfft::static_for<0, R1>([&](auto kc) {
     constexpr int k1 = decltype(kc)::value;
     xr[k1 * (G + 1) + gi] = cmul(v[rfft::bitrev(k1, R1)], twh[gi * k1]);
   });
   __syncwarp();
-  cplx<float> w[PER][G];
+  cplx<T> w[PER][G];
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int k1 = gi * PER + p;
@@ -325,13 +338,13 @@ __global__ void __launch_bounds__(256) k_fft_x_fwd_reg(SrcArgs<float, TV> src, G
   }
   __syncwarp();
   if (!live) return;
-  cplx<float>* out = spec + (size_t)row * g.mp;
+  cplx<T>* out = spec + (size_t)row * g.mp;
   for (int mm = gi; mm <= NH; mm += G) {
-    const cplx<float> zm = xr[mm == NH ? 0 : mm];
-    const cplx<float> zc = cconj(xr[mm == 0 ? 0 : NH - mm]);
-    const cplx<float> E = {0.5f * (zm.x + zc.x), 0.5f * (zm.y + zc.y)};
-    const cplx<float> dd = csub(zm, zc);
-    const cplx<float> O = {0.5f * dd.y, -0.5f * dd.x};   // (zm - zc) / (2i)
+    const cplx<T> zm = xr[mm == NH ? 0 : mm];
+    const cplx<T> zc = cconj(xr[mm == 0 ? 0 : NH - mm]);
+    const cplx<T> E = {T(0.5) * (zm.x + zc.x), T(0.5) * (zm.y + zc.y)};
+    const cplx<T> dd = csub(zm, zc);
+    const cplx<T> O = {T(0.5) * dd.y, T(-0.5) * dd.x};   // (zm - zc) / (2i)
     out[mm] = cadd(E, cmul(twp[mm], O));
   }
 }
@@ -339,47 +352,47 @@ __global__ void __launch_bounds__(256) k_fft_x_fwd_reg(SrcArgs<float, TV> src, G
 // Inverse: thread g forms the pre-processed z_t (from X_t and conj X_{NH-t})
 // for t = g + G r straight from the spectrum, runs the inverse transform and
 // writes x_2t, x_2t+1 of t = k1 + R1 k2.
-template <int NH, int R1, typename TO>
-__global__ void __launch_bounds__(256) k_fft_x_inv_reg(PoissonDst dst, const cplx<float>* __restrict__ spec, Geo g,
-                                                       Metrics mt, const cplx<float>* __restrict__ tw_half,
-                                                       const cplx<float>* __restrict__ tw_post, double V,
+template <int NH, int R1, typename T, typename TO>
+__global__ void __launch_bounds__(256) k_fft_x_inv_reg(PoissonDst dst, const cplx<T>* __restrict__ spec, Geo g,
+                                                       Metrics mt, const cplx<T>* __restrict__ tw_half,
+                                                       const cplx<T>* __restrict__ tw_post, double V,
                                                        TO* __restrict__ out, const double* __restrict__ plane_add,
                                                        const TO* __restrict__ cell_add) {
   constexpr int G = NH / R1, PER = R1 / G;
   static_assert(R1 % G == 0 && 32 % G == 0, "row of whole transforms inside one warp");
-  extern __shared__ __align__(16) float fx_smem[];
-  cplx<float>* twh = reinterpret_cast<cplx<float>*>(fx_smem);   // [NH] (conjugated)
-  cplx<float>* twp = twh + NH;                                   // [NH]
-  cplx<float>* rows = twp + NH;                                  // [ROWS][row stride]
+  extern __shared__ __align__(16) unsigned char fx_smem[];
+  cplx<T>* twh = reinterpret_cast<cplx<T>*>(fx_smem);   // [NH] (conjugated)
+  cplx<T>* twp = twh + NH;                               // [NH]
+  cplx<T>* rows = twp + NH;                              // [ROWS][row stride]
   const int gi = threadIdx.x, ry = threadIdx.y, tid = ry * G + gi;
   const int nthr = G * blockDim.y;
   for (int e = tid; e < NH; e += nthr) {
-    const cplx<float> a = tw_half[e];
+    const cplx<T> a = tw_half[e];
     twh[e] = {a.x, -a.y};
     twp[e] = tw_post[e];
   }
   const int nrows = g.nyc * g.nz;
   const int row = blockIdx.x * blockDim.y + ry;
   const bool live = row < nrows;
-  const cplx<float>* in = spec + (size_t)(live ? row : 0) * g.mp;
+  const cplx<T>* in = spec + (size_t)(live ? row : 0) * g.mp;
   __syncthreads();   // twiddle tables
-  cplx<float> v[R1];
+  cplx<T> v[R1];
 #pragma unroll
   for (int r = 0; r < R1; ++r) {
     const int t = gi + G * r;
-    cplx<float> z = {0.f, 0.f};
+    cplx<T> z = {T(0), T(0)};
     if (live) {
-      const cplx<float> Xm = in[t];
-      const cplx<float> Xc = cconj(in[NH - t]);
-      const cplx<float> sum = cadd(Xm, Xc);
-      const cplx<float> dif = csub(Xm, Xc);
-      const cplx<float> tt = cmul(cconj(twp[t]), dif);
+      const cplx<T> Xm = in[t];
+      const cplx<T> Xc = cconj(in[NH - t]);
+      const cplx<T> sum = cadd(Xm, Xc);
+      const cplx<T> dif = csub(Xm, Xc);
+      const cplx<T> tt = cmul(cconj(twp[t]), dif);
       z = {sum.x - tt.y, sum.y + tt.x};   // sum + i * tt
     }
     v[r] = z;
   }
   rfft::dft<true, R1>(v);
-  cplx<float>* xr = rows + (size_t)ry * fx_row_stride<NH, R1>();
+  cplx<T>* xr = rows + (size_t)ry * fx_row_stride<NH, R1>();
   rfft::static_for<0, R1>([&](auto kc) {
     constexpr int k1 = decltype(kc)::value;
     xr[k1 * (G + 1) + gi] = cmul(v[rfft::bitrev(k1, R1)], twh[gi * k1]);
@@ -389,17 +402,17 @@ __global__ void __launch_bounds__(256) k_fft_x_inv_reg(PoissonDst dst, const cpl
   const int j = row / g.nz;
   const size_t base = (size_t)row * g.nx;
   const double add = dst == PoissonDst::Potential ? V * mt.yc[j] : 0.0;
-  const float addT = dst == PoissonDst::PotentialShadow ? (float)plane_add[j] : 0.f;
+  const T addT = dst == PoissonDst::PotentialShadow ? (T)plane_add[j] : T(0);
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int k1 = gi * PER + p;
-    cplx<float> w[G];
+    cplx<T> w[G];
 #pragma unroll
     for (int q = 0; q < G; ++q) w[q] = xr[k1 * (G + 1) + q];
     rfft::dft<true, G>(w);
     rfft::static_for<0, G>([&](auto kc) {
       constexpr int k2 = decltype(kc)::value;
-      const cplx<float> z = w[rfft::bitrev(k2, G)];
+      const cplx<T> z = w[rfft::bitrev(k2, G)];
       const size_t o = base + 2 * (size_t)(k1 + R1 * k2);
       if (dst == PoissonDst::PotentialShadow) {
         TO a0 = (TO)(addT + z.x), a1 = (TO)(addT + z.y);
@@ -424,9 +437,9 @@ __global__ void __launch_bounds__(256) k_fft_x_inv_reg(PoissonDst dst, const cpl
 // 256 threads on the 256x193x256 workload), and shared memory.
 template <int NH, int R1>
 constexpr int fx_rows() { return 128 / (NH / R1); }
-template <int NH, int R1>
+template <int NH, int R1, typename T>
 constexpr size_t fx_smem() {
-  return sizeof(cplx<float>) * ((size_t)2 * NH + 1 + (size_t)fx_rows<NH, R1>() * fx_row_stride<NH, R1>());
+  return sizeof(cplx<T>) * ((size_t)2 * NH + 1 + (size_t)fx_rows<NH, R1>() * fx_row_stride<NH, R1>());
 }
 
 template <typename T>
@@ -450,7 +463,7 @@ cudaError_t launch_fft_x_fwd(PoissonSrc kind, const TV* u, const TV* v, const TV
                              const T* idyT, const float* la, const float* lb) {
   SrcArgs<T, TV> a{kind, u, v, w, cp, cm, plain, scale, sa, sb, (T)(scale * g.idx), (T)(scale * g.idz), idyT,
                    (T)scale, la, lb};
-  if constexpr (sizeof(T) == sizeof(float)) {
+  {
     auto go = [&](auto kern, int G, int rows, size_t smem) {
       if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -461,12 +474,12 @@ cudaError_t launch_fft_x_fwd(PoissonSrc kind, const TV* u, const TV* v, const TV
       return cudaGetLastError();
     };
     switch (g.nx / 2) {
-      case 16: return go(k_fft_x_fwd_reg<16, 4, TV>, 4, fx_rows<16, 4>(), fx_smem<16, 4>());
-      case 32: return go(k_fft_x_fwd_reg<32, 8, TV>, 4, fx_rows<32, 8>(), fx_smem<32, 8>());
-      case 64: return go(k_fft_x_fwd_reg<64, 8, TV>, 8, fx_rows<64, 8>(), fx_smem<64, 8>());
-      case 128: return go(k_fft_x_fwd_reg<128, 16, TV>, 8, fx_rows<128, 16>(), fx_smem<128, 16>());
-      case 256: return go(k_fft_x_fwd_reg<256, 16, TV>, 16, fx_rows<256, 16>(), fx_smem<256, 16>());
-      case 512: return go(k_fft_x_fwd_reg<512, 32, TV>, 16, fx_rows<512, 32>(), fx_smem<512, 32>());
+      case 16: return go(k_fft_x_fwd_reg<16, 4, T, TV>, 4, fx_rows<16, 4>(), fx_smem<16, 4, T>());
+      case 32: return go(k_fft_x_fwd_reg<32, 8, T, TV>, 4, fx_rows<32, 8>(), fx_smem<32, 8, T>());
+      case 64: return go(k_fft_x_fwd_reg<64, 8, T, TV>, 8, fx_rows<64, 8>(), fx_smem<64, 8, T>());
+      case 128: return go(k_fft_x_fwd_reg<128, 16, T, TV>, 8, fx_rows<128, 16>(), fx_smem<128, 16, T>());
+      case 256: return go(k_fft_x_fwd_reg<256, 16, T, TV>, 16, fx_rows<256, 16>(), fx_smem<256, 16, T>());
+      case 512: return go(k_fft_x_fwd_reg<512, 32, T, TV>, 16, fx_rows<512, 32>(), fx_smem<512, 32, T>());
       default: break;
     }
   }
@@ -538,7 +551,7 @@ template <typename T, typename TO>
 cudaError_t launch_fft_x_inv(PoissonDst dst, const cplx<T>* spec, const Geo& g, const Metrics& m,
                              const cplx<T>* tw_half, const cplx<T>* tw_post, double V, TO* out,
                              cudaStream_t s, const double* plane_add, const TO* cell_add) {
-  if constexpr (sizeof(T) == sizeof(float)) {
+  {
     auto go = [&](auto kern, int G, int rows, size_t smem) {
       if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -550,12 +563,12 @@ cudaError_t launch_fft_x_inv(PoissonDst dst, const cplx<T>* spec, const Geo& g, 
       return cudaGetLastError();
     };
     switch (g.nx / 2) {
-      case 16: return go(k_fft_x_inv_reg<16, 4, TO>, 4, fx_rows<16, 4>(), fx_smem<16, 4>());
-      case 32: return go(k_fft_x_inv_reg<32, 8, TO>, 4, fx_rows<32, 8>(), fx_smem<32, 8>());
-      case 64: return go(k_fft_x_inv_reg<64, 8, TO>, 8, fx_rows<64, 8>(), fx_smem<64, 8>());
-      case 128: return go(k_fft_x_inv_reg<128, 16, TO>, 8, fx_rows<128, 16>(), fx_smem<128, 16>());
-      case 256: return go(k_fft_x_inv_reg<256, 16, TO>, 16, fx_rows<256, 16>(), fx_smem<256, 16>());
-      case 512: return go(k_fft_x_inv_reg<512, 32, TO>, 16, fx_rows<512, 32>(), fx_smem<512, 32>());
+      case 16: return go(k_fft_x_inv_reg<16, 4, T, TO>, 4, fx_rows<16, 4>(), fx_smem<16, 4, T>());
+      case 32: return go(k_fft_x_inv_reg<32, 8, T, TO>, 4, fx_rows<32, 8>(), fx_smem<32, 8, T>());
+      case 64: return go(k_fft_x_inv_reg<64, 8, T, TO>, 8, fx_rows<64, 8>(), fx_smem<64, 8, T>());
+      case 128: return go(k_fft_x_inv_reg<128, 16, T, TO>, 8, fx_rows<128, 16>(), fx_smem<128, 16, T>());
+      case 256: return go(k_fft_x_inv_reg<256, 16, T, TO>, 16, fx_rows<256, 16>(), fx_smem<256, 16, T>());
+      case 512: return go(k_fft_x_inv_reg<512, 32, T, TO>, 16, fx_rows<512, 32>(), fx_smem<512, 32, T>());
       default: break;
     }
   }
@@ -601,35 +614,35 @@ __global__ void k_fft_z(cplx<T>* __restrict__ spec, const cplx<T>* __restrict__ 
   for (int n = threadIdx.y; n < nz; n += blockDim.y) plane[(size_t)n * g.mp + m] = Z[n];
 }
 
-// FP32 z-transform with the two-pass register FFT (pnp_regfft.cuh): a block
+// z-transform with the two-pass register FFT (pnp_regfft.cuh), FP32 or FP64: a block
 // owns TM consecutive m-columns of one y-plane; thread (tm, g) loads the
 // samples n = g + G r of column tm (TM-wide coalesced rows), does the R1-point
 // DFT in registers, multiplies by W_N^{g k1} and exchanges through shared
 // memory; thread g then does the G-point DFTs of its R1 / G values of k1 and
 // stores X[k1 + R1 k2].
-template <int N, int R1, int TM, bool INV>
-__global__ void __launch_bounds__(TM*(N / R1)) k_fft_z_reg(cplx<float>* __restrict__ spec,
-                                                           const cplx<float>* __restrict__ tw, Geo g) {
+template <int N, int R1, int TM, bool INV, typename T>
+__global__ void __launch_bounds__(TM*(N / R1)) k_fft_z_reg(cplx<T>* __restrict__ spec,
+                                                           const cplx<T>* __restrict__ tw, Geo g) {
   constexpr int G = N / R1, PER = R1 / G;
   static_assert(R1 % G == 0, "each thread takes whole G-point transforms");
-  extern __shared__ __align__(16) float fz_smem[];
-  cplx<float>* xs = reinterpret_cast<cplx<float>*>(fz_smem);   // [TM][N + 1] (padded against bank conflicts)
-  cplx<float>* twl = xs + TM * (N + 1);                          // [N]
+  extern __shared__ __align__(16) unsigned char fz_smem[];
+  cplx<T>* xs = reinterpret_cast<cplx<T>*>(fz_smem);   // [TM][N + 1] (padded against bank conflicts)
+  cplx<T>* twl = xs + TM * (N + 1);                      // [N]
   const int tm = threadIdx.x, gi = threadIdx.y, tid = gi * TM + tm;
   for (int e = tid; e < N; e += TM * G) {
-    cplx<float> t = tw[e];
+    cplx<T> t = tw[e];
     if (INV) t.y = -t.y;
     twl[e] = t;
   }
   const int m = blockIdx.x * TM + tm;
   const bool live = m < g.mh;
-  cplx<float>* col = spec + (size_t)blockIdx.y * N * g.mp + (live ? m : 0);
-  cplx<float> v[R1];
+  cplx<T>* col = spec + (size_t)blockIdx.y * N * g.mp + (live ? m : 0);
+  cplx<T> v[R1];
 #pragma unroll
-  for (int r = 0; r < R1; ++r) v[r] = live ? col[(size_t)(gi + G * r) * g.mp] : cplx<float>{0.f, 0.f};
+  for (int r = 0; r < R1; ++r) v[r] = live ? col[(size_t)(gi + G * r) * g.mp] : cplx<T>{T(0), T(0)};
   __syncthreads();   // the twiddle table
   rfft::dft<INV, R1>(v);
-  cplx<float>* xm = xs + tm * (N + 1);
+  cplx<T>* xm = xs + tm * (N + 1);
   rfft::static_for<0, R1>([&](auto kc) {
     constexpr int k1 = decltype(kc)::value;
     xm[k1 * G + gi] = cmul(v[rfft::bitrev(k1, R1)], twl[gi * k1]);
@@ -638,7 +651,7 @@ __global__ void __launch_bounds__(TM*(N / R1)) k_fft_z_reg(cplx<float>* __restri
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int k1 = gi * PER + p;
-    cplx<float> w[G];
+    cplx<T> w[G];
 #pragma unroll
     for (int q = 0; q < G; ++q) w[q] = xm[k1 * G + q];
     rfft::dft<INV, G>(w);
@@ -651,10 +664,10 @@ __global__ void __launch_bounds__(TM*(N / R1)) k_fft_z_reg(cplx<float>* __restri
   }
 }
 
-template <int N, int R1, int TM>
-cudaError_t launch_fft_z_reg(cplx<float>* spec, const cplx<float>* tw, const Geo& g, bool inverse, cudaStream_t s) {
+template <int N, int R1, int TM, typename T>
+cudaError_t launch_fft_z_reg(cplx<T>* spec, const cplx<T>* tw, const Geo& g, bool inverse, cudaStream_t s) {
   constexpr int G = N / R1;
-  const size_t smem = sizeof(cplx<float>) * ((size_t)TM * (N + 1) + N);
+  const size_t smem = sizeof(cplx<T>) * ((size_t)TM * (N + 1) + N);
   const dim3 grd((unsigned)((g.mh + TM - 1) / TM), (unsigned)g.nyc);
   auto go = [&](auto kern) {
     if (smem > 48 * 1024) {
@@ -664,23 +677,21 @@ cudaError_t launch_fft_z_reg(cplx<float>* spec, const cplx<float>* tw, const Geo
     kern<<<grd, dim3(TM, G), smem, s>>>(spec, tw, g);
     return cudaGetLastError();
   };
-  return inverse ? go(k_fft_z_reg<N, R1, TM, true>) : go(k_fft_z_reg<N, R1, TM, false>);
+  return inverse ? go(k_fft_z_reg<N, R1, TM, true, T>) : go(k_fft_z_reg<N, R1, TM, false, T>);
 }
 
 template <typename T>
 cudaError_t launch_fft_z(cplx<T>* spec, const cplx<T>* tw_z, const Geo& g, bool inverse, cudaStream_t s) {
-  if constexpr (sizeof(T) == sizeof(float)) {
-    // register transforms for 16 <= Nz <= 512 unless the stage-by-stage kernel is asked for
-    if (g.lc_fftz_ty != 64) {
-      switch (g.nz) {
-        case 16: return launch_fft_z_reg<16, 4, 32>(spec, tw_z, g, inverse, s);
-        case 32: return launch_fft_z_reg<32, 8, 32>(spec, tw_z, g, inverse, s);
-        case 64: return launch_fft_z_reg<64, 8, 32>(spec, tw_z, g, inverse, s);
-        case 128: return launch_fft_z_reg<128, 16, 32>(spec, tw_z, g, inverse, s);
-        case 256: return launch_fft_z_reg<256, 16, 16>(spec, tw_z, g, inverse, s);
-        case 512: return launch_fft_z_reg<512, 32, 8>(spec, tw_z, g, inverse, s);
-        default: break;
-      }
+  // register transforms for 16 <= Nz <= 512 unless the stage-by-stage kernel is asked for
+  if (g.lc_fftz_ty != 64) {
+    switch (g.nz) {
+      case 16: return launch_fft_z_reg<16, 4, 32, T>(spec, tw_z, g, inverse, s);
+      case 32: return launch_fft_z_reg<32, 8, 32, T>(spec, tw_z, g, inverse, s);
+      case 64: return launch_fft_z_reg<64, 8, 32, T>(spec, tw_z, g, inverse, s);
+      case 128: return launch_fft_z_reg<128, 16, 32, T>(spec, tw_z, g, inverse, s);
+      case 256: return launch_fft_z_reg<256, 16, 16, T>(spec, tw_z, g, inverse, s);
+      case 512: return launch_fft_z_reg<512, 32, 8, T>(spec, tw_z, g, inverse, s);
+      default: break;
     }
   }
   int TM = (int)(128 / sizeof(cplx<T>));   // one 128-byte segment of each z-row

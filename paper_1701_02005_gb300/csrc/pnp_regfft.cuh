@@ -1,4 +1,4 @@
-// Register FFTs for the FP32 transforms of the mixed path.
+// Register FFTs (FP32 for the mixed path, FP64 for the FP64 path).
 //
 // A length-N transform is split N = R1 x G (Cooley-Tukey, one level): with
 // n = g + G r and k = k1 + R1 k2,
@@ -87,40 +87,41 @@ constexpr int bitrev(int k, int M) {
   return r;
 }
 
-// z W_M^I (forward) or z conj(W_M^I) (inverse), W_M = exp(-2 pi i / M)
-template <bool INV, int I, int M>
-__host__ __device__ __forceinline__ cplx<float> twiddle(cplx<float> z) {
+// z W_M^I (forward) or z conj(W_M^I) (inverse), W_M = exp(-2 pi i / M), in
+// the precision T of the transform (float or double)
+template <bool INV, int I, int M, typename T>
+__host__ __device__ __forceinline__ cplx<T> twiddle(cplx<T> z) {
   if constexpr (I == 0) {
     return z;
   } else if constexpr (4 * I == M) {
-    return INV ? cplx<float>{-z.y, z.x} : cplx<float>{z.y, -z.x};
+    return INV ? cplx<T>{-z.y, z.x} : cplx<T>{z.y, -z.x};
   } else {
-    constexpr float c = (float)cos2pi(I, M);
-    constexpr float s = (INV ? 1.0f : -1.0f) * (float)sin2pi(I, M);
+    constexpr T c = (T)cos2pi(I, M);
+    constexpr T s = (INV ? T(1) : T(-1)) * (T)sin2pi(I, M);
     return {z.x * c - z.y * s, z.x * s + z.y * c};
   }
 }
 
-template <bool INV, int HALF, int B, int I>
-__host__ __device__ __forceinline__ void dif_butterflies(cplx<float>* v) {
+template <bool INV, int HALF, int B, int I, typename T>
+__host__ __device__ __forceinline__ void dif_butterflies(cplx<T>* v) {
   if constexpr (I < HALF) {
-    const cplx<float> a = v[B + I], c = v[B + I + HALF];
+    const cplx<T> a = v[B + I], c = v[B + I + HALF];
     v[B + I] = cadd(a, c);
     v[B + I + HALF] = twiddle<INV, I, 2 * HALF>(csub(a, c));
     dif_butterflies<INV, HALF, B, I + 1>(v);
   }
 }
 
-template <bool INV, int M, int HALF, int B>
-__host__ __device__ __forceinline__ void dif_blocks(cplx<float>* v) {
+template <bool INV, int M, int HALF, int B, typename T>
+__host__ __device__ __forceinline__ void dif_blocks(cplx<T>* v) {
   if constexpr (B < M) {
     dif_butterflies<INV, HALF, B, 0>(v);
     dif_blocks<INV, M, HALF, B + 2 * HALF>(v);
   }
 }
 
-template <bool INV, int M, int HALF>
-__host__ __device__ __forceinline__ void dif_stages(cplx<float>* v) {
+template <bool INV, int M, int HALF, typename T>
+__host__ __device__ __forceinline__ void dif_stages(cplx<T>* v) {
   if constexpr (HALF >= 1) {
     dif_blocks<INV, M, HALF, 0>(v);
     dif_stages<INV, M, HALF / 2>(v);
@@ -128,8 +129,8 @@ __host__ __device__ __forceinline__ void dif_stages(cplx<float>* v) {
 }
 
 // In-place M-point DFT of v[0..M); the result X[k] is left at v[bitrev(k, M)].
-template <bool INV, int M>
-__host__ __device__ __forceinline__ void dft(cplx<float>* v) {
+template <bool INV, int M, typename T>
+__host__ __device__ __forceinline__ void dft(cplx<T>* v) {
   dif_stages<INV, M, M / 2>(v);
 }
 
