@@ -245,6 +245,137 @@ def run_large(args, B, Solver, torch):
 
 
 # --------------------------------------------------------------------------
+# Learned wall model at the workload's scale: the turbulent flow at V = 5
+# resolved on 256x193x256 (mixed precision) is the truth; the coarse grid keeps
+# every 4th y-face and every 2nd x/z cell (128x49x128).  Training pairs the
+# coarse run's near-wall features with the fine run's filtered labels over
+# consecutive windows of the fine run (pass 0: coarse run alone; passes 1, 2:
+# coarse run coupled to the previous network, dataset aggregation); a later,
+# unseen window judges c_f against the fine run, and times fine and coarse.
+WM = dict(V=5.0, rx=2, ry=4, window=1000, every=2, spinup=3000, passes=3, iters=3000, batch=65536, chunk=20,
+          mode=2, relax=1.0, potential_gain=0.3, flux_gain=0.3, seed=1705, amp=0.3)
+
+
+def run_wallmodel(args, B, Solver, torch):
+    import numpy as np
+
+    from paper_1701_02005_gb300 import wallmodel as wm
+
+    c = dict(WM)
+    if args.wm_edl is not None:
+        c["potential_gain"], c["flux_gain"] = args.wm_edl
+    nx, ny, nz, st = WL["nx"], WL["ny"], WL["nz"], WL["stretch"]
+    dt = stable_dt(nx, ny, WL["Re"], WL["lam"], c["V"], st)[0]
+    yf = np.tanh(st * (np.arange(ny) * 2.0 / (ny - 1) - 1.0)) / math.tanh(st)
+    yf[0], yf[-1] = -1.0, 1.0
+    mk = lambda n, m, k, faces: Solver(n, m, k, WL["Lx"], WL["Lz"], precision=B.PNP_MIXED, y_faces=faces)
+    fine = mk(nx, ny, nz, yf)
+    fine.set_params(WL["Re"], WL["lam"], WL["Sc"], c["V"], WL["beta"])
+    fine.init_state(B.PNP_IC_PB, c["seed"], c["amp"])
+    ncx, ncy, ncz = nx // c["rx"], (ny - 1) // c["ry"] + 1, nz // c["rx"]
+    yfc = yf[::c["ry"]].copy()
+
+    def coarse():
+        s = mk(ncx, ncy, ncz, yfc)
+        s.set_params(WL["Re"], WL["lam"], WL["Sc"], c["V"], WL["beta"])
+        return s
+
+    def couple(s):
+        wm.set_coupling(s, c["mode"], c["relax"], c["potential_gain"], c["flux_gain"])
+
+    t0 = time.perf_counter()
+    fine.step(c["spinup"], dt)
+    fine.synchronize()
+    rows = 2 * ncz * ncx
+    net, Xs, Ts, losses = None, [], [], []
+    sc = coarse()
+    for p in range(c["passes"]):
+        wm.restrict(fine, sc)
+        if net is not None:
+            couple(sc)
+        for n in range(c["window"] // c["every"]):
+            Xs.append(wm.features(sc, 8))
+            Ts.append(wm.labels(fine, sc))
+            fine.step(c["every"], dt)
+            if net is None:
+                sc.step(c["every"], dt)
+            else:
+                wm.step_with_model(sc, net, c["every"], dt)
+        wm.set_slip(sc, None, None)
+        wm.clear_edl(sc)
+        X, T = torch.cat(Xs), torch.cat(Ts)
+        if net is None:
+            xs, ts = X.mean(0).double(), T.mean(0).double()
+            xsd = torch.maximum(X.double().std(0), 1e-2 * torch.clamp(xs.abs(), min=1e-2))
+            tsd = torch.maximum(T.double().std(0), 1e-2 * torch.clamp(ts.abs(), min=1e-4))
+            net = wm.MLP(max(c["batch"], rows), seed=c["seed"])
+            net.set_normalization(xs.cpu().numpy(), (1.0 / xsd).cpu().numpy(), ts.cpu().numpy(),
+                                  (1.0 / tsd).cpu().numpy())
+        lr0, lr1 = (2e-3, 5e-4) if p == 0 else (1e-3, 3e-4)
+        nb = X.shape[0] // c["batch"]
+        perm = torch.randperm(X.shape[0], device=X.device)
+        Xp, Tp = X[perm].contiguous(), T[perm].contiguous()
+        l0 = net.train_step(Xp[:c["batch"]], Tp[:c["batch"]], lr0, want_loss=True)
+        for it in range(c["iters"]):
+            b = it % nb
+            net.train_step(Xp[b * c["batch"]:(b + 1) * c["batch"]], Tp[b * c["batch"]:(b + 1) * c["batch"]],
+                           lr0 if it < c["iters"] // 2 else lr1)
+        l1 = net.train_step(Xp[:c["batch"]], Tp[:c["batch"]], lr1, want_loss=True)
+        losses.append([l0, l1])
+        del Xp, Tp, perm
+    train_s = time.perf_counter() - t0
+    # the judged window: fine truth, coarse alone, coarse coupled to the network
+    sp, sm = coarse(), coarse()
+    wm.restrict(fine, sp)
+    wm.restrict(fine, sm)
+    couple(sm)
+    cf = {"fine": [], "plain": [], "coupled": []}
+    for n in range(c["window"] // c["chunk"]):
+        fine.step(c["chunk"], dt)
+        sp.step(c["chunk"], dt)
+        wm.step_with_model(sm, net, c["chunk"], dt)
+        cf["fine"].append(fine.diagnostics()["cf"])
+        cf["plain"].append(sp.diagnostics()["cf"])
+        cf["coupled"].append(sm.diagnostics()["cf"])
+    f = np.array(cf["fine"])
+    err = lambda a: float(np.mean(np.abs(np.array(a) - f) / f))
+    merr = lambda a: float(abs(np.mean(a) - np.mean(f)) / np.mean(f))
+
+    # time per step: fine, coarse alone, coarse with the model
+    def timed(fn, s, n=100):
+        fn(10)
+        s.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s.stream)
+        fn(n)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    ms_f = timed(lambda n: fine.step(n, dt), fine)
+    ms_p = timed(lambda n: sp.step(n, dt), sp)
+    ms_c = timed(lambda n: wm.step_with_model(sm, net, n, dt), sm)
+    out = {"workload": f"fine {nx}x{ny}x{nz} (mixed) -> coarse {ncx}x{ncy}x{ncz}, Re {WL['Re']:g}, "
+                       f"lambda_D/h {WL['lam']}, V {c['V']:g}, dt {dt:.4g}, {c['spinup']} spin-up steps, "
+                       f"{c['passes']} training windows + 1 judged window of {c['window']} steps",
+           "coupling": {k: c[k] for k in ("mode", "relax", "potential_gain", "flux_gain")},
+           "training": {"rows": int(sum(x.shape[0] for x in Xs)), "snapshots": len(Xs), "iters_per_pass": c["iters"],
+                        "batch": c["batch"], "loss_first_last": losses, "seconds": train_s},
+           "cf_err_plain": err(cf["plain"]), "cf_err_coupled": err(cf["coupled"]),
+           "mean_cf": {k: float(np.mean(v)) for k, v in cf.items()},
+           "mean_cf_err_plain": merr(cf["plain"]), "mean_cf_err_coupled": merr(cf["coupled"]),
+           "cf_series": {k: [round(x, 6) for x in v[::5]] for k, v in cf.items()},
+           "ms_per_step": {"fine": ms_f, "coarse": ms_p, "coarse_with_model": ms_c},
+           "speedup_coarse_with_model_over_fine": ms_f / ms_c, "mlp_status": net.status(),
+           "status": {"fine": fine.diagnostics()["status"], "coupled": sm.diagnostics()["status"]}}
+    for s in (fine, sc, sp, sm):
+        s.close()
+    net.close()
+    return out
+
+
+# --------------------------------------------------------------------------
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
 
@@ -749,6 +880,10 @@ def run_ours(args):
     if not args.no_large:
         large = run_large(args, B, Solver, torch)
 
+    wallmodel = None
+    if rank == 0 and not args.no_wallmodel:
+        wallmodel = run_wallmodel(args, B, Solver, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -764,6 +899,7 @@ def run_ours(args):
         "mixed_vs_fp64": cmp,
         "ensemble": ensemble,
         "large_case": large,
+        "wallmodel": wallmodel,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "launch_config": launch_cfg,
@@ -813,6 +949,10 @@ def main():
                     help="store the CN right-hand sides instead of fusing the forward elimination into the stencil")
     ap.add_argument("--ensemble-steps", type=int, default=20)
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-wallmodel", action="store_true")
+    ap.add_argument("--wallmodel", action="store_true", help="only the learned wall-model block (fine 256x193x256 "
+                    "at V = 5 against coarse 128x49x128 with and without the network)")
+    ap.add_argument("--wm-edl", type=float, nargs=2, default=None, metavar=("POTENTIAL_GAIN", "FLUX_GAIN"))
     ap.add_argument("--large-steps", type=int, default=20)
     ap.add_argument("--grid", default=None,
                     help="NX,NY,NZ override of the workload grid (small cases for profiler captures only)")
@@ -830,6 +970,14 @@ def main():
         return run_curve(args)
     if args.sweep:
         return run_sweep(args)
+    if args.wallmodel:
+        import torch
+
+        from paper_1701_02005_gb300 import binding as B
+        from paper_1701_02005_gb300.solver import Solver
+
+        print(json.dumps({"wallmodel": run_wallmodel(args, B, Solver, torch)}), flush=True)
+        return 0
     return run_ours(args)
 
 

@@ -428,8 +428,32 @@ int pnp_set_wall_stress(pnp_ctx* ctx, const float* X_dev, int ncells, const floa
  * the wall-shear rates used each step move that fraction of the way from the
  * previous step's to the new prediction (1 = no relaxation). */
 int pnp_set_wallmodel_coupling(pnp_ctx* ctx, int mode, double relax);
+/* Double-layer coupling of pnp_step_wallmodel, beside the wall shear (the
+ * network's columns 2-4; no counterpart in the paper, which resolves the layer).
+ * potential_gain in [0, 1]: before each step the wall potentials move by
+ * potential_gain (phi_pred - phi_1) per wall column, phi_1 the first cell's
+ * potential perturbation Phi - V y_c and phi_pred the predicted one, as offsets
+ * on top of the uniform walls -V, +V (within +-max(1, |V|)), and the potential
+ * of the present ions is solved again under them.  flux_gain in [0, 1]: after
+ * each step, ions move across the first interior face of each wall column so
+ * that the face's total flux F = v c_f - D (dc/dy + s c_f dPhi/dy) moves that
+ * fraction of the way to the predicted one over dt; conservative per column, a
+ * cell gives at most half its ions.  0 switches a part off; potential_gain 0
+ * also removes the offsets (the uniform walls return and the potential is
+ * solved again).  PNP_ERR_UNSUPPORTED from a coupled step when a wall-potential
+ * map of pnp_set_wall_potential is set. */
+int pnp_set_wallmodel_edl(pnp_ctx* ctx, double potential_gain, double flux_gain);
+/* One potential-offset update from device feature rows X [2 Nz Nx][5 ncells]
+ * and outputs Y [2 Nz Nx][5] (the step pnp_step_wallmodel takes before each
+ * step; needs potential_gain > 0).  Stream-ordered on the context's stream. */
+int pnp_set_wall_edl(pnp_ctx* ctx, const float* X_dev, int ncells, const float* Y_dev);
+/* One ion-flux transfer over dt from device outputs Y [2 Nz Nx][5] (the step
+ * pnp_step_wallmodel takes after each step; needs flux_gain > 0 and Nyc >= 4,
+ * so that the two walls' cell pairs are disjoint; PNP_ERR_ARG otherwise). */
+int pnp_correct_wall_flux(pnp_ctx* ctx, const float* Y_dev, double dt);
 /* nsteps steps of the coarse solver with the wall model: before each step,
- * features (8 cells) -> network -> (relaxed) wall rates -> wall slip or stress. */
+ * features (8 cells) -> network -> (relaxed) wall rates -> wall slip or stress
+ * [-> wall-potential offsets]; after it [-> ion-flux transfer]. */
 int pnp_step_wallmodel(pnp_ctx* ctx, pnp_mlp* mlp, int nsteps, double dt);
 
 /* Launch sites timed by pnp_profile, in launch order within a substage. */

@@ -7,7 +7,9 @@ fine state onto a coarse grid made of every ry-th y-face and rx x rz cell
 blocks, near-wall feature columns in the wall frame (rotation (x, y) -> (-x,
 -y) with c+ <-> c-, Phi -> -Phi maps the top wall onto the bottom), training
 labels (filtered fine wall shear rates, first-cell potential perturbation,
-ion fluxes through the first coarse face), and the
+ion fluxes through the first coarse face), the double-layer coupling that
+imposes the predicted first-cell potential (wall-potential offsets) and ion
+fluxes (conservative transfers across the first face), and the
 MLP 40 -> 128 x 4 -> 5 with erf-GELU, MSE loss on normalised outputs,
 backpropagation and Adam.  Pinned by tests/test_oracle_wall.py.
 """
@@ -95,6 +97,65 @@ def wall_labels(gf, gc, prm, st):
         T[rows, 3] = _block_mean(gf, gc, f3).ravel()
         T[rows, 4] = _block_mean(gf, gc, f4).ravel()
     return T
+
+
+# ---------------------------------------------------------------------------
+# Double-layer coupling: the network's columns 2-4 imposed on a coarse state
+# ---------------------------------------------------------------------------
+def edl_offsets(g, X, Y, ncells, gain, B, T, lim):
+    """Wall-potential offsets (lab frame, on top of the uniform walls -V, +V)
+    after one update: each wall column's offset moves by gain (phi_pred - phi_1),
+    phi_1 the feature row's first-cell potential perturbation, phi_pred column 2
+    of the prediction (wall frame: the top wall's sign flips back); clipped to
+    +-lim, a non-finite step leaves the offset alone."""
+    P = g.nz * g.nx
+    db = gain * (Y[:P, 2].astype(np.float64) - X[:P, 4 * ncells].astype(np.float64))
+    dt = gain * (Y[P:, 2].astype(np.float64) - X[P:, 4 * ncells].astype(np.float64))
+    Bn, Tn = np.asarray(B, dtype=np.float64).ravel().copy(), np.asarray(T, dtype=np.float64).ravel().copy()
+    okb, okt = np.isfinite(db), np.isfinite(dt)
+    Bn[okb] = np.clip(Bn[okb] + db[okb], -lim, lim)
+    Tn[okt] = np.clip(Tn[okt] - dt[okt], -lim, lim)
+    return Bn.reshape(g.nz, g.nx), Tn.reshape(g.nz, g.nx)
+
+
+def face_fluxes(g, prm, st, jf):
+    """Total ion fluxes (lab frame, +y) through interior y-face jf, the labels'
+    discrete form F = v c_f - D (dc/dy + s c_f dPhi/dy), c_f the face mean."""
+    a, b = jf - 1, jf
+    dP = (st.Phi[b] - st.Phi[a]) / g.h[jf]
+    cpf, cmf = 0.5 * (st.cp[a] + st.cp[b]), 0.5 * (st.cm[a] + st.cm[b])
+    Fp = st.v[jf] * cpf - prm.D * ((st.cp[b] - st.cp[a]) / g.h[jf] + cpf * dP)
+    Fm = st.v[jf] * cmf - prm.D * ((st.cm[b] - st.cm[a]) / g.h[jf] - cmf * dP)
+    return Fp, Fm
+
+
+def wall_flux_fix(g, prm, st, Y, gain, dt):
+    """c+, c- after one ion-flux transfer: across the first interior face of each
+    wall column (face 1 at the bottom, Nyc-1 at the top) the flux grows by
+    gain (F_pred - F) (F_pred columns 3, 4 of the prediction in the wall frame)
+    for a time dt, moving ions from one of the two cells sharing the face to the
+    other; the cell that gives ions gives at most half of them."""
+    if g.nyc < 4:
+        raise ValueError("the two walls' transfers need disjoint cells (Nyc >= 4)")
+    P = g.nz * g.nx
+    cp, cm = st.cp.copy(), st.cm.copy()
+    for wall in (0, 1):
+        jf = 1 if wall == 0 else g.nyc - 1
+        a, b = jf - 1, jf
+        Fp, Fm = face_fluxes(g, prm, st, jf)
+        y = Y[wall * P:(wall + 1) * P].astype(np.float64).reshape(g.nz, g.nx, 5)
+        if wall == 0:
+            dFp, dFm = gain * (y[..., 3] - Fp), gain * (y[..., 4] - Fm)
+        else:   # wall frame: away from the top wall is -y, and its column 3 is c-
+            dFm, dFp = -gain * (y[..., 3] + Fm), -gain * (y[..., 4] + Fp)
+        for c, dF in ((cp, dFp), (cm, dFm)):
+            dF = np.where(np.isfinite(dF), dF, 0.0)
+            cap = np.where(dF > 0, 0.5 * np.maximum(c[a], 0.0) * g.dy[a] / dt,
+                           0.5 * np.maximum(c[b], 0.0) * g.dy[b] / dt)
+            dF = np.clip(dF, -cap, cap)
+            c[a] = c[a] - dF * dt / g.dy[a]
+            c[b] = c[b] + dF * dt / g.dy[b]
+    return cp, cm
 
 
 # ---------------------------------------------------------------------------

@@ -124,6 +124,9 @@ EXPORTS = {
     "pnp_step_wallmodel": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double]),
     "pnp_set_wall_stress": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "pnp_set_wallmodel_coupling": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
+    "pnp_set_wallmodel_edl": (C.c_int, [C.c_void_p, C.c_double, C.c_double]),
+    "pnp_set_wall_edl": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "pnp_correct_wall_flux": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double]),
     "pnp_error_string": (C.c_char_p, [C.c_int]),
     "pnp_destroy": (None, [C.c_void_p]),
 }
@@ -222,5 +225,8 @@ pnp_set_wall_slip = _fwd("pnp_set_wall_slip")
 pnp_step_wallmodel = _fwd("pnp_step_wallmodel")
 pnp_set_wall_stress = _fwd("pnp_set_wall_stress")
 pnp_set_wallmodel_coupling = _fwd("pnp_set_wallmodel_coupling")
+pnp_set_wallmodel_edl = _fwd("pnp_set_wallmodel_edl")
+pnp_set_wall_edl = _fwd("pnp_set_wall_edl")
+pnp_correct_wall_flux = _fwd("pnp_correct_wall_flux")
 pnp_error_string = _fwd("pnp_error_string")
 pnp_destroy = _fwd("pnp_destroy")

@@ -1,7 +1,7 @@
 // Wall-model data kernels: restriction of a fine state onto a coarse grid,
 // near-wall feature columns of a state, training labels from a fine state,
-// and the wall slip velocities that couple a wall model into the coarse
-// solver.  (The paper resolves the double layer; the learned wall model that
+// and the wall conditions that couple a wall model into the coarse solver
+// (slip velocities or stresses, wall-potential offsets, ion-flux transfers).  (The paper resolves the double layer; the learned wall model that
 // replaces it on a coarse y-grid has no counterpart in the paper.)
 //
 // Coarse grid: Nx_c = Nx_f / rx, Nz_c = Nz_f / rz, and every ry-th fine
@@ -243,6 +243,96 @@ cudaError_t launch_relax_rates(float* Y, float* prev, int rows, float w, cudaStr
   return cudaGetLastError();
 }
 
+// Potential coupling: the wall-potential offsets (lab frame, relative to the
+// uniform walls -V, +V) move by gain (phi_pred - phi_1) per call, phi_1 the
+// first cell's potential perturbation in the feature row and phi_pred the
+// network's (column 2, wall frame: the top wall's sign is flipped back).
+// Offsets stay within +-lim; a non-finite prediction leaves the offset alone.
+__global__ void k_edl_offsets(const float* __restrict__ X, int ncells, const float* __restrict__ Y, size_t P,
+                              double gain, double lim, double* __restrict__ B, double* __restrict__ T) {
+  const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= P) return;
+  const size_t fs = (size_t)5 * ncells;
+  const double db = gain * ((double)Y[c * 5 + 2] - (double)X[c * fs + 4 * ncells]);
+  const double dt = gain * ((double)Y[(P + c) * 5 + 2] - (double)X[(P + c) * fs + 4 * ncells]);
+  if (isfinite(db)) B[c] = fmin(fmax(B[c] + db, -lim), lim);
+  if (isfinite(dt)) T[c] = fmin(fmax(T[c] - dt, -lim), lim);
+}
+
+// Ion-flux coupling: the total ion fluxes through the first interior face of
+// each wall column (face 1 at the bottom, face Nyc-1 at the top) are moved a
+// fraction gain of the way to the predicted ones (columns 3, 4, wall frame) by
+// transferring ions between the two cells that share the face, over dt:
+// conservative per column.  The transfer out of a cell is limited to half its
+// content; the flux of the state is the discrete one of the labels,
+// F = v c_f - D (dc/dy + s c_f dPhi/dy), c_f the face mean.  With the df
+// shadows of a mixed-precision context (S != null) the corrected cells'
+// shadows are rewritten from the FP64 values.
+template <typename TV>
+__global__ void k_wall_flux_fix(double* __restrict__ cp, double* __restrict__ cm, const double* __restrict__ Phi,
+                                const TV* __restrict__ v, const double* __restrict__ idy,
+                                const double* __restrict__ ih, Geo g, double Dion, const float* __restrict__ Y,
+                                double gain, double dt, float* __restrict__ cpS, float* __restrict__ cpL,
+                                float* __restrict__ cmS, float* __restrict__ cmL, const double* __restrict__ crefp,
+                                const double* __restrict__ crefm) {
+  const size_t P = (size_t)g.nz * g.nx;
+  const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= 2 * P) return;
+  const int wall = (int)(r / P);
+  const size_t col = r - (size_t)wall * P;
+  const int jl = wall == 0 ? 0 : g.nyc - 2, ju = jl + 1, jf = jl + 1;   // cells below / above face jf
+  const size_t ol = (size_t)jl * P + col, ou = (size_t)ju * P + col;
+  const double ihf = ih[jf];
+  const double vf = (double)v[(size_t)jf * P + col];
+  const double dP = (Phi[ou] - Phi[ol]) * ihf;
+  const double cpf = 0.5 * (cp[ol] + cp[ou]), cmf = 0.5 * (cm[ol] + cm[ou]);
+  const double Fp = vf * cpf - Dion * ((cp[ou] - cp[ol]) * ihf + cpf * dP);
+  const double Fm = vf * cmf - Dion * ((cm[ou] - cm[ol]) * ihf - cmf * dP);
+  const float* y = Y + r * 5;
+  // wall frame -> lab frame (+y): the top wall's counter-ion column is c-, fluxes flip sign
+  double dFp, dFm;
+  if (wall == 0) {
+    dFp = gain * ((double)y[3] - Fp);
+    dFm = gain * ((double)y[4] - Fm);
+  } else {
+    dFm = -gain * ((double)y[3] + Fm);
+    dFp = -gain * ((double)y[4] + Fp);
+  }
+  auto apply = [&](double* c, double dF, float* S, float* L, const double* cref) {
+    if (!isfinite(dF)) return;
+    // the cell that loses ions gives at most half of them
+    const double cap = dF > 0.0 ? 0.5 * fmax(c[ol], 0.0) / (idy[jl] * dt) : 0.5 * fmax(c[ou], 0.0) / (idy[ju] * dt);
+    dF = fmin(fmax(dF, -cap), cap);
+    c[ol] -= dF * dt * idy[jl];
+    c[ou] += dF * dt * idy[ju];
+    if (S) {
+      const double a = c[ol] - cref[jl], b = c[ou] - cref[ju];
+      S[ol] = (float)a;
+      L[ol] = (float)(a - (double)S[ol]);
+      S[ou] = (float)b;
+      L[ou] = (float)(b - (double)S[ou]);
+    }
+  };
+  apply(cp, dFp, cpS, cpL, crefp);
+  apply(cm, dFm, cmS, cmL, crefm);
+}
+
+cudaError_t launch_edl_offsets(const float* X, int ncells, const float* Y, size_t P, double gain, double lim, double* B,
+                               double* T, cudaStream_t s) {
+  k_edl_offsets<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(X, ncells, Y, P, gain, lim, B, T);
+  return cudaGetLastError();
+}
+
+template <typename TV>
+cudaError_t launch_wall_flux_fix(double* cp, double* cm, const double* Phi, const TV* v, const double* idy,
+                                 const double* ih, const Geo& g, double Dion, const float* Y, double gain, double dt,
+                                 const FluxFixShadows& sh, cudaStream_t s) {
+  const size_t n = 2 * (size_t)g.nz * g.nx;
+  k_wall_flux_fix<TV><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(cp, cm, Phi, v, idy, ih, g, Dion, Y, gain, dt, sh.cpS,
+                                                                 sh.cpL, sh.cmS, sh.cmL, sh.crefp, sh.crefm);
+  return cudaGetLastError();
+}
+
 // ---- launchers ----
 template <typename T>
 cudaError_t launch_restrict(const T* f, const double* dyf, const WallMap& wm, double* out, bool vfield, cudaStream_t s) {
@@ -299,6 +389,12 @@ template cudaError_t launch_wall_labels<double>(const double*, const double*, co
 template cudaError_t launch_wall_labels<float>(const float*, const float*, const float*, const double*, const double*,
                                                const double*, const double*, const double*, const double*,
                                                const WallMap&, double, double, double, double, float*, cudaStream_t);
+template cudaError_t launch_wall_flux_fix<double>(double*, double*, const double*, const double*, const double*,
+                                                  const double*, const Geo&, double, const float*, double, double,
+                                                  const FluxFixShadows&, cudaStream_t);
+template cudaError_t launch_wall_flux_fix<float>(double*, double*, const double*, const float*, const double*,
+                                                 const double*, const Geo&, double, const float*, double, double,
+                                                 const FluxFixShadows&, cudaStream_t);
 template cudaError_t launch_set_slip<double>(const float*, int, const float*, size_t, double, double, double, double*,
                                              double*, cudaStream_t);
 template cudaError_t launch_set_slip<float>(const float*, int, const float*, size_t, double, double, double, float*,

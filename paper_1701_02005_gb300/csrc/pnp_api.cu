@@ -122,6 +122,10 @@ struct pnp_ctx {
   float wm_relax = 1.f;
   bool wm_have_prev = false;
   float* featYprev = nullptr;
+  // double-layer coupling: gains of the wall-potential offsets and of the ion-flux
+  // transfers (0: off); edl_map: the wall-potential map holds the offsets
+  double edl_phi_gain = 0.0, edl_flux_gain = 0.0;
+  bool edl_map = false;
   std::vector<double> href_p, href_m, lyc_p, lyc_m;
   bool refs_valid = false;   // references and shadows match the FP64 fields
   bool fp64_fresh = true;    // FP64 c+-, Phi, Hc+- arrays are current (else the shadows are)
@@ -1448,6 +1452,7 @@ int pnp_set_wall_potential(pnp_ctx* c, const double* bottom, const double* top) 
   if (!c) return PNP_ERR_ARG;
   if (!c->have_params) return PNP_ERR_STATE;
   if ((bottom == nullptr) != (top == nullptr)) return PNP_ERR_ARG;
+  c->edl_map = false;   // a map (or the uniform walls) replaces the wall model's offsets
   const size_t P = (size_t)c->g.nz * c->g.nx;
   if (!bottom) {
     c->wall_map = false;
@@ -2440,10 +2445,98 @@ int pnp_set_wallmodel_coupling(pnp_ctx* c, int mode, double relax) {
   return PNP_OK;
 }
 
+namespace {
+// Lift of the offset map: the charge-free potential of wall offsets B, T kept
+// with their plane means (relative to the uniform walls, so V and the constant
+// offset stay those of pnp_set_params).
+cudaError_t edl_lift(pnp_ctx* c) {
+  const Metrics m = metrics(c);
+  cplx<double>* spec = (cplx<double>*)c->spec;
+  const cplx<double>* twx = (const cplx<double>*)c->twx_d;
+  const cplx<double>* twp = (const cplx<double>*)c->twp_d;
+  const cplx<double>* twz = (const cplx<double>*)c->twz_d;
+  cudaError_t e = launch_wall_lift_source(c->sreal, c->wallB_d, c->wallT_d, 0.0, 0.0, c->yc_d, c->g, c->stream);
+  if (e == cudaSuccess)
+    e = launch_fft_x_fwd<double, double>(PoissonSrc::Plain, nullptr, nullptr, nullptr, nullptr, nullptr, c->sreal, 1.0,
+                                         c->g, m, spec, twx, twp, c->stream);
+  if (e == cudaSuccess) e = spectral_solve<double>(c, spec, twz, false);
+  if (e == cudaSuccess)
+    e = launch_fft_x_inv<double, double>(PoissonDst::Plain, spec, c->g, m, twx, twp, 0.0, c->lift64, c->stream);
+  if (e == cudaSuccess)
+    e = launch_wall_lift_finish(c->lift64, c->lift32, c->wallB_d, c->wallT_d, 0.0, 0.0, 0.0, c->yc_d, c->g, c->stream);
+  return e;
+}
+
+int edl_potential(pnp_ctx* c, const float* X, int ncells, const float* Y) {
+  if (!c->have_state) return PNP_ERR_STATE;
+  const size_t P = (size_t)c->g.nz * c->g.nx;
+  if (!c->edl_map) {
+    if (c->wall_map) return PNP_ERR_UNSUPPORTED;   // the user's wall-potential map is set
+    CK(cudaMemsetAsync(c->wallB_d, 0, sizeof(double) * P, c->stream));
+    CK(cudaMemsetAsync(c->wallT_d, 0, sizeof(double) * P, c->stream));
+    c->edl_map = true;
+    c->wall_map = true;
+    c->wall_off = 0.0;
+    drop_graph(c);
+  }
+  const double lim = std::max(1.0, std::fabs(c->ph.V));
+  CK(launch_edl_offsets(X, ncells, Y, P, c->edl_phi_gain, lim, c->wallB_d, c->wallT_d, c->stream));
+  CK(edl_lift(c));
+  // the potential of the present ions under the moved walls
+  int r = materialize(c);
+  if (r) return r;
+  CK(c->precision == PNP_FP64 ? potential_solve<double>(c) : potential_solve<float>(c));
+  if (c->precision == PNP_MIXED && c->refs_valid)
+    CK(launch_make_shadows(c->cp, c->cm, c->Phi, c->Hcp, c->Hcm, shadows(c), mixed_refs(c), c->Hrefp_d, c->Hrefm_d,
+                           P, c->nc, c->stream));
+  return PNP_OK;
+}
+
+int flux_fix(pnp_ctx* c, const float* Y, double dt) {
+  if (!c->have_state) return PNP_ERR_STATE;
+  int r = materialize(c);
+  if (r) return r;
+  FluxFixShadows sh{};
+  if (c->precision == PNP_MIXED && c->refs_valid)
+    sh = FluxFixShadows{c->cpS, c->cpL, c->cmS, c->cmL, c->cref64p_d, c->cref64m_d};
+  const cudaError_t e =
+      c->precision == PNP_FP64
+          ? launch_wall_flux_fix<double>(c->cp, c->cm, c->Phi, (const double*)c->v, c->idy_d, c->ih_d, c->g, c->ph.D, Y,
+                                         c->edl_flux_gain, dt, sh, c->stream)
+          : launch_wall_flux_fix<float>(c->cp, c->cm, c->Phi, (const float*)c->v, c->idy_d, c->ih_d, c->g, c->ph.D, Y,
+                                        c->edl_flux_gain, dt, sh, c->stream);
+  return e == cudaSuccess ? PNP_OK : PNP_ERR_CUDA;
+}
+}  // namespace
+
+int pnp_set_wallmodel_edl(pnp_ctx* c, double potential_gain, double flux_gain) {
+  if (!c || !(potential_gain >= 0.0 && potential_gain <= 1.0) || !(flux_gain >= 0.0 && flux_gain <= 1.0))
+    return PNP_ERR_ARG;
+  c->edl_phi_gain = potential_gain;
+  c->edl_flux_gain = flux_gain;
+  if (potential_gain == 0.0 && c->edl_map) {   // the uniform walls return
+    c->edl_map = false;
+    return pnp_set_wall_potential(c, nullptr, nullptr);
+  }
+  return PNP_OK;
+}
+
+int pnp_set_wall_edl(pnp_ctx* c, const float* X, int ncells, const float* Y) {
+  if (!c || !X || !Y || ncells < 1 || ncells > 8 || ncells > c->g.nyc || !(c->edl_phi_gain > 0.0))
+    return PNP_ERR_ARG;
+  return edl_potential(c, X, ncells, Y);
+}
+
+int pnp_correct_wall_flux(pnp_ctx* c, const float* Y, double dt) {
+  if (!c || !Y || !(dt > 0.0) || !(c->edl_flux_gain > 0.0) || c->g.nyc < 4) return PNP_ERR_ARG;
+  return flux_fix(c, Y, dt);
+}
+
 int pnp_step_wallmodel(pnp_ctx* c, pnp_mlp* m, int nsteps, double dt) {
   if (!c || !m || nsteps < 0) return PNP_ERR_ARG;
   const int rows = 2 * c->g.nz * c->g.nx;
   if (rows > m->max_batch) return PNP_ERR_ARG;
+  if (c->edl_flux_gain > 0.0 && c->g.nyc < 4) return PNP_ERR_ARG;
   for (int n = 0; n < nsteps; ++n) {
     int r = pnp_wall_features(c, 8, c->featX);
     if (r) return r;
@@ -2455,8 +2548,16 @@ int pnp_step_wallmodel(pnp_ctx* c, pnp_mlp* m, int nsteps, double dt) {
     }
     r = set_wall_values(c, c->featX, 8, c->featY, c->wm_mode >= 1);
     if (r) return r;
+    if (c->edl_phi_gain > 0.0) {
+      r = edl_potential(c, c->featX, 8, c->featY);
+      if (r) return r;
+    }
     r = pnp_step(c, 1, dt);
     if (r) return r;
+    if (c->edl_flux_gain > 0.0) {
+      r = flux_fix(c, c->featY, dt);
+      if (r) return r;
+    }
   }
   return PNP_OK;
 }

@@ -35,6 +35,21 @@ cudaError_t launch_relax_rates(float* Y, float* prev, int rows, float w, cudaStr
 // plane means of the wall-shear-rate columns, per wall, broadcast to its rows
 cudaError_t launch_mean_rates(float* Y, int P, cudaStream_t s);
 
+// wall-potential offsets B, T += gain (predicted - present first-cell potential), within +-lim
+cudaError_t launch_edl_offsets(const float* X, int ncells, const float* Y, size_t P, double gain, double lim, double* B,
+                               double* T, cudaStream_t s);
+// df shadows of the ion fields of a mixed-precision context (all null for FP64)
+struct FluxFixShadows {
+  float *cpS, *cpL, *cmS, *cmL;
+  const double *crefp, *crefm;
+};
+// conservative transfer of ions across the first interior face of each wall
+// column towards the predicted fluxes
+template <typename TV>
+cudaError_t launch_wall_flux_fix(double* cp, double* cm, const double* Phi, const TV* v, const double* idy,
+                                 const double* ih, const Geo& g, double Dion, const float* Y, double gain, double dt,
+                                 const FluxFixShadows& sh, cudaStream_t s);
+
 // ---- MLP 40 -> 128 x 4 (erf-GELU) -> 5 ----
 constexpr int kMlpLayers = 5;
 constexpr int kMlpIn = 40;

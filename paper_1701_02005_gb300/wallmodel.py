@@ -125,5 +125,30 @@ def set_slip(solver, X, Y, ncells=8):
                 "pnp_set_wall_slip")
 
 
+def set_coupling(solver, mode=0, relax=1.0, potential_gain=0.0, flux_gain=0.0):
+    """How step_with_model couples the network: wall shear by slip (0), stress (1)
+    or plane-mean stress (2), its relaxation, and the double-layer gains."""
+    B.check(B.pnp_set_wallmodel_coupling(solver.ctx, int(mode), float(relax)), "pnp_set_wallmodel_coupling")
+    B.check(B.pnp_set_wallmodel_edl(solver.ctx, float(potential_gain), float(flux_gain)), "pnp_set_wallmodel_edl")
+
+
+def clear_edl(solver):
+    """Switch the double-layer coupling off and restore the uniform walls."""
+    B.check(B.pnp_set_wallmodel_edl(solver.ctx, 0.0, 0.0), "pnp_set_wallmodel_edl")
+
+
+def set_wall_edl(solver, X, Y, ncells=8):
+    solver.torch.cuda.synchronize(solver.device)
+    B.check(B.pnp_set_wall_edl(solver.ctx, C.c_void_p(X.data_ptr()), int(ncells), C.c_void_p(Y.data_ptr())),
+            "pnp_set_wall_edl")
+    solver.synchronize()
+
+
+def correct_wall_flux(solver, Y, dt):
+    solver.torch.cuda.synchronize(solver.device)
+    B.check(B.pnp_correct_wall_flux(solver.ctx, C.c_void_p(Y.data_ptr()), float(dt)), "pnp_correct_wall_flux")
+    solver.synchronize()
+
+
 def step_with_model(solver, mlp, nsteps, dt):
     B.check(B.pnp_step_wallmodel(solver.ctx, mlp.m, int(nsteps), float(dt)), "pnp_step_wallmodel")

@@ -128,14 +128,16 @@ def _impulsive(s, g, seed, amp=0.02):
 
 
 def wall_model_case(nfine=(32, 65, 32), ry=4, rxz=2, Re=500.0, dt=0.002, nsteps=200, every=2, train_iters=3000,
-                    passes=1, seed_train=31, seed_judge=32):
+                    passes=3, mode=2, relax=1.0, seed_train=31, seed_judge=32, edl=(0.3, 0.3)):
     """Fine DNS data -> trained network -> coarse runs with and without it, judged
     on the friction coefficient against the fine DNS.  Training pairs the coarse
     solver's own near-wall features with the fine run's filtered labels at the
     same time and initial state: data pass 0 from the coarse run without the
-    model, later passes from the coarse run coupled to the previous pass's network."""
+    model, later passes (dataset aggregation) from the coarse run coupled to the
+    previous pass's network in the coupling judged (`mode`, `relax`, `edl`)."""
     import torch
 
+    from paper_1701_02005_gb300 import binding as B
     from paper_1701_02005_gb300 import wallmodel as wm
 
     nx, ny, nz = nfine
@@ -143,11 +145,17 @@ def wall_model_case(nfine=(32, 65, 32), ry=4, rxz=2, Re=500.0, dt=0.002, nsteps=
     gc = o.Grid(nx // rxz, (ny - 1) // ry + 1, nz // rxz, 2 * math.pi, math.pi, y_faces=gf.yf[::ry])
     prm = o.Params(Re=Re, lam=0.05, Sc=1.0, V=2.0, beta=0.5)
     sf, sc, sm = _solver(gf, prm), _solver(gc, prm), _solver(gc, prm)
+
+    def couple(s):
+        B.check(B.pnp_set_wallmodel_coupling(s.ctx, mode, relax), "pnp_set_wallmodel_coupling")
+        B.check(B.pnp_set_wallmodel_edl(s.ctx, float(edl[0]), float(edl[1])), "pnp_set_wallmodel_edl")
+
     Xs, Ts = [], []
     net, norm, losses = None, None, []
     for rnd in range(passes):
         _impulsive(sf, gf, seed_train)
         wm.restrict(sf, sc)
+        couple(sc)
         for n in range(nsteps // every):
             Xs.append(wm.features(sc, 8))
             Ts.append(wm.labels(sf, sc))
@@ -168,19 +176,25 @@ def wall_model_case(nfine=(32, 65, 32), ry=4, rxz=2, Re=500.0, dt=0.002, nsteps=
             norm = (xs, 1.0 / xsd, ts, 1.0 / tsd)
             net = wm.MLP(nsteps // every * passes * 2 * gc.nz * gc.nx, seed=33)
             net.set_normalization(*norm)
-        l0 = net.train_step(X, T, 2e-3, want_loss=True)
+        lr0, lr1 = (2e-3, 5e-4) if rnd == 0 else (1e-3, 3e-4)
+        l0 = net.train_step(X, T, lr0, want_loss=True)
         for it in range(train_iters):
-            net.train_step(X, T, 2e-3 if it < train_iters // 2 else 5e-4)
-        l1 = net.train_step(X, T, 5e-4, want_loss=True)
+            net.train_step(X, T, lr0 if it < train_iters // 2 else lr1)
+        l1 = net.train_step(X, T, lr1, want_loss=True)
         losses.append((l0, l1))
         wm.set_slip(sc, None, None)
-    # judge run (another seed): fine truth, coarse alone, and the network predicting
-    # the wall shear along the coarse trajectory (one-way); the two-way coupled run
-    # (network -> wall slip -> coarse solver) is reported, not asserted
+        wm.clear_edl(sc)
+    # judge run (another seed): fine truth, coarse alone, the network predicting the
+    # wall shear along the uncoupled coarse trajectory (one-way), and the two-way
+    # coupled run (network -> wall conditions -> coarse solver)
     _impulsive(sf, gf, seed_judge)
     wm.restrict(sf, sc)
     wm.restrict(sf, sm)
+    couple(sm)
+    d0 = sm.diagnostics()
+    N_0 = (d0["n_plus"], d0["n_minus"])
     cf_f, cf_p, cf_m, cf_c = [], [], [], []
+    phi_err = {"plain": [], "coupled": []}   # first-cell potential against the filtered fine one
     chunk = 10
     for n in range(nsteps // chunk):
         sf.step(chunk, dt)
@@ -188,25 +202,44 @@ def wall_model_case(nfine=(32, 65, 32), ry=4, rxz=2, Re=500.0, dt=0.002, nsteps=
         wm.step_with_model(sm, net, chunk, dt)
         cf_f.append(sf.diagnostics()["cf"])
         cf_p.append(sc.diagnostics()["cf"])
-        Y = net.forward(wm.features(sc, 8)).cpu().numpy()
+        Xp = wm.features(sc, 8)
+        Y = net.forward(Xp).cpu().numpy()
         cf_m.append(2.0 * prm.nu * float(Y[:, 0].mean()))     # c_f = 2 tau_w / Uw^2, tau_w = nu <du_rel/dy>
         cf_c.append(sm.diagnostics()["cf"])
+        phi_f = wm.labels(sf, sc).cpu().numpy()[:, 2]
+        for key, X in (("plain", Xp), ("coupled", wm.features(sm, 8))):
+            phi_err[key].append(float(np.mean(np.abs(X.cpu().numpy()[:, 4 * 8] - phi_f)) / np.mean(np.abs(phi_f))))
     cf_f, cf_p, cf_m, cf_c = map(np.array, (cf_f, cf_p, cf_m, cf_c))
     err = lambda a: float(np.mean(np.abs(a - cf_f) / cf_f))
+    status = net.status()
+    dm = sm.diagnostics()
+    N_c = (dm["n_plus"], dm["n_minus"])
     for s in (sf, sc, sm):
         s.close()
     net.close()
-    return dict(loss0=losses[0][0], loss1=losses[-1][1], err_plain=err(cf_p), err_model=err(cf_m),
+    return dict(loss0=losses[0][0], loss1=losses[0][1], err_plain=err(cf_p), err_model=err(cf_m),
                 err_coupled=err(cf_c), cf_fine=cf_f.tolist(), cf_plain=cf_p.tolist(), cf_model=cf_m.tolist(),
-                cf_coupled=cf_c.tolist(), rows=int(X.shape[0]))
+                cf_coupled=cf_c.tolist(), rows=int(Xs[0].shape[0] * len(Xs)), status=status, ions_coupled=N_c,
+                ions_start=N_0, err_phi_plain=float(np.mean(phi_err["plain"])),
+                err_phi_coupled=float(np.mean(phi_err["coupled"])))
 
 
 def test_wall_model_gains_over_coarse_solver():
+    """The coarse solver coupled to the network (plane-mean predicted wall stress,
+    wall-potential offsets and ion-flux transfers at gain 0.3, three passes of
+    dataset aggregation) tracks the fine DNS's friction coefficient better than
+    the coarse solver alone, its first-cell potential follows the filtered fine
+    one, and the flux transfers keep the ion numbers."""
     r = wall_model_case()
     print("wall model:", {k: v for k, v in r.items() if not k.startswith("cf_")})
     print("cf fine ", np.round(r["cf_fine"], 6).tolist())
     print("cf plain", np.round(r["cf_plain"], 6).tolist())
     print("cf model", np.round(r["cf_model"], 6).tolist())
     print("cf coupled", np.round(r["cf_coupled"], 6).tolist())
+    assert r["status"] == 0
     assert r["loss1"] < 0.1 * r["loss0"]
     assert r["err_model"] < r["err_plain"], r
+    assert r["err_coupled"] < 0.75 * r["err_plain"], r
+    assert r["err_phi_coupled"] < 0.1 * r["err_phi_plain"], r
+    for n0, n1 in zip(r["ions_start"], r["ions_coupled"]):
+        assert abs(n1 - n0) <= 1e-12 * n0, r
