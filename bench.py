@@ -252,8 +252,8 @@ def run_large(args, B, Solver, torch):
 # consecutive windows of the fine run (pass 0: coarse run alone; passes 1, 2:
 # coarse run coupled to the previous network, dataset aggregation); a later,
 # unseen window judges c_f against the fine run, and times fine and coarse.
-WM = dict(V=5.0, rx=2, ry=4, window=1000, every=2, spinup=3000, passes=3, iters=3000, batch=65536, chunk=20,
-          mode=2, relax=1.0, potential_gain=0.3, flux_gain=0.3, seed=1705, amp=0.3)
+WM = dict(V=5.0, rx=2, ry=4, window=1000, every=2, spinup=8000, layer_steps=1000, passes=3, iters=3000,
+          batch=65536, chunk=20, mode=2, relax=1.0, potential_gain=0.3, flux_gain=0.3, seed=1705, amp=0.3)
 
 
 def run_wallmodel(args, B, Solver, torch):
@@ -270,7 +270,10 @@ def run_wallmodel(args, B, Solver, torch):
     yf[0], yf[-1] = -1.0, 1.0
     mk = lambda n, m, k, faces: Solver(n, m, k, WL["Lx"], WL["Lz"], precision=B.PNP_MIXED, y_faces=faces)
     fine = mk(nx, ny, nz, yf)
-    fine.set_params(WL["Re"], WL["lam"], WL["Sc"], c["V"], WL["beta"])
+    # turbulence first, at V = 0 and the advective dt (about 100 time units), then the
+    # walls charged to V and the double layers formed over layer_steps at the V-limited dt
+    dt0 = stable_dt(nx, ny, WL["Re"], WL["lam"], 0.0, st)[0]
+    fine.set_params(WL["Re"], WL["lam"], WL["Sc"], 0.0, WL["beta"])
     fine.init_state(B.PNP_IC_PB, c["seed"], c["amp"])
     ncx, ncy, ncz = nx // c["rx"], (ny - 1) // c["ry"] + 1, nz // c["rx"]
     yfc = yf[::c["ry"]].copy()
@@ -284,8 +287,12 @@ def run_wallmodel(args, B, Solver, torch):
         wm.set_coupling(s, c["mode"], c["relax"], c["potential_gain"], c["flux_gain"])
 
     t0 = time.perf_counter()
-    fine.step(c["spinup"], dt)
+    fine.step(c["spinup"], dt0)
+    cf_spun = fine.diagnostics()["cf"]
+    fine.set_params(WL["Re"], WL["lam"], WL["Sc"], c["V"], WL["beta"])
+    fine.step(c["layer_steps"], dt)
     fine.synchronize()
+    spin_s = time.perf_counter() - t0
     rows = 2 * ncz * ncx
     net, Xs, Ts, losses = None, [], [], []
     sc = coarse()
@@ -294,6 +301,8 @@ def run_wallmodel(args, B, Solver, torch):
         if net is not None:
             couple(sc)
         for n in range(c["window"] // c["every"]):
+            if n % 50 == 49 and sc.diagnostics()["status"] != 0:
+                break   # a coupled run that left the valid states ends its window early
             Xs.append(wm.features(sc, 8))
             Ts.append(wm.labels(fine, sc))
             fine.step(c["every"], dt)
@@ -304,6 +313,8 @@ def run_wallmodel(args, B, Solver, torch):
         wm.set_slip(sc, None, None)
         wm.clear_edl(sc)
         X, T = torch.cat(Xs), torch.cat(Ts)
+        ok = torch.isfinite(X).all(1) & torch.isfinite(T).all(1)   # rows of a run gone non-finite stay out
+        X, T = X[ok].contiguous(), T[ok].contiguous()
         if net is None:
             xs, ts = X.mean(0).double(), T.mean(0).double()
             xsd = torch.maximum(X.double().std(0), 1e-2 * torch.clamp(xs.abs(), min=1e-2))
@@ -312,7 +323,7 @@ def run_wallmodel(args, B, Solver, torch):
             net.set_normalization(xs.cpu().numpy(), (1.0 / xsd).cpu().numpy(), ts.cpu().numpy(),
                                   (1.0 / tsd).cpu().numpy())
         lr0, lr1 = (2e-3, 5e-4) if p == 0 else (1e-3, 3e-4)
-        nb = X.shape[0] // c["batch"]
+        nb = max(1, X.shape[0] // c["batch"])
         perm = torch.randperm(X.shape[0], device=X.device)
         Xp, Tp = X[perm].contiguous(), T[perm].contiguous()
         l0 = net.train_step(Xp[:c["batch"]], Tp[:c["batch"]], lr0, want_loss=True)
@@ -357,11 +368,13 @@ def run_wallmodel(args, B, Solver, torch):
     ms_p = timed(lambda n: sp.step(n, dt), sp)
     ms_c = timed(lambda n: wm.step_with_model(sm, net, n, dt), sm)
     out = {"workload": f"fine {nx}x{ny}x{nz} (mixed) -> coarse {ncx}x{ncy}x{ncz}, Re {WL['Re']:g}, "
-                       f"lambda_D/h {WL['lam']}, V {c['V']:g}, dt {dt:.4g}, {c['spinup']} spin-up steps, "
+                       f"lambda_D/h {WL['lam']}, V {c['V']:g}, dt {dt:.4g}, {c['spinup']} spin-up steps at V 0, "
                        f"{c['passes']} training windows + 1 judged window of {c['window']} steps",
            "coupling": {k: c[k] for k in ("mode", "relax", "potential_gain", "flux_gain")},
-           "training": {"rows": int(sum(x.shape[0] for x in Xs)), "snapshots": len(Xs), "iters_per_pass": c["iters"],
-                        "batch": c["batch"], "loss_first_last": losses, "seconds": train_s},
+           "spinup": {"steps_at_V0": c["spinup"], "dt_V0": dt0, "cf_after": cf_spun, "cf_laminar": 2.0 / WL["Re"],
+                      "layer_steps_at_V": c["layer_steps"], "seconds": spin_s},
+           "training": {"rows": int(X.shape[0]), "snapshots": len(Xs), "iters_per_pass": c["iters"],
+                        "batch": c["batch"], "loss_first_last": losses, "seconds": train_s - spin_s},
            "cf_err_plain": err(cf["plain"]), "cf_err_coupled": err(cf["coupled"]),
            "mean_cf": {k: float(np.mean(v)) for k, v in cf.items()},
            "mean_cf_err_plain": merr(cf["plain"]), "mean_cf_err_coupled": merr(cf["coupled"]),
@@ -860,17 +873,29 @@ def run_ours(args):
         t0 = time.perf_counter()
         for nm in names:
             B.check(B.pnp_set_state(s.ctx, FIELD_NAMES[nm], host[nm].data_ptr(), 0), "pnp_set_state")
-        for _ in range(Ke):
+        # the diagnostics of every step are read one step behind (pinned records, an
+        # event per post), so the host never stalls the stream
+        raws = [s.diag_buffer(), s.diag_buffer()]
+        evs = [torch.cuda.Event(), torch.cuda.Event()]
+        for k in range(Ke):
             s.step(1, dt)
-            s.diagnostics()
+            s.diagnostics_post(raws[k % 2])
+            evs[k % 2].record(s.stream)
+            if k > 0:
+                evs[(k - 1) % 2].synchronize()
+                s.diagnostics_read(raws[(k - 1) % 2])
+        evs[(Ke - 1) % 2].synchronize()
+        last = s.diagnostics_read(raws[(Ke - 1) % 2])
         out = torch.empty(host["u"].shape, dtype=torch.float64).pin_memory()
         B.check(B.pnp_get_state(s.ctx, B.PNP_U, out.data_ptr(), 0), "pnp_get_state")
         te = time.perf_counter() - t0
         state_bytes = sum(h.numel() * 8 for h in host.values())
         e2e = {"value": n_cells * Ke / te, "unit": UNIT, "h2d_bytes_per_step": state_bytes / Ke,
                "d2h_bytes_per_step": 128 + out.numel() * 8 / Ke, "steps": Ke,
-               "note": "set_state of all 12 fields from pinned host, then per step pnp_step + pnp_diagnostics "
-                       "(D2H, synchronising), then get_state(u) to pinned host"}
+               "last_step_status": last["status"],
+               "note": "set_state of all 12 fields from pinned host, then per step pnp_step + "
+                       "pnp_diagnostics_post (D2H of the step's diagnostics into a pinned record, read one step "
+                       "behind), then get_state(u) to pinned host"}
 
     ensemble = None
     if not args.no_ensemble:

@@ -145,7 +145,10 @@ int pnp_set_yfaces(pnp_ctx* ctx, const double* y_faces_host, int ny);
 
 /* Control parameters (Numerical methods): Re = rho_w U h / eta, debye_len =
  * lambda_D / h, Sc = eta / (rho_w D), wall_potential = V / V_T (the paper's
- * V-hat is 2 V), beta = eps V_T^2 / (eta D) (typically 0.5). */
+ * V-hat is 2 V), beta = eps V_T^2 / (eta D) (typically 0.5).  Restores the
+ * uniform walls -V, +V.  With a state present (parameters changed mid-run) the
+ * potential of the present ions is solved again under the new parameters
+ * (synchronises). */
 int pnp_set_params(pnp_ctx* ctx, double Re, double debye_len, double Sc,
                    double wall_potential, double beta);
 
@@ -194,6 +197,20 @@ int pnp_step(pnp_ctx* ctx, int nsteps, double dt);
  * as double-float pairs), no FP64 copy of the state; the ion numbers and
  * energies agree with their FP64 evaluation to ~1e-13 relative. */
 int pnp_diagnostics(pnp_ctx* ctx, pnp_diag* out);
+
+/* The same diagnostics in two halves, so that a caller can read them every
+ * step without stalling the GPU.  pnp_diagnostics_post queues the reductions
+ * of the current state on the context's stream and a copy of their raw sums
+ * into raw_host (PNP_DIAG_RAW_BYTES bytes, caller-owned; pinned host memory
+ * keeps the copy asynchronous), and returns without waiting; the record also
+ * keeps the host-side values of that moment (time, step count, dt, reference
+ * sums).  Once the stream has passed the post (an event recorded after it, or
+ * a synchronisation), pnp_diagnostics_read turns the record into a pnp_diag
+ * (host work only) and returns its status.  raw_host must not be reused
+ * before then.  pnp_diagnostics is post + synchronise + read. */
+#define PNP_DIAG_RAW_BYTES 256
+int pnp_diagnostics_post(pnp_ctx* ctx, void* raw_host);
+int pnp_diagnostics_read(const pnp_ctx* ctx, const void* raw_host, pnp_diag* out);
 
 /* Adaptive time step (the explicit parts of the scheme -- advection,
  * migration and with it the dielectric relaxation -- bound dt; Numerical

@@ -12,6 +12,7 @@ import os
 from .build import LIB
 
 PNP_OK = 0
+PNP_DIAG_RAW_BYTES = 256
 PNP_ERR_ARG = -1
 PNP_ERR_GRID = -2
 PNP_ERR_WORKSPACE = -3
@@ -74,6 +75,8 @@ EXPORTS = {
     "pnp_field_size": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_size_t)]),
     "pnp_step": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
     "pnp_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(pnp_diag)]),
+    "pnp_diagnostics_post": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "pnp_diagnostics_read": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(pnp_diag)]),
     "pnp_mean_profile": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "pnp_poisson": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "pnp_poisson_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_double),
@@ -182,6 +185,8 @@ pnp_get_state = _fwd("pnp_get_state")
 pnp_field_size = _fwd("pnp_field_size")
 pnp_step = _fwd("pnp_step")
 pnp_diagnostics = _fwd("pnp_diagnostics")
+pnp_diagnostics_post = _fwd("pnp_diagnostics_post")
+pnp_diagnostics_read = _fwd("pnp_diagnostics_read")
 pnp_mean_profile = _fwd("pnp_mean_profile")
 pnp_poisson = _fwd("pnp_poisson")
 pnp_poisson_noalloc = _fwd("pnp_poisson_noalloc")

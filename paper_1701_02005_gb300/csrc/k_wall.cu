@@ -207,26 +207,36 @@ __global__ void k_relax_rates(float* __restrict__ Y, float* __restrict__ prev, i
 }
 
 // Plane means of the two wall-shear-rate columns of each wall's rows (rows
-// [0, P) bottom, [P, 2P) top), written back to every row of that wall.
+// [0, P) bottom, [P, 2P) top) over the rows with finite predictions, written
+// back to every row of that wall.
 __global__ void k_mean_rates(float* __restrict__ Y, int P) {
-  __shared__ float sh[2][256];
+  __shared__ float sh[3][256];
   const int wall = blockIdx.x;
-  float a = 0.f, b = 0.f;
+  float a = 0.f, b = 0.f, n = 0.f;
   for (int r = threadIdx.x; r < P; r += blockDim.x) {
-    a += Y[(size_t)(wall * P + r) * 5 + 0];
-    b += Y[(size_t)(wall * P + r) * 5 + 1];
+    const float ya = Y[(size_t)(wall * P + r) * 5 + 0], yb = Y[(size_t)(wall * P + r) * 5 + 1];
+    if (isfinite(ya) && isfinite(yb)) {   // a non-finite prediction does not enter the mean
+      a += ya;
+      b += yb;
+      n += 1.f;
+    }
   }
   sh[0][threadIdx.x] = a;
   sh[1][threadIdx.x] = b;
+  sh[2][threadIdx.x] = n;
   __syncthreads();
   for (int st = 128; st > 0; st >>= 1) {
     if (threadIdx.x < st) {
       sh[0][threadIdx.x] += sh[0][threadIdx.x + st];
       sh[1][threadIdx.x] += sh[1][threadIdx.x + st];
+      sh[2][threadIdx.x] += sh[2][threadIdx.x + st];
     }
     __syncthreads();
   }
-  const float ma = sh[0][0] / (float)P, mb = sh[1][0] / (float)P;
+  // no finite row: NaN, which the wall-value kernel turns into the no-slip wall
+  const float cnt = sh[2][0];
+  const float ma = cnt > 0.f ? sh[0][0] / cnt : __int_as_float(0x7fc00000);
+  const float mb = cnt > 0.f ? sh[1][0] / cnt : __int_as_float(0x7fc00000);
   for (int r = threadIdx.x; r < P; r += blockDim.x) {
     Y[(size_t)(wall * P + r) * 5 + 0] = ma;
     Y[(size_t)(wall * P + r) * 5 + 1] = mb;

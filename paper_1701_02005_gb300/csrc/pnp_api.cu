@@ -1232,10 +1232,18 @@ int pnp_set_params(pnp_ctx* c, double Re, double lam, double Sc, double V, doubl
   c->ph.Uw = Uw;
   c->V_set = V;
   c->wall_map = false;   // uniform walls -V, +V
+  c->edl_map = false;
   c->wall_off = 0.0;
   c->have_params = true;
   c->cn_dt = NAN;
   drop_graph(c);
+  if (c->have_state) {   // parameters changed mid-run: the potential of the present ions under them
+    int r = materialize(c);
+    if (r) return r;
+    CK(c->precision == PNP_FP64 ? potential_solve<double>(c) : potential_solve<float>(c));
+    CK(cudaStreamSynchronize(c->stream));
+    c->refs_valid = false;
+  }
   return PNP_OK;
 }
 
@@ -1529,9 +1537,25 @@ int pnp_set_limits(pnp_ctx* c, double cfl_max, double dphi_max) {
   return PNP_OK;
 }
 
-int pnp_diagnostics(pnp_ctx* c, pnp_diag* out) {
-  if (!c || !out) return PNP_ERR_ARG;
+namespace {
+// Raw diagnostics record: device sums and status (written by the copies of a
+// post), then the host-side values of the moment of the post.
+struct DiagRaw {
+  double h[kDiagOutSlots];
+  int st[2];
+  double wall_mean[2];   // plane-mean wall velocities (slip walls)
+  double refN_p, refN_m, refH_p, refH_m;
+  double time, last_dt;
+  long long nstep;
+  int from_shadows, slip_on;
+};
+static_assert(sizeof(DiagRaw) <= PNP_DIAG_RAW_BYTES, "raw diagnostics record");
+}  // namespace
+
+int pnp_diagnostics_post(pnp_ctx* c, void* raw_host) {
+  if (!c || !raw_host) return PNP_ERR_ARG;
   if (!c->have_params || !c->have_state) return PNP_ERR_STATE;
+  DiagRaw* R = static_cast<DiagRaw*>(raw_host);
   // mixed precision with valid shadows: straight from the FP32 fields and the
   // df ion state; otherwise from the FP64 arrays (current after pnp_init_state /
   // pnp_set_state, or brought up to date here)
@@ -1551,33 +1575,47 @@ int pnp_diagnostics(pnp_ctx* c, pnp_diag* out) {
           : launch_diagnostics<float>(fields<float>(c), c->g, metrics(c), c->ph, c->diag_partial, kDiagBlocks,
                                       c->diag_out, c->status_d, lim, c->stream);
   if (e != cudaSuccess) return PNP_ERR_CUDA;
-  double h[kDiagOutSlots];
-  int st2[2] = {0, 0};
-  CK(cudaMemcpyAsync(h, c->diag_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(st2, c->status_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  if (from_shadows) {   // the reference parts of the ion numbers and of the explicit ion terms
-    h[2] += c->refN_p;
-    h[3] += c->refN_m;
-    h[10] += c->refH_p;
-    h[11] += c->refH_m;
+  CK(cudaMemcpyAsync(R->h, c->diag_out, sizeof(R->h), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(R->st, c->status_d, sizeof(R->st), cudaMemcpyDeviceToHost, c->stream));
+  if (c->slip_on) {
+    const int P = c->g.nx * c->g.nz;
+    cudaError_t e2 = c->precision == PNP_FP64
+                         ? launch_mean_profile<double>((const double*)c->wall_u, 2, P, c->diag_out + kDiagOutSlots,
+                                                       c->stream)
+                         : launch_mean_profile<float>((const float*)c->wall_u, 2, P, c->diag_out + kDiagOutSlots,
+                                                      c->stream);
+    if (e2 != cudaSuccess) return PNP_ERR_CUDA;
+    CK(cudaMemcpyAsync(R->wall_mean, c->diag_out + kDiagOutSlots, sizeof(R->wall_mean), cudaMemcpyDeviceToHost,
+                       c->stream));
   }
-  const int st = st2[1] ? st2[1] : st2[0];
+  R->refN_p = c->refN_p;
+  R->refN_m = c->refN_m;
+  R->refH_p = c->refH_p;
+  R->refH_m = c->refH_m;
+  R->time = c->time;
+  R->last_dt = c->last_dt;
+  R->nstep = c->nstep;
+  R->from_shadows = from_shadows ? 1 : 0;
+  R->slip_on = c->slip_on ? 1 : 0;
+  return PNP_OK;
+}
+
+int pnp_diagnostics_read(const pnp_ctx* c, const void* raw_host, pnp_diag* out) {
+  if (!c || !raw_host || !out) return PNP_ERR_ARG;
+  const DiagRaw* R = static_cast<const DiagRaw*>(raw_host);
+  double h[kDiagOutSlots];
+  std::memcpy(h, R->h, sizeof(h));
+  if (R->from_shadows) {   // the reference parts of the ion numbers and of the explicit ion terms
+    h[2] += R->refN_p;
+    h[3] += R->refN_m;
+    h[10] += R->refH_p;
+    h[11] += R->refH_m;
+  }
+  const int st = R->st[1] ? R->st[1] : R->st[0];
   const double P = (double)c->g.nx * c->g.nz;
   const double ub = h[0] / P, ut = h[1] / P;
   const double Uw = c->ph.Uw;
-  double wb = -Uw, wt = Uw;   // plane-mean wall velocities
-  if (c->slip_on) {
-    double m2[2];
-    cudaError_t e2 = c->precision == PNP_FP64
-                         ? launch_mean_profile<double>((const double*)c->wall_u, 2, (int)P, c->stage, c->stream)
-                         : launch_mean_profile<float>((const float*)c->wall_u, 2, (int)P, c->stage, c->stream);
-    if (e2 != cudaSuccess) return PNP_ERR_CUDA;
-    CK(cudaMemcpyAsync(m2, c->stage, sizeof(m2), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    wb = m2[0];
-    wt = m2[1];
-  }
+  const double wb = R->slip_on ? R->wall_mean[0] : -Uw, wt = R->slip_on ? R->wall_mean[1] : Uw;
   std::memset(out, 0, sizeof(*out));
   out->tau_bot = c->ph.nu * (ub - wb) / c->h[0];
   out->tau_top = c->ph.nu * (wt - ut) / c->h[c->g.nyc];
@@ -1592,18 +1630,27 @@ int pnp_diagnostics(pnp_ctx* c, pnp_diag* out) {
   out->flux_plus = -h[10] * c->g.dx * c->g.dz;
   out->flux_minus = -h[11] * c->g.dx * c->g.dz;
   out->wall_flux = std::fabs(out->flux_plus) + std::fabs(out->flux_minus);
-  out->cfl = c->last_dt * h[8];
+  out->cfl = R->last_dt * h[8];
   out->max_dphi = h[9];
   out->dt_cfl = h[8] > 0 ? 1.0 / h[8] : INFINITY;
   out->dt_migration = h[12] > 0 ? 1.0 / (c->ph.D * h[12]) : INFINITY;
   out->dt_dielectric = h[13] > 0 ? 1.0 / (c->ph.D * c->ph.q * h[13]) : INFINITY;
   out->max_div = h[4];
   out->ke = 0.5 * h[5] * c->g.dx * c->g.dz;
-  out->time = c->time;
-  out->nstep = c->nstep;
+  out->time = R->time;
+  out->nstep = R->nstep;
   out->status = st;
   out->precision = c->precision;
   return st;
+}
+
+int pnp_diagnostics(pnp_ctx* c, pnp_diag* out) {
+  if (!c || !out) return PNP_ERR_ARG;
+  DiagRaw raw{};
+  int r = pnp_diagnostics_post(c, &raw);
+  if (r) return r;
+  CK(cudaStreamSynchronize(c->stream));
+  return pnp_diagnostics_read(c, &raw, out);
 }
 
 int pnp_mean_profile(pnp_ctx* c, int field, double* out) {

@@ -105,12 +105,30 @@ class Solver:
     def synchronize(self):
         self.stream.synchronize()
 
+    _STATUS_CODES = (B.PNP_OK, B.PNP_ERR_NONFINITE, B.PNP_ERR_NEGATIVE_C, B.PNP_ERR_TIMEOUT, B.PNP_ERR_CFL,
+                     B.PNP_ERR_DPHI)
+
     def diagnostics(self):
         d = B.pnp_diag()
         code = B.pnp_diagnostics(self.ctx, C.byref(d))
-        if code not in (B.PNP_OK, B.PNP_ERR_NONFINITE, B.PNP_ERR_NEGATIVE_C, B.PNP_ERR_TIMEOUT, B.PNP_ERR_CFL,
-                        B.PNP_ERR_DPHI):
+        if code not in self._STATUS_CODES:
             B.check(code, "pnp_diagnostics")
+        return d.as_dict()
+
+    def diag_buffer(self):
+        """A pinned host record for diagnostics_post / diagnostics_read."""
+        return self.torch.empty(B.PNP_DIAG_RAW_BYTES, dtype=self.torch.uint8).pin_memory()
+
+    def diagnostics_post(self, raw):
+        """Queue the diagnostics of the current state into raw (diag_buffer()); returns at once."""
+        B.check(B.pnp_diagnostics_post(self.ctx, C.c_void_p(raw.data_ptr())), "pnp_diagnostics_post")
+
+    def diagnostics_read(self, raw):
+        """The diagnostics of a completed post (after an event or a synchronisation)."""
+        d = B.pnp_diag()
+        code = B.pnp_diagnostics_read(self.ctx, C.c_void_p(raw.data_ptr()), C.byref(d))
+        if code not in self._STATUS_CODES:
+            B.check(code, "pnp_diagnostics_read")
         return d.as_dict()
 
     def set_wall_potential(self, bottom=None, top=None):

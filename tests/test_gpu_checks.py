@@ -119,3 +119,45 @@ def test_wall_flux_of_the_explicit_ion_terms_vanishes(precision):
     assert d["status"] == 0
     assert d["wall_flux"] <= tol * (scale_p + scale_m), d
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_posted_diagnostics_equal_the_synchronous_ones(precision):
+    """pnp_diagnostics_post / _read: records posted after consecutive steps and
+    read afterwards equal pnp_diagnostics taken at the same moments, in both
+    precisions, with wall slip on (the plane-mean wall velocities ride along)."""
+    import torch
+
+    g = o.Grid(16, 25, 8, 2 * math.pi, math.pi, stretch=1.8)
+    prm = o.Params(Re=200.0, lam=0.1, Sc=1.0, V=2.0, beta=0.5)
+    s = _solver(g, prm, precision)
+    s.init_state(1, 11, 0.05)
+    s.step(2, 0.01)
+    sync = s.diagnostics()
+    raw = s.diag_buffer()
+    s.diagnostics_post(raw)
+    s.synchronize()
+    assert s.diagnostics_read(raw) == sync
+    # two posts in flight, one step apart, then read
+    raws = [s.diag_buffer(), s.diag_buffer()]
+    ref = []
+    for k in range(2):
+        s.step(1, 0.01)
+        s.diagnostics_post(raws[k])
+        ref.append(s.diagnostics())
+    for k in range(2):
+        assert s.diagnostics_read(raws[k]) == ref[k]
+    assert ref[1]["nstep"] == ref[0]["nstep"] + 1
+    # slip walls: the plane-mean wall velocities enter the wall shear
+    from paper_1701_02005_gb300 import wallmodel as wm
+
+    X = wm.features(s, 4)
+    Y = torch.zeros((X.shape[0], 5), dtype=torch.float32, device=X.device)
+    Y[:, 0] = 0.5
+    wm.set_slip(s, X, Y, 4)
+    s.step(1, 0.01)
+    d = s.diagnostics()
+    s.diagnostics_post(raw)
+    s.synchronize()
+    assert s.diagnostics_read(raw) == d
+    s.close()
