@@ -253,7 +253,27 @@ def run_large(args, B, Solver, torch):
 # coarse run coupled to the previous network, dataset aggregation); a later,
 # unseen window judges c_f against the fine run, and times fine and coarse.
 WM = dict(V=5.0, rx=2, ry=4, window=1000, every=2, spinup=8000, layer_steps=1000, passes=3, iters=3000,
-          batch=65536, chunk=20, mode=2, relax=1.0, potential_gain=0.3, flux_gain=0.3, seed=1705, amp=0.3)
+          batch=65536, chunk=20, mode=2, relax=1.0, potential_gain=0.3, flux_gain=0.3, seed=1705, amp=0.05)
+
+
+def vortices_and_streaks(yf, nz, Lz, A=0.15, Bs=0.4, m=1):
+    """Streamwise vortices (a y-z streamfunction psi on the y-face x z-face nodes,
+    zero on the walls) and the streaks they lift up, the structures that carry
+    plane Couette flow into turbulence: v = d_z psi on the y-faces and w = -d_y psi
+    on the z-faces, differenced from psi so that the discrete divergence is zero
+    exactly; u' = Bs (1 - y^2) cos(2 pi m z / Lz).  Arrays over [y][z] (uniform in x)."""
+    import numpy as np
+
+    dy = np.diff(yf)
+    yc = 0.5 * (yf[1:] + yf[:-1])
+    dz = Lz / nz
+    zf = np.arange(nz) * dz
+    zc = zf + 0.5 * dz
+    psi = A * (1.0 - yf[:, None] ** 2) ** 2 * np.sin(2 * np.pi * m * zf[None, :] / Lz)
+    v = (np.roll(psi, -1, axis=1) - psi) / dz
+    w = -(psi[1:] - psi[:-1]) / dy[:, None]
+    u = Bs * (1.0 - yc[:, None] ** 2) * np.cos(2 * np.pi * m * zc[None, :] / Lz)
+    return u, v, w
 
 
 def run_wallmodel(args, B, Solver, torch):
@@ -275,6 +295,9 @@ def run_wallmodel(args, B, Solver, torch):
     dt0 = stable_dt(nx, ny, WL["Re"], WL["lam"], 0.0, st)[0]
     fine.set_params(WL["Re"], WL["lam"], WL["Sc"], 0.0, WL["beta"])
     fine.init_state(B.PNP_IC_PB, c["seed"], c["amp"])
+    du, dv, dw = vortices_and_streaks(yf, nz, WL["Lz"])
+    for name, d in (("u", du), ("v", dv), ("w", dw)):
+        fine.set(name, fine.get(name) + d[:, :, None])
     ncx, ncy, ncz = nx // c["rx"], (ny - 1) // c["ry"] + 1, nz // c["rx"]
     yfc = yf[::c["ry"]].copy()
 
@@ -287,14 +310,17 @@ def run_wallmodel(args, B, Solver, torch):
         wm.set_coupling(s, c["mode"], c["relax"], c["potential_gain"], c["flux_gain"])
 
     t0 = time.perf_counter()
-    fine.step(c["spinup"], dt0)
-    cf_spun = fine.diagnostics()["cf"]
+    cf_spin = []
+    for n in range(10):
+        fine.step(c["spinup"] // 10, dt0)
+        cf_spin.append(fine.diagnostics()["cf"])
+    cf_spun = cf_spin[-1]
     fine.set_params(WL["Re"], WL["lam"], WL["Sc"], c["V"], WL["beta"])
     fine.step(c["layer_steps"], dt)
     fine.synchronize()
     spin_s = time.perf_counter() - t0
     rows = 2 * ncz * ncx
-    net, Xs, Ts, losses = None, [], [], []
+    net, Xs, Ts, losses, good = None, [], [], [], None
     sc = coarse()
     for p in range(c["passes"]):
         wm.restrict(fine, sc)
@@ -314,6 +340,8 @@ def run_wallmodel(args, B, Solver, torch):
         wm.clear_edl(sc)
         X, T = torch.cat(Xs), torch.cat(Ts)
         ok = torch.isfinite(X).all(1) & torch.isfinite(T).all(1)   # rows of a run gone non-finite stay out
+        if net is not None:   # and rows far outside the first pass's spread
+            ok &= (((X.double() - xs) / xsd).abs() < 20).all(1) & (((T.double() - ts) / tsd).abs() < 20).all(1)
         X, T = X[ok].contiguous(), T[ok].contiguous()
         if net is None:
             xs, ts = X.mean(0).double(), T.mean(0).double()
@@ -334,6 +362,11 @@ def run_wallmodel(args, B, Solver, torch):
         l1 = net.train_step(Xp[:c["batch"]], Tp[:c["batch"]], lr1, want_loss=True)
         losses.append([l0, l1])
         del Xp, Tp, perm
+        if not math.isfinite(l1):   # a pass that failed to train: back to the last good network
+            if good is not None:
+                net.set_params(good)
+            break
+        good = net.params()
     train_s = time.perf_counter() - t0
     # the judged window: fine truth, coarse alone, coarse coupled to the network
     sp, sm = coarse(), coarse()
@@ -351,6 +384,12 @@ def run_wallmodel(args, B, Solver, torch):
     f = np.array(cf["fine"])
     err = lambda a: float(np.mean(np.abs(np.array(a) - f) / f))
     merr = lambda a: float(abs(np.mean(a) - np.mean(f)) / np.mean(f))
+    # <u>(y) at the end of the window: the fine profile averaged onto the coarse cells
+    dyf = np.diff(yf)
+    uf = fine.mean_profile("u")
+    ufc = (uf * dyf).reshape(-1, c["ry"]).sum(1) / dyf.reshape(-1, c["ry"]).sum(1)
+    uerr = lambda s: float(np.max(np.abs(s.mean_profile("u") - ufc)))
+    u_err = {"plain": uerr(sp), "coupled": uerr(sm)}
 
     # time per step: fine, coarse alone, coarse with the model
     def timed(fn, s, n=100):
@@ -372,12 +411,14 @@ def run_wallmodel(args, B, Solver, torch):
                        f"{c['passes']} training windows + 1 judged window of {c['window']} steps",
            "coupling": {k: c[k] for k in ("mode", "relax", "potential_gain", "flux_gain")},
            "spinup": {"steps_at_V0": c["spinup"], "dt_V0": dt0, "cf_after": cf_spun, "cf_laminar": 2.0 / WL["Re"],
+                      "cf_series": [round(x, 7) for x in cf_spin], "turbulent": bool(cf_spun > 2.0 * 2.0 / WL["Re"]),
                       "layer_steps_at_V": c["layer_steps"], "seconds": spin_s},
            "training": {"rows": int(X.shape[0]), "snapshots": len(Xs), "iters_per_pass": c["iters"],
                         "batch": c["batch"], "loss_first_last": losses, "seconds": train_s - spin_s},
            "cf_err_plain": err(cf["plain"]), "cf_err_coupled": err(cf["coupled"]),
            "mean_cf": {k: float(np.mean(v)) for k, v in cf.items()},
            "mean_cf_err_plain": merr(cf["plain"]), "mean_cf_err_coupled": merr(cf["coupled"]),
+           "mean_u_max_err": u_err,
            "cf_series": {k: [round(x, 6) for x in v[::5]] for k, v in cf.items()},
            "ms_per_step": {"fine": ms_f, "coarse": ms_p, "coarse_with_model": ms_c},
            "speedup_coarse_with_model_over_fine": ms_f / ms_c, "mlp_status": net.status(),
@@ -869,33 +910,51 @@ def run_ours(args):
             pin.numpy()[...] = a
             host[nm] = pin
         Ke = max(1, min(args.e2e_steps, K))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for nm in names:
-            B.check(B.pnp_set_state(s.ctx, FIELD_NAMES[nm], host[nm].data_ptr(), 0), "pnp_set_state")
-        # the diagnostics of every step are read one step behind (pinned records, an
-        # event per post), so the host never stalls the stream
-        raws = [s.diag_buffer(), s.diag_buffer()]
-        evs = [torch.cuda.Event(), torch.cuda.Event()]
-        for k in range(Ke):
-            s.step(1, dt)
-            s.diagnostics_post(raws[k % 2])
-            evs[k % 2].record(s.stream)
-            if k > 0:
-                evs[(k - 1) % 2].synchronize()
-                s.diagnostics_read(raws[(k - 1) % 2])
-        evs[(Ke - 1) % 2].synchronize()
-        last = s.diagnostics_read(raws[(Ke - 1) % 2])
-        out = torch.empty(host["u"].shape, dtype=torch.float64).pin_memory()
-        B.check(B.pnp_get_state(s.ctx, B.PNP_U, out.data_ptr(), 0), "pnp_get_state")
-        te = time.perf_counter() - t0
         state_bytes = sum(h.numel() * 8 for h in host.values())
-        e2e = {"value": n_cells * Ke / te, "unit": UNIT, "h2d_bytes_per_step": state_bytes / Ke,
-               "d2h_bytes_per_step": 128 + out.numel() * 8 / Ke, "steps": Ke,
-               "last_step_status": last["status"],
+
+        def e2e_run(pipelined):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for nm in names:
+                B.check(B.pnp_set_state(s.ctx, FIELD_NAMES[nm], host[nm].data_ptr(), 0), "pnp_set_state")
+            s.synchronize()
+            t1 = time.perf_counter()
+            if pipelined:
+                # the diagnostics of every step are read one step behind (pinned records,
+                # an event per post), so the host never stalls the stream
+                raws = [s.diag_buffer(), s.diag_buffer()]
+                evs = [torch.cuda.Event(), torch.cuda.Event()]
+                for k in range(Ke):
+                    s.step(1, dt)
+                    s.diagnostics_post(raws[k % 2])
+                    evs[k % 2].record(s.stream)
+                    if k > 0:
+                        evs[(k - 1) % 2].synchronize()
+                        s.diagnostics_read(raws[(k - 1) % 2])
+                evs[(Ke - 1) % 2].synchronize()
+                last = s.diagnostics_read(raws[(Ke - 1) % 2])
+            else:
+                for k in range(Ke):
+                    s.step(1, dt)
+                    last = s.diagnostics()
+            t2 = time.perf_counter()
+            out = torch.empty(host["u"].shape, dtype=torch.float64).pin_memory()
+            B.check(B.pnp_get_state(s.ctx, B.PNP_U, out.data_ptr(), 0), "pnp_get_state")
+            t3 = time.perf_counter()
+            return {"value": n_cells * Ke / (t3 - t0), "set_state_s": t1 - t0, "steps_s": t2 - t1,
+                    "ms_per_step_in_loop": 1e3 * (t2 - t1) / Ke, "get_state_s": t3 - t2,
+                    "d2h": out.numel() * 8, "status": last["status"]}
+
+        r_sync = e2e_run(False)
+        r = e2e_run(True)
+        e2e = {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": state_bytes / Ke,
+               "d2h_bytes_per_step": 128 + r["d2h"] / Ke, "steps": Ke, "last_step_status": r["status"],
+               "phases": {k: r[k] for k in ("set_state_s", "steps_s", "ms_per_step_in_loop", "get_state_s")},
+               "synchronous_diagnostics": {k: r_sync[k] for k in ("value", "set_state_s", "ms_per_step_in_loop")},
                "note": "set_state of all 12 fields from pinned host, then per step pnp_step + "
                        "pnp_diagnostics_post (D2H of the step's diagnostics into a pinned record, read one step "
-                       "behind), then get_state(u) to pinned host"}
+                       "behind), then get_state(u) to pinned host; the same with pnp_diagnostics (synchronising "
+                       "every step) beside it"}
 
     ensemble = None
     if not args.no_ensemble:
