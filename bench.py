@@ -310,10 +310,13 @@ def run_wallmodel(args, B, Solver, torch):
         wm.set_coupling(s, c["mode"], c["relax"], c["potential_gain"], c["flux_gain"])
 
     t0 = time.perf_counter()
-    cf_spin = []
-    for n in range(10):
-        fine.step(c["spinup"] // 10, dt0)
-        cf_spin.append(fine.diagnostics()["cf"])
+    cf_spin, t_spin = [], 0.0
+    log = lambda *a: print("wallmodel:", *a, file=sys.stderr, flush=True)
+    for n in range(10):   # dt from the state's limits (CFL 0.5), at most the advective dt
+        t_spin += float(np.sum(fine.step_adaptive(c["spinup"] // 10, dt0, 0.5, 20)))
+        d = fine.diagnostics()
+        cf_spin.append(d["cf"])
+        log(f"spin-up {n}: t {t_spin:.2f} cf {d['cf']:.6g} status {d['status']}")
     cf_spun = cf_spin[-1]
     fine.set_params(WL["Re"], WL["lam"], WL["Sc"], c["V"], WL["beta"])
     fine.step(c["layer_steps"], dt)
@@ -343,6 +346,10 @@ def run_wallmodel(args, B, Solver, torch):
         if net is not None:   # and rows far outside the first pass's spread
             ok &= (((X.double() - xs) / xsd).abs() < 20).all(1) & (((T.double() - ts) / tsd).abs() < 20).all(1)
         X, T = X[ok].contiguous(), T[ok].contiguous()
+        log(f"pass {p}: {len(Xs)} snapshots, {int(ok.sum())} of {ok.numel()} rows kept, coarse cf "
+            f"{sc.diagnostics()['cf']:.6g}")
+        if X.shape[0] == 0:
+            break
         if net is None:
             xs, ts = X.mean(0).double(), T.mean(0).double()
             xsd = torch.maximum(X.double().std(0), 1e-2 * torch.clamp(xs.abs(), min=1e-2))
@@ -368,6 +375,10 @@ def run_wallmodel(args, B, Solver, torch):
             break
         good = net.params()
     train_s = time.perf_counter() - t0
+    if net is None:
+        for s_ in (fine, sc):
+            s_.close()
+        return {"error": "no finite training rows", "spinup_cf": cf_spin, "spinup_time_units": t_spin}
     # the judged window: fine truth, coarse alone, coarse coupled to the network
     sp, sm = coarse(), coarse()
     wm.restrict(fine, sp)
@@ -410,7 +421,8 @@ def run_wallmodel(args, B, Solver, torch):
                        f"lambda_D/h {WL['lam']}, V {c['V']:g}, dt {dt:.4g}, {c['spinup']} spin-up steps at V 0, "
                        f"{c['passes']} training windows + 1 judged window of {c['window']} steps",
            "coupling": {k: c[k] for k in ("mode", "relax", "potential_gain", "flux_gain")},
-           "spinup": {"steps_at_V0": c["spinup"], "dt_V0": dt0, "cf_after": cf_spun, "cf_laminar": 2.0 / WL["Re"],
+           "spinup": {"steps_at_V0": c["spinup"], "dt_max_V0": dt0, "time_units": t_spin, "cf_after": cf_spun,
+                      "cf_laminar": 2.0 / WL["Re"],
                       "cf_series": [round(x, 7) for x in cf_spin], "turbulent": bool(cf_spun > 2.0 * 2.0 / WL["Re"]),
                       "layer_steps_at_V": c["layer_steps"], "seconds": spin_s},
            "training": {"rows": int(X.shape[0]), "snapshots": len(Xs), "iters_per_pass": c["iters"],

@@ -63,8 +63,7 @@ __global__ void k_restrict_v(const T* __restrict__ f, WallMap wm, double* __rest
 
 // Feature rows: [wall][k][i] x [field][d], d = 0..ncells-1 cells away from the wall.
 template <typename TV>
-__global__ void k_wall_features(const TV* __restrict__ u, const TV* __restrict__ w, const double* __restrict__ cp,
-                                const double* __restrict__ cm, const double* __restrict__ Phi,
+__global__ void k_wall_features(const TV* __restrict__ u, const TV* __restrict__ w, IonView ions,
                                 const double* __restrict__ yc, Geo g, double V, double Uw, int ncells,
                                 float* __restrict__ X) {
   const size_t P = (size_t)g.nz * g.nx;
@@ -76,12 +75,13 @@ __global__ void k_wall_features(const TV* __restrict__ u, const TV* __restrict__
   for (int d = 0; d < ncells; ++d) {
     const int j = wall == 0 ? d : g.nyc - 1 - d;
     const size_t o = (size_t)j * P + col;
-    const double phi = Phi[o] - V * yc[j];
+    const double phi = ions.phv(j, o) - V * yc[j];
     const double ur = wall == 0 ? (double)u[o] + Uw : Uw - (double)u[o];
+    const double cpo = ions.cpv(j, o), cmo = ions.cmv(j, o);
     row[0 * ncells + d] = (float)ur;
     row[1 * ncells + d] = (float)(double)w[o];
-    row[2 * ncells + d] = (float)(wall == 0 ? cp[o] : cm[o]);
-    row[3 * ncells + d] = (float)(wall == 0 ? cm[o] : cp[o]);
+    row[2 * ncells + d] = (float)(wall == 0 ? cpo : cmo);
+    row[3 * ncells + d] = (float)(wall == 0 ? cmo : cpo);
     row[4 * ncells + d] = (float)(wall == 0 ? phi : -phi);
   }
 }
@@ -94,8 +94,7 @@ __global__ void k_wall_features(const TV* __restrict__ u, const TV* __restrict__
 //        face (wall frame: positive away from the wall).
 template <typename TV>
 __global__ void k_wall_labels(const TV* __restrict__ u, const TV* __restrict__ v, const TV* __restrict__ w,
-                              const double* __restrict__ cp, const double* __restrict__ cm,
-                              const double* __restrict__ Phi, const double* __restrict__ ycf,
+                              IonView ions, const double* __restrict__ ycf,
                               const double* __restrict__ dyf, const double* __restrict__ hf, WallMap wm, double h0c,
                               double V, double Uw, double D_ion, float* __restrict__ T) {
   const size_t Pc = (size_t)wm.nz_c * wm.nx_c;
@@ -122,7 +121,7 @@ __global__ void k_wall_labels(const TV* __restrict__ u, const TV* __restrict__ v
         const double wt = dyf[jf];
         ua += wt * (wall == 0 ? (double)u[o] + Uw : Uw - (double)u[o]);
         wa += wt * (double)w[o];
-        const double phi = Phi[o] - V * ycf[jf];
+        const double phi = ions.phv(jf, o) - V * ycf[jf];
         pa += wt * (wall == 0 ? phi : -phi);
         vol += wt;
       }
@@ -134,10 +133,12 @@ __global__ void k_wall_labels(const TV* __restrict__ u, const TV* __restrict__ v
       // total flux F = v c_f - D (dc/dy + s c_f dPhi/dy) on fine face jface (lab frame, +y)
       const size_t oa = (size_t)(jface - 1) * Pf + col, ob = (size_t)jface * Pf + col;
       const double vf = (double)v[(size_t)jface * Pf + col];
-      const double dP = (Phi[ob] - Phi[oa]) * ihf;
-      const double cpf = 0.5 * (cp[oa] + cp[ob]), cmf = 0.5 * (cm[oa] + cm[ob]);
-      const double Fp = vf * cpf - D_ion * ((cp[ob] - cp[oa]) * ihf + cpf * dP);
-      const double Fm = vf * cmf - D_ion * ((cm[ob] - cm[oa]) * ihf - cmf * dP);
+      const double cpa = ions.cpv(jface - 1, oa), cpb = ions.cpv(jface, ob);
+      const double cma = ions.cmv(jface - 1, oa), cmb = ions.cmv(jface, ob);
+      const double dP = (ions.phv(jface, ob) - ions.phv(jface - 1, oa)) * ihf;
+      const double cpf = 0.5 * (cpa + cpb), cmf = 0.5 * (cma + cmb);
+      const double Fp = vf * cpf - D_ion * ((cpb - cpa) * ihf + cpf * dP);
+      const double Fm = vf * cmf - D_ion * ((cmb - cma) * ihf - cmf * dP);
       // wall frame: away from the wall is +y at the bottom, -y at the top; top swaps the ions
       if (wall == 0) { fpl += Fp; fmi += Fm; }
       else { fpl += -Fm; fmi += -Fp; }
@@ -279,12 +280,9 @@ __global__ void k_edl_offsets(const float* __restrict__ X, int ncells, const flo
 // shadows of a mixed-precision context (S != null) the corrected cells'
 // shadows are rewritten from the FP64 values.
 template <typename TV>
-__global__ void k_wall_flux_fix(double* __restrict__ cp, double* __restrict__ cm, const double* __restrict__ Phi,
-                                const TV* __restrict__ v, const double* __restrict__ idy,
+__global__ void k_wall_flux_fix(IonView ions, const TV* __restrict__ v, const double* __restrict__ idy,
                                 const double* __restrict__ ih, Geo g, double Dion, const float* __restrict__ Y,
-                                double gain, double dt, float* __restrict__ cpS, float* __restrict__ cpL,
-                                float* __restrict__ cmS, float* __restrict__ cmL, const double* __restrict__ crefp,
-                                const double* __restrict__ crefm) {
+                                double gain, double dt) {
   const size_t P = (size_t)g.nz * g.nx;
   const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= 2 * P) return;
@@ -294,10 +292,11 @@ __global__ void k_wall_flux_fix(double* __restrict__ cp, double* __restrict__ cm
   const size_t ol = (size_t)jl * P + col, ou = (size_t)ju * P + col;
   const double ihf = ih[jf];
   const double vf = (double)v[(size_t)jf * P + col];
-  const double dP = (Phi[ou] - Phi[ol]) * ihf;
-  const double cpf = 0.5 * (cp[ol] + cp[ou]), cmf = 0.5 * (cm[ol] + cm[ou]);
-  const double Fp = vf * cpf - Dion * ((cp[ou] - cp[ol]) * ihf + cpf * dP);
-  const double Fm = vf * cmf - Dion * ((cm[ou] - cm[ol]) * ihf - cmf * dP);
+  const double dP = (ions.phv(ju, ou) - ions.phv(jl, ol)) * ihf;
+  double cp[2] = {ions.cpv(jl, ol), ions.cpv(ju, ou)}, cm[2] = {ions.cmv(jl, ol), ions.cmv(ju, ou)};
+  const double cpf = 0.5 * (cp[0] + cp[1]), cmf = 0.5 * (cm[0] + cm[1]);
+  const double Fp = vf * cpf - Dion * ((cp[1] - cp[0]) * ihf + cpf * dP);
+  const double Fm = vf * cmf - Dion * ((cm[1] - cm[0]) * ihf - cmf * dP);
   const float* y = Y + r * 5;
   // wall frame -> lab frame (+y): the top wall's counter-ion column is c-, fluxes flip sign
   double dFp, dFm;
@@ -308,23 +307,28 @@ __global__ void k_wall_flux_fix(double* __restrict__ cp, double* __restrict__ cm
     dFm = -gain * ((double)y[3] + Fm);
     dFp = -gain * ((double)y[4] + Fp);
   }
-  auto apply = [&](double* c, double dF, float* S, float* L, const double* cref) {
+  auto apply = [&](double (&c)[2], double dF, double* c64, float* S, float* L, const double* cref) {
     if (!isfinite(dF)) return;
     // the cell that loses ions gives at most half of them
-    const double cap = dF > 0.0 ? 0.5 * fmax(c[ol], 0.0) / (idy[jl] * dt) : 0.5 * fmax(c[ou], 0.0) / (idy[ju] * dt);
+    const double cap = dF > 0.0 ? 0.5 * fmax(c[0], 0.0) / (idy[jl] * dt) : 0.5 * fmax(c[1], 0.0) / (idy[ju] * dt);
     dF = fmin(fmax(dF, -cap), cap);
-    c[ol] -= dF * dt * idy[jl];
-    c[ou] += dF * dt * idy[ju];
-    if (S) {
-      const double a = c[ol] - cref[jl], b = c[ou] - cref[ju];
+    c[0] -= dF * dt * idy[jl];
+    c[1] += dF * dt * idy[ju];
+    if (c64) {
+      c64[ol] = c[0];
+      c64[ou] = c[1];
+    } else {
+      const double a = c[0] - cref[jl], b = c[1] - cref[ju];
       S[ol] = (float)a;
       L[ol] = (float)(a - (double)S[ol]);
       S[ou] = (float)b;
       L[ou] = (float)(b - (double)S[ou]);
     }
   };
-  apply(cp, dFp, cpS, cpL, crefp);
-  apply(cm, dFm, cmS, cmL, crefm);
+  apply(cp, dFp, const_cast<double*>(ions.cp), const_cast<float*>(ions.cpS), const_cast<float*>(ions.cpL),
+        ions.crefp);
+  apply(cm, dFm, const_cast<double*>(ions.cm), const_cast<float*>(ions.cmS), const_cast<float*>(ions.cmL),
+        ions.crefm);
 }
 
 cudaError_t launch_edl_offsets(const float* X, int ncells, const float* Y, size_t P, double gain, double lim, double* B,
@@ -334,12 +338,10 @@ cudaError_t launch_edl_offsets(const float* X, int ncells, const float* Y, size_
 }
 
 template <typename TV>
-cudaError_t launch_wall_flux_fix(double* cp, double* cm, const double* Phi, const TV* v, const double* idy,
-                                 const double* ih, const Geo& g, double Dion, const float* Y, double gain, double dt,
-                                 const FluxFixShadows& sh, cudaStream_t s) {
+cudaError_t launch_wall_flux_fix(const IonView& ions, const TV* v, const double* idy, const double* ih, const Geo& g,
+                                 double Dion, const float* Y, double gain, double dt, cudaStream_t s) {
   const size_t n = 2 * (size_t)g.nz * g.nx;
-  k_wall_flux_fix<TV><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(cp, cm, Phi, v, idy, ih, g, Dion, Y, gain, dt, sh.cpS,
-                                                                 sh.cpL, sh.cmS, sh.cmL, sh.crefp, sh.crefm);
+  k_wall_flux_fix<TV><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(ions, v, idy, ih, g, Dion, Y, gain, dt);
   return cudaGetLastError();
 }
 
@@ -358,22 +360,20 @@ cudaError_t launch_restrict(const T* f, const double* dyf, const WallMap& wm, do
 }
 
 template <typename TV>
-cudaError_t launch_wall_features(const TV* u, const TV* w, const double* cp, const double* cm, const double* Phi,
-                                 const double* yc, const Geo& g, double V, double Uw, int ncells, float* X,
-                                 cudaStream_t s) {
+cudaError_t launch_wall_features(const TV* u, const TV* w, const IonView& ions, const double* yc, const Geo& g,
+                                 double V, double Uw, int ncells, float* X, cudaStream_t s) {
   const size_t n = 2 * (size_t)g.nz * g.nx;
-  k_wall_features<TV><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(u, w, cp, cm, Phi, yc, g, V, Uw, ncells, X);
+  k_wall_features<TV><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(u, w, ions, yc, g, V, Uw, ncells, X);
   return cudaGetLastError();
 }
 
 template <typename TV>
-cudaError_t launch_wall_labels(const TV* u, const TV* v, const TV* w, const double* cp, const double* cm,
-                               const double* Phi, const double* ycf, const double* dyf, const double* hf,
-                               const WallMap& wm, double h0c, double V, double Uw, double D_ion, float* T,
-                               cudaStream_t s) {
+cudaError_t launch_wall_labels(const TV* u, const TV* v, const TV* w, const IonView& ions, const double* ycf,
+                               const double* dyf, const double* hf, const WallMap& wm, double h0c, double V,
+                               double Uw, double D_ion, float* T, cudaStream_t s) {
   const size_t n = 2 * (size_t)wm.nz_c * wm.nx_c;
-  k_wall_labels<TV><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(u, v, w, cp, cm, Phi, ycf, dyf, hf, wm, h0c, V, Uw,
-                                                               D_ion, T);
+  k_wall_labels<TV><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(u, v, w, ions, ycf, dyf, hf, wm, h0c, V, Uw, D_ion,
+                                                               T);
   return cudaGetLastError();
 }
 
@@ -386,25 +386,20 @@ cudaError_t launch_set_slip(const float* X, int ncells, const float* Y, size_t P
 
 template cudaError_t launch_restrict<double>(const double*, const double*, const WallMap&, double*, bool, cudaStream_t);
 template cudaError_t launch_restrict<float>(const float*, const double*, const WallMap&, double*, bool, cudaStream_t);
-template cudaError_t launch_wall_features<double>(const double*, const double*, const double*, const double*,
-                                                  const double*, const double*, const Geo&, double, double, int, float*,
-                                                  cudaStream_t);
-template cudaError_t launch_wall_features<float>(const float*, const float*, const double*, const double*,
-                                                 const double*, const double*, const Geo&, double, double, int, float*,
-                                                 cudaStream_t);
-template cudaError_t launch_wall_labels<double>(const double*, const double*, const double*, const double*,
-                                                const double*, const double*, const double*, const double*,
-                                                const double*, const WallMap&, double, double, double, double, float*,
-                                                cudaStream_t);
-template cudaError_t launch_wall_labels<float>(const float*, const float*, const float*, const double*, const double*,
-                                               const double*, const double*, const double*, const double*,
-                                               const WallMap&, double, double, double, double, float*, cudaStream_t);
-template cudaError_t launch_wall_flux_fix<double>(double*, double*, const double*, const double*, const double*,
-                                                  const double*, const Geo&, double, const float*, double, double,
-                                                  const FluxFixShadows&, cudaStream_t);
-template cudaError_t launch_wall_flux_fix<float>(double*, double*, const double*, const float*, const double*,
-                                                 const double*, const Geo&, double, const float*, double, double,
-                                                 const FluxFixShadows&, cudaStream_t);
+template cudaError_t launch_wall_features<double>(const double*, const double*, const IonView&, const double*,
+                                                  const Geo&, double, double, int, float*, cudaStream_t);
+template cudaError_t launch_wall_features<float>(const float*, const float*, const IonView&, const double*,
+                                                 const Geo&, double, double, int, float*, cudaStream_t);
+template cudaError_t launch_wall_labels<double>(const double*, const double*, const double*, const IonView&,
+                                                const double*, const double*, const double*, const WallMap&, double,
+                                                double, double, double, float*, cudaStream_t);
+template cudaError_t launch_wall_labels<float>(const float*, const float*, const float*, const IonView&, const double*,
+                                               const double*, const double*, const WallMap&, double, double, double,
+                                               double, float*, cudaStream_t);
+template cudaError_t launch_wall_flux_fix<double>(const IonView&, const double*, const double*, const double*,
+                                                  const Geo&, double, const float*, double, double, cudaStream_t);
+template cudaError_t launch_wall_flux_fix<float>(const IonView&, const float*, const double*, const double*,
+                                                 const Geo&, double, const float*, double, double, cudaStream_t);
 template cudaError_t launch_set_slip<double>(const float*, int, const float*, size_t, double, double, double, double*,
                                              double*, cudaStream_t);
 template cudaError_t launch_set_slip<float>(const float*, int, const float*, size_t, double, double, double, float*,

@@ -991,6 +991,21 @@ int materialize(pnp_ctx* c) {
   return PNP_OK;
 }
 
+// c+, c-, Phi as the wall kernels read them: the shadows of a mixed context
+// whose references are valid (what it steps on), else the FP64 arrays
+// (brought up to date first).
+int ion_view(pnp_ctx* c, IonView* v) {
+  if (c->precision == PNP_MIXED && c->refs_valid) {
+    *v = IonView{nullptr, nullptr, nullptr, c->cpS, c->cpL, c->cmS, c->cmL, c->phiS, c->cref64p_d, c->cref64m_d,
+                 c->Phiref64_d};
+    return PNP_OK;
+  }
+  int r = materialize(c);
+  if (r) return r;
+  *v = IonView{c->cp, c->cm, c->Phi, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  return PNP_OK;
+}
+
 // Mixed precision: reference profiles (plane means of c+, c-, Phi) and every
 // per-plane FP64 constant derived from them; then the FP32 shadows.
 int refresh_refs(pnp_ctx* c, double dt) {
@@ -2379,13 +2394,14 @@ void pnp_mlp_destroy(pnp_mlp* m) { delete m; }
 int pnp_wall_features(pnp_ctx* c, int ncells, float* X) {
   if (!c || !X || ncells < 1 || ncells > 8 || ncells > c->g.nyc) return PNP_ERR_ARG;
   if (!c->have_state) return PNP_ERR_STATE;
-  int r = materialize(c);
+  IonView iv{};
+  int r = ion_view(c, &iv);
   if (r) return r;
   cudaError_t e = c->precision == PNP_FP64
-                      ? launch_wall_features<double>((const double*)c->u, (const double*)c->w, c->cp, c->cm, c->Phi,
-                                                     c->yc_d, c->g, c->ph.V, c->ph.Uw, ncells, X, c->stream)
-                      : launch_wall_features<float>((const float*)c->u, (const float*)c->w, c->cp, c->cm, c->Phi,
-                                                    c->yc_d, c->g, c->ph.V, c->ph.Uw, ncells, X, c->stream);
+                      ? launch_wall_features<double>((const double*)c->u, (const double*)c->w, iv, c->yc_d, c->g,
+                                                     c->ph.V, c->ph.Uw, ncells, X, c->stream)
+                      : launch_wall_features<float>((const float*)c->u, (const float*)c->w, iv, c->yc_d, c->g,
+                                                    c->ph.V, c->ph.Uw, ncells, X, c->stream);
   return e == cudaSuccess ? PNP_OK : PNP_ERR_CUDA;
 }
 
@@ -2432,7 +2448,8 @@ int pnp_wall_labels(pnp_ctx* f, pnp_ctx* c, float* T) {
   int err = 0;
   const WallMap wm = wall_map(f, c, &err);
   if (err) return err;
-  int r = materialize(f);
+  IonView iv{};
+  int r = ion_view(f, &iv);
   if (r) return r;
   double* scr = f->stage + f->nv - 3 * (size_t)f->g.ny;   // ycf, dyf, hf
   std::vector<double> pack(3 * (size_t)f->g.ny, 0.0);
@@ -2441,12 +2458,12 @@ int pnp_wall_labels(pnp_ctx* f, pnp_ctx* c, float* T) {
   CK(cudaMemcpyAsync(scr, pack.data(), sizeof(double) * pack.size(), cudaMemcpyHostToDevice, f->stream));
   const double h0c = c->h[0];
   cudaError_t e = f->precision == PNP_FP64
-                      ? launch_wall_labels<double>((const double*)f->u, (const double*)f->v, (const double*)f->w, f->cp,
-                                                   f->cm, f->Phi, scr, scr + f->g.ny, scr + 2 * f->g.ny, wm, h0c,
-                                                   f->ph.V, f->ph.Uw, f->ph.D, T, f->stream)
-                      : launch_wall_labels<float>((const float*)f->u, (const float*)f->v, (const float*)f->w, f->cp,
-                                                  f->cm, f->Phi, scr, scr + f->g.ny, scr + 2 * f->g.ny, wm, h0c,
-                                                  f->ph.V, f->ph.Uw, f->ph.D, T, f->stream);
+                      ? launch_wall_labels<double>((const double*)f->u, (const double*)f->v, (const double*)f->w, iv,
+                                                   scr, scr + f->g.ny, scr + 2 * f->g.ny, wm, h0c, f->ph.V, f->ph.Uw,
+                                                   f->ph.D, T, f->stream)
+                      : launch_wall_labels<float>((const float*)f->u, (const float*)f->v, (const float*)f->w, iv, scr,
+                                                  scr + f->g.ny, scr + 2 * f->g.ny, wm, h0c, f->ph.V, f->ph.Uw,
+                                                  f->ph.D, T, f->stream);
   if (e != cudaSuccess) return PNP_ERR_CUDA;
   CK(cudaStreamSynchronize(f->stream));
   return PNP_OK;
@@ -2529,29 +2546,32 @@ int edl_potential(pnp_ctx* c, const float* X, int ncells, const float* Y) {
   const double lim = std::max(1.0, std::fabs(c->ph.V));
   CK(launch_edl_offsets(X, ncells, Y, P, c->edl_phi_gain, lim, c->wallB_d, c->wallT_d, c->stream));
   CK(edl_lift(c));
-  // the potential of the present ions under the moved walls
+  // the potential of the present ions under the moved walls: in a mixed context that
+  // steps on its shadows, the step's own potential pipeline (writes phi')
+  if (c->precision == PNP_MIXED && c->refs_valid) {
+    CK(c->policy == PNP_POLICY_FP64_SOLVES ? potential_mixed_fp64(c, c->stream, c->spec, c->dscr)
+                                           : potential_mixed(c, c->stream, c->spec, c->dscr));
+    c->fp64_fresh = false;
+    return PNP_OK;
+  }
   int r = materialize(c);
   if (r) return r;
   CK(c->precision == PNP_FP64 ? potential_solve<double>(c) : potential_solve<float>(c));
-  if (c->precision == PNP_MIXED && c->refs_valid)
-    CK(launch_make_shadows(c->cp, c->cm, c->Phi, c->Hcp, c->Hcm, shadows(c), mixed_refs(c), c->Hrefp_d, c->Hrefm_d,
-                           P, c->nc, c->stream));
   return PNP_OK;
 }
 
 int flux_fix(pnp_ctx* c, const float* Y, double dt) {
   if (!c->have_state) return PNP_ERR_STATE;
-  int r = materialize(c);
+  IonView iv{};
+  int r = ion_view(c, &iv);
   if (r) return r;
-  FluxFixShadows sh{};
-  if (c->precision == PNP_MIXED && c->refs_valid)
-    sh = FluxFixShadows{c->cpS, c->cpL, c->cmS, c->cmL, c->cref64p_d, c->cref64m_d};
   const cudaError_t e =
       c->precision == PNP_FP64
-          ? launch_wall_flux_fix<double>(c->cp, c->cm, c->Phi, (const double*)c->v, c->idy_d, c->ih_d, c->g, c->ph.D, Y,
-                                         c->edl_flux_gain, dt, sh, c->stream)
-          : launch_wall_flux_fix<float>(c->cp, c->cm, c->Phi, (const float*)c->v, c->idy_d, c->ih_d, c->g, c->ph.D, Y,
-                                        c->edl_flux_gain, dt, sh, c->stream);
+          ? launch_wall_flux_fix<double>(iv, (const double*)c->v, c->idy_d, c->ih_d, c->g, c->ph.D, Y,
+                                         c->edl_flux_gain, dt, c->stream)
+          : launch_wall_flux_fix<float>(iv, (const float*)c->v, c->idy_d, c->ih_d, c->g, c->ph.D, Y, c->edl_flux_gain,
+                                        dt, c->stream);
+  if (!iv.cp) c->fp64_fresh = false;   // the shadows were updated, not the FP64 copies
   return e == cudaSuccess ? PNP_OK : PNP_ERR_CUDA;
 }
 }  // namespace

@@ -15,17 +15,31 @@ struct WallMap {
   int rx, ry, rz;
 };
 
+// c+, c- and Phi of a state as the wall kernels read them: the FP64 arrays, or
+// (cp == nullptr) the reference profiles plus the double-float shadows of a
+// mixed-precision context, c = c_ref(j) + (S + L), Phi = Phi_ref(j) + phi'.
+struct IonView {
+  const double *cp, *cm, *Phi;
+  const float *cpS, *cpL, *cmS, *cmL, *phiS;
+  const double *crefp, *crefm, *Phiref;
+  __device__ __forceinline__ double cpv(int j, size_t o) const {
+    return cp ? cp[o] : crefp[j] + ((double)cpS[o] + (double)cpL[o]);
+  }
+  __device__ __forceinline__ double cmv(int j, size_t o) const {
+    return cm ? cm[o] : crefm[j] + ((double)cmS[o] + (double)cmL[o]);
+  }
+  __device__ __forceinline__ double phv(int j, size_t o) const { return Phi ? Phi[o] : Phiref[j] + (double)phiS[o]; }
+};
+
 template <typename T>
 cudaError_t launch_restrict(const T* f, const double* dyf, const WallMap& wm, double* out, bool vfield, cudaStream_t s);
 template <typename TV>
-cudaError_t launch_wall_features(const TV* u, const TV* w, const double* cp, const double* cm, const double* Phi,
-                                 const double* yc, const Geo& g, double V, double Uw, int ncells, float* X,
-                                 cudaStream_t s);
+cudaError_t launch_wall_features(const TV* u, const TV* w, const IonView& ions, const double* yc, const Geo& g,
+                                 double V, double Uw, int ncells, float* X, cudaStream_t s);
 template <typename TV>
-cudaError_t launch_wall_labels(const TV* u, const TV* v, const TV* w, const double* cp, const double* cm,
-                               const double* Phi, const double* ycf, const double* dyf, const double* hf,
-                               const WallMap& wm, double h0c, double V, double Uw, double D_ion, float* T,
-                               cudaStream_t s);
+cudaError_t launch_wall_labels(const TV* u, const TV* v, const TV* w, const IonView& ions, const double* ycf,
+                               const double* dyf, const double* hf, const WallMap& wm, double h0c, double V,
+                               double Uw, double D_ion, float* T, cudaStream_t s);
 template <typename TV>
 cudaError_t launch_set_slip(const float* X, int ncells, const float* Y, size_t P, double Uw, double h0b, double h0t,
                             TV* wall_u, TV* wall_w, cudaStream_t s);
@@ -38,17 +52,12 @@ cudaError_t launch_mean_rates(float* Y, int P, cudaStream_t s);
 // wall-potential offsets B, T += gain (predicted - present first-cell potential), within +-lim
 cudaError_t launch_edl_offsets(const float* X, int ncells, const float* Y, size_t P, double gain, double lim, double* B,
                                double* T, cudaStream_t s);
-// df shadows of the ion fields of a mixed-precision context (all null for FP64)
-struct FluxFixShadows {
-  float *cpS, *cpL, *cmS, *cmL;
-  const double *crefp, *crefm;
-};
 // conservative transfer of ions across the first interior face of each wall
-// column towards the predicted fluxes
+// column towards the predicted fluxes; the updated values go to the FP64
+// arrays (ions.cp set) or to the shadows S, L of a mixed-precision context
 template <typename TV>
-cudaError_t launch_wall_flux_fix(double* cp, double* cm, const double* Phi, const TV* v, const double* idy,
-                                 const double* ih, const Geo& g, double Dion, const float* Y, double gain, double dt,
-                                 const FluxFixShadows& sh, cudaStream_t s);
+cudaError_t launch_wall_flux_fix(const IonView& ions, const TV* v, const double* idy, const double* ih, const Geo& g,
+                                 double Dion, const float* Y, double gain, double dt, cudaStream_t s);
 
 // ---- MLP 40 -> 128 x 4 (erf-GELU) -> 5 ----
 constexpr int kMlpLayers = 5;

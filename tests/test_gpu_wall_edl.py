@@ -52,7 +52,8 @@ def test_potential_offsets_match_the_oracle(precision):
     P, nc, gain = g.nz * g.nx, 4, 0.7
     wm.set_coupling(s, 0, 1.0, potential_gain=gain, flux_gain=0.0)
     B, T = np.zeros((g.nz, g.nx)), np.zeros((g.nz, g.nx))
-    tol_phi = 1e-12 if precision == 0 else 1e-6
+    # (the mixed context solves the potential with its own pipeline once it steps on its shadows)
+    tol_phi = 1e-12 if precision == 0 else 1e-5
     tol = 1e-10 if precision == 0 else 1e-5
     dt = 0.01
     for stage, seed in enumerate((11, 12)):   # offsets accumulate over updates
