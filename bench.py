@@ -253,7 +253,7 @@ def run_large(args, B, Solver, torch):
 # coarse run coupled to the previous network, dataset aggregation); a later,
 # unseen window judges c_f against the fine run, and times fine and coarse.
 WM = dict(V=5.0, rx=2, ry=4, window=1000, every=2, spinup=8000, layer_steps=1000, passes=3, iters=3000,
-          batch=65536, chunk=20, mode=2, relax=1.0, potential_gain=0.3, flux_gain=0.3, seed=1705, amp=0.05)
+          batch=65536, chunk=20, mode=3, relax=1.0, potential_gain=0.3, flux_gain=0.3, seed=1705, amp=0.05)
 
 
 def vortices_and_streaks(yf, nz, Lz, A=0.15, Bs=0.4, m=1):
@@ -358,6 +358,12 @@ def run_wallmodel(args, B, Solver, torch):
             net.set_normalization(xs.cpu().numpy(), (1.0 / xsd).cpu().numpy(), ts.cpu().numpy(),
                                   (1.0 / tsd).cpu().numpy())
         lr0, lr1 = (2e-3, 5e-4) if p == 0 else (1e-3, 3e-4)
+        if net is not None and p > 0:
+            pr = net.params()
+            Yc = net.forward(X[:c["batch"]])
+            log(f"pass {p}: params finite {bool(np.isfinite(pr).all())}, forward finite "
+                f"{bool(torch.isfinite(Yc).all())}, max |x| normalised "
+                f"{float((((X[:c['batch']].double() - xs) / xsd).abs().max()))}")
         nb = max(1, X.shape[0] // c["batch"])
         perm = torch.randperm(X.shape[0], device=X.device)
         Xp, Tp = X[perm].contiguous(), T[perm].contiguous()
@@ -368,6 +374,7 @@ def run_wallmodel(args, B, Solver, torch):
                            lr0 if it < c["iters"] // 2 else lr1)
         l1 = net.train_step(Xp[:c["batch"]], Tp[:c["batch"]], lr1, want_loss=True)
         losses.append([l0, l1])
+        log(f"pass {p}: loss {l0:.4g} -> {l1:.4g}")
         del Xp, Tp, perm
         if not math.isfinite(l1):   # a pass that failed to train: back to the last good network
             if good is not None:
@@ -379,19 +386,29 @@ def run_wallmodel(args, B, Solver, torch):
         for s_ in (fine, sc):
             s_.close()
         return {"error": "no finite training rows", "spinup_cf": cf_spin, "spinup_time_units": t_spin}
-    # the judged window: fine truth, coarse alone, coarse coupled to the network
-    sp, sm = coarse(), coarse()
+    # the judged window: fine truth, coarse alone, and the coarse run coupled to the
+    # network in two ways: the double layer only (the solver's own wall shear, mode 3)
+    # and the double layer with the plane-mean predicted wall stress (mode 2)
+    sp = coarse()
+    cpl = {"coupled_edl": coarse(), "coupled_shear": coarse()}
     wm.restrict(fine, sp)
-    wm.restrict(fine, sm)
-    couple(sm)
-    cf = {"fine": [], "plain": [], "coupled": []}
+    for k, s_ in cpl.items():
+        wm.restrict(fine, s_)
+        wm.set_coupling(s_, 3 if k == "coupled_edl" else 2, c["relax"], c["potential_gain"], c["flux_gain"])
+    runs = {"plain": sp, **cpl}
+    cf = {"fine": [], **{k: [] for k in runs}}
+    phi_err = {k: [] for k in runs}
     for n in range(c["window"] // c["chunk"]):
         fine.step(c["chunk"], dt)
         sp.step(c["chunk"], dt)
-        wm.step_with_model(sm, net, c["chunk"], dt)
+        for s_ in cpl.values():
+            wm.step_with_model(s_, net, c["chunk"], dt)
         cf["fine"].append(fine.diagnostics()["cf"])
-        cf["plain"].append(sp.diagnostics()["cf"])
-        cf["coupled"].append(sm.diagnostics()["cf"])
+        phi_f = wm.labels(fine, sp)[:, 2]
+        for k, s_ in runs.items():
+            cf[k].append(s_.diagnostics()["cf"])
+            phi_c = wm.features(s_, 8)[:, 4 * 8]
+            phi_err[k].append(float((phi_c - phi_f).abs().mean() / phi_f.abs().mean()))
     f = np.array(cf["fine"])
     err = lambda a: float(np.mean(np.abs(np.array(a) - f) / f))
     merr = lambda a: float(abs(np.mean(a) - np.mean(f)) / np.mean(f))
@@ -399,8 +416,8 @@ def run_wallmodel(args, B, Solver, torch):
     dyf = np.diff(yf)
     uf = fine.mean_profile("u")
     ufc = (uf * dyf).reshape(-1, c["ry"]).sum(1) / dyf.reshape(-1, c["ry"]).sum(1)
-    uerr = lambda s: float(np.max(np.abs(s.mean_profile("u") - ufc)))
-    u_err = {"plain": uerr(sp), "coupled": uerr(sm)}
+    u_err = {k: float(np.max(np.abs(s_.mean_profile("u") - ufc))) for k, s_ in runs.items()}
+    sm = cpl["coupled_edl"]
 
     # time per step: fine, coarse alone, coarse with the model
     def timed(fn, s, n=100):
@@ -420,23 +437,25 @@ def run_wallmodel(args, B, Solver, torch):
     out = {"workload": f"fine {nx}x{ny}x{nz} (mixed) -> coarse {ncx}x{ncy}x{ncz}, Re {WL['Re']:g}, "
                        f"lambda_D/h {WL['lam']}, V {c['V']:g}, dt {dt:.4g}, {c['spinup']} spin-up steps at V 0, "
                        f"{c['passes']} training windows + 1 judged window of {c['window']} steps",
-           "coupling": {k: c[k] for k in ("mode", "relax", "potential_gain", "flux_gain")},
+           "coupling": {**{k: c[k] for k in ("mode", "relax", "potential_gain", "flux_gain")},
+                        "note": "training passes coupled in this mode; judged in mode 3 (coupled_edl) and mode 2 "
+                                "(coupled_shear)"},
            "spinup": {"steps_at_V0": c["spinup"], "dt_max_V0": dt0, "time_units": t_spin, "cf_after": cf_spun,
                       "cf_laminar": 2.0 / WL["Re"],
                       "cf_series": [round(x, 7) for x in cf_spin], "turbulent": bool(cf_spun > 2.0 * 2.0 / WL["Re"]),
                       "layer_steps_at_V": c["layer_steps"], "seconds": spin_s},
            "training": {"rows": int(X.shape[0]), "snapshots": len(Xs), "iters_per_pass": c["iters"],
                         "batch": c["batch"], "loss_first_last": losses, "seconds": train_s - spin_s},
-           "cf_err_plain": err(cf["plain"]), "cf_err_coupled": err(cf["coupled"]),
+           "cf_err": {k: err(cf[k]) for k in runs}, "mean_cf_err": {k: merr(cf[k]) for k in runs},
+           "first_cell_phi_err": {k: float(np.mean(v)) for k, v in phi_err.items()},
            "mean_cf": {k: float(np.mean(v)) for k, v in cf.items()},
-           "mean_cf_err_plain": merr(cf["plain"]), "mean_cf_err_coupled": merr(cf["coupled"]),
            "mean_u_max_err": u_err,
            "cf_series": {k: [round(x, 6) for x in v[::5]] for k, v in cf.items()},
            "ms_per_step": {"fine": ms_f, "coarse": ms_p, "coarse_with_model": ms_c},
            "speedup_coarse_with_model_over_fine": ms_f / ms_c, "mlp_status": net.status(),
-           "status": {"fine": fine.diagnostics()["status"], "coupled": sm.diagnostics()["status"]}}
-    for s in (fine, sc, sp, sm):
-        s.close()
+           "status": {"fine": fine.diagnostics()["status"], **{k: s_.diagnostics()["status"] for k, s_ in cpl.items()}}}
+    for s_ in (fine, sc, sp, *cpl.values()):
+        s_.close()
     net.close()
     return out
 

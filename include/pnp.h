@@ -441,7 +441,10 @@ int pnp_set_wall_slip(pnp_ctx* ctx, const float* X_dev, int ncells, const float*
 int pnp_set_wall_stress(pnp_ctx* ctx, const float* X_dev, int ncells, const float* Y_dev);
 /* How pnp_step_wallmodel couples the network to the solver: mode 0 = wall slip
  * (pnp_set_wall_slip), 1 = wall stress (pnp_set_wall_stress), 2 = wall stress
- * from the plane means of the predicted rates (one rate per wall); relax in (0, 1]:
+ * from the plane means of the predicted rates (one rate per wall), 3 = no wall
+ * shear from the network (the solver's no-slip walls; for coarse grids that
+ * still resolve the viscous sublayer, with the double-layer coupling of
+ * pnp_set_wallmodel_edl); relax in (0, 1]:
  * the wall-shear rates used each step move that fraction of the way from the
  * previous step's to the new prediction (1 = no relaxation). */
 int pnp_set_wallmodel_coupling(pnp_ctx* ctx, int mode, double relax);

@@ -2502,7 +2502,7 @@ int pnp_set_wall_stress(pnp_ctx* c, const float* X, int ncells, const float* Y) 
 }
 
 int pnp_set_wallmodel_coupling(pnp_ctx* c, int mode, double relax) {
-  if (!c || mode < 0 || mode > 2 || !(relax > 0.0) || relax > 1.0) return PNP_ERR_ARG;
+  if (!c || mode < 0 || mode > 3 || !(relax > 0.0) || relax > 1.0) return PNP_ERR_ARG;
   c->wm_mode = mode;
   c->wm_relax = (float)relax;
   c->wm_have_prev = false;
@@ -2609,12 +2609,17 @@ int pnp_step_wallmodel(pnp_ctx* c, pnp_mlp* m, int nsteps, double dt) {
     if (r) return r;
     CK(mlp_forward(m->b, c->featX, rows, c->featY, c->stream));
     if (c->wm_mode == 2) CK(launch_mean_rates(c->featY, rows / 2, c->stream));
-    if (c->wm_relax < 1.f) {   // the rates used move a fraction of the way to the prediction
-      CK(launch_relax_rates(c->featY, c->featYprev, rows, c->wm_have_prev ? c->wm_relax : 1.f, c->stream));
-      c->wm_have_prev = true;
+    if (c->wm_mode <= 2) {   // mode 3 leaves the wall shear to the solver's own no-slip walls
+      if (c->wm_relax < 1.f) {   // the rates used move a fraction of the way to the prediction
+        CK(launch_relax_rates(c->featY, c->featYprev, rows, c->wm_have_prev ? c->wm_relax : 1.f, c->stream));
+        c->wm_have_prev = true;
+      }
+      r = set_wall_values(c, c->featX, 8, c->featY, c->wm_mode >= 1);
+      if (r) return r;
+    } else if (c->slip_on) {
+      r = set_wall_values(c, nullptr, 0, nullptr, false);
+      if (r) return r;
     }
-    r = set_wall_values(c, c->featX, 8, c->featY, c->wm_mode >= 1);
-    if (r) return r;
     if (c->edl_phi_gain > 0.0) {
       r = edl_potential(c, c->featX, 8, c->featY);
       if (r) return r;
