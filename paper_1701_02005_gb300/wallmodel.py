@@ -51,13 +51,18 @@ class MLP:
         arrs = [_fp(x) for x in (in_shift, in_scale, out_shift, out_scale)]
         B.check(B.pnp_mlp_set_normalization(self.m, *[p for _, p in arrs]), "pnp_mlp_set_normalization")
 
-    def _sync(self):
-        self.torch.cuda.synchronize(self.device)
+    def _after_torch(self, *tensors):
+        """Order the network's stream after the work torch has queued on the tensors
+        it reads (its current stream), and keep their memory from being reused by
+        torch's allocator until the network's stream has used it."""
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+        for t in tensors:
+            t.record_stream(self.stream)
 
     def forward(self, X):
         """X: device float32 tensor [B, 40] -> device tensor [B, 5]."""
         Y = self.torch.empty((X.shape[0], N_OUT), dtype=self.torch.float32, device=self.device)
-        self._sync()
+        self._after_torch(X, Y)
         B.check(B.pnp_mlp_forward(self.m, C.c_void_p(X.data_ptr()), int(X.shape[0]), C.c_void_p(Y.data_ptr())),
                 "pnp_mlp_forward")
         self.stream.synchronize()
@@ -66,13 +71,14 @@ class MLP:
     def gradient(self, X, T):
         g = np.empty(self.nparam, dtype=np.float32)
         loss = C.c_float()
-        self._sync()
+        self._after_torch(X, T)
         B.check(B.pnp_mlp_gradient(self.m, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()), int(X.shape[0]),
                                    g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss)), "pnp_mlp_gradient")
         return g, float(loss.value)
 
     def train_step(self, X, T, lr, want_loss=False):
         loss = C.c_float()
+        self._after_torch(X, T)
         B.check(B.pnp_mlp_train_step(self.m, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()), int(X.shape[0]),
                                      float(lr), C.byref(loss) if want_loss else None), "pnp_mlp_train_step")
         return float(loss.value) if want_loss else None
