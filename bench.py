@@ -112,6 +112,66 @@ def stable_dt(nx, ny, Re, lam, V, stretch, Lx=2 * math.pi):
     return dt, dphi_w * dy0
 
 
+def run_mlp(args, B, torch):
+    """Throughput of the wall model's network on its tcgen05 kernels: forward and
+    training step on 65,536 rows (the training batch; a coupled step of the
+    128x49x128 grid feeds 32,768).  The layers are 40 -> 128 x 4 -> 5: at 128
+    outputs a layer does 2 x 128 FLOPs per FP32 value it reads or writes, so the
+    forward is bound by HBM, not by the tensor cores."""
+    import ctypes as C
+
+    import numpy as np
+
+    from paper_1701_02005_gb300 import wallmodel as wm
+
+    rows, reps = 65536, 50
+    net = wm.MLP(rows, seed=7)
+    net.set_normalization(np.zeros(40), np.ones(40), np.zeros(5), np.ones(5))
+    g = torch.Generator(device="cuda").manual_seed(1707)
+    X = torch.randn((rows, 40), device="cuda", generator=g)
+    T = torch.randn((rows, 5), device="cuda", generator=g)
+    Y = torch.empty((rows, 5), device="cuda")
+    torch.cuda.synchronize()
+    fwd = lambda: B.check(B.pnp_mlp_forward(net.m, C.c_void_p(X.data_ptr()), rows, C.c_void_p(Y.data_ptr())),
+                          "pnp_mlp_forward")
+    trn = lambda: B.check(B.pnp_mlp_train_step(net.m, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()), rows,
+                                               1e-6, None), "pnp_mlp_train_step")
+
+    def timed(fn):
+        for _ in range(5):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        net.stream.synchronize()
+        e0.record(net.stream)
+        for _ in range(reps):
+            fn()
+        e1.record(net.stream)
+        net.stream.synchronize()
+        return e0.elapsed_time(e1) / reps * 1e-3
+
+    t_f, t_t = timed(fwd), timed(trn)
+    macs = 40 * 128 + 3 * 128 * 128 + 128 * 5
+    flops_f = 2.0 * rows * macs
+    # FP32 values read + written per row by the forward launches: input scaling 40 + 40,
+    # layers (40 + 128) + 3 (128 + 128) + (128 + 5), output scaling 5 + 5
+    bytes_f = 4.0 * rows * (80 + 168 + 3 * 256 + 133 + 10)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    out = {"rows": rows, "forward_us": t_f * 1e6, "train_step_us": t_t * 1e6,
+           "forward_tflops": flops_f / t_f / 1e12, "train_step_tflops": 3 * flops_f / t_t / 1e12,
+           "forward_gbs": bytes_f / t_f / 1e9,
+           "roofline_forward": {"bound": "hbm", "achieved": bytes_f / t_f / 1e9, "peak": hbm, "unit": "GB/s",
+                                "frac": bytes_f / t_f / 1e9 / hbm, "per_unit": "4636 B per row x 65536 rows"},
+           "tensor_frac_of_bf16_peak": flops_f / t_f / 1e12 / bf16, "status": net.status()}
+    net.close()
+    return out
+
+
 def ensemble_cases():
     import math as m
     out = []
@@ -995,9 +1055,19 @@ def run_ours(args):
     if not args.no_large:
         large = run_large(args, B, Solver, torch)
 
+    mlp = None
+    if rank == 0 and not args.no_wallmodel:
+        try:
+            mlp = run_mlp(args, B, torch)
+        except Exception as exc:  # noqa: BLE001
+            mlp = {"error": f"{type(exc).__name__}: {exc}"}
+
     wallmodel = None
     if rank == 0 and not args.no_wallmodel:
-        wallmodel = run_wallmodel(args, B, Solver, torch)
+        try:   # a side experiment: its failure must not cost the headline line
+            wallmodel = run_wallmodel(args, B, Solver, torch)
+        except Exception as exc:  # noqa: BLE001
+            wallmodel = {"error": f"{type(exc).__name__}: {exc}"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1015,6 +1085,7 @@ def run_ours(args):
         "ensemble": ensemble,
         "large_case": large,
         "wallmodel": wallmodel,
+        "wallmodel_network": mlp,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "launch_config": launch_cfg,
@@ -1068,6 +1139,7 @@ def main():
     ap.add_argument("--wallmodel", action="store_true", help="only the learned wall-model block (fine 256x193x256 "
                     "at V = 5 against coarse 128x49x128 with and without the network)")
     ap.add_argument("--wm-edl", type=float, nargs=2, default=None, metavar=("POTENTIAL_GAIN", "FLUX_GAIN"))
+    ap.add_argument("--mlp", action="store_true", help="only the wall-model network's forward / training throughput")
     ap.add_argument("--large-steps", type=int, default=20)
     ap.add_argument("--grid", default=None,
                     help="NX,NY,NZ override of the workload grid (small cases for profiler captures only)")
@@ -1085,6 +1157,13 @@ def main():
         return run_curve(args)
     if args.sweep:
         return run_sweep(args)
+    if args.mlp:
+        import torch
+
+        from paper_1701_02005_gb300 import binding as B
+
+        print(json.dumps({"mlp": run_mlp(args, B, torch)}), flush=True)
+        return 0
     if args.wallmodel:
         import torch
 
