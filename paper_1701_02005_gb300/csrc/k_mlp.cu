@@ -96,11 +96,6 @@ __global__ void k_mlp_loss_final(float* loss_partial, int nblk) {
   }
 }
 
-__global__ void k_mlp_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict__ q, size_t n) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) q[t] = __float2bfloat16_rn(p[t]);
-}
-
 __global__ void k_mlp_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                            float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps, float c1,
                            float c2) {
@@ -116,19 +111,20 @@ __global__ void k_mlp_adam(float* __restrict__ p, const float* __restrict__ g, f
 
 // ---------------------------------------------------------------------------
 cudaError_t mlp_sync_bf16(const MlpBufs& b, size_t nparam, cudaStream_t s) {
-  k_mlp_to_bf16<<<(unsigned)((nparam + 255) / 256), 256, 0, s>>>(b.param, b.wbf, nparam);
-  return cudaGetLastError();
+  (void)nparam;
+  return mlp_make_images(b.param, b.wimg, s);
 }
 
 cudaError_t mlp_forward(const MlpBufs& b, const float* X, int B, float* Y, cudaStream_t s) {
   const MlpDims d = mlp_dims();
+  const MlpImg im = mlp_images();
   const size_t ni = (size_t)B * kMlpIn;
   k_mlp_norm_in<<<(unsigned)((ni + 255) / 256), 256, 0, s>>>(X, B, b.in_shift, b.in_scale, b.act[0]);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   for (int l = 0; l < kMlpLayers; ++l) {
-    e = mlp_fwd_layer_tc(b.act[l], d.in[l], l > 0, b.wbf + d.woff[l], b.param + d.boff[l], d.out[l], B, b.act[l + 1],
-                         b.err, s);
+    e = mlp_fwd_layer_tc(b.act[l], d.in[l], l > 0, b.wimg + im.fwd[l], b.param + d.boff[l], d.out[l], B,
+                         b.act[l + 1], b.err, s);
     if (e != cudaSuccess) return e;
   }
   if (Y) {
@@ -141,6 +137,7 @@ cudaError_t mlp_forward(const MlpBufs& b, const float* X, int B, float* Y, cudaS
 // Gradient of the loss for the activations left by mlp_forward on the same batch.
 cudaError_t mlp_backward(const MlpBufs& b, const float* T, int B, int max_partial, cudaStream_t s) {
   const MlpDims d = mlp_dims();
+  const MlpImg im = mlp_images();
   const int nloss = 120;
   k_mlp_loss<<<nloss, 256, 0, s>>>(b.act[kMlpLayers], T, B, b.out_shift, b.out_scale, b.dact, b.loss);
   k_mlp_loss_final<<<1, 32, 0, s>>>(b.loss, nloss);
@@ -158,7 +155,7 @@ cudaError_t mlp_backward(const MlpBufs& b, const float* T, int B, int max_partia
     k_mlp_reduce_partial<<<(len + 255) / 256, 256, 0, s>>>(b.partial, nblk, len, b.grad + d.woff[l],
                                                            b.grad + d.boff[l], N * K);
     if (l > 0) {
-      e = mlp_bwd_data_tc(dz, N, b.wbf + d.woff[l], K, B, b.act[l], other, b.err, s);
+      e = mlp_bwd_data_tc(dz, N, b.wimg + im.bwd[l], K, B, b.act[l], other, b.err, s);
       if (e != cudaSuccess) return e;
       float* t = dz;
       dz = other;

@@ -7,11 +7,14 @@
 //   weight grad  dW[n][k] = sum_b dz[b][n] a(b, k),  dbias[n] = sum_b dz[b][n]
 //
 // Every GEMM is D[M = 128][N] += A[128][K] B[N][K]^T with both operands
-// K-major: a CTA owns 128 rows of D (one per thread of its four warps, which is
-// also the TMEM lane each warp may read), stages A and B as BF16 in the
-// canonical no-swizzle layout (8-row x 16-byte core matrices, the K groups
-// outermost), and one thread issues K/16 MMAs whose completion it commits to
-// an mbarrier; the warps then read their 32 accumulator lanes with tcgen05.ld.
+// K-major: a CTA owns 128 rows of D and stages A and B as BF16 in the canonical
+// no-swizzle layout (8-row x 16-byte core matrices, the K groups outermost):
+// A from the FP32 activations with coalesced vector loads, B as a straight copy
+// of a weight image kept in that layout (rebuilt whenever the weights change).
+// One thread issues K/16 MMAs whose completion it commits to an mbarrier; the
+// eight warps then read the accumulators with tcgen05.ld (warp w its TMEM lanes
+// 32 (w % 4) .. + 31, half of the columns each), stage them in shared memory
+// and write the rows out coalesced.
 // The weight gradient reduces over the batch: its M is the layer's outputs,
 // its N the layer's inputs plus a column of ones (the bias gradient), and its K
 // runs over the CTA's batch rows in 64-row chunks accumulated in TMEM.  Waits
@@ -29,7 +32,7 @@ namespace pnp {
 namespace {
 
 constexpr int kTcRows = 128;      // rows of D per CTA (M of every MMA)
-constexpr int kTcThreads = 128;   // four warps: warp w reads TMEM lanes 32w .. 32w + 31
+constexpr int kTcThreads = 256;   // eight warps: warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31
 constexpr int kWgK = 64;          // batch rows per weight-gradient chunk (four MMAs of K = 16)
 constexpr unsigned long long kTcWaitNs = 2000000000ull;
 
@@ -163,25 +166,31 @@ __device__ __forceinline__ bool mma_tiles(uint32_t tmem, const __nv_bfloat16* sA
   return ok;
 }
 
-// Shared memory: A [128][K] and B [N][K] BF16 tiles, an mbarrier and the TMEM slot.
+// Shared memory: A [128][K] and B [N][K] BF16 tiles (later the FP32 staging of
+// the epilogue, `data` bytes in all), an mbarrier and the TMEM slot.
 struct TcSmem {
   __nv_bfloat16* A;
   __nv_bfloat16* B;
+  float* C;
   unsigned long long* bar;
   uint32_t* slot;
 };
-__device__ __forceinline__ TcSmem tc_smem(unsigned char* base, int Kdim, int N) {
+__host__ __device__ inline size_t tc_data_bytes(int Kdim, int N, size_t stage_bytes) {
+  const size_t ab = ((size_t)kTcRows * Kdim + (size_t)N * Kdim) * 2;
+  return ((ab > stage_bytes ? ab : stage_bytes) + 15) & ~(size_t)15;
+}
+__device__ __forceinline__ TcSmem tc_smem(unsigned char* base, int Kdim, int N, size_t stage_bytes) {
   TcSmem t;
   t.A = reinterpret_cast<__nv_bfloat16*>(base);
   t.B = t.A + (size_t)kTcRows * Kdim;
-  unsigned char* tail = reinterpret_cast<unsigned char*>(t.B + (size_t)N * Kdim);
-  tail = reinterpret_cast<unsigned char*>(((uintptr_t)tail + 15) & ~(uintptr_t)15);
+  t.C = reinterpret_cast<float*>(base);
+  unsigned char* tail = base + tc_data_bytes(Kdim, N, stage_bytes);
   t.bar = reinterpret_cast<unsigned long long*>(tail);
   t.slot = reinterpret_cast<uint32_t*>(tail + 8);
   return t;
 }
-__host__ __device__ inline size_t tc_smem_bytes(int Kdim, int N) {
-  return ((size_t)kTcRows * Kdim + (size_t)N * Kdim) * 2 + 16 + 16;
+__host__ __device__ inline size_t tc_smem_bytes(int Kdim, int N, size_t stage_bytes) {
+  return tc_data_bytes(Kdim, N, stage_bytes) + 16;
 }
 
 __device__ __forceinline__ void set_bf16(__nv_bfloat16* tile, uint32_t off, float x) {
@@ -197,47 +206,154 @@ __device__ __forceinline__ void tc_timeout(int* err, unsigned long long* bar, un
   }
 }
 
+// A[r][k] (r < 128, k < Kp) = act(src[r][k]) for r < rows and k < Kd, zero
+// elsewhere; src holds rows x Kd FP32 values row after row.  Kd % 8 == 0: one
+// float4 load and one 8-byte store per 4 values (consecutive threads read
+// consecutive 16-byte chunks), the padding columns in 16-byte stores.
+__device__ __forceinline__ void stage_a(__nv_bfloat16* A, const float* __restrict__ src, int rows, int Kd, int Kp,
+                                        bool act) {
+  const int tid = threadIdx.x;
+  unsigned char* a = reinterpret_cast<unsigned char*>(A);
+  if ((Kd & 7) == 0) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    const int nq = kTcRows * Kd / 4;
+    for (int q = tid; q < nq; q += kTcThreads) {
+      const int e = 4 * q, r = e / Kd, k = e - r * Kd;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < rows) {
+        x = __ldg(s4 + q);
+        if (act) {
+          x.x = gelu_tc(x.x);
+          x.y = gelu_tc(x.y);
+          x.z = gelu_tc(x.z);
+          x.w = gelu_tc(x.w);
+        }
+      }
+      const __nv_bfloat162 lo = __floats2bfloat162_rn(x.x, x.y), hi = __floats2bfloat162_rn(x.z, x.w);
+      uint2 u;
+      u.x = *reinterpret_cast<const uint32_t*>(&lo);
+      u.y = *reinterpret_cast<const uint32_t*>(&hi);
+      *reinterpret_cast<uint2*>(a + canon(r, k, kTcRows)) = u;
+    }
+    const int nper = (Kp - Kd) >> 3;
+    for (int e = tid; e < kTcRows * nper; e += kTcThreads) {
+      const int r = e / nper, k = Kd + 8 * (e - r * nper);
+      *reinterpret_cast<uint4*>(a + canon(r, k, kTcRows)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+  } else {
+    for (int e = tid; e < kTcRows * Kp; e += kTcThreads) {
+      const int r = e / Kp, k = e - r * Kp;
+      float x = 0.f;
+      if (r < rows && k < Kd) {
+        x = src[(size_t)r * Kd + k];
+        if (act) x = gelu_tc(x);
+      }
+      set_bf16(A, canon(r, k, kTcRows), x);
+    }
+  }
+}
+
+// T[rr][bb] = act(src[bb][rr]) for bb < rows, rr < Rs (the transpose of a chunk
+// of rows, for the weight gradient, whose K is the batch), T[ones_at][bb] = 1
+// for bb < rows when ones_at >= 0, and zero in columns bb >= rows; rows Rs..R-1
+// other than ones_at are left as they are (zero from the start of the kernel).
+__device__ __forceinline__ void stage_t(__nv_bfloat16* T, int R, const float* __restrict__ src, int rows, int Rs,
+                                        bool act, int ones_at) {
+  const int tid = threadIdx.x;
+  if ((Rs & 3) == 0) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    const int nq = rows * Rs / 4;
+    for (int q = tid; q < nq; q += kTcThreads) {
+      const int e = 4 * q, bb = e / Rs, rr = e - bb * Rs;
+      float4 x = __ldg(s4 + q);
+      if (act) {
+        x.x = gelu_tc(x.x);
+        x.y = gelu_tc(x.y);
+        x.z = gelu_tc(x.z);
+        x.w = gelu_tc(x.w);
+      }
+      set_bf16(T, canon(rr, bb, R), x.x);
+      set_bf16(T, canon(rr + 1, bb, R), x.y);
+      set_bf16(T, canon(rr + 2, bb, R), x.z);
+      set_bf16(T, canon(rr + 3, bb, R), x.w);
+    }
+  } else {
+    for (int e = tid; e < rows * Rs; e += kTcThreads) {
+      const int bb = e / Rs, rr = e - bb * Rs;
+      float x = src[e];
+      if (act) x = gelu_tc(x);
+      set_bf16(T, canon(rr, bb, R), x);
+    }
+  }
+  if (ones_at >= 0)
+    for (int bb = tid; bb < kWgK; bb += kTcThreads) set_bf16(T, canon(ones_at, bb, R), bb < rows ? 1.f : 0.f);
+  for (int e = tid; e < (kWgK - rows) * Rs; e += kTcThreads) {
+    const int bb = rows + e / Rs, rr = e % Rs;
+    set_bf16(T, canon(rr, bb, R), 0.f);
+  }
+}
+
+// The weight image of a layer (16-byte chunks, already in the shared-memory layout).
+__device__ __forceinline__ void copy_image(__nv_bfloat16* Bt, const __nv_bfloat16* __restrict__ img, int n16) {
+  const uint4* s = reinterpret_cast<const uint4*>(img);
+  uint4* d = reinterpret_cast<uint4*>(Bt);
+  for (int i = threadIdx.x; i < n16; i += kTcThreads) d[i] = __ldg(s + i);
+}
+
+// Accumulator columns [0, ncol) of the CTA's 128 rows into C[r][c] (row stride
+// ldc floats): warp w reads its lanes 32 (w % 4) .. + 31, the columns 16-wide
+// groups alternately with the warp w +- 4 that shares those lanes.
+__device__ __forceinline__ void tmem_to_smem(uint32_t tmem, int ncol, float* C, int ldc) {
+  const int warp = threadIdx.x >> 5, grp = warp & 3, half = warp >> 2;
+  const int r = 32 * grp + (threadIdx.x & 31);
+  const uint32_t lane = tmem + ((uint32_t)(32 * grp) << 16);
+  for (int c0 = 16 * half; c0 < ncol; c0 += 32) {
+    float v[16];
+    tmem_ld16(lane + c0, v);
+    float4* row = reinterpret_cast<float4*>(C + (size_t)r * ldc + c0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) row[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  }
+}
+
 }  // namespace
 
-// z[b][n] = sum_k a(b, k) W[n][k] + bias[n] for the CTA's 128 rows; Kp, Np: K, N rounded up to 16.
+// z[b][n] = sum_k a(b, k) W[n][k] + bias[n] for the CTA's 128 rows; Kp, Np: K, N
+// rounded up to 16; Wimg: the layer's forward weight image [Np][Kp].
 __global__ void __launch_bounds__(kTcThreads) k_mlp_fwd_tc(const float* __restrict__ in, int K, int act_in,
-                                                           const __nv_bfloat16* __restrict__ W,
+                                                           const __nv_bfloat16* __restrict__ Wimg,
                                                            const float* __restrict__ bias, int N, int B,
                                                            float* __restrict__ out, int* err) {
   extern __shared__ __align__(128) unsigned char tc_raw[];
-  const int Kp = (K + 15) & ~15, Np = (N + 15) & ~15;
-  const TcSmem s = tc_smem(tc_raw, Kp, Np);
+  const int Kp = (K + 15) & ~15, Np = (N + 15) & ~15, ldc = Np + 4;
+  const TcSmem s = tc_smem(tc_raw, Kp, Np, (size_t)kTcRows * ldc * sizeof(float));
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t ncols = tmem_cols(Np);
   if (warp == 0) tmem_alloc(s.slot, ncols);
   if (tid == 0) mbar_init1(s.bar);
-  const int b = blockIdx.x * kTcRows + tid;
-  for (int k = 0; k < Kp; ++k) {
-    float x = 0.f;
-    if (b < B && k < K) {
-      x = in[(size_t)b * K + k];
-      if (act_in) x = gelu_tc(x);
-    }
-    set_bf16(s.A, canon(tid, k, kTcRows), x);
-  }
-  for (int e = tid; e < Np * Kp; e += kTcThreads) {
-    const int n = e / Kp, k = e - n * Kp;
-    const float wv = (n < N && k < K) ? __bfloat162float(W[(size_t)n * K + k]) : 0.f;
-    set_bf16(s.B, canon(n, k, Np), wv);
-  }
+  const int b0 = blockIdx.x * kTcRows, rows = min(kTcRows, B - b0);
+  stage_a(s.A, in + (size_t)b0 * K, rows, K, Kp, act_in != 0);
+  copy_image(s.B, Wimg, Np * Kp / 8);
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *s.slot;
   if (mma_tiles(tmem, s.A, s.B, Np, Kp, false, s.bar, 0)) {
-    const uint32_t lane = tmem + ((uint32_t)(32 * warp) << 16);
-    for (int c0 = 0; c0 < Np; c0 += 16) {
-      float v[16];
-      tmem_ld16(lane + c0, v);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int n = c0 + i;
-        if (b < B && n < N) out[(size_t)b * N + n] = v[i] + bias[n];
+    tmem_to_smem(tmem, Np, s.C, ldc);   // the tiles are free: their MMAs have completed
+    __syncthreads();
+    float* o = out + (size_t)b0 * N;   // the CTA's rows are rows * N consecutive values
+    const int n_el = rows * N;
+    if ((N & 3) == 0) {
+      for (int e = 4 * tid; e < n_el; e += 4 * kTcThreads) {
+        const int r = e / N, n = e - r * N;
+        const float4 c = *reinterpret_cast<const float4*>(s.C + (size_t)r * ldc + n);
+        const float4 bv = *reinterpret_cast<const float4*>(bias + n);
+        *reinterpret_cast<float4*>(o + e) = make_float4(c.x + bv.x, c.y + bv.y, c.z + bv.z, c.w + bv.w);
+      }
+    } else {
+      for (int e = tid; e < n_el; e += kTcThreads) {
+        const int r = e / N, n = e - r * N;
+        o[e] = s.C[(size_t)r * ldc + n] + bias[n];
       }
     }
   } else {
@@ -248,44 +364,43 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_fwd_tc(const float* __restri
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
-// da[b][k] = (sum_n dz[b][n] W[n][k]) GELU'(zprev[b][k]): A = dz [128][Np], B = W^T [Kq][Np].
+// da[b][k] = (sum_n dz[b][n] W[n][k]) GELU'(zprev[b][k]): A = dz [128][Np], B = W^T
+// from the layer's backward weight image [Kq][Np].
 __global__ void __launch_bounds__(kTcThreads) k_mlp_bwd_data_tc(const float* __restrict__ dz, int N,
-                                                                const __nv_bfloat16* __restrict__ W, int K, int B,
+                                                                const __nv_bfloat16* __restrict__ WimgT, int K, int B,
                                                                 const float* __restrict__ zprev,
                                                                 float* __restrict__ out, int* err) {
   extern __shared__ __align__(128) unsigned char tc_raw[];
-  const int Np = (N + 15) & ~15, Kq = (K + 15) & ~15;
-  const TcSmem s = tc_smem(tc_raw, Np, Kq);
+  const int Np = (N + 15) & ~15, Kq = (K + 15) & ~15, ldc = Kq + 4;
+  const TcSmem s = tc_smem(tc_raw, Np, Kq, (size_t)kTcRows * ldc * sizeof(float));
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t ncols = tmem_cols(Kq);
   if (warp == 0) tmem_alloc(s.slot, ncols);
   if (tid == 0) mbar_init1(s.bar);
-  const int b = blockIdx.x * kTcRows + tid;
-  for (int n = 0; n < Np; ++n) {
-    const float g = (b < B && n < N) ? dz[(size_t)b * N + n] : 0.f;
-    set_bf16(s.A, canon(tid, n, kTcRows), g);
-  }
-  for (int e = tid; e < Kq * Np; e += kTcThreads) {
-    const int n = e / Kq, k = e - n * Kq;   // consecutive threads read consecutive W[n][k]
-    const float wv = (n < N && k < K) ? __bfloat162float(W[(size_t)n * K + k]) : 0.f;
-    set_bf16(s.B, canon(k, n, Kq), wv);
-  }
+  const int b0 = blockIdx.x * kTcRows, rows = min(kTcRows, B - b0);
+  stage_a(s.A, dz + (size_t)b0 * N, rows, N, Np, false);
+  copy_image(s.B, WimgT, Kq * Np / 8);
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *s.slot;
   if (mma_tiles(tmem, s.A, s.B, Kq, Np, false, s.bar, 0)) {
-    const uint32_t lane = tmem + ((uint32_t)(32 * warp) << 16);
-    for (int c0 = 0; c0 < Kq; c0 += 16) {
-      float v[16];
-      tmem_ld16(lane + c0, v);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int k = c0 + i;
-        if (b < B && k < K) {
-          const size_t o = (size_t)b * K + k;
-          out[o] = v[i] * gelu_d_tc(zprev[o]);
-        }
+    tmem_to_smem(tmem, Kq, s.C, ldc);
+    __syncthreads();
+    const size_t base = (size_t)b0 * K;
+    const int n_el = rows * K;
+    if ((K & 3) == 0) {
+      for (int e = 4 * tid; e < n_el; e += 4 * kTcThreads) {
+        const int r = e / K, k = e - r * K;
+        const float4 c = *reinterpret_cast<const float4*>(s.C + (size_t)r * ldc + k);
+        const float4 z = __ldg(reinterpret_cast<const float4*>(zprev + base + e));
+        *reinterpret_cast<float4*>(out + base + e) =
+            make_float4(c.x * gelu_d_tc(z.x), c.y * gelu_d_tc(z.y), c.z * gelu_d_tc(z.z), c.w * gelu_d_tc(z.w));
+      }
+    } else {
+      for (int e = tid; e < n_el; e += kTcThreads) {
+        const int r = e / K, k = e - r * K;
+        out[base + e] = s.C[(size_t)r * ldc + k] * gelu_d_tc(zprev[base + e]);
       }
     }
   } else {
@@ -306,11 +421,16 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_wgrad_tc(const float* __rest
                                                              int* err) {
   extern __shared__ __align__(128) unsigned char tc_raw[];
   const int Nw = ((K + 1) + 15) & ~15;   // inputs and the ones column of the bias
-  const TcSmem s = tc_smem(tc_raw, kWgK, Nw);
+  const TcSmem s = tc_smem(tc_raw, kWgK, Nw, 0);
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t ncols = tmem_cols(Nw);
   if (warp == 0) tmem_alloc(s.slot, ncols);
   if (tid == 0) mbar_init1(s.bar);
+  {   // rows N.. of A and K+1.. of B stay zero for the whole kernel
+    uint4* z = reinterpret_cast<uint4*>(s.A);
+    const int n16 = (kTcRows + Nw) * kWgK * 2 / 16;
+    for (int i = tid; i < n16; i += kTcThreads) z[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
   fence_before();
   __syncthreads();
   fence_after();
@@ -324,31 +444,16 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_wgrad_tc(const float* __rest
       fence_before();
       __syncthreads();
     }
-    for (int e = tid; e < kTcRows * kWgK; e += kTcThreads) {
-      const int n = e / kWgK, bb = e - n * kWgK;
-      const float g = (n < N && bb < rows) ? dz[(size_t)(c0 + bb) * N + n] : 0.f;
-      set_bf16(s.A, canon(n, bb, kTcRows), g);
-    }
-    for (int e = tid; e < Nw * kWgK; e += kTcThreads) {
-      const int k = e / kWgK, bb = e - k * kWgK;
-      float x = 0.f;
-      if (bb < rows) {
-        if (k < K) {
-          x = in[(size_t)(c0 + bb) * K + k];
-          if (act_in) x = gelu_tc(x);
-        } else if (k == K) {
-          x = 1.f;
-        }
-      }
-      set_bf16(s.B, canon(k, bb, Nw), x);
-    }
+    stage_t(s.A, kTcRows, dz + (size_t)c0 * N, rows, N, false, -1);
+    stage_t(s.B, Nw, in + (size_t)c0 * K, rows, K, act_in != 0, K);
     ok = mma_tiles(tmem, s.A, s.B, Nw, kWgK, c0 > r0, s.bar, phase);
   }
   float* p = partial + (size_t)blockIdx.x * ((size_t)N * K + N);
   if (ok && r0 < r1) {
-    const uint32_t lane = tmem + ((uint32_t)(32 * warp) << 16);
-    const int n = tid;   // this thread's TMEM lane is output row n
-    for (int c0 = 0; c0 < Nw; c0 += 16) {
+    const int grp = warp & 3, half = warp >> 2;
+    const int n = 32 * grp + (tid & 31);   // this thread's TMEM lane is output row n
+    const uint32_t lane = tmem + ((uint32_t)(32 * grp) << 16);
+    for (int c0 = 16 * half; c0 < Nw; c0 += 32) {
       float v[16];
       tmem_ld16(lane + c0, v);
 #pragma unroll
@@ -368,43 +473,96 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_wgrad_tc(const float* __rest
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
+// Weight images: for every layer, the BF16 weights in the shared-memory layout
+// of the forward GEMM's B tile (rows n < Np, columns k < Kp) and of the data
+// gradient's (rows k < Kp, columns n < Np), zero in the padding.
+MlpImg mlp_images() {
+  const MlpDims d = mlp_dims();
+  MlpImg im{};
+  size_t off = 0;
+  for (int l = 0; l < kMlpLayers; ++l) {
+    const size_t Kp = (size_t)((d.in[l] + 15) & ~15), Np = (size_t)((d.out[l] + 15) & ~15);
+    im.fwd[l] = off;
+    off += Np * Kp;
+    im.bwd[l] = off;
+    off += Kp * Np;
+  }
+  im.total = off;
+  return im;
+}
+
+__global__ void k_mlp_images(const float* __restrict__ param, __nv_bfloat16* __restrict__ img, MlpDims d, MlpImg im) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int l = 0; l < kMlpLayers; ++l) {
+    const int K = d.in[l], N = d.out[l], Kp = (K + 15) & ~15, Np = (N + 15) & ~15;
+    unsigned char* f = reinterpret_cast<unsigned char*>(img + im.fwd[l]);
+    unsigned char* b = reinterpret_cast<unsigned char*>(img + im.bwd[l]);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Np * Kp; e += stride) {
+      const int n = e / Kp, k = e - n * Kp;
+      const __nv_bfloat16 w =
+          __float2bfloat16_rn((n < N && k < K) ? param[d.woff[l] + (size_t)n * K + k] : 0.f);
+      *reinterpret_cast<__nv_bfloat16*>(f + canon(n, k, Np)) = w;
+      *reinterpret_cast<__nv_bfloat16*>(b + canon(k, n, Kp)) = w;
+    }
+  }
+}
+
+cudaError_t mlp_make_images(const float* param, __nv_bfloat16* img, cudaStream_t s) {
+  k_mlp_images<<<64, 256, 0, s>>>(param, img, mlp_dims(), mlp_images());
+  return cudaGetLastError();
+}
+
 // ---- launchers ----
-// Dynamic shared memory of at least 80 KB per CTA keeps at most two CTAs (and
-// at most 2 x 256 tensor-memory columns) on an SM, so an allocation never waits
-// for a CTA that is not running.
-constexpr size_t kTcMinSmem = 80 * 1024;
+namespace {
+uint32_t tmem_cols_host(int n) {
+  uint32_t c = 32;
+  while ((int)c < n) c <<= 1;
+  return c;
+}
+
+// Dynamic shared memory large enough that no more CTAs share an SM than its 512
+// tensor-memory columns hold at once, so an allocation never waits.
+size_t tc_min_smem(uint32_t ncols) {
+  const int fit = 512 / (int)ncols;
+  return fit >= 8 ? 0 : (size_t)(228 * 1024) / (size_t)(fit + 1) + 1024;
+}
 
 template <typename Kern, typename... Args>
-cudaError_t tc_launch(Kern kern, unsigned grid, size_t smem_need, cudaStream_t s, Args... args) {
-  const size_t smem = smem_need > kTcMinSmem ? smem_need : kTcMinSmem;
+cudaError_t tc_launch(Kern kern, unsigned grid, size_t smem_need, uint32_t ncols, cudaStream_t s, Args... args) {
+  if (grid == 0) return cudaSuccess;
+  const size_t floor_b = tc_min_smem(ncols);
+  const size_t smem = smem_need > floor_b ? smem_need : floor_b;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, kTcThreads, smem, s>>>(args...);
   return cudaGetLastError();
 }
+}  // namespace
 
-cudaError_t mlp_fwd_layer_tc(const float* in, int K, bool act_in, const __nv_bfloat16* W, const float* bias, int N,
+cudaError_t mlp_fwd_layer_tc(const float* in, int K, bool act_in, const __nv_bfloat16* Wimg, const float* bias, int N,
                              int B, float* out, int* err, cudaStream_t s) {
   if (K > 256 || N > 256) return cudaErrorInvalidValue;
   const int Kp = (K + 15) & ~15, Np = (N + 15) & ~15;
-  return tc_launch(k_mlp_fwd_tc, (unsigned)((B + kTcRows - 1) / kTcRows), tc_smem_bytes(Kp, Np), s, in, K,
-                   act_in ? 1 : 0, W, bias, N, B, out, err);
+  const size_t smem = tc_smem_bytes(Kp, Np, (size_t)kTcRows * (Np + 4) * sizeof(float));
+  return tc_launch(k_mlp_fwd_tc, (unsigned)((B + kTcRows - 1) / kTcRows), smem, tmem_cols_host(Np), s, in, K,
+                   act_in ? 1 : 0, Wimg, bias, N, B, out, err);
 }
 
-cudaError_t mlp_bwd_data_tc(const float* dz, int N, const __nv_bfloat16* W, int K, int B, const float* zprev,
+cudaError_t mlp_bwd_data_tc(const float* dz, int N, const __nv_bfloat16* WimgT, int K, int B, const float* zprev,
                             float* out, int* err, cudaStream_t s) {
   if (K > 256 || N > 256) return cudaErrorInvalidValue;
   const int Np = (N + 15) & ~15, Kq = (K + 15) & ~15;
-  return tc_launch(k_mlp_bwd_data_tc, (unsigned)((B + kTcRows - 1) / kTcRows), tc_smem_bytes(Np, Kq), s, dz, N, W,
-                   K, B, zprev, out, err);
+  const size_t smem = tc_smem_bytes(Np, Kq, (size_t)kTcRows * (Kq + 4) * sizeof(float));
+  return tc_launch(k_mlp_bwd_data_tc, (unsigned)((B + kTcRows - 1) / kTcRows), smem, tmem_cols_host(Kq), s, dz, N,
+                   WimgT, K, B, zprev, out, err);
 }
 
 cudaError_t mlp_wgrad_tc(const float* dz, int N, const float* in, int K, bool act_in, int B, int rows_per_block,
                          int nblk, float* partial, int* err, cudaStream_t s) {
   if (N > kTcRows || K + 1 > 256) return cudaErrorInvalidValue;
   const int Nw = ((K + 1) + 15) & ~15;
-  return tc_launch(k_mlp_wgrad_tc, (unsigned)nblk, tc_smem_bytes(kWgK, Nw), s, dz, N, in, K, act_in ? 1 : 0, B,
-                   rows_per_block, partial, err);
+  return tc_launch(k_mlp_wgrad_tc, (unsigned)nblk, tc_smem_bytes(kWgK, Nw, 0), tmem_cols_host(Nw), s, dz, N, in, K,
+                   act_in ? 1 : 0, B, rows_per_block, partial, err);
 }
 
 }  // namespace pnp

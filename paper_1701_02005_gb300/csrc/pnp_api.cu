@@ -2218,10 +2218,12 @@ void pnp_ensemble_destroy(pnp_ensemble* e) {
 // ---------------------------------------------------------------------------
 // Learned wall model: MLP workspace and the coupling to a coarse context.
 // ---------------------------------------------------------------------------
+constexpr int kMlpMaxPartial = 160;
+
 struct pnp_mlp {
   MlpBufs b{};
   int max_batch = 0;
-  int max_partial = 64;
+  int max_partial = 64;   // weight-gradient CTAs: one per SM (at most kMlpMaxPartial)
   size_t nparam = 0;
   cudaStream_t stream = nullptr;
   int t_adam = 0;
@@ -2235,7 +2237,7 @@ size_t mlp_carve(pnp_mlp* m, char* base, int max_batch) {
   const size_t np = d.nparam, B = (size_t)max_batch;
   MlpBufs b{};
   b.param = bp.take<float>(np);
-  b.wbf = bp.take<__nv_bfloat16>(np);
+  b.wimg = bp.take<__nv_bfloat16>(mlp_images().total);
   b.grad = bp.take<float>(np);
   b.m = bp.take<float>(np);
   b.v = bp.take<float>(np);
@@ -2243,7 +2245,7 @@ size_t mlp_carve(pnp_mlp* m, char* base, int max_batch) {
   for (int l = 0; l < kMlpLayers; ++l) b.act[l + 1] = bp.take<float>(B * d.out[l]);
   b.dact = bp.take<float>(B * kMlpHidden);
   b.dact2 = bp.take<float>(B * kMlpHidden);
-  b.partial = bp.take<float>(64 * (size_t)(kMlpHidden * kMlpHidden + kMlpHidden));
+  b.partial = bp.take<float>(kMlpMaxPartial * (size_t)(kMlpHidden * kMlpHidden + kMlpHidden));
   b.loss = bp.take<float>(128);
   b.in_shift = bp.take<float>(kMlpIn);
   b.in_scale = bp.take<float>(kMlpIn);
@@ -2300,6 +2302,12 @@ int pnp_mlp_create(pnp_mlp** out, int max_batch, void* ws, size_t bytes, void* s
   if (!m) return PNP_ERR_ARG;
   m->max_batch = max_batch;
   m->stream = (cudaStream_t)stream;
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+      m->max_partial = std::min(sms, kMlpMaxPartial);
+  }
   mlp_carve(m, (char*)ws, max_batch);
   // weights U(-a, a), a = sqrt(6 / fan_in) from SplitMix64; biases 0; unit normalisation
   const MlpDims d = mlp_dims();

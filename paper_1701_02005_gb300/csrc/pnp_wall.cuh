@@ -72,10 +72,19 @@ struct MlpDims {
 };
 MlpDims mlp_dims();
 
+// Offsets (BF16 elements) of the weight images: per layer the forward GEMM's B
+// tile [Np][Kp] and the data gradient's [Kp][Np], in the shared-memory layout.
+struct MlpImg {
+  size_t fwd[kMlpLayers], bwd[kMlpLayers];
+  size_t total;
+};
+MlpImg mlp_images();
+cudaError_t mlp_make_images(const float* param, __nv_bfloat16* img, cudaStream_t s);
+
 // Buffers of one MLP (all device pointers, carved by the host code).
 struct MlpBufs {
   float* param;        // FP32 master weights and biases
-  __nv_bfloat16* wbf;  // BF16 copy of the weights used by the forward GEMMs (same offsets)
+  __nv_bfloat16* wimg; // BF16 weight images of the GEMMs (mlp_images), rebuilt from param
   float* grad;         // gradient of the loss
   float* m;            // Adam first moment
   float* v;            // Adam second moment
@@ -89,9 +98,9 @@ struct MlpBufs {
 };
 
 // Tensor-core (tcgen05) GEMMs of the MLP (k_mlp_tc.cu).
-cudaError_t mlp_fwd_layer_tc(const float* in, int K, bool act_in, const __nv_bfloat16* W, const float* bias, int N,
+cudaError_t mlp_fwd_layer_tc(const float* in, int K, bool act_in, const __nv_bfloat16* Wimg, const float* bias, int N,
                              int B, float* out, int* err, cudaStream_t s);
-cudaError_t mlp_bwd_data_tc(const float* dz, int N, const __nv_bfloat16* W, int K, int B, const float* zprev,
+cudaError_t mlp_bwd_data_tc(const float* dz, int N, const __nv_bfloat16* WimgT, int K, int B, const float* zprev,
                             float* out, int* err, cudaStream_t s);
 cudaError_t mlp_wgrad_tc(const float* dz, int N, const float* in, int K, bool act_in, int B, int rows_per_block,
                          int nblk, float* partial, int* err, cudaStream_t s);
