@@ -217,6 +217,7 @@ __device__ __forceinline__ void stage_a(__nv_bfloat16* A, const float* __restric
   if ((Kd & 7) == 0) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
     const int nq = kTcRows * Kd / 4;
+#pragma unroll 4
     for (int q = tid; q < nq; q += kTcThreads) {
       const int e = 4 * q, r = e / Kd, k = e - r * Kd;
       float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -263,6 +264,7 @@ __device__ __forceinline__ void stage_t(__nv_bfloat16* T, int R, const float* __
   if ((Rs & 3) == 0) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
     const int nq = rows * Rs / 4;
+#pragma unroll 4
     for (int q = tid; q < nq; q += kTcThreads) {
       const int e = 4 * q, bb = e / Rs, rr = e - bb * Rs;
       float4 x = __ldg(s4 + q);
@@ -297,6 +299,7 @@ __device__ __forceinline__ void stage_t(__nv_bfloat16* T, int R, const float* __
 __device__ __forceinline__ void copy_image(__nv_bfloat16* Bt, const __nv_bfloat16* __restrict__ img, int n16) {
   const uint4* s = reinterpret_cast<const uint4*>(img);
   uint4* d = reinterpret_cast<uint4*>(Bt);
+#pragma unroll 4
   for (int i = threadIdx.x; i < n16; i += kTcThreads) d[i] = __ldg(s + i);
 }
 
@@ -344,6 +347,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_fwd_tc(const float* __restri
     float* o = out + (size_t)b0 * N;   // the CTA's rows are rows * N consecutive values
     const int n_el = rows * N;
     if ((N & 3) == 0) {
+#pragma unroll 4
       for (int e = 4 * tid; e < n_el; e += 4 * kTcThreads) {
         const int r = e / N, n = e - r * N;
         const float4 c = *reinterpret_cast<const float4*>(s.C + (size_t)r * ldc + n);
@@ -390,6 +394,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_bwd_data_tc(const float* __r
     const size_t base = (size_t)b0 * K;
     const int n_el = rows * K;
     if ((K & 3) == 0) {
+#pragma unroll 4
       for (int e = 4 * tid; e < n_el; e += 4 * kTcThreads) {
         const int r = e / K, k = e - r * K;
         const float4 c = *reinterpret_cast<const float4*>(s.C + (size_t)r * ldc + k);
