@@ -425,7 +425,8 @@ def run_wallmodel(args, B, Solver, torch):
                 f"{bool(torch.isfinite(Yc).all())}, max |x| normalised "
                 f"{float((((X[:c['batch']].double() - xs) / xsd).abs().max()))}")
         nb = max(1, X.shape[0] // c["batch"])
-        perm = torch.randperm(X.shape[0], device=X.device)
+        gen = torch.Generator(device=X.device).manual_seed(c["seed"] + p)
+        perm = torch.randperm(X.shape[0], device=X.device, generator=gen)
         Xp, Tp = X[perm].contiguous(), T[perm].contiguous()
         l0 = net.train_step(Xp[:c["batch"]], Tp[:c["batch"]], lr0, want_loss=True)
         for it in range(c["iters"]):
