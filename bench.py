@@ -1039,9 +1039,21 @@ def run_ours(args):
 
         r_sync = e2e_run(False)
         r = e2e_run(True)
+        # device time of one diagnostics pass (reductions + record copy) on its own
+        raw = s.diag_buffer()
+        s.diagnostics_post(raw)
+        s.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(s.stream)
+        for _ in range(20):
+            s.diagnostics_post(raw)
+        q1.record(s.stream)
+        s.synchronize()
+        diag_ms = q0.elapsed_time(q1) / 20
         e2e = {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": state_bytes / Ke,
                "d2h_bytes_per_step": 128 + r["d2h"] / Ke, "steps": Ke, "last_step_status": r["status"],
-               "phases": {k: r[k] for k in ("set_state_s", "steps_s", "ms_per_step_in_loop", "get_state_s")},
+               "phases": {**{k: r[k] for k in ("set_state_s", "steps_s", "ms_per_step_in_loop", "get_state_s")},
+                          "diagnostics_ms_alone": diag_ms},
                "synchronous_diagnostics": {k: r_sync[k] for k in ("value", "set_state_s", "ms_per_step_in_loop")},
                "note": "set_state of all 12 fields from pinned host, then per step pnp_step + "
                        "pnp_diagnostics_post (D2H of the step's diagnostics into a pinned record, read one step "
@@ -1126,7 +1138,7 @@ def main():
     ap.add_argument("--sweep-steps", type=int, default=4000)
     ap.add_argument("--sweep-amp", type=float, default=0.3)
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Fields<TV> f, Geo
 // could reach the running maximum, which gives the same maximum; the minimum
 // concentration is FP32; a value is counted non-finite when any input read for
 // it is.  Nx and Nz are powers of two.
-__global__ void __launch_bounds__(kDiagThreads, 4) k_diag_partial_mixed(Fields<float> f, Shadows sh,
+__global__ void __launch_bounds__(kDiagThreads, 3) k_diag_partial_mixed(Fields<float> f, Shadows sh,
                                                                         const float* __restrict__ cref_p,
                                                                         const float* __restrict__ cref_m,
                                                                         const float* __restrict__ dPref,
@@ -328,12 +328,13 @@ cudaError_t launch_diagnostics_mixed(const Fields<float>& f, const Shadows& sh, 
                                      const float* cref_m, const float* dPref, const float2* wgt, const Geo& g,
                                      double* partial, int npartial, double* out, int* status,
                                      const DiagLimits& lim, cudaStream_t s) {
-  // one resident wave: four 256-thread blocks per SM (64 registers a thread)
+  // one resident wave: three 256-thread blocks per SM (up to 85 registers a
+  // thread: the double-float sums of the row runs stay in registers)
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const int nb = std::max(1, std::min(npartial, 4 * sms));
+  const int nb = std::max(1, std::min(npartial, 3 * sms));
   k_diag_partial_mixed<<<nb, kDiagThreads, 0, s>>>(f, sh, cref_p, cref_m, dPref, wgt, g, partial);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
