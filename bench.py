@@ -427,6 +427,8 @@ def run_wallmodel(args, B, Solver, torch):
         nb = max(1, X.shape[0] // c["batch"])
         gen = torch.Generator(device=X.device).manual_seed(c["seed"] + p)
         perm = torch.randperm(X.shape[0], device=X.device, generator=gen)
+        log(f"pass {p}: data sums {float(X.double().sum()):.17g} {float(T.double().sum()):.17g} "
+            f"perm {perm[:4].tolist()} norm {float(xs.sum()):.17g} {float(xsd.sum()):.17g}")
         Xp, Tp = X[perm].contiguous(), T[perm].contiguous()
         l0 = net.train_step(Xp[:c["batch"]], Tp[:c["batch"]], lr0, want_loss=True)
         for it in range(c["iters"]):

@@ -5,7 +5,9 @@ oracle, element by element on the same seeded state.
 * mixed precision at 256 x 65 x 256 (the workload's x/z grid and parameters,
   a shorter y-grid): 256-point register transforms, 64-wide stencil tiles with
   neighbouring tiles in x, the stencil's multi-chunk y-march, three steps;
-  under both solve policies (default, and FP64 transforms and solves).
+  under both solve policies (default, and FP64 transforms and solves), under
+  every launch shape the autotuner can choose (one code at a time), and under
+  the shapes it chooses for the 256 x 193 x 256 benchmark grid.
   Tolerances: fields 1e-5 of each field's scale (velocities at least the wall
   speed), <u>(y) 1e-4 absolute and the wall shear 1e-4 relative (the stated
   accuracy of the mixed path);
@@ -44,26 +46,81 @@ def _scale(name, ref):
     return max(m, 1.0) if name in VEL else max(m, 1e-300)
 
 
-@pytest.mark.parametrize("policy", [0, 1])
-def test_mixed_at_the_workload_x_z_grid_matches_the_oracle(policy):
+MIXED_STEPS = 3
+# launch codes {stencil, CN, spectral y-solve, z-transform}: the built-in shapes, and
+# every other candidate the autotuner can pick, one code at a time
+DEFAULT_CFG = (64, 128, 64, 32)
+CANDIDATES = ((32, 64, 128, 16), (32, 64, 256), (16, 32, 128), (8, 16, 64))
+CFGS = [DEFAULT_CFG] + [tuple(v if j == i else DEFAULT_CFG[j] for j in range(4))
+                        for i, vals in enumerate(CANDIDATES) for v in vals if v != DEFAULT_CFG[i]]
+
+
+@pytest.fixture(scope="module")
+def mixed_reference():
+    """The oracle's three steps at 256 x 65 x 256 from the GPU's initial state
+    (computed once for every launch configuration)."""
     from paper_1701_02005_gb300 import binding as B
 
     g, prm, s, st0 = _setup(256, 65, 256, B.PNP_MIXED)
+    s.close()
+    return g, prm, o.step(g, prm, st0, C2["dt"], MIXED_STEPS)
+
+
+def _mixed_run(g, prm, ref, cfg=None, policy=0):
+    import ctypes as C
+
+    from paper_1701_02005_gb300 import binding as B
+    from paper_1701_02005_gb300.solver import Solver
+
+    s = Solver(g.nx, g.ny, g.nz, g.Lx, g.Lz, precision=B.PNP_MIXED, y_faces=g.yf)
+    s.set_params(prm.Re, prm.lam, prm.Sc, prm.V, prm.beta)
+    if cfg is not None:
+        B.check(B.pnp_set_launch_config(s.ctx, (C.c_int * 4)(*cfg)), "pnp_set_launch_config")
     s.set_policy(policy)
-    nsteps, dt = 3, C2["dt"]
-    s.step(nsteps, dt)
-    ref = o.step(g, prm, st0, dt, nsteps)
+    s.init_state(1, C2["seed"], C2["amp"])
+    s.step(MIXED_STEPS, C2["dt"])
     errs = {n: float(np.max(np.abs(s.get(n) - getattr(ref, n)))) / _scale(n, getattr(ref, n))
             for n in ("u", "v", "w", "cp", "cm", "Phi")}
     du = float(np.max(np.abs(s.mean_profile("u") - o.mean_profile(ref.u))))
     d, dr = s.diagnostics(), o.diagnostics(g, prm, ref)
     tau = max(abs(d["tau_bot"] - dr["tau_bot"]) / abs(dr["tau_bot"]),
               abs(d["tau_top"] - dr["tau_top"]) / abs(dr["tau_top"]))
-    print("mixed 256x65x256 (policy %d) vs oracle:" % policy, errs, "<u>", du, "tau", tau)
+    print("mixed 256x65x256 cfg", cfg, "policy", policy, "vs oracle:", errs, "<u>", du, "tau", tau)
     assert d["status"] == 0
-    assert all(e <= 1e-5 for e in errs.values()), errs
-    assert du <= 1e-4 and tau <= 1e-4, (du, tau)
+    assert all(e <= 1e-5 for e in errs.values()), (cfg, errs)
+    assert du <= 1e-4 and tau <= 1e-4, (cfg, du, tau)
     s.close()
+
+
+@pytest.mark.parametrize("policy", [0, 1])
+def test_mixed_at_the_workload_x_z_grid_matches_the_oracle(mixed_reference, policy):
+    g, prm, ref = mixed_reference
+    _mixed_run(g, prm, ref, None, policy)
+
+
+@pytest.mark.parametrize("cfg", CFGS, ids=lambda c: "cfg" + "-".join(map(str, c)))
+def test_mixed_under_every_launch_shape_the_autotuner_can_pick(mixed_reference, cfg):
+    g, prm, ref = mixed_reference
+    _mixed_run(g, prm, ref, cfg)
+
+
+def test_mixed_under_the_benchmarks_tuned_launch_shapes(mixed_reference):
+    """The autotuner on the 256 x 193 x 256 benchmark grid (the result is cached,
+    so that a benchmark run on the same machine takes the same shapes), its
+    choice applied to the parity grid."""
+    import math as m
+
+    from paper_1701_02005_gb300 import autotune
+    from paper_1701_02005_gb300 import binding as B
+    from paper_1701_02005_gb300.solver import Solver
+
+    s = Solver(256, 193, 256, C2["Lx"], C2["Lz"], stretch=C2["stretch"], precision=B.PNP_MIXED)
+    s.set_params(C2["Re"], C2["lam"], C2["Sc"], C2["V"], C2["beta"])
+    cfg, _ = autotune.tune(s, C2["dt"])
+    s.close()
+    assert m.isfinite(sum(cfg))
+    g, prm, ref = mixed_reference
+    _mixed_run(g, prm, ref, tuple(cfg))
 
 
 def test_fp64_at_the_full_workload_grid_matches_the_oracle_after_five_steps():
