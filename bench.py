@@ -430,6 +430,12 @@ def run_wallmodel(args, B, Solver, torch):
         log(f"pass {p}: data sums {float(X.double().sum()):.17g} {float(T.double().sum()):.17g} "
             f"perm {perm[:4].tolist()} norm {float(xs.sum()):.17g} {float(xsd.sum()):.17g}")
         Xp, Tp = X[perm].contiguous(), T[perm].contiguous()
+        if p == 0:
+            pr = net.params()
+            Yd = net.forward(Xp[:c["batch"]])
+            log(f"pass 0: params {float(np.sum(pr.astype(np.float64))):.17g} batch {float(Xp[:c['batch']].double().sum()):.17g} "
+                f"{float(Tp[:c['batch']].double().sum()):.17g} forward {float(Yd.double().sum()):.17g} "
+                f"ts {float(ts.sum()):.17g} tsd {float(tsd.sum()):.17g}")
         l0 = net.train_step(Xp[:c["batch"]], Tp[:c["batch"]], lr0, want_loss=True)
         for it in range(c["iters"]):
             b = it % nb

@@ -41,6 +41,12 @@ class Solver:
         base = self.ws.data_ptr()
         off = (-base) % 256
         self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        # the workspace is used on the library's stream from here on: order that stream
+        # after the torch work still queued on the memory the allocator handed out (a
+        # block freed a moment ago may still be read there), and keep torch from
+        # handing the block out again before the library's stream is done with it
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        self.ws.record_stream(self.stream)
         ctx = C.c_void_p()
         B.check(B.pnp_init_grid(C.byref(ctx), nx, ny, nz, float(Lx), float(Lz), float(stretch), precision,
                                 C.c_void_p(base + off), C.c_size_t(int(nbytes.value)),

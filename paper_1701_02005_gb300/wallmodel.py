@@ -27,6 +27,11 @@ class MLP:
         self.ws = torch.empty(int(nb.value) + 256, dtype=torch.uint8, device=self.device)
         off = (-self.ws.data_ptr()) % 256
         self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        # the network's stream clears and then owns the workspace: it must come after
+        # whatever torch still has queued on that memory (a block freed a moment ago,
+        # such as the temporary of a reduction still running, may be handed out here)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        self.ws.record_stream(self.stream)
         m = C.c_void_p()
         B.check(B.pnp_mlp_create(C.byref(m), int(max_batch), C.c_void_p(self.ws.data_ptr() + off),
                                  C.c_size_t(int(nb.value)), C.c_void_p(self.stream.cuda_stream), C.c_uint64(seed)),
