@@ -418,24 +418,10 @@ def run_wallmodel(args, B, Solver, torch):
             net.set_normalization(xs.cpu().numpy(), (1.0 / xsd).cpu().numpy(), ts.cpu().numpy(),
                                   (1.0 / tsd).cpu().numpy())
         lr0, lr1 = (2e-3, 5e-4) if p == 0 else (1e-3, 3e-4)
-        if net is not None and p > 0:
-            pr = net.params()
-            Yc = net.forward(X[:c["batch"]])
-            log(f"pass {p}: params finite {bool(np.isfinite(pr).all())}, forward finite "
-                f"{bool(torch.isfinite(Yc).all())}, max |x| normalised "
-                f"{float((((X[:c['batch']].double() - xs) / xsd).abs().max()))}")
         nb = max(1, X.shape[0] // c["batch"])
         gen = torch.Generator(device=X.device).manual_seed(c["seed"] + p)
         perm = torch.randperm(X.shape[0], device=X.device, generator=gen)
-        log(f"pass {p}: data sums {float(X.double().sum()):.17g} {float(T.double().sum()):.17g} "
-            f"perm {perm[:4].tolist()} norm {float(xs.sum()):.17g} {float(xsd.sum()):.17g}")
         Xp, Tp = X[perm].contiguous(), T[perm].contiguous()
-        if p == 0:
-            pr = net.params()
-            Yd = net.forward(Xp[:c["batch"]])
-            log(f"pass 0: params {float(np.sum(pr.astype(np.float64))):.17g} batch {float(Xp[:c['batch']].double().sum()):.17g} "
-                f"{float(Tp[:c['batch']].double().sum()):.17g} forward {float(Yd.double().sum()):.17g} "
-                f"ts {float(ts.sum()):.17g} tsd {float(tsd.sum()):.17g}")
         l0 = net.train_step(Xp[:c["batch"]], Tp[:c["batch"]], lr0, want_loss=True)
         for it in range(c["iters"]):
             b = it % nb
