@@ -336,6 +336,107 @@ def vortices_and_streaks(yf, nz, Lz, A=0.15, Bs=0.4, m=1):
     return u, v, w
 
 
+# The regime the wall model is for: a coarse grid that does not resolve the wall
+# layers.  Walls set in motion at t = 0 under fluid at rest (Stokes layers) on a fine
+# 32x65x32 grid (FP64, Re 500, lambda_D/h 0.05, V 2, tanh gamma 2) and on its 16x17x16
+# coarsening (every 4th y-face: the first coarse cell spans a third of the double
+# layer's thickness, the Stokes layer two cells early on); training as in the large
+# block (three windows, the later two coupled), judged on another seed.
+WMR = dict(nx=32, ny=65, nz=32, stretch=2.0, Re=500.0, lam=0.05, V=2.0, ry=4, rx=2, dt=0.002, steps=200, every=2,
+           iters=3000, passes=3, chunk=10, mode=2, potential_gain=0.3, flux_gain=0.3, seed_train=31, seed_judge=32,
+           amp=0.02, net_seed=33)
+
+
+def run_wallmodel_reduced(args, B, Solver, torch):
+    import numpy as np
+
+    from paper_1701_02005_gb300 import wallmodel as wm
+
+    c = dict(WMR)
+    yf = np.tanh(c["stretch"] * (np.arange(c["ny"]) * 2.0 / (c["ny"] - 1) - 1.0)) / math.tanh(c["stretch"])
+    yf[0], yf[-1] = -1.0, 1.0
+    yc = 0.5 * (yf[1:] + yf[:-1])
+    yfc = yf[::c["ry"]].copy()
+    ncx, ncz = c["nx"] // c["rx"], c["nz"] // c["rx"]
+
+    def mk(n, m, k, faces):
+        s_ = Solver(n, m, k, 2 * math.pi, math.pi, precision=B.PNP_FP64, y_faces=faces)
+        s_.set_params(c["Re"], c["lam"], 1.0, c["V"], 0.5)
+        return s_
+
+    def impulsive(s_, seed):   # the seeded, projected noise minus the Couette profile
+        s_.init_state(B.PNP_IC_PB, seed, c["amp"])
+        s_.set("u", s_.get("u") - yc[:, None, None])
+
+    def couple(s_):
+        wm.set_coupling(s_, c["mode"], 1.0, c["potential_gain"], c["flux_gain"])
+
+    sf, sc = mk(c["nx"], c["ny"], c["nz"], yf), mk(ncx, len(yfc), ncz, yfc)
+    t0 = time.perf_counter()
+    Xs, Ts, net, losses = [], [], None, []
+    for p in range(c["passes"]):
+        impulsive(sf, c["seed_train"])
+        wm.restrict(sf, sc)
+        couple(sc)
+        for n in range(c["steps"] // c["every"]):
+            Xs.append(wm.features(sc, 8))
+            Ts.append(wm.labels(sf, sc))
+            sf.step(c["every"], c["dt"])
+            if net is None:
+                sc.step(c["every"], c["dt"])
+            else:
+                wm.step_with_model(sc, net, c["every"], c["dt"])
+        wm.set_slip(sc, None, None)
+        wm.clear_edl(sc)
+        X, T = torch.cat(Xs), torch.cat(Ts)
+        if net is None:
+            xs, ts = X.double().mean(0), T.double().mean(0)
+            xsd = torch.maximum(X.double().std(0), 1e-2 * torch.clamp(xs.abs(), min=1e-2))
+            tsd = torch.maximum(T.double().std(0), 1e-2 * torch.clamp(ts.abs(), min=1e-4))
+            net = wm.MLP(c["steps"] // c["every"] * c["passes"] * 2 * ncz * ncx, seed=c["net_seed"])
+            net.set_normalization(xs.cpu().numpy(), (1.0 / xsd).cpu().numpy(), ts.cpu().numpy(),
+                                  (1.0 / tsd).cpu().numpy())
+        lr0, lr1 = (2e-3, 5e-4) if p == 0 else (1e-3, 3e-4)
+        l0 = net.train_step(X, T, lr0, want_loss=True)
+        for it in range(c["iters"]):
+            net.train_step(X, T, lr0 if it < c["iters"] // 2 else lr1)
+        losses.append([l0, net.train_step(X, T, lr1, want_loss=True)])
+    train_s = time.perf_counter() - t0
+    sm = mk(ncx, len(yfc), ncz, yfc)
+    impulsive(sf, c["seed_judge"])
+    wm.restrict(sf, sc)
+    wm.restrict(sf, sm)
+    couple(sm)
+    N0 = sm.diagnostics()["n_plus"]
+    cf = {"fine": [], "plain": [], "coupled": []}
+    phi = {"plain": [], "coupled": []}
+    for n in range(c["steps"] // c["chunk"]):
+        sf.step(c["chunk"], c["dt"])
+        sc.step(c["chunk"], c["dt"])
+        wm.step_with_model(sm, net, c["chunk"], c["dt"])
+        for k, s_ in (("fine", sf), ("plain", sc), ("coupled", sm)):
+            cf[k].append(s_.diagnostics()["cf"])
+        pf = wm.labels(sf, sc)[:, 2]
+        for k, s_ in (("plain", sc), ("coupled", sm)):
+            phi[k].append(float((wm.features(s_, 8)[:, 32] - pf).abs().mean() / pf.abs().mean()))
+    f = np.array(cf["fine"])
+    err = lambda a: float(np.mean(np.abs(np.array(a) - f) / f))
+    out = {"workload": f"fine {c['nx']}x{c['ny']}x{c['nz']} (FP64) -> coarse {ncx}x{len(yfc)}x{ncz}, Re {c['Re']:g}, "
+                       f"lambda_D/h {c['lam']}, V {c['V']:g}, dt {c['dt']}, walls set in motion at t = 0, "
+                       f"{c['passes']} training runs of {c['steps']} steps (seed {c['seed_train']}), judged on seed "
+                       f"{c['seed_judge']}",
+           "coupling": {k: c[k] for k in ("mode", "potential_gain", "flux_gain")},
+           "training": {"rows": int(X.shape[0]), "loss_first_last": losses, "seconds": train_s},
+           "cf_err": {k: err(cf[k]) for k in ("plain", "coupled")},
+           "first_cell_phi_err": {k: float(np.mean(v)) for k, v in phi.items()},
+           "ion_number_drift_coupled": abs(sm.diagnostics()["n_plus"] - N0) / N0,
+           "mlp_status": net.status()}
+    for s_ in (sf, sc, sm):
+        s_.close()
+    net.close()
+    return out
+
+
 def run_wallmodel(args, B, Solver, torch):
     import numpy as np
 
@@ -350,8 +451,9 @@ def run_wallmodel(args, B, Solver, torch):
     yf[0], yf[-1] = -1.0, 1.0
     mk = lambda n, m, k, faces: Solver(n, m, k, WL["Lx"], WL["Lz"], precision=B.PNP_MIXED, y_faces=faces)
     fine = mk(nx, ny, nz, yf)
-    # turbulence first, at V = 0 and the advective dt (about 100 time units), then the
-    # walls charged to V and the double layers formed over layer_steps at the V-limited dt
+    # turbulence first, at V = 0 with the adaptive dt (at most the advective one; about
+    # 20 time units), then the walls charged to V and the double layers formed over
+    # layer_steps at the V-limited dt
     dt0 = stable_dt(nx, ny, WL["Re"], WL["lam"], 0.0, st)[0]
     fine.set_params(WL["Re"], WL["lam"], WL["Sc"], 0.0, WL["beta"])
     fine.init_state(B.PNP_IC_PB, c["seed"], c["amp"])
@@ -1075,6 +1177,10 @@ def run_ours(args):
             wallmodel = run_wallmodel(args, B, Solver, torch)
         except Exception as exc:  # noqa: BLE001
             wallmodel = {"error": f"{type(exc).__name__}: {exc}"}
+        try:
+            wallmodel["reduced"] = run_wallmodel_reduced(args, B, Solver, torch)
+        except Exception as exc:  # noqa: BLE001
+            wallmodel["reduced"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1177,7 +1283,9 @@ def main():
         from paper_1701_02005_gb300 import binding as B
         from paper_1701_02005_gb300.solver import Solver
 
-        print(json.dumps({"wallmodel": run_wallmodel(args, B, Solver, torch)}), flush=True)
+        w = run_wallmodel(args, B, Solver, torch)
+        w["reduced"] = run_wallmodel_reduced(args, B, Solver, torch)
+        print(json.dumps({"wallmodel": w}), flush=True)
         return 0
     return run_ours(args)
 
