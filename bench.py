@@ -48,6 +48,17 @@ def cells(wl=WL):
 # dram__bytes_read.sum + dram__bytes_write.sum per launch, turbulent Couette
 # 256x193x256, from the one-pass ncu capture summarised under profiles/
 # (shape = the stencil's tuned launch code the capture ran with)
+# DRAM bytes (read + write) of all 45 launches of one step of that workload, from the
+# one-pass ncu capture summarised under profiles/ (cold cache: ncu flushes L2 before
+# each kernel), per cell-step, for the launch shapes the capture ran with
+STEP_NCU = {}
+
+# Algorithmic bytes per cell-step of the whole step (every input read once, every
+# output written once per phase; the phases the method's synchronisation points
+# separate): 268 B per substage in the mixed path, 352 in FP64
+STEP_BYTES = {"mixed": 804.0, "fp64": 1056.0}
+NOMINAL_HBM_GBS = 7900.0
+
 NCU_TRAFFIC = {
     # mean of three consecutive launches (one per RK3 substage) of the stencil with
     # the fused CN forward elimination, launch code 0 / 64
@@ -1073,6 +1084,22 @@ def run_ours(args):
         roof["traffic"] = nt["bytes"]
         roof["traffic_kernel"] = nt["kernel"]
 
+    # the whole step against the HBM roofline: algorithmic bytes and, where a capture of
+    # this workload and launch shape is committed, the bytes ncu counted
+    step_roof = {"algorithmic_bytes_per_cell_step": STEP_BYTES[pname],
+                 "achieved_gbs": STEP_BYTES[pname] * n_cells * K / t / 1e9}
+    step_roof["frac_of_measured"] = step_roof["achieved_gbs"] / hbm_peak
+    step_roof["frac_of_nominal"] = step_roof["achieved_gbs"] / NOMINAL_HBM_GBS
+    sn = STEP_NCU.get(pname)
+    if sn and sn["cells"] == n_cells and (sn["shape"] is None or (launch_cfg and list(launch_cfg) == sn["shape"])):
+        g_ncu = sn["bytes_per_cell_step"] * n_cells * K / t / 1e9
+        step_roof.update({"ncu_bytes_per_cell_step": sn["bytes_per_cell_step"], "ncu_gbs": g_ncu,
+                          "ncu_frac_of_measured": g_ncu / hbm_peak, "ncu_frac_of_nominal": g_ncu / NOMINAL_HBM_GBS})
+    else:
+        step_roof.update({"ncu_bytes_per_cell_step": None, "ncu_gbs": None, "ncu_frac_of_measured": None,
+                          "ncu_frac_of_nominal": None})
+    step_roof["peaks"] = {"measured_gbs": hbm_peak, "nominal_gbs": NOMINAL_HBM_GBS}
+
     # the FP64 path on the same workload, and the mixed-vs-FP64 error from one initial state
     cmp = None
     if prec == B.PNP_MIXED and not args.no_fp64_compare:
@@ -1194,6 +1221,7 @@ def run_ours(args):
                    "precision": pname, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (working set ~2 GB vs 129 MB), no flush"},
         "roofline": roof,
+        "step_roofline": step_roof,
         "mixed_vs_fp64": cmp,
         "ensemble": ensemble,
         "large_case": large,
