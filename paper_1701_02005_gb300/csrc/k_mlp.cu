@@ -54,17 +54,6 @@ __global__ void k_mlp_norm_in(const float* __restrict__ X, int B, const float* _
   out[t] = (X[t] - shift[f]) * scale[f];
 }
 
-// Physical output Y = y_n / scale + shift, with y_n clipped to +-kClip: the
-// network is not trusted beyond kClip standard deviations of its training labels.
-constexpr float kClip = 6.0f;
-__global__ void k_mlp_denorm_out(const float* __restrict__ yn, int B, const float* __restrict__ shift,
-                                 const float* __restrict__ scale, float* __restrict__ Y) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)B * kMlpOut) return;
-  const int f = (int)(t % kMlpOut);
-  Y[t] = fminf(fmaxf(yn[t], -kClip), kClip) / scale[f] + shift[f];
-}
-
 // dz of the output layer for L = mean((y_n - t_n)^2), with per-block partial losses.
 __global__ void __launch_bounds__(256) k_mlp_loss(const float* __restrict__ yn, const float* __restrict__ T, int B,
                                                   const float* __restrict__ shift, const float* __restrict__ scale,
@@ -116,6 +105,9 @@ cudaError_t mlp_sync_bf16(const MlpBufs& b, size_t nparam, cudaStream_t s) {
 }
 
 cudaError_t mlp_forward(const MlpBufs& b, const float* X, int B, float* Y, cudaStream_t s) {
+  // outputs only: the fused kernel; the layer-by-layer path keeps the activations
+  // the backward pass needs
+  if (Y) return mlp_infer_tc(X, B, b.wimg, b.param, b.in_shift, b.in_scale, b.out_shift, b.out_scale, Y, b.err, s);
   const MlpDims d = mlp_dims();
   const MlpImg im = mlp_images();
   const size_t ni = (size_t)B * kMlpIn;
@@ -126,10 +118,6 @@ cudaError_t mlp_forward(const MlpBufs& b, const float* X, int B, float* Y, cudaS
     e = mlp_fwd_layer_tc(b.act[l], d.in[l], l > 0, b.wimg + im.fwd[l], b.param + d.boff[l], d.out[l], B,
                          b.act[l + 1], b.err, s);
     if (e != cudaSuccess) return e;
-  }
-  if (Y) {
-    const size_t no = (size_t)B * kMlpOut;
-    k_mlp_denorm_out<<<(unsigned)((no + 255) / 256), 256, 0, s>>>(b.act[kMlpLayers], B, b.out_shift, b.out_scale, Y);
   }
   return cudaGetLastError();
 }

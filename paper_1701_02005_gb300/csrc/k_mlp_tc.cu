@@ -22,6 +22,7 @@
 // (bounded) for its MMAs, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "pnp_common.cuh"
@@ -478,6 +479,123 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_wgrad_tc(const float* __rest
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
+// The whole network for inference (the outputs only), one persistent CTA per SM
+// looping over 128-row tiles: the five forward weight images stay in shared
+// memory for the kernel's life, and each layer's accumulators go from TMEM
+// through registers (bias, GELU) straight back into the shared-memory A tile of
+// the next layer, so that nothing between the input rows and the five outputs
+// touches global memory.  Same arithmetic as the layer-by-layer path: the
+// input scaled in FP32, BF16 operands, FP32 accumulation, z + bias in FP32,
+// GELU in FP32 rounded to BF16, the output clipped to +-6 standard deviations
+// and scaled back.
+constexpr float kInferClip = 6.0f;
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_infer_tc(const float* __restrict__ X, int B,
+                                                                const __nv_bfloat16* __restrict__ wimg, MlpImg im,
+                                                                MlpDims d, const float* __restrict__ param,
+                                                                const float* __restrict__ in_shift,
+                                                                const float* __restrict__ in_scale,
+                                                                const float* __restrict__ out_shift,
+                                                                const float* __restrict__ out_scale,
+                                                                float* __restrict__ Y, int* err) {
+  extern __shared__ __align__(128) unsigned char tc_raw[];
+  __nv_bfloat16* W[kMlpLayers];
+  size_t off = 0;
+  for (int l = 0; l < kMlpLayers; ++l) {
+    W[l] = reinterpret_cast<__nv_bfloat16*>(tc_raw + off);
+    off += (size_t)((d.out[l] + 15) & ~15) * ((d.in[l] + 15) & ~15) * 2;
+  }
+  __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(tc_raw + off);   // [128][128] at most
+  off += (size_t)kTcRows * kMlpHidden * 2;
+  float* nsh = reinterpret_cast<float*>(tc_raw + off);                 // input shift, then scale
+  off += 2 * kMlpIn * sizeof(float);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(tc_raw + ((off + 15) & ~(size_t)15));
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, grp = warp & 3, half = warp >> 2;
+  if (warp == 0) tmem_alloc(slot, kMlpHidden);
+  if (tid == 0) mbar_init1(bar);
+  for (int l = 0; l < kMlpLayers; ++l) {
+    const int Kp = (d.in[l] + 15) & ~15, Np = (d.out[l] + 15) & ~15;
+    copy_image(W[l], wimg + im.fwd[l], Np * Kp / 8);
+  }
+  for (int k = tid; k < kMlpIn; k += kTcThreads) {
+    nsh[k] = in_shift[k];
+    nsh[kMlpIn + k] = in_scale[k];
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *slot;
+  const uint32_t lane = tmem + ((uint32_t)(32 * grp) << 16);
+  const int r = 32 * grp + (tid & 31);   // this thread's accumulator row (TMEM lane)
+  const int ntiles = (B + kTcRows - 1) / kTcRows;
+  unsigned phase = 0;
+  bool ok = true;
+  unsigned char* a = reinterpret_cast<unsigned char*>(A);
+  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int b0 = tile * kTcRows, rows = min(kTcRows, B - b0);
+    {   // the scaled input rows, BF16, K padded from 40 to 48
+      const float4* s4 = reinterpret_cast<const float4*>(X + (size_t)b0 * kMlpIn);
+      for (int q = tid; q < kTcRows * kMlpIn / 4; q += kTcThreads) {
+        const int e = 4 * q, rr = e / kMlpIn, k = e - rr * kMlpIn;
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (rr < rows) {
+          x = __ldg(s4 + q);
+          x.x = (x.x - nsh[k]) * nsh[kMlpIn + k];
+          x.y = (x.y - nsh[k + 1]) * nsh[kMlpIn + k + 1];
+          x.z = (x.z - nsh[k + 2]) * nsh[kMlpIn + k + 2];
+          x.w = (x.w - nsh[k + 3]) * nsh[kMlpIn + k + 3];
+        }
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(x.x, x.y), hi = __floats2bfloat162_rn(x.z, x.w);
+        uint2 u;
+        u.x = *reinterpret_cast<const uint32_t*>(&lo);
+        u.y = *reinterpret_cast<const uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(a + canon(rr, k, kTcRows)) = u;
+      }
+      for (int rr = tid; rr < kTcRows; rr += kTcThreads)
+        *reinterpret_cast<uint4*>(a + canon(rr, kMlpIn, kTcRows)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int l = 0; l < kMlpLayers && ok; ++l) {
+      const int Kp = (d.in[l] + 15) & ~15, Np = (d.out[l] + 15) & ~15;
+      ok = mma_tiles(tmem, A, W[l], Np, Kp, false, bar, phase);
+      phase ^= 1u;
+      if (!ok) break;
+      const float* bias = param + d.boff[l];
+      if (l + 1 < kMlpLayers) {
+        // next layer's A: BF16(GELU(z + bias)), 16 columns per load, written as two
+        // 16-byte runs of the core-matrix rows (the MMA that read A has completed)
+        for (int c0 = 16 * half; c0 < Np; c0 += 32) {
+          float v[16];
+          tmem_ld16(lane + c0, v);
+          uint32_t pk[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu_tc(v[2 * i] + bias[c0 + 2 * i]),
+                                                            gelu_tc(v[2 * i + 1] + bias[c0 + 2 * i + 1]));
+            pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
+          }
+          *reinterpret_cast<uint4*>(a + canon(r, c0, kTcRows)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          *reinterpret_cast<uint4*>(a + canon(r, c0 + 8, kTcRows)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+      } else if (half == 0) {
+        float v[16];
+        tmem_ld16(lane, v);
+        if (r < rows) {
+#pragma unroll
+          for (int n = 0; n < kMlpOut; ++n) {
+            const float yn = fminf(fmaxf(v[n] + bias[n], -kInferClip), kInferClip);
+            Y[(size_t)(b0 + r) * kMlpOut + n] = yn / out_scale[n] + out_shift[n];
+          }
+        }
+      }
+    }
+  }
+  if (!ok) tc_timeout(err, bar, phase ^ 1u);
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kMlpHidden);
+}
+
 // Weight images: for every layer, the BF16 weights in the shared-memory layout
 // of the forward GEMM's B tile (rows n < Np, columns k < Kp) and of the data
 // gradient's (rows k < Kp, columns n < Np), zero in the padding.
@@ -560,6 +678,28 @@ cudaError_t mlp_bwd_data_tc(const float* dz, int N, const __nv_bfloat16* WimgT, 
   const size_t smem = tc_smem_bytes(Np, Kq, (size_t)kTcRows * (Kq + 4) * sizeof(float));
   return tc_launch(k_mlp_bwd_data_tc, (unsigned)((B + kTcRows - 1) / kTcRows), smem, tmem_cols_host(Kq), s, dz, N,
                    WimgT, K, B, zprev, out, err);
+}
+
+cudaError_t mlp_infer_tc(const float* X, int B, const __nv_bfloat16* wimg, const float* param,
+                         const float* in_shift, const float* in_scale, const float* out_shift, const float* out_scale,
+                         float* Y, int* err, cudaStream_t s) {
+  if (B < 1) return cudaSuccess;
+  const MlpDims d = mlp_dims();
+  const MlpImg im = mlp_images();
+  size_t smem = 0;
+  for (int l = 0; l < kMlpLayers; ++l) smem += (size_t)((d.out[l] + 15) & ~15) * ((d.in[l] + 15) & ~15) * 2;
+  smem += (size_t)kTcRows * kMlpHidden * 2 + 2 * kMlpIn * sizeof(float);
+  smem = ((smem + 15) & ~(size_t)15) + 16;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int ntiles = (B + kTcRows - 1) / kTcRows;
+  const unsigned grid = (unsigned)std::min(ntiles, std::max(sms, 1));
+  k_mlp_infer_tc<<<grid, kTcThreads, smem, s>>>(X, B, wimg, im, d, param, in_shift, in_scale, out_shift, out_scale, Y,
+                                                err);
+  return cudaGetLastError();
 }
 
 cudaError_t mlp_wgrad_tc(const float* dz, int N, const float* in, int K, bool act_in, int B, int rows_per_block,

@@ -105,6 +105,11 @@ cudaError_t mlp_bwd_data_tc(const float* dz, int N, const __nv_bfloat16* WimgT, 
 cudaError_t mlp_wgrad_tc(const float* dz, int N, const float* in, int K, bool act_in, int B, int rows_per_block,
                          int nblk, float* partial, int* err, cudaStream_t s);
 
+// The whole network in one persistent kernel, outputs only (inference).
+cudaError_t mlp_infer_tc(const float* X, int B, const __nv_bfloat16* wimg, const float* param,
+                         const float* in_shift, const float* in_scale, const float* out_shift, const float* out_scale,
+                         float* Y, int* err, cudaStream_t s);
+
 cudaError_t mlp_sync_bf16(const MlpBufs& b, size_t nparam, cudaStream_t s);
 cudaError_t mlp_forward(const MlpBufs& b, const float* X, int B, float* Y, cudaStream_t s);
 cudaError_t mlp_backward(const MlpBufs& b, const float* T, int B, int max_partial, cudaStream_t s);

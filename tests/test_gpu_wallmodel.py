@@ -243,3 +243,33 @@ def test_wall_model_gains_over_coarse_solver():
     assert r["err_phi_coupled"] < 0.1 * r["err_phi_plain"], r
     for n0, n1 in zip(r["ions_start"], r["ions_coupled"]):
         assert abs(n1 - n0) <= 1e-12 * n0, r
+
+
+def test_fused_inference_matches_the_layer_by_layer_forward():
+    """The outputs-only kernel (all layers in one launch, activations kept on chip)
+    against the layer-by-layer forward the gradient runs, over several tiles and a
+    ragged last tile: the loss of the fused outputs equals the gradient call's loss
+    (same BF16 operands, same FP32 accumulation; nothing near the 6-sigma clip)."""
+    import torch
+
+    from paper_1701_02005_gb300.wallmodel import MLP
+
+    rows = 5 * 128 + 37
+    net = MLP(rows, seed=11)
+    norm = _norm(12)
+    net.set_normalization(*norm)
+    r = seeded.rng(13)
+    X = r.standard_normal((rows, 40)).astype(np.float32)
+    T = r.standard_normal((rows, 5)).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    Y = net.forward(Xd).cpu().numpy().astype(np.float64)
+    yn = (Y - norm[2]) * norm[3]
+    assert np.max(np.abs(yn)) < 5.0
+    loss_fused = float(np.mean((yn - (T - norm[2]) * norm[3]) ** 2))
+    _, loss = net.gradient(Xd, Td)
+    assert abs(loss_fused - loss) <= 1e-5 * loss, (loss_fused, loss)
+    # the parity of the fused outputs with the oracle, row by row
+    Yr, _ = w.forward(net.params(), X, norm, bf16=True, bf16_act=True)
+    assert np.max(np.abs(Y - Yr)) <= 2e-3 * np.max(np.abs(Yr))
+    assert net.status() == 0
+    net.close()
