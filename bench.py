@@ -126,11 +126,12 @@ def stable_dt(nx, ny, Re, lam, V, stretch, Lx=2 * math.pi):
 
 
 def run_mlp(args, B, torch):
-    """Throughput of the wall model's network on its tcgen05 kernels: forward and
-    training step on 65,536 rows (the training batch; a coupled step of the
-    128x49x128 grid feeds 32,768).  The layers are 40 -> 128 x 4 -> 5: at 128
-    outputs a layer does 2 x 128 FLOPs per FP32 value it reads or writes, so the
-    forward is bound by HBM, not by the tensor cores."""
+    """Throughput of the wall model's network on its tcgen05 kernels: inference
+    (the fused kernel: 180 B of input and output per row for 110 kFLOP, so bound by
+    the tensor cores and the on-chip epilogues, not by HBM) and the training step
+    (layer by layer: every z is stored for the backward pass, 64 FLOPs per byte at
+    the 128-wide layers, so HBM-bound) on 65,536 rows (the training batch; a
+    coupled step of the 128x49x128 grid feeds 32,768)."""
     import ctypes as C
 
     import numpy as np
@@ -165,9 +166,11 @@ def run_mlp(args, B, torch):
     t_f, t_t = timed(fwd), timed(trn)
     macs = 40 * 128 + 3 * 128 * 128 + 128 * 5
     flops_f = 2.0 * rows * macs
-    # FP32 values read + written per row by the forward launches: input scaling 40 + 40,
-    # layers (40 + 128) + 3 (128 + 128) + (128 + 5), output scaling 5 + 5
-    bytes_f = 4.0 * rows * (80 + 168 + 3 * 256 + 133 + 10)
+    # the fused inference kernel reads each input row and writes its outputs, nothing else
+    bytes_f = 4.0 * rows * (40 + 5)
+    # the training step's forward stores every layer's z for the backward pass: FP32 values
+    # read + written per row: input scaling 40 + 40, layers (40 + 128) + 3 (128 + 128) + (128 + 5)
+    bytes_train_fwd = 4.0 * rows * (80 + 168 + 3 * 256 + 133)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -178,9 +181,12 @@ def run_mlp(args, B, torch):
     out = {"rows": rows, "forward_us": t_f * 1e6, "train_step_us": t_t * 1e6,
            "forward_tflops": flops_f / t_f / 1e12, "train_step_tflops": 3 * flops_f / t_t / 1e12,
            "forward_gbs": bytes_f / t_f / 1e9,
-           "roofline_forward": {"bound": "hbm", "achieved": bytes_f / t_f / 1e9, "peak": hbm, "unit": "GB/s",
-                                "frac": bytes_f / t_f / 1e9 / hbm, "per_unit": "4636 B per row x 65536 rows"},
-           "tensor_frac_of_bf16_peak": flops_f / t_f / 1e12 / bf16, "status": net.status()}
+           "roofline_forward": {"bound": "tensor", "achieved": flops_f / t_f / 1e12, "peak": bf16,
+                                "unit": "TFLOP/s", "frac": flops_f / t_f / 1e12 / bf16,
+                                "per_unit": f"2 x {macs} FLOPs per row x {rows} rows (180 B per row: "
+                                            f"{bytes_f / t_f / 1e9:.0f} GB/s, {bytes_f / t_f / 1e9 / hbm:.3f} of HBM)",
+                                "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)"},
+           "train_step_forward_bytes_per_row": bytes_train_fwd / rows, "status": net.status()}
     net.close()
     return out
 

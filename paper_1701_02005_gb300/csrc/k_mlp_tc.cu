@@ -489,8 +489,9 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_wgrad_tc(const float* __rest
 // GELU in FP32 rounded to BF16, the output clipped to +-6 standard deviations
 // and scaled back.
 constexpr float kInferClip = 6.0f;
+constexpr int kInferThreads = 512;   // 16 warps: four share each quarter of the TMEM lanes
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_infer_tc(const float* __restrict__ X, int B,
+__global__ void __launch_bounds__(kInferThreads, 1) k_mlp_infer_tc(const float* __restrict__ X, int B,
                                                                 const __nv_bfloat16* __restrict__ wimg, MlpImg im,
                                                                 MlpDims d, const float* __restrict__ param,
                                                                 const float* __restrict__ in_shift,
@@ -511,14 +512,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_infer_tc(const float* __r
   off += 2 * kMlpIn * sizeof(float);
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(tc_raw + ((off + 15) & ~(size_t)15));
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
-  const int tid = threadIdx.x, warp = tid >> 5, grp = warp & 3, half = warp >> 2;
+  const int tid = threadIdx.x, warp = tid >> 5, grp = warp & 3, quarter = warp >> 2;
   if (warp == 0) tmem_alloc(slot, kMlpHidden);
   if (tid == 0) mbar_init1(bar);
   for (int l = 0; l < kMlpLayers; ++l) {
     const int Kp = (d.in[l] + 15) & ~15, Np = (d.out[l] + 15) & ~15;
-    copy_image(W[l], wimg + im.fwd[l], Np * Kp / 8);
+    const uint4* src = reinterpret_cast<const uint4*>(wimg + im.fwd[l]);
+    uint4* dst = reinterpret_cast<uint4*>(W[l]);
+    for (int i = tid; i < Np * Kp / 8; i += kInferThreads) dst[i] = __ldg(src + i);
   }
-  for (int k = tid; k < kMlpIn; k += kTcThreads) {
+  for (int k = tid; k < kMlpIn; k += kInferThreads) {
     nsh[k] = in_shift[k];
     nsh[kMlpIn + k] = in_scale[k];
   }
@@ -536,7 +539,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_infer_tc(const float* __r
     const int b0 = tile * kTcRows, rows = min(kTcRows, B - b0);
     {   // the scaled input rows, BF16, K padded from 40 to 48
       const float4* s4 = reinterpret_cast<const float4*>(X + (size_t)b0 * kMlpIn);
-      for (int q = tid; q < kTcRows * kMlpIn / 4; q += kTcThreads) {
+      for (int q = tid; q < kTcRows * kMlpIn / 4; q += kInferThreads) {
         const int e = 4 * q, rr = e / kMlpIn, k = e - rr * kMlpIn;
         float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
         if (rr < rows) {
@@ -552,7 +555,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_infer_tc(const float* __r
         u.y = *reinterpret_cast<const uint32_t*>(&hi);
         *reinterpret_cast<uint2*>(a + canon(rr, k, kTcRows)) = u;
       }
-      for (int rr = tid; rr < kTcRows; rr += kTcThreads)
+      for (int rr = tid; rr < kTcRows; rr += kInferThreads)
         *reinterpret_cast<uint4*>(a + canon(rr, kMlpIn, kTcRows)) = make_uint4(0u, 0u, 0u, 0u);
     }
     for (int l = 0; l < kMlpLayers && ok; ++l) {
@@ -562,9 +565,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_infer_tc(const float* __r
       if (!ok) break;
       const float* bias = param + d.boff[l];
       if (l + 1 < kMlpLayers) {
-        // next layer's A: BF16(GELU(z + bias)), 16 columns per load, written as two
-        // 16-byte runs of the core-matrix rows (the MMA that read A has completed)
-        for (int c0 = 16 * half; c0 < Np; c0 += 32) {
+        // next layer's A: BF16(GELU(z + bias)), 16 columns per load (the four warps on
+        // a lane quarter take every fourth group), written as two 16-byte runs of the
+        // core-matrix rows (the MMA that read A has completed)
+        for (int c0 = 16 * quarter; c0 < Np; c0 += 64) {
           float v[16];
           tmem_ld16(lane + c0, v);
           uint32_t pk[8];
@@ -577,7 +581,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_infer_tc(const float* __r
           *reinterpret_cast<uint4*>(a + canon(r, c0, kTcRows)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
           *reinterpret_cast<uint4*>(a + canon(r, c0 + 8, kTcRows)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
         }
-      } else if (half == 0) {
+      } else if (quarter == 0) {
         float v[16];
         tmem_ld16(lane, v);
         if (r < rows) {
@@ -697,8 +701,8 @@ cudaError_t mlp_infer_tc(const float* X, int B, const __nv_bfloat16* wimg, const
   if (e != cudaSuccess) return e;
   const int ntiles = (B + kTcRows - 1) / kTcRows;
   const unsigned grid = (unsigned)std::min(ntiles, std::max(sms, 1));
-  k_mlp_infer_tc<<<grid, kTcThreads, smem, s>>>(X, B, wimg, im, d, param, in_shift, in_scale, out_shift, out_scale, Y,
-                                                err);
+  k_mlp_infer_tc<<<grid, kInferThreads, smem, s>>>(X, B, wimg, im, d, param, in_shift, in_scale, out_shift, out_scale,
+                                                   Y, err);
   return cudaGetLastError();
 }
 
