@@ -510,6 +510,8 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_mlp_infer_tc(const float* 
   off += (size_t)kTcRows * kMlpHidden * 2;
   float* nsh = reinterpret_cast<float*>(tc_raw + off);                 // input shift, then scale
   off += 2 * kMlpIn * sizeof(float);
+  float* sbias = reinterpret_cast<float*>(tc_raw + off);               // the five layers' biases
+  off += (size_t)(4 * kMlpHidden + kMlpOut) * sizeof(float);
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(tc_raw + ((off + 15) & ~(size_t)15));
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, grp = warp & 3, quarter = warp >> 2;
@@ -525,6 +527,8 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_mlp_infer_tc(const float* 
     nsh[k] = in_shift[k];
     nsh[kMlpIn + k] = in_scale[k];
   }
+  for (int l = 0, o = 0; l < kMlpLayers; o += d.out[l], ++l)
+    for (int n = tid; n < d.out[l]; n += kInferThreads) sbias[o + n] = param[d.boff[l] + n];
   fence_before();
   __syncthreads();
   fence_after();
@@ -563,7 +567,7 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_mlp_infer_tc(const float* 
       ok = mma_tiles(tmem, A, W[l], Np, Kp, false, bar, phase);
       phase ^= 1u;
       if (!ok) break;
-      const float* bias = param + d.boff[l];
+      const float* bias = sbias + l * kMlpHidden;
       if (l + 1 < kMlpLayers) {
         // next layer's A: BF16(GELU(z + bias)), 16 columns per load (the four warps on
         // a lane quarter take every fourth group), written as two 16-byte runs of the
@@ -692,7 +696,7 @@ cudaError_t mlp_infer_tc(const float* X, int B, const __nv_bfloat16* wimg, const
   const MlpImg im = mlp_images();
   size_t smem = 0;
   for (int l = 0; l < kMlpLayers; ++l) smem += (size_t)((d.out[l] + 15) & ~15) * ((d.in[l] + 15) & ~15) * 2;
-  smem += (size_t)kTcRows * kMlpHidden * 2 + 2 * kMlpIn * sizeof(float);
+  smem += (size_t)kTcRows * kMlpHidden * 2 + (2 * kMlpIn + 4 * kMlpHidden + kMlpOut) * sizeof(float);
   smem = ((smem + 15) & ~(size_t)15) + 16;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
