@@ -275,3 +275,25 @@ def test_fused_forward_elimination_matches_the_unfused_solve(shape):
         r = getattr(ref, n)
         scale = max(np.max(np.abs(r)), 1.0 if n in ("u", "v", "w") else 1e-300)
         assert np.max(np.abs(out[1][n] - r)) <= 1e-5 * scale, n
+
+
+@pytest.mark.parametrize("shape", [(1024, 9, 32), (32, 9, 512), (512, 9, 64), (128, 9, 256)])
+def test_mixed_steps_at_every_register_transform_length(shape):
+    """Two mixed steps against the oracle on flat grids whose x- and z-extents
+    reach every FP32 register-transform length (Nx/2 = 512, 16, 256, 64;
+    Nz = 32, 512, 64, 256), fields to 1e-5 of their scale."""
+    nx, ny, nz = shape
+    g = o.Grid(nx, ny, nz, 2 * math.pi, math.pi, stretch=1.5)
+    prm = o.Params(Re=300.0, lam=0.1, Sc=1.0, V=2.0, beta=0.5)
+    st0 = o.initial_state(g, prm, o.IC_PB, seed=17, amp=0.05)
+    s = _mixed(g, prm)
+    s.set_state(st0)
+    s.step(2, 0.005)
+    ref = o.step(g, prm, st0, 0.005, 2)
+    for n in ("u", "v", "w", "cp", "cm", "Phi"):
+        r = getattr(ref, n)
+        scale = max(float(np.max(np.abs(r))), 1.0) if n in ("u", "v", "w") else float(np.max(np.abs(r)))
+        e = float(np.max(np.abs(s.get(n) - r))) / scale
+        assert e <= 1e-5, (shape, n, e)
+    assert s.diagnostics()["status"] == 0
+    s.close()

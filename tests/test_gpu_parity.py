@@ -42,7 +42,10 @@ def _assert_state(s, ref, tol=TOL, names=FIELDS):
     return errs
 
 
-@pytest.mark.parametrize("shape", [(8, 9, 4), (32, 17, 16), (64, 33, 32)])
+# every register-transform length in x (Nx/2 = 16 .. 512) and z (16 .. 512) in FP64,
+# and the shared-memory transforms of the smallest grids
+@pytest.mark.parametrize("shape", [(8, 9, 4), (32, 17, 16), (64, 33, 32), (128, 5, 64), (256, 5, 128),
+                                   (512, 5, 256), (1024, 5, 512)])
 @pytest.mark.parametrize("bc", ["neumann", "dirichlet"])
 def test_poisson_parity(shape, bc):
     from paper_1701_02005_gb300 import binding as B
