@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Fields<TV> f, Geo
 // could reach the running maximum, which gives the same maximum; the minimum
 // concentration is FP32; a value is counted non-finite when any input read for
 // it is.  Nx and Nz are powers of two.
-__global__ void __launch_bounds__(kDiagThreads, 3) k_diag_partial_mixed(Fields<float> f, Shadows sh,
+__global__ void __launch_bounds__(kDiagThreads, 2) k_diag_partial_mixed(Fields<float> f, Shadows sh,
                                                                         const float* __restrict__ cref_p,
                                                                         const float* __restrict__ cref_m,
                                                                         const float* __restrict__ dPref,
@@ -202,12 +202,17 @@ __global__ void __launch_bounds__(kDiagThreads, 3) k_diag_partial_mixed(Fields<f
   const size_t P = (size_t)nz * nx;
   const int rows = g.nyc * nz, per = (rows + gridDim.x - 1) / gridDim.x;
   const int r0 = blockIdx.x * per, r1 = min(rows, r0 + per);
+  // two cells per thread (paired 8-byte loads); the block's threads cover
+  // `rpp` rows at a time, each thread keeping to one row in rpp
+  const int tpr = min((int)blockDim.x, nx / 2), rpp = (int)blockDim.x / tpr;
+  const int sub = (int)threadIdx.x / tpr, tx = (int)threadIdx.x - sub * tpr;
   // 1/dx, 1/dz as df pairs (per thread, once)
   const float idxh = (float)g.idx, idzh = (float)g.idz;
   const dfl idx{idxh, (float)(g.idx - (double)idxh)}, idz{idzh, (float)(g.idz - (double)idzh)};
   // the current run of rows in plane jr: sums still to be weighted
-  int jr = r0 >> lnz;
+  int jr = (r0 + sub) >> lnz;
   dfl ruw{0.f, 0.f}, rv{0.f, 0.f}, rcp{0.f, 0.f}, rcm{0.f, 0.f}, ru{0.f, 0.f}, rhp{0.f, 0.f}, rhm{0.f, 0.f};
+  bool any = false;
   auto flush = [&]() {
     const float2 dyw = wgt[jr], hw = wgt[g.ny + jr];
     const dfl dy{dyw.x, dyw.y}, h{hw.x, hw.y};
@@ -220,24 +225,23 @@ __global__ void __launch_bounds__(kDiagThreads, 3) k_diag_partial_mixed(Fields<f
     if (jr == g.nyc - 1) sum[1] = df_add(sum[1], ru);
     ruw = rv = rcp = rcm = ru = rhp = rhm = dfl{0.f, 0.f};
   };
-  for (int r = r0; r < r1; ++r) {
+  for (int r = r0 + sub; r < r1 && sub < rpp; r += rpp) {
     const int j = r >> lnz, k = r & (nz - 1);
     if (j != jr) {
       flush();
       jr = j;
     }
+    any = true;
     const int kp = (k + 1) & (nz - 1);
     const float2 iyw = wgt[2 * g.ny + j];
     const float crp = cref_p[j], crm = cref_m[j];
     const float dpy = j + 1 < g.nyc ? dPref[j + 1] : 0.f;   // Phi_ref step across face j+1 (interior faces)
     const float ihy = j + 1 < g.nyc ? 1.f / wgt[g.ny + j + 1].x : 0.f;   // 1 / h of that face
     const size_t rowo = (size_t)r * nx, rowkp = ((size_t)j * nz + kp) * nx;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const size_t c = rowo + i;
-      const int ip = (i + 1) & (nx - 1);
-      const float u = f.u[c], w = f.w[c], p = f.p[c], ph = sh.phi[c], v0 = f.v[c], v1 = f.v[c + P];
-      const float ue = f.u[rowo + ip], wn = f.w[rowkp + i];
-      const float Sp = sh.cp[c], Lp = sh.cpL[c], Sm = sh.cm[c], Lm = sh.cmL[c];
+    const bool top = j + 1 < g.nyc;
+    // one cell: its values and the neighbours east (+x), north (+z) and above (+y)
+    auto cell = [&](float u, float ue, float w, float wn, float p, float ph, float phe, float phn, float phu,
+                    float v0, float v1, float Sp, float Lp, float Sm, float Lm, float Hp, float Hm) {
       ru = df_add_fast(ru, dfl{u, 0.f});
       ruw = df_add_fast(ruw, df_add_fast(df_prod(u, u), df_prod(w, w)));
       rv = df_add_fast(rv, df_prod(v0, v0));
@@ -259,16 +263,29 @@ __global__ void __launch_bounds__(kDiagThreads, 3) k_diag_partial_mixed(Fields<f
       cmin = fminf(cmin, fminf(crp + Sp, crm + Sm));
       maxrate = fmaxf(maxrate, fabsf(0.5f * (u + ue)) * idxh + fabsf(0.5f * (v0 + v1)) * iyw.x +
                                    fabsf(0.5f * (w + wn)) * idzh);
-      const float dpx = fabsf(sh.phi[rowo + ip] - ph), dpz = fabsf(sh.phi[rowkp + i] - ph);
-      const float dpyc = j + 1 < g.nyc ? fabsf(dpy + (sh.phi[c + P] - ph)) : 0.f;
+      const float dpx = fabsf(phe - ph), dpz = fabsf(phn - ph);
+      const float dpyc = top ? fabsf(dpy + (phu - ph)) : 0.f;
       maxdphi = fmaxf(maxdphi, fmaxf(fmaxf(dpx, dpz), dpyc));
       maxmig = fmaxf(maxmig, dpx * idxh * idxh + dpyc * ihy * iyw.x + dpz * idzh * idzh);
       maxcsum = fmaxf(maxcsum, (crp + Sp) + (crm + Sm));
-      rhp = df_add_fast(rhp, dfl{sh.Hcp[c], 0.f});
-      rhm = df_add_fast(rhm, dfl{sh.Hcm[c], 0.f});
+      rhp = df_add_fast(rhp, dfl{Hp, 0.f});
+      rhm = df_add_fast(rhm, dfl{Hm, 0.f});
+    };
+    for (int i = 2 * tx; i < nx; i += 2 * tpr) {
+      const size_t c = rowo + i;
+      const int i2 = (i + 2) & (nx - 1);
+      auto ld2 = [](const float* q, size_t o) { return *reinterpret_cast<const float2*>(q + o); };
+      const float2 u = ld2(f.u, c), w = ld2(f.w, c), p = ld2(f.p, c), ph = ld2(sh.phi, c);
+      const float2 v0 = ld2(f.v, c), v1 = ld2(f.v, c + P), wn = ld2(f.w, rowkp + i), phn = ld2(sh.phi, rowkp + i);
+      const float2 Sp = ld2(sh.cp, c), Lp = ld2(sh.cpL, c), Sm = ld2(sh.cm, c), Lm = ld2(sh.cmL, c);
+      const float2 Hp = ld2(sh.Hcp, c), Hm = ld2(sh.Hcm, c);
+      const float2 phu = top ? ld2(sh.phi, c + P) : make_float2(0.f, 0.f);
+      const float ue2 = f.u[rowo + i2], phe2 = sh.phi[rowo + i2];
+      cell(u.x, u.y, w.x, wn.x, p.x, ph.x, ph.y, phn.x, phu.x, v0.x, v1.x, Sp.x, Lp.x, Sm.x, Lm.x, Hp.x, Hm.x);
+      cell(u.y, ue2, w.y, wn.y, p.y, ph.y, phe2, phn.y, phu.y, v0.y, v1.y, Sp.y, Lp.y, Sm.y, Lm.y, Hp.y, Hm.y);
     }
   }
-  if (r0 < r1) flush();
+  if (any) flush();
   // the top wall face of v
   const size_t nc = (size_t)g.nyc * P;
   const float2 hw = wgt[g.ny + g.nyc];
@@ -328,13 +345,13 @@ cudaError_t launch_diagnostics_mixed(const Fields<float>& f, const Shadows& sh, 
                                      const float* cref_m, const float* dPref, const float2* wgt, const Geo& g,
                                      double* partial, int npartial, double* out, int* status,
                                      const DiagLimits& lim, cudaStream_t s) {
-  // one resident wave: three 256-thread blocks per SM (up to 85 registers a
-  // thread: the double-float sums of the row runs stay in registers)
+  // one resident wave: two 256-thread blocks per SM (up to 128 registers a thread:
+  // two cells each, the double-float sums of the row runs kept in registers)
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const int nb = std::max(1, std::min(npartial, 3 * sms));
+  const int nb = std::max(1, std::min(npartial, 2 * sms));
   k_diag_partial_mixed<<<nb, kDiagThreads, 0, s>>>(f, sh, cref_p, cref_m, dPref, wgt, g, partial);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
