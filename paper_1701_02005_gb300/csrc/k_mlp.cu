@@ -35,12 +35,22 @@ __device__ __forceinline__ float gelu_d(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
+// Sum of the per-CTA partial gradients in a fixed order: four interleaved running
+// sums (partials b = 4q .. 4q + 3), combined as (s0 + s1) + (s2 + s3).
 __global__ void k_mlp_reduce_partial(const float* __restrict__ partial, int nblk, int len, float* __restrict__ gw,
                                      float* __restrict__ gb, int nk) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= len) return;
-  float s = 0.f;
-  for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * len + e];
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  int b = 0;
+  for (; b + 3 < nblk; b += 4) {
+    s0 += partial[(size_t)b * len + e];
+    s1 += partial[(size_t)(b + 1) * len + e];
+    s2 += partial[(size_t)(b + 2) * len + e];
+    s3 += partial[(size_t)(b + 3) * len + e];
+  }
+  for (; b < nblk; ++b) s0 += partial[(size_t)b * len + e];
+  const float s = (s0 + s1) + (s2 + s3);
   if (e < nk) gw[e] = s;
   else gb[e - nk] = s;
 }

@@ -2218,12 +2218,12 @@ void pnp_ensemble_destroy(pnp_ensemble* e) {
 // ---------------------------------------------------------------------------
 // Learned wall model: MLP workspace and the coupling to a coarse context.
 // ---------------------------------------------------------------------------
-constexpr int kMlpMaxPartial = 160;
+constexpr int kMlpMaxPartial = 320;
 
 struct pnp_mlp {
   MlpBufs b{};
   int max_batch = 0;
-  int max_partial = 64;   // weight-gradient CTAs: one per SM (at most kMlpMaxPartial)
+  int max_partial = 64;   // weight-gradient CTAs: two per SM (at most kMlpMaxPartial)
   size_t nparam = 0;
   cudaStream_t stream = nullptr;
   int t_adam = 0;
@@ -2306,7 +2306,7 @@ int pnp_mlp_create(pnp_mlp** out, int max_batch, void* ws, size_t bytes, void* s
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
-      m->max_partial = std::min(sms, kMlpMaxPartial);
+      m->max_partial = std::min(2 * sms, kMlpMaxPartial);
   }
   mlp_carve(m, (char*)ws, max_batch);
   // weights U(-a, a), a = sqrt(6 / fan_in) from SplitMix64; biases 0; unit normalisation
