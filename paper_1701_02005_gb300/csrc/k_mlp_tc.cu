@@ -256,34 +256,44 @@ __device__ __forceinline__ void stage_a(__nv_bfloat16* A, const float* __restric
 }
 
 // T[rr][bb] = act(src[bb][rr]) for bb < rows, rr < Rs (the transpose of a chunk
-// of rows, for the weight gradient, whose K is the batch), zero for bb >= rows,
-// and T[ones_at][bb] = 1 for bb < rows when ones_at >= 0; rows Rs..R-1 other than
-// ones_at are left as they are (zero from the start of the kernel).  A warp
-// fills an 8 x 8 block: lane -> row rr = 8 rb + lane / 4 and the column pair
-// bb = 8 cb + 2 (lane % 4), bb + 1, stored as one 4-byte word -- the 32 words of
-// a warp land in 32 different banks (eight core-matrix rows x four words).
+// of rows, for the weight gradient, whose K is the batch), T[ones_at][bb] = 1
+// for bb < rows when ones_at >= 0, and zero in columns bb >= rows; rows Rs..R-1
+// other than ones_at are left as they are (zero from the start of the kernel).
 __device__ __forceinline__ void stage_t(__nv_bfloat16* T, int R, const float* __restrict__ src, int rows, int Rs,
                                         bool act, int ones_at) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = kTcThreads / 32;
-  const int nrb = (Rs + 7) / 8, units = nrb * (kWgK / 8);
-  unsigned char* t = reinterpret_cast<unsigned char*>(T);
-  for (int u = warp; u < units; u += nwarps) {
-    const int rb = u % nrb, cb = u / nrb;
-    const int rr = 8 * rb + (lane >> 2), bb = 8 * cb + 2 * (lane & 3);
-    if (rr < Rs) {
-      float x0 = 0.f, x1 = 0.f;
-      if (bb < rows) x0 = __ldg(src + (size_t)bb * Rs + rr);
-      if (bb + 1 < rows) x1 = __ldg(src + (size_t)(bb + 1) * Rs + rr);
+  const int tid = threadIdx.x;
+  if ((Rs & 3) == 0) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    const int nq = rows * Rs / 4;
+#pragma unroll 4
+    for (int q = tid; q < nq; q += kTcThreads) {
+      const int e = 4 * q, bb = e / Rs, rr = e - bb * Rs;
+      float4 x = __ldg(s4 + q);
       if (act) {
-        x0 = bb < rows ? gelu_tc(x0) : 0.f;
-        x1 = bb + 1 < rows ? gelu_tc(x1) : 0.f;
+        x.x = gelu_tc(x.x);
+        x.y = gelu_tc(x.y);
+        x.z = gelu_tc(x.z);
+        x.w = gelu_tc(x.w);
       }
-      const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
-      *reinterpret_cast<uint32_t*>(t + canon(rr, bb, R)) = *reinterpret_cast<const uint32_t*>(&h2);
+      set_bf16(T, canon(rr, bb, R), x.x);
+      set_bf16(T, canon(rr + 1, bb, R), x.y);
+      set_bf16(T, canon(rr + 2, bb, R), x.z);
+      set_bf16(T, canon(rr + 3, bb, R), x.w);
+    }
+  } else {
+    for (int e = tid; e < rows * Rs; e += kTcThreads) {
+      const int bb = e / Rs, rr = e - bb * Rs;
+      float x = src[e];
+      if (act) x = gelu_tc(x);
+      set_bf16(T, canon(rr, bb, R), x);
     }
   }
   if (ones_at >= 0)
-    for (int bb = threadIdx.x; bb < kWgK; bb += kTcThreads) set_bf16(T, canon(ones_at, bb, R), bb < rows ? 1.f : 0.f);
+    for (int bb = tid; bb < kWgK; bb += kTcThreads) set_bf16(T, canon(ones_at, bb, R), bb < rows ? 1.f : 0.f);
+  for (int e = tid; e < (kWgK - rows) * Rs; e += kTcThreads) {
+    const int bb = rows + e / Rs, rr = e % Rs;
+    set_bf16(T, canon(rr, bb, R), 0.f);
+  }
 }
 
 // The weight image of a layer (16-byte chunks, already in the shared-memory layout).
