@@ -419,7 +419,11 @@ int pnp_mlp_train_step(pnp_mlp* mlp, const float* X_dev, const float* T_dev, int
 int pnp_mlp_status(pnp_mlp* mlp);
 void pnp_mlp_destroy(pnp_mlp* mlp);
 
-/* Feature rows of a context's state: X[2 Nz Nx][5 ncells] (ncells <= 8). */
+/* Feature rows of a context's state: X[2 Nz Nx][5 ncells] (ncells <= 8).  With
+ * the wall model's potential offsets in place (pnp_set_wallmodel_edl), the
+ * potential column leaves out their charge-free lift: it is the potential the
+ * present ions give between the uniform walls -V, +V, the same quantity the
+ * network sees when it is trained on uncoupled runs. */
 int pnp_wall_features(pnp_ctx* ctx, int ncells, float* X_dev);
 /* Coarse state := volume-weighted restriction of the fine state (u, v, w, p,
  * c+-, Phi); the coarse stored explicit terms are zeroed. */
@@ -452,7 +456,9 @@ int pnp_set_wallmodel_coupling(pnp_ctx* ctx, int mode, double relax);
  * network's columns 2-4; no counterpart in the paper, which resolves the layer).
  * potential_gain in [0, 1]: before each step the wall potentials move by
  * potential_gain (phi_pred - phi_1) per wall column, phi_1 the first cell's
- * potential perturbation Phi - V y_c and phi_pred the predicted one, as offsets
+ * potential perturbation Phi - V y_c and phi_pred the one the network predicts
+ * from features that leave the offsets' own lift out (so that a fixed point
+ * exists: the prediction does not move with the offsets), as offsets
  * on top of the uniform walls -V, +V (within +-max(1, |V|)), and the potential
  * of the present ions is solved again under them.  flux_gain in [0, 1]: after
  * each step, ions move across the first interior face of each wall column so
@@ -464,6 +470,8 @@ int pnp_set_wallmodel_coupling(pnp_ctx* ctx, int mode, double relax);
  * map of pnp_set_wall_potential is set. */
 int pnp_set_wallmodel_edl(pnp_ctx* ctx, double potential_gain, double flux_gain);
 /* One potential-offset update from device feature rows X [2 Nz Nx][5 ncells]
+ * (as pnp_wall_features gives them: without the offsets' lift, which the update
+ * adds back to compare the prediction with the first cell's present potential)
  * and outputs Y [2 Nz Nx][5] (the step pnp_step_wallmodel takes before each
  * step; needs potential_gain > 0).  Stream-ordered on the context's stream. */
 int pnp_set_wall_edl(pnp_ctx* ctx, const float* X_dev, int ncells, const float* Y_dev);

@@ -40,10 +40,14 @@ def restrict(gf, gc, q, vfield=False):
     return num / (w.sum(axis=1) * rx * rz)[:, None, None]
 
 
-def wall_features(g, prm, st, ncells=8):
+def wall_features(g, prm, st, ncells=8, lift=None):
+    """Feature rows; lift (cells, optional): the charge-free potential of wall-model
+    offsets, left out of the potential column."""
     P = g.nz * g.nx
     X = np.empty((2 * P, 5 * ncells))
     phi = st.Phi - prm.V * g.yc[:, None, None]
+    if lift is not None:
+        phi = phi - lift
     for wall in (0, 1):
         for d in range(ncells):
             j = d if wall == 0 else g.nyc - 1 - d
@@ -102,15 +106,31 @@ def wall_labels(gf, gc, prm, st):
 # ---------------------------------------------------------------------------
 # Double-layer coupling: the network's columns 2-4 imposed on a coarse state
 # ---------------------------------------------------------------------------
-def edl_offsets(g, X, Y, ncells, gain, B, T, lim):
+def offsets_lift(g, prm, B, T):
+    """The charge-free potential of wall offsets B, T (lab frame) on top of the
+    uniform walls: the potential of no ions between walls -V + B, V + T less that
+    between -V, V (the solution is linear in the wall data)."""
+    from .pnp_oracle import Params, potential_from_ions
+    zero = np.zeros((g.nyc, g.nz, g.nx))
+    pw = Params(Re=prm.Re, lam=prm.lam, Sc=prm.Sc, V=prm.V, beta=prm.beta, Uw=prm.Uw,
+                wall=(-prm.V + np.asarray(B), prm.V + np.asarray(T)))
+    p0 = Params(Re=prm.Re, lam=prm.lam, Sc=prm.Sc, V=prm.V, beta=prm.beta, Uw=prm.Uw)
+    return potential_from_ions(g, pw, zero, zero) - potential_from_ions(g, p0, zero, zero)
+
+
+def edl_offsets(g, X, Y, ncells, gain, B, T, lim, lift=None):
     """Wall-potential offsets (lab frame, on top of the uniform walls -V, +V)
     after one update: each wall column's offset moves by gain (phi_pred - phi_1),
-    phi_1 the feature row's first-cell potential perturbation, phi_pred column 2
-    of the prediction (wall frame: the top wall's sign flips back); clipped to
-    +-lim, a non-finite step leaves the offset alone."""
+    phi_pred column 2 of the prediction (wall frame: the top wall's sign flips
+    back) and phi_1 the first cell's present potential perturbation: the feature
+    row's value (which leaves the offsets' lift out) plus lift (the offsets'
+    charge-free potential, cells; none: zero); clipped to +-lim, a non-finite step
+    leaves the offset alone."""
     P = g.nz * g.nx
-    db = gain * (Y[:P, 2].astype(np.float64) - X[:P, 4 * ncells].astype(np.float64))
-    dt = gain * (Y[P:, 2].astype(np.float64) - X[P:, 4 * ncells].astype(np.float64))
+    lb = np.zeros(P) if lift is None else lift[0].ravel()
+    lt = np.zeros(P) if lift is None else -lift[g.nyc - 1].ravel()   # wall frame
+    db = gain * (Y[:P, 2].astype(np.float64) - (X[:P, 4 * ncells].astype(np.float64) + lb))
+    dt = gain * (Y[P:, 2].astype(np.float64) - (X[P:, 4 * ncells].astype(np.float64) + lt))
     Bn, Tn = np.asarray(B, dtype=np.float64).ravel().copy(), np.asarray(T, dtype=np.float64).ravel().copy()
     okb, okt = np.isfinite(db), np.isfinite(dt)
     Bn[okb] = np.clip(Bn[okb] + db[okb], -lim, lim)

@@ -65,7 +65,7 @@ __global__ void k_restrict_v(const T* __restrict__ f, WallMap wm, double* __rest
 template <typename TV>
 __global__ void k_wall_features(const TV* __restrict__ u, const TV* __restrict__ w, IonView ions,
                                 const double* __restrict__ yc, Geo g, double V, double Uw, int ncells,
-                                float* __restrict__ X) {
+                                const double* __restrict__ lift, float* __restrict__ X) {
   const size_t P = (size_t)g.nz * g.nx;
   const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= 2 * P) return;
@@ -75,7 +75,7 @@ __global__ void k_wall_features(const TV* __restrict__ u, const TV* __restrict__
   for (int d = 0; d < ncells; ++d) {
     const int j = wall == 0 ? d : g.nyc - 1 - d;
     const size_t o = (size_t)j * P + col;
-    const double phi = ions.phv(j, o) - V * yc[j];
+    const double phi = ions.phv(j, o) - V * yc[j] - (lift ? lift[o] : 0.0);
     const double ur = wall == 0 ? (double)u[o] + Uw : Uw - (double)u[o];
     const double cpo = ions.cpv(j, o), cmo = ions.cmv(j, o);
     row[0 * ncells + d] = (float)ur;
@@ -255,17 +255,21 @@ cudaError_t launch_relax_rates(float* Y, float* prev, int rows, float w, cudaStr
 }
 
 // Potential coupling: the wall-potential offsets (lab frame, relative to the
-// uniform walls -V, +V) move by gain (phi_pred - phi_1) per call, phi_1 the
-// first cell's potential perturbation in the feature row and phi_pred the
-// network's (column 2, wall frame: the top wall's sign is flipped back).
+// uniform walls -V, +V) move by gain (phi_pred - phi_1) per call, phi_pred the
+// network's first-cell potential (column 2, wall frame: the top wall's sign is
+// flipped back) and phi_1 the first cell's present potential perturbation: the
+// feature row's value, which leaves out the charge-free lift of the offsets, plus
+// that lift (lift: its first and last cell planes, or null when there is none).
 // Offsets stay within +-lim; a non-finite prediction leaves the offset alone.
 __global__ void k_edl_offsets(const float* __restrict__ X, int ncells, const float* __restrict__ Y, size_t P,
-                              double gain, double lim, double* __restrict__ B, double* __restrict__ T) {
+                              double gain, double lim, const double* __restrict__ lift, int nyc,
+                              double* __restrict__ B, double* __restrict__ T) {
   const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= P) return;
   const size_t fs = (size_t)5 * ncells;
-  const double db = gain * ((double)Y[c * 5 + 2] - (double)X[c * fs + 4 * ncells]);
-  const double dt = gain * ((double)Y[(P + c) * 5 + 2] - (double)X[(P + c) * fs + 4 * ncells]);
+  const double lb = lift ? lift[c] : 0.0, lt = lift ? -lift[(size_t)(nyc - 1) * P + c] : 0.0;   // wall frame
+  const double db = gain * ((double)Y[c * 5 + 2] - ((double)X[c * fs + 4 * ncells] + lb));
+  const double dt = gain * ((double)Y[(P + c) * 5 + 2] - ((double)X[(P + c) * fs + 4 * ncells] + lt));
   if (isfinite(db)) B[c] = fmin(fmax(B[c] + db, -lim), lim);
   if (isfinite(dt)) T[c] = fmin(fmax(T[c] - dt, -lim), lim);
 }
@@ -331,9 +335,9 @@ __global__ void k_wall_flux_fix(IonView ions, const TV* __restrict__ v, const do
         ions.crefm);
 }
 
-cudaError_t launch_edl_offsets(const float* X, int ncells, const float* Y, size_t P, double gain, double lim, double* B,
-                               double* T, cudaStream_t s) {
-  k_edl_offsets<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(X, ncells, Y, P, gain, lim, B, T);
+cudaError_t launch_edl_offsets(const float* X, int ncells, const float* Y, size_t P, double gain, double lim,
+                               const double* lift, int nyc, double* B, double* T, cudaStream_t s) {
+  k_edl_offsets<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(X, ncells, Y, P, gain, lim, lift, nyc, B, T);
   return cudaGetLastError();
 }
 
@@ -361,9 +365,9 @@ cudaError_t launch_restrict(const T* f, const double* dyf, const WallMap& wm, do
 
 template <typename TV>
 cudaError_t launch_wall_features(const TV* u, const TV* w, const IonView& ions, const double* yc, const Geo& g,
-                                 double V, double Uw, int ncells, float* X, cudaStream_t s) {
+                                 double V, double Uw, int ncells, const double* lift, float* X, cudaStream_t s) {
   const size_t n = 2 * (size_t)g.nz * g.nx;
-  k_wall_features<TV><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(u, w, ions, yc, g, V, Uw, ncells, X);
+  k_wall_features<TV><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(u, w, ions, yc, g, V, Uw, ncells, lift, X);
   return cudaGetLastError();
 }
 
@@ -387,9 +391,11 @@ cudaError_t launch_set_slip(const float* X, int ncells, const float* Y, size_t P
 template cudaError_t launch_restrict<double>(const double*, const double*, const WallMap&, double*, bool, cudaStream_t);
 template cudaError_t launch_restrict<float>(const float*, const double*, const WallMap&, double*, bool, cudaStream_t);
 template cudaError_t launch_wall_features<double>(const double*, const double*, const IonView&, const double*,
-                                                  const Geo&, double, double, int, float*, cudaStream_t);
+                                                  const Geo&, double, double, int, const double*, float*,
+                                                  cudaStream_t);
 template cudaError_t launch_wall_features<float>(const float*, const float*, const IonView&, const double*,
-                                                 const Geo&, double, double, int, float*, cudaStream_t);
+                                                 const Geo&, double, double, int, const double*, float*,
+                                                 cudaStream_t);
 template cudaError_t launch_wall_labels<double>(const double*, const double*, const double*, const IonView&,
                                                 const double*, const double*, const double*, const WallMap&, double,
                                                 double, double, double, float*, cudaStream_t);

@@ -2405,11 +2405,12 @@ int pnp_wall_features(pnp_ctx* c, int ncells, float* X) {
   IonView iv{};
   int r = ion_view(c, &iv);
   if (r) return r;
+  const double* lift = c->edl_map ? c->lift64 : nullptr;   // features see the walls -V, +V alone
   cudaError_t e = c->precision == PNP_FP64
                       ? launch_wall_features<double>((const double*)c->u, (const double*)c->w, iv, c->yc_d, c->g,
-                                                     c->ph.V, c->ph.Uw, ncells, X, c->stream)
+                                                     c->ph.V, c->ph.Uw, ncells, lift, X, c->stream)
                       : launch_wall_features<float>((const float*)c->u, (const float*)c->w, iv, c->yc_d, c->g,
-                                                    c->ph.V, c->ph.Uw, ncells, X, c->stream);
+                                                    c->ph.V, c->ph.Uw, ncells, lift, X, c->stream);
   return e == cudaSuccess ? PNP_OK : PNP_ERR_CUDA;
 }
 
@@ -2546,13 +2547,16 @@ int edl_potential(pnp_ctx* c, const float* X, int ncells, const float* Y) {
     if (c->wall_map) return PNP_ERR_UNSUPPORTED;   // the user's wall-potential map is set
     CK(cudaMemsetAsync(c->wallB_d, 0, sizeof(double) * P, c->stream));
     CK(cudaMemsetAsync(c->wallT_d, 0, sizeof(double) * P, c->stream));
+    CK(cudaMemsetAsync(c->lift64, 0, sizeof(double) * c->nc, c->stream));   // no offsets yet: no lift
+    CK(cudaMemsetAsync(c->lift32, 0, sizeof(float) * c->nc, c->stream));
     c->edl_map = true;
     c->wall_map = true;
     c->wall_off = 0.0;
     drop_graph(c);
   }
   const double lim = std::max(1.0, std::fabs(c->ph.V));
-  CK(launch_edl_offsets(X, ncells, Y, P, c->edl_phi_gain, lim, c->wallB_d, c->wallT_d, c->stream));
+  CK(launch_edl_offsets(X, ncells, Y, P, c->edl_phi_gain, lim, c->lift64, c->g.nyc, c->wallB_d, c->wallT_d,
+                        c->stream));
   CK(edl_lift(c));
   // the potential of the present ions under the moved walls: in a mixed context that
   // steps on its shadows, the step's own potential pipeline (writes phi')

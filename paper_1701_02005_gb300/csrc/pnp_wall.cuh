@@ -33,9 +33,11 @@ struct IonView {
 
 template <typename T>
 cudaError_t launch_restrict(const T* f, const double* dyf, const WallMap& wm, double* out, bool vfield, cudaStream_t s);
+// lift: the charge-free potential of the wall model's offsets, left out of the
+// features' potential (null when there are none)
 template <typename TV>
 cudaError_t launch_wall_features(const TV* u, const TV* w, const IonView& ions, const double* yc, const Geo& g,
-                                 double V, double Uw, int ncells, float* X, cudaStream_t s);
+                                 double V, double Uw, int ncells, const double* lift, float* X, cudaStream_t s);
 template <typename TV>
 cudaError_t launch_wall_labels(const TV* u, const TV* v, const TV* w, const IonView& ions, const double* ycf,
                                const double* dyf, const double* hf, const WallMap& wm, double h0c, double V,
@@ -49,9 +51,10 @@ cudaError_t launch_relax_rates(float* Y, float* prev, int rows, float w, cudaStr
 // plane means of the wall-shear-rate columns, per wall, broadcast to its rows
 cudaError_t launch_mean_rates(float* Y, int P, cudaStream_t s);
 
-// wall-potential offsets B, T += gain (predicted - present first-cell potential), within +-lim
-cudaError_t launch_edl_offsets(const float* X, int ncells, const float* Y, size_t P, double gain, double lim, double* B,
-                               double* T, cudaStream_t s);
+// wall-potential offsets B, T += gain (predicted - present first-cell potential), within +-lim;
+// the present potential is the feature (without the offsets' lift) plus the lift
+cudaError_t launch_edl_offsets(const float* X, int ncells, const float* Y, size_t P, double gain, double lim,
+                               const double* lift, int nyc, double* B, double* T, cudaStream_t s);
 // conservative transfer of ions across the first interior face of each wall
 // column towards the predicted fluxes; the updated values go to the FP64
 // arrays (ions.cp set) or to the shadows S, L of a mixed-precision context

@@ -57,15 +57,21 @@ def test_potential_offsets_match_the_oracle(precision):
     tol = 1e-10 if precision == 0 else 1e-5
     dt = 0.01
     for stage, seed in enumerate((11, 12)):   # offsets accumulate over updates
-        X = w.wall_features(g, prm, st, nc).astype(np.float32)
+        # the features leave the present offsets' lift out; the update adds it back
+        lift = w.offsets_lift(g, prm, B, T) if stage > 0 else None
+        X = w.wall_features(g, prm, st, nc, lift).astype(np.float32)
         Y = seeded.field(seed, (2 * P, 5), 0.3).astype(np.float32)
-        B, T = w.edl_offsets(g, X, Y, nc, gain, B, T, max(1.0, abs(prm.V)))
+        B, T = w.edl_offsets(g, X, Y, nc, gain, B, T, max(1.0, abs(prm.V)), lift)
         wm.set_wall_edl(s, _dev(X), _dev(Y), nc)
         prmw = o.Params(Re=prm.Re, lam=prm.lam, Sc=prm.Sc, V=prm.V, beta=prm.beta,
                         wall=(-prm.V + B, prm.V + T))
         st = st.copy()
         st.Phi = o.potential_from_ions(g, prmw, st.cp, st.cm)
         assert _rel(s.get("Phi"), st.Phi) <= tol_phi, (stage, _rel(s.get("Phi"), st.Phi))
+        # the features the network would now see: the offsets' lift left out
+        Xg = wm.features(s, nc).cpu().numpy()
+        Xo = w.wall_features(g, prm, st, nc, w.offsets_lift(g, prm, B, T))
+        assert _rel(Xg, Xo) <= (1e-6 if precision == 0 else 2e-5), (stage, _rel(Xg, Xo))
         assert np.max(np.abs(B)) > 0.05   # the offsets are not trivially zero
         s.step(3, dt)
         st = o.step(g, prmw, st, dt, 3)

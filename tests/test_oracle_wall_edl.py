@@ -121,6 +121,13 @@ def test_offsets_idle_at_the_present_potential_clipped_and_finite():
     Y[:, 2] = X[:, 4 * nc]
     B, T = w.edl_offsets(g, X, Y, nc, 0.7, B0, T0, 1.0)
     assert np.array_equal(B, B0) and np.array_equal(T, T0)
+    # with a lift the present potential is the feature plus the lift
+    lift = seeded.field(45, (g.nyc, g.nz, g.nx), 0.1)
+    Y2 = Y.copy()
+    Y2[:P, 2] = X[:P, 4 * nc] + lift[0].ravel()
+    Y2[P:, 2] = X[P:, 4 * nc] - lift[g.nyc - 1].ravel()
+    B, T = w.edl_offsets(g, X, Y2, nc, 0.7, B0, T0, 1.0, lift)
+    assert np.allclose(B, B0, rtol=0, atol=1e-15) and np.allclose(T, T0, rtol=0, atol=1e-15)
     Y[:, 2] = X[:, 4 * nc] + 100.0
     Y[0, 2] = np.nan
     B, T = w.edl_offsets(g, X, Y, nc, 1.0, B0, T0, 1.0)
@@ -144,11 +151,29 @@ def test_offsets_converge_to_the_closed_form_on_a_charge_free_state():
     for it in range(40):
         prm = o.Params(Re=100.0, lam=0.1, V=1.5, wall=(-prm0.V + B, prm0.V + T))
         st.Phi = o.potential_from_ions(g, prm, st.cp, st.cm)
-        X = w.wall_features(g, prm0, st, nc)
+        lift = w.offsets_lift(g, prm0, B, T)
+        X = w.wall_features(g, prm0, st, nc, lift)   # what the network sees: no ions, no charge
+        assert np.allclose(X[:, 4 * nc], 0.0, atol=1e-13)
         Y = np.zeros((2 * P, 5))
         Y[:, 2] = a
-        B, T = w.edl_offsets(g, X, Y, nc, 1.0, B, T, 4.0)
+        B, T = w.edl_offsets(g, X, Y, nc, 1.0, B, T, 4.0, lift)
     y0 = g.yc[0]
     assert np.allclose(B, -a / y0, rtol=1e-12)
     assert np.allclose(T, a / y0, rtol=1e-12)
-    assert np.allclose(X[:, 4 * nc], a, rtol=1e-12)
+    # the total first-cell potential reached the prediction
+    Xt = w.wall_features(g, prm0, st, nc)
+    assert np.allclose(Xt[:, 4 * nc], a, rtol=1e-12)
+
+
+def test_offsets_lift_is_the_charge_free_potential_of_the_offsets():
+    """Uniform offsets give the linear blend (1 - y)/2 dB + (1 + y)/2 dT exactly;
+    and the lift is linear in the offsets."""
+    g = o.Grid(8, 13, 4, 2.0, 1.0, stretch=1.6)
+    prm = o.Params(Re=50.0, lam=0.1, V=1.0)
+    L = w.offsets_lift(g, prm, 0.3 * np.ones((g.nz, g.nx)), -0.2 * np.ones((g.nz, g.nx)))
+    y = g.yc[:, None, None]
+    assert np.allclose(L, 0.5 * (1 - y) * 0.3 + 0.5 * (1 + y) * -0.2 + 0 * L, rtol=0, atol=1e-13)
+    B1, T1 = seeded.field(51, (g.nz, g.nx), 0.2), seeded.field(52, (g.nz, g.nx), 0.2)
+    B2, T2 = seeded.field(53, (g.nz, g.nx), 0.2), seeded.field(54, (g.nz, g.nx), 0.2)
+    assert np.allclose(w.offsets_lift(g, prm, B1 + B2, T1 + T2),
+                       w.offsets_lift(g, prm, B1, T1) + w.offsets_lift(g, prm, B2, T2), rtol=0, atol=1e-12)
