@@ -18,7 +18,7 @@ DEFAULT_CACHE = os.environ.get("PNP_AUTOTUNE_CACHE", os.path.join(BUILD, "autotu
 
 
 # bumped whenever the set of candidate kernels behind a launch-shape code changes
-KERNEL_REV = 4
+KERNEL_REV = 5
 
 
 def _key(solver):
