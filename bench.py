@@ -435,9 +435,10 @@ def run_wallmodel_reduced(args, B, Solver, torch):
         wm.step_with_model(sm, net, c["chunk"], c["dt"])
         for k, s_ in (("fine", sf), ("plain", sc), ("coupled", sm)):
             cf[k].append(s_.diagnostics()["cf"])
-        pf = wm.labels(sf, sc)[:, 2]
-        for k, s_ in (("plain", sc), ("coupled", sm)):
-            phi[k].append(float((wm.features(s_, 8)[:, 32] - pf).abs().mean() / pf.abs().mean()))
+        pf = wm.labels(sf, sc)[:, 2].cpu().numpy()
+        for k, s_ in (("plain", sc), ("coupled", sm)):   # the total first-cell potential
+            pc = wm.first_cell_potential(s_, c["V"], 0.5 * (yfc[1:] + yfc[:-1]))
+            phi[k].append(float(np.mean(np.abs(pc - pf)) / np.mean(np.abs(pf))))
     f = np.array(cf["fine"])
     err = lambda a: float(np.mean(np.abs(np.array(a) - f) / f))
     out = {"workload": f"fine {c['nx']}x{c['ny']}x{c['nz']} (FP64) -> coarse {ncx}x{len(yfc)}x{ncz}, Re {c['Re']:g}, "
@@ -580,11 +581,11 @@ def run_wallmodel(args, B, Solver, torch):
         for s_ in cpl.values():
             wm.step_with_model(s_, net, c["chunk"], dt)
         cf["fine"].append(fine.diagnostics()["cf"])
-        phi_f = wm.labels(fine, sp)[:, 2]
+        phi_f = wm.labels(fine, sp)[:, 2].cpu().numpy()
         for k, s_ in runs.items():
             cf[k].append(s_.diagnostics()["cf"])
-            phi_c = wm.features(s_, 8)[:, 4 * 8]
-            phi_err[k].append(float((phi_c - phi_f).abs().mean() / phi_f.abs().mean()))
+            phi_c = wm.first_cell_potential(s_, c["V"], 0.5 * (yfc[1:] + yfc[:-1]))   # offsets included
+            phi_err[k].append(float(np.mean(np.abs(phi_c - phi_f)) / np.mean(np.abs(phi_f))))
     f = np.array(cf["fine"])
     err = lambda a: float(np.mean(np.abs(np.array(a) - f) / f))
     merr = lambda a: float(abs(np.mean(a) - np.mean(f)) / np.mean(f))

@@ -123,6 +123,14 @@ def labels(fine, coarse):
     return T
 
 
+def first_cell_potential(solver, V, yc):
+    """The first cells' potential perturbation Phi - V y_c in the wall frame (the
+    top wall's sign flipped), rows [bottom Nz Nx, top Nz Nx] as in the feature
+    rows: the total potential, wall-model offsets included (host array)."""
+    Phi = solver.get("Phi")
+    return np.concatenate([(Phi[0] - V * yc[0]).ravel(), -(Phi[-1] - V * yc[-1]).ravel()])
+
+
 def restrict(fine, coarse):
     B.check(B.pnp_restrict_state(fine.ctx, coarse.ctx), "pnp_restrict_state")
 

@@ -207,8 +207,9 @@ def wall_model_case(nfine=(32, 65, 32), ry=4, rxz=2, Re=500.0, dt=0.002, nsteps=
         cf_m.append(2.0 * prm.nu * float(Y[:, 0].mean()))     # c_f = 2 tau_w / Uw^2, tau_w = nu <du_rel/dy>
         cf_c.append(sm.diagnostics()["cf"])
         phi_f = wm.labels(sf, sc).cpu().numpy()[:, 2]
-        for key, X in (("plain", Xp), ("coupled", wm.features(sm, 8))):
-            phi_err[key].append(float(np.mean(np.abs(X.cpu().numpy()[:, 4 * 8] - phi_f)) / np.mean(np.abs(phi_f))))
+        for key, s_ in (("plain", sc), ("coupled", sm)):   # the total first-cell potential
+            phi_c = wm.first_cell_potential(s_, prm.V, gc.yc)
+            phi_err[key].append(float(np.mean(np.abs(phi_c - phi_f)) / np.mean(np.abs(phi_f))))
     cf_f, cf_p, cf_m, cf_c = map(np.array, (cf_f, cf_p, cf_m, cf_c))
     err = lambda a: float(np.mean(np.abs(a - cf_f) / cf_f))
     status = net.status()
