@@ -332,7 +332,8 @@ def run_large(args, B, Solver, torch):
 # coarse run coupled to the previous network, dataset aggregation); a later,
 # unseen window judges c_f against the fine run, and times fine and coarse.
 WM = dict(V=5.0, rx=2, ry=4, window=1000, every=2, spinup=8000, layer_steps=1000, passes=3, iters=3000,
-          batch=65536, chunk=20, mode=3, relax=1.0, potential_gain=0.3, flux_gain=0.3, seed=1705, amp=0.05)
+          batch=65536, chunk=20, mode=3, relax=1.0, potential_gain=0.3, flux_gain=0.3, seed=1705, amp=0.05,
+          residual=True)
 
 
 def vortices_and_streaks(yf, nz, Lz, A=0.15, Bs=0.4, m=1):
@@ -363,7 +364,7 @@ def vortices_and_streaks(yf, nz, Lz, A=0.15, Bs=0.4, m=1):
 # block (three windows, the later two coupled), judged on another seed.
 WMR = dict(nx=32, ny=65, nz=32, stretch=2.0, Re=500.0, lam=0.05, V=2.0, ry=4, rx=2, dt=0.002, steps=200, every=2,
            iters=3000, passes=3, chunk=10, mode=2, potential_gain=0.3, flux_gain=0.3, seed_train=31, seed_judge=32,
-           amp=0.02, net_seed=33)
+           amp=0.02, net_seed=33, residual=True)
 
 
 def run_wallmodel_reduced(args, B, Solver, torch):
@@ -372,6 +373,9 @@ def run_wallmodel_reduced(args, B, Solver, torch):
     from paper_1701_02005_gb300 import wallmodel as wm
 
     c = dict(WMR)
+    if args.wm_residual is not None:
+        c["residual"] = bool(args.wm_residual)
+    skip = wm.PHI_SKIP if c["residual"] else None
     yf = np.tanh(c["stretch"] * (np.arange(c["ny"]) * 2.0 / (c["ny"] - 1) - 1.0)) / math.tanh(c["stretch"])
     yf[0], yf[-1] = -1.0, 1.0
     yc = 0.5 * (yf[1:] + yf[:-1])
@@ -409,12 +413,15 @@ def run_wallmodel_reduced(args, B, Solver, torch):
         wm.clear_edl(sc)
         X, T = torch.cat(Xs), torch.cat(Ts)
         if net is None:
-            xs, ts = X.double().mean(0), T.double().mean(0)
+            R = wm.residual_targets(T, X, skip)   # what the network's own outputs learn
+            xs, ts = X.double().mean(0), R.double().mean(0)
             xsd = torch.maximum(X.double().std(0), 1e-2 * torch.clamp(xs.abs(), min=1e-2))
-            tsd = torch.maximum(T.double().std(0), 1e-2 * torch.clamp(ts.abs(), min=1e-4))
+            tsd = torch.maximum(R.double().std(0), 1e-2 * torch.clamp(ts.abs(), min=1e-4))
             net = wm.MLP(c["steps"] // c["every"] * c["passes"] * 2 * ncz * ncx, seed=c["net_seed"])
             net.set_normalization(xs.cpu().numpy(), (1.0 / xsd).cpu().numpy(), ts.cpu().numpy(),
                                   (1.0 / tsd).cpu().numpy())
+            if skip is not None:
+                net.set_skip(*skip)
         lr0, lr1 = (2e-3, 5e-4) if p == 0 else (1e-3, 3e-4)
         l0 = net.train_step(X, T, lr0, want_loss=True)
         for it in range(c["iters"]):
@@ -445,7 +452,7 @@ def run_wallmodel_reduced(args, B, Solver, torch):
                        f"lambda_D/h {c['lam']}, V {c['V']:g}, dt {c['dt']}, walls set in motion at t = 0, "
                        f"{c['passes']} training runs of {c['steps']} steps (seed {c['seed_train']}), judged on seed "
                        f"{c['seed_judge']}",
-           "coupling": {k: c[k] for k in ("mode", "potential_gain", "flux_gain")},
+           "coupling": {k: c[k] for k in ("mode", "potential_gain", "flux_gain", "residual")},
            "training": {"rows": int(X.shape[0]), "loss_first_last": losses, "seconds": train_s},
            "cf_err": {k: err(cf[k]) for k in ("plain", "coupled")},
            "first_cell_phi_err": {k: float(np.mean(v)) for k, v in phi.items()},
@@ -465,6 +472,9 @@ def run_wallmodel(args, B, Solver, torch):
     c = dict(WM)
     if args.wm_edl is not None:
         c["potential_gain"], c["flux_gain"] = args.wm_edl
+    if args.wm_residual is not None:
+        c["residual"] = bool(args.wm_residual)
+    skip = wm.PHI_SKIP if c["residual"] else None
     nx, ny, nz, st = WL["nx"], WL["ny"], WL["nz"], WL["stretch"]
     dt = stable_dt(nx, ny, WL["Re"], WL["lam"], c["V"], st)[0]
     yf = np.tanh(st * (np.arange(ny) * 2.0 / (ny - 1) - 1.0)) / math.tanh(st)
@@ -524,21 +534,25 @@ def run_wallmodel(args, B, Solver, torch):
         wm.set_slip(sc, None, None)
         wm.clear_edl(sc)
         X, T = torch.cat(Xs), torch.cat(Ts)
+        R = wm.residual_targets(T, X, skip)   # what the network's own outputs learn
         ok = torch.isfinite(X).all(1) & torch.isfinite(T).all(1)   # rows of a run gone non-finite stay out
         if net is not None:   # and rows far outside the first pass's spread
-            ok &= (((X.double() - xs) / xsd).abs() < 20).all(1) & (((T.double() - ts) / tsd).abs() < 20).all(1)
-        X, T = X[ok].contiguous(), T[ok].contiguous()
+            ok &= (((X.double() - xs) / xsd).abs() < 20).all(1) & (((R.double() - ts) / tsd).abs() < 20).all(1)
+        X, T, R = X[ok].contiguous(), T[ok].contiguous(), R[ok]
         log(f"pass {p}: {len(Xs)} snapshots, {int(ok.sum())} of {ok.numel()} rows kept, coarse cf "
             f"{sc.diagnostics()['cf']:.6g}")
         if X.shape[0] == 0:
             break
         if net is None:
-            xs, ts = X.mean(0).double(), T.mean(0).double()
+            xs, ts = X.mean(0).double(), R.mean(0).double()
             xsd = torch.maximum(X.double().std(0), 1e-2 * torch.clamp(xs.abs(), min=1e-2))
-            tsd = torch.maximum(T.double().std(0), 1e-2 * torch.clamp(ts.abs(), min=1e-4))
+            tsd = torch.maximum(R.double().std(0), 1e-2 * torch.clamp(ts.abs(), min=1e-4))
             net = wm.MLP(max(c["batch"], rows), seed=c["seed"])
             net.set_normalization(xs.cpu().numpy(), (1.0 / xsd).cpu().numpy(), ts.cpu().numpy(),
                                   (1.0 / tsd).cpu().numpy())
+            if skip is not None:
+                net.set_skip(*skip)
+        del R
         lr0, lr1 = (2e-3, 5e-4) if p == 0 else (1e-3, 3e-4)
         nb = max(1, X.shape[0] // c["batch"])
         gen = torch.Generator(device=X.device).manual_seed(c["seed"] + p)
@@ -614,7 +628,7 @@ def run_wallmodel(args, B, Solver, torch):
     out = {"workload": f"fine {nx}x{ny}x{nz} (mixed) -> coarse {ncx}x{ncy}x{ncz}, Re {WL['Re']:g}, "
                        f"lambda_D/h {WL['lam']}, V {c['V']:g}, dt {dt:.4g}, {c['spinup']} spin-up steps at V 0, "
                        f"{c['passes']} training windows + 1 judged window of {c['window']} steps",
-           "coupling": {**{k: c[k] for k in ("mode", "relax", "potential_gain", "flux_gain")},
+           "coupling": {**{k: c[k] for k in ("mode", "relax", "potential_gain", "flux_gain", "residual")},
                         "note": "training passes coupled in this mode; judged in mode 3 (coupled_edl) and mode 2 "
                                 "(coupled_shear)"},
            "spinup": {"steps_at_V0": c["spinup"], "dt_max_V0": dt0, "time_units": t_spin, "cf_after": cf_spun,
@@ -1297,6 +1311,9 @@ def main():
     ap.add_argument("--wallmodel", action="store_true", help="only the learned wall-model block (fine 256x193x256 "
                     "at V = 5 against coarse 128x49x128 with and without the network)")
     ap.add_argument("--wm-edl", type=float, nargs=2, default=None, metavar=("POTENTIAL_GAIN", "FLUX_GAIN"))
+    ap.add_argument("--wm-residual", type=int, choices=(0, 1), default=None,
+                    help="the network's first-cell potential as the coarse feature plus its own value (1) or "
+                         "absolute (0)")
     ap.add_argument("--mlp", action="store_true", help="only the wall-model network's forward / training throughput")
     ap.add_argument("--large-steps", type=int, default=20)
     ap.add_argument("--grid", default=None,

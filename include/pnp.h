@@ -405,6 +405,14 @@ int pnp_mlp_set_params(pnp_mlp* mlp, const float* host_params, size_t count);
  * out_shift (5 each); host arrays. */
 int pnp_mlp_set_normalization(pnp_mlp* mlp, const float* in_shift, const float* in_scale, const float* out_shift,
                               const float* out_scale);
+/* Residual output: output out_col becomes the network's value plus the raw
+ * input column in_col, y_o = n_o / out_scale_o + out_shift_o + x_i, so that the
+ * network learns y_o - x_i (the output normalisation of column o then applies to
+ * that difference, and the training loss compares the network with t_o - x_i).
+ * out_col < 0 removes it (the default).  PNP_ERR_ARG for out_col >= 5, in_col >=
+ * 40, or in_col < 0 with out_col >= 0.  Host state only; takes effect from the
+ * next call. */
+int pnp_mlp_set_skip(pnp_mlp* mlp, int out_col, int in_col);
 /* Y[B][5] = network(X[B][40]); device arrays; asynchronous.  Normalised
  * outputs are clipped to +-6 (six standard deviations of the training labels
  * when the normalisation is set from them). */

@@ -218,11 +218,13 @@ def _weights(p, bf16):
     return Ws, bs
 
 
-def forward(p, X, norm, bf16=True, bf16_act=False):
+def forward(p, X, norm, bf16=True, bf16_act=False, skip=None):
     """Physical outputs and the cache for backpropagation.  bf16: the GEMMs use
     BF16-rounded weights; bf16_act: their activation operands are rounded to
     BF16 as well (tensor-core GEMMs take both operands in BF16 and accumulate
-    in FP32); biases, GELU and the accumulation stay FP64 here."""
+    in FP32); biases, GELU and the accumulation stay FP64 here.  skip = (j, i):
+    output j is the network's value plus the raw input column i (a residual
+    output: the network learns y_j - x_i)."""
     in_shift, in_scale, out_shift, out_scale = (np.asarray(a, dtype=np.float64) for a in norm)
     Ws, bs = _weights(p, bf16)
     a = (np.asarray(X, dtype=np.float64) - in_shift) * in_scale
@@ -233,18 +235,24 @@ def forward(p, X, norm, bf16=True, bf16_act=False):
             x = bf16_round(x)
         ins.append(x)
         zs.append(x @ W.T + b)
-    yn = zs[-1]
-    return yn / out_scale + out_shift, (ins, zs, Ws)
+    y = zs[-1] / out_scale + out_shift
+    if skip is not None:
+        y[:, skip[0]] += np.asarray(X, dtype=np.float64)[:, skip[1]]
+    return y, (ins, zs, Ws)
 
 
-def loss_and_grad(p, X, T, norm, bf16=True, bf16_act=False):
+def loss_and_grad(p, X, T, norm, bf16=True, bf16_act=False, skip=None):
     """MSE of normalised outputs and its gradient w.r.t. the parameter vector
     (w.r.t. the weights the forward pass used).  bf16_act: the backward GEMMs
     take the output gradients dz in BF16 as well (the weight gradient pairs
-    them with the BF16 layer inputs; the bias gradient sums them)."""
+    them with the BF16 layer inputs; the bias gradient sums them).  skip: as in
+    forward; the normalisation of output j then applies to y_j - x_i."""
     _, _, out_shift, out_scale = (np.asarray(a, dtype=np.float64) for a in norm)
-    _, (ins, zs, Ws) = forward(p, X, norm, bf16, bf16_act)
-    tn = (np.asarray(T, dtype=np.float64) - out_shift) * out_scale
+    _, (ins, zs, Ws) = forward(p, X, norm, bf16, bf16_act, skip)
+    y = np.array(T, dtype=np.float64)
+    if skip is not None:
+        y[:, skip[0]] -= np.asarray(X, dtype=np.float64)[:, skip[1]]
+    tn = (y - out_shift) * out_scale
     e = zs[-1] - tn
     n = e.size
     loss = float(np.sum(e * e) / n)

@@ -114,6 +114,7 @@ EXPORTS = {
     "pnp_mlp_set_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_size_t]),
     "pnp_mlp_set_normalization": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float),
                                             C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "pnp_mlp_set_skip": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "pnp_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "pnp_mlp_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_float),
                                    C.POINTER(C.c_float)]),
@@ -218,6 +219,7 @@ pnp_mlp_create = _fwd("pnp_mlp_create")
 pnp_mlp_get_params = _fwd("pnp_mlp_get_params")
 pnp_mlp_set_params = _fwd("pnp_mlp_set_params")
 pnp_mlp_set_normalization = _fwd("pnp_mlp_set_normalization")
+pnp_mlp_set_skip = _fwd("pnp_mlp_set_skip")
 pnp_mlp_forward = _fwd("pnp_mlp_forward")
 pnp_mlp_gradient = _fwd("pnp_mlp_gradient")
 pnp_mlp_train_step = _fwd("pnp_mlp_train_step")

@@ -64,9 +64,11 @@ __global__ void k_mlp_norm_in(const float* __restrict__ X, int B, const float* _
   out[t] = (X[t] - shift[f]) * scale[f];
 }
 
-// dz of the output layer for L = mean((y_n - t_n)^2), with per-block partial losses.
+// dz of the output layer for L = mean((y_n - t_n)^2), with per-block partial losses;
+// with a residual output the network's target in column skip_out is t - x[skip_in].
 __global__ void __launch_bounds__(256) k_mlp_loss(const float* __restrict__ yn, const float* __restrict__ T, int B,
                                                   const float* __restrict__ shift, const float* __restrict__ scale,
+                                                  const float* __restrict__ X, int skip_out, int skip_in,
                                                   float* __restrict__ dz, float* __restrict__ loss_partial) {
   __shared__ float sh[256];
   const size_t n = (size_t)B * kMlpOut;
@@ -74,7 +76,8 @@ __global__ void __launch_bounds__(256) k_mlp_loss(const float* __restrict__ yn, 
   float acc = 0.f;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
     const int f = (int)(t % kMlpOut);
-    const float e = yn[t] - (T[t] - shift[f]) * scale[f];
+    const float tf = f == skip_out ? T[t] - X[(t / kMlpOut) * kMlpIn + skip_in] : T[t];
+    const float e = yn[t] - (tf - shift[f]) * scale[f];
     dz[t] = 2.0f * e * inv;
     acc += e * e;
   }
@@ -117,7 +120,9 @@ cudaError_t mlp_sync_bf16(const MlpBufs& b, size_t nparam, cudaStream_t s) {
 cudaError_t mlp_forward(const MlpBufs& b, const float* X, int B, float* Y, cudaStream_t s) {
   // outputs only: the fused kernel; the layer-by-layer path keeps the activations
   // the backward pass needs
-  if (Y) return mlp_infer_tc(X, B, b.wimg, b.param, b.in_shift, b.in_scale, b.out_shift, b.out_scale, Y, b.err, s);
+  if (Y)
+    return mlp_infer_tc(X, B, b.wimg, b.param, b.in_shift, b.in_scale, b.out_shift, b.out_scale, b.skip_out,
+                        b.skip_in, Y, b.err, s);
   const MlpDims d = mlp_dims();
   const MlpImg im = mlp_images();
   const size_t ni = (size_t)B * kMlpIn;
@@ -133,11 +138,12 @@ cudaError_t mlp_forward(const MlpBufs& b, const float* X, int B, float* Y, cudaS
 }
 
 // Gradient of the loss for the activations left by mlp_forward on the same batch.
-cudaError_t mlp_backward(const MlpBufs& b, const float* T, int B, int max_partial, cudaStream_t s) {
+cudaError_t mlp_backward(const MlpBufs& b, const float* X, const float* T, int B, int max_partial, cudaStream_t s) {
   const MlpDims d = mlp_dims();
   const MlpImg im = mlp_images();
   const int nloss = 120;
-  k_mlp_loss<<<nloss, 256, 0, s>>>(b.act[kMlpLayers], T, B, b.out_shift, b.out_scale, b.dact, b.loss);
+  k_mlp_loss<<<nloss, 256, 0, s>>>(b.act[kMlpLayers], T, B, b.out_shift, b.out_scale, X, b.skip_out, b.skip_in,
+                                   b.dact, b.loss);
   k_mlp_loss_final<<<1, 32, 0, s>>>(b.loss, nloss);
   // rows per weight-gradient CTA: a multiple of the tensor-core chunk (64 rows)
   int rows_per_block = (B + max_partial - 1) / max_partial;

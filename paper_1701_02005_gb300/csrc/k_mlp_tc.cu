@@ -498,6 +498,7 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_mlp_infer_tc(const float* 
                                                                 const float* __restrict__ in_scale,
                                                                 const float* __restrict__ out_shift,
                                                                 const float* __restrict__ out_scale,
+                                                                int skip_out, int skip_in,
                                                                 float* __restrict__ Y, int* err) {
   extern __shared__ __align__(128) unsigned char tc_raw[];
   __nv_bfloat16* W[kMlpLayers];
@@ -592,7 +593,8 @@ __global__ void __launch_bounds__(kInferThreads, 1) k_mlp_infer_tc(const float* 
 #pragma unroll
           for (int n = 0; n < kMlpOut; ++n) {
             const float yn = fminf(fmaxf(v[n] + bias[n], -kInferClip), kInferClip);
-            Y[(size_t)(b0 + r) * kMlpOut + n] = yn / out_scale[n] + out_shift[n];
+            const float xs = n == skip_out ? __ldg(X + (size_t)(b0 + r) * kMlpIn + skip_in) : 0.f;
+            Y[(size_t)(b0 + r) * kMlpOut + n] = yn / out_scale[n] + out_shift[n] + xs;
           }
         }
       }
@@ -690,8 +692,9 @@ cudaError_t mlp_bwd_data_tc(const float* dz, int N, const __nv_bfloat16* WimgT, 
 
 cudaError_t mlp_infer_tc(const float* X, int B, const __nv_bfloat16* wimg, const float* param,
                          const float* in_shift, const float* in_scale, const float* out_shift, const float* out_scale,
-                         float* Y, int* err, cudaStream_t s) {
+                         int skip_out, int skip_in, float* Y, int* err, cudaStream_t s) {
   if (B < 1) return cudaSuccess;
+  if (skip_out >= kMlpOut || skip_in >= kMlpIn || (skip_out >= 0 && skip_in < 0)) return cudaErrorInvalidValue;
   const MlpDims d = mlp_dims();
   const MlpImg im = mlp_images();
   size_t smem = 0;
@@ -706,7 +709,7 @@ cudaError_t mlp_infer_tc(const float* X, int B, const __nv_bfloat16* wimg, const
   const int ntiles = (B + kTcRows - 1) / kTcRows;
   const unsigned grid = (unsigned)std::min(ntiles, std::max(sms, 1));
   k_mlp_infer_tc<<<grid, kInferThreads, smem, s>>>(X, B, wimg, im, d, param, in_shift, in_scale, out_shift, out_scale,
-                                                   Y, err);
+                                                   skip_out, skip_in, Y, err);
   return cudaGetLastError();
 }
 

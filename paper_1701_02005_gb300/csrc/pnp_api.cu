@@ -2361,6 +2361,13 @@ int pnp_mlp_set_normalization(pnp_mlp* m, const float* in_shift, const float* in
   return PNP_OK;
 }
 
+int pnp_mlp_set_skip(pnp_mlp* m, int out_col, int in_col) {
+  if (!m || out_col >= kMlpOut || in_col >= kMlpIn || (out_col >= 0 && in_col < 0)) return PNP_ERR_ARG;
+  m->b.skip_out = out_col < 0 ? -1 : out_col;
+  m->b.skip_in = out_col < 0 ? -1 : in_col;
+  return PNP_OK;
+}
+
 int pnp_mlp_forward(pnp_mlp* m, const float* X, int B, float* Y) {
   if (!m || !X || !Y || B < 1 || B > m->max_batch) return PNP_ERR_ARG;
   CK(mlp_forward(m->b, X, B, Y, m->stream));
@@ -2370,7 +2377,7 @@ int pnp_mlp_forward(pnp_mlp* m, const float* X, int B, float* Y) {
 int pnp_mlp_gradient(pnp_mlp* m, const float* X, const float* T, int B, float* grad_host, float* loss_host) {
   if (!m || !X || !T || B < 1 || B > m->max_batch) return PNP_ERR_ARG;
   CK(mlp_forward(m->b, X, B, nullptr, m->stream));
-  CK(mlp_backward(m->b, T, B, m->max_partial, m->stream));
+  CK(mlp_backward(m->b, X, T, B, m->max_partial, m->stream));
   if (grad_host) CK(cudaMemcpyAsync(grad_host, m->b.grad, sizeof(float) * m->nparam, cudaMemcpyDeviceToHost, m->stream));
   if (loss_host) CK(cudaMemcpyAsync(loss_host, m->b.loss + 120, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
   CK(cudaStreamSynchronize(m->stream));
@@ -2380,7 +2387,7 @@ int pnp_mlp_gradient(pnp_mlp* m, const float* X, const float* T, int B, float* g
 int pnp_mlp_train_step(pnp_mlp* m, const float* X, const float* T, int B, float lr, float* loss_host) {
   if (!m || !X || !T || B < 1 || B > m->max_batch || !(lr > 0)) return PNP_ERR_ARG;
   CK(mlp_forward(m->b, X, B, nullptr, m->stream));
-  CK(mlp_backward(m->b, T, B, m->max_partial, m->stream));
+  CK(mlp_backward(m->b, X, T, B, m->max_partial, m->stream));
   m->t_adam += 1;
   CK(mlp_adam(m->b, m->nparam, lr, 0.9f, 0.999f, 1e-8f, m->t_adam, m->stream));
   if (loss_host) {

@@ -98,6 +98,8 @@ struct MlpBufs {
   float* loss;         // [partial blocks] then the reduced loss
   float *in_shift, *in_scale, *out_shift, *out_scale;
   int* err;            // device status word (PNP_ERR_TIMEOUT from a bounded tensor-core wait)
+  int skip_out = -1;   // residual output: y[skip_out] = network + x[skip_in] (none when < 0)
+  int skip_in = -1;
 };
 
 // Tensor-core (tcgen05) GEMMs of the MLP (k_mlp_tc.cu).
@@ -111,11 +113,11 @@ cudaError_t mlp_wgrad_tc(const float* dz, int N, const float* in, int K, bool ac
 // The whole network in one persistent kernel, outputs only (inference).
 cudaError_t mlp_infer_tc(const float* X, int B, const __nv_bfloat16* wimg, const float* param,
                          const float* in_shift, const float* in_scale, const float* out_shift, const float* out_scale,
-                         float* Y, int* err, cudaStream_t s);
+                         int skip_out, int skip_in, float* Y, int* err, cudaStream_t s);
 
 cudaError_t mlp_sync_bf16(const MlpBufs& b, size_t nparam, cudaStream_t s);
 cudaError_t mlp_forward(const MlpBufs& b, const float* X, int B, float* Y, cudaStream_t s);
-cudaError_t mlp_backward(const MlpBufs& b, const float* T, int B, int max_partial, cudaStream_t s);
+cudaError_t mlp_backward(const MlpBufs& b, const float* X, const float* T, int B, int max_partial, cudaStream_t s);
 cudaError_t mlp_adam(const MlpBufs& b, size_t nparam, float lr, float beta1, float beta2, float eps, int t,
                      cudaStream_t s);
 

@@ -41,6 +41,7 @@ class MLP:
         n = C.c_size_t()
         B.check(B.pnp_mlp_param_count(C.byref(n)), "pnp_mlp_param_count")
         self.nparam = int(n.value)
+        self.skip = None
 
     def params(self):
         out = np.empty(self.nparam, dtype=np.float32)
@@ -55,6 +56,13 @@ class MLP:
     def set_normalization(self, in_shift, in_scale, out_shift, out_scale):
         arrs = [_fp(x) for x in (in_shift, in_scale, out_shift, out_scale)]
         B.check(B.pnp_mlp_set_normalization(self.m, *[p for _, p in arrs]), "pnp_mlp_set_normalization")
+
+    def set_skip(self, out_col, in_col):
+        """Residual output: output out_col = the network's value + input column in_col
+        (out_col < 0: none); the output normalisation of out_col then describes the
+        difference, the labels' column minus that input."""
+        B.check(B.pnp_mlp_set_skip(self.m, int(out_col), int(in_col)), "pnp_mlp_set_skip")
+        self.skip = (int(out_col), int(in_col)) if out_col >= 0 else None
 
     def _after_torch(self, *tensors):
         """Order the network's stream after the work torch has queued on the tensors
@@ -103,6 +111,19 @@ class MLP:
             self.close()
         except Exception:
             pass
+
+
+PHI_SKIP = (2, 4 * 8)   # first-cell potential: output 2 on feature column 4 ncells (ncells = 8)
+
+
+def residual_targets(T, X, skip):
+    """The targets the network's own outputs learn under a residual output: column
+    skip[0] of T less column skip[1] of X (a copy; T itself when skip is None)."""
+    if skip is None:
+        return T
+    R = T.clone()
+    R[:, skip[0]] -= X[:, skip[1]]
+    return R
 
 
 def features(solver, ncells=8):

@@ -100,6 +100,51 @@ def test_mlp_forward_and_gradient_match_oracle():
     net.close()
 
 
+def test_mlp_residual_output_matches_oracle():
+    """Output 2 as the raw input column 32 plus the network (pnp_mlp_set_skip):
+    the fused inference adds the input after the clip and the output scaling,
+    the loss and gradient take the residual target t_2 - x_32; removing the skip
+    restores the plain outputs; bad columns are rejected."""
+    import torch
+
+    from paper_1701_02005_gb300 import binding as B
+    from paper_1701_02005_gb300.wallmodel import MLP
+
+    net = MLP(512, seed=15)
+    norm = _norm(16)
+    net.set_normalization(*norm)
+    p = net.params()
+    r = seeded.rng(17)
+    X = r.standard_normal((300, 40)).astype(np.float32)
+    X[:, 32] += 5.0   # an input column far from the target's mean: the residual target differs
+    T = r.standard_normal((300, 5)).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    Y0 = net.forward(Xd).cpu().numpy()
+    net.set_skip(2, 32)
+    Y = net.forward(Xd).cpu().numpy()
+    assert np.array_equal(np.delete(Y, 2, 1), np.delete(Y0, 2, 1))
+    assert np.allclose(Y[:, 2], Y0[:, 2] + X[:, 32], rtol=0, atol=1e-6 * np.max(np.abs(Y[:, 2])))
+    Yr, _ = w.forward(p, X, norm, bf16=True, bf16_act=True)
+    Yr = np.clip((Yr - norm[2]) * norm[3], -6, 6) / norm[3] + norm[2]
+    Yr[:, 2] += X[:, 32]
+    assert np.max(np.abs(Y - Yr)) <= 2e-3 * np.max(np.abs(Yr)), np.max(np.abs(Y - Yr)) / np.max(np.abs(Yr))
+    g, loss = net.gradient(Xd, Td)
+    lr, gr = w.loss_and_grad(p, X, T, norm, bf16=True, bf16_act=True, skip=(2, 32))
+    assert abs(loss - lr) <= 2e-3 * lr, (loss, lr)
+    assert abs(lr - w.loss_and_grad(p, X, T, norm, bf16=True, bf16_act=True)[0]) > 1e-2 * lr   # the skip matters
+    sl, _ = w.param_slices()
+    for ws, bs, _, _ in sl:
+        for s_ in (ws, bs):
+            err = np.max(np.abs(g[s_] - gr[s_])) / (np.max(np.abs(gr[s_])) + 1e-12)
+            assert err <= 5e-3, err
+    net.set_skip(-1, 0)
+    assert np.array_equal(net.forward(Xd).cpu().numpy(), Y0)
+    for bad in ((5, 0), (0, 40), (1, -1)):
+        assert B.pnp_mlp_set_skip(net.m, *bad) == B.PNP_ERR_ARG
+    assert net.status() == 0
+    net.close()
+
+
 def test_mlp_training_reduces_loss():
     import torch
 
@@ -128,13 +173,15 @@ def _impulsive(s, g, seed, amp=0.02):
 
 
 def wall_model_case(nfine=(32, 65, 32), ry=4, rxz=2, Re=500.0, dt=0.002, nsteps=200, every=2, train_iters=3000,
-                    passes=3, mode=2, relax=1.0, seed_train=31, seed_judge=32, edl=(0.3, 0.3)):
+                    passes=3, mode=2, relax=1.0, seed_train=31, seed_judge=32, edl=(0.3, 0.3), residual=False):
     """Fine DNS data -> trained network -> coarse runs with and without it, judged
     on the friction coefficient against the fine DNS.  Training pairs the coarse
     solver's own near-wall features with the fine run's filtered labels at the
     same time and initial state: data pass 0 from the coarse run without the
     model, later passes (dataset aggregation) from the coarse run coupled to the
-    previous pass's network in the coupling judged (`mode`, `relax`, `edl`)."""
+    previous pass's network in the coupling judged (`mode`, `relax`, `edl`).
+    residual: the network's potential output is the first-cell feature plus its
+    own value (a residual output)."""
     import torch
 
     from paper_1701_02005_gb300 import binding as B
@@ -145,6 +192,7 @@ def wall_model_case(nfine=(32, 65, 32), ry=4, rxz=2, Re=500.0, dt=0.002, nsteps=
     gc = o.Grid(nx // rxz, (ny - 1) // ry + 1, nz // rxz, 2 * math.pi, math.pi, y_faces=gf.yf[::ry])
     prm = o.Params(Re=Re, lam=0.05, Sc=1.0, V=2.0, beta=0.5)
     sf, sc, sm = _solver(gf, prm), _solver(gc, prm), _solver(gc, prm)
+    skip = wm.PHI_SKIP if residual else None
 
     def couple(s):
         B.check(B.pnp_set_wallmodel_coupling(s.ctx, mode, relax), "pnp_set_wallmodel_coupling")
@@ -165,7 +213,7 @@ def wall_model_case(nfine=(32, 65, 32), ry=4, rxz=2, Re=500.0, dt=0.002, nsteps=
             else:
                 wm.step_with_model(sc, net, every, dt)
         X = torch.cat(Xs)
-        T = torch.cat(Ts)
+        T = wm.residual_targets(torch.cat(Ts), X, skip)   # the normalisation describes these
         if net is None:
             Xh, Th = X.cpu().numpy(), T.cpu().numpy()
             xs, ts = Xh.mean(0), Th.mean(0)
@@ -176,6 +224,9 @@ def wall_model_case(nfine=(32, 65, 32), ry=4, rxz=2, Re=500.0, dt=0.002, nsteps=
             norm = (xs, 1.0 / xsd, ts, 1.0 / tsd)
             net = wm.MLP(nsteps // every * passes * 2 * gc.nz * gc.nx, seed=33)
             net.set_normalization(*norm)
+            if skip is not None:
+                net.set_skip(*skip)
+        T = torch.cat(Ts)   # the network takes the labels themselves
         lr0, lr1 = (2e-3, 5e-4) if rnd == 0 else (1e-3, 3e-4)
         l0 = net.train_step(X, T, lr0, want_loss=True)
         for it in range(train_iters):
@@ -225,13 +276,15 @@ def wall_model_case(nfine=(32, 65, 32), ry=4, rxz=2, Re=500.0, dt=0.002, nsteps=
                 err_phi_coupled=float(np.mean(phi_err["coupled"])))
 
 
-def test_wall_model_gains_over_coarse_solver():
+@pytest.mark.parametrize("residual", [False, True])
+def test_wall_model_gains_over_coarse_solver(residual):
     """The coarse solver coupled to the network (plane-mean predicted wall stress,
     wall-potential offsets and ion-flux transfers at gain 0.3, three passes of
     dataset aggregation) tracks the fine DNS's friction coefficient better than
     the coarse solver alone, its first-cell potential follows the filtered fine
-    one, and the flux transfers keep the ion numbers."""
-    r = wall_model_case()
+    one, and the flux transfers keep the ion numbers; with the potential output
+    absolute or residual (the coarse first-cell potential plus the network)."""
+    r = wall_model_case(residual=residual)
     print("wall model:", {k: v for k, v in r.items() if not k.startswith("cf_")})
     print("cf fine ", np.round(r["cf_fine"], 6).tolist())
     print("cf plain", np.round(r["cf_plain"], 6).tolist())

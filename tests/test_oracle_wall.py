@@ -61,6 +61,35 @@ def test_mlp_gradient_matches_finite_differences():
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])), (i, fd, g[i])
 
 
+def test_residual_output_adds_the_input_column():
+    """skip = (j, i): with zero parameters every output is its shift, and output j
+    the shift plus the raw input x_i; the loss is the mean squared normalised
+    difference of the physical outputs and the targets (so the target of the
+    network's own value is t_j - x_i), and its gradient matches finite differences."""
+    _, total = w.param_slices()
+    r = seeded.rng(5)
+    X = r.standard_normal((9, 40))
+    T = r.standard_normal((9, 5))
+    norm = _norm(6)
+    y0, _ = w.forward(np.zeros(total), X, norm, bf16=False, skip=(2, 32))
+    want = np.tile(norm[2], (9, 1))
+    want[:, 2] += X[:, 32]
+    assert np.allclose(y0, want, rtol=0, atol=1e-15)
+    p = 0.2 * r.standard_normal(total)
+    y, _ = w.forward(p, X, norm, bf16=False, skip=(2, 32))
+    y_plain, _ = w.forward(p, X, norm, bf16=False)
+    assert np.allclose(np.delete(y, 2, 1), np.delete(y_plain, 2, 1), rtol=0, atol=0)
+    loss, g = w.loss_and_grad(p, X, T, norm, bf16=False, skip=(2, 32))
+    direct = lambda q: float(np.mean(((w.forward(q, X, norm, bf16=False, skip=(2, 32))[0] - T) * norm[3]) ** 2))
+    assert abs(loss - direct(p)) <= 1e-12 * loss
+    assert abs(loss - w.loss_and_grad(p, X, T, norm, bf16=False)[0]) > 1e-3 * loss   # the skip matters
+    for i in np.concatenate([r.choice(total, 12, replace=False), [total - 3]]):   # total - 3: output 2's bias
+        e = np.zeros(total)
+        e[i] = 1e-6
+        fd = (direct(p + e) - direct(p - e)) / 2e-6
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])), (i, fd, g[i])
+
+
 def test_adam_first_step_is_signed_lr():
     p = np.array([1.0, -2.0, 3.0])
     g = np.array([0.3, -4.0, 1e-3])
