@@ -323,6 +323,78 @@ def run_large(args, B, Solver, torch):
     return out
 
 
+# The step under the options beyond the headline scheme, each against the default
+# step on the same solver and state (256x193x256 mixed, built-in launch shapes).
+# AF: the periodic x/z sweeps of the approximate factorisation run inside the CN
+# site, on the unfused path: their own time is that site under AF less the same
+# site unfused.  At this workload's taps they run as one pass of circulant
+# convolutions (x and z together) that reads and writes each of the five FP32
+# right-hand sides once: 40 B per cell and substage.
+AF_SWEEP_BYTES = 5 * 8
+
+
+def run_next_rows(args, B, Solver, torch):
+    import numpy as np
+
+    from paper_1701_02005_gb300.solver import profile
+
+    s = Solver(WL["nx"], WL["ny"], WL["nz"], WL["Lx"], WL["Lz"], stretch=WL["stretch"], precision=B.PNP_MIXED)
+    s.set_params(WL["Re"], WL["lam"], WL["Sc"], WL["V"], WL["beta"])
+    s.init_state(B.PNP_IC_PB, WL["seed"], WL["amp"])
+    dt, K, n = WL["dt"], args.next_steps, cells()
+
+    def timed(fn, k=K):
+        fn(1)   # a changed configuration captures its graph on its first step
+        s.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0 = time.perf_counter()
+        e0.record(s.stream)
+        out = fn(k)
+        e1.record(s.stream)
+        s.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        r = {"ms_per_step": ms, "value": n / (ms * 1e-3), "unit": UNIT, "host_ms_per_step":
+             1e3 * (time.perf_counter() - h0) / k, "status": s.diagnostics()["status"]}
+        return r, out
+
+    step = lambda k: s.step(k, dt)
+    base, _ = timed(step)
+    nprof = 3
+    B.check(B.pnp_set_fusion(s.ctx, 0), "pnp_set_fusion")
+    cn_unfused = profile(s, nprof, dt)[0]["cn_thomas"] / (3 * nprof)
+    B.check(B.pnp_set_scheme(s.ctx, B.PNP_SCHEME_AF), "pnp_set_scheme")
+    af, _ = timed(step)
+    cn_af = profile(s, nprof, dt)[0]["cn_thomas"] / (3 * nprof)
+    B.check(B.pnp_set_scheme(s.ctx, B.PNP_SCHEME_CN), "pnp_set_scheme")
+    B.check(B.pnp_set_fusion(s.ctx, 1), "pnp_set_fusion")
+    sweep_ms = cn_af - cn_unfused
+    gbs = AF_SWEEP_BYTES * n / (sweep_ms * 1e-3) / 1e9 if sweep_ms > 0 else None
+    af.update({"vs_default_ms": af["ms_per_step"] - base["ms_per_step"],
+               "cn_site_ms": {"unfused_cn": cn_unfused, "af": cn_af},
+               "sweeps": {"ms_per_substage": sweep_ms, "bytes_per_cell": AF_SWEEP_BYTES, "achieved_gbs": gbs,
+                          "note": "the CN site under AF less the same site unfused; the x and z sweeps of u, v, w, "
+                                  "c+, c- in one pass (each FP32 right-hand side read and written once)"}})
+    # wall potentials varying along the walls (the lift added in the inverse x-transforms)
+    x = (np.arange(WL["nx"]) + 0.5) * WL["Lx"] / WL["nx"]
+    z = (np.arange(WL["nz"]) + 0.5) * WL["Lz"] / WL["nz"]
+    pat = np.outer(np.cos(2 * np.pi * z / WL["Lz"]), np.sin(2 * np.pi * x / WL["Lx"]))
+    s.set_wall_potential(-WL["V"] + 0.5 * pat, WL["V"] + 0.5 * pat[::-1])
+    wp, _ = timed(step)
+    wp.update({"vs_default_ms": wp["ms_per_step"] - base["ms_per_step"],
+               "map": "Phi_wall = -+V + 0.5 cos(2 pi z / Lz) sin(2 pi x / Lx) (top mirrored in z)"})
+    s.set_wall_potential(None, None)
+    # adaptive dt: limits read every 10 steps (each check synchronises), at most twice the fixed dt
+    ad, dts = timed(lambda k: s.step_adaptive(k, 2 * dt, 0.5, 10))
+    dts = np.asarray(dts)
+    ad.update({"dt": {"min": float(dts.min()), "mean": float(dts.mean()), "max": float(dts.max())},
+               "check_every": 10, "cfl": 0.5, "dt_max": 2 * dt,
+               "time_units_per_s": float(dts.sum()) / (1e-3 * ad["host_ms_per_step"] * len(dts)),
+               "time_units_per_s_fixed_dt": dt / (1e-3 * base["ms_per_step"])})
+    s.close()
+    return {"workload": WL_NAME + " (mixed, built-in launch shapes)", "steps": K, "default": base,
+            "approximate_factorisation": af, "wall_potential_map": wp, "adaptive_dt": ad}
+
+
 # --------------------------------------------------------------------------
 # Learned wall model at the workload's scale: the turbulent flow at V = 5
 # resolved on 256x193x256 (mixed precision) is the truth; the coarse grid keeps
@@ -1222,6 +1294,13 @@ def run_ours(args):
     if not args.no_large:
         large = run_large(args, B, Solver, torch)
 
+    next_rows = None
+    if rank == 0 and not args.no_next:
+        try:
+            next_rows = run_next_rows(args, B, Solver, torch)
+        except Exception as exc:  # noqa: BLE001
+            next_rows = {"error": f"{type(exc).__name__}: {exc}"}
+
     mlp = None
     if rank == 0 and not args.no_wallmodel:
         try:
@@ -1256,6 +1335,7 @@ def run_ours(args):
         "mixed_vs_fp64": cmp,
         "ensemble": ensemble,
         "large_case": large,
+        "next_rows": next_rows,
         "wallmodel": wallmodel,
         "wallmodel_network": mlp,
         "cpu_baseline": cpu,
@@ -1316,6 +1396,10 @@ def main():
                          "absolute (0)")
     ap.add_argument("--mlp", action="store_true", help="only the wall-model network's forward / training throughput")
     ap.add_argument("--large-steps", type=int, default=20)
+    ap.add_argument("--no-next", action="store_true",
+                    help="skip the approximate-factorisation, wall-potential-map and adaptive-dt block")
+    ap.add_argument("--next-steps", type=int, default=40)
+    ap.add_argument("--next", action="store_true", help="only that block")
     ap.add_argument("--grid", default=None,
                     help="NX,NY,NZ override of the workload grid (small cases for profiler captures only)")
     args = ap.parse_args()
@@ -1348,6 +1432,14 @@ def main():
         w = run_wallmodel(args, B, Solver, torch)
         w["reduced"] = run_wallmodel_reduced(args, B, Solver, torch)
         print(json.dumps({"wallmodel": w}), flush=True)
+        return 0
+    if args.next:
+        import torch
+
+        from paper_1701_02005_gb300 import binding as B
+        from paper_1701_02005_gb300.solver import Solver
+
+        print(json.dumps({"next_rows": run_next_rows(args, B, Solver, torch)}), flush=True)
         return 0
     return run_ours(args)
 

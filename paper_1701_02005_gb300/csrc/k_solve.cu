@@ -11,6 +11,8 @@
 // is transformed as a length-N/2 complex sequence z_t = x_2t + i x_2t+1 and
 // split into the N/2 + 1 non-negative frequencies.  Forward transforms carry
 // no normalisation; the spectral solve multiplies by 1/(Nx Nz).
+#include <type_traits>
+
 #include "pnp_common.cuh"
 #include "pnp_df.cuh"
 #include "pnp_regfft.cuh"
@@ -1418,6 +1420,165 @@ cudaError_t launch_periodic(const PeriodicArgs<T>& a, const Geo& g, bool zdir, c
 
 template cudaError_t launch_periodic<double>(const PeriodicArgs<double>&, const Geo&, bool, cudaStream_t);
 template cudaError_t launch_periodic<float>(const PeriodicArgs<float>&, const Geo&, bool, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Periodic x / z sweeps as truncated circulant convolutions, both directions in
+// one pass.  Along x (and likewise z) every line of a family solves the same
+// cyclic system (I - s L) with constant coefficients, whose inverse is
+// circulant: x_i = sum_k g_k r_(i-k), g = (I - s L)^-1 e_0 symmetric and
+// decaying like rho^|k|; the host keeps g_0 .. g_K.  The x and z operators act
+// on different axes of a periodic tensor grid and commute, so one pass applies
+// both.  A block owns one plane of one family; a thread owns V consecutive
+// x-columns (one 16-byte vector).  The plane's rows (z) stream through a
+// cp.async ring of kConvRing rows; each row is convolved along x from shared
+// memory (KX taps: the thread's vector and its neighbours', periodic), and
+// each thread convolves its columns along z in a register window of 2 KZ + 1
+// rows.  The march reads rows nz - KZ .. nz - 1 (the window's start), then rows
+// 0 .. nz - 1; the x-results of rows 0 .. KZ - 1 are kept in registers for the
+// window's end.  Each output row is written after the last read of it, so the
+// update is in place.
+// ---------------------------------------------------------------------------
+constexpr int kConvRing = 16;
+
+template <typename T, int KX, int KZ>
+__global__ void __launch_bounds__(512, 1) k_periodic_conv(ConvArgs<T> A, Geo g) {
+  constexpr int V = 16 / sizeof(T);          // columns per thread
+  constexpr int H = (KX + V - 1) / V;        // neighbouring vectors on each side
+  using Vec = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+  extern __shared__ __align__(16) unsigned char conv_smem[];
+  T* ring = reinterpret_cast<T*>(conv_smem);   // [kConvRing][nx]
+  const ConvFam<T>& F = A.f[blockIdx.y];
+  const int j = blockIdx.x;
+  if (j >= F.nplanes) return;   // uniform per block: no barrier is skipped by part of it
+  const int nx = g.nx, nz = g.nz, tid = threadIdx.x, nch = nx / V;
+  T* base = F.r + (size_t)j * nz * nx;
+  const int nseq = nz + KZ;
+  auto row_of = [&](int s) { return (s + nz - KZ) & (nz - 1); };   // nz: a power of two
+  auto issue = [&](int s) {   // one commit group per sequence index, empty past the end
+    if (s < nseq) {
+      const unsigned d = (unsigned)__cvta_generic_to_shared(ring + (size_t)(s % kConvRing) * nx + V * tid);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d),
+                   "l"(base + (size_t)row_of(s) * nx + V * tid)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+#pragma unroll
+  for (int s = 0; s < kConvRing - 1; ++s) issue(s);
+  T gx[KX + 1], gz[KZ + 1];
+#pragma unroll
+  for (int t = 0; t <= KX; ++t) gx[t] = F.gx[t];
+#pragma unroll
+  for (int t = 0; t <= KZ; ++t) gz[t] = F.gz[t];
+  T win[2 * KZ + 1][V], keep[KZ][V];
+#pragma unroll
+  for (int q = 0; q <= 2 * KZ; ++q)
+#pragma unroll
+    for (int o = 0; o < V; ++o) win[q][o] = T(0);
+  // row s: wait for it, convolve it along x, push the result into the window
+  auto row = [&](int s) {
+    asm volatile("cp.async.wait_group %0;" ::"n"(kConvRing - 2) : "memory");   // row s: this thread's copy
+    __syncthreads();   // every thread's copy of row s; every thread done with the slot of row s - 1
+    issue(s + kConvRing - 1);
+    const T* rw = ring + (size_t)(s % kConvRing) * nx;
+    T v[(2 * H + 1) * V];
+#pragma unroll
+    for (int q = -H; q <= H; ++q) {
+      const Vec w = *reinterpret_cast<const Vec*>(rw + V * ((tid + q) & (nch - 1)));
+      const T* wp = reinterpret_cast<const T*>(&w);
+#pragma unroll
+      for (int o = 0; o < V; ++o) v[(q + H) * V + o] = wp[o];
+    }
+#pragma unroll
+    for (int q = 0; q < 2 * KZ; ++q)
+#pragma unroll
+      for (int o = 0; o < V; ++o) win[q][o] = win[q + 1][o];
+#pragma unroll
+    for (int o = 0; o < V; ++o) {
+      const int c = H * V + o;
+      T xv = gx[0] * v[c];
+#pragma unroll
+      for (int t = 1; t <= KX; ++t) xv += gx[t] * (v[c - t] + v[c + t]);
+      win[2 * KZ][o] = xv;
+    }
+  };
+  // output row c from the window's centre
+  auto store = [&](int c) {
+    T y[V];
+#pragma unroll
+    for (int o = 0; o < V; ++o) {
+      y[o] = gz[0] * win[KZ][o];
+#pragma unroll
+      for (int t = 1; t <= KZ; ++t) y[o] += gz[t] * (win[KZ - t][o] + win[KZ + t][o]);
+    }
+    *reinterpret_cast<Vec*>(base + (size_t)c * nx + V * tid) = *reinterpret_cast<const Vec*>(y);
+  };
+  for (int s = 0; s < 2 * KZ; ++s) {   // the window fills; rows 0 .. KZ - 1 are kept
+    row(s);
+#pragma unroll
+    for (int q = 0; q < KZ; ++q)
+      if (s == KZ + q)
+#pragma unroll
+        for (int o = 0; o < V; ++o) keep[q][o] = win[2 * KZ][o];
+  }
+  for (int s = 2 * KZ; s < nseq; ++s) {
+    row(s);
+    store(s - 2 * KZ);
+  }
+#pragma unroll
+  for (int q = 0; q < KZ; ++q) {   // the window's end: rows 0 .. KZ - 1 again
+#pragma unroll
+    for (int p = 0; p < 2 * KZ; ++p)
+#pragma unroll
+      for (int o = 0; o < V; ++o) win[p][o] = win[p + 1][o];
+#pragma unroll
+    for (int o = 0; o < V; ++o) win[2 * KZ][o] = keep[q][o];
+    store(nz - KZ + q);
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");   // no copy outlives the block
+}
+
+template <typename T>
+cudaError_t launch_periodic_conv(const ConvArgs<T>& a, const Geo& g, cudaStream_t s) {
+  constexpr int V = 16 / sizeof(T);
+  const int nt = g.nx / V;
+  if (g.nx % V || nt < 1 || nt > 512 || a.nfam < 1) return cudaErrorInvalidValue;
+  if (a.kz != 2 && a.kz != 4 && a.kz != 8) return cudaErrorInvalidValue;
+  if (2 * a.kz + 1 > g.nz) return cudaErrorInvalidValue;
+  int kx = 0, maxp = 0;
+  for (int q = 0; q < a.nfam; ++q) {
+    kx = a.f[q].kx > kx ? a.f[q].kx : kx;
+    maxp = a.f[q].nplanes > maxp ? a.f[q].nplanes : maxp;
+  }
+  const int KX = kx <= 4 ? 4 : 8;
+  if (kx > kConvMaxK || 2 * KX + 1 > g.nx) return cudaErrorInvalidValue;
+  if (maxp < 1) return cudaSuccess;
+  const size_t smem = (size_t)kConvRing * g.nx * sizeof(T);
+  const dim3 grd((unsigned)maxp, (unsigned)a.nfam);
+  auto go = [&](auto kern) {
+    if (smem > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<grd, nt, smem, s>>>(a, g);
+    return cudaGetLastError();
+  };
+  if (KX == 4) {
+    switch (a.kz) {
+      case 2: return go(k_periodic_conv<T, 4, 2>);
+      case 4: return go(k_periodic_conv<T, 4, 4>);
+      default: return go(k_periodic_conv<T, 4, 8>);
+    }
+  }
+  switch (a.kz) {
+    case 2: return go(k_periodic_conv<T, 8, 2>);
+    case 4: return go(k_periodic_conv<T, 8, 4>);
+    default: return go(k_periodic_conv<T, 8, 8>);
+  }
+}
+
+template cudaError_t launch_periodic_conv<double>(const ConvArgs<double>&, const Geo&, cudaStream_t);
+template cudaError_t launch_periodic_conv<float>(const ConvArgs<float>&, const Geo&, cudaStream_t);
 
 template cudaError_t launch_cn_solves<double>(const Fields<double>&, const Geo&, const CNRows&, const CNRows&,
                                               const CNRows&, cudaStream_t);

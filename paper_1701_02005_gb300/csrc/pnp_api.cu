@@ -149,6 +149,11 @@ struct pnp_ctx {
   double *af_d = nullptr;
   float* af_f = nullptr;
   double af_sc[3][2][2][3] = {};
+  // the sweeps as truncated circulant convolutions: taps g_0 .. g_kConvMaxK of
+  // each inverse (substage, kind, direction) and the taps an FP32 / FP64 pass
+  // needs (-1: more than kConvMaxK, the Thomas sweeps run instead)
+  double af_g[3][2][2][kConvMaxK + 1] = {};
+  int af_kf[3][2][2] = {}, af_kd[3][2][2] = {};
   double af_dt = NAN;
   // the CN forward elimination fused into the mixed stencil: chunk products G
   // [3 substages][3 kinds][ny] for the dt and chunk length they were made for
@@ -569,6 +574,34 @@ int upload_af(pnp_ctx* c, double dt) {
         c->af_sc[l][k][d][0] = lo;
         c->af_sc[l][k][d][1] = lo / gam;
         c->af_sc[l][k][d][2] = 1.0 / (1.0 + q[0] + (lo / gam) * q[n - 1]);
+        // g = (I - s L)^-1 e_0 by the same cyclic solve (Thomas on the corner-free
+        // system, back substitution, Sherman-Morrison correction)
+        std::vector<double> gv(n);
+        double d2 = 0.0;
+        for (int i = 0; i < n; ++i) {
+          d2 = ((i == 0 ? 1.0 : 0.0) - (i ? lo * d2 : 0.0)) * m[i];
+          gv[i] = d2;
+        }
+        const double glast = gv[n - 1];
+        for (int i = n - 2; i >= 0; --i) gv[i] -= cp[i] * gv[i + 1];
+        const double fcor = (gv[0] + (lo / gam) * glast) * c->af_sc[l][k][d][2];
+        for (int i = 0; i < n; ++i) gv[i] -= fcor * q[i];
+        double tot = 0.0;
+        for (int i = 0; i < n; ++i) tot += std::fabs(gv[i]);
+        for (int t = 0; t <= kConvMaxK; ++t)   // symmetric: g_t = g_(n-t)
+          c->af_g[l][k][d][t] = 2 * t < n ? 0.5 * (gv[t] + gv[(n - t) % n]) : 0.0;
+        // taps past which the dropped tail sum_(K < t < n - K) |g_t| is below the
+        // pass's rounding (2^-27 of sum |g| for FP32, 2^-54 for FP64)
+        auto taps = [&](double rel) {
+          for (int K = 0; K <= kConvMaxK && 2 * K + 1 <= n; ++K) {
+            double tail = 0.0;
+            for (int t = K + 1; t < n - K; ++t) tail += std::fabs(gv[t]);
+            if (tail <= rel * tot) return K;
+          }
+          return -1;
+        };
+        c->af_kf[l][k][d] = taps(std::ldexp(1.0, -27));
+        c->af_kd[l][k][d] = taps(std::ldexp(1.0, -54));
       }
     }
   }
@@ -588,6 +621,47 @@ template <typename TR>
 cudaError_t periodic_sweeps(pnp_ctx* c, int l, unsigned fams, TR* ru, TR* rv, TR* rw, TR* rcp, TR* rcm,
                             cudaStream_t st) {
   const size_t P = (size_t)c->g.nz * c->g.nx;
+  // one pass of truncated convolutions when every family's taps fit
+  // (the launch's shapes: 16-byte vectors of columns, at most 512 per row; x
+  // taps rounded up to 4 or 8, z taps to 2, 4 or 8, each within half a line)
+  auto ktaps = [&](int k, int d) { return sizeof(TR) == 8 ? c->af_kd[l][k][d] : c->af_kf[l][k][d]; };
+  const int vec = 16 / (int)sizeof(TR);
+  bool conv = c->g.nx % vec == 0 && c->g.nx / vec <= 512;
+  int kx = 0, kz = 2;
+  for (int k = 0; k < 2; ++k)
+    if (fams & (1u << k)) {
+      if (ktaps(k, 0) < 0 || ktaps(k, 1) < 0) conv = false;
+      kx = std::max(kx, ktaps(k, 0));
+      kz = std::max(kz, ktaps(k, 1));
+    }
+  int kzr = 2;
+  while (kzr < kz) kzr <<= 1;
+  const int kxr = kx <= 4 ? 4 : 8;
+  if (conv && kzr <= kConvMaxK && 2 * kzr + 1 <= c->g.nz && kx <= kConvMaxK && 2 * kxr + 1 <= c->g.nx) {
+    ConvArgs<TR> a{};
+    a.kz = kzr;
+    auto fam = [&](TR* r, int np, int k) {
+      ConvFam<TR> F{};
+      F.r = r;
+      F.nplanes = np;
+      F.kx = ktaps(k, 0);
+      for (int t = 0; t <= kConvMaxK; ++t) {
+        F.gx[t] = t <= kxr ? (TR)c->af_g[l][k][0][t] : TR(0);
+        F.gz[t] = t <= kzr ? (TR)c->af_g[l][k][1][t] : TR(0);
+      }
+      a.f[a.nfam++] = F;
+    };
+    if (fams & 1u) {
+      fam(ru, c->g.nyc, 0);
+      fam(rv + P, c->g.nyc - 1, 0);
+      fam(rw, c->g.nyc, 0);
+    }
+    if (fams & 2u) {
+      fam(rcp, c->g.nyc, 1);
+      fam(rcm, c->g.nyc, 1);
+    }
+    return launch_periodic_conv<TR>(a, c->g, st);
+  }
   for (int d = 0; d < 2; ++d) {
     PeriodicArgs<TR> a{};
     auto fam = [&](TR* r, int np, int k) {

@@ -86,6 +86,28 @@ struct PeriodicArgs {
 template <typename T>
 cudaError_t launch_periodic(const PeriodicArgs<T>& a, const Geo& g, bool zdir, cudaStream_t s);
 
+// The same x and z sweeps as truncated circulant convolutions, both directions
+// in one pass (launch_periodic_conv): the inverse of each constant-coefficient
+// cyclic system is x_i = sum_k g_k r_(i-k), g symmetric and decaying
+// geometrically; taps g_0 .. g_K past which the dropped tail is below the
+// arithmetic's rounding.
+constexpr int kConvMaxK = 8;
+template <typename T>
+struct ConvFam {
+  T* r;          // right-hand side / solution at the family's first plane
+  int nplanes;   // planes of the family (v: the interior faces)
+  int kx;        // x taps beyond the centre (<= kConvMaxK)
+  T gx[kConvMaxK + 1], gz[kConvMaxK + 1];   // g_0 .. g_K along x and z (z: zero past the family's K)
+};
+template <typename T>
+struct ConvArgs {
+  ConvFam<T> f[5];
+  int nfam;
+  int kz;   // z taps beyond the centre of the launch: 1, 2, 4 or 8 (the families' largest, rounded up)
+};
+template <typename T>
+cudaError_t launch_periodic_conv(const ConvArgs<T>& a, const Geo& g, cudaStream_t s);
+
 template <typename TV>
 struct Fields {
   TV *u, *v, *w, *p;
