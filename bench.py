@@ -326,10 +326,10 @@ def run_large(args, B, Solver, torch):
 # The step under the options beyond the headline scheme, each against the default
 # step on the same solver and state (256x193x256 mixed, built-in launch shapes).
 # AF: the periodic x/z sweeps of the approximate factorisation run inside the CN
-# site, on the unfused path: their own time is that site under AF less the same
-# site unfused.  At this workload's taps they run as one pass of circulant
-# convolutions (x and z together) that reads and writes each of the five FP32
-# right-hand sides once: 40 B per cell and substage.
+# site, on the stencil's forward values (the fused path): their own time is that
+# site under AF less the same site without them.  At this workload's taps they
+# run as one pass of circulant convolutions (x and z together) that reads and
+# writes each of the five FP32 arrays once: 40 B per cell and substage.
 AF_SWEEP_BYTES = 5 * 8
 
 
@@ -360,20 +360,23 @@ def run_next_rows(args, B, Solver, torch):
     step = lambda k: s.step(k, dt)
     base, _ = timed(step)
     nprof = 3
-    B.check(B.pnp_set_fusion(s.ctx, 0), "pnp_set_fusion")
-    cn_unfused = profile(s, nprof, dt)[0]["cn_thomas"] / (3 * nprof)
+    cn_default = profile(s, nprof, dt)[0]["cn_thomas"] / (3 * nprof)
     B.check(B.pnp_set_scheme(s.ctx, B.PNP_SCHEME_AF), "pnp_set_scheme")
     af, _ = timed(step)
     cn_af = profile(s, nprof, dt)[0]["cn_thomas"] / (3 * nprof)
-    B.check(B.pnp_set_scheme(s.ctx, B.PNP_SCHEME_CN), "pnp_set_scheme")
+    B.check(B.pnp_set_fusion(s.ctx, 0), "pnp_set_fusion")
+    af_unfused, _ = timed(step)
     B.check(B.pnp_set_fusion(s.ctx, 1), "pnp_set_fusion")
-    sweep_ms = cn_af - cn_unfused
+    B.check(B.pnp_set_scheme(s.ctx, B.PNP_SCHEME_CN), "pnp_set_scheme")
+    sweep_ms = cn_af - cn_default
     gbs = AF_SWEEP_BYTES * n / (sweep_ms * 1e-3) / 1e9 if sweep_ms > 0 else None
     af.update({"vs_default_ms": af["ms_per_step"] - base["ms_per_step"],
-               "cn_site_ms": {"unfused_cn": cn_unfused, "af": cn_af},
+               "unfused_ms_per_step": af_unfused["ms_per_step"],
+               "cn_site_ms": {"default": cn_default, "af": cn_af},
                "sweeps": {"ms_per_substage": sweep_ms, "bytes_per_cell": AF_SWEEP_BYTES, "achieved_gbs": gbs,
-                          "note": "the CN site under AF less the same site unfused; the x and z sweeps of u, v, w, "
-                                  "c+, c- in one pass (each FP32 right-hand side read and written once)"}})
+                          "note": "the CN site under AF less the same site without the sweeps (both fused); the x "
+                                  "and z sweeps of u, v, w, c+, c- in one pass (each FP32 array read and written "
+                                  "once)"}})
     # wall potentials varying along the walls (the lift added in the inverse x-transforms)
     x = (np.arange(WL["nx"]) + 0.5) * WL["Lx"] / WL["nx"]
     z = (np.arange(WL["nz"]) + 0.5) * WL["Lz"] / WL["nz"]

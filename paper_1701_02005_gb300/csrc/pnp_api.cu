@@ -488,9 +488,13 @@ int upload_cn(pnp_ctx* c, double dt) {
 
 // The stencil eliminates forward chunk by chunk (chunk length jc) when the
 // mixed path runs its default policy with the line back substitution.
+// The approximate factorisation fuses too: the y-elimination (chunk-local
+// forward values, chunk carries, back substitution) is linear and the same for
+// every (x, z) column, the x/z sweeps linear and the same for every y-plane, so
+// the sweeps act on the stencil's forward values as they would on the
+// right-hand sides, between the stencil and the back substitution.
 bool cn_fused(const pnp_ctx* c, int* jc_out = nullptr) {
-  if (c->precision != PNP_MIXED || c->policy != PNP_POLICY_DEFAULT || !c->fuse_cn || c->g.lc_cn == 32 ||
-      c->scheme == PNP_SCHEME_AF)
+  if (c->precision != PNP_MIXED || c->policy != PNP_POLICY_DEFAULT || !c->fuse_cn || c->g.lc_cn == 32)
     return false;
   const int jc = mixed_rhs_chunk(c->g, c->rhs_maps_ok);
   if ((c->g.nyc - 1) / jc + 1 > kFusedMaxChunks) return false;
@@ -1001,7 +1005,7 @@ cudaError_t substage_mixed(pnp_ctx* c, double dt, int l) {
   const float* Gl = c->fuseG_d + (size_t)l * kCnKinds * ny;
   const CnFusedG G{Gl + (size_t)kc * ny, Gl + ny, Gl + 2 * ny};
   auto cn = [&](unsigned parts, cudaStream_t s) {
-    if (st.af) {   // the x/z factors first, on the FP32 right-hand sides of these families
+    if (st.af) {   // the x/z factors first, on these families' FP32 right-hand sides (fused: forward values)
       const cudaError_t ea = periodic_sweeps<float>(c, l, (parts & kCnVelocity ? 1u : 0u) | (parts & kCnIons ? 2u : 0u),
                                                     f.ru, f.rv, f.rw, (float*)f.rcp, (float*)f.rcm, s);
       if (ea != cudaSuccess) return ea;

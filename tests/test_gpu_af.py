@@ -52,11 +52,19 @@ def test_af_fp64_matches_the_oracle(shape, nsteps):
     s.close()
 
 
-def test_af_mixed_matches_the_oracle():
+@pytest.mark.parametrize("fusion", [1, 0])
+def test_af_mixed_matches_the_oracle(fusion):
+    """Fused: the x/z sweeps act on the stencil's forward values, between the
+    stencil and the back substitution (the y-elimination and the sweeps are
+    linear maps along different axes and commute); unfused: on the stored
+    right-hand sides, before the y-solves."""
+    from paper_1701_02005_gb300 import binding as B
+
     g = o.Grid(64, 41, 32, 2 * math.pi, math.pi, stretch=2.0)
     prm = o.Params(Re=300.0, lam=0.05, Sc=1.0, V=2.0, beta=0.5, af=True)
     st = o.initial_state(g, prm, o.IC_PB, seed=44, amp=0.1)
     s = _solver(g, prm, 1)
+    B.check(B.pnp_set_fusion(s.ctx, fusion), "pnp_set_fusion")
     s.set_state(st)
     s.step(5, 0.005)
     ref = o.step(g, prm, st, 0.005, 5)
