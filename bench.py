@@ -15,6 +15,7 @@ the host cores instead (bounded slab samples of the same workload).
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -1232,6 +1233,15 @@ def run_ours(args):
         state_bytes = sum(h.numel() * 8 for h in host.values())
 
         def e2e_run(pipelined):
+            # no collection pause of the Python heap inside the timed region
+            gc.collect()
+            gc.disable()
+            try:
+                return e2e_timed(pipelined)
+            finally:
+                gc.enable()
+
+        def e2e_timed(pipelined):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for nm in names:
