@@ -1243,9 +1243,12 @@ def run_ours(args):
 
         def e2e_timed(pipelined):
             torch.cuda.synchronize()
+            u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             t0 = time.perf_counter()
+            u0.record(s.stream)
             for nm in names:
                 B.check(B.pnp_set_state(s.ctx, FIELD_NAMES[nm], host[nm].data_ptr(), 0), "pnp_set_state")
+            u1.record(s.stream)
             s.synchronize()
             t1 = time.perf_counter()
             if pipelined:
@@ -1270,7 +1273,8 @@ def run_ours(args):
             out = torch.empty(host["u"].shape, dtype=torch.float64).pin_memory()
             B.check(B.pnp_get_state(s.ctx, B.PNP_U, out.data_ptr(), 0), "pnp_get_state")
             t3 = time.perf_counter()
-            return {"value": n_cells * Ke / (t3 - t0), "set_state_s": t1 - t0, "steps_s": t2 - t1,
+            return {"value": n_cells * Ke / (t3 - t0), "set_state_s": t1 - t0,
+                    "set_state_device_s": u0.elapsed_time(u1) / 1e3, "steps_s": t2 - t1,
                     "ms_per_step_in_loop": 1e3 * (t2 - t1) / Ke, "get_state_s": t3 - t2,
                     "d2h": out.numel() * 8, "status": last["status"]}
 
@@ -1290,9 +1294,11 @@ def run_ours(args):
         diag_ms = q0.elapsed_time(q1) / 20
         e2e = {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": state_bytes / Ke,
                "d2h_bytes_per_step": 128 + r["d2h"] / Ke, "steps": Ke, "last_step_status": r["status"],
-               "phases": {**{k: r[k] for k in ("set_state_s", "steps_s", "ms_per_step_in_loop", "get_state_s")},
+               "phases": {**{k: r[k] for k in ("set_state_s", "set_state_device_s", "steps_s", "ms_per_step_in_loop",
+                                               "get_state_s")},
                           "diagnostics_ms_alone": diag_ms},
                "runs": [q["value"] for q in runs],
+               "runs_set_state_s": [[q["set_state_s"], q["set_state_device_s"]] for q in runs],
                "synchronous_diagnostics": {k: r_sync[k] for k in ("value", "set_state_s", "ms_per_step_in_loop")},
                "note": "set_state of all 12 fields from pinned host, then per step pnp_step + "
                        "pnp_diagnostics_post (D2H of the step's diagnostics into a pinned record, read one step "

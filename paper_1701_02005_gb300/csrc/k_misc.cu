@@ -105,6 +105,9 @@ cudaError_t launch_init_fields(const Fields<TV>& f, const Geo& g, const Metrics&
 // ---------------------------------------------------------------------------
 constexpr int kDiagSlots = 14;
 constexpr int kDiagThreads = 256;
+constexpr int kDiagPairs = 15;   // paired (8-byte) inputs per cell pair of the mixed diagnostics
+// its dynamic shared memory: two staging slots per thread, or the reduction buffer after the sweep
+constexpr size_t kDiagMixedSmem = (size_t)2 * (kDiagPairs * 8 + 2 * 4) * kDiagThreads;
 
 __device__ __forceinline__ bool diag_is_max(int q) { return q == 4 || q == 8 || q == 9 || q == 12 || q == 13; }
 
@@ -185,30 +188,67 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Fields<TV> f, Geo
 // reference part of the ion numbers, sum_j c_ref(j) dy_j over the plane, is
 // added on the host.  The divergence is summed in df from exact differences
 // (TwoSum) times df coefficients, so that its small value keeps its FP64
-// accuracy -- evaluated only where an FP32 estimate plus its rounding bound
-// could reach the running maximum, which gives the same maximum; the minimum
-// concentration is FP32; a value is counted non-finite when any input read for
-// it is.  Nx and Nz are powers of two.
+// accuracy; the minimum concentration is FP32; a cell is counted non-finite
+// when any input read for it is.  Each thread stages its next cell pair's
+// inputs in its own shared-memory slot by cp.async while it sums the current
+// pair.  Nx and Nz are powers of two.
 __global__ void __launch_bounds__(kDiagThreads, 2) k_diag_partial_mixed(Fields<float> f, Shadows sh,
                                                                         const float* __restrict__ cref_p,
                                                                         const float* __restrict__ cref_m,
                                                                         const float* __restrict__ dPref,
                                                                         const float2* __restrict__ wgt, Geo g,
                                                                         double* partial) {
-  __shared__ double shr[kDiagSlots * kDiagThreads];
+  // dynamic shared memory: the threads' staging slots during the sweep, the
+  // block reduction's buffer after it
+  extern __shared__ __align__(16) unsigned char diag_smem[];
+  double* shr = reinterpret_cast<double*>(diag_smem);
+  float2* st2 = reinterpret_cast<float2*>(diag_smem);                                            // [2][kDiagPairs][threads]
+  float* st1 = reinterpret_cast<float*>(diag_smem + (size_t)2 * kDiagPairs * kDiagThreads * 8);  // [2][2][threads]
+  const int tid = threadIdx.x;
   dfl sum[7] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};   // 0-3, 5, 10, 11
   float maxdiv = 0.f, bad = 0.f, cmin = 3.0e38f, maxrate = 0.f, maxdphi = 0.f, maxmig = 0.f, maxcsum = 0.f;
   const int nx = g.nx, nz = g.nz, lnz = __ffs(nz) - 1;
   const size_t P = (size_t)nz * nx;
   const int rows = g.nyc * nz, per = (rows + gridDim.x - 1) / gridDim.x;
   const int r0 = blockIdx.x * per, r1 = min(rows, r0 + per);
-  // two cells per thread (paired 8-byte loads); the block's threads cover
-  // `rpp` rows at a time, each thread keeping to one row in rpp
-  const int tpr = min((int)blockDim.x, nx / 2), rpp = (int)blockDim.x / tpr;
-  const int sub = (int)threadIdx.x / tpr, tx = (int)threadIdx.x - sub * tpr;
+  // two cells per thread (paired 8-byte copies); the block's threads cover
+  // `rpp` rows at a time, each thread keeping to one row in rpp and taking
+  // `nib` cell pairs of it
+  const int tpr = min((int)blockDim.x, nx / 2), rpp = (int)blockDim.x / tpr, nib = nx / (2 * tpr);
+  const int sub = tid / tpr, tx = tid - sub * tpr;
   // 1/dx, 1/dz as df pairs (per thread, once)
   const float idxh = (float)g.idx, idzh = (float)g.idz;
   const dfl idx{idxh, (float)(g.idx - (double)idxh)}, idz{idzh, (float)(g.idz - (double)idzh)};
+  // work item q of this thread: row r, first cell i
+  auto item = [&](int q, int& r, int& i) {
+    const int a = q / nib, b = q - a * nib;
+    r = r0 + sub + rpp * a;
+    i = 2 * tx + 2 * tpr * b;
+    return sub < rpp && r < r1;
+  };
+  // the item's inputs into this thread's staging slot (only this thread reads
+  // them: no barrier); one commit group per item
+  auto issue = [&](int slot, int r, int i) {
+    const int j = r >> lnz, kp = ((r & (nz - 1)) + 1) & (nz - 1);
+    const size_t c = (size_t)r * nx + i, ckp = ((size_t)j * nz + kp) * nx + i;
+    const size_t ce = (size_t)r * nx + ((i + 2) & (nx - 1));
+    const float* src[kDiagPairs] = {f.u + c,   f.w + c,    f.p + c,    sh.phi + c, f.v + c,    f.v + c + P,
+                                    f.w + ckp, sh.phi + ckp, sh.cp + c, sh.cpL + c, sh.cm + c, sh.cmL + c,
+                                    sh.Hcp + c, sh.Hcm + c, sh.phi + c + P};
+    const int npair = j + 1 < g.nyc ? kDiagPairs : kDiagPairs - 1;   // no plane above the last one
+#pragma unroll
+    for (int k = 0; k < kDiagPairs; ++k) {
+      if (k >= npair) continue;
+      const unsigned d = (unsigned)__cvta_generic_to_shared(st2 + ((size_t)slot * kDiagPairs + k) * kDiagThreads + tid);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src[k]) : "memory");
+    }
+    const float* one[2] = {f.u + ce, sh.phi + ce};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const unsigned d = (unsigned)__cvta_generic_to_shared(st1 + ((size_t)slot * 2 + k) * kDiagThreads + tid);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(one[k]) : "memory");
+    }
+  };
   // the current run of rows in plane jr: sums still to be weighted
   int jr = (r0 + sub) >> lnz;
   dfl ruw{0.f, 0.f}, rv{0.f, 0.f}, rcp{0.f, 0.f}, rcm{0.f, 0.f}, ru{0.f, 0.f}, rhp{0.f, 0.f}, rhm{0.f, 0.f};
@@ -225,41 +265,63 @@ __global__ void __launch_bounds__(kDiagThreads, 2) k_diag_partial_mixed(Fields<f
     if (jr == g.nyc - 1) sum[1] = df_add(sum[1], ru);
     ruw = rv = rcp = rcm = ru = rhp = rhm = dfl{0.f, 0.f};
   };
-  for (int r = r0 + sub; r < r1 && sub < rpp; r += rpp) {
-    const int j = r >> lnz, k = r & (nz - 1);
+  int r = 0, i = 0;
+  bool have = item(0, r, i);
+  if (have) issue(0, r, i);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  for (int q = 0; have; ++q) {
+    int rn = 0, in = 0;
+    const bool hn = item(q + 1, rn, in);
+    if (hn) issue((q + 1) & 1, rn, in);   // the next item's copies fly while this one is summed
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 1;" ::: "memory");   // this item's copies (this thread's own)
+    const int j = r >> lnz;
     if (j != jr) {
       flush();
       jr = j;
     }
     any = true;
-    const int kp = (k + 1) & (nz - 1);
+    const bool wall_row = j == 0 || j == g.nyc - 1;   // the only rows whose sum of u is kept
     const float2 iyw = wgt[2 * g.ny + j];
+    const dfl iy{iyw.x, iyw.y};
     const float crp = cref_p[j], crm = cref_m[j];
-    const float dpy = j + 1 < g.nyc ? dPref[j + 1] : 0.f;   // Phi_ref step across face j+1 (interior faces)
-    const float ihy = j + 1 < g.nyc ? 1.f / wgt[g.ny + j + 1].x : 0.f;   // 1 / h of that face
-    const size_t rowo = (size_t)r * nx, rowkp = ((size_t)j * nz + kp) * nx;
     const bool top = j + 1 < g.nyc;
+    const float dpy = top ? dPref[j + 1] : 0.f;   // Phi_ref step across face j+1 (interior faces)
+    const float ihy = top ? 1.f / wgt[g.ny + j + 1].x : 0.f;   // 1 / h of that face
+    const float2* s2 = st2 + (size_t)(q & 1) * kDiagPairs * kDiagThreads + tid;
+    const float* s1 = st1 + (size_t)(q & 1) * 2 * kDiagThreads + tid;
+    const float2 u = s2[0], w = s2[kDiagThreads], p = s2[2 * kDiagThreads], ph = s2[3 * kDiagThreads];
+    const float2 v0 = s2[4 * kDiagThreads], v1 = s2[5 * kDiagThreads], wn = s2[6 * kDiagThreads];
+    const float2 phn = s2[7 * kDiagThreads], Sp = s2[8 * kDiagThreads], Lp = s2[9 * kDiagThreads];
+    const float2 Sm = s2[10 * kDiagThreads], Lm = s2[11 * kDiagThreads], Hp = s2[12 * kDiagThreads];
+    const float2 Hm = s2[13 * kDiagThreads];
+    const float2 phu = top ? s2[14 * kDiagThreads] : make_float2(0.f, 0.f);
+    const float ue2 = s1[0], phe2 = s1[kDiagThreads];
     // one cell: its values and the neighbours east (+x), north (+z) and above (+y)
     auto cell = [&](float u, float ue, float w, float wn, float p, float ph, float phe, float phn, float phu,
                     float v0, float v1, float Sp, float Lp, float Sm, float Lm, float Hp, float Hm) {
-      ru = df_add_fast(ru, dfl{u, 0.f});
+      if (wall_row) ru = df_add_fast(ru, dfl{u, 0.f});
       ruw = df_add_fast(ruw, df_add_fast(df_prod(u, u), df_prod(w, w)));
       rv = df_add_fast(rv, df_prod(v0, v0));
       rcp = df_add_fast(rcp, dfl{Sp, Lp});
       rcm = df_add_fast(rcm, dfl{Sm, Lm});
-      // the divergence: an FP32 estimate with a bound on its rounding error; the
-      // exact (df) value only where the estimate could reach the running maximum
-      const float t1 = (ue - u) * idxh, t2 = (v1 - v0) * iyw.x, t3 = (wn - w) * idzh;
-      const float est = t1 + t2 + t3;
-      const float bound = 4e-7f * (fabsf(t1) + fabsf(t2) + fabsf(t3)) + 1e-30f;
-      if (!(fabsf(est) + bound < maxdiv)) {
-        const dfl dv = df_add(df_add(df_mul(df_two_sum(ue, -u), idx), df_mul(df_two_sum(v1, -v0), dfl{iyw.x, iyw.y})),
-                              df_mul(df_two_sum(wn, -w), idz));
-        maxdiv = fmaxf(maxdiv, fabsf(__fadd_rn(dv.h, dv.l)));
-      }
-      if (!isfinite(u) || !isfinite(w) || !isfinite(Sp) || !isfinite(Sm) || !isfinite(p) || !isfinite(ph) ||
-          !isfinite(v0) || !isfinite(est))
-        bad += 1.f;
+      // the divergence of the stored fields in df: exact differences (TwoSum),
+      // exact leading products (TwoProduct) and the cross terms with the df
+      // coefficients, the three leading parts summed by TwoSum, the rest in FP32
+      const dfl a1 = df_two_sum(ue, -u), a2 = df_two_sum(v1, -v0), a3 = df_two_sum(wn, -w);
+      const dfl p1 = df_prod(a1.h, idx.h), p2 = df_prod(a2.h, iy.h), p3 = df_prod(a3.h, idz.h);
+      const dfl s1s = df_two_sum(p1.h, p2.h), s2s = df_two_sum(s1s.h, p3.h);
+      float lo = __fadd_rn(__fadd_rn(p1.l, p2.l), p3.l);
+      lo = __fmaf_rn(a1.h, idx.l, lo);
+      lo = __fmaf_rn(a1.l, idx.h, lo);
+      lo = __fmaf_rn(a2.h, iy.l, lo);
+      lo = __fmaf_rn(a2.l, iy.h, lo);
+      lo = __fmaf_rn(a3.h, idz.l, lo);
+      lo = __fmaf_rn(a3.l, idz.h, lo);
+      const float dv = __fadd_rn(s2s.h, __fadd_rn(lo, __fadd_rn(s1s.l, s2s.l)));
+      maxdiv = fmaxf(maxdiv, fabsf(dv));
+      // dv is non-finite when u, ue, v0, v1, w or wn is
+      if (!isfinite(dv) || !isfinite(Sp) || !isfinite(Sm) || !isfinite(p) || !isfinite(ph)) bad += 1.f;
       cmin = fminf(cmin, fminf(crp + Sp, crm + Sm));
       maxrate = fmaxf(maxrate, fabsf(0.5f * (u + ue)) * idxh + fabsf(0.5f * (v0 + v1)) * iyw.x +
                                    fabsf(0.5f * (w + wn)) * idzh);
@@ -271,20 +333,14 @@ __global__ void __launch_bounds__(kDiagThreads, 2) k_diag_partial_mixed(Fields<f
       rhp = df_add_fast(rhp, dfl{Hp, 0.f});
       rhm = df_add_fast(rhm, dfl{Hm, 0.f});
     };
-    for (int i = 2 * tx; i < nx; i += 2 * tpr) {
-      const size_t c = rowo + i;
-      const int i2 = (i + 2) & (nx - 1);
-      auto ld2 = [](const float* q, size_t o) { return *reinterpret_cast<const float2*>(q + o); };
-      const float2 u = ld2(f.u, c), w = ld2(f.w, c), p = ld2(f.p, c), ph = ld2(sh.phi, c);
-      const float2 v0 = ld2(f.v, c), v1 = ld2(f.v, c + P), wn = ld2(f.w, rowkp + i), phn = ld2(sh.phi, rowkp + i);
-      const float2 Sp = ld2(sh.cp, c), Lp = ld2(sh.cpL, c), Sm = ld2(sh.cm, c), Lm = ld2(sh.cmL, c);
-      const float2 Hp = ld2(sh.Hcp, c), Hm = ld2(sh.Hcm, c);
-      const float2 phu = top ? ld2(sh.phi, c + P) : make_float2(0.f, 0.f);
-      const float ue2 = f.u[rowo + i2], phe2 = sh.phi[rowo + i2];
-      cell(u.x, u.y, w.x, wn.x, p.x, ph.x, ph.y, phn.x, phu.x, v0.x, v1.x, Sp.x, Lp.x, Sm.x, Lm.x, Hp.x, Hm.x);
-      cell(u.y, ue2, w.y, wn.y, p.y, ph.y, phe2, phn.y, phu.y, v0.y, v1.y, Sp.y, Lp.y, Sm.y, Lm.y, Hp.y, Hm.y);
-    }
+    cell(u.x, u.y, w.x, wn.x, p.x, ph.x, ph.y, phn.x, phu.x, v0.x, v1.x, Sp.x, Lp.x, Sm.x, Lm.x, Hp.x, Hm.x);
+    cell(u.y, ue2, w.y, wn.y, p.y, ph.y, phe2, phn.y, phu.y, v0.y, v1.y, Sp.y, Lp.y, Sm.y, Lm.y, Hp.y, Hm.y);
+    r = rn;
+    i = in;
+    have = hn;
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();   // the staging slots become the reduction's buffer
   if (any) flush();
   // the top wall face of v
   const size_t nc = (size_t)g.nyc * P;
@@ -352,7 +408,10 @@ cudaError_t launch_diagnostics_mixed(const Fields<float>& f, const Shadows& sh, 
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   const int nb = std::max(1, std::min(npartial, 2 * sms));
-  k_diag_partial_mixed<<<nb, kDiagThreads, 0, s>>>(f, sh, cref_p, cref_m, dPref, wgt, g, partial);
+  static_assert(kDiagMixedSmem >= (size_t)kDiagSlots * kDiagThreads * sizeof(double), "reduction buffer");
+  e = cudaFuncSetAttribute(k_diag_partial_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiagMixedSmem);
+  if (e != cudaSuccess) return e;
+  k_diag_partial_mixed<<<nb, kDiagThreads, kDiagMixedSmem, s>>>(f, sh, cref_p, cref_m, dPref, wgt, g, partial);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_diag_final<<<1, kDiagThreads, 0, s>>>(partial, nb, out, status, lim);
