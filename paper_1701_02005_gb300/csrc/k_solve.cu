@@ -351,6 +351,19 @@ __global__ void __launch_bounds__(256) k_fft_x_fwd_reg(SrcArgs<T, TV> src, Geo g
   }
 }
 
+// n consecutive outputs (n = 2 or 4; out aligned to n elements) in vector stores.
+template <typename TO, int N>
+__device__ __forceinline__ void store_out(TO* out, const TO (&y)[N]) {
+  if constexpr (sizeof(TO) == 4 && N == 4) {
+    *reinterpret_cast<float4*>(out) = make_float4(y[0], y[1], y[2], y[3]);
+  } else if constexpr (sizeof(TO) == 4 && N == 2) {
+    *reinterpret_cast<float2*>(out) = make_float2(y[0], y[1]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < N; q += 2) *reinterpret_cast<double2*>(out + q) = make_double2(y[q], y[q + 1]);
+  }
+}
+
 // Inverse: thread g forms the pre-processed z_t (from X_t and conj X_{NH-t})
 // for t = g + G r straight from the spectrum, runs the inverse transform and
 // writes x_2t, x_2t+1 of t = k1 + R1 k2.
@@ -405,33 +418,43 @@ __global__ void __launch_bounds__(256) k_fft_x_inv_reg(PoissonDst dst, const cpl
   const size_t base = (size_t)row * g.nx;
   const double add = dst == PoissonDst::Potential ? V * mt.yc[j] : 0.0;
   const T addT = dst == PoissonDst::PotentialShadow ? (T)plane_add[j] : T(0);
+  // the thread's PER transforms first, so that the 2 PER consecutive outputs of
+  // each k2 leave in one vector store (k1 = gi PER + p: pairs side by side)
+  cplx<T> w[PER][G];
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int k1 = gi * PER + p;
-    cplx<T> w[G];
 #pragma unroll
-    for (int q = 0; q < G; ++q) w[q] = xr[k1 * (G + 1) + q];
-    rfft::dft<true, G>(w);
-    rfft::static_for<0, G>([&](auto kc) {
-      constexpr int k2 = decltype(kc)::value;
-      const cplx<T> z = w[rfft::bitrev(k2, G)];
-      const size_t o = base + 2 * (size_t)(k1 + R1 * k2);
-      if (dst == PoissonDst::PotentialShadow) {
-        TO a0 = (TO)(addT + z.x), a1 = (TO)(addT + z.y);
-        if (cell_add) { a0 += cell_add[o]; a1 += cell_add[o + 1]; }
-        out[o] = a0;
-        out[o + 1] = a1;
-      } else if (dst == PoissonDst::Potential) {
-        TO a0 = (TO)(add + (double)z.x), a1 = (TO)(add + (double)z.y);
-        if (cell_add) { a0 += cell_add[o]; a1 += cell_add[o + 1]; }
-        out[o] = a0;
-        out[o + 1] = a1;
-      } else {
-        out[o] = (TO)z.x;
-        out[o + 1] = (TO)z.y;
-      }
-    });
+    for (int q = 0; q < G; ++q) w[p][q] = xr[k1 * (G + 1) + q];
+    rfft::dft<true, G>(w[p]);
   }
+  rfft::static_for<0, G>([&](auto kc) {
+    constexpr int k2 = decltype(kc)::value;
+    const size_t o = base + 2 * (size_t)(gi * PER + R1 * k2);
+    TO y[2 * PER];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const cplx<T> z = w[p][rfft::bitrev(k2, G)];
+      TO a0, a1;
+      if (dst == PoissonDst::PotentialShadow) {
+        a0 = (TO)(addT + z.x);
+        a1 = (TO)(addT + z.y);
+      } else if (dst == PoissonDst::Potential) {
+        a0 = (TO)(add + (double)z.x);
+        a1 = (TO)(add + (double)z.y);
+      } else {
+        a0 = (TO)z.x;
+        a1 = (TO)z.y;
+      }
+      if (dst != PoissonDst::Plain && cell_add) {
+        a0 += cell_add[o + 2 * p];
+        a1 += cell_add[o + 2 * p + 1];
+      }
+      y[2 * p] = a0;
+      y[2 * p + 1] = a1;
+    }
+    store_out<TO, 2 * PER>(out + o, y);
+  });
 }
 
 // Rows per 128-thread block of the register x-transforms (smaller blocks share
