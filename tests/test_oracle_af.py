@@ -1,6 +1,7 @@
 """Pins of the oracle's approximate factorisation (x/z viscous and diffusive
 terms implicit, (I - s L_x)(I - s L_z)(I - s L_y) dq = r): the cyclic
-tridiagonal solve against a dense solve, laminar Couette still an exact steady
+tridiagonal solve against a dense solve and against the closed-form kernel of
+the symmetric operator's inverse, laminar Couette still an exact steady
 state, the closed-form amplification of a pure-diffusion ion mode, and the
 factored step's agreement with the unfactored one as dt -> 0."""
 import math
@@ -23,6 +24,36 @@ def test_periodic_solve_against_a_dense_solve():
         got = o.periodic_solve(lo, di, up, r, axis=1)
         want = np.einsum("ij,ajb->aib", np.linalg.inv(A), r)
         assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want)), n
+
+
+def test_periodic_solve_of_the_symmetric_operator_has_the_closed_form_kernel():
+    """(I - s L) on a uniform periodic line, lo = up = -beta, di = 1 + 2 beta: the
+    response to e_0 is g_k = (rho^k + rho^(n-k)) / ((1 - rho^n) beta (1/rho - rho)),
+    rho the smaller root of beta rho^2 - (1 + 2 beta) rho + beta = 0 (the free-space
+    kernel rho^|k| / (beta (1/rho - rho)) summed over the periodic images).  The
+    kernel is symmetric and decays geometrically, so a few taps reproduce the cyclic
+    solve to rounding where beta is small."""
+    for n, beta in ((16, 0.05), (64, 0.3), (256, 5e-4), (32, 4.0)):
+        e0 = np.zeros((n, 1))
+        e0[0, 0] = 1.0
+        g = o.periodic_solve(-beta, 1.0 + 2.0 * beta, -beta, e0, axis=0)[:, 0]
+        # the roots' product is 1 and their difference sqrt(d^2 - 4 beta^2) / beta:
+        # rho and beta (1/rho - rho) without cancellation at small beta
+        d = 1.0 + 2.0 * beta
+        disc = math.sqrt(d * d - 4.0 * beta * beta)
+        rho = 2.0 * beta / (d + disc)
+        k = np.arange(n)
+        want = (rho ** k + rho ** (n - k)) / ((1.0 - rho ** n) * disc)
+        assert np.max(np.abs(g - want)) <= 1e-13 * np.max(np.abs(want)), (n, beta)
+        assert np.max(np.abs(g[1:] - g[1:][::-1])) <= 1e-14 * g[0]   # g_k = g_(n-k)
+    # at the 256x193x256 workload's x-operator (beta ~ 5e-4) three taps past the
+    # centre leave a tail below 2^-27 of the kernel's sum
+    n, beta = 256, 5e-4
+    e0 = np.zeros((n, 1))
+    e0[0, 0] = 1.0
+    g = np.abs(o.periodic_solve(-beta, 1.0 + 2.0 * beta, -beta, e0, axis=0)[:, 0])
+    assert g[4:n - 3].sum() <= 2.0 ** -27 * g.sum()
+    assert g[3:n - 2].sum() > 2.0 ** -54 * g.sum()   # and FP64 needs more of them
 
 
 def test_af_keeps_laminar_couette_exact():
