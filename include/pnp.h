@@ -230,9 +230,15 @@ int pnp_step_adaptive(pnp_ctx* ctx, int nsteps, double dt_max, double cfl, int c
  * (the wall-normal Thomas solves), x/z terms explicit in the RK3 right-hand
  * side.  PNP_SCHEME_AF: Crank-Nicolson in all three directions, approximately
  * factorised, (I - s L_x)(I - s L_z)(I - s L_y) dq = r with r holding the
- * explicit half of the full Laplacian: periodic (cyclic) tridiagonal sweeps in
- * x and z before the wall-normal solve, which lifts the x/z viscous and
- * diffusive stability limits.  Migration and advection stay explicit. */
+ * explicit half of the full Laplacian: periodic (cyclic) tridiagonal solves in
+ * x and z, which lift the x/z viscous and diffusive stability limits.
+ * Migration and advection stay explicit.  The cyclic systems have constant
+ * coefficients, so their inverses are circulant: where the inverse's kernel
+ * falls below the arithmetic's rounding within eight taps, both directions run
+ * as one pass of truncated convolutions (the same result to rounding), else as
+ * cyclic Thomas sweeps.  With the fused CN elimination (pnp_set_fusion) the x/z
+ * solves act on the stencil's forward-elimination values, which they commute
+ * with. */
 enum { PNP_SCHEME_CN = 0, PNP_SCHEME_AF = 1 };
 int pnp_set_scheme(pnp_ctx* ctx, int scheme);
 
