@@ -178,6 +178,36 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(Fields<TV> f, Geo
     for (int q = 0; q < kDiagSlots; ++q) partial[(size_t)blockIdx.x * kDiagSlots + q] = sh[q * kDiagThreads];
 }
 
+// Two df values side by side, one per lane of a float2, for the packed FP32
+// instructions (each lane rounded to nearest, never contracted): the same
+// error-free transforms as pnp_df.cuh, lane by lane.
+struct dfl2 {
+  float2 h, l;
+};
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) {   // a - b, one rounding
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_abs(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ dfl2 p_two_sum(float2 a, float2 b) {
+  const float2 s = p_add(a, b), bb = p_sub(s, a);
+  return {s, p_add(p_sub(a, p_sub(s, bb)), p_sub(b, bb))};
+}
+__device__ __forceinline__ dfl2 p_fast_two_sum(float2 a, float2 b) {
+  const float2 s = p_add(a, b);
+  return {s, p_sub(b, p_sub(s, a))};
+}
+__device__ __forceinline__ dfl2 p_add_fast(dfl2 x, dfl2 y) {
+  const dfl2 s = p_two_sum(x.h, y.h);
+  return p_fast_two_sum(s.h, p_add(s.l, p_add(x.l, y.l)));
+}
+__device__ __forceinline__ dfl2 p_prod(float2 a, float2 b) {
+  const float2 p = p_mul(a, b);
+  return {p, p_fma(a, b, p_mul(p, make_float2(-1.f, -1.f)))};
+}
+
 // Mixed precision: the same partial sums straight from the FP32 fields and the
 // df ion state c = c_ref + S + L, with no FP64 copy of the state and no FP64
 // arithmetic per cell.  A block takes a contiguous range of x-rows, so a
@@ -219,6 +249,8 @@ __global__ void __launch_bounds__(kDiagThreads, 2) k_diag_partial_mixed(Fields<f
   // 1/dx, 1/dz as df pairs (per thread, once)
   const float idxh = (float)g.idx, idzh = (float)g.idz;
   const dfl idx{idxh, (float)(g.idx - (double)idxh)}, idz{idzh, (float)(g.idz - (double)idzh)};
+  const float2 idxh2 = make_float2(idx.h, idx.h), idxl2 = make_float2(idx.l, idx.l);
+  const float2 idzh2 = make_float2(idz.h, idz.h), idzl2 = make_float2(idz.l, idz.l);
   // work item q of this thread: row r, first cell i
   auto item = [&](int q, int& r, int& i) {
     const int a = q / nib, b = q - a * nib;
@@ -251,19 +283,22 @@ __global__ void __launch_bounds__(kDiagThreads, 2) k_diag_partial_mixed(Fields<f
   };
   // the current run of rows in plane jr: sums still to be weighted
   int jr = (r0 + sub) >> lnz;
-  dfl ruw{0.f, 0.f}, rv{0.f, 0.f}, rcp{0.f, 0.f}, rcm{0.f, 0.f}, ru{0.f, 0.f}, rhp{0.f, 0.f}, rhm{0.f, 0.f};
+  // the run's sums, one df value per lane (even and odd cells of the pairs)
+  const dfl2 z2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  dfl2 ruw = z2, rv = z2, rcp = z2, rcm = z2, ru = z2, rhp = z2, rhm = z2;
   bool any = false;
   auto flush = [&]() {
     const float2 dyw = wgt[jr], hw = wgt[g.ny + jr];
     const dfl dy{dyw.x, dyw.y}, h{hw.x, hw.y};
-    sum[4] = df_add(sum[4], df_add(df_mul(ruw, dy), df_mul(rv, h)));
-    sum[2] = df_add(sum[2], df_mul(rcp, dy));
-    sum[3] = df_add(sum[3], df_mul(rcm, dy));
-    sum[5] = df_add(sum[5], df_mul(rhp, dy));
-    sum[6] = df_add(sum[6], df_mul(rhm, dy));
-    if (jr == 0) sum[0] = df_add(sum[0], ru);
-    if (jr == g.nyc - 1) sum[1] = df_add(sum[1], ru);
-    ruw = rv = rcp = rcm = ru = rhp = rhm = dfl{0.f, 0.f};
+    auto lanes = [](dfl2 x) { return df_add(dfl{x.h.x, x.l.x}, dfl{x.h.y, x.l.y}); };
+    sum[4] = df_add(sum[4], df_add(df_mul(lanes(ruw), dy), df_mul(lanes(rv), h)));
+    sum[2] = df_add(sum[2], df_mul(lanes(rcp), dy));
+    sum[3] = df_add(sum[3], df_mul(lanes(rcm), dy));
+    sum[5] = df_add(sum[5], df_mul(lanes(rhp), dy));
+    sum[6] = df_add(sum[6], df_mul(lanes(rhm), dy));
+    if (jr == 0) sum[0] = df_add(sum[0], lanes(ru));
+    if (jr == g.nyc - 1) sum[1] = df_add(sum[1], lanes(ru));
+    ruw = rv = rcp = rcm = ru = rhp = rhm = z2;
   };
   int r = 0, i = 0;
   bool have = item(0, r, i);
@@ -297,44 +332,53 @@ __global__ void __launch_bounds__(kDiagThreads, 2) k_diag_partial_mixed(Fields<f
     const float2 Hm = s2[13 * kDiagThreads];
     const float2 phu = top ? s2[14 * kDiagThreads] : make_float2(0.f, 0.f);
     const float ue2 = s1[0], phe2 = s1[kDiagThreads];
-    // one cell: its values and the neighbours east (+x), north (+z) and above (+y)
-    auto cell = [&](float u, float ue, float w, float wn, float p, float ph, float phe, float phn, float phu,
-                    float v0, float v1, float Sp, float Lp, float Sm, float Lm, float Hp, float Hm) {
-      if (wall_row) ru = df_add_fast(ru, dfl{u, 0.f});
-      ruw = df_add_fast(ruw, df_add_fast(df_prod(u, u), df_prod(w, w)));
-      rv = df_add_fast(rv, df_prod(v0, v0));
-      rcp = df_add_fast(rcp, dfl{Sp, Lp});
-      rcm = df_add_fast(rcm, dfl{Sm, Lm});
-      // the divergence of the stored fields in df: exact differences (TwoSum),
-      // exact leading products (TwoProduct) and the cross terms with the df
-      // coefficients, the three leading parts summed by TwoSum, the rest in FP32
-      const dfl a1 = df_two_sum(ue, -u), a2 = df_two_sum(v1, -v0), a3 = df_two_sum(wn, -w);
-      const dfl p1 = df_prod(a1.h, idx.h), p2 = df_prod(a2.h, iy.h), p3 = df_prod(a3.h, idz.h);
-      const dfl s1s = df_two_sum(p1.h, p2.h), s2s = df_two_sum(s1s.h, p3.h);
-      float lo = __fadd_rn(__fadd_rn(p1.l, p2.l), p3.l);
-      lo = __fmaf_rn(a1.h, idx.l, lo);
-      lo = __fmaf_rn(a1.l, idx.h, lo);
-      lo = __fmaf_rn(a2.h, iy.l, lo);
-      lo = __fmaf_rn(a2.l, iy.h, lo);
-      lo = __fmaf_rn(a3.h, idz.l, lo);
-      lo = __fmaf_rn(a3.l, idz.h, lo);
-      const float dv = __fadd_rn(s2s.h, __fadd_rn(lo, __fadd_rn(s1s.l, s2s.l)));
-      maxdiv = fmaxf(maxdiv, fabsf(dv));
-      // dv is non-finite when u, ue, v0, v1, w or wn is
-      if (!isfinite(dv) || !isfinite(Sp) || !isfinite(Sm) || !isfinite(p) || !isfinite(ph)) bad += 1.f;
-      cmin = fminf(cmin, fminf(crp + Sp, crm + Sm));
-      maxrate = fmaxf(maxrate, fabsf(0.5f * (u + ue)) * idxh + fabsf(0.5f * (v0 + v1)) * iyw.x +
-                                   fabsf(0.5f * (w + wn)) * idzh);
-      const float dpx = fabsf(phe - ph), dpz = fabsf(phn - ph);
-      const float dpyc = top ? fabsf(dpy + (phu - ph)) : 0.f;
-      maxdphi = fmaxf(maxdphi, fmaxf(fmaxf(dpx, dpz), dpyc));
-      maxmig = fmaxf(maxmig, dpx * idxh * idxh + dpyc * ihy * iyw.x + dpz * idzh * idzh);
-      maxcsum = fmaxf(maxcsum, (crp + Sp) + (crm + Sm));
-      rhp = df_add_fast(rhp, dfl{Hp, 0.f});
-      rhm = df_add_fast(rhm, dfl{Hm, 0.f});
-    };
-    cell(u.x, u.y, w.x, wn.x, p.x, ph.x, ph.y, phn.x, phu.x, v0.x, v1.x, Sp.x, Lp.x, Sm.x, Lm.x, Hp.x, Hm.x);
-    cell(u.y, ue2, w.y, wn.y, p.y, ph.y, phe2, phn.y, phu.y, v0.y, v1.y, Sp.y, Lp.y, Sm.y, Lm.y, Hp.y, Hm.y);
+    // the pair's two cells side by side in packed FP32 (lane x: cell i, lane y:
+    // cell i + 1), with their neighbours east (+x), north (+z) and above (+y)
+    const float2 ue = make_float2(u.y, ue2), phe = make_float2(ph.y, phe2);
+    const float2 m1 = make_float2(-1.f, -1.f), zero = make_float2(0.f, 0.f);
+    if (wall_row) ru = p_add_fast(ru, dfl2{u, zero});
+    ruw = p_add_fast(ruw, p_add_fast(p_prod(u, u), p_prod(w, w)));
+    rv = p_add_fast(rv, p_prod(v0, v0));
+    rcp = p_add_fast(rcp, dfl2{Sp, Lp});
+    rcm = p_add_fast(rcm, dfl2{Sm, Lm});
+    rhp = p_add_fast(rhp, dfl2{Hp, zero});
+    rhm = p_add_fast(rhm, dfl2{Hm, zero});
+    // the divergence of the stored fields in df: exact differences (TwoSum),
+    // exact leading products (TwoProduct) and the cross terms with the df
+    // coefficients, the three leading parts summed by TwoSum, the rest in FP32
+    const float2 iyh = make_float2(iy.h, iy.h), iyl = make_float2(iy.l, iy.l);
+    const dfl2 a1 = p_two_sum(ue, p_mul(u, m1)), a2 = p_two_sum(v1, p_mul(v0, m1)), a3 = p_two_sum(wn, p_mul(w, m1));
+    const dfl2 p1 = p_prod(a1.h, idxh2), p2 = p_prod(a2.h, iyh), p3 = p_prod(a3.h, idzh2);
+    const dfl2 q1 = p_two_sum(p1.h, p2.h), q2 = p_two_sum(q1.h, p3.h);
+    float2 lo = p_add(p_add(p1.l, p2.l), p3.l);
+    lo = p_fma(a1.h, idxl2, lo);
+    lo = p_fma(a1.l, idxh2, lo);
+    lo = p_fma(a2.h, iyl, lo);
+    lo = p_fma(a2.l, iyh, lo);
+    lo = p_fma(a3.h, idzl2, lo);
+    lo = p_fma(a3.l, idzh2, lo);
+    const float2 dv = p_add(q2.h, p_add(lo, p_add(q1.l, q2.l)));
+    maxdiv = fmaxf(maxdiv, fmaxf(fabsf(dv.x), fabsf(dv.y)));
+    // non-finite inputs: x - x is 0 for a finite x and NaN otherwise (dv is
+    // non-finite when u, ue, v0, v1, w or wn is); a cell counts once
+    const float2 nf = p_add(p_add(p_sub(dv, dv), p_sub(Sp, Sp)), p_add(p_add(p_sub(Sm, Sm), p_sub(p, p)), p_sub(ph, ph)));
+    bad += (nf.x != 0.f ? 1.f : 0.f) + (nf.y != 0.f ? 1.f : 0.f);
+    const float2 ctp = p_add(make_float2(crp, crp), Sp), ctm = p_add(make_float2(crm, crm), Sm);
+    cmin = fminf(cmin, fminf(fminf(ctp.x, ctp.y), fminf(ctm.x, ctm.y)));
+    const float2 cs = p_add(ctp, ctm);
+    maxcsum = fmaxf(maxcsum, fmaxf(cs.x, cs.y));
+    const float2 hf = make_float2(0.5f, 0.5f);
+    const float2 rate = p_fma(p_abs(p_mul(hf, p_add(u, ue))), idxh2,
+                              p_fma(p_abs(p_mul(hf, p_add(v0, v1))), make_float2(iyw.x, iyw.x),
+                                    p_mul(p_abs(p_mul(hf, p_add(w, wn))), idzh2)));
+    maxrate = fmaxf(maxrate, fmaxf(rate.x, rate.y));
+    const float2 dpx = p_abs(p_sub(phe, ph)), dpz = p_abs(p_sub(phn, ph));
+    const float2 dpyc = top ? p_abs(p_add(make_float2(dpy, dpy), p_sub(phu, ph))) : zero;
+    maxdphi = fmaxf(maxdphi, fmaxf(fmaxf(fmaxf(dpx.x, dpx.y), fmaxf(dpz.x, dpz.y)), fmaxf(dpyc.x, dpyc.y)));
+    const float2 mig = p_fma(p_mul(dpx, idxh2), idxh2,
+                             p_fma(p_mul(dpyc, make_float2(ihy, ihy)), make_float2(iyw.x, iyw.x),
+                                   p_mul(p_mul(dpz, idzh2), idzh2)));
+    maxmig = fmaxf(maxmig, fmaxf(mig.x, mig.y));
     r = rn;
     i = in;
     have = hn;
