@@ -7,7 +7,8 @@ oracle, element by element on the same seeded state.
   neighbouring tiles in x, the stencil's multi-chunk y-march, three steps;
   under both solve policies (default, and FP64 transforms and solves), under
   every launch shape the autotuner can choose (one code at a time), and under
-  the shapes it chooses for the 256 x 193 x 256 benchmark grid.
+  the shapes it chooses for the 256 x 193 x 256 benchmark grid; and at the
+  full 256 x 193 x 256 in those shapes, the benchmark's own configuration.
   Tolerances: fields 1e-5 of each field's scale (velocities at least the wall
   speed), <u>(y) 1e-4 absolute and the wall shear 1e-4 relative (the stated
   accuracy of the mixed path);
@@ -85,7 +86,7 @@ def _mixed_run(g, prm, ref, cfg=None, policy=0):
     d, dr = s.diagnostics(), o.diagnostics(g, prm, ref)
     tau = max(abs(d["tau_bot"] - dr["tau_bot"]) / abs(dr["tau_bot"]),
               abs(d["tau_top"] - dr["tau_top"]) / abs(dr["tau_top"]))
-    print("mixed 256x65x256 cfg", cfg, "policy", policy, "vs oracle:", errs, "<u>", du, "tau", tau)
+    print(f"mixed {g.nx}x{g.ny}x{g.nz} cfg", cfg, "policy", policy, "vs oracle:", errs, "<u>", du, "tau", tau)
     assert d["status"] == 0
     assert all(e <= 1e-5 for e in errs.values()), (cfg, errs)
     assert du <= 1e-4 and tau <= 1e-4, (cfg, du, tau)
@@ -120,6 +121,36 @@ def test_mixed_under_the_benchmarks_tuned_launch_shapes(mixed_reference):
     s.close()
     assert m.isfinite(sum(cfg))
     g, prm, ref = mixed_reference
+    _mixed_run(g, prm, ref, tuple(cfg))
+
+
+@pytest.fixture(scope="module")
+def full_mixed_reference():
+    """The oracle's three steps at the full 256 x 193 x 256 from the mixed
+    context's initial state."""
+    from paper_1701_02005_gb300 import binding as B
+
+    g, prm, s, st0 = _setup(256, 193, 256, B.PNP_MIXED)
+    s.close()
+    return g, prm, o.step(g, prm, st0, C2["dt"], MIXED_STEPS)
+
+
+def test_mixed_at_the_full_workload_grid_in_the_benchmarks_launch_shapes(full_mixed_reference):
+    """The benchmark's own configuration: 256 x 193 x 256, mixed precision, the
+    launch shapes the autotuner picks for that grid (as bench.py does), three
+    steps against the oracle at the mixed path's tolerances."""
+    import math as m
+
+    from paper_1701_02005_gb300 import autotune
+    from paper_1701_02005_gb300 import binding as B
+    from paper_1701_02005_gb300.solver import Solver
+
+    s = Solver(256, 193, 256, C2["Lx"], C2["Lz"], stretch=C2["stretch"], precision=B.PNP_MIXED)
+    s.set_params(C2["Re"], C2["lam"], C2["Sc"], C2["V"], C2["beta"])
+    cfg, _ = autotune.tune(s, C2["dt"])
+    s.close()
+    assert m.isfinite(sum(cfg))
+    g, prm, ref = full_mixed_reference
     _mixed_run(g, prm, ref, tuple(cfg))
 
 
