@@ -340,6 +340,13 @@ def run_next_rows(args, B, Solver, torch):
     from paper_1701_02005_gb300.solver import profile
 
     s = Solver(WL["nx"], WL["ny"], WL["nz"], WL["Lx"], WL["Lz"], stretch=WL["stretch"], precision=B.PNP_MIXED)
+    try:   # the solver's device memory is released whatever happens below
+        return _next_rows(args, B, s, torch, np, profile)
+    finally:
+        s.close()
+
+
+def _next_rows(args, B, s, torch, np, profile):
     s.set_params(WL["Re"], WL["lam"], WL["Sc"], WL["V"], WL["beta"])
     s.init_state(B.PNP_IC_PB, WL["seed"], WL["amp"])
     dt, K, n = WL["dt"], args.next_steps, cells()
@@ -394,7 +401,6 @@ def run_next_rows(args, B, Solver, torch):
                "check_every": 10, "cfl": 0.5, "dt_max": 2 * dt,
                "time_units_per_s": float(dts.sum()) / (1e-3 * ad["host_ms_per_step"] * len(dts)),
                "time_units_per_s_fixed_dt": dt / (1e-3 * base["ms_per_step"])})
-    s.close()
     return {"workload": WL_NAME + " (mixed, built-in launch shapes)", "steps": K, "default": base,
             "approximate_factorisation": af, "wall_potential_map": wp, "adaptive_dt": ad}
 
